@@ -1,0 +1,234 @@
+/*
+ * pt.h -- C ABI of the GB300 (sm_103a) neural path tracer.
+ *
+ * The library implements the data-parallel hot path of "Towards Neural Path
+ * Tracing in SRAM" (Pupilli 2023): a Monte Carlo path tracer without light
+ * sampling whose environment light is an HDR neural image field (NIF), an
+ * MLP over Fourier-encoded equirect coordinates (Sections 3.1 and 3.2), with
+ * the sampling loop alternating between tracing and batched network
+ * inference (Section 3.3).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are CUDA device pointers owned by the caller; the
+ *    library never frees them.  Pointers without the prefix are host memory,
+ *    read during the call only.  Objects the library creates (pt_ctx,
+ *    pt_scene, pt_nif, pt_cache) own their device memory and are released by
+ *    the matching pt_destroy_* call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls taking a stream are asynchronous and stream-ordered:
+ *    they return after enqueueing work.  Device-side failures (stack or queue
+ *    overflow, non-finite radiance, a bounded wait that gave up) set bits in
+ *    the context's device error word and are reported by pt_check().  No
+ *    kernel traps or asserts.
+ *  - Every call returns a pt_status; on failure pt_last_error() describes it.
+ *    No exception or exit() crosses this boundary.
+ *  - A context is used by one host thread at a time.
+ *
+ * Scene conventions: global primitive IDs number spheres first, then quads,
+ * then triangles.  Closest hits take the smallest t > 0; equal t goes to the
+ * smaller ID.  Materials are rows of 8 floats [albedo r, g, b, roughness,
+ * ior, emission r, g, b] with type 0 Lambertian, 1 GGX metal (F0 = albedo,
+ * alpha = roughness^2), 2 dielectric (tint 1).
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PT_API __attribute__((visibility("default")))
+#else
+#define PT_API
+#endif
+
+typedef enum pt_status {
+    PT_OK = 0,
+    PT_EINVAL = 1,        /* invalid argument or inconsistent description */
+    PT_ENOMEM = 2,        /* host or device allocation failed */
+    PT_ECUDA = 3,         /* a CUDA runtime call failed */
+    PT_EDEVICE = 4,       /* a kernel set bits in the device error word */
+    PT_EUNSUPPORTED = 5   /* valid request this build does not implement */
+} pt_status;
+
+/* arithmetic of the neural image field's hidden layers */
+typedef enum pt_precision {
+    PT_FP32 = 0,          /* FP32 CUDA-core arithmetic (the accuracy reference path) */
+    PT_BF16 = 1,          /* BF16 operands on tcgen05 tensor cores, FP32 accumulation */
+    PT_FP8E4M3 = 2        /* FP8 E4M3 operands on tcgen05 tensor cores, FP32 accumulation */
+} pt_precision;
+
+/* bits of the device error word (pt_check) */
+#define PT_ERR_STACK_OVERFLOW 0x1u   /* BVH traversal stack exhausted */
+#define PT_ERR_QUEUE_OVERFLOW 0x2u   /* a ray or escape queue exceeded its capacity */
+#define PT_ERR_NONFINITE      0x4u   /* a non-finite radiance value was produced */
+#define PT_ERR_TIMEOUT        0x8u   /* a bounded device wait gave up */
+#define PT_ERR_ITER_CAP       0x10u  /* traversal exceeded its iteration cap */
+
+typedef struct pt_ctx pt_ctx;
+typedef struct pt_scene pt_scene;
+typedef struct pt_nif pt_nif;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` (made current for the calling
+   thread).  *out receives the handle; release it with pt_destroy. */
+PT_API pt_status pt_create(pt_ctx** out, int device);
+PT_API void pt_destroy(pt_ctx* ctx);
+
+/* Text of the last failure on this context ("" if none); valid until the
+   next call on the context.  ctx may be NULL for failures of pt_create. */
+PT_API const char* pt_last_error(const pt_ctx* ctx);
+
+/* Synchronise `stream`, then read and clear the device error word into
+   *bits (may be NULL).  Returns PT_EDEVICE if any bit was set, PT_ECUDA if
+   the stream reported a CUDA error. */
+PT_API pt_status pt_check(pt_ctx* ctx, void* stream, uint32_t* bits);
+
+/* ------------------------------------------------------------------------ */
+/* Scenes (Section 3.1.1: the scene description is replicated per core and  */
+/* serialised into one binary chunk; here it is one device arena holding     */
+/* packed BVH nodes and primitive arrays).                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct pt_scene_desc {
+    int64_t n_spheres;
+    const float* spheres;      /* [n_spheres][4]: centre x, y, z, radius */
+    const int32_t* sphere_mat; /* [n_spheres] material index */
+    int64_t n_quads;
+    const float* quads;        /* [n_quads][5]: plane position p, lo_u, hi_u, lo_v, hi_v */
+    const int32_t* quad_axis;  /* [n_quads] plane normal axis a; u = (a+1)%3, v = (a+2)%3 */
+    const int32_t* quad_mat;
+    int64_t n_verts;
+    const float* verts;        /* [n_verts][3] */
+    int64_t n_tris;
+    const int32_t* tris;       /* [n_tris][3] vertex indices */
+    const int32_t* tri_mat;
+    int64_t n_mats;
+    const int32_t* mat_type;   /* [n_mats] 0 Lambertian, 1 GGX metal, 2 dielectric */
+    const float* mats;         /* [n_mats][8] see file header */
+    float camera[10];          /* eye[3], target[3], up[3], vertical fov in degrees */
+    int32_t env_is_nif;        /* 1: environment = NIF passed at render; 0: constant env_rgb */
+    float env_rgb[3];
+} pt_scene_desc;
+
+typedef struct pt_scene_info {
+    int64_t n_prims;
+    int64_t n_nodes;           /* interior BVH nodes (leaves hold one primitive, stored in the parent) */
+    int64_t node_bytes;        /* device bytes of the packed node array */
+    int64_t prim_bytes;        /* device bytes of primitive data */
+    int32_t bvh_depth;         /* longest root-to-leaf path */
+    int32_t has_emission;
+} pt_scene_info;
+
+/* Build the BVH on the host (binned SAH, one primitive per leaf, child boxes
+   stored with fp32 origin and fp16 extent rounded so the box never shrinks,
+   Section 3.1.4), pack it for 128-bit loads and upload.  Host arrays are
+   read during the call only.  Fails with PT_EINVAL on out-of-range indices,
+   non-finite coordinates or extents beyond the fp16 range. */
+PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* desc, pt_scene** out);
+PT_API void pt_destroy_scene(pt_scene* scene);
+PT_API pt_status pt_scene_get_info(const pt_scene* scene, pt_scene_info* info);
+
+/* Copy the packed BVH back to the host for inspection: nodes as 12 uint32
+   per node (see the packing in the library source), root reference in
+   *root.  Either buffer may be NULL; sizes come from pt_scene_get_info. */
+PT_API pt_status pt_scene_download_bvh(pt_ctx* ctx, const pt_scene* scene, uint32_t* nodes, uint32_t* root);
+
+/* ------------------------------------------------------------------------ */
+/* Neural image field (Section 3.2): (u, v) -> F Gaussian Fourier           */
+/* frequencies as [sin 2 pi Bx (F), cos 2 pi Bx (F)] -> L dense ReLU layers  */
+/* of width H -> linear layer to 3 -> fixed 3x3 colour matrix M -> exp.     */
+/* ------------------------------------------------------------------------ */
+typedef struct pt_nif_desc {
+    int32_t n_freq;            /* F */
+    int32_t hidden;            /* H */
+    int32_t n_hidden_layers;   /* L (1..8) */
+    const float* params;       /* host, flat: B[F][2], then per layer W[out][in], b[out], then M[3][3] */
+} pt_nif_desc;
+
+/* Upload FP32 master weights and build the BF16 / FP8 operand images used by
+   the tensor-core kernel (when the shape is F = 64, H = 128, L = 3). */
+PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* desc, pt_nif** out);
+PT_API void pt_destroy_nif(pt_nif* nif);
+/* number of floats in the flat layout */
+PT_API int64_t pt_nif_param_count(const pt_nif* nif);
+/* Download the current FP32 master weights in the flat layout (host buffer
+   of pt_nif_param_count floats).  Synchronises the context's device. */
+PT_API pt_status pt_nif_get_params(pt_ctx* ctx, const pt_nif* nif, float* params);
+
+/* Evaluate the NIF at n coordinates: d_uv [n][2] float -> d_rgb [n][3]
+   float, in the requested precision.  PT_EUNSUPPORTED for a tensor-core
+   precision on a shape other than F = 64, H = 128, L = 3. */
+PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nif, int32_t precision, int64_t n, const float* d_uv,
+                             float* d_rgb, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Rendering (Section 3.1: paths without light sampling; radiance gathered   */
+/* at emitters and at escapes, where the NIF is queried; Section 3.3).       */
+/* ------------------------------------------------------------------------ */
+typedef struct pt_render_cfg {
+    int32_t width, height;     /* image size; pixel index = y * width + x */
+    int32_t spp;               /* samples (paths) per pixel */
+    int32_t max_depth;         /* surface interactions per path; rays leaving vertex max_depth are not traced */
+    uint32_t seed;             /* Philox key word 0 (key word 1 = stream tag 0) */
+    int32_t rr;                /* 1: Russian roulette from vertex rr_start, continue prob min(1, max tp) */
+    int32_t rr_start;
+    int32_t precision;         /* pt_precision of the NIF at escapes */
+    int64_t chunk_slots;       /* paths per wavefront chunk; 0 = automatic; rounded to whole samples */
+} pt_render_cfg;
+
+/* Render the image: d_image [height][width][3] float, the mean over spp
+   paths of each pixel.  Path (pixel p, sample s) draws Philox-4x32-10 words
+   with key (seed, 0) and counter (p, s, k, 0) at vertex k (k = 0 for the
+   camera jitter).  `nif` is required when the scene's environment is a NIF
+   and ignored otherwise. */
+PT_API pt_status pt_render(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, const pt_render_cfg* cfg,
+                           float* d_image, void* stream);
+
+/* Render all spp paths of a list of pixels.  d_pixels: [n_pix] int64 pixel
+   indices (NULL = all width*height pixels in order).  Outputs: d_pixel_rgb
+   [n_pix][3] mean radiance; d_slot_rgb (nullable) [spp][n_pix][3] radiance
+   of each path; d_hit_ids (nullable) [spp][n_pix][max_depth] int32 primitive
+   hit at each vertex, -1 for an escape, -2 when not traced. */
+PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, const pt_render_cfg* cfg,
+                                  int64_t n_pix, const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb,
+                                  int32_t* d_hit_ids, void* stream);
+
+/* Statistics of the last pt_render / pt_render_pixels call on this context
+   (valid after pt_check): rays traced per vertex and escapes shaded by the
+   NIF.  counts: [max_depth + 1] int64 -> counts[k-1] = rays traced at vertex
+   k, counts[max_depth] = NIF evaluations. */
+PT_API pt_status pt_last_render_counts(pt_ctx* ctx, int64_t* counts, int32_t n);
+
+/* ------------------------------------------------------------------------ */
+/* Building blocks of the same path, exposed for testing and for callers    */
+/* that stream their own rays (Section 3.1.2).                               */
+/* ------------------------------------------------------------------------ */
+
+/* Philox-4x32-10 (Salmon et al. 2011): d_ctr [n][4] counters with key
+   (seed, tag) -> d_out [n][4] words. */
+PT_API pt_status pt_philox(pt_ctx* ctx, uint32_t seed, uint32_t tag, int64_t n, const uint32_t* d_ctr,
+                           uint32_t* d_out, void* stream);
+
+/* Camera rays of slots [first_slot, first_slot + n) where slot = s * W * H +
+   p: d_org, d_dir [n][3] float (directions unit length). */
+PT_API pt_status pt_primary_rays(pt_ctx* ctx, const pt_scene* scene, const pt_render_cfg* cfg, int64_t first_slot,
+                                 int64_t n, float* d_org, float* d_dir, void* stream);
+
+/* Closest hit of n rays through the packed BVH: d_org, d_dir [n][3] float
+   (directions need not be normalised for triangles and quads; spheres
+   assume unit length) -> d_t [n] (INFINITY on a miss), d_prim [n] int32
+   (-1 on a miss). */
+PT_API pt_status pt_trace_rays(pt_ctx* ctx, const pt_scene* scene, int64_t n, const float* d_org, const float* d_dir,
+                               float* d_t, int32_t* d_prim, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PT_H */

@@ -1,0 +1,609 @@
+// C ABI of the path tracer (include/pt.h): argument checking, device
+// memory of scenes / networks / wavefront scratch, and the render loop that
+// alternates traversal-and-shading steps with batched NIF evaluation
+// (Section 3.3).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "pt_internal.h"
+
+using namespace ptk;
+
+struct pt_ctx {
+    int device = 0;
+    int sm_count = 0;
+    std::string last_error;
+    uint32_t* d_err = nullptr;
+    // wavefront scratch
+    uint32_t chunk_cap = 0;
+    RayQueue q[2] = {};
+    EscapeRec* esc = nullptr;
+    float* slot_L = nullptr;
+    uint32_t* counters = nullptr;          // [kCounters]
+    unsigned long long* stats = nullptr;   // [kMaxDepth + 1]
+    int last_depth = 0;
+};
+
+struct pt_scene {
+    pt_ctx* ctx = nullptr;
+    DevScene dev = {};
+    pt_scene_info info = {};
+    std::vector<void*> allocs;
+};
+
+struct pt_nif {
+    pt_ctx* ctx = nullptr;
+    int32_t F = 0, H = 0, L = 0;
+    int64_t n_params = 0;
+    float* d_params = nullptr;   // flat FP32 master weights
+    float* d_fp32 = nullptr;     // packed FP32 layout (Wt, bias, Wout, bout)
+    DevNif dev = {};
+};
+
+namespace {
+
+constexpr int kMaxDepth = 64;
+constexpr int kCounters = kMaxDepth + 8;
+constexpr int kEscCounter = kMaxDepth + 2;
+
+pt_status fail(pt_ctx* ctx, pt_status st, const std::string& msg)
+{
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+pt_status cuda_fail(pt_ctx* ctx, cudaError_t e, const char* what)
+{
+    return fail(ctx, PT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define PT_CUDA(call)                                      \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+void free_scratch(pt_ctx* ctx)
+{
+    for (auto& q : ctx->q) {
+        cudaFree(q.o); cudaFree(q.d); cudaFree(q.tp); cudaFree(q.L);
+        q = RayQueue{};
+    }
+    cudaFree(ctx->esc); ctx->esc = nullptr;
+    cudaFree(ctx->slot_L); ctx->slot_L = nullptr;
+    ctx->chunk_cap = 0;
+}
+
+pt_status ensure_scratch(pt_ctx* ctx, uint32_t chunk)
+{
+    if (ctx->chunk_cap >= chunk) return PT_OK;
+    free_scratch(ctx);
+    for (auto& q : ctx->q) {
+        if (dalloc(&q.o, chunk) || dalloc(&q.d, chunk) || dalloc(&q.tp, chunk) || dalloc(&q.L, chunk)) {
+            free_scratch(ctx);
+            return fail(ctx, PT_ENOMEM, "wavefront queue allocation failed");
+        }
+    }
+    if (dalloc(&ctx->esc, chunk) || dalloc(&ctx->slot_L, (size_t)chunk * 3)) {
+        free_scratch(ctx);
+        return fail(ctx, PT_ENOMEM, "escape queue allocation failed");
+    }
+    ctx->chunk_cap = chunk;
+    return PT_OK;
+}
+
+bool finite3(const float* p, int64_t n)
+{
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+void camera_basis(const float cam[10], DevScene& d)
+{
+    const double eye[3] = {cam[0], cam[1], cam[2]};
+    double f[3] = {cam[3] - eye[0], cam[4] - eye[1], cam[5] - eye[2]};
+    const double up[3] = {cam[6], cam[7], cam[8]};
+    double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    for (double& x : f) x /= fl;
+    double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+    double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    for (double& x : r) x /= rl;
+    const double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+    for (int a = 0; a < 3; ++a) {
+        d.eye[a] = (float)eye[a];
+        d.fwd[a] = (float)f[a];
+        d.right[a] = (float)r[a];
+        d.up[a] = (float)u[a];
+    }
+    d.tan_half = (float)std::tan(0.5 * (double)cam[9] * 3.14159265358979323846 / 180.0);
+    d.aspect = 1.f;
+}
+
+pt_status check_cfg(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, const pt_render_cfg* cfg)
+{
+    if (!ctx || !scene || !cfg) return fail(ctx, PT_EINVAL, "null argument");
+    if (cfg->width < 1 || cfg->height < 1 || cfg->spp < 1) return fail(ctx, PT_EINVAL, "image size and spp must be >= 1");
+    if (cfg->max_depth < 1 || cfg->max_depth > kMaxDepth) return fail(ctx, PT_EINVAL, "max_depth must be in [1, 64]");
+    if ((int64_t)cfg->width * cfg->height > (1ll << 31)) return fail(ctx, PT_EINVAL, "image too large");
+    if (cfg->rr && cfg->rr_start < 1) return fail(ctx, PT_EINVAL, "rr_start must be >= 1");
+    if (scene->dev.env_is_nif && !nif) return fail(ctx, PT_EINVAL, "scene environment is a NIF but no NIF was given");
+    if (cfg->precision != PT_FP32 && cfg->precision != PT_BF16 && cfg->precision != PT_FP8E4M3)
+        return fail(ctx, PT_EINVAL, "unknown precision");
+    return PT_OK;
+}
+
+pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, cudaStream_t s)
+{
+    NifEvalParams p = {};
+    p.nif = nif->dev;
+    p.esc = ctx->esc;
+    p.esc_count = ctx->counters + kEscCounter;
+    p.esc_cap = ctx->chunk_cap;
+    p.slot_L = ctx->slot_L;
+    p.err = ctx->d_err;
+    p.stats = ctx->stats + ctx->last_depth;
+    if (precision == PT_FP32) {
+        PT_CUDA(launch_nif_fp32(p, 1, ctx->sm_count, s));
+        return PT_OK;
+    }
+    return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF precision not available in this build");
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+PT_API pt_status pt_create(pt_ctx** out, int device)
+{
+    if (!out) return PT_EINVAL;
+    *out = nullptr;
+    pt_ctx* ctx = new pt_ctx();
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->counters, kCounters * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->stats, (kMaxDepth + 1) * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, (kMaxDepth + 1) * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(ctx->d_err);
+        cudaFree(ctx->counters);
+        cudaFree(ctx->stats);
+        delete ctx;
+        return PT_ECUDA;
+    }
+    *out = ctx;
+    return PT_OK;
+}
+
+PT_API void pt_destroy(pt_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    free_scratch(ctx);
+    cudaFree(ctx->d_err);
+    cudaFree(ctx->counters);
+    cudaFree(ctx->stats);
+    delete ctx;
+}
+
+PT_API const char* pt_last_error(const pt_ctx* ctx)
+{
+    if (!ctx) return "no context (pt_create failed or was not called)";
+    return ctx->last_error.c_str();
+}
+
+PT_API pt_status pt_check(pt_ctx* ctx, void* stream, uint32_t* bits)
+{
+    if (!ctx) return PT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    PT_CUDA(cudaStreamSynchronize(s));
+    PT_CUDA(cudaGetLastError());
+    uint32_t h = 0;
+    PT_CUDA(cudaMemcpy(&h, ctx->d_err, sizeof(h), cudaMemcpyDeviceToHost));
+    PT_CUDA(cudaMemset(ctx->d_err, 0, sizeof(uint32_t)));
+    if (bits) *bits = h;
+    if (h) {
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "device error word 0x%x", h);
+        return fail(ctx, PT_EDEVICE, buf);
+    }
+    return PT_OK;
+}
+
+// ---------------------------------------------------------------------------
+PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene** out)
+{
+    if (!ctx || !d || !out) return fail(ctx, PT_EINVAL, "null argument");
+    *out = nullptr;
+    if (d->n_spheres < 0 || d->n_quads < 0 || d->n_tris < 0 || d->n_verts < 0 || d->n_mats < 1)
+        return fail(ctx, PT_EINVAL, "negative counts or no materials");
+    const int64_t nS = d->n_spheres, nQ = d->n_quads, nT = d->n_tris, nP = nS + nQ + nT;
+    if (nP >= (int64_t)kLeafBit - 1) return fail(ctx, PT_EINVAL, "too many primitives");
+    if ((nS && (!d->spheres || !d->sphere_mat)) || (nQ && (!d->quads || !d->quad_axis || !d->quad_mat)) ||
+        (nT && (!d->tris || !d->tri_mat || !d->verts)) || !d->mat_type || !d->mats)
+        return fail(ctx, PT_EINVAL, "missing primitive arrays");
+    if (!finite3(d->spheres, 4 * nS) || !finite3(d->quads, 5 * nQ) || !finite3(d->verts, 3 * d->n_verts) ||
+        !finite3(d->mats, 8 * d->n_mats) || !finite3(d->camera, 10))
+        return fail(ctx, PT_EINVAL, "non-finite scene values");
+    for (int64_t i = 0; i < d->n_mats; ++i)
+        if (d->mat_type[i] < 0 || d->mat_type[i] > 2) return fail(ctx, PT_EINVAL, "unknown material type");
+    auto bad_mat = [&](const int32_t* m, int64_t n) {
+        for (int64_t i = 0; i < n; ++i)
+            if (m[i] < 0 || m[i] >= d->n_mats) return true;
+        return false;
+    };
+    if (bad_mat(d->sphere_mat, nS) || bad_mat(d->quad_mat, nQ) || bad_mat(d->tri_mat, nT))
+        return fail(ctx, PT_EINVAL, "material index out of range");
+    for (int64_t i = 0; i < nQ; ++i)
+        if (d->quad_axis[i] < 0 || d->quad_axis[i] > 2) return fail(ctx, PT_EINVAL, "quad axis out of range");
+    for (int64_t i = 0; i < 3 * nT; ++i)
+        if (d->tris[i] < 0 || d->tris[i] >= d->n_verts) return fail(ctx, PT_EINVAL, "triangle vertex index out of range");
+    for (int64_t i = 0; i < nS; ++i)
+        if (!(d->spheres[4 * i + 3] > 0.f)) return fail(ctx, PT_EINVAL, "sphere radius must be > 0");
+
+    // primitive bounds, centroids, device records
+    BuildInput bin;
+    bin.n_prims = nP;
+    bin.lo.resize(3 * nP);
+    bin.hi.resize(3 * nP);
+    bin.cen.resize(3 * nP);
+    std::vector<float4> sph(nS), quad(2 * nQ), tri(3 * nT);
+    std::vector<int32_t> pmat(nP);
+    for (int64_t i = 0; i < nS; ++i) {
+        const float* s = d->spheres + 4 * i;
+        sph[i] = make_float4(s[0], s[1], s[2], s[3]);
+        for (int a = 0; a < 3; ++a) {
+            // float bounds that contain the exact sphere
+            bin.lo[3 * i + a] = std::nextafter(s[a] - s[3], -INFINITY);
+            bin.hi[3 * i + a] = std::nextafter(s[a] + s[3], INFINITY);
+        }
+        pmat[i] = d->sphere_mat[i];
+    }
+    for (int64_t i = 0; i < nQ; ++i) {
+        const float* q = d->quads + 5 * i;
+        const int a = d->quad_axis[i], u = (a + 1) % 3, v = (a + 2) % 3;
+        int32_t ab = a;
+        float abf;
+        std::memcpy(&abf, &ab, 4);
+        quad[2 * i] = make_float4(q[0], q[1], q[2], q[3]);
+        quad[2 * i + 1] = make_float4(q[4], abf, 0.f, 0.f);
+        const int64_t g = nS + i;
+        bin.lo[3 * g + a] = bin.hi[3 * g + a] = q[0];
+        bin.lo[3 * g + u] = q[1]; bin.hi[3 * g + u] = q[2];
+        bin.lo[3 * g + v] = q[3]; bin.hi[3 * g + v] = q[4];
+        pmat[g] = d->quad_mat[i];
+    }
+    for (int64_t i = 0; i < nT; ++i) {
+        const int64_t g = nS + nQ + i;
+        for (int k = 0; k < 3; ++k) {
+            const float* p = d->verts + 3 * (int64_t)d->tris[3 * i + k];
+            tri[3 * i + k] = make_float4(p[0], p[1], p[2], 0.f);
+            for (int a = 0; a < 3; ++a) {
+                if (k == 0) { bin.lo[3 * g + a] = p[a]; bin.hi[3 * g + a] = p[a]; }
+                bin.lo[3 * g + a] = std::min(bin.lo[3 * g + a], p[a]);
+                bin.hi[3 * g + a] = std::max(bin.hi[3 * g + a], p[a]);
+            }
+        }
+        pmat[g] = d->tri_mat[i];
+    }
+    for (int64_t i = 0; i < nP; ++i)
+        for (int a = 0; a < 3; ++a) bin.cen[3 * i + a] = 0.5f * (bin.lo[3 * i + a] + bin.hi[3 * i + a]);
+    BuildOutput bo;
+    if (!build_bvh(bin, bo)) return fail(ctx, PT_EINVAL, bo.error);
+    if (bo.depth > kStackSize) return fail(ctx, PT_EUNSUPPORTED, "BVH deeper than the traversal stack");
+
+    std::vector<float4> mat(2 * d->n_mats);
+    int has_em = 0;
+    for (int64_t i = 0; i < d->n_mats; ++i) {
+        const float* m = d->mats + 8 * i;
+        mat[2 * i] = make_float4(m[0], m[1], m[2], m[3]);
+        mat[2 * i + 1] = make_float4(m[4], m[5], m[6], m[7]);
+        if (m[5] != 0.f || m[6] != 0.f || m[7] != 0.f) has_em = 1;
+    }
+
+    pt_scene* sc = new pt_scene();
+    sc->ctx = ctx;
+    auto upload = [&](const void* src, size_t bytes, void** dst) -> bool {
+        if (cudaMalloc(dst, bytes ? bytes : 16) != cudaSuccess) return false;
+        sc->allocs.push_back(*dst);
+        return bytes == 0 || cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    void *dn, *ds, *dq, *dt, *dpm, *dm, *dmt;
+    bool ok = upload(bo.nodes.data(), bo.nodes.size() * sizeof(PackedNode), &dn) &&
+              upload(sph.data(), sph.size() * sizeof(float4), &ds) &&
+              upload(quad.data(), quad.size() * sizeof(float4), &dq) &&
+              upload(tri.data(), tri.size() * sizeof(float4), &dt) &&
+              upload(pmat.data(), pmat.size() * sizeof(int32_t), &dpm) &&
+              upload(mat.data(), mat.size() * sizeof(float4), &dm) &&
+              upload(d->mat_type, d->n_mats * sizeof(int32_t), &dmt);
+    if (!ok) {
+        pt_destroy_scene(sc);
+        return fail(ctx, PT_ENOMEM, "scene upload failed");
+    }
+    DevScene& v = sc->dev;
+    v.nodes = (const uint4*)dn;
+    v.root = bo.root;
+    v.nS = (uint32_t)nS; v.nQ = (uint32_t)nQ; v.nT = (uint32_t)nT;
+    v.sph = (const float4*)ds; v.quad = (const float4*)dq; v.tri = (const float4*)dt;
+    v.prim_mat = (const int32_t*)dpm; v.mat = (const float4*)dm; v.mat_type = (const int32_t*)dmt;
+    camera_basis(d->camera, v);
+    v.env_is_nif = d->env_is_nif ? 1 : 0;
+    for (int a = 0; a < 3; ++a) v.env[a] = d->env_rgb[a];
+    v.has_emission = has_em;
+    sc->info.n_prims = nP;
+    sc->info.n_nodes = (int64_t)bo.nodes.size();
+    sc->info.node_bytes = (int64_t)(bo.nodes.size() * sizeof(PackedNode));
+    sc->info.prim_bytes = (int64_t)((sph.size() + quad.size() + tri.size()) * sizeof(float4) + pmat.size() * 4);
+    sc->info.bvh_depth = bo.depth;
+    sc->info.has_emission = has_em;
+    *out = sc;
+    return PT_OK;
+}
+
+PT_API void pt_destroy_scene(pt_scene* sc)
+{
+    if (!sc) return;
+    for (void* p : sc->allocs) cudaFree(p);
+    delete sc;
+}
+
+PT_API pt_status pt_scene_get_info(const pt_scene* sc, pt_scene_info* info)
+{
+    if (!sc || !info) return PT_EINVAL;
+    *info = sc->info;
+    return PT_OK;
+}
+
+PT_API pt_status pt_scene_download_bvh(pt_ctx* ctx, const pt_scene* sc, uint32_t* nodes, uint32_t* root)
+{
+    if (!ctx || !sc) return fail(ctx, PT_EINVAL, "null argument");
+    if (root) *root = sc->dev.root;
+    if (nodes && sc->info.n_nodes)
+        PT_CUDA(cudaMemcpy(nodes, sc->dev.nodes, sc->info.node_bytes, cudaMemcpyDeviceToHost));
+    return PT_OK;
+}
+
+// ---------------------------------------------------------------------------
+PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
+{
+    if (!ctx || !d || !out || !d->params) return fail(ctx, PT_EINVAL, "null argument");
+    *out = nullptr;
+    const int F = d->n_freq, H = d->hidden, L = d->n_hidden_layers;
+    if (F < 1 || 2 * F > 128 || H < 1 || H > 128 || L < 1 || L > 8)
+        return fail(ctx, PT_EUNSUPPORTED, "NIF shape outside 2F <= 128, H <= 128, 1 <= L <= 8");
+    int64_t n = 2 * F;
+    for (int l = 0; l <= L; ++l) {
+        const int in = l == 0 ? 2 * F : H, o = l == L ? 3 : H;
+        n += (int64_t)in * o + o;
+    }
+    n += 9;
+    if (!finite3(d->params, n)) return fail(ctx, PT_EINVAL, "non-finite NIF parameters");
+    // FP32 packed layout
+    const size_t fp32_floats = (size_t)L * 128 * 128 + (size_t)L * 128 + 3 * 128 + 3 + 2 * F;
+    std::vector<float> pk(fp32_floats, 0.f);
+    float* Wt = pk.data();
+    float* bias = Wt + (size_t)L * 128 * 128;
+    float* Wout = bias + (size_t)L * 128;
+    float* bout = Wout + 3 * 128;
+    float* Bc = bout + 3;
+    const float* p = d->params;
+    for (int i = 0; i < 2 * F; ++i) Bc[i] = *p++;
+    for (int l = 0; l <= L; ++l) {
+        const int in = l == 0 ? 2 * F : H, o = l == L ? 3 : H;
+        if (l < L) {
+            for (int j = 0; j < o; ++j)
+                for (int k = 0; k < in; ++k) Wt[(size_t)l * 128 * 128 + (size_t)k * 128 + j] = p[(size_t)j * in + k];
+            p += (size_t)in * o;
+            for (int j = 0; j < o; ++j) bias[l * 128 + j] = p[j];
+            p += o;
+        } else {
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < in; ++k) Wout[j * 128 + k] = p[(size_t)j * in + k];
+            p += (size_t)in * 3;
+            for (int j = 0; j < 3; ++j) bout[j] = p[j];
+            p += 3;
+        }
+    }
+    pt_nif* nf = new pt_nif();
+    nf->ctx = ctx;
+    nf->F = F; nf->H = H; nf->L = L; nf->n_params = n;
+    if (cudaMalloc((void**)&nf->d_params, n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&nf->d_fp32, fp32_floats * sizeof(float)) != cudaSuccess) {
+        pt_destroy_nif(nf);
+        return fail(ctx, PT_ENOMEM, "NIF allocation failed");
+    }
+    if (cudaMemcpy(nf->d_params, d->params, n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(nf->d_fp32, pk.data(), fp32_floats * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+        pt_destroy_nif(nf);
+        return fail(ctx, PT_ECUDA, "NIF upload failed");
+    }
+    DevNif& v = nf->dev;
+    v.F = F; v.H = H; v.L = L;
+    v.Wt = nf->d_fp32;
+    v.bias = nf->d_fp32 + (size_t)L * 128 * 128;
+    v.Wout = v.bias + (size_t)L * 128;
+    v.bout = v.Wout + 3 * 128;
+    v.B = v.bout + 3;
+    for (int i = 0; i < 9; ++i) v.M[i] = d->params[n - 9 + i];
+    *out = nf;
+    return PT_OK;
+}
+
+PT_API void pt_destroy_nif(pt_nif* nf)
+{
+    if (!nf) return;
+    cudaFree(nf->d_params);
+    cudaFree(nf->d_fp32);
+    delete nf;
+}
+
+PT_API int64_t pt_nif_param_count(const pt_nif* nf) { return nf ? nf->n_params : 0; }
+
+PT_API pt_status pt_nif_get_params(pt_ctx* ctx, const pt_nif* nf, float* params)
+{
+    if (!ctx || !nf || !params) return fail(ctx, PT_EINVAL, "null argument");
+    PT_CUDA(cudaDeviceSynchronize());
+    PT_CUDA(cudaMemcpy(params, nf->d_params, nf->n_params * sizeof(float), cudaMemcpyDeviceToHost));
+    return PT_OK;
+}
+
+PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, int64_t n, const float* d_uv,
+                             float* d_rgb, void* stream)
+{
+    if (!ctx || !nf || n < 0 || (n > 0 && (!d_uv || !d_rgb))) return fail(ctx, PT_EINVAL, "bad argument");
+    if (n == 0) return PT_OK;
+    NifEvalParams p = {};
+    p.nif = nf->dev;
+    p.uv = d_uv;
+    p.rgb = d_rgb;
+    p.n = n;
+    p.err = ctx->d_err;
+    if (precision == PT_FP32) {
+        PT_CUDA(launch_nif_fp32(p, 0, ctx->sm_count, (cudaStream_t)stream));
+        return PT_OK;
+    }
+    if (precision == PT_BF16 || precision == PT_FP8E4M3)
+        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF precision not available in this build");
+    return fail(ctx, PT_EINVAL, "unknown precision");
+}
+
+// ---------------------------------------------------------------------------
+PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
+                                  int64_t n_pix, const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb,
+                                  int32_t* d_hit_ids, void* stream)
+{
+    pt_status st = check_cfg(ctx, sc, nf, cfg);
+    if (st != PT_OK) return st;
+    const int64_t WH = (int64_t)cfg->width * cfg->height;
+    if (!d_pixels) n_pix = WH;
+    if (n_pix < 0 || (n_pix > 0 && !d_pixel_rgb)) return fail(ctx, PT_EINVAL, "bad pixel list or output");
+    if (n_pix == 0) return PT_OK;
+    const int64_t n_slots = n_pix * (int64_t)cfg->spp;
+    if (n_slots > 0xFFFFFFFFll) return fail(ctx, PT_EINVAL, "more than 2^32 - 1 paths in one call");
+    if (sc->dev.env_is_nif && cfg->precision != PT_FP32)
+        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF precision not available in this build");
+    cudaStream_t s = (cudaStream_t)stream;
+    // chunk = whole samples
+    int64_t chunk = cfg->chunk_slots > 0 ? cfg->chunk_slots : (int64_t)1 << 24;
+    chunk = std::max<int64_t>(n_pix, (chunk / n_pix) * n_pix);
+    chunk = std::min(chunk, n_slots);
+    if (chunk > 0x7FFFFFFFll) chunk = (0x7FFFFFFFll / n_pix) * n_pix;
+    st = ensure_scratch(ctx, (uint32_t)chunk);
+    if (st != PT_OK) return st;
+    ctx->last_depth = cfg->max_depth;
+    PT_CUDA(cudaMemsetAsync(ctx->stats, 0, (kMaxDepth + 1) * sizeof(unsigned long long), s));
+    if (d_hit_ids) PT_CUDA(launch_fill_i32(d_hit_ids, n_slots * cfg->max_depth, -2, s));
+
+    BounceParams bp = {};
+    bp.sc = sc->dev;
+    bp.sc.aspect = (float)((double)cfg->width / (double)cfg->height);
+    bp.max_depth = cfg->max_depth;
+    bp.rr = cfg->rr;
+    bp.rr_start = cfg->rr_start;
+    bp.seed = cfg->seed;
+    bp.n_pix = (uint32_t)n_pix;
+    bp.pixels = d_pixels;
+    bp.W = cfg->width;
+    bp.H = cfg->height;
+    bp.esc = ctx->esc;
+    bp.esc_count = ctx->counters + kEscCounter;
+    bp.slot_L = ctx->slot_L;
+    bp.hit_ids = d_hit_ids;
+    bp.err = ctx->d_err;
+    bp.stats = ctx->stats;
+    bp.cap = (uint32_t)chunk;
+    const int64_t n_chunks = (n_slots + chunk - 1) / chunk;
+    for (int64_t c = 0; c < n_chunks; ++c) {
+        const int64_t first = c * chunk;
+        const int64_t n = std::min(chunk, n_slots - first);
+        PT_CUDA(cudaMemsetAsync(ctx->counters, 0, kCounters * sizeof(uint32_t), s));
+        bp.chunk_first = (uint64_t)first;
+        bp.n_chunk = (uint32_t)n;
+        for (int k = 1; k <= cfg->max_depth; ++k) {
+            bp.k = k;
+            bp.qin = ctx->q[(k + 1) & 1];
+            bp.qout = ctx->q[k & 1];
+            bp.count_in = ctx->counters + (k - 1);
+            bp.count_out = ctx->counters + k;
+            PT_CUDA(launch_bounce(bp, ctx->sm_count, s));
+        }
+        if (sc->dev.env_is_nif) {
+            st = eval_nif_escapes(ctx, nf, cfg->precision, s);
+            if (st != PT_OK) return st;
+        }
+        const float scale = (c == n_chunks - 1) ? (float)(1.0 / cfg->spp) : 1.f;
+        PT_CUDA(launch_reduce(ctx->slot_L, d_pixel_rgb, (uint32_t)n_pix, (uint32_t)(n / n_pix), c == 0, scale, s));
+        if (d_slot_rgb)
+            PT_CUDA(cudaMemcpyAsync(d_slot_rgb + 3 * first, ctx->slot_L, (size_t)n * 3 * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, s));
+    }
+    return PT_OK;
+}
+
+PT_API pt_status pt_render(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
+                           float* d_image, void* stream)
+{
+    if (!d_image) return fail(ctx, PT_EINVAL, "null image");
+    return pt_render_pixels(ctx, sc, nf, cfg, 0, nullptr, d_image, nullptr, nullptr, stream);
+}
+
+PT_API pt_status pt_last_render_counts(pt_ctx* ctx, int64_t* counts, int32_t n)
+{
+    if (!ctx || !counts || n < 0) return fail(ctx, PT_EINVAL, "bad argument");
+    std::vector<unsigned long long> h(kMaxDepth + 1);
+    PT_CUDA(cudaDeviceSynchronize());
+    PT_CUDA(cudaMemcpy(h.data(), ctx->stats, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    const int D = ctx->last_depth;
+    for (int i = 0; i < n; ++i) counts[i] = (i < D) ? (int64_t)h[i] : (i == D ? (int64_t)h[D] : 0);
+    return PT_OK;
+}
+
+// ---------------------------------------------------------------------------
+PT_API pt_status pt_philox(pt_ctx* ctx, uint32_t seed, uint32_t tag, int64_t n, const uint32_t* d_ctr, uint32_t* d_out,
+                           void* stream)
+{
+    if (!ctx || n < 0 || (n > 0 && (!d_ctr || !d_out))) return fail(ctx, PT_EINVAL, "bad argument");
+    PT_CUDA(launch_philox(seed, tag, n, d_ctr, d_out, (cudaStream_t)stream));
+    return PT_OK;
+}
+
+PT_API pt_status pt_primary_rays(pt_ctx* ctx, const pt_scene* sc, const pt_render_cfg* cfg, int64_t first_slot,
+                                 int64_t n, float* d_org, float* d_dir, void* stream)
+{
+    if (!ctx || !sc || !cfg || n < 0 || first_slot < 0 || (n > 0 && (!d_org || !d_dir)))
+        return fail(ctx, PT_EINVAL, "bad argument");
+    if (cfg->width < 1 || cfg->height < 1) return fail(ctx, PT_EINVAL, "image size must be >= 1");
+    DevScene v = sc->dev;
+    v.aspect = (float)((double)cfg->width / (double)cfg->height);
+    PT_CUDA(launch_primary(v, cfg->width, cfg->height, cfg->seed, first_slot, n, d_org, d_dir, (cudaStream_t)stream));
+    return PT_OK;
+}
+
+PT_API pt_status pt_trace_rays(pt_ctx* ctx, const pt_scene* sc, int64_t n, const float* d_org, const float* d_dir,
+                               float* d_t, int32_t* d_prim, void* stream)
+{
+    if (!ctx || !sc || n < 0 || (n > 0 && (!d_org || !d_dir || !d_t || !d_prim)))
+        return fail(ctx, PT_EINVAL, "bad argument");
+    PT_CUDA(launch_trace_rays(sc->dev, n, d_org, d_dir, d_t, d_prim, ctx->d_err, (cudaStream_t)stream));
+    return PT_OK;
+}
+
+}  // extern "C"

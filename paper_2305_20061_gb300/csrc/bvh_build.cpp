@@ -1,0 +1,211 @@
+// Host BVH builder: binned SAH, one primitive per leaf, nodes packed for the
+// device with the two children's boxes stored in the parent.
+//
+// Section 3.1.4 builds a BVH-2 on the host, compacts it into pointer-less
+// nodes with the first child stored next in the array, and stores box
+// extents in fp16 with a rounding that never shrinks the box.  The layout
+// here keeps those three properties (depth-first order, so an interior left
+// child is the next node; fp32 origin + fp16 extent rounded up) but places
+// both child boxes in the parent so one node fetch tests two boxes.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cuda_fp16.h>
+
+#include "pt_internal.h"
+
+namespace ptk {
+
+namespace {
+
+struct Box {
+    float lo[3] = {INFINITY, INFINITY, INFINITY};
+    float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    void grow(const float* l, const float* h)
+    {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], l[a]);
+            hi[a] = std::max(hi[a], h[a]);
+        }
+    }
+    void grow(const Box& b) { grow(b.lo, b.hi); }
+    double area() const
+    {
+        if (lo[0] > hi[0]) return 0.0;
+        const double dx = (double)hi[0] - lo[0], dy = (double)hi[1] - lo[1], dz = (double)hi[2] - lo[2];
+        return 2.0 * (dx * dy + dy * dz + dz * dx);
+    }
+};
+
+constexpr int kBins = 16;
+
+struct Builder {
+    const BuildInput& in;
+    std::vector<uint32_t> idx;
+    std::vector<PackedNode> nodes;
+    int32_t max_depth = 0;
+    std::string error;
+
+    explicit Builder(const BuildInput& i) : in(i) {}
+
+    Box range_box(int64_t b, int64_t e) const
+    {
+        Box bx;
+        for (int64_t i = b; i < e; ++i) bx.grow(&in.lo[3 * idx[i]], &in.hi[3 * idx[i]]);
+        return bx;
+    }
+
+    // choose a split of idx[b, e) (count >= 2); returns the midpoint
+    int64_t split(int64_t b, int64_t e)
+    {
+        const int64_t n = e - b;
+        float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t i = b; i < e; ++i)
+            for (int a = 0; a < 3; ++a) {
+                const float c = in.cen[3 * idx[i] + a];
+                clo[a] = std::min(clo[a], c);
+                chi[a] = std::max(chi[a], c);
+            }
+        double best_cost = INFINITY;
+        int best_axis = -1, best_bin = -1;
+        for (int a = 0; a < 3; ++a) {
+            const float ext = chi[a] - clo[a];
+            if (!(ext > 0.f)) continue;
+            Box bb[kBins];
+            int64_t cnt[kBins] = {0};
+            const float scale = kBins / ext;
+            for (int64_t i = b; i < e; ++i) {
+                const uint32_t p = idx[i];
+                int k = (int)((in.cen[3 * p + a] - clo[a]) * scale);
+                k = std::min(std::max(k, 0), kBins - 1);
+                cnt[k]++;
+                bb[k].grow(&in.lo[3 * p], &in.hi[3 * p]);
+            }
+            double left_area[kBins];
+            int64_t left_cnt[kBins];
+            Box acc;
+            int64_t c = 0;
+            for (int k = 0; k < kBins - 1; ++k) {
+                acc.grow(bb[k]);
+                c += cnt[k];
+                left_area[k] = acc.area();
+                left_cnt[k] = c;
+            }
+            Box racc;
+            int64_t rc = 0;
+            for (int k = kBins - 1; k >= 1; --k) {
+                racc.grow(bb[k]);
+                rc += cnt[k];
+                const int64_t lc = left_cnt[k - 1];
+                if (lc == 0 || rc == 0) continue;
+                const double cost = left_area[k - 1] * (double)lc + racc.area() * (double)rc;
+                if (cost < best_cost) { best_cost = cost; best_axis = a; best_bin = k; }
+            }
+        }
+        int64_t mid;
+        if (best_axis >= 0) {
+            const int a = best_axis;
+            const float ext = chi[a] - clo[a];
+            const float scale = kBins / ext;
+            auto it = std::partition(idx.begin() + b, idx.begin() + e, [&](uint32_t p) {
+                int k = (int)((in.cen[3 * p + a] - clo[a]) * scale);
+                k = std::min(std::max(k, 0), kBins - 1);
+                return k < best_bin;
+            });
+            mid = it - idx.begin();
+        } else {
+            mid = b + n / 2;  // all centroids coincide: split the list in half
+        }
+        if (mid <= b || mid >= e) mid = b + n / 2;
+        return mid;
+    }
+
+    // build idx[b, e); returns the child reference
+    uint32_t build(int64_t b, int64_t e, int depth)
+    {
+        max_depth = std::max(max_depth, depth);
+        if (e - b == 1) return kLeafBit | idx[b];
+        const uint32_t me = (uint32_t)nodes.size();
+        nodes.emplace_back();
+        const int64_t mid = split(b, e);
+        const Box bl = range_box(b, mid), br = range_box(mid, e);
+        const uint32_t cl = build(b, mid, depth + 1);
+        const uint32_t cr = build(mid, e, depth + 1);
+        if (!error.empty()) return kEmptyRef;
+        uint16_t el[3], er[3];
+        for (int a = 0; a < 3; ++a) {
+            if (!round_up_half_extent(bl.lo[a], bl.hi[a], &el[a]) || !round_up_half_extent(br.lo[a], br.hi[a], &er[a])) {
+                error = "BVH box extent exceeds the fp16 range";
+                return kEmptyRef;
+            }
+        }
+        PackedNode& nd = nodes[me];
+        std::memset(&nd, 0, sizeof(nd));
+        std::memcpy(&nd.w[0], &bl.lo[0], 4);
+        std::memcpy(&nd.w[1], &bl.lo[1], 4);
+        std::memcpy(&nd.w[2], &bl.lo[2], 4);
+        std::memcpy(&nd.w[3], &br.lo[0], 4);
+        std::memcpy(&nd.w[4], &br.lo[1], 4);
+        std::memcpy(&nd.w[5], &br.lo[2], 4);
+        nd.w[6] = (uint32_t)el[0] | ((uint32_t)el[1] << 16);
+        nd.w[7] = (uint32_t)el[2] | ((uint32_t)er[0] << 16);
+        nd.w[8] = (uint32_t)er[1] | ((uint32_t)er[2] << 16);
+        nd.w[9] = cl;
+        nd.w[10] = cr;
+        nd.w[11] = 0;
+        return me;
+    }
+};
+
+}  // namespace
+
+// Smallest fp16 extent h >= 0 such that lo + float(h), evaluated in fp32,
+// is >= hi: the decoded box then contains [lo, hi] ("round-to-nearest-not-
+// lower").  Fails if no finite half qualifies.
+bool round_up_half_extent(float lo, float hi, uint16_t* out_bits)
+{
+    const double ext = std::max(0.0, (double)hi - (double)lo);
+    if (!(ext <= 65504.0)) return false;
+    __half h = __float2half_rn((float)ext);
+    uint16_t bits;
+    std::memcpy(&bits, &h, 2);
+    for (int guard = 0; guard < 64; ++guard) {
+        __half hh;
+        std::memcpy(&hh, &bits, 2);
+        const float e = __half2float(hh);
+        if (!std::isfinite(e)) return false;
+        volatile float top = lo + e;  // fp32 addition as the device performs it
+        if ((double)e >= ext && top >= hi) {
+            *out_bits = bits;
+            return true;
+        }
+        bits = (uint16_t)(bits + 1);  // next larger half (positive values)
+    }
+    return false;
+}
+
+bool build_bvh(const BuildInput& in, BuildOutput& out)
+{
+    out.nodes.clear();
+    out.depth = 0;
+    if (in.n_prims == 0) {
+        out.root = kEmptyRef;
+        return true;
+    }
+    Builder bd(in);
+    bd.idx.resize((size_t)in.n_prims);
+    for (int64_t i = 0; i < in.n_prims; ++i) bd.idx[(size_t)i] = (uint32_t)i;
+    bd.nodes.reserve((size_t)std::max<int64_t>(in.n_prims - 1, 1));
+    out.root = bd.build(0, in.n_prims, 0);
+    if (!bd.error.empty()) {
+        out.error = bd.error;
+        return false;
+    }
+    out.nodes = std::move(bd.nodes);
+    out.depth = bd.max_depth;
+    return true;
+}
+
+}  // namespace ptk

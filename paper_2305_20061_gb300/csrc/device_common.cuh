@@ -1,0 +1,231 @@
+// Device helpers of the path tracer: counter-based RNG, small vector math,
+// ray-primitive tests and BVH traversal.  FP32 throughout.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cstdint>
+
+#include "pt_internal.h"
+
+namespace ptk {
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplications with a Weyl-sequence key schedule.  It stands in
+// for the IPU's hardware generator (Section 3.1.3).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// uniform in [0, 1): top 24 bits times 2^-24 (exact)
+__device__ __forceinline__ float u01(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 operator*(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b)
+{
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 norm3(float3 a) { return a * rsqrtf(dot3(a, a)); }
+__device__ __forceinline__ float comp3(float3 a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
+
+// ---------------------------------------------------------------------------
+// Ray-primitive tests (Section 3.1.3).  Each returns t > 0 or +inf.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float isect_sphere(float4 s, float3 o, float3 d)
+{
+    // closest-approach discriminant, product form for the second root
+    const float3 oc = o - f3(s.x, s.y, s.z);
+    const float b = dot3(oc, d);
+    const float3 l = oc - d * b;
+    const float disc = s.w * s.w - dot3(l, l);
+    if (disc < 0.f) return INFINITY;
+    const float sq = sqrtf(disc);
+    const float q = -b - copysignf(sq, b);
+    const float cc = dot3(oc, oc) - s.w * s.w;
+    const float t0 = q, t1 = cc / q;
+    const float tn = fminf(t0, t1), tf = fmaxf(t0, t1);
+    return tn > 0.f ? tn : (tf > 0.f ? tf : INFINITY);
+}
+
+__device__ __forceinline__ float isect_quad(float4 q0, float4 q1, float3 o, float3 d)
+{
+    const int a = __float_as_int(q1.y);
+    const int u = a == 2 ? 0 : a + 1, v = a == 0 ? 2 : a - 1;  // (a+1)%3, (a+2)%3
+    const float t = (q0.x - comp3(o, a)) / comp3(d, a);
+    if (!(t > 0.f) || !(t < INFINITY)) return INFINITY;
+    const float pu = comp3(o, u) + t * comp3(d, u);
+    const float pv = comp3(o, v) + t * comp3(d, v);
+    if (pu < q0.y || pu > q0.z || pv < q0.w || pv > q1.x) return INFINITY;
+    return t;
+}
+
+// Per-ray set-up of the watertight triangle test (Woop, Benthin, Wald 2013).
+struct TriRay {
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+    float ox, oy, oz;   // origin permuted
+};
+
+__device__ __forceinline__ TriRay tri_setup(float3 o, float3 d)
+{
+    TriRay r;
+    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    const float dz = comp3(d, kz);
+    if (dz < 0.f) { int t = kx; kx = ky; ky = t; }
+    r.kx = kx; r.ky = ky; r.kz = kz;
+    r.Sx = comp3(d, kx) / dz;
+    r.Sy = comp3(d, ky) / dz;
+    r.Sz = 1.f / dz;
+    r.ox = comp3(o, kx); r.oy = comp3(o, ky); r.oz = comp3(o, kz);
+    return r;
+}
+
+// Edge functions are evaluated with explicitly rounded products so that the
+// two triangles sharing an edge compute exactly negated values (no FMA
+// contraction), which is what makes the test watertight.
+__device__ __forceinline__ float edge_fn(float ax, float ay, float bx, float by)
+{
+    return __fsub_rn(__fmul_rn(ax, by), __fmul_rn(ay, bx));
+}
+
+__device__ __forceinline__ float isect_tri(const TriRay& r, float4 v0, float4 v1, float4 v2)
+{
+    const float3 p0 = f3(v0.x, v0.y, v0.z), p1 = f3(v1.x, v1.y, v1.z), p2 = f3(v2.x, v2.y, v2.z);
+    const float Az = comp3(p0, r.kz) - r.oz, Bz = comp3(p1, r.kz) - r.oz, Cz = comp3(p2, r.kz) - r.oz;
+    const float Ax = __fsub_rn(comp3(p0, r.kx) - r.ox, __fmul_rn(r.Sx, Az));
+    const float Ay = __fsub_rn(comp3(p0, r.ky) - r.oy, __fmul_rn(r.Sy, Az));
+    const float Bx = __fsub_rn(comp3(p1, r.kx) - r.ox, __fmul_rn(r.Sx, Bz));
+    const float By = __fsub_rn(comp3(p1, r.ky) - r.oy, __fmul_rn(r.Sy, Bz));
+    const float Cx = __fsub_rn(comp3(p2, r.kx) - r.ox, __fmul_rn(r.Sx, Cz));
+    const float Cy = __fsub_rn(comp3(p2, r.ky) - r.oy, __fmul_rn(r.Sy, Cz));
+    float U = edge_fn(Cx, Cy, Bx, By);
+    float V = edge_fn(Ax, Ay, Cx, Cy);
+    float W = edge_fn(Bx, By, Ax, Ay);
+    if (U == 0.f || V == 0.f || W == 0.f) {
+        // exactly on an edge in float: decide in double (as PBRT-v3 does)
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return INFINITY;
+    const float det = U + V + W;
+    if (det == 0.f) return INFINITY;
+    const float T = U * (r.Sz * Az) + V * (r.Sz * Bz) + W * (r.Sz * Cz);
+    const float t = T / det;
+    return (t > 0.f && t < INFINITY) ? t : INFINITY;
+}
+
+// ---------------------------------------------------------------------------
+// Closest hit through the packed BVH with a per-thread short stack.
+// ---------------------------------------------------------------------------
+struct Hit { float t; int32_t prim; };
+
+__device__ __forceinline__ void isect_prim(const DevScene& sc, uint32_t id, float3 o, float3 d, const TriRay& tr,
+                                           float& tbest, int32_t& best)
+{
+    float t;
+    if (id < sc.nS) {
+        t = isect_sphere(__ldg(&sc.sph[id]), o, d);
+    } else if (id < sc.nS + sc.nQ) {
+        const uint32_t q = id - sc.nS;
+        t = isect_quad(__ldg(&sc.quad[2 * q]), __ldg(&sc.quad[2 * q + 1]), o, d);
+    } else {
+        const uint32_t q = id - sc.nS - sc.nQ;
+        t = isect_tri(tr, __ldg(&sc.tri[3 * q]), __ldg(&sc.tri[3 * q + 1]), __ldg(&sc.tri[3 * q + 2]));
+    }
+    if (t < tbest || (t == tbest && t < INFINITY && (int32_t)id < best)) { tbest = t; best = (int32_t)id; }
+}
+
+__device__ __forceinline__ float half_bits_to_float(uint32_t bits16) { return __half2float(__ushort_as_half((unsigned short)bits16)); }
+
+// slab test of one child box; returns entry distance or +inf
+__device__ __forceinline__ float slab(float3 lo, float3 ext, float3 o, float3 inv, float tbest)
+{
+    const float3 hi = lo + ext;
+    const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
+    const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
+    const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
+    const float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+    float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+    tmax *= 1.0000004f;  // 1 + 2 gamma_3 (PBRT): rounding can never drop a true hit
+    return (tmin <= tmax && tmin <= tbest) ? tmin : INFINITY;
+}
+
+__device__ __forceinline__ float safe_inv(float d) { return 1.f / (fabsf(d) > 1e-30f ? d : copysignf(1e-30f, d)); }
+
+template <bool kCountVisits>
+__device__ __forceinline__ Hit trace_closest(const DevScene& sc, float3 o, float3 d, uint32_t* err,
+                                             uint32_t* visits = nullptr)
+{
+    Hit h{INFINITY, -1};
+    uint32_t cur = sc.root;
+    if (cur == kEmptyRef) return h;
+    const TriRay tr = tri_setup(o, d);
+    if (cur & kLeafBit) {
+        isect_prim(sc, cur & ~kLeafBit, o, d, tr, h.t, h.prim);
+        return h;
+    }
+    const float3 inv = f3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+    uint32_t stack_ref[kStackSize];
+    float stack_t[kStackSize];
+    int sp = 0;
+    uint32_t iters = 0;
+    while (true) {
+        if (++iters > kIterCap) { atomicOr(err, PT_ERR_ITER_CAP); break; }
+        const uint4* np = sc.nodes + 3 * (size_t)cur;
+        const uint4 q0 = __ldg(np), q1 = __ldg(np + 1), q2 = __ldg(np + 2);
+        const float3 lo_l = f3(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z));
+        const float3 lo_r = f3(__uint_as_float(q0.w), __uint_as_float(q1.x), __uint_as_float(q1.y));
+        const float3 ext_l = f3(half_bits_to_float(q1.z & 0xFFFFu), half_bits_to_float(q1.z >> 16),
+                                half_bits_to_float(q1.w & 0xFFFFu));
+        const float3 ext_r = f3(half_bits_to_float(q1.w >> 16), half_bits_to_float(q2.x & 0xFFFFu),
+                                half_bits_to_float(q2.x >> 16));
+        const uint32_t cl = q2.y, cr = q2.z;
+        float tl = slab(lo_l, ext_l, o, inv, h.t);
+        float trr = slab(lo_r, ext_r, o, inv, h.t);
+        if (kCountVisits) ++*visits;
+        // leaf children are intersected right away
+        if ((cl & kLeafBit) && tl < INFINITY) { isect_prim(sc, cl & ~kLeafBit, o, d, tr, h.t, h.prim); tl = INFINITY; }
+        if ((cr & kLeafBit) && trr < INFINITY) { isect_prim(sc, cr & ~kLeafBit, o, d, tr, h.t, h.prim); trr = INFINITY; }
+        const bool hl = tl <= h.t, hr = trr <= h.t;
+        if (hl && hr) {
+            const bool left_first = tl <= trr;
+            if (sp >= kStackSize) { atomicOr(err, PT_ERR_STACK_OVERFLOW); break; }
+            stack_ref[sp] = left_first ? cr : cl;
+            stack_t[sp] = left_first ? trr : tl;
+            ++sp;
+            cur = left_first ? cl : cr;
+            continue;
+        }
+        if (hl) { cur = cl; continue; }
+        if (hr) { cur = cr; continue; }
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            if (stack_t[sp] <= h.t) { cur = stack_ref[sp]; found = true; break; }
+        }
+        if (!found) break;
+    }
+    return h;
+}
+
+}  // namespace ptk

@@ -1,0 +1,146 @@
+// Internal data layouts shared by the library's host and device sources.
+// Nothing here is part of the C ABI (include/pt.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "pt.h"
+
+namespace ptk {
+
+constexpr uint32_t kLeafBit = 0x80000000u;   // child reference is a primitive
+constexpr uint32_t kEmptyRef = 0xFFFFFFFFu;  // empty scene
+constexpr int kStackSize = 64;               // traversal stack entries per ray
+constexpr uint32_t kIterCap = 1u << 22;      // node visits per ray before giving up
+
+// Packed BVH node: the two children's boxes live in the parent (one fetch
+// tests both), each as fp32 origin + fp16 extent rounded up so the decoded
+// box contains the exact one (Section 3.1.4's "round-to-nearest-not-lower").
+// 48 bytes = three 128-bit loads:
+//   q0 = lo_l.x lo_l.y lo_l.z lo_r.x
+//   q1 = lo_r.y lo_r.z (ext_l.x|ext_l.y<<16) (ext_l.z|ext_r.x<<16)
+//   q2 = (ext_r.y|ext_r.z<<16) child_l child_r 0
+// A child reference with kLeafBit set holds a global primitive ID.
+struct PackedNode { uint32_t w[12]; };
+static_assert(sizeof(PackedNode) == 48, "node packing");
+
+// Device view of a scene (passed by value in kernel parameters).
+struct DevScene {
+    const uint4* nodes;     // 3 x uint4 per node
+    uint32_t root;          // node index, leaf reference, or kEmptyRef
+    uint32_t nS, nQ, nT;    // primitive counts; IDs: [0,nS) spheres, [nS,nS+nQ) quads, rest triangles
+    const float4* sph;      // (cx, cy, cz, r)
+    const float4* quad;     // 2 per quad: (p, lo_u, hi_u, lo_v), (hi_v, axis, 0, 0)
+    const float4* tri;      // 3 per triangle: v0, v1, v2 (w = 0)
+    const int32_t* prim_mat;  // material per global primitive
+    const float4* mat;      // 2 per material: (albedo rgb, roughness), (ior, emission rgb)
+    const int32_t* mat_type;
+    // camera (basis computed on the host in double, stored in float)
+    float eye[3], right[3], up[3], fwd[3];
+    float tan_half, aspect;
+    int32_t env_is_nif;
+    float env[3];
+    int32_t has_emission;
+};
+
+// Escape record handed from the shading kernel to the NIF kernel (24 B).
+struct EscapeRec {
+    uint32_t slot;          // chunk-relative path index
+    float u, v;             // equirect coordinates of the escape direction
+    float tr, tg, tb;       // path throughput
+};
+static_assert(sizeof(EscapeRec) == 24, "escape record");
+
+// Ray queue in structure-of-arrays form (one float4 stream per field).
+struct RayQueue {
+    float4* o;   // origin xyz, w = chunk-relative slot (bits)
+    float4* d;   // direction xyz
+    float4* tp;  // throughput rgb
+    float4* L;   // radiance gathered so far (only when the scene emits)
+};
+
+struct BounceParams {
+    DevScene sc;
+    int32_t k;              // vertex index of the rays traced now (1 = camera rays)
+    int32_t max_depth;
+    int32_t rr, rr_start;
+    uint32_t seed;
+    uint64_t chunk_first;   // global slot of the chunk's first path
+    uint32_t n_chunk;       // paths in the chunk
+    uint32_t n_pix;
+    const int64_t* pixels;  // nullable pixel list
+    int32_t W, H;
+    RayQueue qin;           // unused when k == 1
+    const uint32_t* count_in;
+    RayQueue qout;
+    uint32_t* count_out;
+    uint32_t cap;
+    EscapeRec* esc;
+    uint32_t* esc_count;
+    float* slot_L;          // [n_chunk][3]
+    int32_t* hit_ids;       // nullable [global slot][max_depth]
+    uint32_t* err;
+    unsigned long long* stats;  // [max_depth + 1]
+};
+
+// NIF parameters on the device.
+struct DevNif {
+    int32_t F, H, L;         // frequencies, hidden width, hidden layers
+    const float* B;          // [F][2]
+    // FP32 path: each linear layer padded to 128 x 128 and stored transposed
+    // ([in][out]); the output layer is stored [3][H] untransposed
+    const float* Wt;         // [L][128][128]
+    const float* bias;       // [L][128]
+    const float* Wout;       // [3][128]
+    const float* bout;       // [3]
+    float M[9];
+};
+
+struct NifEvalParams {
+    DevNif nif;
+    // mode 0: plain evaluation of uv[] -> rgb[]
+    const float* uv;
+    float* rgb;
+    int64_t n;
+    // mode 1: escape records -> slot radiance += tp * rgb
+    const EscapeRec* esc;
+    const uint32_t* esc_count;
+    uint32_t esc_cap;
+    float* slot_L;
+    uint32_t* err;
+    unsigned long long* stats;
+};
+
+// kernel launchers (trace.cu)
+cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s);
+cudaError_t launch_reduce(const float* slot_L, float* pix, uint32_t n_pix, uint32_t s_count, int first, float scale,
+                          cudaStream_t s);
+cudaError_t launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
+cudaError_t launch_philox(uint32_t seed, uint32_t tag, int64_t n, const uint32_t* ctr, uint32_t* out, cudaStream_t s);
+cudaError_t launch_primary(const DevScene& sc, int W, int H, uint32_t seed, int64_t first, int64_t n, float* org,
+                           float* dir, cudaStream_t s);
+cudaError_t launch_trace_rays(const DevScene& sc, int64_t n, const float* org, const float* dir, float* t,
+                              int32_t* prim, uint32_t* err, cudaStream_t s);
+// NIF kernels (nif_fp32.cu)
+cudaError_t launch_nif_fp32(const NifEvalParams& p, int mode, int sm_count, cudaStream_t s);
+
+// host BVH builder (bvh_build.cpp)
+struct BuildInput {
+    int64_t n_prims;
+    std::vector<float> lo, hi;  // [n][3] primitive bounds
+    std::vector<float> cen;     // [n][3] centroids
+};
+struct BuildOutput {
+    std::vector<PackedNode> nodes;
+    uint32_t root = kEmptyRef;
+    int32_t depth = 0;
+    std::string error;
+};
+bool build_bvh(const BuildInput& in, BuildOutput& out);
+bool round_up_half_extent(float lo, float hi, uint16_t* out_bits);
+
+}  // namespace ptk

@@ -1,0 +1,378 @@
+// Wavefront path tracing kernels (Section 3.1): camera rays from Philox
+// words, closest-hit traversal, BSDF sampling of the next bounce, and
+// warp-aggregated compaction of surviving rays and environment escapes.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace ptk {
+
+namespace {
+
+constexpr float kPi = 3.14159265358979323846f;
+
+struct PathState {
+    float3 o, d, tp, L;
+    uint32_t slot;
+};
+
+__device__ __forceinline__ void slot_to_pixel(const BounceParams& p, uint32_t j, uint32_t& pix, uint32_t& smp)
+{
+    const uint64_t g = p.chunk_first + j;
+    smp = (uint32_t)(g / p.n_pix);
+    const uint32_t i = (uint32_t)(g - (uint64_t)smp * p.n_pix);
+    pix = p.pixels ? (uint32_t)p.pixels[i] : i;
+}
+
+__device__ __forceinline__ float3 camera_dir(const DevScene& sc, int W, int H, uint32_t pix, float jx, float jy)
+{
+    const float x = (float)(pix % (uint32_t)W), y = (float)(pix / (uint32_t)W);
+    const float fx = ((x + jx) / (float)W * 2.f - 1.f) * sc.tan_half * sc.aspect;
+    const float fy = (1.f - (y + jy) / (float)H * 2.f) * sc.tan_half;
+    const float3 d = f3(fx * sc.right[0] + fy * sc.up[0] + sc.fwd[0], fx * sc.right[1] + fy * sc.up[1] + sc.fwd[1],
+                        fx * sc.right[2] + fy * sc.up[2] + sc.fwd[2]);
+    return norm3(d);
+}
+
+__device__ __forceinline__ float3 geometric_normal(const DevScene& sc, uint32_t id, float3 p)
+{
+    if (id < sc.nS) {
+        const float4 s = __ldg(&sc.sph[id]);
+        return norm3(p - f3(s.x, s.y, s.z));
+    }
+    if (id < sc.nS + sc.nQ) {
+        const int a = __float_as_int(__ldg(&sc.quad[2 * (id - sc.nS) + 1]).y);
+        return f3(a == 0 ? 1.f : 0.f, a == 1 ? 1.f : 0.f, a == 2 ? 1.f : 0.f);
+    }
+    const uint32_t q = id - sc.nS - sc.nQ;
+    const float4 v0 = __ldg(&sc.tri[3 * q]), v1 = __ldg(&sc.tri[3 * q + 1]), v2 = __ldg(&sc.tri[3 * q + 2]);
+    return norm3(cross3(f3(v1.x - v0.x, v1.y - v0.y, v1.z - v0.z), f3(v2.x - v0.x, v2.y - v0.y, v2.z - v0.z)));
+}
+
+// Orthonormal basis around unit n (Duff et al., JCGT 2017).
+__device__ __forceinline__ void onb(float3 n, float3& t, float3& b)
+{
+    const float sign = copysignf(1.f, n.z);
+    const float a = -1.f / (sign + n.z);
+    const float bb = n.x * n.y * a;
+    t = f3(1.f + sign * n.x * n.x * a, sign * bb, -sign * n.x);
+    b = f3(bb, sign + n.y * n.y * a, -n.y);
+}
+
+// Sample the next direction at a hit; false = absorbed.
+__device__ __forceinline__ bool sample_bsdf(const DevScene& sc, int32_t mat, float3 d, float3 ng, float u1, float u2,
+                                            float ul, float3& wi, float3& wt)
+{
+    const float4 m0 = __ldg(&sc.mat[2 * mat]), m1 = __ldg(&sc.mat[2 * mat + 1]);
+    const int type = __ldg(&sc.mat_type[mat]);
+    if (type == 2) {  // dielectric: exact unpolarised Fresnel, reflect w.p. F, weight 1
+        const bool entering = dot3(d, ng) < 0.f;
+        const float3 n = entering ? ng : ng * -1.f;
+        const float ei = entering ? 1.f : m1.x, et = entering ? m1.x : 1.f;
+        const float cosi = -dot3(d, n);
+        const float eta = ei / et;
+        const float sin2t = eta * eta * (1.f - cosi * cosi);
+        const float3 refl = d + n * (2.f * cosi);
+        if (sin2t >= 1.f) {
+            wi = norm3(refl);
+        } else {
+            const float cost = sqrtf(1.f - sin2t);
+            const float rs = (ei * cosi - et * cost) / (ei * cosi + et * cost);
+            const float rp = (et * cosi - ei * cost) / (et * cosi + ei * cost);
+            const float F = 0.5f * (rs * rs + rp * rp);
+            wi = (ul < F) ? norm3(refl) : norm3(d * eta + n * (eta * cosi - cost));
+        }
+        wt = f3(1.f, 1.f, 1.f);
+        return true;
+    }
+    const float3 n = dot3(ng, d) < 0.f ? ng : ng * -1.f;
+    float3 t, b;
+    onb(n, t, b);
+    if (type == 0) {  // Lambertian, cosine-weighted hemisphere
+        const float r = sqrtf(u1);
+        float sp, cp;
+        sincospif(2.f * u2, &sp, &cp);
+        const float lz = sqrtf(fmaxf(0.f, 1.f - u1));
+        wi = norm3(t * (r * cp) + b * (r * sp) + n * lz);
+        wt = f3(m0.x, m0.y, m0.z);
+        return true;
+    }
+    // GGX metal: sample the normal distribution (Walter et al. 2007), reflect
+    const float alpha = m0.w * m0.w;
+    const float3 wo = d * -1.f;
+    const float no = dot3(n, wo);
+    if (!(no > 0.f)) return false;
+    const float tan2 = alpha * alpha * u1 / (1.f - u1);
+    const float ch = rsqrtf(1.f + tan2);
+    const float sh = sqrtf(fmaxf(0.f, 1.f - ch * ch));
+    float sp, cp;
+    sincospif(2.f * u2, &sp, &cp);
+    const float3 h = norm3(t * (sh * cp) + b * (sh * sp) + n * ch);
+    const float oh = dot3(wo, h);
+    if (!(oh > 0.f)) return false;
+    const float3 w = norm3(h * (2.f * oh) - wo);
+    const float ni = dot3(n, w);
+    if (!(ni > 0.f)) return false;
+    const float nh = dot3(n, h);
+    const float t2o = (1.f - no * no) / (no * no), t2i = (1.f - ni * ni) / (ni * ni);
+    const float a2 = alpha * alpha;
+    const float G = (2.f / (1.f + sqrtf(1.f + a2 * t2o))) * (2.f / (1.f + sqrtf(1.f + a2 * t2i)));
+    const float x = 1.f - oh, x2 = x * x, fw = x2 * x2 * x;
+    const float k = G * oh / (no * nh);
+    wi = w;
+    wt = f3((m0.x + (1.f - m0.x) * fw) * k, (m0.y + (1.f - m0.y) * fw) * k, (m0.z + (1.f - m0.z) * fw) * k);
+    return true;
+}
+
+// Warp-aggregated append: returns this lane's index in the queue.
+__device__ __forceinline__ uint32_t warp_append(bool pred, uint32_t* counter)
+{
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (mask) {
+        const int leader = __ffs(mask) - 1;
+        if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    }
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ void store_L(float* slot_L, uint32_t slot, float3 L, uint32_t* err)
+{
+    if (!(isfinite(L.x) && isfinite(L.y) && isfinite(L.z))) atomicOr(err, PT_ERR_NONFINITE);
+    slot_L[3 * (size_t)slot] = L.x;
+    slot_L[3 * (size_t)slot + 1] = L.y;
+    slot_L[3 * (size_t)slot + 2] = L.z;
+}
+
+// One wavefront step at vertex k for every ray of the input queue.
+__global__ void __launch_bounds__(256) k_bounce(const BounceParams p)
+{
+    const uint32_t count = (p.k == 1) ? p.n_chunk : min(*p.count_in, p.cap);  // counters may pass cap on overflow
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    uint32_t traced = 0;
+    for (uint32_t base = warp * 32; base < count; base += n_warps * 32) {
+        const uint32_t i = base + lane;
+        const bool active = i < count;
+        PathState s;
+        uint32_t pix = 0, smp = 0;
+        if (active) {
+            if (p.k == 1) {
+                s.slot = i;
+                slot_to_pixel(p, i, pix, smp);
+                const uint4 w = philox4x32_10(make_uint4(pix, smp, 0u, 0u), p.seed, 0u);
+                s.o = f3(p.sc.eye[0], p.sc.eye[1], p.sc.eye[2]);
+                s.d = camera_dir(p.sc, p.W, p.H, pix, u01(w.x), u01(w.y));
+                s.tp = f3(1.f, 1.f, 1.f);
+                s.L = f3(0.f, 0.f, 0.f);
+            } else {
+                const float4 o = p.qin.o[i], d = p.qin.d[i], tp = p.qin.tp[i];
+                s.o = f3(o.x, o.y, o.z);
+                s.slot = __float_as_uint(o.w);
+                s.d = f3(d.x, d.y, d.z);
+                s.tp = f3(tp.x, tp.y, tp.z);
+                if (p.sc.has_emission) {
+                    const float4 L = p.qin.L[i];
+                    s.L = f3(L.x, L.y, L.z);
+                } else {
+                    s.L = f3(0.f, 0.f, 0.f);
+                }
+                slot_to_pixel(p, s.slot, pix, smp);
+            }
+        }
+        bool survive = false, escape_nif = false;
+        float eu = 0.f, ev = 0.f;
+        if (active) {
+            ++traced;
+            const Hit h = trace_closest<false>(p.sc, s.o, s.d, p.err);
+            if (p.hit_ids) p.hit_ids[(p.chunk_first + s.slot) * (uint64_t)p.max_depth + (p.k - 1)] = h.prim;
+            if (h.prim < 0) {
+                if (p.sc.env_is_nif) {
+                    // Section 3.3: direction -> equirect (u, v), shaded later by the NIF
+                    eu = 0.5f + atan2f(s.d.x, -s.d.z) * (0.5f / kPi);
+                    ev = acosf(fminf(1.f, fmaxf(-1.f, s.d.y))) * (1.f / kPi);
+                    escape_nif = true;
+                    store_L(p.slot_L, s.slot, s.L, p.err);
+                } else {
+                    s.L = s.L + s.tp * f3(p.sc.env[0], p.sc.env[1], p.sc.env[2]);
+                    store_L(p.slot_L, s.slot, s.L, p.err);
+                }
+            } else {
+                const float3 hp = s.o + s.d * h.t;
+                const int32_t mat = __ldg(&p.sc.prim_mat[h.prim]);
+                if (p.sc.has_emission) {
+                    const float4 m1 = __ldg(&p.sc.mat[2 * mat + 1]);
+                    s.L = s.L + s.tp * f3(m1.y, m1.z, m1.w);
+                }
+                bool alive = p.k < p.max_depth;
+                if (alive) {
+                    const uint4 w = philox4x32_10(make_uint4(pix, smp, (uint32_t)p.k, 0u), p.seed, 0u);
+                    const float3 ng = geometric_normal(p.sc, (uint32_t)h.prim, hp);
+                    float3 wi, wt;
+                    alive = sample_bsdf(p.sc, mat, s.d, ng, u01(w.x), u01(w.y), u01(w.z), wi, wt);
+                    if (alive) {
+                        s.tp = s.tp * wt;
+                        if (p.rr && p.k >= p.rr_start) {
+                            const float q = fminf(1.f, fmaxf(s.tp.x, fmaxf(s.tp.y, s.tp.z)));
+                            if (u01(w.w) < q) s.tp = s.tp * (1.f / q);
+                            else alive = false;
+                        }
+                    }
+                    if (alive) {
+                        const float eps = 1e-4f * fmaxf(1.f, fmaxf(fabsf(hp.x), fmaxf(fabsf(hp.y), fabsf(hp.z))));
+                        const float3 off = dot3(wi, ng) > 0.f ? ng : ng * -1.f;
+                        s.o = hp + off * eps;
+                        s.d = wi;
+                    }
+                }
+                if (alive) survive = true;
+                else store_L(p.slot_L, s.slot, s.L, p.err);
+            }
+        }
+        // compaction: survivors into the next queue, escapes into the NIF queue
+        const uint32_t qi = warp_append(survive, p.count_out);
+        if (survive) {
+            if (qi < p.cap) {
+                p.qout.o[qi] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.slot));
+                p.qout.d[qi] = make_float4(s.d.x, s.d.y, s.d.z, 0.f);
+                p.qout.tp[qi] = make_float4(s.tp.x, s.tp.y, s.tp.z, 0.f);
+                if (p.sc.has_emission) p.qout.L[qi] = make_float4(s.L.x, s.L.y, s.L.z, 0.f);
+            } else {
+                atomicOr(p.err, PT_ERR_QUEUE_OVERFLOW);
+            }
+        }
+        const uint32_t ei = warp_append(escape_nif, p.esc_count);
+        if (escape_nif) {
+            if (ei < p.cap) {
+                EscapeRec r;
+                r.slot = s.slot; r.u = eu; r.v = ev; r.tr = s.tp.x; r.tg = s.tp.y; r.tb = s.tp.z;
+                float2* dst = reinterpret_cast<float2*>(p.esc + ei);
+                dst[0] = make_float2(__uint_as_float(r.slot), r.u);
+                dst[1] = make_float2(r.v, r.tr);
+                dst[2] = make_float2(r.tg, r.tb);
+            } else {
+                atomicOr(p.err, PT_ERR_QUEUE_OVERFLOW);
+            }
+        }
+    }
+    // per-vertex ray count
+    for (int off = 16; off > 0; off >>= 1) traced += __shfl_down_sync(0xFFFFFFFFu, traced, off);
+    if (lane == 0 && traced) atomicAdd(&p.stats[p.k - 1], (unsigned long long)traced);
+}
+
+// image[i] (+)= sum over the chunk's samples in sample order; scaled at the end
+__global__ void k_reduce(const float* __restrict__ slot_L, float* __restrict__ pix, uint32_t n_pix, uint32_t s_count,
+                         int first, float scale)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pix) return;
+    float r = first ? 0.f : pix[3 * (size_t)i], g = first ? 0.f : pix[3 * (size_t)i + 1],
+          b = first ? 0.f : pix[3 * (size_t)i + 2];
+    for (uint32_t s = 0; s < s_count; ++s) {
+        const size_t o = 3 * ((size_t)s * n_pix + i);
+        r += slot_L[o];
+        g += slot_L[o + 1];
+        b += slot_L[o + 2];
+    }
+    pix[3 * (size_t)i] = r * scale;
+    pix[3 * (size_t)i + 1] = g * scale;
+    pix[3 * (size_t)i + 2] = b * scale;
+}
+
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+__global__ void k_philox(uint32_t seed, uint32_t tag, int64_t n, const uint4* __restrict__ ctr, uint4* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = philox4x32_10(ctr[i], seed, tag);
+}
+
+__global__ void k_primary(const DevScene sc, int W, int H, uint32_t seed, int64_t first, int64_t n, float* org,
+                          float* dir)
+{
+    const int64_t WH = (int64_t)W * H;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = first + i;
+        const uint32_t pix = (uint32_t)(g % WH), smp = (uint32_t)(g / WH);
+        const uint4 w = philox4x32_10(make_uint4(pix, smp, 0u, 0u), seed, 0u);
+        const float3 d = camera_dir(sc, W, H, pix, u01(w.x), u01(w.y));
+        org[3 * i] = sc.eye[0]; org[3 * i + 1] = sc.eye[1]; org[3 * i + 2] = sc.eye[2];
+        dir[3 * i] = d.x; dir[3 * i + 1] = d.y; dir[3 * i + 2] = d.z;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_trace_rays(const DevScene sc, int64_t n, const float* __restrict__ org,
+                                                     const float* __restrict__ dir, float* t, int32_t* prim,
+                                                     uint32_t* err)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float3 o = f3(org[3 * i], org[3 * i + 1], org[3 * i + 2]);
+        const float3 d = f3(dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]);
+        const Hit h = trace_closest<false>(sc, o, d, err);
+        t[i] = h.t;
+        prim[i] = h.prim;
+    }
+}
+
+int grid_for(int64_t n, int block, int sm_count, int per_sm)
+{
+    int64_t g = (n + block - 1) / block;
+    const int64_t cap = (int64_t)sm_count * per_sm;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s)
+{
+    // persistent grid: 8 blocks of 256 threads per SM, grid-stride over the queue
+    k_bounce<<<sm_count * 8, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const float* slot_L, float* pix, uint32_t n_pix, uint32_t s_count, int first, float scale,
+                          cudaStream_t s)
+{
+    k_reduce<<<(n_pix + 255) / 256, 256, 0, s>>>(slot_L, pix, n_pix, s_count, first, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_fill_i32<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(uint32_t seed, uint32_t tag, int64_t n, const uint32_t* ctr, uint32_t* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_philox<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(seed, tag, n, reinterpret_cast<const uint4*>(ctr),
+                                                      reinterpret_cast<uint4*>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_primary(const DevScene& sc, int W, int H, uint32_t seed, int64_t first, int64_t n, float* org,
+                           float* dir, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_primary<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(sc, W, H, seed, first, n, org, dir);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_rays(const DevScene& sc, int64_t n, const float* org, const float* dir, float* t,
+                              int32_t* prim, uint32_t* err, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_trace_rays<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(sc, n, org, dir, t, prim, err);
+    return cudaGetLastError();
+}
+
+}  // namespace ptk

@@ -1,0 +1,299 @@
+"""Thin Python binding of the C ABI in include/pt.h.
+
+Argument marshalling only: every step of the path runs in libpt.so's CUDA
+kernels.  PyTorch supplies device memory (tensors' data pointers) and
+streams.  Importing this module raises if the compiled library is missing;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import inputs as I
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpt.so")
+
+PT_OK, PT_EINVAL, PT_ENOMEM, PT_ECUDA, PT_EDEVICE, PT_EUNSUPPORTED = range(6)
+PT_FP32, PT_BF16, PT_FP8E4M3 = 0, 1, 2
+PRECISIONS = {"fp32": PT_FP32, "bf16": PT_BF16, "fp8": PT_FP8E4M3}
+ERR_BITS = {0x1: "stack_overflow", 0x2: "queue_overflow", 0x4: "nonfinite", 0x8: "timeout", 0x10: "iter_cap"}
+
+P = C.c_void_p
+I32 = C.c_int32
+I64 = C.c_int64
+U32 = C.c_uint32
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("n_spheres", I64), ("spheres", P), ("sphere_mat", P),
+                ("n_quads", I64), ("quads", P), ("quad_axis", P), ("quad_mat", P),
+                ("n_verts", I64), ("verts", P), ("n_tris", I64), ("tris", P), ("tri_mat", P),
+                ("n_mats", I64), ("mat_type", P), ("mats", P),
+                ("camera", C.c_float * 10), ("env_is_nif", I32), ("env_rgb", C.c_float * 3)]
+
+
+class SceneInfo(C.Structure):
+    _fields_ = [("n_prims", I64), ("n_nodes", I64), ("node_bytes", I64), ("prim_bytes", I64),
+                ("bvh_depth", I32), ("has_emission", I32)]
+
+
+class NifDesc(C.Structure):
+    _fields_ = [("n_freq", I32), ("hidden", I32), ("n_hidden_layers", I32), ("params", P)]
+
+
+class RenderCfg(C.Structure):
+    _fields_ = [("width", I32), ("height", I32), ("spp", I32), ("max_depth", I32), ("seed", U32),
+                ("rr", I32), ("rr_start", I32), ("precision", I32), ("chunk_slots", I64)]
+
+
+class PTError(RuntimeError):
+    def __init__(self, status: int, msg: str, bits: int = 0):
+        super().__init__(f"pt status {status}: {msg}")
+        self.status = status
+        self.bits = bits
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2305_20061_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        sig = {
+            "pt_create": ([P, C.c_int], I32),
+            "pt_destroy": ([P], None),
+            "pt_last_error": ([P], C.c_char_p),
+            "pt_check": ([P, P, P], I32),
+            "pt_create_scene": ([P, P, P], I32),
+            "pt_destroy_scene": ([P], None),
+            "pt_scene_get_info": ([P, P], I32),
+            "pt_scene_download_bvh": ([P, P, P, P], I32),
+            "pt_load_nif": ([P, P, P], I32),
+            "pt_destroy_nif": ([P], None),
+            "pt_nif_param_count": ([P], I64),
+            "pt_nif_get_params": ([P, P, P], I32),
+            "pt_nif_eval": ([P, P, I32, I64, P, P, P], I32),
+            "pt_render": ([P, P, P, P, P, P], I32),
+            "pt_render_pixels": ([P, P, P, P, I64, P, P, P, P, P], I32),
+            "pt_last_render_counts": ([P, P, I32], I32),
+            "pt_philox": ([P, U32, U32, I64, P, P, P], I32),
+            "pt_primary_rays": ([P, P, P, I64, I64, P, P, P], I32),
+            "pt_trace_rays": ([P, P, I64, P, P, P, P, P], I32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _np_ptr(a: Optional[np.ndarray]):
+    return None if a is None or a.size == 0 else a.ctypes.data_as(P)
+
+
+def _dptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return P(t.data_ptr())
+
+
+def _stream(stream) -> P:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return P(stream.cuda_stream)
+
+
+class Context:
+    """A library context on one CUDA device (pt_create / pt_destroy)."""
+
+    def __init__(self, device: int = 0):
+        self.h = P()
+        st = lib().pt_create(C.byref(self.h), int(device))
+        if st != PT_OK:
+            raise PTError(st, "pt_create failed")
+        self.device = device
+
+    def _raise(self, st: int):
+        if st != PT_OK:
+            raise PTError(st, lib().pt_last_error(self.h).decode())
+
+    def check(self, stream=None) -> int:
+        """Synchronise and read (and clear) the device error word."""
+        bits = U32(0)
+        st = lib().pt_check(self.h, _stream(stream), C.byref(bits))
+        if st not in (PT_OK, PT_EDEVICE):
+            self._raise(st)
+        if st == PT_EDEVICE:
+            names = [n for b, n in ERR_BITS.items() if bits.value & b]
+            raise PTError(st, "device error bits " + ",".join(names), bits.value)
+        return bits.value
+
+    def close(self):
+        if self.h:
+            lib().pt_destroy(self.h)
+            self.h = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scene:
+    """pt_create_scene from an inputs.Scene (host arrays, read during the call)."""
+
+    def __init__(self, ctx: Context, scene: I.Scene):
+        scene.validate()
+        self.ctx = ctx
+        self.src = scene
+        d = SceneDesc()
+        d.n_spheres, d.spheres, d.sphere_mat = len(scene.sphere), _np_ptr(scene.sphere), _np_ptr(scene.sphere_mat)
+        d.n_quads, d.quads, d.quad_axis, d.quad_mat = (len(scene.quad), _np_ptr(scene.quad),
+                                                       _np_ptr(scene.quad_axis), _np_ptr(scene.quad_mat))
+        d.n_verts, d.verts = len(scene.vert), _np_ptr(scene.vert)
+        d.n_tris, d.tris, d.tri_mat = len(scene.tri), _np_ptr(scene.tri), _np_ptr(scene.tri_mat)
+        d.n_mats, d.mat_type, d.mats = len(scene.mat), _np_ptr(scene.mat_type), _np_ptr(scene.mat)
+        cam = np.concatenate([scene.camera.eye, scene.camera.target, scene.camera.up, [scene.camera.fov_deg]])
+        for i in range(10):
+            d.camera[i] = float(cam[i])
+        d.env_is_nif = 0 if scene.env_const is not None else 1
+        env = scene.env_const if scene.env_const is not None else np.zeros(3)
+        for i in range(3):
+            d.env_rgb[i] = float(env[i])
+        self.h = P()
+        ctx._raise(lib().pt_create_scene(ctx.h, C.byref(d), C.byref(self.h)))
+
+    def info(self) -> dict:
+        inf = SceneInfo()
+        self.ctx._raise(lib().pt_scene_get_info(self.h, C.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in SceneInfo._fields_}
+
+    def download_bvh(self):
+        n = self.info()["n_nodes"]
+        nodes = np.zeros((max(n, 1), 12), np.uint32)
+        root = U32(0)
+        self.ctx._raise(lib().pt_scene_download_bvh(self.ctx.h, self.h, _np_ptr(nodes), C.byref(root)))
+        return nodes[:n], root.value
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().pt_destroy_scene(self.h)
+            self.h = None
+
+
+def nif_flat(nif: I.NIF) -> np.ndarray:
+    """Flat float32 parameter layout of include/pt.h (B, per layer W and b, M)."""
+    parts = [nif.B.ravel()]
+    for W, b in zip(nif.W, nif.b):
+        parts += [W.ravel(), b.ravel()]
+    parts.append(nif.M.ravel())
+    return np.ascontiguousarray(np.concatenate(parts).astype(np.float32))
+
+
+class Nif:
+    """pt_load_nif from an inputs.NIF."""
+
+    def __init__(self, ctx: Context, nif: I.NIF):
+        self.ctx = ctx
+        self.src = nif
+        flat = nif_flat(nif)
+        d = NifDesc(nif.n_freq, nif.hidden, nif.n_hidden_layers, _np_ptr(flat))
+        self.h = P()
+        ctx._raise(lib().pt_load_nif(ctx.h, C.byref(d), C.byref(self.h)))
+
+    @property
+    def param_count(self) -> int:
+        return int(lib().pt_nif_param_count(self.h))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.param_count, np.float32)
+        self.ctx._raise(lib().pt_nif_get_params(self.ctx.h, self.h, _np_ptr(out)))
+        return out
+
+    def eval(self, uv: torch.Tensor, precision: str = "fp32", stream=None) -> torch.Tensor:
+        uv = uv.contiguous()
+        rgb = torch.empty((uv.shape[0], 3), dtype=torch.float32, device=uv.device)
+        self.ctx._raise(lib().pt_nif_eval(self.ctx.h, self.h, PRECISIONS[precision], uv.shape[0], _dptr(uv),
+                                          _dptr(rgb), _stream(stream)))
+        return rgb
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().pt_destroy_nif(self.h)
+            self.h = None
+
+
+def make_cfg(cfg: I.RenderCfg, precision: str = "fp32", chunk_slots: int = 0) -> RenderCfg:
+    return RenderCfg(cfg.width, cfg.height, cfg.spp, cfg.max_depth, cfg.seed, int(cfg.rr), cfg.rr_start,
+                     PRECISIONS[precision], int(chunk_slots))
+
+
+def render(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderCfg, precision: str = "fp32",
+           out: Optional[torch.Tensor] = None, chunk_slots: int = 0, stream=None) -> torch.Tensor:
+    """pt_render: returns the [H, W, 3] float32 image on the context's device."""
+    if out is None:
+        out = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=f"cuda:{ctx.device}")
+    c = make_cfg(cfg, precision, chunk_slots)
+    ctx._raise(lib().pt_render(ctx.h, scene.h, nif.h if nif is not None else None, C.byref(c), _dptr(out),
+                               _stream(stream)))
+    return out
+
+
+def render_pixels(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderCfg, pixels: Optional[torch.Tensor],
+                  precision: str = "fp32", want_slots: bool = False, want_ids: bool = False, chunk_slots: int = 0,
+                  stream=None):
+    """pt_render_pixels: (pixel_rgb [n,3], slot_rgb [spp,n,3] or None, hit_ids [spp,n,D] or None)."""
+    dev = f"cuda:{ctx.device}"
+    n = cfg.width * cfg.height if pixels is None else int(pixels.shape[0])
+    pix = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    slots = torch.empty((cfg.spp, n, 3), dtype=torch.float32, device=dev) if want_slots else None
+    ids = torch.empty((cfg.spp, n, cfg.max_depth), dtype=torch.int32, device=dev) if want_ids else None
+    c = make_cfg(cfg, precision, chunk_slots)
+    ctx._raise(lib().pt_render_pixels(ctx.h, scene.h, nif.h if nif is not None else None, C.byref(c), n,
+                                      _dptr(pixels), _dptr(pix), _dptr(slots), _dptr(ids), _stream(stream)))
+    return pix, slots, ids
+
+
+def last_render_counts(ctx: Context, max_depth: int) -> np.ndarray:
+    out = np.zeros(max_depth + 1, np.int64)
+    ctx._raise(lib().pt_last_render_counts(ctx.h, _np_ptr(out), max_depth + 1))
+    return out
+
+
+def philox(ctx: Context, seed: int, tag: int, ctr: torch.Tensor, stream=None) -> torch.Tensor:
+    ctr = ctr.contiguous()
+    out = torch.empty_like(ctr)
+    ctx._raise(lib().pt_philox(ctx.h, seed, tag, ctr.shape[0], _dptr(ctr), _dptr(out), _stream(stream)))
+    return out
+
+
+def primary_rays(ctx: Context, scene: Scene, cfg: I.RenderCfg, first_slot: int, n: int, stream=None):
+    dev = f"cuda:{ctx.device}"
+    org = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    dir = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    c = make_cfg(cfg)
+    ctx._raise(lib().pt_primary_rays(ctx.h, scene.h, C.byref(c), first_slot, n, _dptr(org), _dptr(dir),
+                                     _stream(stream)))
+    return org, dir
+
+
+def trace_rays(ctx: Context, scene: Scene, org: torch.Tensor, dir: torch.Tensor, stream=None):
+    org, dir = org.contiguous(), dir.contiguous()
+    n = org.shape[0]
+    t = torch.empty(n, dtype=torch.float32, device=org.device)
+    prim = torch.empty(n, dtype=torch.int32, device=org.device)
+    ctx._raise(lib().pt_trace_rays(ctx.h, scene.h, n, _dptr(org), _dptr(dir), _dptr(t), _dptr(prim),
+                                   _stream(stream)))
+    return t, prim
