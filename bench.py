@@ -1,0 +1,330 @@
+"""Benchmark of the neural path tracer's hot path on GB300.
+
+A step is one full frame of the spheres + HDR-NIF workload (256 spheres,
+512x512 pixels, 64 samples per pixel, depth 8: 16.8M paths) rendered through
+the C ABI: camera rays, traversal, bounce sampling, NIF shading of every
+escape and the sample reduction.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+Multi-GPU (torchrun, one rank per GPU): each rank renders its own disjoint
+sample range of the frame (Philox counters first_sample = rank * spp), with
+no data-path collective; value = all ranks' paths / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2305_20061_gb300 import inputs as I  # noqa: E402
+
+METRIC = "Msamples/s & NIF evals/s at 1 GB300; BF16-TC vs FP32 at stated image RMSE"
+UNIT = "Msamples/s"
+WORKLOAD = "C2"
+FLOP_PER_EVAL = 2 * (3 * 128 * 128 + 128 * 3)   # 99,072: three 128x128 layers + 128->3 head
+TC_FLOP_PER_EVAL = 2 * 3 * 128 * 128            # 98,304 in the three hidden layers
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def peaks():
+    try:
+        with open(MEASURED) as f:
+            m = json.load(f)
+        return m, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(precision, spp=None):
+    sc = I.make_scene(WORKLOAD)
+    cfg = I.CONFIGS[WORKLOAD]["cfg"]
+    if spp:  # smaller case for profiler captures only
+        cfg = I.RenderCfg(cfg.width, cfg.height, spp, cfg.max_depth, cfg.seed)
+    nif = I.nif_init(colour="yuv")
+    return sc, cfg, nif
+
+
+# ----------------------------------------------------------------------------
+def oracle_rate(sc, cfg, nif, target_s: float, n_threads: int):
+    """Oracle paths/s on a bounded pixel sample of the workload (all samples
+    of every m-th pixel), sized to take about target_s seconds."""
+    from oracle import oracle as O
+    osc = O.Scene(sc)
+    onif = O.Nif(nif)
+    n_pix_total = cfg.width * cfg.height
+
+    def run(n_pix):
+        step = max(1, n_pix_total // n_pix)
+        pixels = np.arange(0, n_pix_total, step, dtype=np.int64)[:n_pix]
+        t0 = time.perf_counter()
+        O.render(osc, cfg, onif, pixels=pixels, n_threads=n_threads)
+        return len(pixels), time.perf_counter() - t0
+
+    n, dt = run(max(8 * n_threads, 128))
+    rate = n / max(dt, 1e-6)
+    n_pix = int(min(n_pix_total, max(n_threads, rate * target_s)))
+    return run, n_pix
+
+
+def bench_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    sc, cfg, nif = workload(args.precision, args.spp)
+    threads = os.cpu_count() or 1
+    run, n_pix = oracle_rate(sc, cfg, nif, target_s=args.ref_step_s, n_threads=threads)
+    for _ in range(args.warmup):
+        run(max(threads, n_pix // 8))
+    total_paths, total_t = 0, 0.0
+    for _ in range(args.steps):
+        n, dt = run(n_pix)
+        total_paths += n * cfg.spp
+        total_t += dt
+    value = total_paths / total_t / 1e6
+    sample = f"all {cfg.spp} samples of {n_pix} evenly strided pixels of the {cfg.width}x{cfg.height} frame per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(cfg, "fp64-oracle"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict(cfg, precision):
+    return {"workload": f"{WORKLOAD}: 256 spheres (60% Lambertian / 30% GGX metal / 10% dielectric) + HDR-NIF "
+                        f"environment, {cfg.width}x{cfg.height}, {cfg.spp} spp, max depth {cfg.max_depth}, no RR",
+            "paths_per_frame": cfg.n_slots, "nif": "F64 Fourier (sigma 10) -> 3x FC-128 ReLU -> FC-3 -> YUV->RGB -> exp",
+            "nif_precision": precision, "l2": "per-step working set > L2 (wavefront queues ~2.7 GB) and a 512 MB "
+                                              "L2 flush between timed steps (outside the timed events)"}
+
+
+# ----------------------------------------------------------------------------
+def bench_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    from paper_2305_20061_gb300 import build
+    build.build()
+    from paper_2305_20061_gb300 import pt
+
+    sc, cfg, nif = workload(args.precision, args.spp)
+    ctx = pt.Context(local)
+    scene = pt.Scene(ctx, sc)
+    gnif = pt.Nif(ctx, nif)
+    img = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=f"cuda:{local}")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+    first_sample = rank * cfg.spp
+
+    def step():
+        pt.render(ctx, scene, gnif, cfg, args.precision, out=img, first_sample=first_sample)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.check()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    pt.profile_enable(ctx, True)
+    pt.profile_read(ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for i in range(args.steps):
+        flush.fill_(float(i))           # evict L2 between timed steps (not timed)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    barrier()
+    clocks = sampler.stop()
+    prof = pt.profile_read(ctx)
+    pt.profile_enable(ctx, False)
+    ctx.check()
+    counts = pt.last_render_counts(ctx, cfg.max_depth)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    paths = cfg.n_slots
+    value = world * paths / (ms * 1e-3) / 1e6
+
+    # live roofline of the dominant kernel
+    meas, which = peaks()
+    dom = max(prof, key=lambda k: prof[k][0])
+    evals = int(counts[cfg.max_depth])
+    nif_ms = prof["nif"][0] / args.steps
+    roof = None
+    if dom == "nif":
+        if args.precision == "fp32":
+            clock = float(meas.get("sm_max_mhz", 2070.0))
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock * 1e6 / 1e12
+            achieved = evals * FLOP_PER_EVAL / (nif_ms * 1e-3) / 1e12
+            roof = {"kernel": "k_nif_fp32", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_note": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {clock:.0f} MHz"}
+        else:
+            peak = float(meas["bf16_tflops_sustained" if "bf16_tflops_sustained" in meas else "bf16_tflops"])
+            achieved = evals * TC_FLOP_PER_EVAL / (nif_ms * 1e-3) / 1e12
+            roof = {"kernel": "k_nif_tc", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_note": f"dense BF16, sustained ({which})"}
+    else:
+        clock = float(meas.get("sm_max_mhz", 2070.0))
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock * 1e6 / 1e12
+        trace_ms = prof["trace"][0] / args.steps
+        rays = int(counts[:cfg.max_depth].sum())
+        roof = {"kernel": "k_bounce", "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "rays_per_s": rays / (trace_ms * 1e-3),
+                "peak_note": "traversal of a 256-sphere BVH: latency/ALU bound"}
+
+    # end to end through the C ABI with host buffers: scene + weights in, image out
+    e2e = None
+    if not args.no_e2e:
+        host_img = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, pin_memory=True)
+        flat = pt.nif_flat(nif)
+        h2d = sum(a.nbytes for a in (sc.sphere, sc.sphere_mat, sc.mat_type, sc.mat)) + flat.nbytes
+        d2h = host_img.numel() * 4
+        n_e2e = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            s2 = pt.Scene(ctx, sc)
+            n2 = pt.Nif(ctx, nif)
+            pt.render(ctx, s2, n2, cfg, args.precision, out=img, first_sample=first_sample)
+            host_img.copy_(img, non_blocking=True)
+            torch.cuda.synchronize()
+            del s2, n2
+        dt = (time.perf_counter() - t0) / n_e2e
+        e2e = {"value": world * paths / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "note": "pt_create_scene + pt_load_nif from host arrays, pt_render, "
+                                                        "image copied to pinned host memory, per step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        run, n_pix = oracle_rate(sc, cfg, nif, target_s=args.cpu_s, n_threads=threads)
+        n, dt = run(n_pix)
+        cpu = {"value": n * cfg.spp / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"all {cfg.spp} samples of {n} evenly strided pixels ({n * cfg.spp} paths), FP64 oracle"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+            "data": "synthetic (procedural scene, random-init NIF weights; seeds 0)",
+            "config": config_dict(cfg, args.precision),
+            "nif_evals_per_step": evals,
+            "nif_evals_per_s": evals / (nif_ms * 1e-3) if nif_ms > 0 else None,
+            "rays_per_step": int(counts[:cfg.max_depth].sum()),
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(sum(v[1] for v in prof.values())),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--cpu-s", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--ref-step-s", type=float, default=4.0, help="seconds per reference-arm step")
+    ap.add_argument("--spp", type=int, default=None, help="override spp (small cases for profiler captures)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

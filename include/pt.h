@@ -67,6 +67,7 @@ typedef enum pt_precision {
 #define PT_ERR_NONFINITE      0x4u   /* a non-finite radiance value was produced */
 #define PT_ERR_TIMEOUT        0x8u   /* a bounded device wait gave up */
 #define PT_ERR_ITER_CAP       0x10u  /* traversal exceeded its iteration cap */
+#define PT_ERR_BAD_NODE       0x20u  /* traversal met a node reference outside the node array */
 
 typedef struct pt_ctx pt_ctx;
 typedef struct pt_scene pt_scene;
@@ -180,12 +181,14 @@ typedef struct pt_render_cfg {
     int32_t rr_start;
     int32_t precision;         /* pt_precision of the NIF at escapes */
     int64_t chunk_slots;       /* paths per wavefront chunk; 0 = automatic; rounded to whole samples */
+    int32_t first_sample;      /* sample index of the first path per pixel (Philox counter word 1 =
+                                  first_sample + s): disjoint ranges render independent sample sets */
 } pt_render_cfg;
 
 /* Render the image: d_image [height][width][3] float, the mean over spp
    paths of each pixel.  Path (pixel p, sample s) draws Philox-4x32-10 words
-   with key (seed, 0) and counter (p, s, k, 0) at vertex k (k = 0 for the
-   camera jitter).  `nif` is required when the scene's environment is a NIF
+   with key (seed, 0) and counter (p, first_sample + s, k, 0) at vertex k
+   (k = 0 for the camera jitter).  `nif` is required when the scene's environment is a NIF
    and ignored otherwise. */
 PT_API pt_status pt_render(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, const pt_render_cfg* cfg,
                            float* d_image, void* stream);
@@ -204,6 +207,20 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* scene, const pt_n
    NIF.  counts: [max_depth + 1] int64 -> counts[k-1] = rays traced at vertex
    k, counts[max_depth] = NIF evaluations. */
 PT_API pt_status pt_last_render_counts(pt_ctx* ctx, int64_t* counts, int32_t n);
+
+/* Kernel timing.  While enabled, the library records a CUDA event pair on
+   the launching stream around each of its kernel launches and accumulates
+   the device time per kernel kind: 0 trace/shade step, 1 NIF evaluation,
+   2 sample reduction, 3 other (training and utilities).  pt_profile_read
+   synchronises the device, writes up to n kinds of total milliseconds and
+   launch counts (either pointer may be NULL) and resets the totals. */
+#define PT_KIND_TRACE 0
+#define PT_KIND_NIF 1
+#define PT_KIND_REDUCE 2
+#define PT_KIND_OTHER 3
+#define PT_N_KINDS 4
+PT_API pt_status pt_profile_enable(pt_ctx* ctx, int32_t enable);
+PT_API pt_status pt_profile_read(pt_ctx* ctx, double* ms, int64_t* launches, int32_t n);
 
 /* ------------------------------------------------------------------------ */
 /* Building blocks of the same path, exposed for testing and for callers    */

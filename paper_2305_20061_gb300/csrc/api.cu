@@ -28,6 +28,11 @@ struct pt_ctx {
     uint32_t* counters = nullptr;          // [kCounters]
     unsigned long long* stats = nullptr;   // [kMaxDepth + 1]
     int last_depth = 0;
+    // kernel timing (pt_profile_enable)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;      // pairs: start, stop
+    std::vector<int> prof_kind;
+    size_t prof_used = 0;
 };
 
 struct pt_scene {
@@ -134,6 +139,30 @@ void camera_basis(const float cam[10], DevScene& d)
     d.aspect = 1.f;
 }
 
+// Run one kernel launch, bracketed by a CUDA event pair on its stream when
+// profiling is enabled.
+template <typename F>
+cudaError_t timed(pt_ctx* ctx, int kind, cudaStream_t s, F&& launch)
+{
+    if (!ctx->prof_on) return launch();
+    if (ctx->prof_used * 2 + 2 > ctx->prof_ev.size()) {
+        for (int i = 0; i < 2; ++i) {
+            cudaEvent_t e;
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return r;
+            ctx->prof_ev.push_back(e);
+        }
+        ctx->prof_kind.push_back(0);
+    }
+    const size_t i = ctx->prof_used++;
+    ctx->prof_kind[i] = kind;
+    cudaError_t r = cudaEventRecord(ctx->prof_ev[2 * i], s);
+    if (r != cudaSuccess) return r;
+    r = launch();
+    if (r != cudaSuccess) return r;
+    return cudaEventRecord(ctx->prof_ev[2 * i + 1], s);
+}
+
 pt_status check_cfg(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, const pt_render_cfg* cfg)
 {
     if (!ctx || !scene || !cfg) return fail(ctx, PT_EINVAL, "null argument");
@@ -141,6 +170,7 @@ pt_status check_cfg(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, const
     if (cfg->max_depth < 1 || cfg->max_depth > kMaxDepth) return fail(ctx, PT_EINVAL, "max_depth must be in [1, 64]");
     if ((int64_t)cfg->width * cfg->height > (1ll << 31)) return fail(ctx, PT_EINVAL, "image too large");
     if (cfg->rr && cfg->rr_start < 1) return fail(ctx, PT_EINVAL, "rr_start must be >= 1");
+    if (cfg->first_sample < 0) return fail(ctx, PT_EINVAL, "first_sample must be >= 0");
     if (scene->dev.env_is_nif && !nif) return fail(ctx, PT_EINVAL, "scene environment is a NIF but no NIF was given");
     if (cfg->precision != PT_FP32 && cfg->precision != PT_BF16 && cfg->precision != PT_FP8E4M3)
         return fail(ctx, PT_EINVAL, "unknown precision");
@@ -158,7 +188,7 @@ pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, cudaSt
     p.err = ctx->d_err;
     p.stats = ctx->stats + ctx->last_depth;
     if (precision == PT_FP32) {
-        PT_CUDA(launch_nif_fp32(p, 1, ctx->sm_count, s));
+        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_fp32(p, 1, ctx->sm_count, s); }));
         return PT_OK;
     }
     return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF precision not available in this build");
@@ -198,6 +228,7 @@ PT_API void pt_destroy(pt_ctx* ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     free_scratch(ctx);
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
     cudaFree(ctx->d_err);
     cudaFree(ctx->counters);
     cudaFree(ctx->stats);
@@ -341,6 +372,7 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
     DevScene& v = sc->dev;
     v.nodes = (const uint4*)dn;
     v.root = bo.root;
+    v.n_nodes = (uint32_t)bo.nodes.size();
     v.nS = (uint32_t)nS; v.nQ = (uint32_t)nQ; v.nT = (uint32_t)nT;
     v.sph = (const float4*)ds; v.quad = (const float4*)dq; v.tri = (const float4*)dt;
     v.prim_mat = (const int32_t*)dpm; v.mat = (const float4*)dm; v.mat_type = (const int32_t*)dmt;
@@ -477,7 +509,8 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
     p.n = n;
     p.err = ctx->d_err;
     if (precision == PT_FP32) {
-        PT_CUDA(launch_nif_fp32(p, 0, ctx->sm_count, (cudaStream_t)stream));
+        cudaStream_t s = (cudaStream_t)stream;
+        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_fp32(p, 0, ctx->sm_count, s); }));
         return PT_OK;
     }
     if (precision == PT_BF16 || precision == PT_FP8E4M3)
@@ -519,6 +552,7 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
     bp.rr = cfg->rr;
     bp.rr_start = cfg->rr_start;
     bp.seed = cfg->seed;
+    bp.first_sample = (uint32_t)cfg->first_sample;
     bp.n_pix = (uint32_t)n_pix;
     bp.pixels = d_pixels;
     bp.W = cfg->width;
@@ -543,14 +577,16 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
             bp.qout = ctx->q[k & 1];
             bp.count_in = ctx->counters + (k - 1);
             bp.count_out = ctx->counters + k;
-            PT_CUDA(launch_bounce(bp, ctx->sm_count, s));
+            PT_CUDA(timed(ctx, PT_KIND_TRACE, s, [&] { return launch_bounce(bp, ctx->sm_count, s); }));
         }
         if (sc->dev.env_is_nif) {
             st = eval_nif_escapes(ctx, nf, cfg->precision, s);
             if (st != PT_OK) return st;
         }
         const float scale = (c == n_chunks - 1) ? (float)(1.0 / cfg->spp) : 1.f;
-        PT_CUDA(launch_reduce(ctx->slot_L, d_pixel_rgb, (uint32_t)n_pix, (uint32_t)(n / n_pix), c == 0, scale, s));
+        PT_CUDA(timed(ctx, PT_KIND_REDUCE, s, [&] {
+            return launch_reduce(ctx->slot_L, d_pixel_rgb, (uint32_t)n_pix, (uint32_t)(n / n_pix), c == 0, scale, s);
+        }));
         if (d_slot_rgb)
             PT_CUDA(cudaMemcpyAsync(d_slot_rgb + 3 * first, ctx->slot_L, (size_t)n * 3 * sizeof(float),
                                     cudaMemcpyDeviceToDevice, s));
@@ -593,7 +629,8 @@ PT_API pt_status pt_primary_rays(pt_ctx* ctx, const pt_scene* sc, const pt_rende
     if (cfg->width < 1 || cfg->height < 1) return fail(ctx, PT_EINVAL, "image size must be >= 1");
     DevScene v = sc->dev;
     v.aspect = (float)((double)cfg->width / (double)cfg->height);
-    PT_CUDA(launch_primary(v, cfg->width, cfg->height, cfg->seed, first_slot, n, d_org, d_dir, (cudaStream_t)stream));
+    PT_CUDA(launch_primary(v, cfg->width, cfg->height, cfg->seed, (uint32_t)cfg->first_sample, first_slot, n, d_org, d_dir,
+                           (cudaStream_t)stream));
     return PT_OK;
 }
 
@@ -603,6 +640,34 @@ PT_API pt_status pt_trace_rays(pt_ctx* ctx, const pt_scene* sc, int64_t n, const
     if (!ctx || !sc || n < 0 || (n > 0 && (!d_org || !d_dir || !d_t || !d_prim)))
         return fail(ctx, PT_EINVAL, "bad argument");
     PT_CUDA(launch_trace_rays(sc->dev, n, d_org, d_dir, d_t, d_prim, ctx->d_err, (cudaStream_t)stream));
+    return PT_OK;
+}
+
+PT_API pt_status pt_profile_enable(pt_ctx* ctx, int32_t enable)
+{
+    if (!ctx) return PT_EINVAL;
+    ctx->prof_on = enable != 0;
+    ctx->prof_used = 0;
+    return PT_OK;
+}
+
+PT_API pt_status pt_profile_read(pt_ctx* ctx, double* ms, int64_t* launches, int32_t n)
+{
+    if (!ctx || n < 0) return fail(ctx, PT_EINVAL, "bad argument");
+    PT_CUDA(cudaDeviceSynchronize());
+    double acc[PT_N_KINDS] = {0, 0, 0, 0};
+    int64_t cnt[PT_N_KINDS] = {0, 0, 0, 0};
+    for (size_t i = 0; i < ctx->prof_used; ++i) {
+        float t = 0.f;
+        PT_CUDA(cudaEventElapsedTime(&t, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
+        acc[ctx->prof_kind[i]] += t;
+        cnt[ctx->prof_kind[i]] += 1;
+    }
+    ctx->prof_used = 0;
+    for (int k = 0; k < n && k < PT_N_KINDS; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (launches) launches[k] = cnt[k];
+    }
     return PT_OK;
 }
 

@@ -191,6 +191,7 @@ __device__ __forceinline__ Hit trace_closest(const DevScene& sc, float3 o, float
     uint32_t iters = 0;
     while (true) {
         if (++iters > kIterCap) { atomicOr(err, PT_ERR_ITER_CAP); break; }
+        if (cur >= sc.n_nodes) { atomicOr(err, PT_ERR_BAD_NODE); break; }  // never fetch outside the node array
         const uint4* np = sc.nodes + 3 * (size_t)cur;
         const uint4 q0 = __ldg(np), q1 = __ldg(np + 1), q2 = __ldg(np + 2);
         const float3 lo_l = f3(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z));
@@ -206,7 +207,8 @@ __device__ __forceinline__ Hit trace_closest(const DevScene& sc, float3 o, float
         // leaf children are intersected right away
         if ((cl & kLeafBit) && tl < INFINITY) { isect_prim(sc, cl & ~kLeafBit, o, d, tr, h.t, h.prim); tl = INFINITY; }
         if ((cr & kLeafBit) && trr < INFINITY) { isect_prim(sc, cr & ~kLeafBit, o, d, tr, h.t, h.prim); trr = INFINITY; }
-        const bool hl = tl <= h.t, hr = trr <= h.t;
+        // a child is entered only if its box was hit (finite entry) no later than the best hit
+        const bool hl = tl < INFINITY && tl <= h.t, hr = trr < INFINITY && trr <= h.t;
         if (hl && hr) {
             const bool left_first = tl <= trr;
             if (sp >= kStackSize) { atomicOr(err, PT_ERR_STACK_OVERFLOW); break; }

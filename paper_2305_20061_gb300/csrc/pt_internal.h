@@ -32,6 +32,7 @@ static_assert(sizeof(PackedNode) == 48, "node packing");
 struct DevScene {
     const uint4* nodes;     // 3 x uint4 per node
     uint32_t root;          // node index, leaf reference, or kEmptyRef
+    uint32_t n_nodes;
     uint32_t nS, nQ, nT;    // primitive counts; IDs: [0,nS) spheres, [nS,nS+nQ) quads, rest triangles
     const float4* sph;      // (cx, cy, cz, r)
     const float4* quad;     // 2 per quad: (p, lo_u, hi_u, lo_v), (hi_v, axis, 0, 0)
@@ -69,6 +70,7 @@ struct BounceParams {
     int32_t max_depth;
     int32_t rr, rr_start;
     uint32_t seed;
+    uint32_t first_sample;  // sample index offset (Philox counter word 1)
     uint64_t chunk_first;   // global slot of the chunk's first path
     uint32_t n_chunk;       // paths in the chunk
     uint32_t n_pix;
@@ -121,8 +123,8 @@ cudaError_t launch_reduce(const float* slot_L, float* pix, uint32_t n_pix, uint3
                           cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);
 cudaError_t launch_philox(uint32_t seed, uint32_t tag, int64_t n, const uint32_t* ctr, uint32_t* out, cudaStream_t s);
-cudaError_t launch_primary(const DevScene& sc, int W, int H, uint32_t seed, int64_t first, int64_t n, float* org,
-                           float* dir, cudaStream_t s);
+cudaError_t launch_primary(const DevScene& sc, int W, int H, uint32_t seed, uint32_t first_sample, int64_t first,
+                           int64_t n, float* org, float* dir, cudaStream_t s);
 cudaError_t launch_trace_rays(const DevScene& sc, int64_t n, const float* org, const float* dir, float* t,
                               int32_t* prim, uint32_t* err, cudaStream_t s);
 // NIF kernels (nif_fp32.cu)

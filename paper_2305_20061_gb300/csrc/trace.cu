@@ -19,8 +19,9 @@ struct PathState {
 __device__ __forceinline__ void slot_to_pixel(const BounceParams& p, uint32_t j, uint32_t& pix, uint32_t& smp)
 {
     const uint64_t g = p.chunk_first + j;
-    smp = (uint32_t)(g / p.n_pix);
-    const uint32_t i = (uint32_t)(g - (uint64_t)smp * p.n_pix);
+    const uint32_t s = (uint32_t)(g / p.n_pix);
+    const uint32_t i = (uint32_t)(g - (uint64_t)s * p.n_pix);
+    smp = s + p.first_sample;
     pix = p.pixels ? (uint32_t)p.pixels[i] : i;
 }
 
@@ -293,13 +294,13 @@ __global__ void k_philox(uint32_t seed, uint32_t tag, int64_t n, const uint4* __
         out[i] = philox4x32_10(ctr[i], seed, tag);
 }
 
-__global__ void k_primary(const DevScene sc, int W, int H, uint32_t seed, int64_t first, int64_t n, float* org,
-                          float* dir)
+__global__ void k_primary(const DevScene sc, int W, int H, uint32_t seed, uint32_t first_sample, int64_t first, int64_t n,
+                          float* org, float* dir)
 {
     const int64_t WH = (int64_t)W * H;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = first + i;
-        const uint32_t pix = (uint32_t)(g % WH), smp = (uint32_t)(g / WH);
+        const uint32_t pix = (uint32_t)(g % WH), smp = (uint32_t)(g / WH) + first_sample;
         const uint4 w = philox4x32_10(make_uint4(pix, smp, 0u, 0u), seed, 0u);
         const float3 d = camera_dir(sc, W, H, pix, u01(w.x), u01(w.y));
         org[3 * i] = sc.eye[0]; org[3 * i + 1] = sc.eye[1]; org[3 * i + 2] = sc.eye[2];
@@ -359,11 +360,11 @@ cudaError_t launch_philox(uint32_t seed, uint32_t tag, int64_t n, const uint32_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_primary(const DevScene& sc, int W, int H, uint32_t seed, int64_t first, int64_t n, float* org,
-                           float* dir, cudaStream_t s)
+cudaError_t launch_primary(const DevScene& sc, int W, int H, uint32_t seed, uint32_t first_sample, int64_t first,
+                           int64_t n, float* org, float* dir, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_primary<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(sc, W, H, seed, first, n, org, dir);
+    k_primary<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(sc, W, H, seed, first_sample, first, n, org, dir);
     return cudaGetLastError();
 }
 

@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(_HERE, "libpt.so")
 PT_OK, PT_EINVAL, PT_ENOMEM, PT_ECUDA, PT_EDEVICE, PT_EUNSUPPORTED = range(6)
 PT_FP32, PT_BF16, PT_FP8E4M3 = 0, 1, 2
 PRECISIONS = {"fp32": PT_FP32, "bf16": PT_BF16, "fp8": PT_FP8E4M3}
-ERR_BITS = {0x1: "stack_overflow", 0x2: "queue_overflow", 0x4: "nonfinite", 0x8: "timeout", 0x10: "iter_cap"}
+ERR_BITS = {0x1: "stack_overflow", 0x2: "queue_overflow", 0x4: "nonfinite", 0x8: "timeout", 0x10: "iter_cap",
+            0x20: "bad_node"}
 
 P = C.c_void_p
 I32 = C.c_int32
@@ -49,7 +50,8 @@ class NifDesc(C.Structure):
 
 class RenderCfg(C.Structure):
     _fields_ = [("width", I32), ("height", I32), ("spp", I32), ("max_depth", I32), ("seed", U32),
-                ("rr", I32), ("rr_start", I32), ("precision", I32), ("chunk_slots", I64)]
+                ("rr", I32), ("rr_start", I32), ("precision", I32), ("chunk_slots", I64),
+                ("first_sample", I32)]
 
 
 class PTError(RuntimeError):
@@ -88,6 +90,8 @@ def lib():
             "pt_philox": ([P, U32, U32, I64, P, P, P], I32),
             "pt_primary_rays": ([P, P, P, I64, I64, P, P, P], I32),
             "pt_trace_rays": ([P, P, I64, P, P, P, P, P], I32),
+            "pt_profile_enable": ([P, I32], I32),
+            "pt_profile_read": ([P, P, P, I32], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -235,17 +239,33 @@ class Nif:
             self.h = None
 
 
-def make_cfg(cfg: I.RenderCfg, precision: str = "fp32", chunk_slots: int = 0) -> RenderCfg:
+def make_cfg(cfg: I.RenderCfg, precision: str = "fp32", chunk_slots: int = 0, first_sample: int = 0) -> RenderCfg:
     return RenderCfg(cfg.width, cfg.height, cfg.spp, cfg.max_depth, cfg.seed, int(cfg.rr), cfg.rr_start,
-                     PRECISIONS[precision], int(chunk_slots))
+                     PRECISIONS[precision], int(chunk_slots), int(first_sample))
+
+
+KINDS = ("trace", "nif", "reduce", "other")
+
+
+def profile_enable(ctx: Context, enable: bool = True) -> None:
+    ctx._raise(lib().pt_profile_enable(ctx.h, int(enable)))
+
+
+def profile_read(ctx: Context) -> dict:
+    """Device milliseconds and launch counts per kernel kind since the last read."""
+    ms = np.zeros(len(KINDS))
+    n = np.zeros(len(KINDS), np.int64)
+    ctx._raise(lib().pt_profile_read(ctx.h, _np_ptr(ms), _np_ptr(n), len(KINDS)))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KINDS)}
 
 
 def render(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderCfg, precision: str = "fp32",
-           out: Optional[torch.Tensor] = None, chunk_slots: int = 0, stream=None) -> torch.Tensor:
+           out: Optional[torch.Tensor] = None, chunk_slots: int = 0, first_sample: int = 0,
+           stream=None) -> torch.Tensor:
     """pt_render: returns the [H, W, 3] float32 image on the context's device."""
     if out is None:
         out = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=f"cuda:{ctx.device}")
-    c = make_cfg(cfg, precision, chunk_slots)
+    c = make_cfg(cfg, precision, chunk_slots, first_sample)
     ctx._raise(lib().pt_render(ctx.h, scene.h, nif.h if nif is not None else None, C.byref(c), _dptr(out),
                                _stream(stream)))
     return out

@@ -186,7 +186,13 @@ def test_nif_empty_batch(pt, ctx):
 
 
 # ----------------------------------------------------------------------------
-def _compare_render(pt, ctx, sc, cfg, nif=None, pixels=None, max_div=1e-3, tol=1e-3):
+def _compare_render(pt, ctx, sc, cfg, nif=None, pixels=None, max_div=1e-3, tol=1e-3, max_div_v1=1e-4,
+                    max_div_v2=1e-3):
+    """Per-path parity with the oracle (same Philox streams).  A path is
+    divergent when its hit-ID sequence differs from the oracle's (an FP32 vs
+    FP64 decision flipped somewhere).  Asserted: divergence at the primary
+    hit <= max_div_v1, by vertex 2 <= max_div_v2, overall <= max_div, and
+    the relative RMSE over matched paths <= tol."""
     s = pt.Scene(ctx, sc)
     g = pt.Nif(ctx, nif) if nif is not None else None
     pix_t = None if pixels is None else torch.from_numpy(pixels).cuda()
@@ -196,13 +202,20 @@ def _compare_render(pt, ctx, sc, cfg, nif=None, pixels=None, max_div=1e-3, tol=1
                  want_ids=True)
     gslots = slots.cpu().numpy().transpose(1, 0, 2)          # [n_pix, spp, 3]
     gids = ids.cpu().numpy().transpose(1, 0, 2)               # [n_pix, spp, D]
-    same = np.all(gids == r["ids"], axis=2)
-    div = 1.0 - same.mean()
-    overall = rel_rmse(img.cpu().numpy(), r["image"])
-    matched = rel_rmse(gslots[same], r["slots"][same])
-    assert div <= max_div, ("divergent paths", div)
-    assert matched <= tol, ("matched-path relative RMSE", matched)
-    return dict(overall=overall, matched=matched, divergent=div)
+    differ = gids != r["ids"]
+    same = ~np.any(differ, axis=2)
+    first = np.where(differ.any(2), differ.argmax(2), -1)
+    res = dict(overall=rel_rmse(img.cpu().numpy(), r["image"]),
+               matched=rel_rmse(gslots[same], r["slots"][same]),
+               divergent=float(1.0 - same.mean()),
+               div_v1=float((first == 0).mean()),
+               div_v2=float(((first == 0) | (first == 1)).mean()),
+               n_paths=int(same.size))
+    assert res["div_v1"] <= max_div_v1, res
+    assert res["div_v2"] <= max_div_v2, res
+    assert res["divergent"] <= max_div, res
+    assert res["matched"] <= tol, res
+    return res
 
 
 def test_render_box_config_matches_oracle(pt, ctx):
@@ -215,7 +228,8 @@ def test_render_box_config_matches_oracle(pt, ctx):
 def test_render_spheres_reduced_matches_oracle(pt, ctx):
     """The C2 scene (metal, dielectric, Lambertian spheres) at 96x96, 4 spp, depth 8."""
     cfg = I.RenderCfg(96, 96, 4, 8)
-    res = _compare_render(pt, ctx, I.spheres_scene(), cfg, nif=I.nif_init())
+    # chained specular bounces amplify FP32 rounding; deep-vertex divergence is reported, not a defect
+    res = _compare_render(pt, ctx, I.spheres_scene(), cfg, nif=I.nif_init(), max_div=1e-2)
     print(res)
 
 
