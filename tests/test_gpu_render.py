@@ -228,8 +228,42 @@ def test_render_box_config_matches_oracle(pt, ctx):
 def test_render_spheres_reduced_matches_oracle(pt, ctx):
     """The C2 scene (metal, dielectric, Lambertian spheres) at 96x96, 4 spp, depth 8."""
     cfg = I.RenderCfg(96, 96, 4, 8)
-    # chained specular bounces amplify FP32 rounding; deep-vertex divergence is reported, not a defect
-    res = _compare_render(pt, ctx, I.spheres_scene(), cfg, nif=I.nif_init(), max_div=1e-2)
+    # Chained specular bounces amplify FP32 rounding of directions; the escape
+    # direction then feeds a sigma = 10 Fourier-feature field, so full-depth
+    # paths agree only statistically.  Tight per-path parity is asserted at
+    # depth 2 and 3 below; here divergence and matched-path error are bounded
+    # loosely and printed.
+    res = _compare_render(pt, ctx, I.spheres_scene(), cfg, nif=I.nif_init(), max_div=1e-2, tol=1e-2)
+    assert res["overall"] <= 2e-2, res
+    print(res)
+
+
+@pytest.mark.parametrize("depth", [2, 3])
+def test_render_spheres_shallow_matches_oracle(pt, ctx, depth):
+    """One or two bounces off Lambertian, GGX-metal and dielectric spheres:
+    per-path radiance matches the oracle to 1e-3 (pins every lobe's weight
+    and direction on the GPU)."""
+    cfg = I.RenderCfg(128, 128, 4, depth)
+    # a single divergent path can carry more image error than all matched
+    # paths together, so the matched-path RMSE is the quantity held to 1e-3
+    # and divergence is bounded separately
+    res = _compare_render(pt, ctx, I.spheres_scene(), cfg, nif=I.nif_init(), max_div=1e-4)
+    print(res)
+
+
+@pytest.mark.parametrize("kind", [I.METAL, I.DIELECTRIC])
+def test_furnace_specular_on_gpu(pt, ctx, kind):
+    """Specular furnaces on the GPU: dielectric paths gather exactly 0 or 1;
+    metal (F0 = 1) paths agree with the oracle path by path."""
+    sc = I.furnace_sphere_outside(kind=kind, f0=1.0, roughness=0.3)
+    cfg = I.RenderCfg(48, 48, 4, 6)
+    res = _compare_render(pt, ctx, sc, cfg, max_div=2e-3, tol=1e-4)
+    if kind == I.DIELECTRIC:
+        s = pt.Scene(ctx, sc)
+        _, slots, _ = pt.render_pixels(ctx, s, None, cfg, None, want_slots=True)
+        ctx.check()
+        L = slots.cpu().numpy()
+        assert np.all((L == 0.0) | (L == 1.0))
     print(res)
 
 
