@@ -244,6 +244,30 @@ PT_API pt_status pt_primary_rays(pt_ctx* ctx, const pt_scene* scene, const pt_re
 PT_API pt_status pt_trace_rays(pt_ctx* ctx, const pt_scene* scene, int64_t n, const float* d_org, const float* d_dir,
                                float* d_t, int32_t* d_prim, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Rendering without device allocation.  The paper has no counterpart: this */
+/* serves callers that may not allocate device memory at render time (a host */
+/* application that owns all GPU memory through its own pool, or a real-time */
+/* loop that must stay off the driver's allocator).                         */
+/* ------------------------------------------------------------------------ */
+
+/* Same image as pt_render with precision PT_FP32, but every byte of wavefront
+   scratch comes from one fixed array compiled into the library (about 41 MiB
+   per GPU, held until the process exits); the call makes no cudaMalloc,
+   cudaFree or other allocating call.  Limits: at most 262144 pixels per
+   frame (one sample of the frame must fit the array) and the FP32 network;
+   larger frames return PT_EINVAL, other precisions PT_EUNSUPPORTED.
+   The scene's device must be current.  The first call on a device looks up
+   the array's device address there; make that first call before capturing
+   the stream into a graph.  All calls share the array and it keeps the last
+   call's contents (the call clears what must start at zero), so calls whose
+   GPU work overlaps race: serialise them on one stream.  d_err (nullable,
+   caller-owned device word) receives the PT_ERR_* bits the kernels set;
+   without it they are discarded.  No context is needed; failures are
+   reported by the return code only. */
+PT_API pt_status pt_render_noalloc(const pt_scene* scene, const pt_nif* nif, const pt_render_cfg* cfg,
+                                   float* d_image, uint32_t* d_err, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

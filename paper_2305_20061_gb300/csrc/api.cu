@@ -196,6 +196,12 @@ pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, cudaSt
 
 }  // namespace
 
+// Read-only views of the opaque handles for other translation units.
+namespace ptk {
+const DevScene* scene_view(const pt_scene* s, int* device) { if (device) *device = s->ctx->device; return &s->dev; }
+const DevNif* nif_view(const pt_nif* n) { return &n->dev; }
+}  // namespace ptk
+
 // ---------------------------------------------------------------------------
 extern "C" {
 

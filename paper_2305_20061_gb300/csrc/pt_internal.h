@@ -130,6 +130,10 @@ cudaError_t launch_trace_rays(const DevScene& sc, int64_t n, const float* org, c
 // NIF kernels (nif_fp32.cu)
 cudaError_t launch_nif_fp32(const NifEvalParams& p, int mode, int sm_count, cudaStream_t s);
 
+// read-only views of the C-ABI handles (api.cu)
+const DevScene* scene_view(const pt_scene* s, int* device);
+const DevNif* nif_view(const pt_nif* n);
+
 // host BVH builder (bvh_build.cpp)
 struct BuildInput {
     int64_t n_prims;

@@ -92,6 +92,7 @@ def lib():
             "pt_trace_rays": ([P, P, I64, P, P, P, P, P], I32),
             "pt_profile_enable": ([P, I32], I32),
             "pt_profile_read": ([P, P, P, I32], I32),
+            "pt_render_noalloc": ([P, P, P, P, P, P], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
