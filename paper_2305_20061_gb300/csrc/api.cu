@@ -48,6 +48,7 @@ struct pt_nif {
     int64_t n_params = 0;
     float* d_params = nullptr;   // flat FP32 master weights
     float* d_fp32 = nullptr;     // packed FP32 layout (Wt, bias, Wout, bout)
+    unsigned char* d_tc = nullptr;  // BF16 shared-memory image of the tensor-core kernel (F=64, H=128, L=3 only)
     DevNif dev = {};
 };
 
@@ -191,7 +192,11 @@ pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, cudaSt
         PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_fp32(p, 1, ctx->sm_count, s); }));
         return PT_OK;
     }
-    return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF precision not available in this build");
+    if (precision == PT_BF16 && nif->d_tc) {
+        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nif->d_tc, p, 1, ctx->sm_count, s); }));
+        return PT_OK;
+    }
+    return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3 (FP8 not in this build)");
 }
 
 }  // namespace
@@ -481,6 +486,14 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
     v.bout = v.Wout + 3 * 128;
     v.B = v.bout + 3;
     for (int i = 0; i < 9; ++i) v.M[i] = d->params[n - 9 + i];
+    std::vector<unsigned char> img;
+    if (pack_nif_tc_image(d->params, F, H, L, img)) {
+        if (cudaMalloc((void**)&nf->d_tc, img.size()) != cudaSuccess ||
+            cudaMemcpy(nf->d_tc, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            pt_destroy_nif(nf);
+            return fail(ctx, PT_ENOMEM, "NIF tensor-core image upload failed");
+        }
+    }
     *out = nf;
     return PT_OK;
 }
@@ -490,6 +503,7 @@ PT_API void pt_destroy_nif(pt_nif* nf)
     if (!nf) return;
     cudaFree(nf->d_params);
     cudaFree(nf->d_fp32);
+    cudaFree(nf->d_tc);
     delete nf;
 }
 
@@ -514,13 +528,17 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
     p.rgb = d_rgb;
     p.n = n;
     p.err = ctx->d_err;
+    cudaStream_t s = (cudaStream_t)stream;
     if (precision == PT_FP32) {
-        cudaStream_t s = (cudaStream_t)stream;
         PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_fp32(p, 0, ctx->sm_count, s); }));
         return PT_OK;
     }
+    if (precision == PT_BF16 && nf->d_tc) {
+        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nf->d_tc, p, 0, ctx->sm_count, s); }));
+        return PT_OK;
+    }
     if (precision == PT_BF16 || precision == PT_FP8E4M3)
-        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF precision not available in this build");
+        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3 (FP8 not in this build)");
     return fail(ctx, PT_EINVAL, "unknown precision");
 }
 
@@ -537,8 +555,8 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
     if (n_pix == 0) return PT_OK;
     const int64_t n_slots = n_pix * (int64_t)cfg->spp;
     if (n_slots > 0xFFFFFFFFll) return fail(ctx, PT_EINVAL, "more than 2^32 - 1 paths in one call");
-    if (sc->dev.env_is_nif && cfg->precision != PT_FP32)
-        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF precision not available in this build");
+    if (sc->dev.env_is_nif && cfg->precision != PT_FP32 && !(cfg->precision == PT_BF16 && nf->d_tc))
+        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3 (FP8 not in this build)");
     cudaStream_t s = (cudaStream_t)stream;
     // chunk = whole samples
     int64_t chunk = cfg->chunk_slots > 0 ? cfg->chunk_slots : (int64_t)1 << 24;

@@ -1,0 +1,481 @@
+// Fused tensor-core evaluation of the HDR neural image field (Section 3.2)
+// for the shape F = 64 frequencies, three hidden FC-128 ReLU layers, FC-3
+// head, on sm_103a tcgen05 tensor cores.
+//
+// The paper keeps the network's weights in IPU tile SRAM and lets the
+// Poplibs planner replicate layers across tiles (Section 3.3.1); here one
+// persistent CTA per SM holds all BF16 weights in shared memory for the
+// whole kernel and streams 128-row tiles of queries through them:
+//
+//   warps 0..11  three warpgroups; warpgroup s owns tile slot s.  Thread t
+//                of a warpgroup owns row t of its tile, which is TMEM lane t.
+//                It computes the row's Fourier features, and after each MMA
+//                reads its accumulator row from TMEM, adds the bias, applies
+//                ReLU while packing to BF16 and writes the row back into the
+//                slot's operand buffer in the UMMA SWIZZLE_128B K-major layout.
+//   warp 12      allocates TMEM; lane 0 issues every tcgen05.mma (128x128x16
+//                BF16 -> FP32 for the hidden layers, 128x16x16 for the head)
+//                and commits each layer to the slot's mbarrier.
+//
+// Three slots in flight let the epilogue of one tile overlap the MMAs of
+// the others.  Every wait is bounded in time: a wait that gives up sets
+// PT_ERR_TIMEOUT, raises a CTA-wide abort flag, drains in-flight MMAs and
+// frees TMEM before the CTA returns.
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace ptk {
+
+namespace {
+
+constexpr int kF = 64, kH = 128, kRows = 128;
+constexpr int kSlots = 3;
+constexpr int kThreads = 13 * 32;
+constexpr int kMmaWarp = 12;
+constexpr uint32_t kTmemCols = 512;
+
+// shared-memory image (offsets from a 1024-byte aligned base)
+constexpr uint32_t kWBytes = kH * kH * 2;            // 32 KB per hidden layer (2 K-blocks x 128 rows x 128 B)
+constexpr uint32_t kHeadRows = 16;
+constexpr uint32_t kHeadBytes = kHeadRows * kH * 2;  // 4 KB
+constexpr uint32_t kOffW = 0;                        // W1 | W2 | W3
+constexpr uint32_t kOffHead = 3 * kWBytes;           // 98304
+constexpr uint32_t kOffTail = kOffHead + kHeadBytes; // 102400: fp32 b1 b2 b3 [384], b4 [4], B [128], M [12]
+constexpr uint32_t kTailFloats = 3 * kH + 4 + 2 * kF + 12;
+constexpr uint32_t kImageBytes = kOffTail + kTailFloats * 4;  // 104512
+constexpr uint32_t kOffA = 105472;                   // 1024-aligned, three 32 KB activation buffers
+constexpr uint32_t kABytes = kRows * kH * 2;
+constexpr uint32_t kOffBar = kOffA + kSlots * kABytes;  // 203776
+constexpr uint32_t kSmemBytes = kOffBar + 128 + 1024;   // barriers + alignment slack
+
+static_assert(kImageBytes % 16 == 0, "bulk copy size");
+static_assert(kOffA % 1024 == 0 && kOffHead % 1024 == 0, "swizzle atoms need 1024-byte alignment");
+
+// --- PTX wrappers -----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kWaitBudgetNs = 2000000000ull;  // 2 s per wait
+
+// Bounded wait for `parity` on an mbarrier; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t* err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+        if (global_ns() - t0 > kWaitBudgetNs) {
+            atomicOr(err, PT_ERR_TIMEOUT);
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, SWIZZLE_128B, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(1024u >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+#define TMEM_LD32(taddr, r)                                                                                       \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "                                                        \
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"                                      \
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                     \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), \
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),      \
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),    \
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),    \
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                                          \
+                 : "r"(taddr))
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t r[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi)
+{
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// byte offset of the 16-byte chunk holding elements [8c, 8c+8) of row r of a
+// 128-row, 128-column BF16 operand in SWIZZLE_128B K-major form
+__device__ __forceinline__ uint32_t sw128_chunk(uint32_t r, uint32_t c)
+{
+    return (c >> 3) * (kRows * 128) + r * 128 + (((c & 7) ^ (r & 7)) << 4);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+struct TcParams {
+    const unsigned char* image;  // packed weights (kImageBytes)
+    // mode 0
+    const float* uv;
+    float* rgb;
+    int64_t n;
+    // mode 1
+    const EscapeRec* esc;
+    const uint32_t* esc_count;
+    uint32_t esc_cap;
+    float* slot_L;
+    uint32_t* err;
+    unsigned long long* stats;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mode)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar_a = sbase + kOffBar;            // [kSlots] operand ready (count 128)
+    const uint32_t bar_acc = bar_a + 8 * kSlots;        // [kSlots] accumulator ready (commit)
+    const uint32_t bar_w = bar_acc + 8 * kSlots;        // weights loaded
+    const uint32_t bar_drain = bar_w + 8;               // final drain after an abort
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 64);
+    volatile int* abort = reinterpret_cast<volatile int*>(smem + kOffBar + 68);
+    const float* tail = reinterpret_cast<const float*>(smem + kOffTail);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t count = mode == 0 ? p.n : (int64_t)min(*p.esc_count, p.esc_cap);
+    const int64_t n_tiles = (count + kRows - 1) / kRows;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(bar_a + 8 * s, kRows);
+            mbar_init(bar_acc + 8 * s, 1);
+        }
+        mbar_init(bar_w, 1);
+        mbar_init(bar_drain, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // one bulk copy per 32 KB piece of the weight image, all on bar_w
+        mbar_expect_tx(bar_w, kImageBytes);
+        for (uint32_t off = 0; off < kImageBytes; off += 32768u) {
+            const uint32_t sz = min(32768u, kImageBytes - off);
+            bulk_g2s(sbase + off, p.image + off, sz, bar_w);
+        }
+    }
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    mbar_wait(bar_w, 0, abort, p.err);
+
+    if (warp == kMmaWarp) {
+        // ------------------------------------------------------------- MMA issuer
+        if (lane == 0 && !*abort) {
+            const uint32_t id_h = idesc_bf16(128, 128), id_o = idesc_bf16(128, kHeadRows);
+            uint32_t ph[kSlots] = {0, 0, 0};
+            bool stop = false;
+            for (int64_t i = 0; !stop; ++i) {
+                bool any = false;
+                for (int stage = 0; stage < 4 && !stop; ++stage) {
+                    for (int s = 0; s < kSlots; ++s) {
+                        const int64_t tile = ((int64_t)i * gridDim.x + blockIdx.x) * kSlots + s;
+                        if (tile >= n_tiles) continue;
+                        any = true;
+                        if (!mbar_wait(bar_a + 8 * s, ph[s], abort, p.err)) { stop = true; break; }
+                        ph[s] ^= 1;
+                        tc_fence_after();
+                        const uint32_t a_base = sbase + kOffA + s * kABytes;
+                        if (stage < 3) {
+                            const uint32_t w_base = sbase + kOffW + stage * kWBytes;
+                            const uint32_t d = tmem + s * 128;
+#pragma unroll
+                            for (int kk = 0; kk < 8; ++kk) {
+                                const uint32_t koff = (kk >> 2) * (kRows * 128) + (kk & 3) * 32;
+                                mma_bf16(d, sw128_desc(a_base + koff), sw128_desc(w_base + koff), id_h, kk > 0);
+                            }
+                        } else {
+                            const uint32_t d = tmem + 384 + 32 * s;
+#pragma unroll
+                            for (int kk = 0; kk < 8; ++kk) {
+                                const uint32_t aoff = (kk >> 2) * (kRows * 128) + (kk & 3) * 32;
+                                const uint32_t boff = (kk >> 2) * (kHeadRows * 128) + (kk & 3) * 32;
+                                mma_bf16(d, sw128_desc(a_base + aoff), sw128_desc(sbase + kOffHead + boff), id_o, kk > 0);
+                            }
+                        }
+                        mma_commit(bar_acc + 8 * s);
+                    }
+                }
+                if (!any) break;
+            }
+            if (*abort) {
+                // make sure no MMA is still writing TMEM before it is freed
+                mma_commit(bar_drain);
+                const uint64_t t0 = global_ns();
+                while (!mbar_try_wait(bar_drain, 0) && global_ns() - t0 < kWaitBudgetNs) {
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------- epilogue warps
+        const int s = warp >> 2;                       // tile slot
+        const uint32_t row = (warp & 3) * 32 + lane;   // row in tile == TMEM lane
+        const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
+        const uint32_t a_base = sbase + kOffA + s * kABytes;
+        const float* Bm = tail + 3 * kH + 4;
+        const float* Mm = Bm + 2 * kF;
+        uint32_t ph = 0;
+        for (int64_t i = 0;; ++i) {
+            const int64_t tile = ((int64_t)i * gridDim.x + blockIdx.x) * kSlots + s;
+            if (tile >= n_tiles) break;
+            if (__any_sync(0xFFFFFFFFu, *abort != 0)) break;  // warp-uniform exit
+            const int64_t g = tile * kRows + row;
+            const bool valid = g < count;
+            float u = 0.f, v = 0.f, tr = 0.f, tg = 0.f, tb = 0.f;
+            uint32_t slot = 0;
+            if (valid) {
+                if (mode == 0) {
+                    const float2 q = reinterpret_cast<const float2*>(p.uv)[g];
+                    u = q.x; v = q.y;
+                } else {
+                    const float2* e = reinterpret_cast<const float2*>(p.esc + g);
+                    const float2 a = e[0], b = e[1], c = e[2];
+                    slot = __float_as_uint(a.x); u = a.y; v = b.x; tr = b.y; tg = c.x; tb = c.y;
+                }
+            }
+            // Fourier features [sin 2 pi (Bx)_i, cos 2 pi (Bx)_i]: phase reduced to one turn in FP32,
+            // then the hardware sine / cosine (the result is rounded to BF16)
+#pragma unroll 1
+            for (int c8 = 0; c8 < kF / 8; ++c8) {
+                uint32_t sp[4], cp[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float sv[2], cv[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int f = c8 * 8 + 2 * j + h;
+                        const float t = fmaf(Bm[2 * f], u, Bm[2 * f + 1] * v);
+                        const float r = t - rintf(t);
+                        __sincosf(6.28318530717958648f * r, &sv[h], &cv[h]);
+                    }
+                    sp[j] = pack_bf16(sv[0], sv[1]);
+                    cp[j] = pack_bf16(cv[0], cv[1]);
+                }
+                st_shared_v4(a_base + sw128_chunk(row, c8), sp[0], sp[1], sp[2], sp[3]);
+                st_shared_v4(a_base + sw128_chunk(row, kF / 8 + c8), cp[0], cp[1], cp[2], cp[3]);
+            }
+            fence_proxy_async();
+            mbar_arrive(bar_a + 8 * s);
+
+            bool ok = true;
+            for (int layer = 0; layer < 3; ++layer) {
+                const bool got = mbar_wait(bar_acc + 8 * s, ph, abort, p.err);
+                if (!__all_sync(0xFFFFFFFFu, got)) { ok = false; break; }  // tcgen05.ld needs the whole warp
+                ph ^= 1;
+                tc_fence_after();
+                const float* bias = tail + layer * kH;
+#pragma unroll 1
+                for (int c32 = 0; c32 < 4; ++c32) {
+                    uint32_t r[32];
+                    TMEM_LD32(tmem + lane_base + s * 128 + c32 * 32, r);
+                    tmem_wait_ld();
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float lo = __uint_as_float(r[2 * j]) + bias[c32 * 32 + 2 * j];
+                        const float hi = __uint_as_float(r[2 * j + 1]) + bias[c32 * 32 + 2 * j + 1];
+                        pk[j] = pack_relu_bf16(lo, hi);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        st_shared_v4(a_base + sw128_chunk(row, c32 * 4 + q), pk[4 * q], pk[4 * q + 1],
+                                     pk[4 * q + 2], pk[4 * q + 3]);
+                }
+                tc_fence_before();
+                fence_proxy_async();
+                mbar_arrive(bar_a + 8 * s);
+            }
+            if (!ok) break;
+            const bool got_head = mbar_wait(bar_acc + 8 * s, ph, abort, p.err);
+            if (!__all_sync(0xFFFFFFFFu, got_head)) break;
+            ph ^= 1;
+            tc_fence_after();
+            uint32_t yr[4];
+            tmem_ld4(tmem + lane_base + 384 + 32 * s, yr);
+            tmem_wait_ld();
+            const float* b4 = tail + 3 * kH;
+            const float y0 = __uint_as_float(yr[0]) + b4[0];
+            const float y1 = __uint_as_float(yr[1]) + b4[1];
+            const float y2 = __uint_as_float(yr[2]) + b4[2];
+            const float r0 = expf(Mm[0] * y0 + Mm[1] * y1 + Mm[2] * y2);
+            const float r1 = expf(Mm[3] * y0 + Mm[4] * y1 + Mm[5] * y2);
+            const float r2 = expf(Mm[6] * y0 + Mm[7] * y1 + Mm[8] * y2);
+            if (valid) {
+                if (mode == 0) {
+                    p.rgb[3 * g] = r0; p.rgb[3 * g + 1] = r1; p.rgb[3 * g + 2] = r2;
+                } else {
+                    float* L = p.slot_L + 3 * (size_t)slot;
+                    const float a = L[0] + tr * r0, b = L[1] + tg * r1, c = L[2] + tb * r2;
+                    if (!(isfinite(a) && isfinite(b) && isfinite(c))) atomicOr(p.err, PT_ERR_NONFINITE);
+                    L[0] = a; L[1] = b; L[2] = c;
+                }
+            }
+            tc_fence_before();
+        }
+    }
+    if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0 && p.stats) atomicAdd(p.stats, (unsigned long long)count);
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+}  // namespace
+
+// Host-side packing of the weight image for k_nif_tc (see the offsets above).
+// W[l] are PyTorch-layout [out][in] float matrices.
+bool pack_nif_tc_image(const float* params, int F, int H, int L, std::vector<unsigned char>& out)
+{
+    if (F != kF || H != kH || L != 3) return false;
+    out.assign(kImageBytes, 0);
+    auto to_bf16 = [](float x) -> uint16_t {
+        uint32_t u;
+        std::memcpy(&u, &x, 4);
+        const uint32_t rounding = 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even
+        return (uint16_t)((u + rounding) >> 16);
+    };
+    auto put = [&](uint32_t base, uint32_t rows_total, uint32_t r, uint32_t k, float x) {
+        const uint32_t off = base + (k >> 6) * (rows_total * 128) + r * 128 + ((((k & 63) >> 3) ^ (r & 7)) << 4) +
+                             (k & 7) * 2;
+        const uint16_t b = to_bf16(x);
+        std::memcpy(&out[off], &b, 2);
+    };
+    const float* p = params;
+    const float* Bsrc = p;
+    p += 2 * F;
+    float* tail = reinterpret_cast<float*>(&out[kOffTail]);
+    for (int l = 0; l <= L; ++l) {
+        const int in = l == 0 ? 2 * F : H, o = l == L ? 3 : H;
+        if (l < L) {
+            for (int j = 0; j < o; ++j)
+                for (int k = 0; k < in; ++k) put(kOffW + l * kWBytes, kRows, j, k, p[(size_t)j * in + k]);
+            p += (size_t)in * o;
+            for (int j = 0; j < o; ++j) tail[l * kH + j] = p[j];
+            p += o;
+        } else {
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < in; ++k) put(kOffHead, kHeadRows, j, k, p[(size_t)j * in + k]);
+            p += (size_t)in * 3;
+            for (int j = 0; j < 3; ++j) tail[3 * kH + j] = p[j];
+            p += 3;
+        }
+    }
+    for (int i = 0; i < 2 * F; ++i) tail[3 * kH + 4 + i] = Bsrc[i];
+    for (int i = 0; i < 9; ++i) tail[3 * kH + 4 + 2 * F + i] = p[i];
+    return true;
+}
+
+cudaError_t launch_nif_tc(const unsigned char* image, const NifEvalParams& np, int mode, int sm_count, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_nif_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    TcParams p = {};
+    p.image = image;
+    p.uv = np.uv;
+    p.rgb = np.rgb;
+    p.n = np.n;
+    p.esc = np.esc;
+    p.esc_count = np.esc_count;
+    p.esc_cap = np.esc_cap;
+    p.slot_L = np.slot_L;
+    p.err = np.err;
+    p.stats = np.stats;
+    k_nif_tc<<<sm_count, kThreads, kSmemBytes, s>>>(p, mode);
+    return cudaGetLastError();
+}
+
+size_t nif_tc_image_bytes() { return kImageBytes; }
+
+}  // namespace ptk

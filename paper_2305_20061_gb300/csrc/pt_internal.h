@@ -130,6 +130,11 @@ cudaError_t launch_trace_rays(const DevScene& sc, int64_t n, const float* org, c
 // NIF kernels (nif_fp32.cu)
 cudaError_t launch_nif_fp32(const NifEvalParams& p, int mode, int sm_count, cudaStream_t s);
 
+// tensor-core NIF (nif_tc.cu): F = 64, H = 128, L = 3 only
+bool pack_nif_tc_image(const float* params, int F, int H, int L, std::vector<unsigned char>& out);
+cudaError_t launch_nif_tc(const unsigned char* image, const NifEvalParams& p, int mode, int sm_count, cudaStream_t s);
+size_t nif_tc_image_bytes();
+
 // read-only views of the C-ABI handles (api.cu)
 const DevScene* scene_view(const pt_scene* s, int* device);
 const DevNif* nif_view(const pt_nif* n);

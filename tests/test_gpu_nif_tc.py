@@ -1,0 +1,107 @@
+"""The fused tcgen05 BF16 NIF kernel through the C ABI.
+
+Two references: a numpy model of the kernel's own rounding (BF16 operands,
+FP32 accumulation, FP32 bias, ReLU, BF16 repack between layers), which the
+kernel must match to FP32 accumulation-order noise, and the FP64 oracle, from
+which the BF16 error is reported as a log-RMSE."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2305_20061_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pt():
+    from paper_2305_20061_gb300 import build
+    build.build()
+    from paper_2305_20061_gb300 import pt as _pt
+    return _pt
+
+
+@pytest.fixture(scope="module")
+def ctx(pt):
+    return pt.Context(0)
+
+
+def bf16(x):
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def bf16_model(nif, uv):
+    """Rounding model of the tensor-core kernel (FP64 sums stand in for FP32
+    accumulation; the difference is accumulation-order noise)."""
+    uv = uv.astype(np.float32)
+    B = nif.B.astype(np.float64)
+    t = (B[:, 0][None] * uv[:, :1].astype(np.float64) + B[:, 1][None] * uv[:, 1:].astype(np.float64))
+    t = t.astype(np.float32).astype(np.float64)
+    r = t - np.rint(t)
+    h = bf16(np.concatenate([np.sin(2 * np.pi * r), np.cos(2 * np.pi * r)], 1).astype(np.float32))
+    h = h.astype(np.float64)
+    for W, b in zip(nif.W[:-1], nif.b[:-1]):
+        a = h @ bf16(W).astype(np.float64).T + b.astype(np.float64)
+        h = bf16(np.maximum(a, 0).astype(np.float32)).astype(np.float64)
+    y = h @ bf16(nif.W[-1]).astype(np.float64).T + nif.b[-1].astype(np.float64)
+    z = y @ nif.M.astype(np.float64).T
+    return np.exp(z)
+
+
+@pytest.mark.parametrize("n", [1, 127, 128 * 3 + 5, 128 * 152 * 3 * 2 + 77])
+def test_bf16_nif_matches_rounding_model(pt, ctx, n):
+    nif = I.nif_init(colour="yuv")
+    rng = np.random.default_rng(n)
+    for b in nif.b:
+        b[:] = rng.normal(0, 0.05, b.shape)
+    g = pt.Nif(ctx, nif)
+    uv = I.uniform_uv(n, seed=n)
+    got = g.eval(torch.from_numpy(uv).cuda(), precision="bf16").cpu().numpy().astype(np.float64)
+    ctx.check()
+    ref = bf16_model(nif, uv)
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert np.all(np.isfinite(got))
+    assert np.median(rel) <= 2e-4 and rel.max() <= 2e-2, (np.median(rel), rel.max())
+
+
+def test_bf16_nif_error_vs_oracle(pt, ctx):
+    """BF16 operands with FP32 accumulation against the FP64 oracle: the
+    per-channel log-RMSE is reported (no threshold is fixed by the method);
+    a loose bound guards against gross errors."""
+    nif = I.nif_init(colour="yuv")
+    g = pt.Nif(ctx, nif)
+    uv = I.uniform_uv(20000, seed=9)
+    got = g.eval(torch.from_numpy(uv).cuda(), precision="bf16").cpu().numpy().astype(np.float64)
+    f32 = g.eval(torch.from_numpy(uv).cuda(), precision="fp32").cpu().numpy().astype(np.float64)
+    ctx.check()
+    ref, _ = O.Nif(nif).forward(uv.astype(np.float64))
+    log_rmse = float(np.sqrt(np.mean((np.log(got) - np.log(ref)) ** 2)))
+    log_rmse_f32 = float(np.sqrt(np.mean((np.log(f32) - np.log(ref)) ** 2)))
+    print({"bf16_log_rmse": log_rmse, "fp32_log_rmse": log_rmse_f32})
+    assert log_rmse < 0.05 and log_rmse_f32 < 1e-5
+
+
+def test_bf16_nif_rejects_other_shapes(pt, ctx):
+    g = pt.Nif(ctx, I.nif_init(n_freq=32))
+    with pytest.raises(pt.PTError) as e:
+        g.eval(torch.zeros((10, 2), device="cuda"), precision="bf16")
+    assert e.value.status == pt.PT_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("config", ["C1", "C2"])
+def test_bf16_render_close_to_fp32(pt, ctx, config):
+    sc = I.make_scene(config)
+    cfg = I.RenderCfg(128, 128, 4, 4)
+    s = pt.Scene(ctx, sc)
+    g = pt.Nif(ctx, I.nif_init(colour="yuv"))
+    a = pt.render(ctx, s, g, cfg, "fp32").cpu().numpy().astype(np.float64)
+    b = pt.render(ctx, s, g, cfg, "bf16").cpu().numpy().astype(np.float64)
+    b2 = pt.render(ctx, s, g, cfg, "bf16").cpu().numpy().astype(np.float64)
+    ctx.check()
+    rel = float(np.sqrt(((a - b) ** 2).sum() / (a ** 2).sum()))
+    print({"config": config, "bf16_vs_fp32_rel_rmse": rel})
+    assert np.array_equal(b, b2)
+    assert rel < 0.05
