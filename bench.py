@@ -3,9 +3,11 @@
 A step is one full frame of the spheres + HDR-NIF workload (256 spheres,
 512x512 pixels, 64 samples per pixel, depth 8: 16.8M paths) rendered through
 the C ABI: camera rays, traversal, bounce sampling, NIF shading of every
-escape and the sample reduction.  Prints one JSON line (rank 0).
+escape (BF16 tensor-core kernel by default) and the sample reduction.  The
+same line reports the FP32-network frame rate and the relative RMSE between
+the BF16 and FP32 frames.  Prints one JSON line (rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
   python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
 
 Multi-GPU (torchrun, one rank per GPU): each rank renders its own disjoint
@@ -35,14 +37,15 @@ FLOP_PER_EVAL = 2 * (3 * 128 * 128 + 128 * 3)   # 99,072: three 128x128 layers +
 TC_FLOP_PER_EVAL = 2 * 3 * 128 * 128            # 98,304 in the three hidden layers
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# FP32 operations per traversal step as implemented
+OPS_NODE, OPS_SPHERE, OPS_QUAD, OPS_TRI = 58, 36, 12, 46
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
 def peaks():
     try:
         with open(MEASURED) as f:
-            m = json.load(f)
-        return m, "measured"
+            return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
             "fallback"
@@ -82,7 +85,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -91,22 +94,33 @@ class ClockSampler:
             try:
                 sm.append(float(f[1]))
                 mx.append(float(f[2]))
+                pw.append(float(f[3]))
             except ValueError:
                 continue
             for n, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload(precision, spp=None):
+def workload(spp=None):
     sc = I.make_scene(WORKLOAD)
     cfg = I.CONFIGS[WORKLOAD]["cfg"]
     if spp:  # smaller case for profiler captures only
         cfg = I.RenderCfg(cfg.width, cfg.height, spp, cfg.max_depth, cfg.seed)
     nif = I.nif_init(colour="yuv")
     return sc, cfg, nif
+
+
+def config_dict(cfg, precision):
+    return {"workload": f"{WORKLOAD}: 256 spheres (60% Lambertian / 30% GGX metal / 10% dielectric) + HDR-NIF "
+                        f"environment, {cfg.width}x{cfg.height}, {cfg.spp} spp, max depth {cfg.max_depth}, no RR",
+            "paths_per_frame": cfg.n_slots,
+            "nif": "F=64 Gaussian Fourier (sigma 10) -> 3x FC-128 ReLU -> FC-3 -> YUV->RGB -> exp, random init",
+            "nif_precision": precision,
+            "l2": "per-step working set > L2 (wavefront queues ~2.7 GB) and a 512 MB L2 flush between timed "
+                  "steps (outside the timed events)"}
 
 
 # ----------------------------------------------------------------------------
@@ -132,10 +146,9 @@ def oracle_rate(sc, cfg, nif, target_s: float, n_threads: int):
 
 
 def bench_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return 0
-    sc, cfg, nif = workload(args.precision, args.spp)
+    sc, cfg, nif = workload(args.spp)
     threads = os.cpu_count() or 1
     run, n_pix = oracle_rate(sc, cfg, nif, target_s=args.ref_step_s, n_threads=threads)
     for _ in range(args.warmup):
@@ -147,24 +160,15 @@ def bench_reference(args):
         total_t += dt
     value = total_paths / total_t / 1e6
     sample = f"all {cfg.spp} samples of {n_pix} evenly strided pixels of the {cfg.width}x{cfg.height} frame per step"
-    line = {
+    print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_dict(cfg, "fp64-oracle"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line))
+    }))
     return 0
-
-
-def config_dict(cfg, precision):
-    return {"workload": f"{WORKLOAD}: 256 spheres (60% Lambertian / 30% GGX metal / 10% dielectric) + HDR-NIF "
-                        f"environment, {cfg.width}x{cfg.height}, {cfg.spp} spp, max depth {cfg.max_depth}, no RR",
-            "paths_per_frame": cfg.n_slots, "nif": "F64 Fourier (sigma 10) -> 3x FC-128 ReLU -> FC-3 -> YUV->RGB -> exp",
-            "nif_precision": precision, "l2": "per-step working set > L2 (wavefront queues ~2.7 GB) and a 512 MB "
-                                              "L2 flush between timed steps (outside the timed events)"}
 
 
 # ----------------------------------------------------------------------------
@@ -182,88 +186,126 @@ def bench_ours(args):
     build.build()
     from paper_2305_20061_gb300 import pt
 
-    sc, cfg, nif = workload(args.precision, args.spp)
+    dev = f"cuda:{local}"
+    sc, cfg, nif = workload(args.spp)
     ctx = pt.Context(local)
     scene = pt.Scene(ctx, sc)
     gnif = pt.Nif(ctx, nif)
-    img = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=f"cuda:{local}")
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    img = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     first_sample = rank * cfg.spp
-
-    def step():
-        pt.render(ctx, scene, gnif, cfg, args.precision, out=img, first_sample=first_sample)
-
-    for _ in range(args.warmup):
-        step()
-    ctx.check()
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
+    def timed_frames(precision, steps, profile=False):
+        for _ in range(args.warmup):
+            pt.render(ctx, scene, gnif, cfg, precision, out=img, first_sample=first_sample)
+        ctx.check()
+        if profile:
+            pt.profile_enable(ctx, True)
+            pt.profile_read(ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        for i in range(steps):
+            flush.fill_(float(i))           # evict L2 between timed steps (not timed)
+            ev[i][0].record(stream)
+            pt.render(ctx, scene, gnif, cfg, precision, out=img, first_sample=first_sample)
+            ev[i][1].record(stream)
+        barrier()
+        prof = pt.profile_read(ctx) if profile else None
+        if profile:
+            pt.profile_enable(ctx, False)
+        ctx.check()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, prof
+
     sampler = ClockSampler(local)
     sampler.start()
-    time.sleep(0.25)
-    pt.profile_enable(ctx, True)
-    pt.profile_read(ctx)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    for i in range(args.steps):
-        flush.fill_(float(i))           # evict L2 between timed steps (not timed)
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
-    barrier()
+    time.sleep(0.3)
+    ms, prof = timed_frames(args.precision, args.steps, profile=True)
     clocks = sampler.stop()
-    prof = pt.profile_read(ctx)
-    pt.profile_enable(ctx, False)
-    ctx.check()
     counts = pt.last_render_counts(ctx, cfg.max_depth)
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    work = pt.last_render_work(ctx)
     paths = cfg.n_slots
     value = world * paths / (ms * 1e-3) / 1e6
-
-    # live roofline of the dominant kernel
-    meas, which = peaks()
-    dom = max(prof, key=lambda k: prof[k][0])
     evals = int(counts[cfg.max_depth])
+    rays = int(counts[:cfg.max_depth].sum())
     nif_ms = prof["nif"][0] / args.steps
-    roof = None
-    if dom == "nif":
-        if args.precision == "fp32":
-            clock = float(meas.get("sm_max_mhz", 2070.0))
-            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock * 1e6 / 1e12
-            achieved = evals * FLOP_PER_EVAL / (nif_ms * 1e-3) / 1e12
-            roof = {"kernel": "k_nif_fp32", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "peak_note": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 FLOP x {clock:.0f} MHz"}
-        else:
-            peak = float(meas["bf16_tflops_sustained" if "bf16_tflops_sustained" in meas else "bf16_tflops"])
-            achieved = evals * TC_FLOP_PER_EVAL / (nif_ms * 1e-3) / 1e12
-            roof = {"kernel": "k_nif_tc", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "peak_note": f"dense BF16, sustained ({which})"}
-    else:
-        clock = float(meas.get("sm_max_mhz", 2070.0))
+    trace_ms = prof["trace"][0] / args.steps
+
+    # the other precision on the same frame, and the image difference between them
+    other = "fp32" if args.precision == "bf16" else "bf16"
+    ms_other, rel_rmse = None, None
+    if not args.no_compare:
+        ms_other, _ = timed_frames(other, max(2, min(args.steps, 5)))
+        a = pt.render(ctx, scene, gnif, cfg, "bf16", first_sample=first_sample).double()
+        b = pt.render(ctx, scene, gnif, cfg, "fp32", first_sample=first_sample).double()
+        ctx.check()
+        rel_rmse = float(torch.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()).item())
+
+    # standalone NIF throughput: 2^24 uniform (u, v) through each kernel
+    uv = torch.from_numpy(I.uniform_uv(1 << 24, seed=1)).to(dev)
+    nif_alone = {}
+    for prec in (() if args.no_compare else ("bf16", "fp32")):
+        gnif.eval(uv, prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            gnif.eval(uv, prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        nif_alone[prec] = {"evals_per_s": (1 << 24) / (t * 1e-3), "ms": t,
+                           "tflops": (1 << 24) * (TC_FLOP_PER_EVAL if prec == "bf16" else FLOP_PER_EVAL) / (t * 1e-3)
+                           / 1e12}
+    ctx.check()
+
+    # live roofline of the dominant kernel of the timed frames
+    meas, which = peaks()
+    clock = float(meas.get("sm_max_mhz", 2070.0))
+    dom = max(("trace", "nif", "reduce"), key=lambda k: prof[k][0])
+    if dom == "nif" and args.precision == "bf16":
+        peak = float(meas.get("bf16_tflops_sustained", meas["bf16_tflops"]))
+        achieved = evals * TC_FLOP_PER_EVAL / (nif_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_nif_tc", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "per_unit": f"{TC_FLOP_PER_EVAL} tensor FLOP per NIF evaluation x {evals} evaluations per launch",
+                "peak_note": f"dense BF16, sustained ({which})"}
+    elif dom == "nif":
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock * 1e6 / 1e12
-        trace_ms = prof["trace"][0] / args.steps
-        rays = int(counts[:cfg.max_depth].sum())
-        roof = {"kernel": "k_bounce", "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "rays_per_s": rays / (trace_ms * 1e-3),
-                "peak_note": "traversal of a 256-sphere BVH: latency/ALU bound"}
+        achieved = evals * FLOP_PER_EVAL / (nif_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_nif_fp32", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "per_unit": f"{FLOP_PER_EVAL} FLOP per NIF evaluation x {evals} evaluations per launch",
+                "peak_note": f"FP32 FFMA derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clock:.0f} MHz"}
+    else:
+        ops = (OPS_NODE * work["nodes"] + OPS_SPHERE * work["sphere"] + OPS_QUAD * work["quad"] +
+               OPS_TRI * work["triangle"])
+        peak = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6 / 1e12
+        achieved = ops / (trace_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_bounce", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
+                "frac": achieved / peak, "traffic": None,
+                "per_unit": f"FP32 ops per node fetch {OPS_NODE}, per sphere/quad/triangle test "
+                            f"{OPS_SPHERE}/{OPS_QUAD}/{OPS_TRI}; {work['nodes']} node fetches and "
+                            f"{work['sphere']} sphere tests per frame ({cfg.max_depth} launches)",
+                "peak_note": f"FP32 issue rate derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x {clock:.0f} MHz"}
 
     # end to end through the C ABI with host buffers: scene + weights in, image out
     e2e = None
     if not args.no_e2e:
         host_img = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, pin_memory=True)
         flat = pt.nif_flat(nif)
-        h2d = sum(a.nbytes for a in (sc.sphere, sc.sphere_mat, sc.mat_type, sc.mat)) + flat.nbytes
+        h2d = sum(x.nbytes for x in (sc.sphere, sc.sphere_mat, sc.mat_type, sc.mat)) + flat.nbytes
         d2h = host_img.numel() * 4
         n_e2e = max(3, min(args.steps, 10))
         torch.cuda.synchronize()
@@ -289,20 +331,22 @@ def bench_ours(args):
                "sample": f"all {cfg.spp} samples of {n} evenly strided pixels ({n * cfg.spp} paths), FP64 oracle"}
 
     if rank == 0:
-        line = {
+        print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+            "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32",
             "data": "synthetic (procedural scene, random-init NIF weights; seeds 0)",
             "config": config_dict(cfg, args.precision),
-            "nif_evals_per_step": evals,
-            "nif_evals_per_s": evals / (nif_ms * 1e-3) if nif_ms > 0 else None,
-            "rays_per_step": int(counts[:cfg.max_depth].sum()),
+            f"{other}_value": world * paths / (ms_other * 1e-3) / 1e6 if ms_other else None,
+            "bf16_vs_fp32_image_rel_rmse": rel_rmse,
+            "nif_evals_per_step": evals, "rays_per_step": rays,
+            "nif_evals_per_s_in_render": evals / (nif_ms * 1e-3) if nif_ms > 0 else None,
+            "nif_standalone_2p24": nif_alone,
+            "traversal_work_per_step": work,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(sum(v[1] for v in prof.values())),
-        }
-        print(json.dumps(line))
+        }))
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -314,11 +358,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--precision", choices=["bf16", "fp32"], default="bf16")
+    ap.add_argument("--spp", type=int, default=None, help="override spp (small cases for profiler captures)")
     ap.add_argument("--cpu-s", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=4.0, help="seconds per reference-arm step")
-    ap.add_argument("--spp", type=int, default=None, help="override spp (small cases for profiler captures)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the other-precision frames and standalone NIF runs (profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -208,6 +208,11 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* scene, const pt_n
    k, counts[max_depth] = NIF evaluations. */
 PT_API pt_status pt_last_render_counts(pt_ctx* ctx, int64_t* counts, int32_t n);
 
+/* Traversal work of the last render (valid after pt_check): work[0] BVH
+   node fetches (each tests the two child boxes), work[1] sphere, work[2]
+   quad, work[3] triangle intersection tests.  Writes min(n, 4) values. */
+PT_API pt_status pt_last_render_work(pt_ctx* ctx, int64_t* work, int32_t n);
+
 /* Kernel timing.  While enabled, the library records a CUDA event pair on
    the launching stream around each of its kernel launches and accumulates
    the device time per kernel kind: 0 trace/shade step, 1 NIF evaluation,

@@ -57,6 +57,8 @@ namespace {
 constexpr int kMaxDepth = 64;
 constexpr int kCounters = kMaxDepth + 8;
 constexpr int kEscCounter = kMaxDepth + 2;
+constexpr int kStats = kMaxDepth + 1 + 4;     // rays per vertex, NIF evaluations, traversal work [4]
+constexpr int kWorkBase = kMaxDepth + 1;
 
 pt_status fail(pt_ctx* ctx, pt_status st, const std::string& msg)
 {
@@ -178,13 +180,14 @@ pt_status check_cfg(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, const
     return PT_OK;
 }
 
-pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, cudaStream_t s)
+pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, int accumulate, cudaStream_t s)
 {
     NifEvalParams p = {};
     p.nif = nif->dev;
     p.esc = ctx->esc;
     p.esc_count = ctx->counters + kEscCounter;
     p.esc_cap = ctx->chunk_cap;
+    p.accumulate = accumulate;
     p.slot_L = ctx->slot_L;
     p.err = ctx->d_err;
     p.stats = ctx->stats + ctx->last_depth;
@@ -221,8 +224,8 @@ PT_API pt_status pt_create(pt_ctx** out, int device)
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_err, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->counters, kCounters * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->stats, (kMaxDepth + 1) * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, (kMaxDepth + 1) * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->stats, kStats * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, kStats * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         cudaFree(ctx->d_err);
         cudaFree(ctx->counters);
@@ -566,7 +569,7 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
     st = ensure_scratch(ctx, (uint32_t)chunk);
     if (st != PT_OK) return st;
     ctx->last_depth = cfg->max_depth;
-    PT_CUDA(cudaMemsetAsync(ctx->stats, 0, (kMaxDepth + 1) * sizeof(unsigned long long), s));
+    PT_CUDA(cudaMemsetAsync(ctx->stats, 0, kStats * sizeof(unsigned long long), s));
     if (d_hit_ids) PT_CUDA(launch_fill_i32(d_hit_ids, n_slots * cfg->max_depth, -2, s));
 
     BounceParams bp = {};
@@ -587,6 +590,7 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
     bp.hit_ids = d_hit_ids;
     bp.err = ctx->d_err;
     bp.stats = ctx->stats;
+    bp.work = ctx->stats + kWorkBase;
     bp.cap = (uint32_t)chunk;
     const int64_t n_chunks = (n_slots + chunk - 1) / chunk;
     for (int64_t c = 0; c < n_chunks; ++c) {
@@ -604,7 +608,7 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
             PT_CUDA(timed(ctx, PT_KIND_TRACE, s, [&] { return launch_bounce(bp, ctx->sm_count, s); }));
         }
         if (sc->dev.env_is_nif) {
-            st = eval_nif_escapes(ctx, nf, cfg->precision, s);
+            st = eval_nif_escapes(ctx, nf, cfg->precision, sc->dev.has_emission, s);
             if (st != PT_OK) return st;
         }
         const float scale = (c == n_chunks - 1) ? (float)(1.0 / cfg->spp) : 1.f;
@@ -623,6 +627,16 @@ PT_API pt_status pt_render(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, co
 {
     if (!d_image) return fail(ctx, PT_EINVAL, "null image");
     return pt_render_pixels(ctx, sc, nf, cfg, 0, nullptr, d_image, nullptr, nullptr, stream);
+}
+
+PT_API pt_status pt_last_render_work(pt_ctx* ctx, int64_t* work, int32_t n)
+{
+    if (!ctx || !work || n < 0) return fail(ctx, PT_EINVAL, "bad argument");
+    unsigned long long h[4] = {0, 0, 0, 0};
+    PT_CUDA(cudaDeviceSynchronize());
+    PT_CUDA(cudaMemcpy(h, ctx->stats + kWorkBase, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i) work[i] = i < 4 ? (int64_t)h[i] : 0;
+    return PT_OK;
 }
 
 PT_API pt_status pt_last_render_counts(pt_ctx* ctx, int64_t* counts, int32_t n)

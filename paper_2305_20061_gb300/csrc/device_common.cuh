@@ -139,16 +139,23 @@ __device__ __forceinline__ float isect_tri(const TriRay& r, float4 v0, float4 v1
 // ---------------------------------------------------------------------------
 struct Hit { float t; int32_t prim; };
 
+// Traversal work of one ray: child-pair node fetches and primitive tests by
+// kind (the algorithmic work behind the traversal roofline).
+struct Work { uint32_t nodes = 0, sph = 0, quad = 0, tri = 0; };
+
 __device__ __forceinline__ void isect_prim(const DevScene& sc, uint32_t id, float3 o, float3 d, const TriRay& tr,
-                                           float& tbest, int32_t& best)
+                                           float& tbest, int32_t& best, Work& w)
 {
     float t;
     if (id < sc.nS) {
+        ++w.sph;
         t = isect_sphere(__ldg(&sc.sph[id]), o, d);
     } else if (id < sc.nS + sc.nQ) {
+        ++w.quad;
         const uint32_t q = id - sc.nS;
         t = isect_quad(__ldg(&sc.quad[2 * q]), __ldg(&sc.quad[2 * q + 1]), o, d);
     } else {
+        ++w.tri;
         const uint32_t q = id - sc.nS - sc.nQ;
         t = isect_tri(tr, __ldg(&sc.tri[3 * q]), __ldg(&sc.tri[3 * q + 1]), __ldg(&sc.tri[3 * q + 2]));
     }
@@ -172,16 +179,15 @@ __device__ __forceinline__ float slab(float3 lo, float3 ext, float3 o, float3 in
 
 __device__ __forceinline__ float safe_inv(float d) { return 1.f / (fabsf(d) > 1e-30f ? d : copysignf(1e-30f, d)); }
 
-template <bool kCountVisits>
-__device__ __forceinline__ Hit trace_closest(const DevScene& sc, float3 o, float3 d, uint32_t* err,
-                                             uint32_t* visits = nullptr)
+__device__ __forceinline__ Hit trace_closest(const DevScene& sc, float3 o, float3 d, uint32_t* err, Work& w)
 {
     Hit h{INFINITY, -1};
     uint32_t cur = sc.root;
     if (cur == kEmptyRef) return h;
-    const TriRay tr = tri_setup(o, d);
+    TriRay tr;
+    if (sc.nT) tr = tri_setup(o, d);  // only triangles use the sheared ray
     if (cur & kLeafBit) {
-        isect_prim(sc, cur & ~kLeafBit, o, d, tr, h.t, h.prim);
+        isect_prim(sc, cur & ~kLeafBit, o, d, tr, h.t, h.prim, w);
         return h;
     }
     const float3 inv = f3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
@@ -203,10 +209,10 @@ __device__ __forceinline__ Hit trace_closest(const DevScene& sc, float3 o, float
         const uint32_t cl = q2.y, cr = q2.z;
         float tl = slab(lo_l, ext_l, o, inv, h.t);
         float trr = slab(lo_r, ext_r, o, inv, h.t);
-        if (kCountVisits) ++*visits;
+        ++w.nodes;
         // leaf children are intersected right away
-        if ((cl & kLeafBit) && tl < INFINITY) { isect_prim(sc, cl & ~kLeafBit, o, d, tr, h.t, h.prim); tl = INFINITY; }
-        if ((cr & kLeafBit) && trr < INFINITY) { isect_prim(sc, cr & ~kLeafBit, o, d, tr, h.t, h.prim); trr = INFINITY; }
+        if ((cl & kLeafBit) && tl < INFINITY) { isect_prim(sc, cl & ~kLeafBit, o, d, tr, h.t, h.prim, w); tl = INFINITY; }
+        if ((cr & kLeafBit) && trr < INFINITY) { isect_prim(sc, cr & ~kLeafBit, o, d, tr, h.t, h.prim, w); trr = INFINITY; }
         // a child is entered only if its box was hit (finite entry) no later than the best hit
         const bool hl = tl < INFINITY && tl <= h.t, hr = trr < INFINITY && trr <= h.t;
         if (hl && hr) {

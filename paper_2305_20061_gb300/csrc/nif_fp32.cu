@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_fp32(const NifEvalParams p,
                 p.rgb[3 * g] = r0; p.rgb[3 * g + 1] = r1; p.rgb[3 * g + 2] = r2;
             } else {
                 float* L = p.slot_L + 3 * (size_t)slot;
-                const float a = L[0] + tr * r0, b = L[1] + tg * r1, c = L[2] + tb * r2;
+                float a = tr * r0, b = tg * r1, c = tb * r2;
+                if (p.accumulate) { a += L[0]; b += L[1]; c += L[2]; }
                 if (!(isfinite(a) && isfinite(b) && isfinite(c))) atomicOr(p.err, PT_ERR_NONFINITE);
                 L[0] = a; L[1] = b; L[2] = c;
             }

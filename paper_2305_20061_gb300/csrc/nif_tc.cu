@@ -7,13 +7,15 @@
 // persistent CTA per SM holds all BF16 weights in shared memory for the
 // whole kernel and streams 128-row tiles of queries through them:
 //
-//   warps 0..11  three warpgroups; warpgroup s owns tile slot s.  Thread t
-//                of a warpgroup owns row t of its tile, which is TMEM lane t.
-//                It computes the row's Fourier features, and after each MMA
-//                reads its accumulator row from TMEM, adds the bias, applies
-//                ReLU while packing to BF16 and writes the row back into the
-//                slot's operand buffer in the UMMA SWIZZLE_128B K-major layout.
-//   warp 12      allocates TMEM; lane 0 issues every tcgen05.mma (128x128x16
+//   warps 0..23  three groups of eight; group s owns tile slot s.  Within a
+//                group, warps 4h..4h+3 handle half h of every row: row t is
+//                TMEM lane t, and half h covers accumulator columns
+//                [64h, 64h + 64) and Fourier frequencies [32h, 32h + 32).
+//                They compute the features, and after each MMA read their
+//                accumulator half-row from TMEM, add the bias, apply ReLU
+//                while packing to BF16 and write it back into the slot's
+//                operand buffer in the UMMA SWIZZLE_128B K-major layout.
+//   warp 24      allocates TMEM; lane 0 issues every tcgen05.mma (128x128x16
 //                BF16 -> FP32 for the hidden layers, 128x16x16 for the head)
 //                and commits each layer to the slot's mbarrier.
 //
@@ -34,8 +36,8 @@ namespace {
 
 constexpr int kF = 64, kH = 128, kRows = 128;
 constexpr int kSlots = 3;
-constexpr int kThreads = 13 * 32;
-constexpr int kMmaWarp = 12;
+constexpr int kThreads = 25 * 32;        // 3 slots x 8 epilogue warps + the MMA warp
+constexpr int kMmaWarp = 24;
 constexpr uint32_t kTmemCols = 512;
 
 // shared-memory image (offsets from a 1024-byte aligned base)
@@ -176,6 +178,20 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return d;
 }
 
+__device__ __forceinline__ uint64_t pack_u64(uint32_t lo, uint32_t hi)
+{
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(lo), "r"(hi));
+    return d;
+}
+// two IEEE FP32 additions in one instruction (round to nearest per element)
+__device__ __forceinline__ uint64_t add_f32x2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // byte offset of the 16-byte chunk holding elements [8c, 8c+8) of row r of a
 // 128-row, 128-column BF16 operand in SWIZZLE_128B K-major form
 __device__ __forceinline__ uint32_t sw128_chunk(uint32_t r, uint32_t c)
@@ -188,6 +204,11 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
     asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
+struct TileIn {
+    float u, v, tr, tg, tb;
+    uint32_t slot;
+};
+
 struct TcParams {
     const unsigned char* image;  // packed weights (kImageBytes)
     // mode 0
@@ -199,6 +220,7 @@ struct TcParams {
     const uint32_t* esc_count;
     uint32_t esc_cap;
     float* slot_L;
+    int accumulate;   // 1: add to the radiance the path gathered before escaping
     uint32_t* err;
     unsigned long long* stats;
 };
@@ -222,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kSlots; ++s) {
-            mbar_init(bar_a + 8 * s, kRows);
+            mbar_init(bar_a + 8 * s, 2 * kRows);   // both halves of the slot arrive
             mbar_init(bar_acc + 8 * s, 1);
         }
         mbar_init(bar_w, 1);
@@ -299,35 +321,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
         }
     } else {
         // ------------------------------------------------------- epilogue warps
-        const int s = warp >> 2;                       // tile slot
+        const int s = warp >> 3;                       // tile slot (8 warps each)
+        const int half = (warp >> 2) & 1;              // which 64 columns / 32 frequencies of the row
         const uint32_t row = (warp & 3) * 32 + lane;   // row in tile == TMEM lane
         const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
         const uint32_t a_base = sbase + kOffA + s * kABytes;
         const float* Bm = tail + 3 * kH + 4;
         const float* Mm = Bm + 2 * kF;
         uint32_t ph = 0;
+        // inputs of this thread's row of a tile, loaded one tile ahead so the
+        // global-memory latency hides behind the previous tile's MMA chain
+        auto load_inputs = [&](int64_t tile) {
+            TileIn t = {};
+            const int64_t gg = tile * kRows + row;
+            if (tile < n_tiles && gg < count) {
+                if (mode == 0) {
+                    const float2 q = reinterpret_cast<const float2*>(p.uv)[gg];
+                    t.u = q.x; t.v = q.y;
+                } else {
+                    const float2* e = reinterpret_cast<const float2*>(p.esc + gg);
+                    const float2 a = e[0], b = e[1], c = e[2];
+                    t.slot = __float_as_uint(a.x); t.u = a.y; t.v = b.x; t.tr = b.y; t.tg = c.x; t.tb = c.y;
+                }
+            }
+            return t;
+        };
+        TileIn in = load_inputs(((int64_t)0 * gridDim.x + blockIdx.x) * kSlots + s);
         for (int64_t i = 0;; ++i) {
             const int64_t tile = ((int64_t)i * gridDim.x + blockIdx.x) * kSlots + s;
             if (tile >= n_tiles) break;
             if (__any_sync(0xFFFFFFFFu, *abort != 0)) break;  // warp-uniform exit
             const int64_t g = tile * kRows + row;
             const bool valid = g < count;
-            float u = 0.f, v = 0.f, tr = 0.f, tg = 0.f, tb = 0.f;
-            uint32_t slot = 0;
-            if (valid) {
-                if (mode == 0) {
-                    const float2 q = reinterpret_cast<const float2*>(p.uv)[g];
-                    u = q.x; v = q.y;
-                } else {
-                    const float2* e = reinterpret_cast<const float2*>(p.esc + g);
-                    const float2 a = e[0], b = e[1], c = e[2];
-                    slot = __float_as_uint(a.x); u = a.y; v = b.x; tr = b.y; tg = c.x; tb = c.y;
-                }
-            }
+            const float u = in.u, v = in.v, tr = in.tr, tg = in.tg, tb = in.tb;
+            const uint32_t slot = in.slot;
             // Fourier features [sin 2 pi (Bx)_i, cos 2 pi (Bx)_i]: phase reduced to one turn in FP32,
             // then the hardware sine / cosine (the result is rounded to BF16)
 #pragma unroll 1
-            for (int c8 = 0; c8 < kF / 8; ++c8) {
+            for (int c8 = half * 4; c8 < half * 4 + 4; ++c8) {
                 uint32_t sp[4], cp[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -347,6 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
             }
             fence_proxy_async();
             mbar_arrive(bar_a + 8 * s);
+            const TileIn next = load_inputs(((int64_t)(i + 1) * gridDim.x + blockIdx.x) * kSlots + s);
 
             bool ok = true;
             for (int layer = 0; layer < 3; ++layer) {
@@ -356,16 +388,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
                 tc_fence_after();
                 const float* bias = tail + layer * kH;
 #pragma unroll 1
-                for (int c32 = 0; c32 < 4; ++c32) {
+                for (int c32 = half * 2; c32 < half * 2 + 2; ++c32) {
                     uint32_t r[32];
                     TMEM_LD32(tmem + lane_base + s * 128 + c32 * 32, r);
                     tmem_wait_ld();
                     uint32_t pk[16];
+                    const uint64_t* b2v = reinterpret_cast<const uint64_t*>(bias + c32 * 32);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const float lo = __uint_as_float(r[2 * j]) + bias[c32 * 32 + 2 * j];
-                        const float hi = __uint_as_float(r[2 * j + 1]) + bias[c32 * 32 + 2 * j + 1];
-                        pk[j] = pack_relu_bf16(lo, hi);
+                        // packed FP32 pair add of the bias, then ReLU while rounding the pair to BF16
+                        const uint64_t sum = add_f32x2(pack_u64(r[2 * j], r[2 * j + 1]), b2v[j]);
+                        pk[j] = pack_relu_bf16(__uint_as_float((uint32_t)sum), __uint_as_float((uint32_t)(sum >> 32)));
                     }
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
@@ -381,6 +414,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
             if (!__all_sync(0xFFFFFFFFu, got_head)) break;
             ph ^= 1;
             tc_fence_after();
+            if (half == 1) {  // the other half of the slot owns the output
+                in = next;
+                continue;
+            }
             uint32_t yr[4];
             tmem_ld4(tmem + lane_base + 384 + 32 * s, yr);
             tmem_wait_ld();
@@ -396,12 +433,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
                     p.rgb[3 * g] = r0; p.rgb[3 * g + 1] = r1; p.rgb[3 * g + 2] = r2;
                 } else {
                     float* L = p.slot_L + 3 * (size_t)slot;
-                    const float a = L[0] + tr * r0, b = L[1] + tg * r1, c = L[2] + tb * r2;
+                    float a = tr * r0, b = tg * r1, c = tb * r2;
+                    if (p.accumulate) { a += L[0]; b += L[1]; c += L[2]; }  // radiance gathered before the escape
                     if (!(isfinite(a) && isfinite(b) && isfinite(c))) atomicOr(p.err, PT_ERR_NONFINITE);
                     L[0] = a; L[1] = b; L[2] = c;
                 }
             }
             tc_fence_before();
+            in = next;
         }
     }
     if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0 && p.stats) atomicAdd(p.stats, (unsigned long long)count);
@@ -470,6 +509,7 @@ cudaError_t launch_nif_tc(const unsigned char* image, const NifEvalParams& np, i
     p.esc_count = np.esc_count;
     p.esc_cap = np.esc_cap;
     p.slot_L = np.slot_L;
+    p.accumulate = np.accumulate;
     p.err = np.err;
     p.stats = np.stats;
     k_nif_tc<<<sm_count, kThreads, kSmemBytes, s>>>(p, mode);

@@ -87,6 +87,7 @@ struct BounceParams {
     int32_t* hit_ids;       // nullable [global slot][max_depth]
     uint32_t* err;
     unsigned long long* stats;  // [max_depth + 1]
+    unsigned long long* work;   // nullable [4]: node fetches, sphere, quad, triangle tests
 };
 
 // NIF parameters on the device.
@@ -113,6 +114,7 @@ struct NifEvalParams {
     const uint32_t* esc_count;
     uint32_t esc_cap;
     float* slot_L;
+    int accumulate;         // 1: slot radiance += tp * rgb; 0: slot radiance = tp * rgb (no emitters)
     uint32_t* err;
     unsigned long long* stats;
 };

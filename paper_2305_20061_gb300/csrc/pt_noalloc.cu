@@ -140,6 +140,7 @@ extern "C" PT_API pt_status pt_render_noalloc(const pt_scene* scene, const pt_ni
             np.esc = esc;
             np.esc_count = counters + kMaxDepthNA + 2;
             np.esc_cap = (uint32_t)chunk;
+            np.accumulate = sv->has_emission;
             np.slot_L = slot_L;
             np.err = err;
             np.stats = stats + cfg->max_depth;

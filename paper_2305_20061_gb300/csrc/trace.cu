@@ -18,9 +18,10 @@ struct PathState {
 
 __device__ __forceinline__ void slot_to_pixel(const BounceParams& p, uint32_t j, uint32_t& pix, uint32_t& smp)
 {
-    const uint64_t g = p.chunk_first + j;
-    const uint32_t s = (uint32_t)(g / p.n_pix);
-    const uint32_t i = (uint32_t)(g - (uint64_t)s * p.n_pix);
+    // a call renders fewer than 2^32 paths (checked on the host), so 32-bit arithmetic is exact
+    const uint32_t g = (uint32_t)(p.chunk_first + j);
+    const uint32_t s = g / p.n_pix;
+    const uint32_t i = g - s * p.n_pix;
     smp = s + p.first_sample;
     pix = p.pixels ? (uint32_t)p.pixels[i] : i;
 }
@@ -148,13 +149,14 @@ __device__ __forceinline__ void store_L(float* slot_L, uint32_t slot, float3 L, 
 }
 
 // One wavefront step at vertex k for every ray of the input queue.
-__global__ void __launch_bounds__(256) k_bounce(const BounceParams p)
+__global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
 {
     const uint32_t count = (p.k == 1) ? p.n_chunk : min(*p.count_in, p.cap);  // counters may pass cap on overflow
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     uint32_t traced = 0;
+    Work work;
     for (uint32_t base = warp * 32; base < count; base += n_warps * 32) {
         const uint32_t i = base + lane;
         const bool active = i < count;
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(256) k_bounce(const BounceParams p)
         float eu = 0.f, ev = 0.f;
         if (active) {
             ++traced;
-            const Hit h = trace_closest<false>(p.sc, s.o, s.d, p.err);
+            const Hit h = trace_closest(p.sc, s.o, s.d, p.err, work);
             if (p.hit_ids) p.hit_ids[(p.chunk_first + s.slot) * (uint64_t)p.max_depth + (p.k - 1)] = h.prim;
             if (h.prim < 0) {
                 if (p.sc.env_is_nif) {
@@ -196,7 +198,8 @@ __global__ void __launch_bounds__(256) k_bounce(const BounceParams p)
                     eu = 0.5f + atan2f(s.d.x, -s.d.z) * (0.5f / kPi);
                     ev = acosf(fminf(1.f, fmaxf(-1.f, s.d.y))) * (1.f / kPi);
                     escape_nif = true;
-                    store_L(p.slot_L, s.slot, s.L, p.err);
+                    // without emitters the NIF kernel stores the path's whole radiance itself
+                    if (p.sc.has_emission) store_L(p.slot_L, s.slot, s.L, p.err);
                 } else {
                     s.L = s.L + s.tp * f3(p.sc.env[0], p.sc.env[1], p.sc.env[2]);
                     store_L(p.slot_L, s.slot, s.L, p.err);
@@ -259,9 +262,21 @@ __global__ void __launch_bounds__(256) k_bounce(const BounceParams p)
             }
         }
     }
-    // per-vertex ray count
-    for (int off = 16; off > 0; off >>= 1) traced += __shfl_down_sync(0xFFFFFFFFu, traced, off);
+    // per-vertex ray count and traversal work, one atomic per warp
+    for (int off = 16; off > 0; off >>= 1) {
+        traced += __shfl_down_sync(0xFFFFFFFFu, traced, off);
+        work.nodes += __shfl_down_sync(0xFFFFFFFFu, work.nodes, off);
+        work.sph += __shfl_down_sync(0xFFFFFFFFu, work.sph, off);
+        work.quad += __shfl_down_sync(0xFFFFFFFFu, work.quad, off);
+        work.tri += __shfl_down_sync(0xFFFFFFFFu, work.tri, off);
+    }
     if (lane == 0 && traced) atomicAdd(&p.stats[p.k - 1], (unsigned long long)traced);
+    if (lane == 0 && p.work && traced) {
+        atomicAdd(&p.work[0], (unsigned long long)work.nodes);
+        atomicAdd(&p.work[1], (unsigned long long)work.sph);
+        atomicAdd(&p.work[2], (unsigned long long)work.quad);
+        atomicAdd(&p.work[3], (unsigned long long)work.tri);
+    }
 }
 
 // image[i] (+)= sum over the chunk's samples in sample order; scaled at the end
@@ -315,7 +330,8 @@ __global__ void __launch_bounds__(256) k_trace_rays(const DevScene sc, int64_t n
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float3 o = f3(org[3 * i], org[3 * i + 1], org[3 * i + 2]);
         const float3 d = f3(dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]);
-        const Hit h = trace_closest<false>(sc, o, d, err);
+        Work w;
+        const Hit h = trace_closest(sc, o, d, err, w);
         t[i] = h.t;
         prim[i] = h.prim;
     }

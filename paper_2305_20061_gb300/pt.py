@@ -93,6 +93,7 @@ def lib():
             "pt_profile_enable": ([P, I32], I32),
             "pt_profile_read": ([P, P, P, I32], I32),
             "pt_render_noalloc": ([P, P, P, P, P, P], I32),
+            "pt_last_render_work": ([P, P, I32], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -291,6 +292,13 @@ def last_render_counts(ctx: Context, max_depth: int) -> np.ndarray:
     out = np.zeros(max_depth + 1, np.int64)
     ctx._raise(lib().pt_last_render_counts(ctx.h, _np_ptr(out), max_depth + 1))
     return out
+
+
+def last_render_work(ctx: Context) -> dict:
+    """Traversal work of the last render: node fetches and primitive tests."""
+    out = np.zeros(4, np.int64)
+    ctx._raise(lib().pt_last_render_work(ctx.h, _np_ptr(out), 4))
+    return dict(nodes=int(out[0]), sphere=int(out[1]), quad=int(out[2]), triangle=int(out[3]))
 
 
 def philox(ctx: Context, seed: int, tag: int, ctr: torch.Tensor, stream=None) -> torch.Tensor:
