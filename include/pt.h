@@ -168,6 +168,40 @@ PT_API pt_status pt_nif_get_params(pt_ctx* ctx, const pt_nif* nif, float* params
 PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nif, int32_t precision, int64_t n, const float* d_uv,
                              float* d_rgb, void* stream);
 
+/* Replace the FP32 master weights (host, flat layout of pt_nif_desc) and
+   rebuild the derived layouts.  Synchronises `stream`. */
+PT_API pt_status pt_nif_set_params(pt_ctx* ctx, pt_nif* nif, const float* params, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* NIF training (Section 3.2.1): uniform (u, v) samples, bilinear sub-pixel */
+/* lookup of the HDR image, target log(max(rgb, 1e-6)), Huber loss on the   */
+/* colour-matrix output, Adam on the FP32 master weights (B and M fixed).   */
+/* ------------------------------------------------------------------------ */
+typedef struct pt_train_cfg {
+    int64_t steps;             /* Adam steps in this call */
+    int64_t batch;             /* samples per step */
+    float lr, beta1, beta2, eps;  /* Adam (Kingma & Ba) with bias correction */
+    float huber_delta;         /* Huber loss threshold (the paper uses 1e-3) */
+    uint32_t seed;             /* Philox key (seed, 1); counter (sample, global step, 0, 0) */
+} pt_train_cfg;
+
+/* Train for cfg->steps steps on d_sky, an equirect HDR image [h][w][3] float
+   (row 0 = zenith, pixel centres at ((i + 0.5)/w, (j + 0.5)/h), u wraps, v
+   clamps).  d_losses (nullable) receives the mean Huber loss of each step.
+   Adam moments and the global step count persist in the pt_nif across calls,
+   so calls continue one run.  The FP32 and tensor-core layouts are rebuilt
+   at the end of the call.  FP32 arithmetic, loss sums in FP64,
+   deterministic. */
+PT_API pt_status pt_train_nif(pt_ctx* ctx, pt_nif* nif, const float* d_sky, int32_t w, int32_t h,
+                              const pt_train_cfg* cfg, float* d_losses, void* stream);
+
+/* Loss and gradient of one batch without updating: d_uv [n][2], d_target
+   [n][3] (log space, compared with the colour-matrix output) -> d_grad
+   (nullable; trainable part of the flat layout: per layer W then b) and
+   *d_loss (nullable device double, mean Huber loss over n x 3). */
+PT_API pt_status pt_nif_loss_grad(pt_ctx* ctx, pt_nif* nif, int64_t n, const float* d_uv, const float* d_target,
+                                  float delta, float* d_grad, double* d_loss, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Rendering (Section 3.1: paths without light sampling; radiance gathered   */
 /* at emitters and at escapes, where the NIF is queried; Section 3.3).       */

@@ -50,6 +50,17 @@ struct pt_nif {
     float* d_fp32 = nullptr;     // packed FP32 layout (Wt, bias, Wout, bout)
     unsigned char* d_tc = nullptr;  // BF16 shared-memory image of the tensor-core kernel (F=64, H=128, L=3 only)
     DevNif dev = {};
+    // training state (allocated by the first training call)
+    int64_t n_trainable = 0;
+    float* d_grad = nullptr;
+    float* d_m = nullptr;
+    float* d_v = nullptr;
+    int64_t adam_t = 0;             // Adam steps taken; also the Philox step counter of the samples
+    int64_t work_cap = 0;           // batch rows the work buffers hold
+    void* d_work = nullptr;         // activations, gradients, partials
+    TrainWork work = {};
+    float* d_batch = nullptr;       // uv [cap][2] + target [cap][3] for pt_train_nif
+    double* d_loss = nullptr;
 };
 
 namespace {
@@ -507,6 +518,12 @@ PT_API void pt_destroy_nif(pt_nif* nf)
     cudaFree(nf->d_params);
     cudaFree(nf->d_fp32);
     cudaFree(nf->d_tc);
+    cudaFree(nf->d_grad);
+    cudaFree(nf->d_m);
+    cudaFree(nf->d_v);
+    cudaFree(nf->d_work);
+    cudaFree(nf->d_batch);
+    cudaFree(nf->d_loss);
     delete nf;
 }
 
@@ -543,6 +560,138 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
     if (precision == PT_BF16 || precision == PT_FP8E4M3)
         return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3 (FP8 not in this build)");
     return fail(ctx, PT_EINVAL, "unknown precision");
+}
+
+// ---------------------------------------------------------------------------
+// NIF training (Section 3.2.1)
+namespace {
+
+TrainNet make_train_net(pt_nif* nf)
+{
+    TrainNet t = {};
+    t.F = nf->F; t.H = nf->H; t.L = nf->L;
+    const float* p = nf->d_params;
+    float* g = nf->d_grad;
+    t.B = p;
+    p += 2 * nf->F;
+    for (int l = 0; l <= nf->L; ++l) {
+        const int in = l == 0 ? 2 * nf->F : nf->H, o = l == nf->L ? 3 : nf->H;
+        t.W[l] = p; t.gW[l] = g;
+        p += (size_t)in * o; g += (size_t)in * o;
+        t.b[l] = p; t.gb[l] = g;
+        p += o; g += o;
+    }
+    t.M = p;
+    return t;
+}
+
+pt_status ensure_train(pt_ctx* ctx, pt_nif* nf, int64_t B)
+{
+    if (!nf->d_grad) {
+        nf->n_trainable = nf->n_params - 2 * nf->F - 9;
+        if (cudaMalloc((void**)&nf->d_grad, nf->n_trainable * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&nf->d_m, nf->n_trainable * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&nf->d_v, nf->n_trainable * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&nf->d_loss, sizeof(double)) != cudaSuccess)
+            return fail(ctx, PT_ENOMEM, "training state allocation failed");
+        if (cudaMemset(nf->d_m, 0, nf->n_trainable * sizeof(float)) != cudaSuccess ||
+            cudaMemset(nf->d_v, 0, nf->n_trainable * sizeof(float)) != cudaSuccess)
+            return fail(ctx, PT_ECUDA, "training state initialisation failed");
+    }
+    if (nf->work_cap >= B) return PT_OK;
+    cudaFree(nf->d_work);
+    cudaFree(nf->d_batch);
+    nf->d_work = nullptr;
+    nf->d_batch = nullptr;
+    const int G = ctx->sm_count;
+    const size_t rows = (size_t)B * 128;
+    const size_t bytes = (size_t)(nf->L + 1 + 2) * rows * sizeof(float) + (size_t)G * (128 * 128 + 128) * sizeof(float) +
+                         (size_t)G * sizeof(double) + 4096;
+    if (cudaMalloc(&nf->d_work, bytes) != cudaSuccess || cudaMalloc((void**)&nf->d_batch, (size_t)B * 5 * sizeof(float)) != cudaSuccess) {
+        nf->work_cap = 0;
+        return fail(ctx, PT_ENOMEM, "training work buffers allocation failed");
+    }
+    char* w = static_cast<char*>(nf->d_work);
+    nf->work = TrainWork{};
+    nf->work.n_blocks = G;
+    for (int l = 0; l <= nf->L; ++l) { nf->work.X[l] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
+    for (int i = 0; i < 2; ++i) { nf->work.dX[i] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
+    nf->work.partial = reinterpret_cast<float*>(w);
+    w += (size_t)G * (128 * 128 + 128) * sizeof(float);
+    nf->work.loss_partial = reinterpret_cast<double*>(w);
+    nf->work_cap = B;
+    return PT_OK;
+}
+
+// FP32 packed layout and tensor-core image follow the master weights
+pt_status refresh_layouts(pt_ctx* ctx, pt_nif* nf, cudaStream_t s)
+{
+    PT_CUDA(repack_nif_fp32(nf->d_params, nf->F, nf->H, nf->L, nf->d_fp32, s));
+    if (nf->d_tc) PT_CUDA(repack_nif_tc_image(nf->d_params, nf->d_tc, s));
+    return PT_OK;
+}
+
+}  // namespace
+
+PT_API pt_status pt_nif_loss_grad(pt_ctx* ctx, pt_nif* nf, int64_t n, const float* d_uv, const float* d_target,
+                                  float delta, float* d_grad, double* d_loss, void* stream)
+{
+    if (!ctx || !nf || n < 1 || !d_uv || !d_target || !(delta > 0.f)) return fail(ctx, PT_EINVAL, "bad argument");
+    pt_status st = ensure_train(ctx, nf, n);
+    if (st != PT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    TrainNet net = make_train_net(nf);
+    PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] {
+        return nif_loss_grad(net, n, d_uv, d_target, delta, nf->work, d_loss ? d_loss : nf->d_loss, nullptr, s);
+    }));
+    if (d_grad)
+        PT_CUDA(cudaMemcpyAsync(d_grad, nf->d_grad, nf->n_trainable * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return PT_OK;
+}
+
+PT_API pt_status pt_train_nif(pt_ctx* ctx, pt_nif* nf, const float* d_sky, int32_t w, int32_t h, const pt_train_cfg* cfg,
+                              float* d_losses, void* stream)
+{
+    if (!ctx || !nf || !d_sky || !cfg || w < 1 || h < 1) return fail(ctx, PT_EINVAL, "bad argument");
+    if (cfg->steps < 0 || cfg->batch < 1 || !(cfg->lr > 0.f) || !(cfg->huber_delta > 0.f) || !(cfg->beta1 >= 0.f) ||
+        !(cfg->beta1 < 1.f) || !(cfg->beta2 >= 0.f) || !(cfg->beta2 < 1.f) || !(cfg->eps > 0.f))
+        return fail(ctx, PT_EINVAL, "bad training configuration");
+    pt_status st = ensure_train(ctx, nf, cfg->batch);
+    if (st != PT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    TrainNet net = make_train_net(nf);
+    float* uv = nf->d_batch;
+    float* target = uv + 2 * cfg->batch;
+    for (int64_t i = 0; i < cfg->steps; ++i) {
+        const int64_t t = nf->adam_t;  // global step index: Philox counter word 1 and Adam's t - 1
+        PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] {
+            return train_inputs(cfg->seed, (uint32_t)t, cfg->batch, d_sky, w, h, uv, target, s);
+        }));
+        PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] {
+            return nif_loss_grad(net, cfg->batch, uv, target, cfg->huber_delta, nf->work, nullptr,
+                                 d_losses ? d_losses + i : nullptr, s);
+        }));
+        const double c1 = 1.0 - std::pow((double)cfg->beta1, (double)(t + 1));
+        const double c2 = 1.0 - std::pow((double)cfg->beta2, (double)(t + 1));
+        float* wts = nf->d_params + 2 * nf->F;
+        PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] {
+            return adam_step(nf->n_trainable, wts, nf->d_grad, nf->d_m, nf->d_v, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps,
+                             (float)c1, (float)c2, s);
+        }));
+        nf->adam_t = t + 1;
+    }
+    return refresh_layouts(ctx, nf, s);
+}
+
+PT_API pt_status pt_nif_set_params(pt_ctx* ctx, pt_nif* nf, const float* params, void* stream)
+{
+    if (!ctx || !nf || !params) return fail(ctx, PT_EINVAL, "bad argument");
+    if (!finite3(params, nf->n_params)) return fail(ctx, PT_EINVAL, "non-finite NIF parameters");
+    cudaStream_t s = (cudaStream_t)stream;
+    PT_CUDA(cudaMemcpyAsync(nf->d_params, params, nf->n_params * sizeof(float), cudaMemcpyHostToDevice, s));
+    PT_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < 9; ++i) nf->dev.M[i] = params[nf->n_params - 9 + i];
+    return refresh_layouts(ctx, nf, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -45,6 +45,25 @@ __device__ __forceinline__ float3 norm3(float3 a) { return a * rsqrtf(dot3(a, a)
 __device__ __forceinline__ float comp3(float3 a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
 
 // ---------------------------------------------------------------------------
+// Fourier features with an error-free phase (Section 3.2's positional
+// embedding evaluated in FP32): t = B0 u + B1 v is carried as an unevaluated
+// sum hi + lo (exact products via fma, exact sum via TwoSum), the integer
+// part is removed exactly, and sinpi/cospi of 2r give sin(2 pi t) and
+// cos(2 pi t) to ~1e-7 absolute even for |t| ~ 100 turns.
+__device__ __forceinline__ void fourier_feature(float b0, float b1, float u, float v, float& s, float& c)
+{
+    const float p0 = b0 * u, e0 = fmaf(b0, u, -p0);
+    const float p1 = b1 * v, e1 = fmaf(b1, v, -p1);
+    const float hi = p0 + p1;
+    const float bp = hi - p0;
+    const float es = (p0 - (hi - bp)) + (p1 - bp);
+    const float lo = e0 + e1 + es;
+    const float n = rintf(hi);
+    const float r = (hi - n) + lo;
+    sincospif(2.f * r, &s, &c);
+}
+
+// ---------------------------------------------------------------------------
 // Ray-primitive tests (Section 3.1.3).  Each returns t > 0 or +inf.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float isect_sphere(float4 s, float3 o, float3 d)

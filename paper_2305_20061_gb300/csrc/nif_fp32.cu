@@ -18,23 +18,6 @@ constexpr int kDim = 128;       // padded layer width
 constexpr int kThreads = 128;
 constexpr size_t kSmemBytes = 2 * kDim * kDim * sizeof(float);
 
-// Fourier features with an error-free phase: t = B0 u + B1 v is carried as
-// an unevaluated sum hi + lo (exact products via fma, exact sum via TwoSum),
-// the integer part is removed exactly, and sinpi/cospi of 2 r evaluate
-// sin(2 pi t) and cos(2 pi t) to ~1e-7 absolute even for |t| ~ 100 turns.
-__device__ __forceinline__ void fourier_feature(float b0, float b1, float u, float v, float& s, float& c)
-{
-    const float p0 = b0 * u, e0 = fmaf(b0, u, -p0);
-    const float p1 = b1 * v, e1 = fmaf(b1, v, -p1);
-    const float hi = p0 + p1;
-    const float bp = hi - p0;
-    const float es = (p0 - (hi - bp)) + (p1 - bp);
-    const float lo = e0 + e1 + es;
-    const float n = rintf(hi);
-    const float r = (hi - n) + lo;
-    sincospif(2.f * r, &s, &c);
-}
-
 __device__ __forceinline__ void stage_weights(float* Ws, const float* __restrict__ Wt)
 {
     const float4* src = reinterpret_cast<const float4*>(Wt);
@@ -158,4 +141,59 @@ cudaError_t launch_nif_fp32(const NifEvalParams& p, int mode, int sm_count, cuda
     return cudaGetLastError();
 }
 
+}  // namespace ptk
+
+namespace ptk {
+namespace {
+// Flat master weights -> packed FP32 layout of k_nif_fp32:
+// [L][128][128] transposed hidden weights, [L][128] biases, [3][128] output
+// weights, [3] output bias, [2F] frequencies (zero padding elsewhere).
+__global__ void k_repack_fp32(const float* __restrict__ params, int F, int H, int L, float* __restrict__ packed)
+{
+    float* Wt = packed;
+    float* bias = Wt + (size_t)L * 128 * 128;
+    float* Wout = bias + (size_t)L * 128;
+    float* bout = Wout + 3 * 128;
+    float* Bc = bout + 3;
+    const size_t total = (size_t)L * 128 * 128 + (size_t)L * 128 + 3 * 128 + 3 + 2 * F;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        float val = 0.f;
+        if (idx < (size_t)L * 128 * 128) {
+            const int l = (int)(idx / (128 * 128)), k = (int)((idx / 128) % 128), j = (int)(idx % 128);
+            const int in = l == 0 ? 2 * F : H;
+            size_t off = 2 * (size_t)F;
+            for (int q = 0; q < l; ++q) off += (size_t)(q == 0 ? 2 * F : H) * H + H;
+            if (j < H && k < in) val = params[off + (size_t)j * in + k];
+            Wt[idx] = val;
+        } else if (idx < (size_t)L * 128 * 128 + (size_t)L * 128) {
+            const size_t r = idx - (size_t)L * 128 * 128;
+            const int l = (int)(r / 128), j = (int)(r % 128);
+            const int in = l == 0 ? 2 * F : H;
+            size_t off = 2 * (size_t)F;
+            for (int q = 0; q < l; ++q) off += (size_t)(q == 0 ? 2 * F : H) * H + H;
+            if (j < H) val = params[off + (size_t)in * H + j];
+            bias[r] = val;
+        } else {
+            size_t off = 2 * (size_t)F;
+            for (int q = 0; q < L; ++q) off += (size_t)(q == 0 ? 2 * F : H) * H + H;
+            const size_t r = idx - (size_t)L * 128 * 128 - (size_t)L * 128;
+            if (r < 3 * 128) {
+                const int c = (int)(r / 128), k = (int)(r % 128);
+                if (k < H) val = params[off + (size_t)c * H + k];
+                Wout[r] = val;
+            } else if (r < 3 * 128 + 3) {
+                bout[r - 3 * 128] = params[off + 3 * (size_t)H + (r - 3 * 128)];
+            } else {
+                Bc[r - 3 * 128 - 3] = params[r - 3 * 128 - 3];
+            }
+        }
+    }
+}
+}  // namespace
+
+cudaError_t repack_nif_fp32(const float* params, int F, int H, int L, float* packed, cudaStream_t s)
+{
+    k_repack_fp32<<<256, 256, 0, s>>>(params, F, H, L, packed);
+    return cudaGetLastError();
+}
 }  // namespace ptk

@@ -26,6 +26,7 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -78,6 +79,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     asm volatile(
         "{\n.reg .pred p;\n"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// non-blocking probe of a phase (used by the MMA issuer's event loop)
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         "selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
         : "r"(bar), "r"(parity)
@@ -276,40 +290,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
         // ------------------------------------------------------------- MMA issuer
         if (lane == 0 && !*abort) {
             const uint32_t id_h = idesc_bf16(128, 128), id_o = idesc_bf16(128, kHeadRows);
+            // Event loop: serve whichever slot has its operand ready, so a slow
+            // epilogue in one slot never holds back the MMAs of the others.
             uint32_t ph[kSlots] = {0, 0, 0};
-            bool stop = false;
-            for (int64_t i = 0; !stop; ++i) {
-                bool any = false;
-                for (int stage = 0; stage < 4 && !stop; ++stage) {
-                    for (int s = 0; s < kSlots; ++s) {
-                        const int64_t tile = ((int64_t)i * gridDim.x + blockIdx.x) * kSlots + s;
-                        if (tile >= n_tiles) continue;
-                        any = true;
-                        if (!mbar_wait(bar_a + 8 * s, ph[s], abort, p.err)) { stop = true; break; }
-                        ph[s] ^= 1;
-                        tc_fence_after();
-                        const uint32_t a_base = sbase + kOffA + s * kABytes;
-                        if (stage < 3) {
-                            const uint32_t w_base = sbase + kOffW + stage * kWBytes;
-                            const uint32_t d = tmem + s * 128;
+            int stage[kSlots] = {0, 0, 0};
+            int64_t it[kSlots] = {0, 0, 0};
+            int live = 0;
+            bool done[kSlots];
+            for (int s = 0; s < kSlots; ++s) {
+                done[s] = ((int64_t)blockIdx.x * kSlots + s) >= n_tiles;
+                live += done[s] ? 0 : 1;
+            }
+            uint64_t last = global_ns();
+            while (live > 0 && !*abort) {
+                bool progressed = false;
+                for (int s = 0; s < kSlots; ++s) {
+                    if (done[s] || !mbar_test_wait(bar_a + 8 * s, ph[s])) continue;
+                    progressed = true;
+                    ph[s] ^= 1;
+                    tc_fence_after();
+                    const uint32_t a_base = sbase + kOffA + s * kABytes;
+                    if (stage[s] < 3) {
+                        const uint32_t w_base = sbase + kOffW + stage[s] * kWBytes;
+                        const uint32_t d = tmem + s * 128;
 #pragma unroll
-                            for (int kk = 0; kk < 8; ++kk) {
-                                const uint32_t koff = (kk >> 2) * (kRows * 128) + (kk & 3) * 32;
-                                mma_bf16(d, sw128_desc(a_base + koff), sw128_desc(w_base + koff), id_h, kk > 0);
-                            }
-                        } else {
-                            const uint32_t d = tmem + 384 + 32 * s;
-#pragma unroll
-                            for (int kk = 0; kk < 8; ++kk) {
-                                const uint32_t aoff = (kk >> 2) * (kRows * 128) + (kk & 3) * 32;
-                                const uint32_t boff = (kk >> 2) * (kHeadRows * 128) + (kk & 3) * 32;
-                                mma_bf16(d, sw128_desc(a_base + aoff), sw128_desc(sbase + kOffHead + boff), id_o, kk > 0);
-                            }
+                        for (int kk = 0; kk < 8; ++kk) {
+                            const uint32_t koff = (kk >> 2) * (kRows * 128) + (kk & 3) * 32;
+                            mma_bf16(d, sw128_desc(a_base + koff), sw128_desc(w_base + koff), id_h, kk > 0);
                         }
-                        mma_commit(bar_acc + 8 * s);
+                    } else {
+                        const uint32_t d = tmem + 384 + 32 * s;
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk) {
+                            const uint32_t aoff = (kk >> 2) * (kRows * 128) + (kk & 3) * 32;
+                            const uint32_t boff = (kk >> 2) * (kHeadRows * 128) + (kk & 3) * 32;
+                            mma_bf16(d, sw128_desc(a_base + aoff), sw128_desc(sbase + kOffHead + boff), id_o, kk > 0);
+                        }
+                    }
+                    mma_commit(bar_acc + 8 * s);
+                    if (++stage[s] == 4) {
+                        stage[s] = 0;
+                        ++it[s];
+                        if ((it[s] * gridDim.x + blockIdx.x) * kSlots + s >= n_tiles) {
+                            done[s] = true;
+                            --live;
+                        }
                     }
                 }
-                if (!any) break;
+                if (progressed) {
+                    last = global_ns();
+                } else if (global_ns() - last > kWaitBudgetNs) {
+                    atomicOr(p.err, PT_ERR_TIMEOUT);
+                    *abort = 1;
+                }
             }
             if (*abort) {
                 // make sure no MMA is still writing TMEM before it is freed
@@ -518,4 +551,65 @@ cudaError_t launch_nif_tc(const unsigned char* image, const NifEvalParams& np, i
 
 size_t nif_tc_image_bytes() { return kImageBytes; }
 
+}  // namespace ptk
+
+namespace ptk {
+namespace {
+// Flat master weights -> the tensor-core kernel's shared-memory image (same
+// layout as pack_nif_tc_image builds on the host; BF16 round-to-nearest-even).
+__global__ void k_repack_tc(const float* __restrict__ params, unsigned char* __restrict__ image)
+{
+    const float* W[4];
+    const float* b[4];
+    const float* p = params + 2 * kF;
+    for (int l = 0; l < 4; ++l) {
+        const int in = l == 0 ? 2 * kF : kH, o = l == 3 ? 3 : kH;
+        W[l] = p;
+        p += (size_t)in * o;
+        b[l] = p;
+        p += o;
+    }
+    const float* Mp = p;
+    const int n_hidden = 3 * kH * kH, n_head = kHeadRows * kH;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_hidden + n_head + (int)kTailFloats;
+         idx += gridDim.x * blockDim.x) {
+        if (idx < n_hidden + n_head) {
+            uint32_t base, rows, r, k;
+            float x;
+            if (idx < n_hidden) {
+                const int l = idx / (kH * kH);
+                r = (idx / kH) % kH;
+                k = idx % kH;
+                base = kOffW + l * kWBytes;
+                rows = kRows;
+                x = W[l][(size_t)r * kH + k];
+            } else {
+                const int q = idx - n_hidden;
+                r = q / kH;
+                k = q % kH;
+                base = kOffHead;
+                rows = kHeadRows;
+                x = r < 3 ? W[3][(size_t)r * kH + k] : 0.f;
+            }
+            const uint32_t off = base + (k >> 6) * (rows * 128) + r * 128 + ((((k & 63) >> 3) ^ (r & 7)) << 4) + (k & 7) * 2;
+            const unsigned short bits = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+            *reinterpret_cast<unsigned short*>(image + off) = bits;
+        } else {
+            const int t = idx - n_hidden - n_head;
+            float val = 0.f;
+            if (t < 3 * kH) val = b[t / kH][t % kH];
+            else if (t < 3 * kH + 4) val = (t - 3 * kH) < 3 ? b[3][t - 3 * kH] : 0.f;
+            else if (t < 3 * kH + 4 + 2 * kF) val = params[t - 3 * kH - 4];
+            else if (t < 3 * kH + 4 + 2 * kF + 9) val = Mp[t - 3 * kH - 4 - 2 * kF];
+            reinterpret_cast<float*>(image + kOffTail)[t] = val;
+        }
+    }
+}
+}  // namespace
+
+cudaError_t repack_nif_tc_image(const float* params, unsigned char* image, cudaStream_t s)
+{
+    k_repack_tc<<<128, 256, 0, s>>>(params, image);
+    return cudaGetLastError();
+}
 }  // namespace ptk

@@ -137,6 +137,34 @@ bool pack_nif_tc_image(const float* params, int F, int H, int L, std::vector<uns
 cudaError_t launch_nif_tc(const unsigned char* image, const NifEvalParams& p, int mode, int sm_count, cudaStream_t s);
 size_t nif_tc_image_bytes();
 
+// NIF training (train.cu).  Pointers into the flat FP32 master weights and
+// into the flat gradient (same order as the trainable part of the weights).
+struct TrainNet {
+    int32_t F, H, L;
+    const float* B;                 // [F][2]
+    const float* W[9];              // per linear layer, [out][in]
+    const float* b[9];
+    const float* M;                 // [3][3]
+    float* gW[9];
+    float* gb[9];
+};
+struct TrainWork {
+    int32_t n_blocks;               // CTAs of the batch GEMMs (one partial each)
+    float* X[9];                    // X[0] features, X[l] hidden outputs, each [batch][128]
+    float* dX[2];                   // ping-pong [batch][128]
+    float* partial;                 // [n_blocks][128 * 128 + 128]
+    double* loss_partial;           // [n_blocks]
+};
+cudaError_t train_inputs(uint32_t seed, uint32_t step, int64_t B, const float* sky, int w, int h, float* uv,
+                         float* target, cudaStream_t s);
+cudaError_t nif_loss_grad(const TrainNet& net, int64_t B, const float* uv, const float* target, float delta,
+                          TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s);
+cudaError_t adam_step(int64_t n, float* w, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
+                      float c1, float c2, cudaStream_t s);
+// rebuild the packed FP32 layout and (when present) the tensor-core image from the master weights
+cudaError_t repack_nif_fp32(const float* params, int F, int H, int L, float* packed, cudaStream_t s);
+cudaError_t repack_nif_tc_image(const float* params, unsigned char* image, cudaStream_t s);
+
 // read-only views of the C-ABI handles (api.cu)
 const DevScene* scene_view(const pt_scene* s, int* device);
 const DevNif* nif_view(const pt_nif* n);

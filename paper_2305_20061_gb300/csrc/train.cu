@@ -1,0 +1,428 @@
+// Training of the HDR neural image field (Section 3.2.1): uniform (u, v)
+// samples with a bilinear sub-pixel lookup of the HDR image, log-compressed
+// targets, Huber loss, backpropagation and Adam, all in hand-written CUDA.
+//
+// Layers are padded to 128 x 128.  Activations are kept in HBM as [sample]
+// [128] FP32 rows.  Every GEMM is a 128-row tile times a 128 x 128 matrix
+// staged in shared memory with a 4 x 32 register tile per thread; weight
+// gradients are split over the batch into one partial per CTA and summed in a
+// fixed order, so a training step is deterministic.  The loss is summed in
+// FP64.
+#include <algorithm>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace ptk {
+
+namespace {
+
+constexpr int kT = 128;           // rows per tile == threads per CTA
+constexpr int kD = 128;           // padded width
+constexpr size_t kGemmSmem = 2 * kD * kD * sizeof(float);
+
+// thread -> (4 rows, 32 columns) of a 128 x 128 output tile
+struct TileMap {
+    int rg, og;
+    __device__ TileMap()
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        rg = warp * 8 + (lane & 7);
+        og = lane >> 3;
+    }
+};
+
+// acc[r][j] += sum_k As[k][4 rg + r] * Bs[k][32 og + j]  (As: [k][row], Bs: [k][col])
+__device__ __forceinline__ void tile_mma(const float* As, const float* Bs, const TileMap& m, float acc[4][32])
+{
+#pragma unroll 2
+    for (int k = 0; k < kD; ++k) {
+        const float4 a = *reinterpret_cast<const float4*>(&As[k * kD + 4 * m.rg]);
+        const float4* brow = reinterpret_cast<const float4*>(&Bs[k * kD + 32 * m.og]);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float4 b = brow[q];
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                acc[0][4 * q + e] = fmaf(a.x, bv[e], acc[0][4 * q + e]);
+                acc[1][4 * q + e] = fmaf(a.y, bv[e], acc[1][4 * q + e]);
+                acc[2][4 * q + e] = fmaf(a.z, bv[e], acc[2][4 * q + e]);
+                acc[3][4 * q + e] = fmaf(a.w, bv[e], acc[3][4 * q + e]);
+            }
+        }
+    }
+}
+
+// rows [tile*128, tile*128+128) of a [B][128] matrix -> smem [k][row] (zeros past B)
+__device__ __forceinline__ void load_rows_transposed(float* S, const float* __restrict__ X, int64_t tile, int64_t B)
+{
+    const int r = threadIdx.x;
+    const int64_t g = tile * kT + r;
+    const float4* src = reinterpret_cast<const float4*>(X + g * kD);
+#pragma unroll 4
+    for (int q = 0; q < kD / 4; ++q) {
+        const float4 v = g < B ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        S[(4 * q + 0) * kD + r] = v.x;
+        S[(4 * q + 1) * kD + r] = v.y;
+        S[(4 * q + 2) * kD + r] = v.z;
+        S[(4 * q + 3) * kD + r] = v.w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// training inputs: Philox key (seed, 1), counter (i, step, 0, 0) -> (u, v);
+// bilinear lookup (u wraps, v clamps, pixel centres at (i + 0.5) / w) and
+// target = log(max(rgb, 1e-6))
+__global__ void k_train_inputs(uint32_t seed, uint32_t step, int64_t B, const float* __restrict__ sky, int w, int h,
+                               float* __restrict__ uv, float* __restrict__ target)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 wd = philox4x32_10(make_uint4((uint32_t)i, step, 0u, 0u), seed, 1u);
+        const float u = u01(wd.x), v = u01(wd.y);
+        uv[2 * i] = u;
+        uv[2 * i + 1] = v;
+        const float x = u * (float)w - 0.5f, y = v * (float)h - 0.5f;
+        const float x0 = floorf(x), y0 = floorf(y);
+        const float fx = x - x0, fy = y - y0;
+        int ix0 = (int)x0, iy0 = (int)y0;
+        const int xa = ((ix0 % w) + w) % w, xb = (((ix0 + 1) % w) + w) % w;
+        const int ya = min(max(iy0, 0), h - 1), yb = min(max(iy0 + 1, 0), h - 1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float p00 = sky[((size_t)ya * w + xa) * 3 + c], p10 = sky[((size_t)ya * w + xb) * 3 + c];
+            const float p01 = sky[((size_t)yb * w + xa) * 3 + c], p11 = sky[((size_t)yb * w + xb) * 3 + c];
+            const float val = (1.f - fy) * ((1.f - fx) * p00 + fx * p10) + fy * ((1.f - fx) * p01 + fx * p11);
+            target[3 * i + c] = logf(fmaxf(val, 1e-6f));
+        }
+    }
+}
+
+// X0[i] = [sin 2 pi (B uv_i), cos 2 pi (B uv_i)] padded to 128
+__global__ void k_train_features(int64_t B, const float* __restrict__ uv, const float* __restrict__ Bm, int F,
+                                 float* __restrict__ X0)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B; i += (int64_t)gridDim.x * blockDim.x) {
+        const float u = uv[2 * i], v = uv[2 * i + 1];
+        float* row = X0 + i * kD;
+        for (int f = 0; f < F; ++f) {
+            float s, c;
+            fourier_feature(__ldg(&Bm[2 * f]), __ldg(&Bm[2 * f + 1]), u, v, s, c);
+            row[f] = s;
+            row[F + f] = c;
+        }
+        for (int k = 2 * F; k < kD; ++k) row[k] = 0.f;
+    }
+}
+
+// Xout = relu(Xin W^T + b); W is [out][in] row-major (PyTorch layout)
+__global__ void __launch_bounds__(kT, 1) k_layer_fwd(int64_t B, const float* __restrict__ Xin, float* __restrict__ Xout,
+                                                     const float* __restrict__ W, const float* __restrict__ b, int in,
+                                                     int out)
+{
+    extern __shared__ float4 smem4[];
+    float* Ws = reinterpret_cast<float*>(smem4);   // [k][j] = W[j][k]
+    float* Xs = Ws + kD * kD;                       // [k][row]
+    for (int idx = threadIdx.x; idx < kD * kD; idx += kT) {
+        const int j = idx / kD, k = idx % kD;
+        Ws[k * kD + j] = (j < out && k < in) ? W[(size_t)j * in + k] : 0.f;
+    }
+    const TileMap m;
+    const int64_t n_tiles = (B + kT - 1) / kT;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        __syncthreads();
+        load_rows_transposed(Xs, Xin, tile, B);
+        __syncthreads();
+        float acc[4][32];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[r][j] = 0.f;
+        tile_mma(Xs, Ws, m, acc);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t g = tile * kT + 4 * m.rg + r;
+            if (g >= B) continue;
+            float4* dst = reinterpret_cast<float4*>(Xout + g * kD + 32 * m.og);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int j = 32 * m.og + 4 * q + e;
+                    o[e] = j < out ? fmaxf(acc[r][4 * q + e] + __ldg(&b[j]), 0.f) : 0.f;
+                }
+                dst[q] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        }
+    }
+}
+
+// dXin = (dXout W) * [Xin > 0]; W is [out][in]
+__global__ void __launch_bounds__(kT, 1) k_layer_bwd_dx(int64_t B, const float* __restrict__ dXout,
+                                                        const float* __restrict__ Xin, float* __restrict__ dXin,
+                                                        const float* __restrict__ W, int in, int out)
+{
+    extern __shared__ float4 smem4[];
+    float* Ws = reinterpret_cast<float*>(smem4);   // [j][k] = W[j][k]
+    float* Ds = Ws + kD * kD;                       // [j][row]
+    for (int idx = threadIdx.x; idx < kD * kD; idx += kT) {
+        const int j = idx / kD, k = idx % kD;
+        Ws[j * kD + k] = (j < out && k < in) ? W[(size_t)j * in + k] : 0.f;
+    }
+    const TileMap m;
+    const int64_t n_tiles = (B + kT - 1) / kT;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        __syncthreads();
+        load_rows_transposed(Ds, dXout, tile, B);
+        __syncthreads();
+        float acc[4][32];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[r][j] = 0.f;
+        tile_mma(Ds, Ws, m, acc);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t g = tile * kT + 4 * m.rg + r;
+            if (g >= B) continue;
+            const float4* xin = reinterpret_cast<const float4*>(Xin + g * kD + 32 * m.og);
+            float4* dst = reinterpret_cast<float4*>(dXin + g * kD + 32 * m.og);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 x = xin[q];
+                dst[q] = make_float4(x.x > 0.f ? acc[r][4 * q] : 0.f, x.y > 0.f ? acc[r][4 * q + 1] : 0.f,
+                                     x.z > 0.f ? acc[r][4 * q + 2] : 0.f, x.w > 0.f ? acc[r][4 * q + 3] : 0.f);
+            }
+        }
+    }
+}
+
+// per-CTA partials of dW = dXout^T Xin and db = sum dXout over the CTA's tiles:
+// partial[block] = [128 x 128 dW (j-major)] [128 db]
+__global__ void __launch_bounds__(kT, 1) k_layer_bwd_dw(int64_t B, const float* __restrict__ dXout,
+                                                        const float* __restrict__ Xin, float* __restrict__ partial)
+{
+    extern __shared__ float4 smem4[];
+    float* Ds = reinterpret_cast<float*>(smem4);   // [i][j] (natural layout: reduction index first)
+    float* Xs = Ds + kD * kD;                       // [i][k]
+    const TileMap m;                                // rows of dW: j = 4 rg + r, columns k = 32 og + c
+    float acc[4][32];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[r][j] = 0.f;
+    float db[4] = {0.f, 0.f, 0.f, 0.f};
+    const int64_t n_tiles = (B + kT - 1) / kT;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kD * kD / 4; idx += kT) {
+            const int i = idx / (kD / 4), q = idx % (kD / 4);
+            const int64_t g = tile * kT + i;
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            reinterpret_cast<float4*>(Ds)[idx] = g < B ? reinterpret_cast<const float4*>(dXout + g * kD)[q] : z;
+            reinterpret_cast<float4*>(Xs)[idx] = g < B ? reinterpret_cast<const float4*>(Xin + g * kD)[q] : z;
+        }
+        __syncthreads();
+        tile_mma(Ds, Xs, m, acc);
+        if (m.og == 0) {
+            for (int i = 0; i < kT; ++i) {
+                const float4 d = *reinterpret_cast<const float4*>(&Ds[i * kD + 4 * m.rg]);
+                db[0] += d.x; db[1] += d.y; db[2] += d.z; db[3] += d.w;
+            }
+        }
+    }
+    float* P = partial + (size_t)blockIdx.x * (kD * kD + kD);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        float4* dst = reinterpret_cast<float4*>(P + (4 * m.rg + r) * kD + 32 * m.og);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            dst[q] = make_float4(acc[r][4 * q], acc[r][4 * q + 1], acc[r][4 * q + 2], acc[r][4 * q + 3]);
+    }
+    if (m.og == 0)
+        for (int r = 0; r < 4; ++r) P[kD * kD + 4 * m.rg + r] = db[r];
+}
+
+// output layer, colour matrix, Huber loss: dXlast = relu-masked W4^T dy,
+// partial head gradients and FP64 loss partials per CTA.
+// head partial[block] = [3 x 128 dW4] [3 db4]
+__global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __restrict__ X, const float* __restrict__ target,
+                                                     const float* __restrict__ W4, const float* __restrict__ b4, int H,
+                                                     const float* __restrict__ Mm, float delta, float inv_n,
+                                                     float* __restrict__ dX, float* __restrict__ head_partial,
+                                                     double* __restrict__ loss_partial)
+{
+    __shared__ float dys[kT][3];
+    __shared__ double lsum[kT];
+    float gW[3] = {0.f, 0.f, 0.f};   // this thread's column k = threadIdx.x of dW4
+    float gb[3] = {0.f, 0.f, 0.f};
+    double loss = 0.0;
+    float M[9];
+    for (int i = 0; i < 9; ++i) M[i] = Mm[i];
+    const int64_t n_tiles = (B + kT - 1) / kT;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t g = tile * kT + threadIdx.x;
+        float dy[3] = {0.f, 0.f, 0.f};
+        if (g < B) {
+            const float* x = X + g * kD;
+            float y[3] = {__ldg(&b4[0]), __ldg(&b4[1]), __ldg(&b4[2])};
+            for (int k = 0; k < H; ++k) {
+                const float xv = x[k];
+                y[0] = fmaf(__ldg(&W4[k]), xv, y[0]);
+                y[1] = fmaf(__ldg(&W4[H + k]), xv, y[1]);
+                y[2] = fmaf(__ldg(&W4[2 * H + k]), xv, y[2]);
+            }
+            float dz[3];
+            for (int c = 0; c < 3; ++c) {
+                const float z = M[3 * c] * y[0] + M[3 * c + 1] * y[1] + M[3 * c + 2] * y[2];
+                const float r = z - target[3 * g + c];
+                const float a = fabsf(r);
+                loss += a <= delta ? 0.5 * (double)r * (double)r : (double)delta * ((double)a - 0.5 * (double)delta);
+                dz[c] = (a <= delta ? r : copysignf(delta, r)) * inv_n;
+            }
+            for (int j = 0; j < 3; ++j) dy[j] = M[j] * dz[0] + M[3 + j] * dz[1] + M[6 + j] * dz[2];
+            float* dxr = dX + g * kD;
+            for (int k = 0; k < kD; ++k) {
+                const float v = k < H ? dy[0] * __ldg(&W4[k]) + dy[1] * __ldg(&W4[H + k]) + dy[2] * __ldg(&W4[2 * H + k])
+                                      : 0.f;
+                dxr[k] = (k < H && x[k] > 0.f) ? v : 0.f;
+            }
+        }
+        __syncthreads();
+        dys[threadIdx.x][0] = dy[0]; dys[threadIdx.x][1] = dy[1]; dys[threadIdx.x][2] = dy[2];
+        __syncthreads();
+        // column k = threadIdx.x of dW4 over the tile's samples, in sample order
+        const int k = threadIdx.x;
+        for (int i = 0; i < kT; ++i) {
+            const int64_t gi = tile * kT + i;
+            if (gi >= B) break;
+            const float xv = X[gi * kD + k];
+            gW[0] = fmaf(dys[i][0], xv, gW[0]);
+            gW[1] = fmaf(dys[i][1], xv, gW[1]);
+            gW[2] = fmaf(dys[i][2], xv, gW[2]);
+            if (k < 3) gb[k] += dys[i][k];
+        }
+    }
+    float* P = head_partial + (size_t)blockIdx.x * (3 * kD + 3);
+    P[threadIdx.x] = gW[0];
+    P[kD + threadIdx.x] = gW[1];
+    P[2 * kD + threadIdx.x] = gW[2];
+    if (threadIdx.x < 3) P[3 * kD + threadIdx.x] = gb[threadIdx.x];
+    lsum[threadIdx.x] = loss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < kT; ++i) s += lsum[i];
+        loss_partial[blockIdx.x] = s;
+    }
+}
+
+// Fixed-order sum of per-CTA partials into the flat gradient layout:
+// dst_W[j * in + k] for j < out, k < in, then dst_b[j].  stride/wofs/bofs
+// describe the partial layout ([block][stride], W block at wofs with row
+// pitch pitch, bias at bofs).
+__global__ void k_sum_partials(const float* __restrict__ partial, int n_blocks, int stride, int pitch, int bofs,
+                               int in, int out, float* __restrict__ dst_W, float* __restrict__ dst_b)
+{
+    const int n = out * in + out;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        int src;
+        float* dst;
+        if (idx < out * in) {
+            const int j = idx / in, k = idx % in;
+            src = j * pitch + k;
+            dst = dst_W + idx;
+        } else {
+            src = bofs + (idx - out * in);
+            dst = dst_b + (idx - out * in);
+        }
+        float s = 0.f;
+        for (int b = 0; b < n_blocks; ++b) s += partial[(size_t)b * stride + src];
+        *dst = s;
+    }
+}
+
+__global__ void k_sum_loss(const double* __restrict__ partial, int n, double scale, double* __restrict__ out_d,
+                           float* __restrict__ out_f)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += partial[i];
+    s *= scale;   // mean over samples and channels
+    if (out_d) *out_d = s;
+    if (out_f) *out_f = (float)s;
+}
+
+// Adam (Kingma & Ba 2015) with bias-corrected moments
+__global__ void k_adam(int64_t n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+cudaError_t train_inputs(uint32_t seed, uint32_t step, int64_t B, const float* sky, int w, int h, float* uv,
+                         float* target, cudaStream_t s)
+{
+    k_train_inputs<<<(unsigned)std::min<int64_t>((B + 255) / 256, 152 * 16), 256, 0, s>>>(seed, step, B, sky, w, h, uv,
+                                                                                           target);
+    return cudaGetLastError();
+}
+
+// Loss and gradient of a batch: uv [B][2], target [B][3] (log space) ->
+// grad (flat trainable layout) and the loss (FP64 and/or FP32 copies).
+cudaError_t nif_loss_grad(const TrainNet& net, int64_t B, const float* uv, const float* target, float delta,
+                          TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s)
+{
+    if (B <= 0) return cudaSuccess;
+    cudaError_t e;
+    const int G = wk.n_blocks;
+    for (auto fn : {(const void*)k_layer_fwd, (const void*)k_layer_bwd_dx, (const void*)k_layer_bwd_dw}) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+        if (e != cudaSuccess) return e;
+    }
+    k_train_features<<<(unsigned)std::min<int64_t>((B + 127) / 128, 152 * 8), 128, 0, s>>>(B, uv, net.B, net.F, wk.X[0]);
+    // forward through the hidden layers
+    for (int l = 0; l < net.L; ++l) {
+        const int in = l == 0 ? 2 * net.F : net.H;
+        k_layer_fwd<<<G, kT, kGemmSmem, s>>>(B, wk.X[l], wk.X[l + 1], net.W[l], net.b[l], in, net.H);
+    }
+    // head + loss
+    k_head_loss<<<G, kT, 0, s>>>(B, wk.X[net.L], target, net.W[net.L], net.b[net.L], net.H, net.M, delta,
+                                 1.f / (3.f * (float)B), wk.dX[0], wk.partial, wk.loss_partial);
+    k_sum_partials<<<4, 256, 0, s>>>(wk.partial, G, 3 * kD + 3, kD, 3 * kD, net.H, 3, net.gW[net.L], net.gb[net.L]);
+    k_sum_loss<<<1, 32, 0, s>>>(wk.loss_partial, G, 1.0 / (3.0 * (double)B), loss_d, loss_f);
+    // backward through the hidden layers
+    int cur = 0;
+    for (int l = net.L - 1; l >= 0; --l) {
+        const int in = l == 0 ? 2 * net.F : net.H;
+        k_layer_bwd_dw<<<G, kT, kGemmSmem, s>>>(B, wk.dX[cur], wk.X[l], wk.partial);
+        k_sum_partials<<<64, 256, 0, s>>>(wk.partial, G, kD * kD + kD, kD, kD * kD, in, net.H, net.gW[l], net.gb[l]);
+        if (l > 0) {
+            k_layer_bwd_dx<<<G, kT, kGemmSmem, s>>>(B, wk.dX[cur], wk.X[l], wk.dX[cur ^ 1], net.W[l], in, net.H);
+            cur ^= 1;
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t adam_step(int64_t n, float* w, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
+                      float c1, float c2, cudaStream_t s)
+{
+    k_adam<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(n, w, g, m, v, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+}  // namespace ptk

@@ -54,6 +54,11 @@ class RenderCfg(C.Structure):
                 ("first_sample", I32)]
 
 
+class TrainCfg(C.Structure):
+    _fields_ = [("steps", I64), ("batch", I64), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float), ("huber_delta", C.c_float), ("seed", U32)]
+
+
 class PTError(RuntimeError):
     def __init__(self, status: int, msg: str, bits: int = 0):
         super().__init__(f"pt status {status}: {msg}")
@@ -94,6 +99,9 @@ def lib():
             "pt_profile_read": ([P, P, P, I32], I32),
             "pt_render_noalloc": ([P, P, P, P, P, P], I32),
             "pt_last_render_work": ([P, P, I32], I32),
+            "pt_nif_set_params": ([P, P, P, P], I32),
+            "pt_train_nif": ([P, P, P, I32, I32, P, P, P], I32),
+            "pt_nif_loss_grad": ([P, P, I64, P, P, C.c_float, P, P, P], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -227,6 +235,31 @@ class Nif:
         out = np.zeros(self.param_count, np.float32)
         self.ctx._raise(lib().pt_nif_get_params(self.ctx.h, self.h, _np_ptr(out)))
         return out
+
+    def set_params(self, flat: np.ndarray, stream=None) -> None:
+        flat = np.ascontiguousarray(flat, np.float32)
+        assert flat.size == self.param_count
+        self.ctx._raise(lib().pt_nif_set_params(self.ctx.h, self.h, _np_ptr(flat), _stream(stream)))
+
+    def train(self, sky: torch.Tensor, steps: int, batch: int = 1 << 16, lr: float = 1e-3, beta1: float = 0.9,
+              beta2: float = 0.999, eps: float = 1e-7, delta: float = 1e-3, seed: int = 0, stream=None) -> torch.Tensor:
+        """pt_train_nif on an HDR image [h, w, 3] (device tensor); returns per-step losses."""
+        sky = sky.contiguous()
+        losses = torch.zeros(max(steps, 1), dtype=torch.float32, device=sky.device)
+        cfg = TrainCfg(steps, batch, lr, beta1, beta2, eps, delta, seed)
+        self.ctx._raise(lib().pt_train_nif(self.ctx.h, self.h, _dptr(sky), sky.shape[1], sky.shape[0], C.byref(cfg),
+                                           _dptr(losses), _stream(stream)))
+        return losses[:steps]
+
+    def loss_grad(self, uv: torch.Tensor, target: torch.Tensor, delta: float = 1e-3, stream=None):
+        """pt_nif_loss_grad: (loss as a device double tensor, gradient in the trainable flat layout)."""
+        uv, target = uv.contiguous(), target.contiguous()
+        n_tr = self.param_count - 2 * self.src.n_freq - 9
+        grad = torch.empty(n_tr, dtype=torch.float32, device=uv.device)
+        loss = torch.zeros(1, dtype=torch.float64, device=uv.device)
+        self.ctx._raise(lib().pt_nif_loss_grad(self.ctx.h, self.h, uv.shape[0], _dptr(uv), _dptr(target), delta,
+                                               _dptr(grad), _dptr(loss), _stream(stream)))
+        return loss, grad
 
     def eval(self, uv: torch.Tensor, precision: str = "fp32", stream=None) -> torch.Tensor:
         uv = uv.contiguous()

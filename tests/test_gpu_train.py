@@ -1,0 +1,146 @@
+"""NIF training through the C ABI against the FP64 oracle: loss and
+gradient of a batch, Adam steps on the procedural sky, refreshed FP32 and
+BF16 layouts after training, and determinism."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2305_20061_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pt():
+    from paper_2305_20061_gb300 import build
+    build.build()
+    from paper_2305_20061_gb300 import pt as _pt
+    return _pt
+
+
+@pytest.fixture(scope="module")
+def ctx(pt):
+    return pt.Context(0)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _nif(F=64, H=128, L=3, seed=0):
+    nif = I.nif_init(n_freq=F, hidden=H, n_hidden_layers=L, colour="yuv", seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    for b in nif.b:
+        b[:] = rng.normal(0, 0.05, b.shape).astype(np.float32)
+    return nif
+
+
+def _split(nif, flat):
+    """trainable flat vector -> per-layer (W, b) pieces"""
+    out, p = [], 0
+    for W, b in zip(nif.W, nif.b):
+        out.append((flat[p:p + W.size], flat[p + W.size:p + W.size + b.size]))
+        p += W.size + b.size
+    return out
+
+
+@pytest.mark.parametrize("delta", [10.0, 1e-3])
+@pytest.mark.parametrize("shape", [(64, 128, 3), (5, 12, 2)])
+def test_loss_and_gradient_match_oracle(pt, ctx, delta, shape):
+    nif = _nif(*shape)
+    g = pt.Nif(ctx, nif)
+    n = 128 * 37 + 5
+    uv = I.uniform_uv(n, seed=3)
+    _, z = O.Nif(nif).forward(uv.astype(np.float64))
+    target = (z + np.random.default_rng(4).normal(0, 0.5, z.shape)).astype(np.float32)
+    loss, grad = g.loss_grad(torch.from_numpy(uv).cuda(), torch.from_numpy(target).cuda(), delta)
+    ctx.check()
+    ref_loss, ref_grad = O.Nif(nif).loss_grad(uv.astype(np.float64), target.astype(np.float64), delta)
+    assert abs(float(loss.item()) - ref_loss) <= 1e-5 * abs(ref_loss)
+    got = grad.cpu().numpy().astype(np.float64)
+    for (gw, gb), (rw, rb) in zip(_split(nif, got), _split(nif, ref_grad)):
+        assert _rel(gw, rw) <= 1e-4 and _rel(gb, rb) <= 1e-4, (_rel(gw, rw), _rel(gb, rb))
+
+
+def test_adam_steps_match_oracle(pt, ctx):
+    """Three training steps from the same weights on the same Philox samples:
+    the per-step losses agree and every weight moved by the same Adam step
+    (to a small fraction of the learning rate)."""
+    nif = _nif()
+    sky = I.procedural_sky(128, 64)
+    g = pt.Nif(ctx, nif)
+    steps, batch, lr = 3, 512, 1e-3
+    losses = g.train(torch.from_numpy(sky).cuda(), steps=steps, batch=batch, lr=lr, seed=5).cpu().numpy()
+    ctx.check()
+    on = O.Nif(nif)
+    ref_losses = on.train(sky, seed=5, steps=steps, batch=batch, lr=lr)
+    assert np.allclose(losses, ref_losses, rtol=1e-4), (losses, ref_losses)
+    got = g.get_params().astype(np.float64)
+    F = nif.n_freq
+    got_tr = got[2 * F:-9]
+    ref_tr = on.get_trainable()
+    init_tr = O.Nif(nif).get_trainable()
+    moved_gpu, moved_ref = got_tr - init_tr, ref_tr - init_tr
+    diff = np.abs(moved_gpu - moved_ref) / lr
+    assert np.median(diff) < 1e-3 and np.mean(diff > 0.05) < 0.01, (np.median(diff), np.mean(diff > 0.05))
+    assert np.all(np.abs(moved_gpu) <= steps * lr * 1.0001)
+
+
+def test_layouts_follow_training_and_run_is_deterministic(pt, ctx):
+    """After training, the FP32 kernel evaluates the downloaded weights to
+    1e-5 of the oracle and the BF16 kernel matches its rounding model; two
+    identical runs produce bit-identical weights."""
+    from test_gpu_nif_tc import bf16_model
+    nif = _nif()
+    sky = torch.from_numpy(I.procedural_sky(256, 128)).cuda()
+    runs = []
+    for _ in range(2):
+        g = pt.Nif(ctx, nif)
+        losses = g.train(sky, steps=60, batch=2048, lr=1e-2, seed=1).cpu().numpy()
+        ctx.check()
+        runs.append((g, g.get_params(), losses))
+    assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][2], runs[1][2])
+    g, params, losses = runs[0]
+    assert losses[-10:].mean() < losses[:3].mean()
+    trained = nif.copy()
+    p = 2 * nif.n_freq
+    for W, b in zip(trained.W, trained.b):
+        W[:] = params[p:p + W.size].reshape(W.shape)
+        p += W.size
+        b[:] = params[p:p + b.size]
+        p += b.size
+    uv = I.uniform_uv(5000, seed=8)
+    f32 = g.eval(torch.from_numpy(uv).cuda(), "fp32").cpu().numpy().astype(np.float64)
+    b16 = g.eval(torch.from_numpy(uv).cuda(), "bf16").cpu().numpy().astype(np.float64)
+    ctx.check()
+    ref, _ = O.Nif(trained).forward(uv.astype(np.float64))
+    assert (np.abs(f32 - ref) / np.abs(ref)).max() <= 1e-5
+    model = bf16_model(trained, uv)
+    rel = np.abs(b16 - model) / np.abs(model)
+    assert np.median(rel) <= 2e-4 and rel.max() <= 2e-2
+
+
+def test_training_on_procedural_sky_improves_reconstruction(pt, ctx):
+    """A trained NIF reconstructs the 2048 x 1024 sky better than its
+    initialisation (log-RMSE on the pixel-centre grid, reported)."""
+    nif = I.nif_init(colour="yuv")
+    sky_np = I.procedural_sky()
+    sky = torch.from_numpy(sky_np).cuda()
+    g = pt.Nif(ctx, nif)
+    H, W = sky_np.shape[:2]
+    jj, ii = np.meshgrid(np.arange(0, H, 4), np.arange(0, W, 4), indexing="ij")
+    uv = np.stack([(ii.ravel() + 0.5) / W, (jj.ravel() + 0.5) / H], 1).astype(np.float32)
+    ref = np.log(np.maximum(sky_np[jj.ravel(), ii.ravel()].astype(np.float64), 1e-6))
+
+    def log_rmse():
+        out = g.eval(torch.from_numpy(uv).cuda(), "fp32").cpu().numpy().astype(np.float64)
+        return float(np.sqrt(np.mean((np.log(out) - ref) ** 2)))
+
+    before = log_rmse()
+    losses = g.train(sky, steps=1500, batch=1 << 14, lr=1e-3, seed=0).cpu().numpy()
+    ctx.check()
+    after = log_rmse()
+    print({"log_rmse_before": before, "log_rmse_after": after, "loss_first": float(losses[0]),
+           "loss_last": float(losses[-20:].mean())})
+    assert after < 0.5 * before
