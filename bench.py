@@ -1,13 +1,16 @@
 """Benchmark of the neural path tracer's hot path on GB300.
 
-A step is one full frame of the spheres + HDR-NIF workload (256 spheres,
-512x512 pixels, 64 samples per pixel, depth 8: 16.8M paths) rendered through
-the C ABI: camera rays, traversal, bounce sampling, NIF shading of every
-escape (BF16 tensor-core kernel by default) and the sample reduction.  The
-same line reports the FP32-network frame rate and the relative RMSE between
-the BF16 and FP32 frames.  Prints one JSON line (rank 0).
+A step is one full frame rendered through the C ABI: camera rays,
+traversal, bounce sampling, NIF shading of every escape (BF16 tensor-core
+kernel by default) and the sample reduction.  The default workload is the
+spheres + HDR-NIF scene (256 spheres, 512x512 pixels, 64 samples per pixel,
+depth 8: 16.8M paths per frame) whose environment NIF is first trained on the
+procedural 2048x1024 sky with pt_train_nif.  The same line reports the
+FP32-network frame rate and the relative RMSE between the BF16 and FP32
+frames.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
+                  [--workload C1|C2|C3|C4]
   python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
 
 Multi-GPU (torchrun, one rank per GPU): each rank renders its own disjoint
@@ -32,13 +35,14 @@ from paper_2305_20061_gb300 import inputs as I  # noqa: E402
 
 METRIC = "Msamples/s & NIF evals/s at 1 GB300; BF16-TC vs FP32 at stated image RMSE"
 UNIT = "Msamples/s"
-WORKLOAD = "C2"
 FLOP_PER_EVAL = 2 * (3 * 128 * 128 + 128 * 3)   # 99,072: three 128x128 layers + 128->3 head
 TC_FLOP_PER_EVAL = 2 * 3 * 128 * 128            # 98,304 in the three hidden layers
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# FP32 operations per traversal step as implemented (see DESIGN.md section 5)
+# FP32 operations per traversal step as implemented (DESIGN.md section 5)
 OPS_NODE, OPS_SPHERE, OPS_QUAD, OPS_TRI = 58, 36, 12, 46
+# algorithmic bytes per traversal step and per ray-bounce of queue traffic
+BYTES_NODE, BYTES_SPHERE, BYTES_QUAD, BYTES_TRI, BYTES_RAY = 48, 16, 32, 48, 140
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -104,23 +108,26 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload(spp=None):
-    sc = I.make_scene(WORKLOAD)
-    cfg = I.CONFIGS[WORKLOAD]["cfg"]
+def workload(name, spp=None):
+    sc = I.make_scene(name)
+    cfg = I.CONFIGS[name]["cfg"]
     if spp:  # smaller case for profiler captures only
         cfg = I.RenderCfg(cfg.width, cfg.height, spp, cfg.max_depth, cfg.seed)
-    nif = I.nif_init(colour="yuv")
+    nif = I.nif_init(colour="identity" if name == "C1" else "yuv") if sc.env_const is None else None
     return sc, cfg, nif
 
 
-def config_dict(cfg, precision):
-    return {"workload": f"{WORKLOAD}: 256 spheres (60% Lambertian / 30% GGX metal / 10% dielectric) + HDR-NIF "
-                        f"environment, {cfg.width}x{cfg.height}, {cfg.spp} spp, max depth {cfg.max_depth}, no RR",
-            "paths_per_frame": cfg.n_slots,
-            "nif": "F=64 Gaussian Fourier (sigma 10) -> 3x FC-128 ReLU -> FC-3 -> YUV->RGB -> exp, random init",
-            "nif_precision": precision,
-            "l2": "per-step working set > L2 (wavefront queues ~2.7 GB) and a 512 MB L2 flush between timed "
-                  "steps (outside the timed events)"}
+def config_dict(name, cfg, precision, trained):
+    d = {"workload": f"{name}: {I.CONFIGS[name]['desc']}; rendered {cfg.width}x{cfg.height}, {cfg.spp} spp, "
+                     f"max depth {cfg.max_depth}, no RR",
+         "paths_per_frame": cfg.n_slots,
+         "l2": "per-step working set > L2 (wavefront queues ~2.7 GB per 2^24 paths) and a 512 MB L2 flush between "
+               "timed steps (outside the timed events)"}
+    if precision is not None:
+        d["nif"] = ("F=64 Gaussian Fourier (sigma 10) -> 3x FC-128 ReLU -> FC-3 -> colour matrix -> exp; " +
+                    ("weights trained by pt_train_nif on the procedural 2048x1024 sky" if trained else "random init"))
+        d["nif_precision"] = precision
+    return d
 
 
 # ----------------------------------------------------------------------------
@@ -129,7 +136,7 @@ def oracle_rate(sc, cfg, nif, target_s: float, n_threads: int):
     of every m-th pixel), sized to take about target_s seconds."""
     from oracle import oracle as O
     osc = O.Scene(sc)
-    onif = O.Nif(nif)
+    onif = O.Nif(nif) if nif is not None else None
     n_pix_total = cfg.width * cfg.height
 
     def run(n_pix):
@@ -148,7 +155,7 @@ def oracle_rate(sc, cfg, nif, target_s: float, n_threads: int):
 def bench_reference(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
-    sc, cfg, nif = workload(args.spp)
+    sc, cfg, nif = workload(args.workload, args.spp)
     threads = os.cpu_count() or 1
     run, n_pix = oracle_rate(sc, cfg, nif, target_s=args.ref_step_s, n_threads=threads)
     for _ in range(args.warmup):
@@ -164,7 +171,7 @@ def bench_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_dict(cfg, "fp64-oracle"),
+        "data": "synthetic", "config": config_dict(args.workload, cfg, "fp64-oracle" if nif else None, False),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -187,23 +194,57 @@ def bench_ours(args):
     from paper_2305_20061_gb300 import pt
 
     dev = f"cuda:{local}"
-    sc, cfg, nif = workload(args.spp)
+    sc, cfg, nif = workload(args.workload, args.spp)
+    uses_nif = nif is not None
+    precision = args.precision if uses_nif else None
     ctx = pt.Context(local)
+    t_build = time.perf_counter()
     scene = pt.Scene(ctx, sc)
-    gnif = pt.Nif(ctx, nif)
+    t_build = time.perf_counter() - t_build
+    gnif = pt.Nif(ctx, nif) if uses_nif else None
+
+    # the environment NIF is trained on the procedural 2048 x 1024 HDR sky first (not timed as a frame)
+    train = None
+    if uses_nif and args.train_steps > 0:
+        sky = torch.from_numpy(I.procedural_sky()).to(dev)
+        batch = 1 << 16
+        gnif.train(sky, steps=5, batch=batch, lr=1e-3, seed=0)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        losses = gnif.train(sky, steps=args.train_steps, batch=batch, lr=1e-3, seed=0)
+        t1.record()
+        torch.cuda.synchronize()
+        ctx.check()
+        tms = t0.elapsed_time(t1)
+        train = {"steps": args.train_steps + 5, "batch": batch, "ms_per_step": tms / args.train_steps,
+                 "samples_per_s": args.train_steps * batch / (tms * 1e-3),
+                 "fwd_bwd_tflops": args.train_steps * batch * 3 * FLOP_PER_EVAL / (tms * 1e-3) / 1e12,
+                 "loss_first": float(losses[0].item()), "loss_last": float(losses[-50:].mean().item())}
+        del sky
+        # host copy of the trained weights (used by the end-to-end leg and the CPU baseline)
+        params = gnif.get_params()
+        p = 2 * nif.n_freq
+        for W, b in zip(nif.W, nif.b):
+            W[:] = params[p:p + W.size].reshape(W.shape)
+            p += W.size
+            b[:] = params[p:p + b.size]
+            p += b.size
     img = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     first_sample = rank * cfg.spp
+    rprec = precision or "fp32"
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed_frames(precision, steps, profile=False):
+    def timed_frames(prec, steps, profile=False):
         for _ in range(args.warmup):
-            pt.render(ctx, scene, gnif, cfg, precision, out=img, first_sample=first_sample)
+            pt.render(ctx, scene, gnif, cfg, prec, out=img, first_sample=first_sample)
         ctx.check()
         if profile:
             pt.profile_enable(ctx, True)
@@ -213,7 +254,7 @@ def bench_ours(args):
         for i in range(steps):
             flush.fill_(float(i))           # evict L2 between timed steps (not timed)
             ev[i][0].record(stream)
-            pt.render(ctx, scene, gnif, cfg, precision, out=img, first_sample=first_sample)
+            pt.render(ctx, scene, gnif, cfg, prec, out=img, first_sample=first_sample)
             ev[i][1].record(stream)
         barrier()
         prof = pt.profile_read(ctx) if profile else None
@@ -230,7 +271,7 @@ def bench_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    ms, prof = timed_frames(args.precision, args.steps, profile=True)
+    ms, prof = timed_frames(rprec, args.steps, profile=True)
     clocks = sampler.stop()
     counts = pt.last_render_counts(ctx, cfg.max_depth)
     work = pt.last_render_work(ctx)
@@ -242,9 +283,9 @@ def bench_ours(args):
     trace_ms = prof["trace"][0] / args.steps
 
     # the other precision on the same frame, and the image difference between them
-    other = "fp32" if args.precision == "bf16" else "bf16"
+    other = "fp32" if rprec == "bf16" else "bf16"
     ms_other, rel_rmse = None, None
-    if not args.no_compare:
+    if uses_nif and not args.no_compare:
         ms_other, _ = timed_frames(other, max(2, min(args.steps, 5)))
         a = pt.render(ctx, scene, gnif, cfg, "bf16", first_sample=first_sample).double()
         b = pt.render(ctx, scene, gnif, cfg, "fp32", first_sample=first_sample).double()
@@ -252,29 +293,31 @@ def bench_ours(args):
         rel_rmse = float(torch.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()).item())
 
     # standalone NIF throughput: 2^24 uniform (u, v) through each kernel
-    uv = torch.from_numpy(I.uniform_uv(1 << 24, seed=1)).to(dev)
     nif_alone = {}
-    for prec in (() if args.no_compare else ("bf16", "fp32")):
-        gnif.eval(uv, prec)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 3
-        e0.record(stream)
-        for _ in range(reps):
+    if uses_nif and not args.no_compare:
+        uv = torch.from_numpy(I.uniform_uv(1 << 24, seed=1)).to(dev)
+        for prec in ("bf16", "fp32"):
             gnif.eval(uv, prec)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / reps
-        nif_alone[prec] = {"evals_per_s": (1 << 24) / (t * 1e-3), "ms": t,
-                           "tflops": (1 << 24) * (TC_FLOP_PER_EVAL if prec == "bf16" else FLOP_PER_EVAL) / (t * 1e-3)
-                           / 1e12}
-    ctx.check()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            e0.record(stream)
+            for _ in range(reps):
+                gnif.eval(uv, prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / reps
+            flop = TC_FLOP_PER_EVAL if prec == "bf16" else FLOP_PER_EVAL
+            nif_alone[prec] = {"evals_per_s": (1 << 24) / (t * 1e-3), "ms": t,
+                               "tflops": (1 << 24) * flop / (t * 1e-3) / 1e12}
+        ctx.check()
 
     # live roofline of the dominant kernel of the timed frames
     meas, which = peaks()
     clock = float(meas.get("sm_max_mhz", 2070.0))
     dom = max(("trace", "nif", "reduce"), key=lambda k: prof[k][0])
-    if dom == "nif" and args.precision == "bf16":
+    big_scene = scene.info()["node_bytes"] > 128 * 1024 * 1024   # BVH larger than L2
+    if dom == "nif" and rprec == "bf16":
         peak = float(meas.get("bf16_tflops_sustained", meas["bf16_tflops"]))
         achieved = evals * TC_FLOP_PER_EVAL / (nif_ms * 1e-3) / 1e12
         roof = {"kernel": "k_nif_tc", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -288,6 +331,17 @@ def bench_ours(args):
                 "frac": achieved / peak, "traffic": None,
                 "per_unit": f"{FLOP_PER_EVAL} FLOP per NIF evaluation x {evals} evaluations per launch",
                 "peak_note": f"FP32 FFMA derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clock:.0f} MHz"}
+    elif big_scene:
+        nbytes = (BYTES_NODE * work["nodes"] + BYTES_SPHERE * work["sphere"] + BYTES_QUAD * work["quad"] +
+                  BYTES_TRI * work["triangle"] + BYTES_RAY * rays)
+        peak = float(meas["hbm_gbs"])
+        achieved = nbytes / (trace_ms * 1e-3) / 1e9
+        roof = {"kernel": "k_bounce", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "per_unit": f"bytes per node fetch {BYTES_NODE}, per sphere/quad/triangle test "
+                            f"{BYTES_SPHERE}/{BYTES_QUAD}/{BYTES_TRI}, per ray {BYTES_RAY}; {work['nodes']} node "
+                            f"fetches, {work['triangle']} triangle tests, {rays} rays per frame",
+                "peak_note": f"HBM copy bandwidth ({which}); BVH {scene.info()['node_bytes'] / 2**20:.0f} MiB > L2"}
     else:
         ops = (OPS_NODE * work["nodes"] + OPS_SPHERE * work["sphere"] + OPS_QUAD * work["quad"] +
                OPS_TRI * work["triangle"])
@@ -297,30 +351,32 @@ def bench_ours(args):
                 "frac": achieved / peak, "traffic": None,
                 "per_unit": f"FP32 ops per node fetch {OPS_NODE}, per sphere/quad/triangle test "
                             f"{OPS_SPHERE}/{OPS_QUAD}/{OPS_TRI}; {work['nodes']} node fetches and "
-                            f"{work['sphere']} sphere tests per frame ({cfg.max_depth} launches)",
+                            f"{work['sphere'] + work['quad'] + work['triangle']} primitive tests per frame "
+                            f"({cfg.max_depth} launches)",
                 "peak_note": f"FP32 issue rate derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x {clock:.0f} MHz"}
 
     # end to end through the C ABI with host buffers: scene + weights in, image out
     e2e = None
     if not args.no_e2e:
         host_img = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, pin_memory=True)
-        flat = pt.nif_flat(nif)
-        h2d = sum(x.nbytes for x in (sc.sphere, sc.sphere_mat, sc.mat_type, sc.mat)) + flat.nbytes
+        scene_arrays = (sc.sphere, sc.sphere_mat, sc.quad, sc.quad_axis, sc.quad_mat, sc.vert, sc.tri, sc.tri_mat,
+                        sc.mat_type, sc.mat)
+        h2d = sum(x.nbytes for x in scene_arrays) + (pt.nif_flat(nif).nbytes if uses_nif else 0)
         d2h = host_img.numel() * 4
-        n_e2e = max(3, min(args.steps, 10))
+        n_e2e = max(3, min(args.steps, 10)) if not big_scene else 1
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             s2 = pt.Scene(ctx, sc)
-            n2 = pt.Nif(ctx, nif)
-            pt.render(ctx, s2, n2, cfg, args.precision, out=img, first_sample=first_sample)
+            n2 = pt.Nif(ctx, nif) if uses_nif else None
+            pt.render(ctx, s2, n2, cfg, rprec, out=img, first_sample=first_sample)
             host_img.copy_(img, non_blocking=True)
             torch.cuda.synchronize()
             del s2, n2
         dt = (time.perf_counter() - t0) / n_e2e
         e2e = {"value": world * paths / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "note": "pt_create_scene + pt_load_nif from host arrays, pt_render, "
-                                                        "image copied to pinned host memory, per step"}
+               "d2h_bytes_per_step": int(d2h), "note": "pt_create_scene (host BVH build) + pt_load_nif from host "
+                                                        "arrays, pt_render, image copied to pinned host memory, per step"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -331,22 +387,26 @@ def bench_ours(args):
                "sample": f"all {cfg.spp} samples of {n} evenly strided pixels ({n * cfg.spp} paths), FP64 oracle"}
 
     if rank == 0:
-        print(json.dumps({
+        line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32",
-            "data": "synthetic (procedural scene, random-init NIF weights; seeds 0)",
-            "config": config_dict(cfg, args.precision),
-            f"{other}_value": world * paths / (ms_other * 1e-3) / 1e6 if ms_other else None,
-            "bf16_vs_fp32_image_rel_rmse": rel_rmse,
-            "nif_evals_per_step": evals, "rays_per_step": rays,
-            "nif_evals_per_s_in_render": evals / (nif_ms * 1e-3) if nif_ms > 0 else None,
-            "nif_standalone_2p24": nif_alone,
-            "traversal_work_per_step": work,
+            "vs_baseline": None, "dtype": "bf16" if rprec == "bf16" and uses_nif else "f32",
+            "data": "synthetic (procedural scene" + (" and sky, NIF trained on the sky" if train else "") + "; seeds 0)",
+            "config": config_dict(args.workload, cfg, precision, train is not None),
+            "rays_per_step": rays, "traversal_work_per_step": work,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "scene_build_s": t_build, "bvh_nodes": scene.info()["n_nodes"], "bvh_depth": scene.info()["bvh_depth"],
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(sum(v[1] for v in prof.values())),
-        }))
+        }
+        if uses_nif:
+            line.update({
+                f"{other}_value": world * paths / (ms_other * 1e-3) / 1e6 if ms_other else None,
+                "bf16_vs_fp32_image_rel_rmse": rel_rmse,
+                "nif_evals_per_step": evals,
+                "nif_evals_per_s_in_render": evals / (nif_ms * 1e-3) if nif_ms > 0 else None,
+                "nif_standalone_2p24": nif_alone, "nif_training": train})
+        print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -358,10 +418,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["C1", "C2", "C3", "C4"], default="C2")
     ap.add_argument("--precision", choices=["bf16", "fp32"], default="bf16")
     ap.add_argument("--spp", type=int, default=None, help="override spp (small cases for profiler captures)")
     ap.add_argument("--cpu-s", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=4.0, help="seconds per reference-arm step")
+    ap.add_argument("--train-steps", type=int, default=2000,
+                    help="Adam steps of the environment NIF on the procedural sky before the frames (0: random init)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the other-precision frames and standalone NIF runs (profiler captures)")
