@@ -168,6 +168,14 @@ PT_API pt_status pt_nif_get_params(pt_ctx* ctx, const pt_nif* nif, float* params
 PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nif, int32_t precision, int64_t n, const float* d_uv,
                              float* d_rgb, void* stream);
 
+/* FP8 E4M3 quantisation of the tensor-core NIF (PT_FP8E4M3): scales[0..3]
+   are the activation scales of the features and of hidden layers 1..3
+   (value = scale x E4M3 code).  Features use 1/448; hidden layers use their
+   maximum over the FP32 network on a 32 x 32 grid of (u, v) pixel centres,
+   divided by 448.  Weights use one scale per output row (row max / 448).
+   PT_EUNSUPPORTED for shapes other than F = 64, H = 128, L = 3. */
+PT_API pt_status pt_nif_fp8_scales(const pt_nif* nif, float* scales);
+
 /* Replace the FP32 master weights (host, flat layout of pt_nif_desc) and
    rebuild the derived layouts.  Synchronises `stream`. */
 PT_API pt_status pt_nif_set_params(pt_ctx* ctx, pt_nif* nif, const float* params, void* stream);

@@ -49,6 +49,8 @@ struct pt_nif {
     float* d_params = nullptr;   // flat FP32 master weights
     float* d_fp32 = nullptr;     // packed FP32 layout (Wt, bias, Wout, bout)
     unsigned char* d_tc = nullptr;  // BF16 shared-memory image of the tensor-core kernel (F=64, H=128, L=3 only)
+    unsigned char* d_fp8 = nullptr; // FP8 E4M3 image of the same shape
+    float fp8_scales[4] = {0, 0, 0, 0};
     DevNif dev = {};
     // training state (allocated by the first training call)
     int64_t n_trainable = 0;
@@ -210,7 +212,11 @@ pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, int ac
         PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nif->d_tc, p, 1, ctx->sm_count, s); }));
         return PT_OK;
     }
-    return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3 (FP8 not in this build)");
+    if (precision == PT_FP8E4M3 && nif->d_fp8) {
+        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_fp8(nif->d_fp8, p, 1, ctx->sm_count, s); }));
+        return PT_OK;
+    }
+    return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3");
 }
 
 }  // namespace
@@ -508,6 +514,13 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
             return fail(ctx, PT_ENOMEM, "NIF tensor-core image upload failed");
         }
     }
+    if (pack_nif_fp8_image(d->params, F, H, L, img, nf->fp8_scales)) {
+        if (cudaMalloc((void**)&nf->d_fp8, img.size()) != cudaSuccess ||
+            cudaMemcpy(nf->d_fp8, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            pt_destroy_nif(nf);
+            return fail(ctx, PT_ENOMEM, "NIF FP8 image upload failed");
+        }
+    }
     *out = nf;
     return PT_OK;
 }
@@ -518,6 +531,7 @@ PT_API void pt_destroy_nif(pt_nif* nf)
     cudaFree(nf->d_params);
     cudaFree(nf->d_fp32);
     cudaFree(nf->d_tc);
+    cudaFree(nf->d_fp8);
     cudaFree(nf->d_grad);
     cudaFree(nf->d_m);
     cudaFree(nf->d_v);
@@ -557,8 +571,12 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
         PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nf->d_tc, p, 0, ctx->sm_count, s); }));
         return PT_OK;
     }
+    if (precision == PT_FP8E4M3 && nf->d_fp8) {
+        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_fp8(nf->d_fp8, p, 0, ctx->sm_count, s); }));
+        return PT_OK;
+    }
     if (precision == PT_BF16 || precision == PT_FP8E4M3)
-        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3 (FP8 not in this build)");
+        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3");
     return fail(ctx, PT_EINVAL, "unknown precision");
 }
 
@@ -628,6 +646,17 @@ pt_status refresh_layouts(pt_ctx* ctx, pt_nif* nf, cudaStream_t s)
 {
     PT_CUDA(repack_nif_fp32(nf->d_params, nf->F, nf->H, nf->L, nf->d_fp32, s));
     if (nf->d_tc) PT_CUDA(repack_nif_tc_image(nf->d_params, nf->d_tc, s));
+    if (nf->d_fp8) {
+        // the FP8 image needs the host calibration pass: round-trip the master weights
+        std::vector<float> host(nf->n_params);
+        std::vector<unsigned char> img;
+        PT_CUDA(cudaMemcpyAsync(host.data(), nf->d_params, host.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+        PT_CUDA(cudaStreamSynchronize(s));
+        if (!pack_nif_fp8_image(host.data(), nf->F, nf->H, nf->L, img, nf->fp8_scales))
+            return fail(ctx, PT_EINVAL, "FP8 repack failed");
+        PT_CUDA(cudaMemcpyAsync(nf->d_fp8, img.data(), img.size(), cudaMemcpyHostToDevice, s));
+        PT_CUDA(cudaStreamSynchronize(s));
+    }
     return PT_OK;
 }
 
@@ -683,6 +712,14 @@ PT_API pt_status pt_train_nif(pt_ctx* ctx, pt_nif* nf, const float* d_sky, int32
     return refresh_layouts(ctx, nf, s);
 }
 
+PT_API pt_status pt_nif_fp8_scales(const pt_nif* nf, float* scales)
+{
+    if (!nf || !scales) return PT_EINVAL;
+    if (!nf->d_fp8) return PT_EUNSUPPORTED;
+    for (int i = 0; i < 4; ++i) scales[i] = nf->fp8_scales[i];
+    return PT_OK;
+}
+
 PT_API pt_status pt_nif_set_params(pt_ctx* ctx, pt_nif* nf, const float* params, void* stream)
 {
     if (!ctx || !nf || !params) return fail(ctx, PT_EINVAL, "bad argument");
@@ -707,8 +744,9 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
     if (n_pix == 0) return PT_OK;
     const int64_t n_slots = n_pix * (int64_t)cfg->spp;
     if (n_slots > 0xFFFFFFFFll) return fail(ctx, PT_EINVAL, "more than 2^32 - 1 paths in one call");
-    if (sc->dev.env_is_nif && cfg->precision != PT_FP32 && !(cfg->precision == PT_BF16 && nf->d_tc))
-        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3 (FP8 not in this build)");
+    if (sc->dev.env_is_nif && cfg->precision != PT_FP32 && !(cfg->precision == PT_BF16 && nf->d_tc) &&
+        !(cfg->precision == PT_FP8E4M3 && nf->d_fp8))
+        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3");
     cudaStream_t s = (cudaStream_t)stream;
     // chunk = whole samples
     int64_t chunk = cfg->chunk_slots > 0 ? cfg->chunk_slots : (int64_t)1 << 24;

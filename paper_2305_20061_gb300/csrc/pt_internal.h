@@ -136,6 +136,9 @@ cudaError_t launch_nif_fp32(const NifEvalParams& p, int mode, int sm_count, cuda
 bool pack_nif_tc_image(const float* params, int F, int H, int L, std::vector<unsigned char>& out);
 cudaError_t launch_nif_tc(const unsigned char* image, const NifEvalParams& p, int mode, int sm_count, cudaStream_t s);
 size_t nif_tc_image_bytes();
+// FP8 E4M3 tensor-core NIF (nif_fp8.cu): same shape; scales_out [4] = activation scales
+bool pack_nif_fp8_image(const float* params, int F, int H, int L, std::vector<unsigned char>& out, float* scales_out);
+cudaError_t launch_nif_fp8(const unsigned char* image, const NifEvalParams& p, int mode, int sm_count, cudaStream_t s);
 
 // NIF training (train.cu).  Pointers into the flat FP32 master weights and
 // into the flat gradient (same order as the trainable part of the weights).

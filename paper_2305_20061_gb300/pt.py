@@ -100,6 +100,7 @@ def lib():
             "pt_render_noalloc": ([P, P, P, P, P, P], I32),
             "pt_last_render_work": ([P, P, I32], I32),
             "pt_nif_set_params": ([P, P, P, P], I32),
+            "pt_nif_fp8_scales": ([P, P], I32),
             "pt_train_nif": ([P, P, P, I32, I32, P, P, P], I32),
             "pt_nif_loss_grad": ([P, P, I64, P, P, C.c_float, P, P, P], I32),
         }
@@ -234,6 +235,11 @@ class Nif:
     def get_params(self) -> np.ndarray:
         out = np.zeros(self.param_count, np.float32)
         self.ctx._raise(lib().pt_nif_get_params(self.ctx.h, self.h, _np_ptr(out)))
+        return out
+
+    def fp8_scales(self) -> np.ndarray:
+        out = np.zeros(4, np.float32)
+        self.ctx._raise(lib().pt_nif_fp8_scales(self.h, _np_ptr(out)))
         return out
 
     def set_params(self, flat: np.ndarray, stream=None) -> None:

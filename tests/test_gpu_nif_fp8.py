@@ -1,0 +1,135 @@
+"""The fused tcgen05 FP8 (E4M3) NIF kernel through the C ABI: exactness
+against a numpy model of its quantisation (same scales, E4M3 round-to-
+nearest-even with saturation, FP32 accumulation), the error against the FP64
+oracle (reported as log-RMSE), and FP8 renders."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2305_20061_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pt():
+    from paper_2305_20061_gb300 import build
+    build.build()
+    from paper_2305_20061_gb300 import pt as _pt
+    return _pt
+
+
+@pytest.fixture(scope="module")
+def ctx(pt):
+    return pt.Context(0)
+
+
+def e4m3(x):
+    """Round to the nearest E4M3 value (ties to even), saturating at +-448."""
+    x = np.asarray(x, np.float64)
+    a = np.minimum(np.abs(x), 448.0)
+    e = np.maximum(np.floor(np.log2(np.maximum(a, 1e-30))), -6.0)
+    q = 2.0 ** (e - 3)
+    r = np.minimum(np.round(a / q) * q, 448.0)
+    return np.sign(x) * r
+
+
+def f32(x):
+    return np.asarray(x, np.float64).astype(np.float32).astype(np.float64)
+
+
+def fp8_model(nif, uv, scales):
+    uv = uv.astype(np.float32)
+    B = nif.B.astype(np.float64)
+    t = f32(B[:, 0][None] * uv[:, :1].astype(np.float64) + B[:, 1][None] * uv[:, 1:].astype(np.float64))
+    r = t - np.rint(t)
+    feat = f32(np.concatenate([np.sin(2 * np.pi * r), np.cos(2 * np.pi * r)], 1))
+    q = e4m3(f32(feat * 448.0))
+    s = [np.float32(v) for v in scales]
+    for l in range(3):
+        W = nif.W[l].astype(np.float32)
+        sw = (np.abs(W).max(1) / np.float32(448.0)).astype(np.float32)
+        W8 = e4m3(f32(W / sw[:, None]))
+        mul = f32((s[l] * sw / s[l + 1]).astype(np.float32))
+        add = f32((nif.b[l].astype(np.float32) / s[l + 1]).astype(np.float32))
+        acc = q @ W8.T
+        q = e4m3(np.maximum(f32(acc * mul + add), 0.0))
+    W = nif.W[3].astype(np.float32)
+    sw = (np.abs(W).max(1) / np.float32(448.0)).astype(np.float32)
+    W8 = e4m3(f32(W / sw[:, None]))
+    hm = f32((s[3] * sw).astype(np.float32))
+    y = f32((q @ W8.T) * hm + nif.b[3].astype(np.float64))
+    return np.exp(y @ nif.M.astype(np.float64).T)
+
+
+def _nif():
+    nif = I.nif_init(colour="yuv")
+    rng = np.random.default_rng(7)
+    for b in nif.b:
+        b[:] = rng.normal(0, 0.05, b.shape).astype(np.float32)
+    return nif
+
+
+@pytest.mark.parametrize("n", [1, 200, 128 * 152 * 4 * 2 + 33])
+def test_fp8_nif_matches_quantisation_model(pt, ctx, n):
+    nif = _nif()
+    g = pt.Nif(ctx, nif)
+    scales = g.fp8_scales()
+    assert abs(scales[0] - 1 / 448) < 1e-9 and np.all(scales > 0)
+    uv = I.uniform_uv(n, seed=n + 1)
+    got = g.eval(torch.from_numpy(uv).cuda(), precision="fp8").cpu().numpy().astype(np.float64)
+    ctx.check()
+    ref = fp8_model(nif, uv, scales)
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert np.all(np.isfinite(got))
+    # quantisation decisions taken on values within rounding of a tie may flip; almost all rows agree closely
+    assert np.median(rel) <= 1e-3 and np.mean(rel > 5e-2) <= 2e-3, (np.median(rel), np.mean(rel > 5e-2))
+
+
+def test_fp8_and_bf16_error_vs_oracle(pt, ctx):
+    nif = _nif()
+    g = pt.Nif(ctx, nif)
+    uv = I.uniform_uv(20000, seed=21)
+    ref, _ = O.Nif(nif).forward(uv.astype(np.float64))
+    out = {}
+    for prec in ("fp8", "bf16", "fp32"):
+        v = g.eval(torch.from_numpy(uv).cuda(), precision=prec).cpu().numpy().astype(np.float64)
+        out[prec] = float(np.sqrt(np.mean((np.log(v) - np.log(ref)) ** 2)))
+    ctx.check()
+    print({"log_rmse": out})
+    assert out["fp32"] < 1e-5 and out["bf16"] < out["fp8"] < 0.2
+
+
+def test_fp8_render_and_training_refresh(pt, ctx):
+    """FP8 renders stay close to FP32 renders; after training the FP8 image
+    is rebuilt from the new weights (scales follow the trained network)."""
+    sc = I.make_scene("C3")
+    nif = _nif()
+    s = pt.Scene(ctx, sc)
+    g = pt.Nif(ctx, nif)
+    cfg = I.RenderCfg(256, 256, 4, 6)
+    a = pt.render(ctx, s, g, cfg, "fp32").cpu().numpy().astype(np.float64)
+    b = pt.render(ctx, s, g, cfg, "fp8").cpu().numpy().astype(np.float64)
+    ctx.check()
+    rel = float(np.sqrt(((a - b) ** 2).sum() / (a ** 2).sum()))
+    print({"fp8_vs_fp32_render_rel_rmse": rel})
+    assert rel < 0.1
+    before = g.fp8_scales().copy()
+    g.train(torch.from_numpy(I.procedural_sky(256, 128)).cuda(), steps=20, batch=4096, lr=1e-2)
+    ctx.check()
+    after = g.fp8_scales()
+    assert not np.array_equal(before[1:], after[1:])
+    params = g.get_params()
+    trained = nif.copy()
+    p = 2 * nif.n_freq
+    for W, bb in zip(trained.W, trained.b):
+        W[:] = params[p:p + W.size].reshape(W.shape)
+        p += W.size
+        bb[:] = params[p:p + bb.size]
+        p += bb.size
+    uv = I.uniform_uv(3000, seed=2)
+    got = g.eval(torch.from_numpy(uv).cuda(), precision="fp8").cpu().numpy().astype(np.float64)
+    ref = fp8_model(trained, uv, after)
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert np.median(rel) <= 1e-3
