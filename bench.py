@@ -317,13 +317,14 @@ def bench_ours(args):
     clock = float(meas.get("sm_max_mhz", 2070.0))
     dom = max(("trace", "nif", "reduce"), key=lambda k: prof[k][0])
     big_scene = scene.info()["node_bytes"] > 128 * 1024 * 1024   # BVH larger than L2
-    if dom == "nif" and rprec == "bf16":
-        peak = float(meas.get("bf16_tflops_sustained", meas["bf16_tflops"]))
+    if dom == "nif" and rprec in ("bf16", "fp8"):
+        peak = float(meas.get("bf16_tflops_sustained", meas["bf16_tflops"])) * (2.0 if rprec == "fp8" else 1.0)
         achieved = evals * TC_FLOP_PER_EVAL / (nif_ms * 1e-3) / 1e12
-        roof = {"kernel": "k_nif_tc", "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+        roof = {"kernel": "k_nif_tc" if rprec == "bf16" else "k_nif_fp8", "bound": "tensor", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "per_unit": f"{TC_FLOP_PER_EVAL} tensor FLOP per NIF evaluation x {evals} evaluations per launch",
-                "peak_note": f"dense BF16, sustained ({which})"}
+                "peak_note": (f"dense BF16, sustained ({which})" if rprec == "bf16" else
+                              f"dense FP8 = sustained BF16 ({which}) x 2 (nominal 4.5 / 2.25 PFLOP/s)")}
     elif dom == "nif":
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock * 1e6 / 1e12
         achieved = evals * FLOP_PER_EVAL / (nif_ms * 1e-3) / 1e12
@@ -419,7 +420,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["C1", "C2", "C3", "C4"], default="C2")
-    ap.add_argument("--precision", choices=["bf16", "fp32"], default="bf16")
+    ap.add_argument("--precision", choices=["bf16", "fp32", "fp8"], default="bf16")
     ap.add_argument("--spp", type=int, default=None, help="override spp (small cases for profiler captures)")
     ap.add_argument("--cpu-s", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=4.0, help="seconds per reference-arm step")

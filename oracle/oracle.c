@@ -21,6 +21,9 @@
  *   NIF forward ........... pinned (B = 0, zero weights, relu(x) - relu(-x) = x wiring)
  *   NIF backward / Adam ... pinned (central finite differences, Adam closed-form steps)
  *   sky lookup ............ pinned (pixel centres, wrap/clamp, four-centre average)
+ *   radiance cache ........ pinned (zero weights, wiring closed forms, fixed-denominator
+ *                           finite differences, output-bias closed form, furnace suffix
+ *                           radiance and cached-render closed forms)
  */
 #include <math.h>
 #include <pthread.h>
@@ -983,4 +986,254 @@ OR_API int or_sample_bsdf(const OrScene* s, int mat, const double* d, const doub
     weight[0] = wt.x; weight[1] = wt.y; weight[2] = wt.z;
     if (!ok) { wi[0] = wi[1] = wi[2] = 0.0; weight[0] = weight[1] = weight[2] = 0.0; }
     return ok;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neural radiance cache (cited in Section 2.1, Mueller et al. 2021): an MLP */
+/* from (position, direction, normal) to outgoing radiance, queried where   */
+/* paths terminate early and trained online on the radiance of longer       */
+/* training paths.  Encoding: position normalised to the cache's box, then  */
+/* [sin(2^j pi p_a) (j < J), cos(2^j pi p_a) (j < J)] per axis a, then the   */
+/* direction and the normal (3 + 3).  Hidden ReLU layers, linear output.    */
+/* Flat parameters: per layer W (out x in), b (out).                        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int J, H, L, nl, in0;
+    int in[10], out[10];
+    double *W[10], *b[10];
+    double lo[3], hi[3];
+} OrCache;
+
+OR_API OrCache* or_cache_create(int J, int H, int L, const float* flat, const float* bounds /* lo3 hi3 */)
+{
+    if (L < 1 || L > 9) return NULL;
+    OrCache* c = (OrCache*)calloc(1, sizeof(OrCache));
+    c->J = J; c->H = H; c->L = L; c->nl = L + 1; c->in0 = 6 * J + 6;
+    const float* p = flat;
+    for (int l = 0; l < c->nl; ++l) {
+        c->in[l] = l == 0 ? c->in0 : H;
+        c->out[l] = l == c->nl - 1 ? 3 : H;
+        c->W[l] = (double*)malloc(sizeof(double) * c->in[l] * c->out[l]);
+        c->b[l] = (double*)malloc(sizeof(double) * c->out[l]);
+        for (int i = 0; i < c->in[l] * c->out[l]; ++i) c->W[l][i] = *p++;
+        for (int i = 0; i < c->out[l]; ++i) c->b[l][i] = *p++;
+    }
+    for (int a = 0; a < 3; ++a) { c->lo[a] = bounds[a]; c->hi[a] = bounds[3 + a]; }
+    return c;
+}
+
+OR_API void or_cache_destroy(OrCache* c)
+{
+    if (!c) return;
+    for (int l = 0; l < c->nl; ++l) { free(c->W[l]); free(c->b[l]); }
+    free(c);
+}
+
+OR_API int64_t or_cache_n_params(const OrCache* c)
+{
+    int64_t n = 0;
+    for (int l = 0; l < c->nl; ++l) n += (int64_t)c->in[l] * c->out[l] + c->out[l];
+    return n;
+}
+
+OR_API void or_cache_get_params(const OrCache* c, double* out)
+{
+    double* p = out;
+    for (int l = 0; l < c->nl; ++l) {
+        memcpy(p, c->W[l], sizeof(double) * c->in[l] * c->out[l]); p += c->in[l] * c->out[l];
+        memcpy(p, c->b[l], sizeof(double) * c->out[l]); p += c->out[l];
+    }
+}
+OR_API void or_cache_set_params(OrCache* c, const double* in)
+{
+    const double* p = in;
+    for (int l = 0; l < c->nl; ++l) {
+        memcpy(c->W[l], p, sizeof(double) * c->in[l] * c->out[l]); p += c->in[l] * c->out[l];
+        memcpy(c->b[l], p, sizeof(double) * c->out[l]); p += c->out[l];
+    }
+}
+
+/* query = (x, direction, normal) -> encoding e [in0] */
+static void cache_encode(const OrCache* c, const double* q, double* e)
+{
+    int k = 0;
+    for (int a = 0; a < 3; ++a) {
+        double p = (q[a] - c->lo[a]) / (c->hi[a] - c->lo[a]);
+        for (int j = 0; j < c->J; ++j) e[k + j] = sin(ldexp(1.0, j) * OR_PI * p);
+        for (int j = 0; j < c->J; ++j) e[k + c->J + j] = cos(ldexp(1.0, j) * OR_PI * p);
+        k += 2 * c->J;
+    }
+    for (int i = 0; i < 6; ++i) e[k + i] = q[3 + i];
+}
+
+static void cache_forward_one(const OrCache* c, const double* q, double* enc, double* hid, double* pre, double y[3])
+{
+    cache_encode(c, q, enc);
+    const double* x = enc;
+    for (int l = 0; l < c->L; ++l) {
+        double* h = hid + (size_t)l * c->H;
+        for (int j = 0; j < c->H; ++j) {
+            double acc = c->b[l][j];
+            for (int k = 0; k < c->in[l]; ++k) acc += c->W[l][(size_t)j * c->in[l] + k] * x[k];
+            if (pre) pre[(size_t)l * c->H + j] = acc;
+            h[j] = acc > 0.0 ? acc : 0.0;
+        }
+        x = h;
+    }
+    int lo = c->nl - 1;
+    for (int j = 0; j < 3; ++j) {
+        double acc = c->b[lo][j];
+        for (int k = 0; k < c->H; ++k) acc += c->W[lo][(size_t)j * c->H + k] * x[k];
+        y[j] = acc;
+    }
+}
+
+OR_API void or_cache_forward(const OrCache* c, int64_t n, const double* q /* n x 9 */, double* out /* n x 3 */)
+{
+    double* enc = (double*)malloc(sizeof(double) * c->in0);
+    double* hid = (double*)malloc(sizeof(double) * c->L * c->H);
+    for (int64_t i = 0; i < n; ++i) cache_forward_one(c, q + 9 * i, enc, hid, NULL, out + 3 * i);
+    free(enc); free(hid);
+}
+
+/* Relative L2 loss (Mueller et al. 2021): mean over samples and channels of
+   (y - t)^2 / (sg(y)^2 + 0.01), where sg() holds the prediction constant in
+   the gradient.  denom (optional, n x 3) replaces sg(y)^2 + 0.01 by fixed
+   values, which makes the loss an ordinary function of the weights.  mask
+   (optional, n) excludes samples; the mean is over all n x 3 entries. */
+OR_API double or_cache_loss_grad(const OrCache* c, int64_t n, const double* q, const double* target,
+                                 const double* denom, const int32_t* mask, double* grad)
+{
+    int H = c->H, L = c->L;
+    int64_t np = or_cache_n_params(c);
+    memset(grad, 0, sizeof(double) * (size_t)np);
+    double* gW[10]; double* gb[10];
+    double* p = grad;
+    for (int l = 0; l < c->nl; ++l) { gW[l] = p; p += c->in[l] * c->out[l]; gb[l] = p; p += c->out[l]; }
+    double* enc = (double*)malloc(sizeof(double) * c->in0);
+    double* hid = (double*)malloc(sizeof(double) * L * H);
+    double* pre = (double*)malloc(sizeof(double) * L * H);
+    double* dh = (double*)malloc(sizeof(double) * H);
+    double* dprev = (double*)malloc(sizeof(double) * H);
+    double loss = 0.0, scale = 1.0 / (3.0 * (double)n);
+    for (int64_t s = 0; s < n; ++s) {
+        if (mask && !mask[s]) continue;
+        double y[3], dy[3];
+        cache_forward_one(c, q + 9 * s, enc, hid, pre, y);
+        for (int ch = 0; ch < 3; ++ch) {
+            double d = denom ? denom[3 * s + ch] : y[ch] * y[ch] + 0.01;
+            double r = y[ch] - target[3 * s + ch];
+            loss += r * r / d * scale;
+            dy[ch] = 2.0 * r / d * scale;
+        }
+        int lo = c->nl - 1;
+        const double* xin = hid + (size_t)(L - 1) * H;
+        for (int j = 0; j < 3; ++j) {
+            gb[lo][j] += dy[j];
+            for (int k = 0; k < H; ++k) gW[lo][(size_t)j * H + k] += dy[j] * xin[k];
+        }
+        for (int k = 0; k < H; ++k) {
+            double acc = 0.0;
+            for (int j = 0; j < 3; ++j) acc += c->W[lo][(size_t)j * H + k] * dy[j];
+            dh[k] = acc;
+        }
+        for (int l = L - 1; l >= 0; --l) {
+            const double* pl = pre + (size_t)l * H;
+            for (int j = 0; j < H; ++j) dh[j] = pl[j] > 0.0 ? dh[j] : 0.0;
+            const double* x = (l == 0) ? enc : hid + (size_t)(l - 1) * H;
+            int nin = c->in[l];
+            for (int j = 0; j < H; ++j) {
+                gb[l][j] += dh[j];
+                for (int k = 0; k < nin; ++k) gW[l][(size_t)j * nin + k] += dh[j] * x[k];
+            }
+            if (l > 0) {
+                for (int k = 0; k < H; ++k) {
+                    double acc = 0.0;
+                    for (int j = 0; j < H; ++j) acc += c->W[l][(size_t)j * nin + k] * dh[j];
+                    dprev[k] = acc;
+                }
+                memcpy(dh, dprev, sizeof(double) * H);
+            }
+        }
+    }
+    free(enc); free(hid); free(pre); free(dh); free(dprev);
+    return loss;
+}
+
+/* Path with the cache: like trace_path, but a hit at vertex cache_vertex
+   adds tp * max(cache(x, -d, n), 0) and ends the path (n faces the incoming
+   ray).  Records at rec_vertex (rec, 16 doubles: x, -d, n, tp, gathered
+   radiance before the vertex, valid) when rec is given. */
+static V3 trace_path_ex(const RenderJob* j, int64_t pix, int64_t smp, int64_t* ids, const OrCache* cache,
+                        int cache_vertex, int rec_vertex, double* rec)
+{
+    const OrScene* s = j->s;
+    uint32_t w[4];
+    philox_words(j->seed, 0u, (uint32_t)pix, (uint32_t)smp, 0u, 0u, w);
+    V3 o = v3(j->cam.eye[0], j->cam.eye[1], j->cam.eye[2]);
+    V3 d = camera_dir(&j->cam, j->W, j->H, (int)(pix % j->W), (int)(pix / j->W), u01(w[0]), u01(w[1]));
+    V3 tp = v3(1, 1, 1), L = v3(0, 0, 0);
+    if (ids) for (int k = 0; k < j->depth; ++k) ids[k] = -2;
+    if (rec) for (int k = 0; k < 16; ++k) rec[k] = 0.0;
+    for (int k = 1; k <= j->depth; ++k) {
+        double t;
+        int64_t id;
+        closest_hit(s, o, d, 0, &t, &id);
+        if (ids) ids[k - 1] = id;
+        if (id < 0) {
+            L = add(L, hadamard(tp, env_radiance(j, d)));
+            break;
+        }
+        V3 p = add(o, mul(d, t));
+        V3 ng = geometric_normal(s, id, p);
+        V3 nf = dot(ng, d) < 0.0 ? ng : mul(ng, -1.0);
+        if (rec && k == rec_vertex) {
+            double v[16] = {p.x, p.y, p.z, -d.x, -d.y, -d.z, nf.x, nf.y, nf.z, tp.x, tp.y, tp.z, L.x, L.y, L.z, 1.0};
+            memcpy(rec, v, sizeof v);
+        }
+        if (cache && k == cache_vertex) {
+            double q[9] = {p.x, p.y, p.z, -d.x, -d.y, -d.z, nf.x, nf.y, nf.z}, y[3];
+            or_cache_forward(cache, 1, q, y);
+            L = add(L, hadamard(tp, v3(maxd(y[0], 0.0), maxd(y[1], 0.0), maxd(y[2], 0.0))));
+            break;
+        }
+        int mat = prim_material(s, id);
+        const double* m = s->mat + 8 * mat;
+        L = add(L, hadamard(tp, v3(m[5], m[6], m[7])));
+        if (k == j->depth) break;
+        philox_words(j->seed, 0u, (uint32_t)pix, (uint32_t)smp, (uint32_t)k, 0u, w);
+        V3 wi, wt;
+        if (!sample_bsdf(s, mat, d, ng, u01(w[0]), u01(w[1]), u01(w[2]), &wi, &wt)) break;
+        tp = hadamard(tp, wt);
+        if (j->rr && k >= j->rr_start) {
+            double qq = mind(1.0, maxd(tp.x, maxd(tp.y, tp.z)));
+            if (u01(w[3]) < qq) tp = mul(tp, 1.0 / qq);
+            else break;
+        }
+        double eps = 1e-4 * maxd(1.0, maxd(fabs(p.x), maxd(fabs(p.y), fabs(p.z))));
+        V3 off = dot(wi, ng) > 0.0 ? ng : mul(ng, -1.0);
+        o = add(p, mul(off, eps));
+        d = wi;
+    }
+    return L;
+}
+
+/* Paths (pixel[i], sample[i]) with an optional cache at cache_vertex (0 =
+   none) and vertex records at rec_vertex (0 = none): L_out [n][3], rec_out
+   [n][16] (nullable), ids_out [n][depth] (nullable).  Single-threaded. */
+OR_API void or_trace_paths(const OrScene* s, const OrNif* nif, const float* env_const, const float* cam, int W, int H,
+                           int depth, uint32_t seed, int64_t n, const int64_t* pixels, const int64_t* samples,
+                           const OrCache* cache, int cache_vertex, int rec_vertex, double* L_out, double* rec_out,
+                           int64_t* ids_out)
+{
+    RenderJob j;
+    memset(&j, 0, sizeof(j));
+    j.s = s; j.nif = nif; j.env_const = env_const;
+    make_camera(cam, W, H, &j.cam);
+    j.W = W; j.H = H; j.spp = 1; j.depth = depth; j.seed = seed;
+    for (int64_t i = 0; i < n; ++i) {
+        V3 L = trace_path_ex(&j, pixels[i], samples[i], ids_out ? ids_out + i * depth : NULL, cache, cache_vertex,
+                             rec_vertex, rec_out ? rec_out + 16 * i : NULL);
+        L_out[3 * i] = L.x; L_out[3 * i + 1] = L.y; L_out[3 * i + 2] = L.z;
+    }
 }

@@ -241,3 +241,96 @@ def sample_bsdf(oscene: Scene, mat: int, d, ng, u1: float, u2: float, ul: float)
     wt = np.zeros(3)
     ok = lib().or_sample_bsdf(oscene.h, mat, _ptr(d), _ptr(ng), u1, u2, ul, _ptr(wi), _ptr(wt))
     return bool(ok), wi, wt
+
+
+# ----------------------------------------------------------------------------
+# radiance cache
+def _cache_sigs(L):
+    if getattr(L, "_cache_sigs", False):
+        return
+    L.or_cache_create.argtypes = [C.c_int, C.c_int, C.c_int, P, P]
+    L.or_cache_create.restype = P
+    L.or_cache_destroy.argtypes = [P]
+    L.or_cache_n_params.argtypes = [P]
+    L.or_cache_n_params.restype = I64
+    L.or_cache_get_params.argtypes = [P, P]
+    L.or_cache_set_params.argtypes = [P, P]
+    L.or_cache_forward.argtypes = [P, I64, P, P]
+    L.or_cache_loss_grad.argtypes = [P, I64, P, P, P, P, P]
+    L.or_cache_loss_grad.restype = C.c_double
+    L.or_trace_paths.argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_int, U32, I64, P, P, P, C.c_int, C.c_int, P, P, P]
+    L._cache_sigs = True
+
+
+def cache_flat(cache) -> np.ndarray:
+    parts = []
+    for W, b in zip(cache.W, cache.b):
+        parts += [W.ravel(), b.ravel()]
+    return np.ascontiguousarray(np.concatenate(parts).astype(np.float32))
+
+
+class Cache:
+    """Oracle copy of a radiance cache (inputs.CacheNet)."""
+
+    def __init__(self, cache):
+        L = lib()
+        _cache_sigs(L)
+        self.src = cache
+        self.flat = cache_flat(cache)
+        self.bounds = np.ascontiguousarray(np.concatenate([cache.lo, cache.hi]).astype(np.float32))
+        self.h = L.or_cache_create(cache.n_freq, cache.hidden, cache.n_hidden_layers, _ptr(self.flat), _ptr(self.bounds))
+        if not self.h:
+            raise ValueError("unsupported cache shape")
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.or_cache_destroy(self.h)
+            self.h = None
+
+    @property
+    def n_params(self) -> int:
+        return int(lib().or_cache_n_params(self.h))
+
+    def get_params(self) -> np.ndarray:
+        w = np.zeros(self.n_params)
+        lib().or_cache_get_params(self.h, _ptr(w))
+        return w
+
+    def set_params(self, w) -> None:
+        w = np.ascontiguousarray(w, np.float64)
+        lib().or_cache_set_params(self.h, _ptr(w))
+
+    def forward(self, q: np.ndarray) -> np.ndarray:
+        q = np.ascontiguousarray(q, np.float64).reshape(-1, 9)
+        out = np.zeros((len(q), 3))
+        lib().or_cache_forward(self.h, len(q), _ptr(q), _ptr(out))
+        return out
+
+    def loss_grad(self, q, target, denom=None, mask=None):
+        q = np.ascontiguousarray(q, np.float64).reshape(-1, 9)
+        target = np.ascontiguousarray(target, np.float64).reshape(-1, 3)
+        denom = None if denom is None else np.ascontiguousarray(denom, np.float64).reshape(-1, 3)
+        mask = None if mask is None else np.ascontiguousarray(mask, np.int32)
+        g = np.zeros(self.n_params)
+        loss = lib().or_cache_loss_grad(self.h, len(q), _ptr(q), _ptr(target), _ptr(denom), _ptr(mask), _ptr(g))
+        return float(loss), g
+
+
+def trace_paths(oscene: Scene, cam, W: int, H: int, depth: int, seed: int, pixels, samples, nif: Optional[Nif] = None,
+                cache: Optional[Cache] = None, cache_vertex: int = 0, rec_vertex: int = 0, want_ids: bool = False):
+    """Individual paths (pixel, sample): radiance [n,3], vertex records [n,16] (x, -d, n, tp, L before, valid)."""
+    L = lib()
+    _cache_sigs(L)
+    sc = oscene.src
+    pixels = np.ascontiguousarray(pixels, np.int64)
+    samples = np.ascontiguousarray(samples, np.int64)
+    n = len(pixels)
+    env = None if sc.env_const is None else np.ascontiguousarray(sc.env_const, np.float32)
+    ca = camera_array(cam)
+    Lo = np.zeros((n, 3))
+    rec = np.zeros((n, 16)) if rec_vertex else None
+    ids = np.zeros((n, depth), np.int64) if want_ids else None
+    L.or_trace_paths(oscene.h, nif.h if nif is not None else None, _ptr(env), _ptr(ca), W, H, depth, seed, n,
+                     _ptr(pixels), _ptr(samples), cache.h if cache is not None else None, int(cache_vertex),
+                     int(rec_vertex), _ptr(Lo), _ptr(rec), _ptr(ids))
+    return Lo, rec, ids

@@ -389,6 +389,71 @@ def procedural_sky(width: int = 2048, height: int = 1024, seed: int = 0) -> np.n
     return np.ascontiguousarray(sky.astype(np.float32))
 
 
+TAG_CACHE_INIT = 9
+
+
+@dataclasses.dataclass
+class CacheNet:
+    """Neural radiance cache parameters (float32, PyTorch Linear layout):
+    J frequencies per position axis, hidden width H, L hidden layers, and
+    the box [lo, hi] that positions are normalised to."""
+    n_freq: int
+    W: List[np.ndarray]
+    b: List[np.ndarray]
+    lo: np.ndarray
+    hi: np.ndarray
+
+    @property
+    def hidden(self) -> int:
+        return int(self.W[0].shape[0])
+
+    @property
+    def n_hidden_layers(self) -> int:
+        return len(self.W) - 1
+
+    @property
+    def in_dim(self) -> int:
+        return 6 * self.n_freq + 6
+
+    def copy(self) -> "CacheNet":
+        return CacheNet(self.n_freq, [w.copy() for w in self.W], [x.copy() for x in self.b], self.lo.copy(),
+                        self.hi.copy())
+
+
+def scene_bounds(scene: Scene) -> Tuple[np.ndarray, np.ndarray]:
+    """Axis-aligned float32 bounds of every primitive of a scene."""
+    lo = np.full(3, np.inf, np.float32)
+    hi = np.full(3, -np.inf, np.float32)
+    if len(scene.sphere):
+        lo = np.minimum(lo, (scene.sphere[:, :3] - scene.sphere[:, 3:]).min(0))
+        hi = np.maximum(hi, (scene.sphere[:, :3] + scene.sphere[:, 3:]).max(0))
+    if len(scene.tri):
+        used = scene.vert[np.unique(scene.tri)]
+        lo = np.minimum(lo, used.min(0))
+        hi = np.maximum(hi, used.max(0))
+    for i in range(len(scene.quad)):
+        a = scene.quad_axis[i]
+        u, v = (a + 1) % 3, (a + 2) % 3
+        p = scene.quad[i]
+        qlo = np.zeros(3, np.float32)
+        qhi = np.zeros(3, np.float32)
+        qlo[a] = qhi[a] = p[0]
+        qlo[u], qhi[u], qlo[v], qhi[v] = p[1], p[2], p[3], p[4]
+        lo, hi = np.minimum(lo, qlo), np.maximum(hi, qhi)
+    return lo.astype(np.float32), hi.astype(np.float32)
+
+
+def cache_init(lo, hi, n_freq: int = 12, hidden: int = 64, n_hidden_layers: int = 5, seed: int = 0) -> CacheNet:
+    """Random-init radiance cache: W ~ N(0, 1/fan_in), zero biases."""
+    rng = _rng(seed, TAG_CACHE_INIT)
+    dims = [6 * n_freq + 6] + [hidden] * n_hidden_layers + [3]
+    W, b = [], []
+    for i in range(len(dims) - 1):
+        W.append(rng.normal(0.0, 1.0 / math.sqrt(dims[i]), size=(dims[i + 1], dims[i])).astype(np.float32))
+        b.append(np.zeros((dims[i + 1],), np.float32))
+    return CacheNet(n_freq, W, b, np.asarray(lo, np.float32), np.asarray(hi, np.float32))
+
+
 # ----------------------------------------------------------------------------
 # The five workload configurations
 # ----------------------------------------------------------------------------
