@@ -72,6 +72,7 @@ typedef enum pt_precision {
 typedef struct pt_ctx pt_ctx;
 typedef struct pt_scene pt_scene;
 typedef struct pt_nif pt_nif;
+typedef struct pt_cache pt_cache;
 
 /* ------------------------------------------------------------------------ */
 /* Context                                                                   */
@@ -258,14 +259,16 @@ PT_API pt_status pt_last_render_work(pt_ctx* ctx, int64_t* work, int32_t n);
 /* Kernel timing.  While enabled, the library records a CUDA event pair on
    the launching stream around each of its kernel launches and accumulates
    the device time per kernel kind: 0 trace/shade step, 1 NIF evaluation,
-   2 sample reduction, 3 other (training and utilities).  pt_profile_read
+   2 sample reduction, 3 other (training and utilities), 4 radiance-cache
+   queries.  pt_profile_read
    synchronises the device, writes up to n kinds of total milliseconds and
    launch counts (either pointer may be NULL) and resets the totals. */
 #define PT_KIND_TRACE 0
 #define PT_KIND_NIF 1
 #define PT_KIND_REDUCE 2
 #define PT_KIND_OTHER 3
-#define PT_N_KINDS 4
+#define PT_KIND_CACHE 4    /* radiance-cache queries */
+#define PT_N_KINDS 5
 PT_API pt_status pt_profile_enable(pt_ctx* ctx, int32_t enable);
 PT_API pt_status pt_profile_read(pt_ctx* ctx, double* ms, int64_t* launches, int32_t n);
 
@@ -290,6 +293,79 @@ PT_API pt_status pt_primary_rays(pt_ctx* ctx, const pt_scene* scene, const pt_re
    (-1 on a miss). */
 PT_API pt_status pt_trace_rays(pt_ctx* ctx, const pt_scene* scene, int64_t n, const float* d_org, const float* d_dir,
                                float* d_t, int32_t* d_prim, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Neural radiance cache (Mueller et al. 2021; Section 2.1 cites it as the  */
+/* way to end paths early).  A path that hits at the cache vertex stops     */
+/* there and takes tp * max(cache(x, wo, n), 0) as the rest of its          */
+/* radiance.  Inputs: position normalised to the box [lo, hi] and encoded   */
+/* as sin/cos(2^j pi p) for j < n_freq per axis, then wo (unit vector to    */
+/* the previous vertex) and n (geometric normal facing wo), both raw.       */
+/* Network: n_hidden_layers x FC-hidden ReLU, then FC-3 (linear).  FP32.    */
+/* ------------------------------------------------------------------------ */
+typedef struct pt_cache_desc {
+    int32_t n_freq;            /* J: frequencies per axis (1..15) */
+    int32_t hidden;            /* must be 64 */
+    int32_t n_hidden_layers;   /* L: 1..7 */
+    const float* params;       /* host: W0 [hidden][6J+6], b0, W1 [hidden][hidden], b1, ..., WL [3][hidden], bL
+                                  (PyTorch Linear layout, layers in order) */
+    float lo[3], hi[3];        /* position box (hi > lo per axis) */
+} pt_cache_desc;
+
+/* Create a cache on the context's device; parameters are copied. */
+PT_API pt_status pt_create_cache(pt_ctx* ctx, const pt_cache_desc* desc, pt_cache** out);
+PT_API void pt_destroy_cache(pt_cache* cache);
+PT_API int64_t pt_cache_param_count(const pt_cache* cache);
+/* host copy of / replacement for the flat FP32 parameters (pt_cache_desc layout); set_params resets Adam */
+PT_API pt_status pt_cache_get_params(pt_ctx* ctx, const pt_cache* cache, float* params);
+PT_API pt_status pt_cache_set_params(pt_ctx* ctx, pt_cache* cache, const float* params, void* stream);
+
+/* Raw network outputs (no clamp) for d_q [n][9] = x, wo, n -> d_out [n][3]. */
+PT_API pt_status pt_cache_eval(pt_ctx* ctx, const pt_cache* cache, int64_t n, const float* d_q, float* d_out,
+                               void* stream);
+
+/* Relative L2 loss (y - t)^2 / (sg(y)^2 + 0.01), sg() holding the
+   prediction constant in the gradient, averaged over all n x 3 entries;
+   rows with d_mask[i] == 0 (d_mask nullable) contribute zero.  d_q [n][9],
+   d_target [n][3] -> d_grad (nullable, flat layout) and *d_loss (nullable
+   device double).  Nothing is updated. */
+PT_API pt_status pt_cache_loss_grad(pt_ctx* ctx, pt_cache* cache, int64_t n, const float* d_q, const float* d_target,
+                                    const int32_t* d_mask, float* d_grad, double* d_loss, void* stream);
+
+typedef struct pt_cache_train_cfg {
+    int32_t width, height;     /* image whose pixels the training paths start from */
+    int32_t n_train;           /* training paths per frame (2^16) */
+    int32_t max_depth;         /* their depth (plain path tracing, no cache) */
+    int32_t rec_vertex;        /* the vertex whose suffix radiance is the target (the cache vertex) */
+    uint32_t seed;             /* Philox key word 0 */
+    uint32_t frame;            /* frame index */
+    int32_t precision;         /* NIF precision at the training paths' escapes */
+    float lr, beta1, beta2, eps;  /* Adam */
+} pt_cache_train_cfg;
+
+/* One online training step of a frame.  Pixel i of the n_train training
+   paths is word 0 of Philox (key (seed, 2), counter (i, frame, 0, 0)) modulo
+   width*height; path i is that pixel's render path with sample index
+   2^30 + frame (key (seed, 0); renders whose sample indices stay below 2^30
+   never share a stream with it), traced to max_depth without the cache.
+   A path that hits at rec_vertex gives the sample (x, wo, n) -> (L_path -
+   L_before) / tp, the radiance it gathered from that vertex on divided by
+   the throughput reaching it; other paths are masked out.  Then one Adam
+   step on the relative L2 loss of pt_cache_loss_grad.  d_loss (nullable
+   device float) receives the loss.  Adam's moments and step count persist
+   in the cache. */
+PT_API pt_status pt_train_cache(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, pt_cache* cache,
+                                const pt_cache_train_cfg* cfg, float* d_loss, void* stream);
+
+/* pt_render_pixels with a radiance cache at vertex cache_vertex (cache and
+   cache_vertex >= 2 together, or NULL and 0) and, when rec_vertex > 0,
+   vertex records d_rec [spp][n_pix][16] of each path at rec_vertex: x[3],
+   wo[3], n[3], throughput[3], radiance gathered before the vertex[3], valid
+   (1.0 when the path hit there, else 0.0). */
+PT_API pt_status pt_render_cached(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, const pt_cache* cache,
+                                  int32_t cache_vertex, int32_t rec_vertex, const pt_render_cfg* cfg, int64_t n_pix,
+                                  const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb, float* d_rec,
+                                  int32_t* d_hit_ids, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Rendering without device allocation.  The paper has no counterpart: this */

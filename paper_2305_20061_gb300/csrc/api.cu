@@ -27,6 +27,8 @@ struct pt_ctx {
     float* slot_L = nullptr;
     uint32_t* counters = nullptr;          // [kCounters]
     unsigned long long* stats = nullptr;   // [kMaxDepth + 1]
+    float* cache_rows = nullptr;           // radiance-cache query rows [cache_cap][16]
+    uint32_t cache_cap = 0;
     int last_depth = 0;
     // kernel timing (pt_profile_enable)
     bool prof_on = false;
@@ -65,11 +67,36 @@ struct pt_nif {
     double* d_loss = nullptr;
 };
 
+struct pt_cache {
+    pt_ctx* ctx = nullptr;
+    int32_t J = 0, H = 0, L = 0, in0 = 0;
+    int64_t n_params = 0;
+    float* d_params = nullptr;      // flat FP32 weights (pt_cache_desc layout)
+    CacheBox box = {};
+    // online training state
+    float* d_grad = nullptr;
+    float* d_m = nullptr;
+    float* d_v = nullptr;
+    int64_t adam_t = 0;
+    int64_t work_cap = 0;
+    void* d_work = nullptr;
+    TrainWork work = {};
+    int64_t train_cap = 0;          // training paths the buffers below hold
+    void* d_train = nullptr;        // one allocation: pixels, records, radiance, targets, mask
+    int64_t* d_pixels = nullptr;
+    float* d_rec = nullptr;         // [n][16]
+    float* d_Lpath = nullptr;       // [n][3]
+    float* d_target = nullptr;      // [n][3]
+    int32_t* d_mask = nullptr;      // [n]
+    double* d_loss = nullptr;
+};
+
 namespace {
 
 constexpr int kMaxDepth = 64;
 constexpr int kCounters = kMaxDepth + 8;
 constexpr int kEscCounter = kMaxDepth + 2;
+constexpr int kCacheCounter = kMaxDepth + 3;
 constexpr int kStats = kMaxDepth + 1 + 4;     // rays per vertex, NIF evaluations, traversal work [4]
 constexpr int kWorkBase = kMaxDepth + 1;
 
@@ -107,6 +134,8 @@ void free_scratch(pt_ctx* ctx)
     cudaFree(ctx->esc); ctx->esc = nullptr;
     cudaFree(ctx->slot_L); ctx->slot_L = nullptr;
     ctx->chunk_cap = 0;
+    cudaFree(ctx->cache_rows); ctx->cache_rows = nullptr;
+    ctx->cache_cap = 0;
 }
 
 pt_status ensure_scratch(pt_ctx* ctx, uint32_t chunk)
@@ -588,6 +617,7 @@ TrainNet make_train_net(pt_nif* nf)
 {
     TrainNet t = {};
     t.F = nf->F; t.H = nf->H; t.L = nf->L;
+    t.in0 = 2 * nf->F;
     const float* p = nf->d_params;
     float* g = nf->d_grad;
     t.B = p;
@@ -732,12 +762,251 @@ PT_API pt_status pt_nif_set_params(pt_ctx* ctx, pt_nif* nf, const float* params,
 }
 
 // ---------------------------------------------------------------------------
-PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
-                                  int64_t n_pix, const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb,
-                                  int32_t* d_hit_ids, void* stream)
+// Neural radiance cache (Mueller et al. 2021, cited in Section 2.1)
+static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
+                             uint32_t first_sample, const pt_cache* cache, int cache_vertex, int rec_vertex, float* d_rec,
+                             int64_t n_pix, const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb,
+                             int32_t* d_hit_ids, cudaStream_t s);
+namespace {
+
+TrainNet make_cache_net(pt_cache* c)
 {
-    pt_status st = check_cfg(ctx, sc, nf, cfg);
+    TrainNet t = {};
+    t.F = 0; t.H = c->H; t.L = c->L;
+    t.in0 = c->in0;
+    const float* p = c->d_params;
+    float* g = c->d_grad;
+    for (int l = 0; l <= c->L; ++l) {
+        const int in = l == 0 ? c->in0 : c->H, o = l == c->L ? 3 : c->H;
+        t.W[l] = p; t.gW[l] = g;
+        p += (size_t)in * o; g += (size_t)in * o;
+        t.b[l] = p; t.gb[l] = g;
+        p += o; g += o;
+    }
+    return t;
+}
+
+pt_status ensure_cache_train(pt_ctx* ctx, pt_cache* c, int64_t B)
+{
+    if (!c->d_grad) {
+        if (cudaMalloc((void**)&c->d_grad, c->n_params * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&c->d_m, c->n_params * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&c->d_v, c->n_params * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&c->d_loss, sizeof(double)) != cudaSuccess)
+            return fail(ctx, PT_ENOMEM, "cache training state allocation failed");
+        if (cudaMemset(c->d_m, 0, c->n_params * sizeof(float)) != cudaSuccess ||
+            cudaMemset(c->d_v, 0, c->n_params * sizeof(float)) != cudaSuccess)
+            return fail(ctx, PT_ECUDA, "cache training state initialisation failed");
+    }
+    if (c->work_cap >= B) return PT_OK;
+    cudaFree(c->d_work);
+    c->d_work = nullptr;
+    c->work_cap = 0;
+    const int G = ctx->sm_count;
+    const size_t rows = (size_t)B * 128;
+    const size_t bytes = (size_t)(c->L + 1 + 2) * rows * sizeof(float) + (size_t)G * (128 * 128 + 128) * sizeof(float) +
+                         (size_t)G * sizeof(double) + 4096;
+    if (cudaMalloc(&c->d_work, bytes) != cudaSuccess) return fail(ctx, PT_ENOMEM, "cache work buffers allocation failed");
+    char* w = static_cast<char*>(c->d_work);
+    c->work = TrainWork{};
+    c->work.n_blocks = G;
+    for (int l = 0; l <= c->L; ++l) { c->work.X[l] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
+    for (int i = 0; i < 2; ++i) { c->work.dX[i] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
+    c->work.partial = reinterpret_cast<float*>(w);
+    w += (size_t)G * (128 * 128 + 128) * sizeof(float);
+    c->work.loss_partial = reinterpret_cast<double*>(w);
+    c->work_cap = B;
+    return PT_OK;
+}
+
+pt_status ensure_cache_paths(pt_ctx* ctx, pt_cache* c, int64_t n)
+{
+    if (c->train_cap >= n) return PT_OK;
+    cudaFree(c->d_train);
+    c->d_train = nullptr;
+    c->train_cap = 0;
+    const size_t bytes = (size_t)n * (8 + 16 * 4 + 3 * 4 + 3 * 4 + 4) + 1024;
+    if (cudaMalloc(&c->d_train, bytes) != cudaSuccess) return fail(ctx, PT_ENOMEM, "cache training paths allocation failed");
+    char* w = static_cast<char*>(c->d_train);
+    c->d_pixels = reinterpret_cast<int64_t*>(w); w += (size_t)n * 8;
+    c->d_rec = reinterpret_cast<float*>(w); w += (size_t)n * 64;
+    c->d_Lpath = reinterpret_cast<float*>(w); w += (size_t)n * 12;
+    c->d_target = reinterpret_cast<float*>(w); w += (size_t)n * 12;
+    c->d_mask = reinterpret_cast<int32_t*>(w);
+    c->train_cap = n;
+    return PT_OK;
+}
+
+bool adam_cfg_ok(float lr, float b1, float b2, float eps)
+{
+    return lr > 0.f && b1 >= 0.f && b1 < 1.f && b2 >= 0.f && b2 < 1.f && eps > 0.f;
+}
+
+}  // namespace
+
+PT_API pt_status pt_create_cache(pt_ctx* ctx, const pt_cache_desc* d, pt_cache** out)
+{
+    if (!ctx || !d || !out || !d->params) return fail(ctx, PT_EINVAL, "null argument");
+    *out = nullptr;
+    if (d->hidden != 64) return fail(ctx, PT_EUNSUPPORTED, "the cache kernels need hidden = 64");
+    if (d->n_freq < 1 || d->n_freq > 15 || d->n_hidden_layers < 1 || d->n_hidden_layers > 7)
+        return fail(ctx, PT_EINVAL, "n_freq must be in [1, 15] and n_hidden_layers in [1, 7]");
+    const int J = d->n_freq, H = d->hidden, L = d->n_hidden_layers, in0 = 6 * J + 6;
+    if (cache_eval_smem_bytes(in0, L) > 227 * 1024) return fail(ctx, PT_EUNSUPPORTED, "cache too large for shared memory");
+    const int64_t np = (int64_t)in0 * H + H + (int64_t)(L - 1) * (H * H + H) + 3 * H + 3;
+    if (!finite3(d->params, np)) return fail(ctx, PT_EINVAL, "non-finite cache parameters");
+    CacheBox box = {};
+    box.J = J;
+    for (int a = 0; a < 3; ++a) {
+        if (!(std::isfinite(d->lo[a]) && std::isfinite(d->hi[a]) && d->hi[a] > d->lo[a]))
+            return fail(ctx, PT_EINVAL, "cache box needs finite hi > lo");
+        const double ext = (double)d->hi[a] - (double)d->lo[a];
+        box.lo[a] = d->lo[a];
+        box.eh[a] = (float)ext;
+        box.el[a] = (float)(ext - (double)box.eh[a]);
+    }
+    PT_CUDA(cudaSetDevice(ctx->device));
+    pt_cache* c = new pt_cache;
+    c->ctx = ctx;
+    c->J = J; c->H = H; c->L = L; c->in0 = in0;
+    c->n_params = np;
+    c->box = box;
+    if (cudaMalloc((void**)&c->d_params, np * sizeof(float)) != cudaSuccess ||
+        cudaMemcpy(c->d_params, d->params, np * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+        pt_destroy_cache(c);
+        return fail(ctx, PT_ENOMEM, "cache parameter upload failed");
+    }
+    *out = c;
+    return PT_OK;
+}
+
+PT_API void pt_destroy_cache(pt_cache* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->ctx->device);
+    cudaFree(c->d_params);
+    cudaFree(c->d_grad);
+    cudaFree(c->d_m);
+    cudaFree(c->d_v);
+    cudaFree(c->d_work);
+    cudaFree(c->d_train);
+    cudaFree(c->d_loss);
+    delete c;
+}
+
+PT_API int64_t pt_cache_param_count(const pt_cache* c) { return c ? c->n_params : 0; }
+
+PT_API pt_status pt_cache_get_params(pt_ctx* ctx, const pt_cache* c, float* params)
+{
+    if (!ctx || !c || !params) return fail(ctx, PT_EINVAL, "null argument");
+    PT_CUDA(cudaDeviceSynchronize());
+    PT_CUDA(cudaMemcpy(params, c->d_params, c->n_params * sizeof(float), cudaMemcpyDeviceToHost));
+    return PT_OK;
+}
+
+PT_API pt_status pt_cache_set_params(pt_ctx* ctx, pt_cache* c, const float* params, void* stream)
+{
+    if (!ctx || !c || !params) return fail(ctx, PT_EINVAL, "null argument");
+    if (!finite3(params, c->n_params)) return fail(ctx, PT_EINVAL, "non-finite cache parameters");
+    cudaStream_t s = (cudaStream_t)stream;
+    PT_CUDA(cudaMemcpyAsync(c->d_params, params, c->n_params * sizeof(float), cudaMemcpyHostToDevice, s));
+    if (c->d_m) {
+        PT_CUDA(cudaMemsetAsync(c->d_m, 0, c->n_params * sizeof(float), s));
+        PT_CUDA(cudaMemsetAsync(c->d_v, 0, c->n_params * sizeof(float), s));
+    }
+    c->adam_t = 0;
+    PT_CUDA(cudaStreamSynchronize(s));
+    return PT_OK;
+}
+
+PT_API pt_status pt_cache_eval(pt_ctx* ctx, const pt_cache* c, int64_t n, const float* d_q, float* d_out, void* stream)
+{
+    if (!ctx || !c || n < 0 || (n > 0 && (!d_q || !d_out))) return fail(ctx, PT_EINVAL, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    PT_CUDA(timed(ctx, PT_KIND_CACHE, s, [&] {
+        return cache_eval(c->d_params, c->J, c->L, c->box, n, d_q, d_out, ctx->sm_count, s);
+    }));
+    return PT_OK;
+}
+
+PT_API pt_status pt_cache_loss_grad(pt_ctx* ctx, pt_cache* c, int64_t n, const float* d_q, const float* d_target,
+                                    const int32_t* d_mask, float* d_grad, double* d_loss, void* stream)
+{
+    if (!ctx || !c || n < 1 || !d_q || !d_target) return fail(ctx, PT_EINVAL, "bad argument");
+    pt_status st = ensure_cache_train(ctx, c, n);
     if (st != PT_OK) return st;
+    st = ensure_cache_paths(ctx, c, n);
+    if (st != PT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // queries -> 16-float record rows (valid = 1) so that the training feature kernel reads them
+    PT_CUDA(cudaMemsetAsync(c->d_rec, 0, (size_t)n * 64, s));
+    PT_CUDA(cudaMemcpy2DAsync(c->d_rec, 64, d_q, 36, 36, (size_t)n, cudaMemcpyDeviceToDevice, s));
+    TrainNet net = make_cache_net(c);
+    PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] {
+        cudaError_t e = cache_train_inputs(n, c->d_rec, nullptr, c->box, c->work.X[0], nullptr, nullptr, s);
+        if (e != cudaSuccess) return e;
+        return mlp_loss_grad(net, n, d_target, 0.f, 1, d_mask, c->work, d_loss ? d_loss : c->d_loss, nullptr, s);
+    }));
+    if (d_grad) PT_CUDA(cudaMemcpyAsync(d_grad, c->d_grad, c->n_params * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return PT_OK;
+}
+
+PT_API pt_status pt_train_cache(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, pt_cache* c,
+                                const pt_cache_train_cfg* cfg, float* d_loss, void* stream)
+{
+    if (!ctx || !sc || !c || !cfg) return fail(ctx, PT_EINVAL, "null argument");
+    if (cfg->n_train < 1 || cfg->max_depth < 1 || cfg->max_depth > kMaxDepth || cfg->rec_vertex < 1 ||
+        cfg->rec_vertex > cfg->max_depth || !adam_cfg_ok(cfg->lr, cfg->beta1, cfg->beta2, cfg->eps))
+        return fail(ctx, PT_EINVAL, "bad cache training configuration");
+    pt_render_cfg rc = {};
+    rc.width = cfg->width;
+    rc.height = cfg->height;
+    rc.spp = 1;
+    rc.max_depth = cfg->max_depth;
+    rc.seed = cfg->seed;
+    rc.precision = cfg->precision;
+    pt_status st = check_cfg(ctx, sc, nf, &rc);
+    if (st != PT_OK) return st;
+    const int64_t n = cfg->n_train;
+    st = ensure_cache_train(ctx, c, n);
+    if (st != PT_OK) return st;
+    st = ensure_cache_paths(ctx, c, n);
+    if (st != PT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t n_pix = (uint32_t)((int64_t)cfg->width * cfg->height);
+    PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] { return cache_train_pixels(cfg->seed, cfg->frame, n, n_pix, c->d_pixels, s); }));
+    // plain training paths with records at rec_vertex; spp 1, so the pixel means are the path radiances
+    st = render_impl(ctx, sc, nf, &rc, 0x40000000u + cfg->frame, nullptr, 0, cfg->rec_vertex, c->d_rec, n, c->d_pixels,
+                     c->d_Lpath, nullptr, nullptr, s);
+    if (st != PT_OK) return st;
+    TrainNet net = make_cache_net(c);
+    PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] {
+        cudaError_t e = cache_train_inputs(n, c->d_rec, c->d_Lpath, c->box, c->work.X[0], c->d_target, c->d_mask, s);
+        if (e != cudaSuccess) return e;
+        return mlp_loss_grad(net, n, c->d_target, 0.f, 1, c->d_mask, c->work, c->d_loss, d_loss, s);
+    }));
+    const int64_t t = c->adam_t;
+    const double c1 = 1.0 - std::pow((double)cfg->beta1, (double)(t + 1));
+    const double c2 = 1.0 - std::pow((double)cfg->beta2, (double)(t + 1));
+    PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] {
+        return adam_step(c->n_params, c->d_params, c->d_grad, c->d_m, c->d_v, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps,
+                         (float)c1, (float)c2, s);
+    }));
+    c->adam_t = t + 1;
+    return PT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The render loop behind pt_render / pt_render_pixels / pt_render_cached and
+// the training paths of pt_train_cache.  first_sample is the Philox sample
+// index of the first path per pixel; cache (nullable) ends paths at
+// cache_vertex; rec_vertex > 0 writes vertex records to d_rec.
+static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
+                             uint32_t first_sample, const pt_cache* cache, int cache_vertex, int rec_vertex, float* d_rec,
+                             int64_t n_pix, const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb,
+                             int32_t* d_hit_ids, cudaStream_t s)
+{
+    pt_status st = PT_OK;
     const int64_t WH = (int64_t)cfg->width * cfg->height;
     if (!d_pixels) n_pix = WH;
     if (n_pix < 0 || (n_pix > 0 && !d_pixel_rgb)) return fail(ctx, PT_EINVAL, "bad pixel list or output");
@@ -747,7 +1016,6 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
     if (sc->dev.env_is_nif && cfg->precision != PT_FP32 && !(cfg->precision == PT_BF16 && nf->d_tc) &&
         !(cfg->precision == PT_FP8E4M3 && nf->d_fp8))
         return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3");
-    cudaStream_t s = (cudaStream_t)stream;
     // chunk = whole samples
     int64_t chunk = cfg->chunk_slots > 0 ? cfg->chunk_slots : (int64_t)1 << 24;
     chunk = std::max<int64_t>(n_pix, (chunk / n_pix) * n_pix);
@@ -755,6 +1023,14 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
     if (chunk > 0x7FFFFFFFll) chunk = (0x7FFFFFFFll / n_pix) * n_pix;
     st = ensure_scratch(ctx, (uint32_t)chunk);
     if (st != PT_OK) return st;
+    if (cache && ctx->cache_cap < (uint32_t)chunk) {
+        cudaFree(ctx->cache_rows);
+        ctx->cache_rows = nullptr;
+        ctx->cache_cap = 0;
+        if (dalloc(&ctx->cache_rows, (size_t)chunk * 16)) return fail(ctx, PT_ENOMEM, "cache query rows allocation failed");
+        ctx->cache_cap = (uint32_t)chunk;
+    }
+    if (rec_vertex > 0) PT_CUDA(cudaMemsetAsync(d_rec, 0, (size_t)n_slots * 16 * sizeof(float), s));
     ctx->last_depth = cfg->max_depth;
     PT_CUDA(cudaMemsetAsync(ctx->stats, 0, kStats * sizeof(unsigned long long), s));
     if (d_hit_ids) PT_CUDA(launch_fill_i32(d_hit_ids, n_slots * cfg->max_depth, -2, s));
@@ -766,7 +1042,7 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
     bp.rr = cfg->rr;
     bp.rr_start = cfg->rr_start;
     bp.seed = cfg->seed;
-    bp.first_sample = (uint32_t)cfg->first_sample;
+    bp.first_sample = first_sample;
     bp.n_pix = (uint32_t)n_pix;
     bp.pixels = d_pixels;
     bp.W = cfg->width;
@@ -779,6 +1055,11 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
     bp.stats = ctx->stats;
     bp.work = ctx->stats + kWorkBase;
     bp.cap = (uint32_t)chunk;
+    bp.cache_vertex = cache ? cache_vertex : 0;
+    bp.cache_rows = ctx->cache_rows;
+    bp.cache_count = ctx->counters + kCacheCounter;
+    bp.rec_vertex = rec_vertex;
+    bp.rec = d_rec;
     const int64_t n_chunks = (n_slots + chunk - 1) / chunk;
     for (int64_t c = 0; c < n_chunks; ++c) {
         const int64_t first = c * chunk;
@@ -798,6 +1079,13 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
             st = eval_nif_escapes(ctx, nf, cfg->precision, sc->dev.has_emission, s);
             if (st != PT_OK) return st;
         }
+        if (cache) {
+            PT_CUDA(timed(ctx, PT_KIND_CACHE, s, [&] {
+                return cache_query(cache->d_params, cache->J, cache->L, cache->box, chunk,
+                                   ctx->counters + kCacheCounter, ctx->cache_rows, ctx->slot_L, sc->dev.has_emission,
+                                   ctx->d_err, ctx->sm_count, s);
+            }));
+        }
         const float scale = (c == n_chunks - 1) ? (float)(1.0 / cfg->spp) : 1.f;
         PT_CUDA(timed(ctx, PT_KIND_REDUCE, s, [&] {
             return launch_reduce(ctx->slot_L, d_pixel_rgb, (uint32_t)n_pix, (uint32_t)(n / n_pix), c == 0, scale, s);
@@ -807,6 +1095,32 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
                                     cudaMemcpyDeviceToDevice, s));
     }
     return PT_OK;
+}
+
+PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
+                                  int64_t n_pix, const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb,
+                                  int32_t* d_hit_ids, void* stream)
+{
+    pt_status st = check_cfg(ctx, sc, nf, cfg);
+    if (st != PT_OK) return st;
+    return render_impl(ctx, sc, nf, cfg, (uint32_t)cfg->first_sample, nullptr, 0, 0, nullptr, n_pix, d_pixels,
+                       d_pixel_rgb, d_slot_rgb, d_hit_ids, (cudaStream_t)stream);
+}
+
+PT_API pt_status pt_render_cached(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_cache* cache,
+                                  int32_t cache_vertex, int32_t rec_vertex, const pt_render_cfg* cfg, int64_t n_pix,
+                                  const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb, float* d_rec,
+                                  int32_t* d_hit_ids, void* stream)
+{
+    pt_status st = check_cfg(ctx, sc, nf, cfg);
+    if (st != PT_OK) return st;
+    if ((cache != nullptr) != (cache_vertex != 0) || cache_vertex < 0 || cache_vertex == 1)
+        return fail(ctx, PT_EINVAL, "cache and cache_vertex >= 2 go together");
+    if (cache && cache->ctx->device != ctx->device) return fail(ctx, PT_EINVAL, "cache lives on another device");
+    if (rec_vertex < 0 || rec_vertex > cfg->max_depth || (rec_vertex > 0 && !d_rec))
+        return fail(ctx, PT_EINVAL, "rec_vertex must be in [0, max_depth] with d_rec");
+    return render_impl(ctx, sc, nf, cfg, (uint32_t)cfg->first_sample, cache, cache_vertex, rec_vertex, d_rec, n_pix,
+                       d_pixels, d_pixel_rgb, d_slot_rgb, d_hit_ids, (cudaStream_t)stream);
 }
 
 PT_API pt_status pt_render(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
@@ -880,8 +1194,8 @@ PT_API pt_status pt_profile_read(pt_ctx* ctx, double* ms, int64_t* launches, int
 {
     if (!ctx || n < 0) return fail(ctx, PT_EINVAL, "bad argument");
     PT_CUDA(cudaDeviceSynchronize());
-    double acc[PT_N_KINDS] = {0, 0, 0, 0};
-    int64_t cnt[PT_N_KINDS] = {0, 0, 0, 0};
+    double acc[PT_N_KINDS] = {};
+    int64_t cnt[PT_N_KINDS] = {};
     for (size_t i = 0; i < ctx->prof_used; ++i) {
         float t = 0.f;
         PT_CUDA(cudaEventElapsedTime(&t, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));

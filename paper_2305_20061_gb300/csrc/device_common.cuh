@@ -63,6 +63,32 @@ __device__ __forceinline__ void fourier_feature(float b0, float b1, float u, flo
     sincospif(2.f * r, &s, &c);
 }
 
+// Radiance-cache position encoding (frequency encoding of Mueller et al.
+// 2021): p = (q - lo) / ext carried as a float pair ph + pl (TwoSum for the
+// numerator, ext = eh + el exact, one correction step for the quotient), so
+// that the top frequencies 2^j p keep a phase error of ~1e-7 instead of
+// 2^j ulp(p).  Writes sin(2^j pi p) to s[j] and cos(2^j pi p) to c[j].
+__device__ __forceinline__ void cache_axis_features(float q, float lo, float eh, float el, int J, float* s, int s_stride,
+                                                    float* c, int c_stride)
+{
+    const float d = q - lo;
+    const float bv = d - q;
+    const float e = (q - (d - bv)) + (-lo - bv);           // q - lo = d + e exactly
+    const float ph = __fdiv_rn(d, eh);
+    const float rem = fmaf(-ph, eh, d) + e - ph * el;      // first term exact
+    const float pl = __fdiv_rn(rem, eh);
+    float sc = 1.f;
+    for (int j = 0; j < J; ++j) {
+        const float x = ph * sc;                            // exact: power-of-two scale
+        const float xr = x - 2.f * floorf(0.5f * x);        // exact removal of whole turns
+        float sv, cv;
+        sincospif(xr + pl * sc, &sv, &cv);
+        s[j * s_stride] = sv;
+        c[j * c_stride] = cv;
+        sc *= 2.f;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Ray-primitive tests (Section 3.1.3).  Each returns t > 0 or +inf.
 // ---------------------------------------------------------------------------

@@ -88,6 +88,15 @@ struct BounceParams {
     uint32_t* err;
     unsigned long long* stats;  // [max_depth + 1]
     unsigned long long* work;   // nullable [4]: node fetches, sphere, quad, triangle tests
+    // radiance cache: a path that hits at vertex cache_vertex (0 = off) ends
+    // there with a query row (16 floats) appended to cache_rows
+    int32_t cache_vertex;
+    float* cache_rows;
+    uint32_t* cache_count;
+    // vertex records: the state at vertex rec_vertex (0 = off) of each path,
+    // rec [global slot][16] (the caller clears the valid words beforehand)
+    int32_t rec_vertex;
+    float* rec;
 };
 
 // NIF parameters on the device.
@@ -144,6 +153,7 @@ cudaError_t launch_nif_fp8(const unsigned char* image, const NifEvalParams& p, i
 // into the flat gradient (same order as the trainable part of the weights).
 struct TrainNet {
     int32_t F, H, L;
+    int32_t in0;                    // width of layer 0's input (2F for the NIF, 6J + 6 for the cache)
     const float* B;                 // [F][2]
     const float* W[9];              // per linear layer, [out][in]
     const float* b[9];
@@ -164,6 +174,27 @@ cudaError_t nif_loss_grad(const TrainNet& net, int64_t B, const float* uv, const
                           TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s);
 cudaError_t adam_step(int64_t n, float* w, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
                       float c1, float c2, cudaStream_t s);
+cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, float delta, int mode,
+                          const int32_t* mask, TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s);
+
+// Radiance cache (train.cu).  Rows of 16 floats: x[3], wo[3], n[3], tp[3],
+// L[3] (radiance gathered before the vertex), slot (query) or valid (record).
+struct CacheBox {
+    float lo[3];
+    float eh[3], el[3];             // hi - lo as an exact float pair eh + el
+    int32_t J;                      // frequencies per axis
+};
+// layer-0 inputs from record rows; with slot_L (path radiance) also targets and mask
+cudaError_t cache_train_inputs(int64_t n, const float* rec, const float* slot_L, CacheBox box, float* X0, float* target,
+                               int32_t* mask, cudaStream_t s);
+cudaError_t cache_train_pixels(uint32_t seed, uint32_t frame, int64_t n, uint32_t n_pix, int64_t* pixels, cudaStream_t s);
+// fused cache MLP (cache.cu): H = 64 only.  q [n][9] -> raw outputs [n][3];
+// render queries (rows [cap][16], live count on the device) -> slot radiance
+size_t cache_eval_smem_bytes(int in0, int L);
+cudaError_t cache_eval(const float* params, int J, int L, CacheBox box, int64_t n, const float* q, float* out,
+                       int sm_count, cudaStream_t s);
+cudaError_t cache_query(const float* params, int J, int L, CacheBox box, int64_t cap, const uint32_t* n_dev,
+                        const float* rows, float* slot_L, int accumulate, uint32_t* err, int sm_count, cudaStream_t s);
 // rebuild the packed FP32 layout and (when present) the tensor-core image from the master weights
 cudaError_t repack_nif_fp32(const float* params, int F, int H, int L, float* packed, cudaStream_t s);
 cudaError_t repack_nif_tc_image(const float* params, unsigned char* image, cudaStream_t s);

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
                 slot_to_pixel(p, s.slot, pix, smp);
             }
         }
-        bool survive = false, escape_nif = false;
+        bool survive = false, escape_nif = false, cache_q = false;
         float eu = 0.f, ev = 0.f;
         if (active) {
             ++traced;
@@ -207,11 +207,41 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
             } else {
                 const float3 hp = s.o + s.d * h.t;
                 const int32_t mat = __ldg(&p.sc.prim_mat[h.prim]);
-                if (p.sc.has_emission) {
+                if (p.rec_vertex == p.k || p.cache_vertex == p.k) {
+                    // state at this vertex: position, direction to the previous vertex, normal facing it,
+                    // throughput reaching it and radiance gathered before it
+                    const float3 ng0 = geometric_normal(p.sc, (uint32_t)h.prim, hp);
+                    const float3 nf = dot3(ng0, s.d) < 0.f ? ng0 : ng0 * -1.f;
+                    float* row = nullptr;
+                    float last = 1.f;   // record: valid
+                    if (p.rec_vertex == p.k) row = p.rec + 16 * (p.chunk_first + s.slot);
+                    if (p.cache_vertex == p.k) {
+                        // the path ends here; its query row goes to the cache queue (aggregated over the
+                        // lanes that arrive together)
+                        cache_q = true;
+                        const unsigned m = __activemask();
+                        const int leader = __ffs(m) - 1;
+                        uint32_t base = 0;
+                        if ((int)lane == leader) base = atomicAdd(p.cache_count, (uint32_t)__popc(m));
+                        base = __shfl_sync(m, base, leader);
+                        const uint32_t ci = base + __popc(m & ((1u << lane) - 1u));
+                        if (ci < p.cap) row = p.cache_rows + 16 * (size_t)ci;
+                        else atomicOr(p.err, PT_ERR_QUEUE_OVERFLOW);
+                        last = __uint_as_float(s.slot);
+                    }
+                    if (row) {
+                        float4* r = reinterpret_cast<float4*>(row);
+                        r[0] = make_float4(hp.x, hp.y, hp.z, -s.d.x);
+                        r[1] = make_float4(-s.d.y, -s.d.z, nf.x, nf.y);
+                        r[2] = make_float4(nf.z, s.tp.x, s.tp.y, s.tp.z);
+                        r[3] = make_float4(s.L.x, s.L.y, s.L.z, last);
+                    }
+                }
+                if (p.sc.has_emission && !cache_q) {
                     const float4 m1 = __ldg(&p.sc.mat[2 * mat + 1]);
                     s.L = s.L + s.tp * f3(m1.y, m1.z, m1.w);
                 }
-                bool alive = p.k < p.max_depth;
+                bool alive = p.k < p.max_depth && !cache_q;
                 if (alive) {
                     const uint4 w = philox4x32_10(make_uint4(pix, smp, (uint32_t)p.k, 0u), p.seed, 0u);
                     const float3 ng = geometric_normal(p.sc, (uint32_t)h.prim, hp);
@@ -233,7 +263,7 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
                     }
                 }
                 if (alive) survive = true;
-                else store_L(p.slot_L, s.slot, s.L, p.err);
+                else if (!cache_q) store_L(p.slot_L, s.slot, s.L, p.err);   // a cache query writes it later
             }
         }
         // compaction: survivors into the next queue, escapes into the NIF queue

@@ -117,11 +117,14 @@ __global__ void k_train_features(int64_t B, const float* __restrict__ uv, const 
     }
 }
 
-// Xout = relu(Xin W^T + b); W is [out][in] row-major (PyTorch layout)
-__global__ void __launch_bounds__(kT, 1) k_layer_fwd(int64_t B, const float* __restrict__ Xin, float* __restrict__ Xout,
+// Xout = relu(Xin W^T + b); W is [out][in] row-major (PyTorch layout).
+// n_dev (nullable): live row count on the device, at most B.
+__global__ void __launch_bounds__(kT, 1) k_layer_fwd(int64_t B, const uint32_t* __restrict__ n_dev,
+                                                     const float* __restrict__ Xin, float* __restrict__ Xout,
                                                      const float* __restrict__ W, const float* __restrict__ b, int in,
                                                      int out)
 {
+    if (n_dev) B = min((int64_t)*n_dev, B);
     extern __shared__ float4 smem4[];
     float* Ws = reinterpret_cast<float*>(smem4);   // [k][j] = W[j][k]
     float* Xs = Ws + kD * kD;                       // [k][row]
@@ -246,14 +249,18 @@ __global__ void __launch_bounds__(kT, 1) k_layer_bwd_dw(int64_t B, const float* 
         for (int r = 0; r < 4; ++r) P[kD * kD + 4 * m.rg + r] = db[r];
 }
 
-// output layer, colour matrix, Huber loss: dXlast = relu-masked W4^T dy,
-// partial head gradients and FP64 loss partials per CTA.
-// head partial[block] = [3 x 128 dW4] [3 db4]
+// Output layer and loss: dXlast = relu-masked W4^T dy, partial head
+// gradients and FP64 loss partials per CTA.  head partial[block] = [3 x 128
+// dW4] [3 db4].
+//   mode 0 (NIF): Huber(delta) between M y and the target (log space).
+//   mode 1 (radiance cache): relative L2, (y - t)^2 / (sg(y)^2 + 0.01), on
+//          the linear output; rows with mask == 0 contribute nothing.
 __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __restrict__ X, const float* __restrict__ target,
                                                      const float* __restrict__ W4, const float* __restrict__ b4, int H,
                                                      const float* __restrict__ Mm, float delta, float inv_n,
                                                      float* __restrict__ dX, float* __restrict__ head_partial,
-                                                     double* __restrict__ loss_partial)
+                                                     double* __restrict__ loss_partial, int mode,
+                                                     const int32_t* __restrict__ mask)
 {
     __shared__ float dys[kT][3];
     __shared__ double lsum[kT];
@@ -261,12 +268,15 @@ __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __r
     float gb[3] = {0.f, 0.f, 0.f};
     double loss = 0.0;
     float M[9];
-    for (int i = 0; i < 9; ++i) M[i] = Mm[i];
+    for (int i = 0; i < 9; ++i) M[i] = mode == 0 ? Mm[i] : (i % 4 == 0 ? 1.f : 0.f);
     const int64_t n_tiles = (B + kT - 1) / kT;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t g = tile * kT + threadIdx.x;
         float dy[3] = {0.f, 0.f, 0.f};
-        if (g < B) {
+        if (g < B && mask && !mask[g]) {
+            float* dxr = dX + g * kD;
+            for (int k = 0; k < kD; ++k) dxr[k] = 0.f;
+        } else if (g < B) {
             const float* x = X + g * kD;
             float y[3] = {__ldg(&b4[0]), __ldg(&b4[1]), __ldg(&b4[2])};
             for (int k = 0; k < H; ++k) {
@@ -279,9 +289,15 @@ __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __r
             for (int c = 0; c < 3; ++c) {
                 const float z = M[3 * c] * y[0] + M[3 * c + 1] * y[1] + M[3 * c + 2] * y[2];
                 const float r = z - target[3 * g + c];
-                const float a = fabsf(r);
-                loss += a <= delta ? 0.5 * (double)r * (double)r : (double)delta * ((double)a - 0.5 * (double)delta);
-                dz[c] = (a <= delta ? r : copysignf(delta, r)) * inv_n;
+                if (mode == 0) {
+                    const float a = fabsf(r);
+                    loss += a <= delta ? 0.5 * (double)r * (double)r : (double)delta * ((double)a - 0.5 * (double)delta);
+                    dz[c] = (a <= delta ? r : copysignf(delta, r)) * inv_n;
+                } else {
+                    const float den = z * z + 0.01f;   // held constant in the gradient
+                    loss += (double)r * (double)r / (double)den;
+                    dz[c] = 2.f * r / den * inv_n;
+                }
             }
             for (int j = 0; j < 3; ++j) dy[j] = M[j] * dz[0] + M[3 + j] * dz[1] + M[6 + j] * dz[2];
             float* dxr = dX + g * kD;
@@ -381,10 +397,12 @@ cudaError_t train_inputs(uint32_t seed, uint32_t step, int64_t B, const float* s
     return cudaGetLastError();
 }
 
-// Loss and gradient of a batch: uv [B][2], target [B][3] (log space) ->
-// grad (flat trainable layout) and the loss (FP64 and/or FP32 copies).
-cudaError_t nif_loss_grad(const TrainNet& net, int64_t B, const float* uv, const float* target, float delta,
-                          TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s)
+// Loss and gradient of a batch whose layer-0 inputs are already in X[0]:
+// target [B][3] -> grad (flat trainable layout) and the loss (FP64 and/or
+// FP32 copies).  mode 0: NIF (Huber, colour matrix); mode 1: radiance cache
+// (relative L2, rows masked by mask).
+cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, float delta, int mode,
+                          const int32_t* mask, TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s)
 {
     if (B <= 0) return cudaSuccess;
     cudaError_t e;
@@ -393,21 +411,20 @@ cudaError_t nif_loss_grad(const TrainNet& net, int64_t B, const float* uv, const
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
         if (e != cudaSuccess) return e;
     }
-    k_train_features<<<(unsigned)std::min<int64_t>((B + 127) / 128, 152 * 8), 128, 0, s>>>(B, uv, net.B, net.F, wk.X[0]);
     // forward through the hidden layers
     for (int l = 0; l < net.L; ++l) {
-        const int in = l == 0 ? 2 * net.F : net.H;
-        k_layer_fwd<<<G, kT, kGemmSmem, s>>>(B, wk.X[l], wk.X[l + 1], net.W[l], net.b[l], in, net.H);
+        const int in = l == 0 ? net.in0 : net.H;
+        k_layer_fwd<<<G, kT, kGemmSmem, s>>>(B, nullptr, wk.X[l], wk.X[l + 1], net.W[l], net.b[l], in, net.H);
     }
     // head + loss
     k_head_loss<<<G, kT, 0, s>>>(B, wk.X[net.L], target, net.W[net.L], net.b[net.L], net.H, net.M, delta,
-                                 1.f / (3.f * (float)B), wk.dX[0], wk.partial, wk.loss_partial);
+                                 1.f / (3.f * (float)B), wk.dX[0], wk.partial, wk.loss_partial, mode, mask);
     k_sum_partials<<<4, 256, 0, s>>>(wk.partial, G, 3 * kD + 3, kD, 3 * kD, net.H, 3, net.gW[net.L], net.gb[net.L]);
     k_sum_loss<<<1, 32, 0, s>>>(wk.loss_partial, G, 1.0 / (3.0 * (double)B), loss_d, loss_f);
     // backward through the hidden layers
     int cur = 0;
     for (int l = net.L - 1; l >= 0; --l) {
-        const int in = l == 0 ? 2 * net.F : net.H;
+        const int in = l == 0 ? net.in0 : net.H;
         k_layer_bwd_dw<<<G, kT, kGemmSmem, s>>>(B, wk.dX[cur], wk.X[l], wk.partial);
         k_sum_partials<<<64, 256, 0, s>>>(wk.partial, G, kD * kD + kD, kD, kD * kD, in, net.H, net.gW[l], net.gb[l]);
         if (l > 0) {
@@ -415,6 +432,77 @@ cudaError_t nif_loss_grad(const TrainNet& net, int64_t B, const float* uv, const
             cur ^= 1;
         }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t nif_loss_grad(const TrainNet& net, int64_t B, const float* uv, const float* target, float delta,
+                          TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s)
+{
+    if (B <= 0) return cudaSuccess;
+    k_train_features<<<(unsigned)std::min<int64_t>((B + 127) / 128, 152 * 8), 128, 0, s>>>(B, uv, net.B, net.F, wk.X[0]);
+    return mlp_loss_grad(net, B, target, delta, 0, nullptr, wk, loss_d, loss_f, s);
+}
+
+// ---------------------------------------------------------------------------
+// Radiance cache (Mueller et al. 2021, cited in Section 2.1)
+namespace {
+
+// query / record rows: 16 floats = x[3], wo[3], n[3], tp[3], L[3], slot or valid (bits)
+__global__ void k_cache_features(int64_t cap, const uint32_t* __restrict__ n_dev, const float* __restrict__ rows,
+                                 CacheBox box, float* __restrict__ X0)
+{
+    const int64_t n = n_dev ? min((int64_t)*n_dev, cap) : cap;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float* q = rows + 16 * i;
+        float* row = X0 + i * kD;
+        int k = 0;
+        for (int a = 0; a < 3; ++a) {
+            cache_axis_features(q[a], box.lo[a], box.eh[a], box.el[a], box.J, row + k, 1, row + k + box.J, 1);
+            k += 2 * box.J;
+        }
+        for (int t = 0; t < 6; ++t) row[k + t] = q[3 + t];
+        for (int t = k + 6; t < kD; ++t) row[t] = 0.f;
+    }
+}
+
+// training targets from vertex records: (L_path - L_before) / tp, masked where the path never got there
+__global__ void k_cache_targets(int64_t n, const float* __restrict__ rec, const float* __restrict__ slot_L,
+                                float* __restrict__ target, int32_t* __restrict__ mask)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float* r = rec + 16 * i;
+        bool ok = r[15] != 0.f;
+        float t[3];
+        for (int c = 0; c < 3; ++c) {
+            ok = ok && r[9 + c] > 0.f;
+            t[c] = ok ? (slot_L[3 * i + c] - r[12 + c]) / r[9 + c] : 0.f;
+        }
+        mask[i] = ok ? 1 : 0;
+        for (int c = 0; c < 3; ++c) target[3 * i + c] = ok ? t[c] : 0.f;
+    }
+}
+
+// training pixels of a frame: Philox key (seed, 2), counter (i, frame, 0, 0), word 0 mod (W * H)
+__global__ void k_train_pixels(uint32_t seed, uint32_t frame, int64_t n, uint32_t n_pix, int64_t* pixels)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        pixels[i] = (int64_t)(philox4x32_10(make_uint4((uint32_t)i, frame, 0u, 0u), seed, 2u).x % n_pix);
+}
+
+}  // namespace
+
+cudaError_t cache_train_inputs(int64_t n, const float* rec, const float* slot_L, CacheBox box, float* X0, float* target,
+                               int32_t* mask, cudaStream_t s)
+{
+    const unsigned g = (unsigned)std::min<int64_t>((n + 127) / 128, 152 * 8);
+    k_cache_features<<<g, 128, 0, s>>>(n, nullptr, rec, box, X0);
+    if (slot_L) k_cache_targets<<<g, 128, 0, s>>>(n, rec, slot_L, target, mask);
+    return cudaGetLastError();
+}
+
+cudaError_t cache_train_pixels(uint32_t seed, uint32_t frame, int64_t n, uint32_t n_pix, int64_t* pixels, cudaStream_t s)
+{
+    k_train_pixels<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(seed, frame, n, n_pix, pixels);
     return cudaGetLastError();
 }
 

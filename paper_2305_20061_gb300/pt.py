@@ -59,6 +59,17 @@ class TrainCfg(C.Structure):
                 ("eps", C.c_float), ("huber_delta", C.c_float), ("seed", U32)]
 
 
+class CacheDesc(C.Structure):
+    _fields_ = [("n_freq", I32), ("hidden", I32), ("n_hidden_layers", I32), ("params", P),
+                ("lo", C.c_float * 3), ("hi", C.c_float * 3)]
+
+
+class CacheTrainCfg(C.Structure):
+    _fields_ = [("width", I32), ("height", I32), ("n_train", I32), ("max_depth", I32), ("rec_vertex", I32),
+                ("seed", U32), ("frame", U32), ("precision", I32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float)]
+
+
 class PTError(RuntimeError):
     def __init__(self, status: int, msg: str, bits: int = 0):
         super().__init__(f"pt status {status}: {msg}")
@@ -103,6 +114,15 @@ def lib():
             "pt_nif_fp8_scales": ([P, P], I32),
             "pt_train_nif": ([P, P, P, I32, I32, P, P, P], I32),
             "pt_nif_loss_grad": ([P, P, I64, P, P, C.c_float, P, P, P], I32),
+            "pt_create_cache": ([P, P, P], I32),
+            "pt_destroy_cache": ([P], None),
+            "pt_cache_param_count": ([P], I64),
+            "pt_cache_get_params": ([P, P, P], I32),
+            "pt_cache_set_params": ([P, P, P, P], I32),
+            "pt_cache_eval": ([P, P, I64, P, P, P], I32),
+            "pt_cache_loss_grad": ([P, P, I64, P, P, P, P, P, P], I32),
+            "pt_train_cache": ([P, P, P, P, P, P, P], I32),
+            "pt_render_cached": ([P, P, P, P, I32, I32, P, I64, P, P, P, P, P, P], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -280,12 +300,82 @@ class Nif:
             self.h = None
 
 
+def cache_flat(cache: I.CacheNet) -> np.ndarray:
+    """Flat float32 parameter layout of pt_cache_desc (per layer W then b)."""
+    parts = []
+    for W, b in zip(cache.W, cache.b):
+        parts += [W.ravel(), b.ravel()]
+    return np.ascontiguousarray(np.concatenate(parts).astype(np.float32))
+
+
+class Cache:
+    """pt_create_cache from an inputs.CacheNet."""
+
+    def __init__(self, ctx: Context, cache: I.CacheNet):
+        self.ctx = ctx
+        self.src = cache
+        flat = cache_flat(cache)
+        d = CacheDesc(cache.n_freq, cache.hidden, cache.n_hidden_layers, _np_ptr(flat))
+        for a in range(3):
+            d.lo[a] = float(cache.lo[a])
+            d.hi[a] = float(cache.hi[a])
+        self.h = P()
+        ctx._raise(lib().pt_create_cache(ctx.h, C.byref(d), C.byref(self.h)))
+
+    @property
+    def param_count(self) -> int:
+        return int(lib().pt_cache_param_count(self.h))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.param_count, np.float32)
+        self.ctx._raise(lib().pt_cache_get_params(self.ctx.h, self.h, _np_ptr(out)))
+        return out
+
+    def set_params(self, flat: np.ndarray, stream=None) -> None:
+        flat = np.ascontiguousarray(flat, np.float32)
+        assert flat.size == self.param_count
+        self.ctx._raise(lib().pt_cache_set_params(self.ctx.h, self.h, _np_ptr(flat), _stream(stream)))
+
+    def eval(self, q: torch.Tensor, stream=None) -> torch.Tensor:
+        """pt_cache_eval: raw outputs [n, 3] for queries [n, 9] (x, wo, n)."""
+        q = q.contiguous()
+        out = torch.empty((q.shape[0], 3), dtype=torch.float32, device=q.device)
+        self.ctx._raise(lib().pt_cache_eval(self.ctx.h, self.h, q.shape[0], _dptr(q), _dptr(out), _stream(stream)))
+        return out
+
+    def loss_grad(self, q: torch.Tensor, target: torch.Tensor, mask: Optional[torch.Tensor] = None, stream=None):
+        """pt_cache_loss_grad: (loss as a device double tensor, flat gradient)."""
+        q, target = q.contiguous(), target.contiguous()
+        grad = torch.empty(self.param_count, dtype=torch.float32, device=q.device)
+        loss = torch.zeros(1, dtype=torch.float64, device=q.device)
+        self.ctx._raise(lib().pt_cache_loss_grad(self.ctx.h, self.h, q.shape[0], _dptr(q), _dptr(target),
+                                                 _dptr(None if mask is None else mask.contiguous()), _dptr(grad),
+                                                 _dptr(loss), _stream(stream)))
+        return loss, grad
+
+    def train_frame(self, scene: "Scene", nif: Optional["Nif"], width: int, height: int, frame: int,
+                    n_train: int = 1 << 16, max_depth: int = 6, rec_vertex: int = 2, seed: int = 0,
+                    precision: str = "fp32", lr: float = 1e-2, beta1: float = 0.9, beta2: float = 0.999,
+                    eps: float = 1e-7, loss: Optional[torch.Tensor] = None, stream=None) -> Optional[torch.Tensor]:
+        """pt_train_cache: one online training step; loss (optional [1] float32 device tensor) receives the loss."""
+        cfg = CacheTrainCfg(width, height, n_train, max_depth, rec_vertex, seed, frame, PRECISIONS[precision], lr,
+                            beta1, beta2, eps)
+        self.ctx._raise(lib().pt_train_cache(self.ctx.h, scene.h, nif.h if nif is not None else None, self.h,
+                                             C.byref(cfg), _dptr(loss), _stream(stream)))
+        return loss
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().pt_destroy_cache(self.h)
+            self.h = None
+
+
 def make_cfg(cfg: I.RenderCfg, precision: str = "fp32", chunk_slots: int = 0, first_sample: int = 0) -> RenderCfg:
     return RenderCfg(cfg.width, cfg.height, cfg.spp, cfg.max_depth, cfg.seed, int(cfg.rr), cfg.rr_start,
                      PRECISIONS[precision], int(chunk_slots), int(first_sample))
 
 
-KINDS = ("trace", "nif", "reduce", "other")
+KINDS = ("trace", "nif", "reduce", "other", "cache")
 
 
 def profile_enable(ctx: Context, enable: bool = True) -> None:
@@ -325,6 +415,26 @@ def render_pixels(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderC
     ctx._raise(lib().pt_render_pixels(ctx.h, scene.h, nif.h if nif is not None else None, C.byref(c), n,
                                       _dptr(pixels), _dptr(pix), _dptr(slots), _dptr(ids), _stream(stream)))
     return pix, slots, ids
+
+
+def render_cached(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderCfg, pixels: Optional[torch.Tensor],
+                  cache: Optional[Cache] = None, cache_vertex: int = 0, rec_vertex: int = 0, precision: str = "fp32",
+                  want_slots: bool = False, want_ids: bool = False, chunk_slots: int = 0, first_sample: int = 0,
+                  stream=None):
+    """pt_render_cached: (pixel_rgb [n,3], slot_rgb [spp,n,3] or None, records [spp,n,16] or None,
+    hit_ids [spp,n,D] or None)."""
+    dev = f"cuda:{ctx.device}"
+    n = cfg.width * cfg.height if pixels is None else int(pixels.shape[0])
+    pix = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    slots = torch.empty((cfg.spp, n, 3), dtype=torch.float32, device=dev) if want_slots else None
+    rec = torch.empty((cfg.spp, n, 16), dtype=torch.float32, device=dev) if rec_vertex else None
+    ids = torch.empty((cfg.spp, n, cfg.max_depth), dtype=torch.int32, device=dev) if want_ids else None
+    c = make_cfg(cfg, precision, chunk_slots, first_sample)
+    ctx._raise(lib().pt_render_cached(ctx.h, scene.h, nif.h if nif is not None else None,
+                                      cache.h if cache is not None else None, cache_vertex, rec_vertex, C.byref(c), n,
+                                      _dptr(pixels), _dptr(pix), _dptr(slots), _dptr(rec), _dptr(ids),
+                                      _stream(stream)))
+    return pix, slots, rec, ids
 
 
 def last_render_counts(ctx: Context, max_depth: int) -> np.ndarray:
