@@ -9,8 +9,14 @@ procedural 2048x1024 sky with pt_train_nif.  The same line reports the
 FP32-network frame rate and the relative RMSE between the BF16 and FP32
 frames.  Prints one JSON line (rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
-                  [--workload C1|C2|C3|C4]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32|fp8]
+                  [--workload C1|C2|C3|C4|C5]
+
+Workload C5 (neural radiance cache on the heightfield scene): a step is one
+frame of the online loop, i.e. one pt_train_cache step on 2^16 training
+paths plus the 1024x1024, 4 spp render whose paths end in the cache at
+vertex 2.  The line adds the plain full-depth FP32 and BF16 frame times and
+the cache's bias against a plain 4096-spp FP32 reference.
   python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
 
 Multi-GPU (torchrun, one rank per GPU): each rank renders its own disjoint
@@ -39,7 +45,8 @@ FLOP_PER_EVAL = 2 * (3 * 128 * 128 + 128 * 3)   # 99,072: three 128x128 layers +
 TC_FLOP_PER_EVAL = 2 * 3 * 128 * 128            # 98,304 in the three hidden layers
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# FP32 operations per traversal step as implemented
+# FP32 operations per traversal step as implemented in k_bounce (node slab test of both children, sphere,
+# axis-aligned quad and watertight triangle tests)
 OPS_NODE, OPS_SPHERE, OPS_QUAD, OPS_TRI = 58, 36, 12, 46
 # algorithmic bytes per traversal step and per ray-bounce of queue traffic
 BYTES_NODE, BYTES_SPHERE, BYTES_QUAD, BYTES_TRI, BYTES_RAY = 48, 16, 32, 48, 140
@@ -156,6 +163,23 @@ def bench_reference(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
     sc, cfg, nif = workload(args.workload, args.spp)
+    if args.workload == "C5":
+        cache0 = I.cache_init(*I.scene_bounds(sc))
+        vals = []
+        for i in range(args.warmup + args.steps):
+            v, sample = oracle_c5_rate(sc, nif, cache0, cfg, args.ref_step_s)
+            if i >= args.warmup:
+                vals.append(v)
+        value = float(np.mean(vals))
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * cfg.n_slots / (value * 1e6),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"C5: {I.CONFIGS['C5']['desc']}", "paths_per_frame": cfg.n_slots},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return 0
     threads = os.cpu_count() or 1
     run, n_pix = oracle_rate(sc, cfg, nif, target_s=args.ref_step_s, n_threads=threads)
     for _ in range(args.warmup):
@@ -176,6 +200,37 @@ def bench_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
     return 0
+
+
+def train_env_nif(pt, ctx, gnif, nif, steps, dev):
+    """Train the environment NIF on the procedural 2048 x 1024 HDR sky (not
+    timed as a frame); copies the trained weights back into `nif`."""
+    import torch
+    sky = torch.from_numpy(I.procedural_sky()).to(dev)
+    batch = 1 << 16
+    gnif.train(sky, steps=5, batch=batch, lr=1e-3, seed=0)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    losses = gnif.train(sky, steps=steps, batch=batch, lr=1e-3, seed=0)
+    t1.record()
+    torch.cuda.synchronize()
+    ctx.check()
+    tms = t0.elapsed_time(t1)
+    train = {"steps": steps + 5, "batch": batch, "ms_per_step": tms / steps,
+             "samples_per_s": steps * batch / (tms * 1e-3),
+             "fwd_bwd_tflops": steps * batch * 3 * FLOP_PER_EVAL / (tms * 1e-3) / 1e12,
+             "loss_first": float(losses[0].item()), "loss_last": float(losses[-50:].mean().item())}
+    del sky
+    params = gnif.get_params()
+    p = 2 * nif.n_freq
+    for W, b in zip(nif.W, nif.b):
+        W[:] = params[p:p + W.size].reshape(W.shape)
+        p += W.size
+        b[:] = params[p:p + b.size]
+        p += b.size
+    return train
 
 
 # ----------------------------------------------------------------------------
@@ -204,33 +259,7 @@ def bench_ours(args):
     gnif = pt.Nif(ctx, nif) if uses_nif else None
 
     # the environment NIF is trained on the procedural 2048 x 1024 HDR sky first (not timed as a frame)
-    train = None
-    if uses_nif and args.train_steps > 0:
-        sky = torch.from_numpy(I.procedural_sky()).to(dev)
-        batch = 1 << 16
-        gnif.train(sky, steps=5, batch=batch, lr=1e-3, seed=0)
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record()
-        losses = gnif.train(sky, steps=args.train_steps, batch=batch, lr=1e-3, seed=0)
-        t1.record()
-        torch.cuda.synchronize()
-        ctx.check()
-        tms = t0.elapsed_time(t1)
-        train = {"steps": args.train_steps + 5, "batch": batch, "ms_per_step": tms / args.train_steps,
-                 "samples_per_s": args.train_steps * batch / (tms * 1e-3),
-                 "fwd_bwd_tflops": args.train_steps * batch * 3 * FLOP_PER_EVAL / (tms * 1e-3) / 1e12,
-                 "loss_first": float(losses[0].item()), "loss_last": float(losses[-50:].mean().item())}
-        del sky
-        # host copy of the trained weights (used by the end-to-end leg and the CPU baseline)
-        params = gnif.get_params()
-        p = 2 * nif.n_freq
-        for W, b in zip(nif.W, nif.b):
-            W[:] = params[p:p + W.size].reshape(W.shape)
-            p += W.size
-            b[:] = params[p:p + b.size]
-            p += b.size
+    train = train_env_nif(pt, ctx, gnif, nif, args.train_steps, dev) if uses_nif and args.train_steps > 0 else None
     img = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -412,6 +441,300 @@ def bench_ours(args):
         dist.destroy_process_group()
     return 0
 
+# ----------------------------------------------------------------------------
+CACHE_FLOP_PER_QUERY = 2 * (78 * 64 + 4 * 64 * 64 + 64 * 3)   # 43,136: 5 x FC-64 + FC-3 on 78 inputs
+N_TRAIN = 1 << 16
+CACHE_VERTEX = 2
+C5_FRAMES = 60
+
+
+def image_stats(X_batches, R_mean, R_var):
+    """Relative RMSE of the mean of X_batches against R_mean, and the bias
+    with both images' noise taken out: E[(X - R)^2] = bias^2 + var X + var R
+    per pixel and channel (variances of the means from the batch spread)."""
+    import torch
+    nb = X_batches.shape[0]
+    X = X_batches.mean(0)
+    vX = X_batches.var(0) / nb
+    den = (R_mean ** 2).sum()
+    d2 = ((X - R_mean) ** 2).sum()
+    b2 = float((d2 - vX.sum() - R_var.sum()) / den)
+    H, W = R_mean.shape[0], R_mean.shape[1]
+
+    def blk(Y):
+        return Y.reshape(H // 8, 8, W // 8, 8, 3).mean((1, 3))
+    return {"rel_rmse": float(torch.sqrt(d2 / den)), "bias_rel_rmse": float(np.sign(b2) * np.sqrt(abs(b2))),
+            "noise_rel_rmse": float(torch.sqrt(vX.sum() / den)),
+            "rel_rmse_8x8_blocks": float(torch.sqrt(((blk(X) - blk(R_mean)) ** 2).sum() / (blk(R_mean) ** 2).sum()))}
+
+
+def oracle_c5_rate(sc, nif, cache, cfg, target_s):
+    """Oracle frame rate of the cached loop on a bounded sample: cached render
+    paths, plain training paths with vertex records and the relative-L2
+    loss/gradient, each timed on a slice and scaled to one frame (2^16
+    training samples + W*H*spp render paths).  Single-threaded."""
+    from oracle import oracle as O
+    osc, onif, oc = O.Scene(sc), O.Nif(nif), O.Cache(cache)
+    n_pix = cfg.width * cfg.height
+
+    def rate(fn, n0):
+        n = n0
+        while True:
+            t0 = time.perf_counter()
+            fn(n)
+            dt = time.perf_counter() - t0
+            if dt > target_s / 6 or n >= 1 << 20:
+                return n / dt, n
+            n *= 4
+
+    def render_paths(n):
+        pix = np.arange(n, dtype=np.int64) * 7919 % n_pix
+        O.trace_paths(osc, sc.camera, cfg.width, cfg.height, cfg.max_depth, 0, pix, np.zeros(n, np.int64),
+                      nif=onif, cache=oc, cache_vertex=CACHE_VERTEX)
+
+    def train_paths(n):
+        pix = np.arange(n, dtype=np.int64) * 104729 % n_pix
+        L, rec, _ = O.trace_paths(osc, sc.camera, cfg.width, cfg.height, cfg.max_depth, 0, pix,
+                                  np.full(n, 1 << 30, np.int64), nif=onif, rec_vertex=CACHE_VERTEX)
+        ok = rec[:, 15] == 1
+        tgt = np.zeros((n, 3))
+        tgt[ok] = (L[ok] - rec[ok, 12:15]) / rec[ok, 9:12]
+        oc.loss_grad(rec[:, :9], tgt, mask=ok.astype(np.int32))
+
+    r_render, n_r = rate(render_paths, 256)
+    r_train, n_t = rate(train_paths, 64)
+    frame_s = cfg.n_slots / r_render + N_TRAIN / r_train
+    return cfg.n_slots / frame_s / 1e6, (f"{n_r} cached render paths and {n_t} training paths (+ loss/gradient) timed, "
+                                          f"scaled to one frame of {cfg.n_slots} render paths + {N_TRAIN} training "
+                                          f"samples; FP64 oracle, single-threaded")
+
+
+def bench_c5(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    from paper_2305_20061_gb300 import build
+    build.build()
+    from paper_2305_20061_gb300 import pt
+
+    dev = f"cuda:{local}"
+    sc, cfg, nif = workload("C5", args.spp)
+    prec = args.precision
+    ctx = pt.Context(local)
+    t_build = time.perf_counter()
+    scene = pt.Scene(ctx, sc)
+    t_build = time.perf_counter() - t_build
+    gnif = pt.Nif(ctx, nif)
+    train = train_env_nif(pt, ctx, gnif, nif, args.train_steps, dev) if args.train_steps > 0 else None
+    lo, hi = I.scene_bounds(sc)
+    cache0 = I.cache_init(lo, hi)
+    gc = pt.Cache(ctx, cache0)
+    W, H, spp = cfg.width, cfg.height, cfg.spp
+    img = torch.empty((W * H, 3), dtype=torch.float32, device=dev)
+    img_plain = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    losses = torch.zeros(max(C5_FRAMES, args.warmup + args.steps), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def frame(f):
+        # each rank runs its own online loop on its own samples (replicas, no collective)
+        gc.train_frame(scene, gnif, W, H, f * world + rank, n_train=N_TRAIN, max_depth=cfg.max_depth,
+                       rec_vertex=CACHE_VERTEX, seed=0, precision=prec, loss=losses[f:f + 1])
+        pt.render_cached(ctx, scene, gnif, cfg, None, cache=gc, cache_vertex=CACHE_VERTEX, precision=prec,
+                         first_sample=(f * world + rank) * spp, out=img)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for f in range(args.warmup):
+        frame(f)
+    ctx.check()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    pt.profile_enable(ctx, True)
+    pt.profile_read(ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for i in range(args.steps):
+        flush.fill_(float(i))           # evict L2 between timed frames (not timed)
+        ev[i][0].record(stream)
+        frame(args.warmup + i)
+        ev[i][1].record(stream)
+    barrier()
+    prof = pt.profile_read(ctx)
+    clocks = sampler.stop()
+    ctx.check()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * cfg.n_slots / (ms * 1e-3) / 1e6
+    n_done = args.warmup + args.steps
+
+    # split of one more frame: the training step, then the cached render alone
+    gc.train_frame(scene, gnif, W, H, n_done * world + rank, n_train=N_TRAIN, max_depth=cfg.max_depth,
+                   rec_vertex=CACHE_VERTEX, seed=0, precision=prec, loss=losses[n_done:n_done + 1])
+    prof_train = pt.profile_read(ctx)
+    pt.render_cached(ctx, scene, gnif, cfg, None, cache=gc, cache_vertex=CACHE_VERTEX, precision=prec,
+                     first_sample=(n_done * world + rank) * spp, out=img)
+    prof_render = pt.profile_read(ctx)
+    pt.profile_enable(ctx, False)
+    counts = pt.last_render_counts(ctx, cfg.max_depth, with_cache=True)
+    work = pt.last_render_work(ctx)
+    n_done += 1
+    ctx.check()
+
+    # the plain full-depth frame of the same size, FP32 and the chosen precision
+    def plain_ms(p, reps=3):
+        pt.render(ctx, scene, gnif, cfg, p, out=img_plain)
+        torch.cuda.synchronize()
+        e = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for i in range(reps):
+            flush.fill_(float(i))
+            e[i][0].record(stream)
+            pt.render(ctx, scene, gnif, cfg, p, out=img_plain, first_sample=(i + 1) * spp)
+            e[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in e) / reps
+    plain = {"fp32_ms": plain_ms("fp32")}
+    plain[f"{prec}_ms"] = plain_ms(prec)
+    plain["fp32_msamples_s"] = cfg.n_slots / (plain["fp32_ms"] * 1e-3) / 1e6
+    ctx.check()
+
+    # bias of the cache after the 60-frame loop: frozen cache at 1024 spp vs the plain 4096-spp FP32 render
+    bias = None
+    if not args.no_bias and args.spp is None:
+        while n_done < C5_FRAMES:
+            frame(n_done)
+            n_done += 1
+        base = 1 << 24
+        R = []
+        for b in range(16):
+            rc = I.RenderCfg(W, H, 256, cfg.max_depth, 0)
+            R.append(pt.render(ctx, scene, gnif, rc, "fp32", first_sample=base + 256 * b).double())
+        R = torch.stack(R)
+        R_mean, R_var = R.mean(0), R.var(0) / R.shape[0]
+        del R
+        X = []
+        for b in range(8):
+            rc = I.RenderCfg(W, H, 128, cfg.max_depth, 0)
+            X.append(pt.render_cached(ctx, scene, gnif, rc, None, cache=gc, cache_vertex=CACHE_VERTEX, precision=prec,
+                                      first_sample=2 * base + 128 * b)[0].double().reshape(H, W, 3))
+        X = torch.stack(X)
+        ctx.check()
+        bias = {"frames_trained": n_done, "reference": "plain FP32 render, 4096 spp (16 batches of 256)",
+                "cached": f"frozen cache after {n_done} frames, {prec} NIF, 1024 spp (8 batches of 128)",
+                "reference_noise_rel_rmse": float(torch.sqrt(R_var.sum() / (R_mean ** 2).sum()))}
+        bias.update(image_stats(X, R_mean, R_var))
+        del X, R_mean, R_var
+
+    # roofline of the dominant kernel kind inside the frame
+    meas, which = peaks()
+    clock = float(meas.get("sm_max_mhz", 2070.0))
+    kinds = {k: v[0] / args.steps for k, v in prof.items()}
+    dom = max(("trace", "nif", "cache"), key=lambda k: kinds[k])
+    rays = int(counts[:cfg.max_depth].sum())
+    queries = int(counts[cfg.max_depth + 1])
+    if dom == "cache":
+        t_c = prof_render["cache"][0]
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock * 1e6 / 1e12
+        achieved = queries * CACHE_FLOP_PER_QUERY / (t_c * 1e-3) / 1e12
+        roof = {"kernel": "k_cache_eval", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "per_unit": f"{CACHE_FLOP_PER_QUERY} FLOP per query x {queries} queries per launch",
+                "peak_note": f"FP32 FFMA derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clock:.0f} MHz"}
+    else:
+        t_tr = prof_render["trace"][0]
+        ops = (OPS_NODE * work["nodes"] + OPS_SPHERE * work["sphere"] + OPS_QUAD * work["quad"] +
+               OPS_TRI * work["triangle"])
+        peak = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6 / 1e12
+        achieved = ops / (t_tr * 1e-3) / 1e12
+        roof = {"kernel": "k_bounce", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
+                "frac": achieved / peak, "traffic": None,
+                "per_unit": f"FP32 ops per node fetch {OPS_NODE}, per triangle test {OPS_TRI}; {work['nodes']} node "
+                            f"fetches and {work['triangle']} triangle tests in the cached render "
+                            f"({CACHE_VERTEX} launches, {t_tr:.3f} ms)",
+                "peak_note": f"FP32 issue rate derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x {clock:.0f} MHz"}
+
+    e2e = None
+    if not args.no_e2e:
+        host_img = torch.empty((W * H, 3), dtype=torch.float32, pin_memory=True)
+        scene_arrays = (sc.sphere, sc.sphere_mat, sc.quad, sc.quad_axis, sc.quad_mat, sc.vert, sc.tri, sc.tri_mat,
+                        sc.mat_type, sc.mat)
+        cache_host = I.cache_init(lo, hi)
+        flat = gc.get_params()
+        pos = 0
+        for Wl, bl in zip(cache_host.W, cache_host.b):
+            Wl[:] = flat[pos:pos + Wl.size].reshape(Wl.shape)
+            pos += Wl.size
+            bl[:] = flat[pos:pos + bl.size]
+            pos += bl.size
+        h2d = sum(x.nbytes for x in scene_arrays) + pt.nif_flat(nif).nbytes + pt.cache_flat(cache_host).nbytes
+        d2h = host_img.numel() * 4
+        n_e2e = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(n_e2e):
+            s2, n2, c2 = pt.Scene(ctx, sc), pt.Nif(ctx, nif), pt.Cache(ctx, cache_host)
+            c2.train_frame(s2, n2, W, H, n_done + i, n_train=N_TRAIN, max_depth=cfg.max_depth,
+                           rec_vertex=CACHE_VERTEX, seed=0, precision=prec)
+            pt.render_cached(ctx, s2, n2, cfg, None, cache=c2, cache_vertex=CACHE_VERTEX, precision=prec,
+                             first_sample=(n_done + i) * spp, out=img)
+            host_img.copy_(img, non_blocking=True)
+            torch.cuda.synchronize()
+            del s2, n2, c2
+        dt = (time.perf_counter() - t0) / n_e2e
+        e2e = {"value": world * cfg.n_slots / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h),
+               "note": "pt_create_scene (host BVH build) + pt_load_nif + pt_create_cache from host arrays, "
+                       "pt_train_cache, pt_render_cached, image copied to pinned host memory, per step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample = oracle_c5_rate(sc, nif, cache0, cfg, args.cpu_s)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        loss_h = losses[:n_done].cpu().numpy()
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec,
+            "data": "synthetic (procedural heightfield and sky, NIF trained on the sky, cache trained online; seeds 0)",
+            "config": {"workload": f"C5: {I.CONFIGS['C5']['desc']}; a step = one frame = pt_train_cache "
+                                   f"({N_TRAIN} training paths, depth {cfg.max_depth}, records at vertex "
+                                   f"{CACHE_VERTEX}) + pt_render_cached ({W}x{H}, {spp} spp, paths end in the cache "
+                                   f"at vertex {CACHE_VERTEX})",
+                       "paths_per_frame": cfg.n_slots, "nif_precision": prec,
+                       "cache": "12 freqs/axis position encoding + direction + normal (78) -> 5x FC-64 ReLU -> FC-3, "
+                                "FP32, Adam lr 1e-2, relative L2",
+                       "l2": "512 MB L2 flush between timed frames (outside the timed events)"},
+            "kernel_ms_per_step": kinds,
+            "frame_split_ms": {"train": {k: v[0] for k, v in prof_train.items()},
+                               "render": {k: v[0] for k, v in prof_render.items()}},
+            "plain_full_depth": plain,
+            "speedup_vs_plain_fp32": plain["fp32_ms"] / ms,
+            "cache_bias": bias,
+            "cache_loss": {"first": float(loss_h[0]), "last10_mean": float(loss_h[-10:].mean())},
+            "rays_per_render": rays, "cache_queries_per_render": queries,
+            "nif_evals_per_render": int(counts[cfg.max_depth]),
+            "scene_build_s": t_build, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": int(sum(v[1] for v in prof.values())), "nif_training": train,
+        }))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -419,7 +742,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["C1", "C2", "C3", "C4"], default="C2")
+    ap.add_argument("--workload", choices=["C1", "C2", "C3", "C4", "C5"], default="C2")
     ap.add_argument("--precision", choices=["bf16", "fp32", "fp8"], default="bf16")
     ap.add_argument("--spp", type=int, default=None, help="override spp (small cases for profiler captures)")
     ap.add_argument("--cpu-s", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
@@ -430,9 +753,12 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the other-precision frames and standalone NIF runs (profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bias", action="store_true", help="C5: skip the bias measurement against the 4096-spp render")
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)
+    if args.workload == "C5":
+        return bench_c5(args)
     return bench_ours(args)
 
 

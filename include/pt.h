@@ -248,7 +248,8 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* scene, const pt_n
 /* Statistics of the last pt_render / pt_render_pixels call on this context
    (valid after pt_check): rays traced per vertex and escapes shaded by the
    NIF.  counts: [max_depth + 1] int64 -> counts[k-1] = rays traced at vertex
-   k, counts[max_depth] = NIF evaluations. */
+   k, counts[max_depth] = NIF evaluations; with n >= max_depth + 2,
+   counts[max_depth + 1] = radiance-cache queries (pt_render_cached). */
 PT_API pt_status pt_last_render_counts(pt_ctx* ctx, int64_t* counts, int32_t n);
 
 /* Traversal work of the last render (valid after pt_check): work[0] BVH

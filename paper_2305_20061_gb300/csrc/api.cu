@@ -97,7 +97,8 @@ constexpr int kMaxDepth = 64;
 constexpr int kCounters = kMaxDepth + 8;
 constexpr int kEscCounter = kMaxDepth + 2;
 constexpr int kCacheCounter = kMaxDepth + 3;
-constexpr int kStats = kMaxDepth + 1 + 4;     // rays per vertex, NIF evaluations, traversal work [4]
+constexpr int kStats = kMaxDepth + 1 + 4 + 1; // rays per vertex, NIF evaluations, traversal work [4], cache queries
+constexpr int kCacheStat = kMaxDepth + 5;
 constexpr int kWorkBase = kMaxDepth + 1;
 
 pt_status fail(pt_ctx* ctx, pt_status st, const std::string& msg)
@@ -1067,7 +1068,9 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
         PT_CUDA(cudaMemsetAsync(ctx->counters, 0, kCounters * sizeof(uint32_t), s));
         bp.chunk_first = (uint64_t)first;
         bp.n_chunk = (uint32_t)n;
-        for (int k = 1; k <= cfg->max_depth; ++k) {
+        // with a cache no path outlives its cache vertex
+        const int k_end = cache ? std::min(cfg->max_depth, cache_vertex) : cfg->max_depth;
+        for (int k = 1; k <= k_end; ++k) {
             bp.k = k;
             bp.qin = ctx->q[(k + 1) & 1];
             bp.qout = ctx->q[k & 1];
@@ -1083,7 +1086,7 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
             PT_CUDA(timed(ctx, PT_KIND_CACHE, s, [&] {
                 return cache_query(cache->d_params, cache->J, cache->L, cache->box, chunk,
                                    ctx->counters + kCacheCounter, ctx->cache_rows, ctx->slot_L, sc->dev.has_emission,
-                                   ctx->d_err, ctx->sm_count, s);
+                                   ctx->d_err, ctx->stats + kCacheStat, ctx->sm_count, s);
             }));
         }
         const float scale = (c == n_chunks - 1) ? (float)(1.0 / cfg->spp) : 1.f;
@@ -1143,11 +1146,12 @@ PT_API pt_status pt_last_render_work(pt_ctx* ctx, int64_t* work, int32_t n)
 PT_API pt_status pt_last_render_counts(pt_ctx* ctx, int64_t* counts, int32_t n)
 {
     if (!ctx || !counts || n < 0) return fail(ctx, PT_EINVAL, "bad argument");
-    std::vector<unsigned long long> h(kMaxDepth + 1);
+    std::vector<unsigned long long> h(kStats);
     PT_CUDA(cudaDeviceSynchronize());
     PT_CUDA(cudaMemcpy(h.data(), ctx->stats, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     const int D = ctx->last_depth;
-    for (int i = 0; i < n; ++i) counts[i] = (i < D) ? (int64_t)h[i] : (i == D ? (int64_t)h[D] : 0);
+    for (int i = 0; i < n; ++i)
+        counts[i] = (i < D) ? (int64_t)h[i] : (i == D ? (int64_t)h[D] : (i == D + 1 ? (int64_t)h[kCacheStat] : 0));
     return PT_OK;
 }
 

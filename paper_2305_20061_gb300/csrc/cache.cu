@@ -61,6 +61,7 @@ struct EvalParams {
     float* slot_L;           // stride 16: path radiance [slot][3]
     int accumulate;
     uint32_t* err;
+    unsigned long long* stats;   // nullable: += queries evaluated
 };
 
 // acc[r][c] += sum_k X[k][4 lane + r] * Wt[k][8 warp + c]
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cache_eval(const EvalParams p)
     }
     const int64_t n = p.n_dev ? min((int64_t)*p.n_dev, p.cap) : p.cap;
     const int64_t n_tiles = (n + kRows - 1) / kRows;
+    if (p.stats && blockIdx.x == 0 && tid == 0) atomicAdd(p.stats, (unsigned long long)n);
     float* A = sm + lay.act_a;
     float* Bf = sm + lay.act_b;
     const int J = p.J;
@@ -207,9 +209,11 @@ cudaError_t cache_eval(const float* params, int J, int L, CacheBox box, int64_t 
 }
 
 cudaError_t cache_query(const float* params, int J, int L, CacheBox box, int64_t cap, const uint32_t* n_dev,
-                        const float* rows, float* slot_L, int accumulate, uint32_t* err, int sm_count, cudaStream_t s)
+                        const float* rows, float* slot_L, int accumulate, uint32_t* err, unsigned long long* stats,
+                        int sm_count, cudaStream_t s)
 {
     EvalParams p = {};
+    p.stats = stats;
     p.params = params; p.J = J; p.L = L; p.in0 = 6 * J + 6; p.box = box;
     p.rows = rows; p.stride = 16; p.cap = cap; p.n_dev = n_dev;
     p.slot_L = slot_L; p.accumulate = accumulate; p.err = err;

@@ -194,7 +194,8 @@ size_t cache_eval_smem_bytes(int in0, int L);
 cudaError_t cache_eval(const float* params, int J, int L, CacheBox box, int64_t n, const float* q, float* out,
                        int sm_count, cudaStream_t s);
 cudaError_t cache_query(const float* params, int J, int L, CacheBox box, int64_t cap, const uint32_t* n_dev,
-                        const float* rows, float* slot_L, int accumulate, uint32_t* err, int sm_count, cudaStream_t s);
+                        const float* rows, float* slot_L, int accumulate, uint32_t* err, unsigned long long* stats,
+                        int sm_count, cudaStream_t s);
 // rebuild the packed FP32 layout and (when present) the tensor-core image from the master weights
 cudaError_t repack_nif_fp32(const float* params, int F, int H, int L, float* packed, cudaStream_t s);
 cudaError_t repack_nif_tc_image(const float* params, unsigned char* image, cudaStream_t s);

@@ -420,12 +420,12 @@ def render_pixels(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderC
 def render_cached(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderCfg, pixels: Optional[torch.Tensor],
                   cache: Optional[Cache] = None, cache_vertex: int = 0, rec_vertex: int = 0, precision: str = "fp32",
                   want_slots: bool = False, want_ids: bool = False, chunk_slots: int = 0, first_sample: int = 0,
-                  stream=None):
+                  out: Optional[torch.Tensor] = None, stream=None):
     """pt_render_cached: (pixel_rgb [n,3], slot_rgb [spp,n,3] or None, records [spp,n,16] or None,
-    hit_ids [spp,n,D] or None)."""
+    hit_ids [spp,n,D] or None).  out (optional): preallocated pixel_rgb."""
     dev = f"cuda:{ctx.device}"
     n = cfg.width * cfg.height if pixels is None else int(pixels.shape[0])
-    pix = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    pix = out if out is not None else torch.empty((n, 3), dtype=torch.float32, device=dev)
     slots = torch.empty((cfg.spp, n, 3), dtype=torch.float32, device=dev) if want_slots else None
     rec = torch.empty((cfg.spp, n, 16), dtype=torch.float32, device=dev) if rec_vertex else None
     ids = torch.empty((cfg.spp, n, cfg.max_depth), dtype=torch.int32, device=dev) if want_ids else None
@@ -437,9 +437,10 @@ def render_cached(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderC
     return pix, slots, rec, ids
 
 
-def last_render_counts(ctx: Context, max_depth: int) -> np.ndarray:
-    out = np.zeros(max_depth + 1, np.int64)
-    ctx._raise(lib().pt_last_render_counts(ctx.h, _np_ptr(out), max_depth + 1))
+def last_render_counts(ctx: Context, max_depth: int, with_cache: bool = False) -> np.ndarray:
+    """Rays traced per vertex, then NIF evaluations (and cache queries with with_cache)."""
+    out = np.zeros(max_depth + 1 + int(with_cache), np.int64)
+    ctx._raise(lib().pt_last_render_counts(ctx.h, _np_ptr(out), len(out)))
     return out
 
 
