@@ -312,11 +312,12 @@ def bench_ours(args):
     trace_ms = prof["trace"][0] / args.steps
 
     # the other precision on the same frame, and the image difference between them
-    other = "fp32" if rprec == "bf16" else "bf16"
+    other = "fp32" if rprec != "fp32" else "bf16"
+    lowp = rprec if rprec != "fp32" else "bf16"
     ms_other, rel_rmse = None, None
     if uses_nif and not args.no_compare:
         ms_other, _ = timed_frames(other, max(2, min(args.steps, 5)))
-        a = pt.render(ctx, scene, gnif, cfg, "bf16", first_sample=first_sample).double()
+        a = pt.render(ctx, scene, gnif, cfg, lowp, first_sample=first_sample).double()
         b = pt.render(ctx, scene, gnif, cfg, "fp32", first_sample=first_sample).double()
         ctx.check()
         rel_rmse = float(torch.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()).item())
@@ -325,7 +326,7 @@ def bench_ours(args):
     nif_alone = {}
     if uses_nif and not args.no_compare:
         uv = torch.from_numpy(I.uniform_uv(1 << 24, seed=1)).to(dev)
-        for prec in ("bf16", "fp32"):
+        for prec in ("bf16", "fp8", "fp32"):
             gnif.eval(uv, prec)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -336,7 +337,7 @@ def bench_ours(args):
             e1.record(stream)
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1) / reps
-            flop = TC_FLOP_PER_EVAL if prec == "bf16" else FLOP_PER_EVAL
+            flop = TC_FLOP_PER_EVAL if prec != "fp32" else FLOP_PER_EVAL
             nif_alone[prec] = {"evals_per_s": (1 << 24) / (t * 1e-3), "ms": t,
                                "tflops": (1 << 24) * flop / (t * 1e-3) / 1e12}
         ctx.check()
@@ -420,7 +421,7 @@ def bench_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16" if rprec == "bf16" and uses_nif else "f32",
+            "vs_baseline": None, "dtype": rprec if uses_nif and rprec != "fp32" else "f32",
             "data": "synthetic (procedural scene" + (" and sky, NIF trained on the sky" if train else "") + "; seeds 0)",
             "config": config_dict(args.workload, cfg, precision, train is not None),
             "rays_per_step": rays, "traversal_work_per_step": work,
@@ -432,7 +433,7 @@ def bench_ours(args):
         if uses_nif:
             line.update({
                 f"{other}_value": world * paths / (ms_other * 1e-3) / 1e6 if ms_other else None,
-                "bf16_vs_fp32_image_rel_rmse": rel_rmse,
+                f"{lowp}_vs_fp32_image_rel_rmse": rel_rmse,
                 "nif_evals_per_step": evals,
                 "nif_evals_per_s_in_render": evals / (nif_ms * 1e-3) if nif_ms > 0 else None,
                 "nif_standalone_2p24": nif_alone, "nif_training": train})

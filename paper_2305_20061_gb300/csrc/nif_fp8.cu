@@ -162,7 +162,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_fp8(const Fp8Params p, int 
                 }
                 if (progressed) {
                     last = global_ns();
-                } else if (global_ns() - last > kWaitBudgetNs) {
+                } else {
+                    __nanosleep(32);   // nothing ready: yield the issue slots to the epilogue warps
+                }
+                if (!progressed && global_ns() - last > kWaitBudgetNs) {
                     atomicOr(p.err, PT_ERR_TIMEOUT);
                     *abort = 1;
                 }

@@ -12,12 +12,13 @@
 //                TMEM lane t, and half h covers accumulator columns
 //                [64h, 64h + 64) and Fourier frequencies [32h, 32h + 32).
 //                They compute the features, and after each MMA read their
-//                accumulator half-row from TMEM, add the bias, apply ReLU
+//                accumulator half-row from TMEM (bias included), apply ReLU
 //                while packing to BF16 and write it back into the slot's
 //                operand buffer in the UMMA SWIZZLE_128B K-major layout.
 //   warp 24      allocates TMEM; lane 0 issues every tcgen05.mma (128x128x16
-//                BF16 -> FP32 for the hidden layers, 128x16x16 for the head)
-//                and commits each layer to the slot's mbarrier.
+//                BF16 -> FP32 for the hidden layers plus one K = 16 step that
+//                adds the bias, 128x16x16 for the head) and commits each
+//                layer to the slot's mbarrier.
 //
 // Three slots in flight let the epilogue of one tile overlap the MMAs of
 // the others.  Every wait is bounded in time: a wait that gives up sets
@@ -48,19 +49,34 @@ constexpr uint32_t kHeadRows = 16;
 constexpr uint32_t kHeadBytes = kHeadRows * kH * 2;  // 4 KB
 constexpr uint32_t kOffW = 0;                        // W1 | W2 | W3
 constexpr uint32_t kOffHead = 3 * kWBytes;           // 98304
-constexpr uint32_t kOffTail = kOffHead + kHeadBytes; // 102400: fp32 b1 b2 b3 [384], b4 [4], B [128], M [12]
+// Hidden-layer biases ride on the tensor core as one more K = 16 step: A is a
+// block of ones (columns 0 and 1), B holds bias = hi + lo in BF16 (columns 0
+// and 1), both K-major without swizzle (core matrices 8 rows x 16 B, K step
+// 128 B, 8-row step 256 B).
+constexpr uint32_t kBiasBytes = kRows * 32;              // 4096 per block
+constexpr uint32_t kBiasLbo = 128, kBiasSbo = 256;
+constexpr uint32_t kOffBias = kOffHead + kHeadBytes;     // 102400: b1 | b2 | b3
+constexpr uint32_t kOffOnes = kOffBias + 3 * kBiasBytes; // 114688
+constexpr uint32_t kOffTail = kOffOnes + kBiasBytes;     // 118784: fp32 b1 b2 b3 [384], b4 [4], B [128], M [12]
 constexpr uint32_t kTailFloats = 3 * kH + 4 + 2 * kF + 12;
-constexpr uint32_t kImageBytes = kOffTail + kTailFloats * 4;  // 104512
-constexpr uint32_t kOffA = 105472;                   // 1024-aligned, three 32 KB activation buffers
+constexpr uint32_t kImageBytes = kOffTail + kTailFloats * 4;  // 120896
+constexpr uint32_t kOffA = 121856;                   // 1024-aligned, three 32 KB activation buffers
 constexpr uint32_t kABytes = kRows * kH * 2;
 constexpr uint32_t kOffBar = kOffA + kSlots * kABytes;  // 203776
 constexpr uint32_t kSmemBytes = kOffBar + 128 + 1024;   // barriers + alignment slack
 
 static_assert(kImageBytes % 16 == 0, "bulk copy size");
+static_assert(kImageBytes <= kOffA && kSmemBytes <= 227 * 1024, "shared-memory budget");
 static_assert(kOffA % 1024 == 0 && kOffHead % 1024 == 0, "swizzle atoms need 1024-byte alignment");
 
 // --- PTX wrappers: tc_ptx.cuh ------------------------------------------------
 using namespace tc;
+
+// byte offset of element (row r, k < 16) of a bias / ones block
+__host__ __device__ constexpr uint32_t bias_elem(uint32_t r, uint32_t k)
+{
+    return (r >> 3) * kBiasSbo + (k >> 3) * kBiasLbo + (r & 7) * 16 + (k & 7) * 2;
+}
 
 // byte offset of the 16-byte chunk holding elements [8c, 8c+8) of row r of a
 // 128-row, 128-column BF16 operand in SWIZZLE_128B K-major form
@@ -170,6 +186,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
                             const uint32_t koff = (kk >> 2) * (kRows * 128) + (kk & 3) * 32;
                             mma_bf16(d, sw128_desc(a_base + koff), sw128_desc(w_base + koff), id_h, kk > 0);
                         }
+                        // + bias: ones x (hi, lo)
+                        mma_bf16(d, plain_desc(sbase + kOffOnes, kBiasLbo, kBiasSbo),
+                                 plain_desc(sbase + kOffBias + stage[s] * kBiasBytes, kBiasLbo, kBiasSbo), id_h, 1);
                     } else {
                         const uint32_t d = tmem + 384 + 32 * s;
 #pragma unroll
@@ -191,7 +210,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
                 }
                 if (progressed) {
                     last = global_ns();
-                } else if (global_ns() - last > kWaitBudgetNs) {
+                } else {
+                    __nanosleep(32);   // nothing ready: yield the issue slots to the epilogue warps
+                }
+                if (!progressed && global_ns() - last > kWaitBudgetNs) {
                     atomicOr(p.err, PT_ERR_TIMEOUT);
                     *abort = 1;
                 }
@@ -271,20 +293,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
                 if (!__all_sync(0xFFFFFFFFu, got)) { ok = false; break; }  // tcgen05.ld needs the whole warp
                 ph ^= 1;
                 tc_fence_after();
-                const float* bias = tail + layer * kH;
 #pragma unroll 1
                 for (int c32 = half * 2; c32 < half * 2 + 2; ++c32) {
                     uint32_t r[32];
                     TMEM_LD32(tmem + lane_base + s * 128 + c32 * 32, r);
                     tmem_wait_ld();
                     uint32_t pk[16];
-                    const uint64_t* b2v = reinterpret_cast<const uint64_t*>(bias + c32 * 32);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        // packed FP32 pair add of the bias, then ReLU while rounding the pair to BF16
-                        const uint64_t sum = add_f32x2(pack_u64(r[2 * j], r[2 * j + 1]), b2v[j]);
-                        pk[j] = pack_relu_bf16(__uint_as_float((uint32_t)sum), __uint_as_float((uint32_t)(sum >> 32)));
-                    }
+                    for (int j = 0; j < 16; ++j)   // the bias is already in the accumulator: ReLU while rounding to BF16
+                        pk[j] = pack_relu_bf16(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         st_shared_v4(a_base + sw128_chunk(row, c32 * 4 + q), pk[4 * q], pk[4 * q + 1],
@@ -356,6 +373,20 @@ bool pack_nif_tc_image(const float* params, int F, int H, int L, std::vector<uns
         const uint16_t b = to_bf16(x);
         std::memcpy(&out[off], &b, 2);
     };
+    auto put_plain = [&](uint32_t off, float x) {
+        const uint16_t b = to_bf16(x);
+        std::memcpy(&out[off], &b, 2);
+    };
+    auto from_bf16 = [](uint16_t b) -> float {
+        const uint32_t u = (uint32_t)b << 16;
+        float x;
+        std::memcpy(&x, &u, 4);
+        return x;
+    };
+    for (uint32_t r = 0; r < kRows; ++r) {
+        put_plain(kOffOnes + bias_elem(r, 0), 1.f);
+        put_plain(kOffOnes + bias_elem(r, 1), 1.f);
+    }
     const float* p = params;
     const float* Bsrc = p;
     p += 2 * F;
@@ -366,7 +397,12 @@ bool pack_nif_tc_image(const float* params, int F, int H, int L, std::vector<uns
             for (int j = 0; j < o; ++j)
                 for (int k = 0; k < in; ++k) put(kOffW + l * kWBytes, kRows, j, k, p[(size_t)j * in + k]);
             p += (size_t)in * o;
-            for (int j = 0; j < o; ++j) tail[l * kH + j] = p[j];
+            for (int j = 0; j < o; ++j) {
+                tail[l * kH + j] = p[j];
+                const float hi = from_bf16(to_bf16(p[j]));
+                put_plain(kOffBias + l * kBiasBytes + bias_elem(j, 0), hi);
+                put_plain(kOffBias + l * kBiasBytes + bias_elem(j, 1), p[j] - hi);
+            }
             p += o;
         } else {
             for (int j = 0; j < 3; ++j)
@@ -422,6 +458,21 @@ __global__ void k_repack_tc(const float* __restrict__ params, unsigned char* __r
         p += o;
     }
     const float* Mp = p;
+    // bias blocks (hi, lo in columns 0, 1) and the block of ones; the rest of those blocks stays zero
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 4 * kRows; idx += gridDim.x * blockDim.x) {
+        const int l = idx / kRows, r = idx % kRows;
+        unsigned short* hi = reinterpret_cast<unsigned short*>(image + kOffBias + l * kBiasBytes + bias_elem(r, 0));
+        unsigned short* lo = reinterpret_cast<unsigned short*>(image + kOffBias + l * kBiasBytes + bias_elem(r, 1));
+        if (l < 3) {
+            const float x = b[l][r];
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            *hi = __bfloat16_as_ushort(h);
+            *lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+        } else {   // l == 3: the ones block directly follows the bias blocks
+            *hi = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
+            *lo = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
+        }
+    }
     const int n_hidden = 3 * kH * kH, n_head = kHeadRows * kH;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_hidden + n_head + (int)kTailFloats;
          idx += gridDim.x * blockDim.x) {

@@ -37,6 +37,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
+// try_wait with a suspend-time hint: a waiting thread sleeps (no issue slots)
+// until the phase completes or about hint_ns nanoseconds pass
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
 // non-blocking probe of a phase (used by the MMA issuer's event loop)
 __device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity)
 {
@@ -58,6 +72,7 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 constexpr uint64_t kWaitBudgetNs = 2000000000ull;  // 2 s per wait
+constexpr uint32_t kSleepHintNs = 20000;            // suspend-time hint of a blocked wait
 
 // Bounded wait for `parity` on an mbarrier; false on timeout or abort.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t* err)
@@ -65,7 +80,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_sleep(bar, parity, kSleepHintNs)) return true;
         if (*abort) return false;
         if (global_ns() - t0 > kWaitBudgetNs) {
             atomicOr(err, PT_ERR_TIMEOUT);
@@ -90,6 +105,13 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
 {
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(1024u >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+// K-major operand without swizzle: 8-row x 16-byte core matrices, lbo = byte
+// step between core matrices along K, sbo = byte step between 8-row groups
+__device__ __forceinline__ uint64_t plain_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
 }
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
