@@ -107,7 +107,7 @@ struct TcParams {
     unsigned long long* stats;
 };
 
-__global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mode)
+__global__ void __maxnreg__(80) k_nif_tc(const TcParams p, int mode)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -264,19 +264,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
             const uint32_t slot = in.slot;
             // Fourier features [sin 2 pi (Bx)_i, cos 2 pi (Bx)_i]: phase reduced to one turn in FP32,
             // then the hardware sine / cosine (the result is rounded to BF16)
+            const uint64_t uu = pack_f32x2(u, u), vv = pack_f32x2(v, v);
+            const uint64_t two_pi = pack_f32x2(6.28318530717958648f, 6.28318530717958648f);
 #pragma unroll 1
             for (int c8 = half * 4; c8 < half * 4 + 4; ++c8) {
                 uint32_t sp[4], cp[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
+                    // frequencies f, f + 1 in packed FP32 pairs: t = B0 u + B1 v, r = t - rint(t)
+                    const int f = c8 * 8 + 2 * j;
+                    const float4 bq = *reinterpret_cast<const float4*>(Bm + 2 * f);   // B0 B1 of f, f + 1
+                    const uint64_t t = fma_f32x2(pack_f32x2(bq.x, bq.z), uu, mul_f32x2(pack_f32x2(bq.y, bq.w), vv));
+                    const uint64_t r = sub_f32x2(t, pack_f32x2(rintf(lo_f32(t)), rintf(hi_f32(t))));
+                    const uint64_t a = mul_f32x2(r, two_pi);
                     float sv[2], cv[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int f = c8 * 8 + 2 * j + h;
-                        const float t = fmaf(Bm[2 * f], u, Bm[2 * f + 1] * v);
-                        const float r = t - rintf(t);
-                        __sincosf(6.28318530717958648f * r, &sv[h], &cv[h]);
-                    }
+                    __sincosf(lo_f32(a), &sv[0], &cv[0]);
+                    __sincosf(hi_f32(a), &sv[1], &cv[1]);
                     sp[j] = pack_bf16(sv[0], sv[1]);
                     cp[j] = pack_bf16(cv[0], cv[1]);
                 }
@@ -293,20 +296,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
                 if (!__all_sync(0xFFFFFFFFu, got)) { ok = false; break; }  // tcgen05.ld needs the whole warp
                 ph ^= 1;
                 tc_fence_after();
-#pragma unroll 1
-                for (int c32 = half * 2; c32 < half * 2 + 2; ++c32) {
-                    uint32_t r[32];
-                    TMEM_LD32(tmem + lane_base + s * 128 + c32 * 32, r);
-                    tmem_wait_ld();
-                    uint32_t pk[16];
+                // this half-row's 64 accumulator columns in four groups of 16, the TMEM load of
+                // group g + 1 in flight while group g is packed (the bias is already in the
+                // accumulator: ReLU while rounding to BF16) and stored
+                const uint32_t tcol = tmem + lane_base + s * 128 + half * 64;
+                uint32_t ra[16], rb[16];
+                auto put16 = [&](const uint32_t (&x)[16], int g) {
+                    uint32_t pk[8];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)   // the bias is already in the accumulator: ReLU while rounding to BF16
-                        pk[j] = pack_relu_bf16(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        st_shared_v4(a_base + sw128_chunk(row, c32 * 4 + q), pk[4 * q], pk[4 * q + 1],
-                                     pk[4 * q + 2], pk[4 * q + 3]);
-                }
+                    for (int j = 0; j < 8; ++j) pk[j] = pack_relu_bf16(__uint_as_float(x[2 * j]), __uint_as_float(x[2 * j + 1]));
+                    const int c8 = half * 8 + 2 * g;
+                    st_shared_v4(a_base + sw128_chunk(row, c8), pk[0], pk[1], pk[2], pk[3]);
+                    st_shared_v4(a_base + sw128_chunk(row, c8 + 1), pk[4], pk[5], pk[6], pk[7]);
+                };
+                tmem_ld16(tcol, ra);
+                tmem_wait_ld();
+                tmem_ld16(tcol + 16, rb);
+                put16(ra, 0);
+                tmem_wait_ld();
+                tmem_ld16(tcol + 32, ra);
+                put16(rb, 1);
+                tmem_wait_ld();
+                tmem_ld16(tcol + 48, rb);
+                put16(ra, 2);
+                tmem_wait_ld();
+                put16(rb, 3);
                 tc_fence_before();
                 fence_proxy_async();
                 mbar_arrive(bar_a + 8 * s);
