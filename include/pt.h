@@ -376,7 +376,7 @@ PT_API pt_status pt_render_cached(pt_ctx* ctx, const pt_scene* scene, const pt_n
 /* ------------------------------------------------------------------------ */
 
 /* Same image as pt_render with precision PT_FP32, but every byte of wavefront
-   scratch comes from one fixed array compiled into the library (about 41 MiB
+   scratch comes from one fixed array compiled into the library (about 43 MiB
    per GPU, held until the process exits); the call makes no cudaMalloc,
    cudaFree or other allocating call.  Limits: at most 262144 pixels per
    frame (one sample of the frame must fit the array) and the FP32 network;

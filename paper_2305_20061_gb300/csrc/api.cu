@@ -27,6 +27,7 @@ struct pt_ctx {
     float* slot_L = nullptr;
     uint32_t* counters = nullptr;          // [kCounters]
     unsigned long long* stats = nullptr;   // [kMaxDepth + 1]
+    int2* hits = nullptr;                  // traversal results [chunk_cap]
     float* cache_rows = nullptr;           // radiance-cache query rows [cache_cap][16]
     uint32_t cache_cap = 0;
     int last_depth = 0;
@@ -97,6 +98,7 @@ constexpr int kMaxDepth = 64;
 constexpr int kCounters = kMaxDepth + 8;
 constexpr int kEscCounter = kMaxDepth + 2;
 constexpr int kCacheCounter = kMaxDepth + 3;
+constexpr int kFetchCounter = kMaxDepth + 4;
 constexpr int kStats = kMaxDepth + 1 + 4 + 1; // rays per vertex, NIF evaluations, traversal work [4], cache queries
 constexpr int kCacheStat = kMaxDepth + 5;
 constexpr int kWorkBase = kMaxDepth + 1;
@@ -134,6 +136,7 @@ void free_scratch(pt_ctx* ctx)
     }
     cudaFree(ctx->esc); ctx->esc = nullptr;
     cudaFree(ctx->slot_L); ctx->slot_L = nullptr;
+    cudaFree(ctx->hits); ctx->hits = nullptr;
     ctx->chunk_cap = 0;
     cudaFree(ctx->cache_rows); ctx->cache_rows = nullptr;
     ctx->cache_cap = 0;
@@ -149,7 +152,7 @@ pt_status ensure_scratch(pt_ctx* ctx, uint32_t chunk)
             return fail(ctx, PT_ENOMEM, "wavefront queue allocation failed");
         }
     }
-    if (dalloc(&ctx->esc, chunk) || dalloc(&ctx->slot_L, (size_t)chunk * 3)) {
+    if (dalloc(&ctx->esc, chunk) || dalloc(&ctx->slot_L, (size_t)chunk * 3) || dalloc(&ctx->hits, chunk)) {
         free_scratch(ctx);
         return fail(ctx, PT_ENOMEM, "escape queue allocation failed");
     }
@@ -1061,6 +1064,8 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
     bp.cache_count = ctx->counters + kCacheCounter;
     bp.rec_vertex = rec_vertex;
     bp.rec = d_rec;
+    bp.hits = ctx->hits;
+    bp.fetch = ctx->counters + kFetchCounter;
     const int64_t n_chunks = (n_slots + chunk - 1) / chunk;
     for (int64_t c = 0; c < n_chunks; ++c) {
         const int64_t first = c * chunk;

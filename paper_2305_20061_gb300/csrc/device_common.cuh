@@ -224,61 +224,91 @@ __device__ __forceinline__ float slab(float3 lo, float3 ext, float3 o, float3 in
 
 __device__ __forceinline__ float safe_inv(float d) { return 1.f / (fabsf(d) > 1e-30f ? d : copysignf(1e-30f, d)); }
 
+// Resumable closest-hit traversal: trav_init sets up a ray, trav_step
+// visits one node (both children's boxes, leaf children intersected right
+// away, near child first, far child stacked with its entry distance).  Both
+// return true once the ray's closest hit is final.
+struct Trav {
+    float3 o, d, inv;
+    TriRay tr;
+    Hit h;
+    uint32_t cur, iters;
+    int sp;
+};
+
+__device__ __forceinline__ bool trav_init(const DevScene& sc, float3 o, float3 d, Trav& s, Work& w)
+{
+    s.o = o;
+    s.d = d;
+    s.h = Hit{INFINITY, -1};
+    s.cur = sc.root;
+    s.sp = 0;
+    s.iters = 0;
+    if (s.cur == kEmptyRef) return true;
+    if (sc.nT) s.tr = tri_setup(o, d);  // only triangles use the sheared ray
+    if (s.cur & kLeafBit) {
+        isect_prim(sc, s.cur & ~kLeafBit, o, d, s.tr, s.h.t, s.h.prim, w);
+        return true;
+    }
+    s.inv = f3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+    return false;
+}
+
+__device__ __forceinline__ bool trav_step(const DevScene& sc, Trav& s, uint32_t* stack_ref, float* stack_t,
+                                          uint32_t* err, Work& w)
+{
+    if (++s.iters > kIterCap) { atomicOr(err, PT_ERR_ITER_CAP); return true; }
+    if (s.cur >= sc.n_nodes) { atomicOr(err, PT_ERR_BAD_NODE); return true; }  // never fetch outside the node array
+    const uint4* np = sc.nodes + 3 * (size_t)s.cur;
+    const uint4 q0 = __ldg(np), q1 = __ldg(np + 1), q2 = __ldg(np + 2);
+    const float3 lo_l = f3(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z));
+    const float3 lo_r = f3(__uint_as_float(q0.w), __uint_as_float(q1.x), __uint_as_float(q1.y));
+    const float3 ext_l = f3(half_bits_to_float(q1.z & 0xFFFFu), half_bits_to_float(q1.z >> 16),
+                            half_bits_to_float(q1.w & 0xFFFFu));
+    const float3 ext_r = f3(half_bits_to_float(q1.w >> 16), half_bits_to_float(q2.x & 0xFFFFu),
+                            half_bits_to_float(q2.x >> 16));
+    const uint32_t cl = q2.y, cr = q2.z;
+    float tl = slab(lo_l, ext_l, s.o, s.inv, s.h.t);
+    float trr = slab(lo_r, ext_r, s.o, s.inv, s.h.t);
+    ++w.nodes;
+    // leaf children are intersected right away
+    if ((cl & kLeafBit) && tl < INFINITY) {
+        isect_prim(sc, cl & ~kLeafBit, s.o, s.d, s.tr, s.h.t, s.h.prim, w);
+        tl = INFINITY;
+    }
+    if ((cr & kLeafBit) && trr < INFINITY) {
+        isect_prim(sc, cr & ~kLeafBit, s.o, s.d, s.tr, s.h.t, s.h.prim, w);
+        trr = INFINITY;
+    }
+    // a child is entered only if its box was hit (finite entry) no later than the best hit
+    const bool hl = tl < INFINITY && tl <= s.h.t, hr = trr < INFINITY && trr <= s.h.t;
+    if (hl && hr) {
+        const bool left_first = tl <= trr;
+        if (s.sp >= kStackSize) { atomicOr(err, PT_ERR_STACK_OVERFLOW); return true; }
+        stack_ref[s.sp] = left_first ? cr : cl;
+        stack_t[s.sp] = left_first ? trr : tl;
+        ++s.sp;
+        s.cur = left_first ? cl : cr;
+        return false;
+    }
+    if (hl) { s.cur = cl; return false; }
+    if (hr) { s.cur = cr; return false; }
+    while (s.sp > 0) {
+        --s.sp;
+        if (stack_t[s.sp] <= s.h.t) { s.cur = stack_ref[s.sp]; return false; }
+    }
+    return true;
+}
+
 __device__ __forceinline__ Hit trace_closest(const DevScene& sc, float3 o, float3 d, uint32_t* err, Work& w)
 {
-    Hit h{INFINITY, -1};
-    uint32_t cur = sc.root;
-    if (cur == kEmptyRef) return h;
-    TriRay tr;
-    if (sc.nT) tr = tri_setup(o, d);  // only triangles use the sheared ray
-    if (cur & kLeafBit) {
-        isect_prim(sc, cur & ~kLeafBit, o, d, tr, h.t, h.prim, w);
-        return h;
-    }
-    const float3 inv = f3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+    Trav s;
+    if (trav_init(sc, o, d, s, w)) return s.h;
     uint32_t stack_ref[kStackSize];
     float stack_t[kStackSize];
-    int sp = 0;
-    uint32_t iters = 0;
-    while (true) {
-        if (++iters > kIterCap) { atomicOr(err, PT_ERR_ITER_CAP); break; }
-        if (cur >= sc.n_nodes) { atomicOr(err, PT_ERR_BAD_NODE); break; }  // never fetch outside the node array
-        const uint4* np = sc.nodes + 3 * (size_t)cur;
-        const uint4 q0 = __ldg(np), q1 = __ldg(np + 1), q2 = __ldg(np + 2);
-        const float3 lo_l = f3(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z));
-        const float3 lo_r = f3(__uint_as_float(q0.w), __uint_as_float(q1.x), __uint_as_float(q1.y));
-        const float3 ext_l = f3(half_bits_to_float(q1.z & 0xFFFFu), half_bits_to_float(q1.z >> 16),
-                                half_bits_to_float(q1.w & 0xFFFFu));
-        const float3 ext_r = f3(half_bits_to_float(q1.w >> 16), half_bits_to_float(q2.x & 0xFFFFu),
-                                half_bits_to_float(q2.x >> 16));
-        const uint32_t cl = q2.y, cr = q2.z;
-        float tl = slab(lo_l, ext_l, o, inv, h.t);
-        float trr = slab(lo_r, ext_r, o, inv, h.t);
-        ++w.nodes;
-        // leaf children are intersected right away
-        if ((cl & kLeafBit) && tl < INFINITY) { isect_prim(sc, cl & ~kLeafBit, o, d, tr, h.t, h.prim, w); tl = INFINITY; }
-        if ((cr & kLeafBit) && trr < INFINITY) { isect_prim(sc, cr & ~kLeafBit, o, d, tr, h.t, h.prim, w); trr = INFINITY; }
-        // a child is entered only if its box was hit (finite entry) no later than the best hit
-        const bool hl = tl < INFINITY && tl <= h.t, hr = trr < INFINITY && trr <= h.t;
-        if (hl && hr) {
-            const bool left_first = tl <= trr;
-            if (sp >= kStackSize) { atomicOr(err, PT_ERR_STACK_OVERFLOW); break; }
-            stack_ref[sp] = left_first ? cr : cl;
-            stack_t[sp] = left_first ? trr : tl;
-            ++sp;
-            cur = left_first ? cl : cr;
-            continue;
-        }
-        if (hl) { cur = cl; continue; }
-        if (hr) { cur = cr; continue; }
-        bool found = false;
-        while (sp > 0) {
-            --sp;
-            if (stack_t[sp] <= h.t) { cur = stack_ref[sp]; found = true; break; }
-        }
-        if (!found) break;
+    while (!trav_step(sc, s, stack_ref, stack_t, err, w)) {
     }
-    return h;
+    return s.h;
 }
 
 }  // namespace ptk

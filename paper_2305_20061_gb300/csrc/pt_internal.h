@@ -97,6 +97,9 @@ struct BounceParams {
     // rec [global slot][16] (the caller clears the valid words beforehand)
     int32_t rec_vertex;
     float* rec;
+    // traversal results handed from k_trace to the shading kernel: (t bits, primitive) per queue entry
+    int2* hits;
+    uint32_t* fetch;        // ray-index claim counter of k_trace (zero before the launch)
 };
 
 // NIF parameters on the device.

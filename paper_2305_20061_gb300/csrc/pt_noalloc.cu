@@ -29,8 +29,8 @@ namespace {
 constexpr uint32_t kMaxSlots = 1u << 18;   // paths per chunk; the frame must have <= this many pixels
 constexpr int kMaxDepthNA = 64;
 constexpr size_t kHeaderBytes = 2048;      // counters (128 x u32), stats (65 x u64), error word
-constexpr size_t kBytesPerSlot = 2 * 4 * sizeof(float4) + sizeof(EscapeRec) + 3 * sizeof(float);  // 164
-constexpr size_t kScratchBytes = kHeaderBytes + (size_t)kMaxSlots * kBytesPerSlot;            // ~41 MiB
+constexpr size_t kBytesPerSlot = 2 * 4 * sizeof(float4) + sizeof(EscapeRec) + sizeof(int2) + 3 * sizeof(float);  // 172
+constexpr size_t kScratchBytes = kHeaderBytes + (size_t)kMaxSlots * kBytesPerSlot;            // ~43 MiB
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -91,6 +91,7 @@ extern "C" PT_API pt_status pt_render_noalloc(const pt_scene* scene, const pt_ni
         qq.L = reinterpret_cast<float4*>(p); p += (size_t)kMaxSlots * sizeof(float4);
     }
     EscapeRec* esc = reinterpret_cast<EscapeRec*>(p); p += (size_t)kMaxSlots * sizeof(EscapeRec);
+    int2* hits = reinterpret_cast<int2*>(p); p += (size_t)kMaxSlots * sizeof(int2);
     float* slot_L = reinterpret_cast<float*>(p);
 
     int sm_count = 0;
@@ -118,6 +119,8 @@ extern "C" PT_API pt_status pt_render_noalloc(const pt_scene* scene, const pt_ni
     bp.err = err;
     bp.stats = stats;
     bp.cap = (uint32_t)chunk;
+    bp.hits = hits;
+    bp.fetch = counters + kMaxDepthNA + 4;
     const int64_t n_chunks = (n_slots + chunk - 1) / chunk;
     for (int64_t c = 0; c < n_chunks; ++c) {
         const int64_t first = c * chunk;

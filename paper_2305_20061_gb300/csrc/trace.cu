@@ -148,7 +148,97 @@ __device__ __forceinline__ void store_L(float* slot_L, uint32_t slot, float3 L, 
     slot_L[3 * (size_t)slot + 2] = L.z;
 }
 
-// One wavefront step at vertex k for every ray of the input queue.
+// Closest hits of every ray of the input queue (vertex k) into p.hits.
+// Persistent warps keep their lanes busy: whenever at least kRefillMin lanes
+// have finished, the idle lanes take the next ray indices from a range the
+// warp claimed with one atomic (kFetchRange indices at a time), so a warp no
+// longer waits for its slowest ray before starting new ones.
+#ifndef PT_TRACE_REFILL_MIN
+#define PT_TRACE_REFILL_MIN 12
+#endif
+#ifndef PT_TRACE_STEPS
+#define PT_TRACE_STEPS 3
+#endif
+constexpr uint32_t kFetchRange = 128;
+constexpr int kRefillMin = PT_TRACE_REFILL_MIN;
+constexpr int kStepsPerCheck = PT_TRACE_STEPS;
+
+__global__ void __launch_bounds__(256, 4) k_trace(const BounceParams p)
+{
+    const uint32_t count = (p.k == 1) ? p.n_chunk : min(*p.count_in, p.cap);
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned lanes_below = (1u << lane) - 1u;
+    Work work;
+    Trav t;
+    uint32_t stack_ref[kStackSize];
+    float stack_t[kStackSize];
+    bool live = false, exhausted = false;
+    uint32_t ri = 0;
+    uint32_t rnext = 0, rend = 0;   // the warp's claimed index range (warp-uniform)
+    while (true) {
+        const unsigned idle = __ballot_sync(0xFFFFFFFFu, !live);
+        if (idle && !exhausted && (__popc(idle) >= kRefillMin || idle == 0xFFFFFFFFu)) {
+            const uint32_t n = __popc(idle), rank = __popc(idle & lanes_below);
+            const uint32_t avail = rend - rnext;
+            uint32_t idx = rnext + rank;
+            if (avail < n) {
+                uint32_t nb = 0;
+                if (lane == 0) nb = atomicAdd(p.fetch, kFetchRange);
+                nb = __shfl_sync(0xFFFFFFFFu, nb, 0);
+                if (rank >= avail) idx = nb + (rank - avail);
+                rnext = nb + (n - avail);
+                rend = nb + kFetchRange;
+            } else {
+                rnext += n;
+            }
+            exhausted = rnext >= count;   // claims only grow: nothing below count is left for this warp
+            if (!live && idx < count) {
+                float3 o, d;
+                if (p.k == 1) {
+                    uint32_t pix, smp;
+                    slot_to_pixel(p, idx, pix, smp);
+                    const uint4 w = philox4x32_10(make_uint4(pix, smp, 0u, 0u), p.seed, 0u);
+                    o = f3(p.sc.eye[0], p.sc.eye[1], p.sc.eye[2]);
+                    d = camera_dir(p.sc, p.W, p.H, pix, u01(w.x), u01(w.y));
+                } else {
+                    const float4 o4 = p.qin.o[idx], d4 = p.qin.d[idx];
+                    o = f3(o4.x, o4.y, o4.z);
+                    d = f3(d4.x, d4.y, d4.z);
+                }
+                ri = idx;
+                if (trav_init(p.sc, o, d, t, work)) p.hits[ri] = make_int2(__float_as_int(t.h.t), t.h.prim);
+                else live = true;
+            }
+        }
+        if (!__any_sync(0xFFFFFFFFu, live)) {
+            if (exhausted) break;
+            continue;
+        }
+#pragma unroll 1
+        for (int st = 0; st < kStepsPerCheck; ++st) {
+            if (live && trav_step(p.sc, t, stack_ref, stack_t, p.err, work)) {
+                p.hits[ri] = make_int2(__float_as_int(t.h.t), t.h.prim);
+                live = false;
+            }
+        }
+    }
+    // traversal work, one atomic per warp
+    for (int off = 16; off > 0; off >>= 1) {
+        work.nodes += __shfl_down_sync(0xFFFFFFFFu, work.nodes, off);
+        work.sph += __shfl_down_sync(0xFFFFFFFFu, work.sph, off);
+        work.quad += __shfl_down_sync(0xFFFFFFFFu, work.quad, off);
+        work.tri += __shfl_down_sync(0xFFFFFFFFu, work.tri, off);
+    }
+    if (lane == 0 && p.work && work.nodes + work.sph + work.quad + work.tri) {
+        atomicAdd(&p.work[0], (unsigned long long)work.nodes);
+        atomicAdd(&p.work[1], (unsigned long long)work.sph);
+        atomicAdd(&p.work[2], (unsigned long long)work.quad);
+        atomicAdd(&p.work[3], (unsigned long long)work.tri);
+    }
+}
+
+// One wavefront step at vertex k for every ray of the input queue: shading of
+// the hits k_trace found, next-bounce sampling and compaction.
 __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
 {
     const uint32_t count = (p.k == 1) ? p.n_chunk : min(*p.count_in, p.cap);  // counters may pass cap on overflow
@@ -156,7 +246,6 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     uint32_t traced = 0;
-    Work work;
     for (uint32_t base = warp * 32; base < count; base += n_warps * 32) {
         const uint32_t i = base + lane;
         const bool active = i < count;
@@ -190,7 +279,8 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
         float eu = 0.f, ev = 0.f;
         if (active) {
             ++traced;
-            const Hit h = trace_closest(p.sc, s.o, s.d, p.err, work);
+            const int2 hv = p.hits[i];
+            const Hit h{__int_as_float(hv.x), hv.y};
             if (p.hit_ids) p.hit_ids[(p.chunk_first + s.slot) * (uint64_t)p.max_depth + (p.k - 1)] = h.prim;
             if (h.prim < 0) {
                 if (p.sc.env_is_nif) {
@@ -292,21 +382,11 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
             }
         }
     }
-    // per-vertex ray count and traversal work, one atomic per warp
-    for (int off = 16; off > 0; off >>= 1) {
-        traced += __shfl_down_sync(0xFFFFFFFFu, traced, off);
-        work.nodes += __shfl_down_sync(0xFFFFFFFFu, work.nodes, off);
-        work.sph += __shfl_down_sync(0xFFFFFFFFu, work.sph, off);
-        work.quad += __shfl_down_sync(0xFFFFFFFFu, work.quad, off);
-        work.tri += __shfl_down_sync(0xFFFFFFFFu, work.tri, off);
-    }
+    // k_trace of this vertex has finished: its claim counter starts the next vertex at zero
+    if (blockIdx.x == 0 && threadIdx.x == 0) *p.fetch = 0;
+    // per-vertex ray count, one atomic per warp
+    for (int off = 16; off > 0; off >>= 1) traced += __shfl_down_sync(0xFFFFFFFFu, traced, off);
     if (lane == 0 && traced) atomicAdd(&p.stats[p.k - 1], (unsigned long long)traced);
-    if (lane == 0 && p.work && traced) {
-        atomicAdd(&p.work[0], (unsigned long long)work.nodes);
-        atomicAdd(&p.work[1], (unsigned long long)work.sph);
-        atomicAdd(&p.work[2], (unsigned long long)work.quad);
-        atomicAdd(&p.work[3], (unsigned long long)work.tri);
-    }
 }
 
 // image[i] (+)= sum over the chunk's samples in sample order; scaled at the end
@@ -379,7 +459,8 @@ int grid_for(int64_t n, int block, int sm_count, int per_sm)
 
 cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s)
 {
-    // persistent grid: 8 blocks of 256 threads per SM, grid-stride over the queue
+    // traversal: persistent, 4 resident blocks of 256 threads per SM; shading: grid-stride over the queue
+    k_trace<<<sm_count * 4, 256, 0, s>>>(p);
     k_bounce<<<sm_count * 8, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
