@@ -159,7 +159,9 @@ __device__ __forceinline__ void store_L(float* slot_L, uint32_t slot, float3 L, 
 #ifndef PT_TRACE_STEPS
 #define PT_TRACE_STEPS 3
 #endif
-constexpr uint32_t kFetchRange = 128;
+#ifndef PT_TRACE_RANGE_DIV
+#define PT_TRACE_RANGE_DIV 4096
+#endif
 constexpr int kRefillMin = PT_TRACE_REFILL_MIN;
 constexpr int kStepsPerCheck = PT_TRACE_STEPS;
 
@@ -168,6 +170,11 @@ __global__ void __launch_bounds__(256, 4) k_trace(const BounceParams p)
     const uint32_t count = (p.k == 1) ? p.n_chunk : min(*p.count_in, p.cap);
     const uint32_t lane = threadIdx.x & 31;
     const unsigned lanes_below = (1u << lane) - 1u;
+    // indices claimed per atomic: 128 when every warp has many rays, down to 32 for short queues so that
+    // the work still spreads over all warps
+    const uint32_t n_warps = gridDim.x * (blockDim.x >> 5);
+    const uint32_t per_warp = count / n_warps;
+    const uint32_t kFetchRange = per_warp >= PT_TRACE_RANGE_DIV ? 128u : (per_warp >= PT_TRACE_RANGE_DIV / 4 ? 64u : 32u);
     Work work;
     Trav t;
     uint32_t stack_ref[kStackSize];

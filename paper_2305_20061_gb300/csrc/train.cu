@@ -23,26 +23,37 @@ constexpr int kT = 128;           // rows per tile == threads per CTA
 constexpr int kD = 128;           // padded width
 constexpr size_t kGemmSmem = 2 * kD * kD * sizeof(float);
 
-// thread -> (4 rows, 32 columns) of a 128 x 128 output tile
+// Output tiles of MT rows x NT columns computed by the 128 threads of a CTA:
+// MT / 4 row groups of 4 rows, the remaining thread index picks a group of
+// NT / (128 / (MT / 4)) columns.  Row groups are spread within a warp so that
+// each operand read is a broadcast or a conflict-free float4.
+template <int MT, int NT>
 struct TileMap {
+    static constexpr int kRG = MT / 4;             // row groups
+    static constexpr int kOG = kT / kRG;           // column groups
+    static constexpr int kC = NT / kOG;            // columns per thread
+    static_assert(kC % 4 == 0 && kRG % 4 == 0, "tile shape");
     int rg, og;
     __device__ TileMap()
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        rg = warp * 8 + (lane & 7);
-        og = lane >> 3;
+        rg = warp * (kRG / 4) + (lane % (kRG / 4));
+        og = lane / (kRG / 4);
     }
 };
 
-// acc[r][j] += sum_k As[k][4 rg + r] * Bs[k][32 og + j]  (As: [k][row], Bs: [k][col])
-__device__ __forceinline__ void tile_mma(const float* As, const float* Bs, const TileMap& m, float acc[4][32])
+// acc[r][c] += sum_{k < K} As[k][4 rg + r] * Bs[k][kC og + c]  (As: [k][MT], Bs: [k][NT])
+template <int MT, int NT>
+__device__ __forceinline__ void tile_mma(const float* As, const float* Bs, int K, const TileMap<MT, NT>& m,
+                                         float (&acc)[4][TileMap<MT, NT>::kC])
 {
+    constexpr int C = TileMap<MT, NT>::kC;
 #pragma unroll 2
-    for (int k = 0; k < kD; ++k) {
-        const float4 a = *reinterpret_cast<const float4*>(&As[k * kD + 4 * m.rg]);
-        const float4* brow = reinterpret_cast<const float4*>(&Bs[k * kD + 32 * m.og]);
+    for (int k = 0; k < K; ++k) {
+        const float4 a = *reinterpret_cast<const float4*>(&As[k * MT + 4 * m.rg]);
+        const float4* brow = reinterpret_cast<const float4*>(&Bs[k * NT + C * m.og]);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < C / 4; ++q) {
             const float4 b = brow[q];
             const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
@@ -56,21 +67,27 @@ __device__ __forceinline__ void tile_mma(const float* As, const float* Bs, const
     }
 }
 
-// rows [tile*128, tile*128+128) of a [B][128] matrix -> smem [k][row] (zeros past B)
-__device__ __forceinline__ void load_rows_transposed(float* S, const float* __restrict__ X, int64_t tile, int64_t B)
+// columns [0, K) of rows [tile*128, tile*128+128) of a [B][128] matrix -> smem [k][row] (zeros past B)
+__device__ __forceinline__ void load_rows_transposed(float* S, const float* __restrict__ X, int64_t tile, int64_t B,
+                                                     int K)
 {
     const int r = threadIdx.x;
     const int64_t g = tile * kT + r;
     const float4* src = reinterpret_cast<const float4*>(X + g * kD);
 #pragma unroll 4
-    for (int q = 0; q < kD / 4; ++q) {
+    for (int q = 0; q < K / 4; ++q) {
         const float4 v = g < B ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-        S[(4 * q + 0) * kD + r] = v.x;
-        S[(4 * q + 1) * kD + r] = v.y;
-        S[(4 * q + 2) * kD + r] = v.z;
-        S[(4 * q + 3) * kD + r] = v.w;
+        S[(4 * q + 0) * kT + r] = v.x;
+        S[(4 * q + 1) * kT + r] = v.y;
+        S[(4 * q + 2) * kT + r] = v.z;
+        S[(4 * q + 3) * kT + r] = v.w;
     }
 }
+
+// padded width (64 or 128) of a layer dimension
+inline int pad_width(int n) { return n <= 64 ? 64 : 128; }
+// reduction length rounded up to a multiple of 4 (the float4 row loads)
+inline int pad_k(int n) { return (n + 3) & ~3; }
 
 // ---------------------------------------------------------------------------
 // training inputs: Philox key (seed, 1), counter (i, step, 0, 0) -> (u, v);
@@ -117,44 +134,45 @@ __global__ void k_train_features(int64_t B, const float* __restrict__ uv, const 
     }
 }
 
-// Xout = relu(Xin W^T + b); W is [out][in] row-major (PyTorch layout).
-// n_dev (nullable): live row count on the device, at most B.
-__global__ void __launch_bounds__(kT, 1) k_layer_fwd(int64_t B, const uint32_t* __restrict__ n_dev,
-                                                     const float* __restrict__ Xin, float* __restrict__ Xout,
+// Xout = relu(Xin W^T + b) for columns [0, NT); W is [out][in] row-major
+// (PyTorch layout); the reduction runs over K >= in padded columns of Xin.
+template <int NT>
+__global__ void __launch_bounds__(kT, 1) k_layer_fwd(int64_t B, const float* __restrict__ Xin, float* __restrict__ Xout,
                                                      const float* __restrict__ W, const float* __restrict__ b, int in,
-                                                     int out)
+                                                     int out, int K)
 {
-    if (n_dev) B = min((int64_t)*n_dev, B);
     extern __shared__ float4 smem4[];
     float* Ws = reinterpret_cast<float*>(smem4);   // [k][j] = W[j][k]
-    float* Xs = Ws + kD * kD;                       // [k][row]
-    for (int idx = threadIdx.x; idx < kD * kD; idx += kT) {
-        const int j = idx / kD, k = idx % kD;
-        Ws[k * kD + j] = (j < out && k < in) ? W[(size_t)j * in + k] : 0.f;
+    float* Xs = Ws + K * NT;                        // [k][row]
+    for (int idx = threadIdx.x; idx < K * NT; idx += kT) {
+        const int k = idx / NT, j = idx % NT;
+        Ws[idx] = (j < out && k < in) ? W[(size_t)j * in + k] : 0.f;
     }
-    const TileMap m;
+    using Map = TileMap<kT, NT>;
+    constexpr int C = Map::kC;
+    const Map m;
     const int64_t n_tiles = (B + kT - 1) / kT;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         __syncthreads();
-        load_rows_transposed(Xs, Xin, tile, B);
+        load_rows_transposed(Xs, Xin, tile, B, K);
         __syncthreads();
-        float acc[4][32];
+        float acc[4][C];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc[r][j] = 0.f;
-        tile_mma(Xs, Ws, m, acc);
+            for (int j = 0; j < C; ++j) acc[r][j] = 0.f;
+        tile_mma<kT, NT>(Xs, Ws, K, m, acc);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int64_t g = tile * kT + 4 * m.rg + r;
             if (g >= B) continue;
-            float4* dst = reinterpret_cast<float4*>(Xout + g * kD + 32 * m.og);
+            float4* dst = reinterpret_cast<float4*>(Xout + g * kD + C * m.og);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < C / 4; ++q) {
                 float o[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int j = 32 * m.og + 4 * q + e;
+                    const int j = C * m.og + 4 * q + e;
                     o[e] = j < out ? fmaxf(acc[r][4 * q + e] + __ldg(&b[j]), 0.f) : 0.f;
                 }
                 dst[q] = make_float4(o[0], o[1], o[2], o[3]);
@@ -163,38 +181,42 @@ __global__ void __launch_bounds__(kT, 1) k_layer_fwd(int64_t B, const uint32_t* 
     }
 }
 
-// dXin = (dXout W) * [Xin > 0]; W is [out][in]
+// dXin = (dXout W) * [Xin > 0] for columns [0, NT) of dXin; the reduction
+// runs over the K >= out padded columns of dXout; W is [out][in]
+template <int NT>
 __global__ void __launch_bounds__(kT, 1) k_layer_bwd_dx(int64_t B, const float* __restrict__ dXout,
                                                         const float* __restrict__ Xin, float* __restrict__ dXin,
-                                                        const float* __restrict__ W, int in, int out)
+                                                        const float* __restrict__ W, int in, int out, int K)
 {
     extern __shared__ float4 smem4[];
     float* Ws = reinterpret_cast<float*>(smem4);   // [j][k] = W[j][k]
-    float* Ds = Ws + kD * kD;                       // [j][row]
-    for (int idx = threadIdx.x; idx < kD * kD; idx += kT) {
-        const int j = idx / kD, k = idx % kD;
-        Ws[j * kD + k] = (j < out && k < in) ? W[(size_t)j * in + k] : 0.f;
+    float* Ds = Ws + K * NT;                        // [j][row]
+    for (int idx = threadIdx.x; idx < K * NT; idx += kT) {
+        const int j = idx / NT, k = idx % NT;
+        Ws[idx] = (j < out && k < in) ? W[(size_t)j * in + k] : 0.f;
     }
-    const TileMap m;
+    using Map = TileMap<kT, NT>;
+    constexpr int C = Map::kC;
+    const Map m;
     const int64_t n_tiles = (B + kT - 1) / kT;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         __syncthreads();
-        load_rows_transposed(Ds, dXout, tile, B);
+        load_rows_transposed(Ds, dXout, tile, B, K);
         __syncthreads();
-        float acc[4][32];
+        float acc[4][C];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc[r][j] = 0.f;
-        tile_mma(Ds, Ws, m, acc);
+            for (int j = 0; j < C; ++j) acc[r][j] = 0.f;
+        tile_mma<kT, NT>(Ds, Ws, K, m, acc);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int64_t g = tile * kT + 4 * m.rg + r;
             if (g >= B) continue;
-            const float4* xin = reinterpret_cast<const float4*>(Xin + g * kD + 32 * m.og);
-            float4* dst = reinterpret_cast<float4*>(dXin + g * kD + 32 * m.og);
+            const float4* xin = reinterpret_cast<const float4*>(Xin + g * kD + C * m.og);
+            float4* dst = reinterpret_cast<float4*>(dXin + g * kD + C * m.og);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < C / 4; ++q) {
                 const float4 x = xin[q];
                 dst[q] = make_float4(x.x > 0.f ? acc[r][4 * q] : 0.f, x.y > 0.f ? acc[r][4 * q + 1] : 0.f,
                                      x.z > 0.f ? acc[r][4 * q + 2] : 0.f, x.w > 0.f ? acc[r][4 * q + 3] : 0.f);
@@ -203,50 +225,57 @@ __global__ void __launch_bounds__(kT, 1) k_layer_bwd_dx(int64_t B, const float* 
     }
 }
 
-// per-CTA partials of dW = dXout^T Xin and db = sum dXout over the CTA's tiles:
-// partial[block] = [128 x 128 dW (j-major)] [128 db]
+// per-CTA partials of dW = dXout^T Xin ([MT rows j][NT columns k]) and
+// db = sum dXout over the CTA's tiles: partial[block] = [MT x NT dW] [MT db]
+template <int MT, int NT>
 __global__ void __launch_bounds__(kT, 1) k_layer_bwd_dw(int64_t B, const float* __restrict__ dXout,
                                                         const float* __restrict__ Xin, float* __restrict__ partial)
 {
     extern __shared__ float4 smem4[];
-    float* Ds = reinterpret_cast<float*>(smem4);   // [i][j] (natural layout: reduction index first)
-    float* Xs = Ds + kD * kD;                       // [i][k]
-    const TileMap m;                                // rows of dW: j = 4 rg + r, columns k = 32 og + c
-    float acc[4][32];
+    float* Ds = reinterpret_cast<float*>(smem4);   // [i][j] (reduction index first)
+    float* Xs = Ds + kT * MT;                       // [i][k]
+    using Map = TileMap<MT, NT>;
+    constexpr int C = Map::kC;
+    const Map m;                                    // rows of dW: j = 4 rg + r, columns k = C og + c
+    float acc[4][C];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[r][j] = 0.f;
+        for (int j = 0; j < C; ++j) acc[r][j] = 0.f;
     float db[4] = {0.f, 0.f, 0.f, 0.f};
     const int64_t n_tiles = (B + kT - 1) / kT;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         __syncthreads();
-        for (int idx = threadIdx.x; idx < kD * kD / 4; idx += kT) {
-            const int i = idx / (kD / 4), q = idx % (kD / 4);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int idx = threadIdx.x; idx < kT * MT / 4; idx += kT) {
+            const int i = idx / (MT / 4), q = idx % (MT / 4);
             const int64_t g = tile * kT + i;
-            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             reinterpret_cast<float4*>(Ds)[idx] = g < B ? reinterpret_cast<const float4*>(dXout + g * kD)[q] : z;
+        }
+        for (int idx = threadIdx.x; idx < kT * NT / 4; idx += kT) {
+            const int i = idx / (NT / 4), q = idx % (NT / 4);
+            const int64_t g = tile * kT + i;
             reinterpret_cast<float4*>(Xs)[idx] = g < B ? reinterpret_cast<const float4*>(Xin + g * kD)[q] : z;
         }
         __syncthreads();
-        tile_mma(Ds, Xs, m, acc);
+        tile_mma<MT, NT>(Ds, Xs, kT, m, acc);
         if (m.og == 0) {
             for (int i = 0; i < kT; ++i) {
-                const float4 d = *reinterpret_cast<const float4*>(&Ds[i * kD + 4 * m.rg]);
+                const float4 d = *reinterpret_cast<const float4*>(&Ds[i * MT + 4 * m.rg]);
                 db[0] += d.x; db[1] += d.y; db[2] += d.z; db[3] += d.w;
             }
         }
     }
-    float* P = partial + (size_t)blockIdx.x * (kD * kD + kD);
+    float* P = partial + (size_t)blockIdx.x * (MT * NT + MT);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        float4* dst = reinterpret_cast<float4*>(P + (4 * m.rg + r) * kD + 32 * m.og);
+        float4* dst = reinterpret_cast<float4*>(P + (4 * m.rg + r) * NT + C * m.og);
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
+        for (int q = 0; q < C / 4; ++q)
             dst[q] = make_float4(acc[r][4 * q], acc[r][4 * q + 1], acc[r][4 * q + 2], acc[r][4 * q + 3]);
     }
     if (m.og == 0)
-        for (int r = 0; r < 4; ++r) P[kD * kD + 4 * m.rg + r] = db[r];
+        for (int r = 0; r < 4; ++r) P[MT * NT + 4 * m.rg + r] = db[r];
 }
 
 // Output layer and loss: dXlast = relu-masked W4^T dy, partial head
@@ -401,20 +430,73 @@ cudaError_t train_inputs(uint32_t seed, uint32_t step, int64_t B, const float* s
 // target [B][3] -> grad (flat trainable layout) and the loss (FP64 and/or
 // FP32 copies).  mode 0: NIF (Huber, colour matrix); mode 1: radiance cache
 // (relative L2, rows masked by mask).
+namespace {
+
+cudaError_t set_smem(const void* fn)
+{
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+}
+
+// launches of the three GEMM kernels with tile widths chosen per layer
+// (64 when the dimension fits, else 128)
+void layer_fwd(int G, int64_t B, const float* Xin, float* Xout, const float* W, const float* b, int in, int out,
+               cudaStream_t s)
+{
+    const int K = pad_k(in);
+    if (pad_width(out) == 64) {
+        const size_t sm = (size_t)K * (64 + kT) * sizeof(float);
+        k_layer_fwd<64><<<G, kT, sm, s>>>(B, Xin, Xout, W, b, in, out, K);
+    } else {
+        const size_t sm = (size_t)K * (128 + kT) * sizeof(float);
+        k_layer_fwd<128><<<G, kT, sm, s>>>(B, Xin, Xout, W, b, in, out, K);
+    }
+}
+
+void layer_bwd_dx(int G, int64_t B, const float* dXout, const float* Xin, float* dXin, const float* W, int in, int out,
+                  cudaStream_t s)
+{
+    const int K = pad_k(out);
+    if (pad_width(in) == 64) {
+        const size_t sm = (size_t)K * (64 + kT) * sizeof(float);
+        k_layer_bwd_dx<64><<<G, kT, sm, s>>>(B, dXout, Xin, dXin, W, in, out, K);
+    } else {
+        const size_t sm = (size_t)K * (128 + kT) * sizeof(float);
+        k_layer_bwd_dx<128><<<G, kT, sm, s>>>(B, dXout, Xin, dXin, W, in, out, K);
+    }
+}
+
+// returns the partial layout's column pitch (NT) and row count (MT)
+void layer_bwd_dw(int G, int64_t B, const float* dXout, const float* Xin, float* partial, int in, int out, int* MT,
+                  int* NT, cudaStream_t s)
+{
+    *MT = pad_width(out);
+    *NT = pad_width(in);
+    const size_t sm = (size_t)kT * (*MT + *NT) * sizeof(float);
+    if (*MT == 64 && *NT == 64) k_layer_bwd_dw<64, 64><<<G, kT, sm, s>>>(B, dXout, Xin, partial);
+    else if (*MT == 64) k_layer_bwd_dw<64, 128><<<G, kT, sm, s>>>(B, dXout, Xin, partial);
+    else if (*NT == 64) k_layer_bwd_dw<128, 64><<<G, kT, sm, s>>>(B, dXout, Xin, partial);
+    else k_layer_bwd_dw<128, 128><<<G, kT, sm, s>>>(B, dXout, Xin, partial);
+}
+
+}  // namespace
+
 cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, float delta, int mode,
                           const int32_t* mask, TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s)
 {
     if (B <= 0) return cudaSuccess;
     cudaError_t e;
     const int G = wk.n_blocks;
-    for (auto fn : {(const void*)k_layer_fwd, (const void*)k_layer_bwd_dx, (const void*)k_layer_bwd_dw}) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+    for (auto fn : {(const void*)k_layer_fwd<64>, (const void*)k_layer_fwd<128>, (const void*)k_layer_bwd_dx<64>,
+                    (const void*)k_layer_bwd_dx<128>, (const void*)k_layer_bwd_dw<64, 64>,
+                    (const void*)k_layer_bwd_dw<64, 128>, (const void*)k_layer_bwd_dw<128, 64>,
+                    (const void*)k_layer_bwd_dw<128, 128>}) {
+        e = set_smem(fn);
         if (e != cudaSuccess) return e;
     }
     // forward through the hidden layers
     for (int l = 0; l < net.L; ++l) {
         const int in = l == 0 ? net.in0 : net.H;
-        k_layer_fwd<<<G, kT, kGemmSmem, s>>>(B, nullptr, wk.X[l], wk.X[l + 1], net.W[l], net.b[l], in, net.H);
+        layer_fwd(G, B, wk.X[l], wk.X[l + 1], net.W[l], net.b[l], in, net.H, s);
     }
     // head + loss
     k_head_loss<<<G, kT, 0, s>>>(B, wk.X[net.L], target, net.W[net.L], net.b[net.L], net.H, net.M, delta,
@@ -425,10 +507,11 @@ cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, f
     int cur = 0;
     for (int l = net.L - 1; l >= 0; --l) {
         const int in = l == 0 ? net.in0 : net.H;
-        k_layer_bwd_dw<<<G, kT, kGemmSmem, s>>>(B, wk.dX[cur], wk.X[l], wk.partial);
-        k_sum_partials<<<64, 256, 0, s>>>(wk.partial, G, kD * kD + kD, kD, kD * kD, in, net.H, net.gW[l], net.gb[l]);
+        int MT = 0, NT = 0;
+        layer_bwd_dw(G, B, wk.dX[cur], wk.X[l], wk.partial, in, net.H, &MT, &NT, s);
+        k_sum_partials<<<64, 256, 0, s>>>(wk.partial, G, MT * NT + MT, NT, MT * NT, in, net.H, net.gW[l], net.gb[l]);
         if (l > 0) {
-            k_layer_bwd_dx<<<G, kT, kGemmSmem, s>>>(B, wk.dX[cur], wk.X[l], wk.dX[cur ^ 1], net.W[l], in, net.H);
+            layer_bwd_dx(G, B, wk.dX[cur], wk.X[l], wk.dX[cur ^ 1], net.W[l], in, net.H, s);
             cur ^= 1;
         }
     }
