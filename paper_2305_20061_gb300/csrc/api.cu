@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "pt_internal.h"
@@ -158,6 +159,13 @@ pt_status ensure_scratch(pt_ctx* ctx, uint32_t chunk)
     }
     ctx->chunk_cap = chunk;
     return PT_OK;
+}
+
+float half_to_float_host(uint16_t bits)
+{
+    __half h;
+    std::memcpy(&h, &bits, 2);
+    return __half2float(h);
 }
 
 bool finite3(const float* p, int64_t n)
@@ -432,6 +440,34 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
     if (!ok) {
         pt_destroy_scene(sc);
         return fail(ctx, PT_ENOMEM, "scene upload failed");
+    }
+    // BVHs that fit comfortably in L2 also get the decoded 64-byte form
+    constexpr size_t kWideLimit = 48u << 20;
+    if (!bo.nodes.empty() && bo.nodes.size() * 64 <= kWideLimit) {
+        std::vector<float> wide(bo.nodes.size() * 16, 0.f);
+        for (size_t i = 0; i < bo.nodes.size(); ++i) {
+            const uint32_t* w = bo.nodes[i].w;
+            float lo[6], hi[6];
+            for (int a = 0; a < 6; ++a) std::memcpy(&lo[a], &w[a], 4);
+            const uint16_t ext[6] = {(uint16_t)(w[6] & 0xFFFFu), (uint16_t)(w[6] >> 16), (uint16_t)(w[7] & 0xFFFFu),
+                                     (uint16_t)(w[7] >> 16), (uint16_t)(w[8] & 0xFFFFu), (uint16_t)(w[8] >> 16)};
+            for (int a = 0; a < 6; ++a) {
+                volatile float top = lo[a] + half_to_float_host(ext[a]);   // FP32 add, as the device does
+                hi[a] = top;
+            }
+            float* o = &wide[16 * i];
+            o[0] = lo[0]; o[1] = lo[1]; o[2] = lo[2]; o[3] = hi[0];
+            o[4] = hi[1]; o[5] = hi[2]; o[6] = lo[3]; o[7] = lo[4];
+            o[8] = lo[5]; o[9] = hi[3]; o[10] = hi[4]; o[11] = hi[5];
+            std::memcpy(&o[12], &w[9], 4);
+            std::memcpy(&o[13], &w[10], 4);
+        }
+        void* dw = nullptr;
+        if (!upload(wide.data(), wide.size() * sizeof(float), &dw)) {
+            pt_destroy_scene(sc);
+            return fail(ctx, PT_ENOMEM, "scene upload failed");
+        }
+        sc->dev.wnodes = (const uint4*)dw;
     }
     DevScene& v = sc->dev;
     v.nodes = (const uint4*)dn;

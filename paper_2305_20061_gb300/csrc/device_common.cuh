@@ -209,10 +209,9 @@ __device__ __forceinline__ void isect_prim(const DevScene& sc, uint32_t id, floa
 
 __device__ __forceinline__ float half_bits_to_float(uint32_t bits16) { return __half2float(__ushort_as_half((unsigned short)bits16)); }
 
-// slab test of one child box; returns entry distance or +inf
-__device__ __forceinline__ float slab(float3 lo, float3 ext, float3 o, float3 inv, float tbest)
+// slab test of one child box [lo, hi]; returns entry distance or +inf
+__device__ __forceinline__ float slab_box(float3 lo, float3 hi, float3 o, float3 inv, float tbest)
 {
-    const float3 hi = lo + ext;
     const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
     const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
     const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
@@ -220,6 +219,11 @@ __device__ __forceinline__ float slab(float3 lo, float3 ext, float3 o, float3 in
     float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
     tmax *= 1.0000004f;  // 1 + 2 gamma_3 (PBRT): rounding can never drop a true hit
     return (tmin <= tmax && tmin <= tbest) ? tmin : INFINITY;
+}
+// the same for a box stored as lo + extent (hi = lo + ext rounded in FP32)
+__device__ __forceinline__ float slab(float3 lo, float3 ext, float3 o, float3 inv, float tbest)
+{
+    return slab_box(lo, lo + ext, o, inv, tbest);
 }
 
 __device__ __forceinline__ float safe_inv(float d) { return 1.f / (fabsf(d) > 1e-30f ? d : copysignf(1e-30f, d)); }
@@ -254,22 +258,40 @@ __device__ __forceinline__ bool trav_init(const DevScene& sc, float3 o, float3 d
     return false;
 }
 
+template <bool kWide>
 __device__ __forceinline__ bool trav_step(const DevScene& sc, Trav& s, uint32_t* stack_ref, float* stack_t,
                                           uint32_t* err, Work& w)
 {
     if (++s.iters > kIterCap) { atomicOr(err, PT_ERR_ITER_CAP); return true; }
     if (s.cur >= sc.n_nodes) { atomicOr(err, PT_ERR_BAD_NODE); return true; }  // never fetch outside the node array
-    const uint4* np = sc.nodes + 3 * (size_t)s.cur;
-    const uint4 q0 = __ldg(np), q1 = __ldg(np + 1), q2 = __ldg(np + 2);
-    const float3 lo_l = f3(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z));
-    const float3 lo_r = f3(__uint_as_float(q0.w), __uint_as_float(q1.x), __uint_as_float(q1.y));
-    const float3 ext_l = f3(half_bits_to_float(q1.z & 0xFFFFu), half_bits_to_float(q1.z >> 16),
-                            half_bits_to_float(q1.w & 0xFFFFu));
-    const float3 ext_r = f3(half_bits_to_float(q1.w >> 16), half_bits_to_float(q2.x & 0xFFFFu),
-                            half_bits_to_float(q2.x >> 16));
-    const uint32_t cl = q2.y, cr = q2.z;
-    float tl = slab(lo_l, ext_l, s.o, s.inv, s.h.t);
-    float trr = slab(lo_r, ext_r, s.o, s.inv, s.h.t);
+    uint32_t cl, cr;
+    float tl, trr;
+    if (kWide) {
+        // decoded boxes: the same bounds the packed form decodes to, without the fp16 conversions
+        const uint4* np = sc.wnodes + 4 * (size_t)s.cur;
+        const uint4 q0 = __ldg(np), q1 = __ldg(np + 1), q2 = __ldg(np + 2), q3 = __ldg(np + 3);
+        const float3 lo_l = f3(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z));
+        const float3 hi_l = f3(__uint_as_float(q0.w), __uint_as_float(q1.x), __uint_as_float(q1.y));
+        const float3 lo_r = f3(__uint_as_float(q1.z), __uint_as_float(q1.w), __uint_as_float(q2.x));
+        const float3 hi_r = f3(__uint_as_float(q2.y), __uint_as_float(q2.z), __uint_as_float(q2.w));
+        cl = q3.x;
+        cr = q3.y;
+        tl = slab_box(lo_l, hi_l, s.o, s.inv, s.h.t);
+        trr = slab_box(lo_r, hi_r, s.o, s.inv, s.h.t);
+    } else {
+        const uint4* np = sc.nodes + 3 * (size_t)s.cur;
+        const uint4 q0 = __ldg(np), q1 = __ldg(np + 1), q2 = __ldg(np + 2);
+        const float3 lo_l = f3(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z));
+        const float3 lo_r = f3(__uint_as_float(q0.w), __uint_as_float(q1.x), __uint_as_float(q1.y));
+        const float3 ext_l = f3(half_bits_to_float(q1.z & 0xFFFFu), half_bits_to_float(q1.z >> 16),
+                                half_bits_to_float(q1.w & 0xFFFFu));
+        const float3 ext_r = f3(half_bits_to_float(q1.w >> 16), half_bits_to_float(q2.x & 0xFFFFu),
+                                half_bits_to_float(q2.x >> 16));
+        cl = q2.y;
+        cr = q2.z;
+        tl = slab(lo_l, ext_l, s.o, s.inv, s.h.t);
+        trr = slab(lo_r, ext_r, s.o, s.inv, s.h.t);
+    }
     ++w.nodes;
     // leaf children are intersected right away
     if ((cl & kLeafBit) && tl < INFINITY) {
@@ -306,7 +328,7 @@ __device__ __forceinline__ Hit trace_closest(const DevScene& sc, float3 o, float
     if (trav_init(sc, o, d, s, w)) return s.h;
     uint32_t stack_ref[kStackSize];
     float stack_t[kStackSize];
-    while (!trav_step(sc, s, stack_ref, stack_t, err, w)) {
+    while (!trav_step<false>(sc, s, stack_ref, stack_t, err, w)) {
     }
     return s.h;
 }

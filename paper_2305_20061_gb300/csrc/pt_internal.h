@@ -31,6 +31,10 @@ static_assert(sizeof(PackedNode) == 48, "node packing");
 // Device view of a scene (passed by value in kernel parameters).
 struct DevScene {
     const uint4* nodes;     // 3 x uint4 per node
+    // nullable: the same tree with both child boxes decoded to fp32 (lo, hi), 4 x uint4 per node:
+    //   lo_l.xyz hi_l.x | hi_l.yz lo_r.xy | lo_r.z hi_r.xyz | child_l child_r 0 0
+    // kept for BVHs small enough to stay cache-resident, where decoding costs more than the bytes
+    const uint4* wnodes;
     uint32_t root;          // node index, leaf reference, or kEmptyRef
     uint32_t n_nodes;
     uint32_t nS, nQ, nT;    // primitive counts; IDs: [0,nS) spheres, [nS,nS+nQ) quads, rest triangles

@@ -165,6 +165,7 @@ __device__ __forceinline__ void store_L(float* slot_L, uint32_t slot, float3 L, 
 constexpr int kRefillMin = PT_TRACE_REFILL_MIN;
 constexpr int kStepsPerCheck = PT_TRACE_STEPS;
 
+template <bool kWide>
 __global__ void __launch_bounds__(256, 4) k_trace(const BounceParams p)
 {
     const uint32_t count = (p.k == 1) ? p.n_chunk : min(*p.count_in, p.cap);
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(256, 4) k_trace(const BounceParams p)
         }
 #pragma unroll 1
         for (int st = 0; st < kStepsPerCheck; ++st) {
-            if (live && trav_step(p.sc, t, stack_ref, stack_t, p.err, work)) {
+            if (live && trav_step<kWide>(p.sc, t, stack_ref, stack_t, p.err, work)) {
                 p.hits[ri] = make_int2(__float_as_int(t.h.t), t.h.prim);
                 live = false;
             }
@@ -467,7 +468,8 @@ int grid_for(int64_t n, int block, int sm_count, int per_sm)
 cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s)
 {
     // traversal: persistent, 4 resident blocks of 256 threads per SM; shading: grid-stride over the queue
-    k_trace<<<sm_count * 4, 256, 0, s>>>(p);
+    if (p.sc.wnodes) k_trace<true><<<sm_count * 4, 256, 0, s>>>(p);
+    else k_trace<false><<<sm_count * 4, 256, 0, s>>>(p);
     k_bounce<<<sm_count * 8, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
