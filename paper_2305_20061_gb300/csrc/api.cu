@@ -691,7 +691,7 @@ pt_status ensure_train(pt_ctx* ctx, pt_nif* nf, int64_t B)
     cudaFree(nf->d_batch);
     nf->d_work = nullptr;
     nf->d_batch = nullptr;
-    const int G = ctx->sm_count;
+    const int G = 4 * ctx->sm_count;   // partial slots: up to four GEMM CTAs per SM
     const size_t rows = (size_t)B * 128;
     const size_t bytes = (size_t)(nf->L + 1 + 2) * rows * sizeof(float) + (size_t)G * (128 * 128 + 128) * sizeof(float) +
                          (size_t)G * sizeof(double) + 4096;
@@ -702,6 +702,7 @@ pt_status ensure_train(pt_ctx* ctx, pt_nif* nf, int64_t B)
     char* w = static_cast<char*>(nf->d_work);
     nf->work = TrainWork{};
     nf->work.n_blocks = G;
+    nf->work.sm_count = ctx->sm_count;
     for (int l = 0; l <= nf->L; ++l) { nf->work.X[l] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
     for (int i = 0; i < 2; ++i) { nf->work.dX[i] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
     nf->work.partial = reinterpret_cast<float*>(w);
@@ -842,7 +843,7 @@ pt_status ensure_cache_train(pt_ctx* ctx, pt_cache* c, int64_t B)
     cudaFree(c->d_work);
     c->d_work = nullptr;
     c->work_cap = 0;
-    const int G = ctx->sm_count;
+    const int G = 4 * ctx->sm_count;   // partial slots: up to four GEMM CTAs per SM
     const size_t rows = (size_t)B * 128;
     const size_t bytes = (size_t)(c->L + 1 + 2) * rows * sizeof(float) + (size_t)G * (128 * 128 + 128) * sizeof(float) +
                          (size_t)G * sizeof(double) + 4096;
@@ -850,6 +851,7 @@ pt_status ensure_cache_train(pt_ctx* ctx, pt_cache* c, int64_t B)
     char* w = static_cast<char*>(c->d_work);
     c->work = TrainWork{};
     c->work.n_blocks = G;
+    c->work.sm_count = ctx->sm_count;
     for (int l = 0; l <= c->L; ++l) { c->work.X[l] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
     for (int i = 0; i < 2; ++i) { c->work.dX[i] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
     c->work.partial = reinterpret_cast<float*>(w);

@@ -169,7 +169,8 @@ struct TrainNet {
     float* gb[9];
 };
 struct TrainWork {
-    int32_t n_blocks;               // CTAs of the batch GEMMs (one partial each)
+    int32_t n_blocks;               // partial slots allocated (at most this many CTAs per launch)
+    int32_t sm_count;
     float* X[9];                    // X[0] features, X[l] hidden outputs, each [batch][128]
     float* dX[2];                   // ping-pong [batch][128]
     float* partial;                 // [n_blocks][128 * 128 + 128]

@@ -85,9 +85,9 @@ __device__ __forceinline__ void load_rows_transposed(float* S, const float* __re
 }
 
 // padded width (64 or 128) of a layer dimension
-inline int pad_width(int n) { return n <= 64 ? 64 : 128; }
+__host__ __device__ inline int pad_width(int n) { return n <= 64 ? 64 : 128; }
 // reduction length rounded up to a multiple of 4 (the float4 row loads)
-inline int pad_k(int n) { return (n + 3) & ~3; }
+__host__ __device__ inline int pad_k(int n) { return (n + 3) & ~3; }
 
 // ---------------------------------------------------------------------------
 // training inputs: Philox key (seed, 1), counter (i, step, 0, 0) -> (u, v);
@@ -117,20 +117,24 @@ __global__ void k_train_inputs(uint32_t seed, uint32_t step, int64_t B, const fl
     }
 }
 
-// X0[i] = [sin 2 pi (B uv_i), cos 2 pi (B uv_i)] padded to 128
+// X0[i] = [sin 2 pi (B uv_i), cos 2 pi (B uv_i)] padded to 128; one thread per (sample, frequency)
 __global__ void k_train_features(int64_t B, const float* __restrict__ uv, const float* __restrict__ Bm, int F,
                                  float* __restrict__ X0)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B; i += (int64_t)gridDim.x * blockDim.x) {
-        const float u = uv[2 * i], v = uv[2 * i + 1];
-        float* row = X0 + i * kD;
-        for (int f = 0; f < F; ++f) {
-            float s, c;
-            fourier_feature(__ldg(&Bm[2 * f]), __ldg(&Bm[2 * f + 1]), u, v, s, c);
-            row[f] = s;
-            row[F + f] = c;
+    const int64_t n = B * F, npad = B * (kD - 2 * F);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n + npad;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        if (idx < n) {
+            const int64_t i = idx / F;
+            const int f = (int)(idx - i * F);
+            float sv, cv;
+            fourier_feature(__ldg(&Bm[2 * f]), __ldg(&Bm[2 * f + 1]), uv[2 * i], uv[2 * i + 1], sv, cv);
+            X0[i * kD + f] = sv;
+            X0[i * kD + F + f] = cv;
+        } else {
+            const int64_t q = idx - n, i = q / (kD - 2 * F);
+            X0[i * kD + 2 * F + (q - i * (kD - 2 * F))] = 0.f;
         }
-        for (int k = 2 * F; k < kD; ++k) row[k] = 0.f;
     }
 }
 
@@ -291,28 +295,34 @@ __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __r
                                                      double* __restrict__ loss_partial, int mode,
                                                      const int32_t* __restrict__ mask)
 {
+    extern __shared__ float4 smem4[];
+    float* Xs = reinterpret_cast<float*>(smem4);   // the tile's last hidden layer, [k][row]
     __shared__ float dys[kT][3];
     __shared__ double lsum[kT];
+    const int Kh = pad_k(H);
     float gW[3] = {0.f, 0.f, 0.f};   // this thread's column k = threadIdx.x of dW4
     float gb[3] = {0.f, 0.f, 0.f};
     double loss = 0.0;
     float M[9];
     for (int i = 0; i < 9; ++i) M[i] = mode == 0 ? Mm[i] : (i % 4 == 0 ? 1.f : 0.f);
+    const int k = threadIdx.x;
+    const float w0 = k < H ? __ldg(&W4[k]) : 0.f, w1 = k < H ? __ldg(&W4[H + k]) : 0.f,
+                w2 = k < H ? __ldg(&W4[2 * H + k]) : 0.f;
     const int64_t n_tiles = (B + kT - 1) / kT;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        __syncthreads();   // the previous tile's readers of Xs and dys are done
+        load_rows_transposed(Xs, X, tile, B, Kh);
+        __syncthreads();
+        // thread = row: output, loss and dL/dy
         const int64_t g = tile * kT + threadIdx.x;
         float dy[3] = {0.f, 0.f, 0.f};
-        if (g < B && mask && !mask[g]) {
-            float* dxr = dX + g * kD;
-            for (int k = 0; k < kD; ++k) dxr[k] = 0.f;
-        } else if (g < B) {
-            const float* x = X + g * kD;
+        if (g < B && !(mask && !mask[g])) {
             float y[3] = {__ldg(&b4[0]), __ldg(&b4[1]), __ldg(&b4[2])};
-            for (int k = 0; k < H; ++k) {
-                const float xv = x[k];
-                y[0] = fmaf(__ldg(&W4[k]), xv, y[0]);
-                y[1] = fmaf(__ldg(&W4[H + k]), xv, y[1]);
-                y[2] = fmaf(__ldg(&W4[2 * H + k]), xv, y[2]);
+            for (int kk = 0; kk < H; ++kk) {
+                const float xv = Xs[kk * kT + threadIdx.x];
+                y[0] = fmaf(__ldg(&W4[kk]), xv, y[0]);
+                y[1] = fmaf(__ldg(&W4[H + kk]), xv, y[1]);
+                y[2] = fmaf(__ldg(&W4[2 * H + kk]), xv, y[2]);
             }
             float dz[3];
             for (int c = 0; c < 3; ++c) {
@@ -329,22 +339,18 @@ __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __r
                 }
             }
             for (int j = 0; j < 3; ++j) dy[j] = M[j] * dz[0] + M[3 + j] * dz[1] + M[6 + j] * dz[2];
-            float* dxr = dX + g * kD;
-            for (int k = 0; k < kD; ++k) {
-                const float v = k < H ? dy[0] * __ldg(&W4[k]) + dy[1] * __ldg(&W4[H + k]) + dy[2] * __ldg(&W4[2 * H + k])
-                                      : 0.f;
-                dxr[k] = (k < H && x[k] > 0.f) ? v : 0.f;
-            }
         }
-        __syncthreads();
         dys[threadIdx.x][0] = dy[0]; dys[threadIdx.x][1] = dy[1]; dys[threadIdx.x][2] = dy[2];
         __syncthreads();
-        // column k = threadIdx.x of dW4 over the tile's samples, in sample order
-        const int k = threadIdx.x;
-        for (int i = 0; i < kT; ++i) {
+        // thread = column k: the tile's rows of dX = relu-masked W4^T dy (coalesced) and column k of dW4,
+        // in sample order
+        const int rows = (int)min((int64_t)kT, B - tile * kT);
+#pragma unroll 8
+        for (int i = 0; i < rows; ++i) {
             const int64_t gi = tile * kT + i;
-            if (gi >= B) break;
             const float xv = X[gi * kD + k];
+            const float v = dys[i][0] * w0 + dys[i][1] * w1 + dys[i][2] * w2;
+            dX[gi * kD + k] = (k < H && xv > 0.f) ? v : 0.f;
             gW[0] = fmaf(dys[i][0], xv, gW[0]);
             gW[1] = fmaf(dys[i][1], xv, gW[1]);
             gW[2] = fmaf(dys[i][2], xv, gW[2]);
@@ -359,9 +365,9 @@ __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __r
     lsum[threadIdx.x] = loss;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < kT; ++i) s += lsum[i];
-        loss_partial[blockIdx.x] = s;
+        double sum = 0.0;
+        for (int i = 0; i < kT; ++i) sum += lsum[i];
+        loss_partial[blockIdx.x] = sum;
     }
 }
 
@@ -369,33 +375,45 @@ __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __r
 // dst_W[j * in + k] for j < out, k < in, then dst_b[j].  stride/wofs/bofs
 // describe the partial layout ([block][stride], W block at wofs with row
 // pitch pitch, bias at bofs).
-__global__ void k_sum_partials(const float* __restrict__ partial, int n_blocks, int stride, int pitch, int bofs,
-                               int in, int out, float* __restrict__ dst_W, float* __restrict__ dst_b)
+__global__ void __launch_bounds__(256) k_sum_partials(const float* __restrict__ partial, int n_blocks, int stride,
+                                                      int pitch, int bofs, int in, int out, float* __restrict__ dst_W,
+                                                      float* __restrict__ dst_b)
 {
+    // 32 elements per CTA; warp w sums the partials b = w, w + 8, ... in order, then the eight
+    // running sums are combined in a fixed tree (deterministic, independent of scheduling)
+    __shared__ float part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int n = out * in + out;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        int src;
-        float* dst;
-        if (idx < out * in) {
-            const int j = idx / in, k = idx % in;
-            src = j * pitch + k;
-            dst = dst_W + idx;
-        } else {
-            src = bofs + (idx - out * in);
-            dst = dst_b + (idx - out * in);
-        }
-        float s = 0.f;
-        for (int b = 0; b < n_blocks; ++b) s += partial[(size_t)b * stride + src];
-        *dst = s;
+    const int idx = blockIdx.x * 32 + lane;
+    int src = 0;
+    float* dst = nullptr;
+    if (idx < out * in) {
+        const int j = idx / in, k = idx % in;
+        src = j * pitch + k;
+        dst = dst_W + idx;
+    } else if (idx < n) {
+        src = bofs + (idx - out * in);
+        dst = dst_b + (idx - out * in);
     }
+    float acc = 0.f;
+    if (idx < n)
+        for (int b = w; b < n_blocks; b += 8) acc += partial[(size_t)b * stride + src];
+    part[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && idx < n)
+        *dst = ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane])) +
+               ((part[4][lane] + part[5][lane]) + (part[6][lane] + part[7][lane]));
 }
 
+// one warp: lane l sums partials l, l + 32, ... in order, then a fixed shuffle tree
 __global__ void k_sum_loss(const double* __restrict__ partial, int n, double scale, double* __restrict__ out_d,
                            float* __restrict__ out_f)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     double s = 0.0;
-    for (int i = 0; i < n; ++i) s += partial[i];
+    for (int i = threadIdx.x; i < n; i += 32) s += partial[i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, off);
+    if (threadIdx.x != 0) return;
     s *= scale;   // mean over samples and channels
     if (out_d) *out_d = s;
     if (out_f) *out_f = (float)s;
@@ -437,45 +455,67 @@ cudaError_t set_smem(const void* fn)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
 }
 
+// CTAs of a batch launch: as many as fit on the GPU at once (occupancy of
+// the instance with its shared memory), no more than the tiles or the
+// partial slots
+int grid_of(const TrainWork& wk, int64_t B, const void* fn, size_t smem)
+{
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kT, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+    const int64_t tiles = (B + kT - 1) / kT;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(tiles, (int64_t)per_sm * wk.sm_count),
+                                                       wk.n_blocks));
+}
+
 // launches of the three GEMM kernels with tile widths chosen per layer
 // (64 when the dimension fits, else 128)
-void layer_fwd(int G, int64_t B, const float* Xin, float* Xout, const float* W, const float* b, int in, int out,
+void layer_fwd(const TrainWork& wk, int64_t B, const float* Xin, float* Xout, const float* W, const float* b, int in, int out,
                cudaStream_t s)
 {
     const int K = pad_k(in);
     if (pad_width(out) == 64) {
         const size_t sm = (size_t)K * (64 + kT) * sizeof(float);
+        const int G = grid_of(wk, B, (const void*)k_layer_fwd<64>, sm);
         k_layer_fwd<64><<<G, kT, sm, s>>>(B, Xin, Xout, W, b, in, out, K);
     } else {
         const size_t sm = (size_t)K * (128 + kT) * sizeof(float);
+        const int G = grid_of(wk, B, (const void*)k_layer_fwd<128>, sm);
         k_layer_fwd<128><<<G, kT, sm, s>>>(B, Xin, Xout, W, b, in, out, K);
     }
 }
 
-void layer_bwd_dx(int G, int64_t B, const float* dXout, const float* Xin, float* dXin, const float* W, int in, int out,
+void layer_bwd_dx(const TrainWork& wk, int64_t B, const float* dXout, const float* Xin, float* dXin, const float* W, int in, int out,
                   cudaStream_t s)
 {
     const int K = pad_k(out);
     if (pad_width(in) == 64) {
         const size_t sm = (size_t)K * (64 + kT) * sizeof(float);
+        const int G = grid_of(wk, B, (const void*)k_layer_bwd_dx<64>, sm);
         k_layer_bwd_dx<64><<<G, kT, sm, s>>>(B, dXout, Xin, dXin, W, in, out, K);
     } else {
         const size_t sm = (size_t)K * (128 + kT) * sizeof(float);
+        const int G = grid_of(wk, B, (const void*)k_layer_bwd_dx<128>, sm);
         k_layer_bwd_dx<128><<<G, kT, sm, s>>>(B, dXout, Xin, dXin, W, in, out, K);
     }
 }
 
-// returns the partial layout's column pitch (NT) and row count (MT)
-void layer_bwd_dw(int G, int64_t B, const float* dXout, const float* Xin, float* partial, int in, int out, int* MT,
-                  int* NT, cudaStream_t s)
+// returns the partial layout's column pitch (NT), row count (MT) and the CTAs (partials) used
+int layer_bwd_dw(const TrainWork& wk, int64_t B, const float* dXout, const float* Xin, float* partial, int in, int out,
+                 int* MT, int* NT, cudaStream_t s)
 {
     *MT = pad_width(out);
     *NT = pad_width(in);
     const size_t sm = (size_t)kT * (*MT + *NT) * sizeof(float);
+    const void* fn = (*MT == 64 && *NT == 64) ? (const void*)k_layer_bwd_dw<64, 64>
+                     : (*MT == 64)            ? (const void*)k_layer_bwd_dw<64, 128>
+                     : (*NT == 64)            ? (const void*)k_layer_bwd_dw<128, 64>
+                                              : (const void*)k_layer_bwd_dw<128, 128>;
+    const int G = grid_of(wk, B, fn, sm);
     if (*MT == 64 && *NT == 64) k_layer_bwd_dw<64, 64><<<G, kT, sm, s>>>(B, dXout, Xin, partial);
     else if (*MT == 64) k_layer_bwd_dw<64, 128><<<G, kT, sm, s>>>(B, dXout, Xin, partial);
     else if (*NT == 64) k_layer_bwd_dw<128, 64><<<G, kT, sm, s>>>(B, dXout, Xin, partial);
     else k_layer_bwd_dw<128, 128><<<G, kT, sm, s>>>(B, dXout, Xin, partial);
+    return G;
 }
 
 }  // namespace
@@ -485,7 +525,6 @@ cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, f
 {
     if (B <= 0) return cudaSuccess;
     cudaError_t e;
-    const int G = wk.n_blocks;
     for (auto fn : {(const void*)k_layer_fwd<64>, (const void*)k_layer_fwd<128>, (const void*)k_layer_bwd_dx<64>,
                     (const void*)k_layer_bwd_dx<128>, (const void*)k_layer_bwd_dw<64, 64>,
                     (const void*)k_layer_bwd_dw<64, 128>, (const void*)k_layer_bwd_dw<128, 64>,
@@ -496,22 +535,28 @@ cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, f
     // forward through the hidden layers
     for (int l = 0; l < net.L; ++l) {
         const int in = l == 0 ? net.in0 : net.H;
-        layer_fwd(G, B, wk.X[l], wk.X[l + 1], net.W[l], net.b[l], in, net.H, s);
+        layer_fwd(wk, B, wk.X[l], wk.X[l + 1], net.W[l], net.b[l], in, net.H, s);
     }
     // head + loss
-    k_head_loss<<<G, kT, 0, s>>>(B, wk.X[net.L], target, net.W[net.L], net.b[net.L], net.H, net.M, delta,
-                                 1.f / (3.f * (float)B), wk.dX[0], wk.partial, wk.loss_partial, mode, mask);
-    k_sum_partials<<<4, 256, 0, s>>>(wk.partial, G, 3 * kD + 3, kD, 3 * kD, net.H, 3, net.gW[net.L], net.gb[net.L]);
-    k_sum_loss<<<1, 32, 0, s>>>(wk.loss_partial, G, 1.0 / (3.0 * (double)B), loss_d, loss_f);
+    e = set_smem((const void*)k_head_loss);
+    if (e != cudaSuccess) return e;
+    const size_t hsm = (size_t)pad_k(net.H) * kT * sizeof(float);
+    const int Gh = grid_of(wk, B, (const void*)k_head_loss, hsm);
+    k_head_loss<<<Gh, kT, hsm, s>>>(B, wk.X[net.L], target, net.W[net.L], net.b[net.L], net.H, net.M, delta,
+                                    1.f / (3.f * (float)B), wk.dX[0], wk.partial, wk.loss_partial, mode, mask);
+    k_sum_partials<<<(3 * net.H + 3 + 31) / 32, 256, 0, s>>>(wk.partial, Gh, 3 * kD + 3, kD, 3 * kD, net.H, 3,
+                                                             net.gW[net.L], net.gb[net.L]);
+    k_sum_loss<<<1, 32, 0, s>>>(wk.loss_partial, Gh, 1.0 / (3.0 * (double)B), loss_d, loss_f);
     // backward through the hidden layers
     int cur = 0;
     for (int l = net.L - 1; l >= 0; --l) {
         const int in = l == 0 ? net.in0 : net.H;
         int MT = 0, NT = 0;
-        layer_bwd_dw(G, B, wk.dX[cur], wk.X[l], wk.partial, in, net.H, &MT, &NT, s);
-        k_sum_partials<<<64, 256, 0, s>>>(wk.partial, G, MT * NT + MT, NT, MT * NT, in, net.H, net.gW[l], net.gb[l]);
+        const int Gw = layer_bwd_dw(wk, B, wk.dX[cur], wk.X[l], wk.partial, in, net.H, &MT, &NT, s);
+        k_sum_partials<<<(in * net.H + net.H + 31) / 32, 256, 0, s>>>(wk.partial, Gw, MT * NT + MT, NT, MT * NT, in,
+                                                                       net.H, net.gW[l], net.gb[l]);
         if (l > 0) {
-            layer_bwd_dx(G, B, wk.dX[cur], wk.X[l], wk.dX[cur ^ 1], net.W[l], in, net.H, s);
+            layer_bwd_dx(wk, B, wk.dX[cur], wk.X[l], wk.dX[cur ^ 1], net.W[l], in, net.H, s);
             cur ^= 1;
         }
     }
@@ -522,7 +567,8 @@ cudaError_t nif_loss_grad(const TrainNet& net, int64_t B, const float* uv, const
                           TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s)
 {
     if (B <= 0) return cudaSuccess;
-    k_train_features<<<(unsigned)std::min<int64_t>((B + 127) / 128, 152 * 8), 128, 0, s>>>(B, uv, net.B, net.F, wk.X[0]);
+    k_train_features<<<(unsigned)std::min<int64_t>((B * 64 + 255) / 256, 152 * 32), 256, 0, s>>>(B, uv, net.B, net.F,
+                                                                                                 wk.X[0]);
     return mlp_loss_grad(net, B, target, delta, 0, nullptr, wk, loss_d, loss_f, s);
 }
 
