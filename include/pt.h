@@ -321,9 +321,12 @@ PT_API int64_t pt_cache_param_count(const pt_cache* cache);
 PT_API pt_status pt_cache_get_params(pt_ctx* ctx, const pt_cache* cache, float* params);
 PT_API pt_status pt_cache_set_params(pt_ctx* ctx, pt_cache* cache, const float* params, void* stream);
 
-/* Raw network outputs (no clamp) for d_q [n][9] = x, wo, n -> d_out [n][3]. */
-PT_API pt_status pt_cache_eval(pt_ctx* ctx, const pt_cache* cache, int64_t n, const float* d_q, float* d_out,
-                               void* stream);
+/* Raw network outputs (no clamp) for d_q [n][9] = x, wo, n -> d_out [n][3].
+   precision PT_FP32 (FP32 throughout) or PT_BF16 (tcgen05 tensor cores: BF16
+   inputs, weights and activations, FP32 accumulation and biases; needs
+   n_freq = 12, hidden = 64, 5 hidden layers, else PT_EUNSUPPORTED). */
+PT_API pt_status pt_cache_eval(pt_ctx* ctx, const pt_cache* cache, int32_t precision, int64_t n, const float* d_q,
+                               float* d_out, void* stream);
 
 /* Relative L2 loss (y - t)^2 / (sg(y)^2 + 0.01), sg() holding the
    prediction constant in the gradient, averaged over all n x 3 entries;
@@ -359,7 +362,9 @@ PT_API pt_status pt_train_cache(pt_ctx* ctx, const pt_scene* scene, const pt_nif
                                 const pt_cache_train_cfg* cfg, float* d_loss, void* stream);
 
 /* pt_render_pixels with a radiance cache at vertex cache_vertex (cache and
-   cache_vertex >= 2 together, or NULL and 0) and, when rec_vertex > 0,
+   cache_vertex >= 2 together, or NULL and 0; the cache runs in BF16 on the
+   tensor cores when cfg->precision is not PT_FP32 and its shape allows, else
+   in FP32) and, when rec_vertex > 0,
    vertex records d_rec [spp][n_pix][16] of each path at rec_vertex: x[3],
    wo[3], n[3], throughput[3], radiance gathered before the vertex[3], valid
    (1.0 when the path hit there, else 0.0). */

@@ -74,6 +74,7 @@ struct pt_cache {
     int32_t J = 0, H = 0, L = 0, in0 = 0;
     int64_t n_params = 0;
     float* d_params = nullptr;      // flat FP32 weights (pt_cache_desc layout)
+    unsigned char* d_tc = nullptr;  // BF16 tensor-core image (J = 12, H = 64, L = 5 only), follows d_params
     CacheBox box = {};
     // online training state
     float* d_grad = nullptr;
@@ -918,6 +919,14 @@ PT_API pt_status pt_create_cache(pt_ctx* ctx, const pt_cache_desc* d, pt_cache**
         pt_destroy_cache(c);
         return fail(ctx, PT_ENOMEM, "cache parameter upload failed");
     }
+    if (cache_tc_supported(J, H, L)) {
+        if (cudaMalloc((void**)&c->d_tc, cache_tc_image_bytes()) != cudaSuccess ||
+            cudaMemset(c->d_tc, 0, cache_tc_image_bytes()) != cudaSuccess ||
+            repack_cache_tc(c->d_params, c->d_tc, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+            pt_destroy_cache(c);
+            return fail(ctx, PT_ENOMEM, "cache tensor-core image failed");
+        }
+    }
     *out = c;
     return PT_OK;
 }
@@ -927,6 +936,7 @@ PT_API void pt_destroy_cache(pt_cache* c)
     if (!c) return;
     cudaSetDevice(c->ctx->device);
     cudaFree(c->d_params);
+    cudaFree(c->d_tc);
     cudaFree(c->d_grad);
     cudaFree(c->d_m);
     cudaFree(c->d_v);
@@ -956,17 +966,27 @@ PT_API pt_status pt_cache_set_params(pt_ctx* ctx, pt_cache* c, const float* para
         PT_CUDA(cudaMemsetAsync(c->d_m, 0, c->n_params * sizeof(float), s));
         PT_CUDA(cudaMemsetAsync(c->d_v, 0, c->n_params * sizeof(float), s));
     }
+    if (c->d_tc) PT_CUDA(repack_cache_tc(c->d_params, c->d_tc, s));
     c->adam_t = 0;
     PT_CUDA(cudaStreamSynchronize(s));
     return PT_OK;
 }
 
-PT_API pt_status pt_cache_eval(pt_ctx* ctx, const pt_cache* c, int64_t n, const float* d_q, float* d_out, void* stream)
+PT_API pt_status pt_cache_eval(pt_ctx* ctx, const pt_cache* c, int32_t precision, int64_t n, const float* d_q,
+                               float* d_out, void* stream)
 {
     if (!ctx || !c || n < 0 || (n > 0 && (!d_q || !d_out))) return fail(ctx, PT_EINVAL, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;
+    if (precision == PT_FP32) {
+        PT_CUDA(timed(ctx, PT_KIND_CACHE, s, [&] {
+            return cache_eval(c->d_params, c->J, c->L, c->box, n, d_q, d_out, ctx->sm_count, s);
+        }));
+        return PT_OK;
+    }
+    if (precision != PT_BF16) return fail(ctx, PT_EINVAL, "cache precision is PT_FP32 or PT_BF16");
+    if (!c->d_tc) return fail(ctx, PT_EUNSUPPORTED, "the BF16 cache needs n_freq = 12, hidden = 64, 5 hidden layers");
     PT_CUDA(timed(ctx, PT_KIND_CACHE, s, [&] {
-        return cache_eval(c->d_params, c->J, c->L, c->box, n, d_q, d_out, ctx->sm_count, s);
+        return cache_eval_tc(c->d_tc, c->box, n, d_q, d_out, ctx->d_err, ctx->sm_count, s);
     }));
     return PT_OK;
 }
@@ -1031,8 +1051,10 @@ PT_API pt_status pt_train_cache(pt_ctx* ctx, const pt_scene* sc, const pt_nif* n
     const double c1 = 1.0 - std::pow((double)cfg->beta1, (double)(t + 1));
     const double c2 = 1.0 - std::pow((double)cfg->beta2, (double)(t + 1));
     PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] {
-        return adam_step(c->n_params, c->d_params, c->d_grad, c->d_m, c->d_v, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps,
-                         (float)c1, (float)c2, s);
+        cudaError_t e = adam_step(c->n_params, c->d_params, c->d_grad, c->d_m, c->d_v, cfg->lr, cfg->beta1, cfg->beta2,
+                                  cfg->eps, (float)c1, (float)c2, s);
+        if (e != cudaSuccess || !c->d_tc) return e;
+        return repack_cache_tc(c->d_params, c->d_tc, s);   // the BF16 image follows the master weights
     }));
     c->adam_t = t + 1;
     return PT_OK;
@@ -1126,7 +1148,13 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
             if (st != PT_OK) return st;
         }
         if (cache) {
+            // the cache runs in BF16 on the tensor cores whenever the NIF does (and the shape allows it)
+            const bool tc = cfg->precision != PT_FP32 && cache->d_tc;
             PT_CUDA(timed(ctx, PT_KIND_CACHE, s, [&] {
+                if (tc)
+                    return cache_query_tc(cache->d_tc, cache->box, chunk, ctx->counters + kCacheCounter,
+                                          ctx->cache_rows, ctx->slot_L, sc->dev.has_emission, ctx->d_err,
+                                          ctx->stats + kCacheStat, ctx->sm_count, s);
                 return cache_query(cache->d_params, cache->J, cache->L, cache->box, chunk,
                                    ctx->counters + kCacheCounter, ctx->cache_rows, ctx->slot_L, sc->dev.has_emission,
                                    ctx->d_err, ctx->stats + kCacheStat, ctx->sm_count, s);

@@ -107,7 +107,8 @@ struct TcParams {
     unsigned long long* stats;
 };
 
-__global__ void __maxnreg__(80) k_nif_tc(const TcParams p, int mode)
+// 25 warps: the busiest SM sub-partition holds seven of them (16K registers), so at most 72 per thread
+__global__ void __maxnreg__(72) k_nif_tc(const TcParams p, int mode)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);

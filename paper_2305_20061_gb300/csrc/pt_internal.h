@@ -204,6 +204,15 @@ cudaError_t cache_eval(const float* params, int J, int L, CacheBox box, int64_t 
 cudaError_t cache_query(const float* params, int J, int L, CacheBox box, int64_t cap, const uint32_t* n_dev,
                         const float* rows, float* slot_L, int accumulate, uint32_t* err, unsigned long long* stats,
                         int sm_count, cudaStream_t s);
+// BF16 tensor-core cache (cache_tc.cu): J = 12, H = 64, L = 5 only
+bool cache_tc_supported(int J, int H, int L);
+size_t cache_tc_image_bytes();
+cudaError_t repack_cache_tc(const float* params, unsigned char* image, cudaStream_t s);
+cudaError_t cache_eval_tc(const unsigned char* image, CacheBox box, int64_t n, const float* q, float* out,
+                          uint32_t* err, int sm_count, cudaStream_t s);
+cudaError_t cache_query_tc(const unsigned char* image, CacheBox box, int64_t cap, const uint32_t* n_dev,
+                           const float* rows, float* slot_L, int accumulate, uint32_t* err, unsigned long long* stats,
+                           int sm_count, cudaStream_t s);
 // rebuild the packed FP32 layout and (when present) the tensor-core image from the master weights
 cudaError_t repack_nif_fp32(const float* params, int F, int H, int L, float* packed, cudaStream_t s);
 cudaError_t repack_nif_tc_image(const float* params, unsigned char* image, cudaStream_t s);

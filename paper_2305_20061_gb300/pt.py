@@ -119,7 +119,7 @@ def lib():
             "pt_cache_param_count": ([P], I64),
             "pt_cache_get_params": ([P, P, P], I32),
             "pt_cache_set_params": ([P, P, P, P], I32),
-            "pt_cache_eval": ([P, P, I64, P, P, P], I32),
+            "pt_cache_eval": ([P, P, I32, I64, P, P, P], I32),
             "pt_cache_loss_grad": ([P, P, I64, P, P, P, P, P, P], I32),
             "pt_train_cache": ([P, P, P, P, P, P, P], I32),
             "pt_render_cached": ([P, P, P, P, I32, I32, P, I64, P, P, P, P, P, P], I32),
@@ -336,11 +336,12 @@ class Cache:
         assert flat.size == self.param_count
         self.ctx._raise(lib().pt_cache_set_params(self.ctx.h, self.h, _np_ptr(flat), _stream(stream)))
 
-    def eval(self, q: torch.Tensor, stream=None) -> torch.Tensor:
+    def eval(self, q: torch.Tensor, precision: str = "fp32", stream=None) -> torch.Tensor:
         """pt_cache_eval: raw outputs [n, 3] for queries [n, 9] (x, wo, n)."""
         q = q.contiguous()
         out = torch.empty((q.shape[0], 3), dtype=torch.float32, device=q.device)
-        self.ctx._raise(lib().pt_cache_eval(self.ctx.h, self.h, q.shape[0], _dptr(q), _dptr(out), _stream(stream)))
+        self.ctx._raise(lib().pt_cache_eval(self.ctx.h, self.h, PRECISIONS[precision], q.shape[0], _dptr(q),
+                                            _dptr(out), _stream(stream)))
         return out
 
     def loss_grad(self, q: torch.Tensor, target: torch.Tensor, mask: Optional[torch.Tensor] = None, stream=None):

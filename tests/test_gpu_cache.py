@@ -70,6 +70,69 @@ def test_cache_eval_empty(pt, ctx):
     assert out.shape == (0, 3)
 
 
+def _bf16(x):
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    return ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32).view(np.float32)
+
+
+def _bf16_cache_model(c, q):
+    """Rounding model of the tensor-core cache: BF16 encoding, weights and
+    activations, biases as BF16 hi + lo, FP64 sums standing in for FP32
+    accumulation, FP32 output bias."""
+    q = q.astype(np.float64)
+    lo, hi = c.lo.astype(np.float64), c.hi.astype(np.float64)
+    p = (q[:, :3] - lo) / (hi - lo)
+    feats = []
+    for a in range(3):
+        ang = np.pi * p[:, a:a + 1] * (2.0 ** np.arange(c.n_freq))[None]
+        feats += [np.sin(ang), np.cos(ang)]
+    x = _bf16(np.concatenate(feats + [q[:, 3:9]], 1).astype(np.float32)).astype(np.float64)
+    for W, b in zip(c.W[:-1], c.b[:-1]):
+        bh = _bf16(b).astype(np.float64)
+        bl = _bf16((b.astype(np.float64) - bh).astype(np.float32)).astype(np.float64)
+        x = _bf16(np.maximum(x @ _bf16(W).astype(np.float64).T + bh + bl, 0).astype(np.float32)).astype(np.float64)
+    return x @ _bf16(c.W[-1]).astype(np.float64).T + c.b[-1].astype(np.float64)
+
+
+@pytest.mark.parametrize("n", [1, 129, 128 * 152 * 4 * 2 + 77])
+def test_bf16_cache_matches_rounding_model(pt, ctx, n):
+    """The tcgen05 cache kernel against a numpy model of its own rounding, and
+    its error against the FP64 oracle (reported; a loose bound guards against
+    gross errors)."""
+    lo, hi = np.array([-1.0, -0.2, -1.0], np.float32), np.array([1.0, 0.2, 1.0], np.float32)
+    c = _cache(lo, hi, seed=41)
+    q = _queries(n, lo, hi, seed=n + 3)
+    gc = pt.Cache(ctx, c)
+    got = gc.eval(torch.from_numpy(q).cuda(), precision="bf16").cpu().numpy().astype(np.float64)
+    ctx.check()
+    ref = _bf16_cache_model(c, q)
+    scale = np.abs(ref).max()
+    err = np.abs(got - ref)
+    assert np.median(err) <= 2e-3 * scale and err.max() <= 3e-2 * scale, (np.median(err) / scale, err.max() / scale)
+    exact = O.Cache(c).forward(q.astype(np.float64))
+    rel = float(np.sqrt(((got - exact) ** 2).sum() / (exact ** 2).sum()))
+    print(f"BF16 cache vs FP64 oracle: relative RMSE {rel:.3e} over {n} queries")
+    assert rel <= 5e-2
+
+
+def test_bf16_cached_render_close_to_fp32(pt, ctx):
+    """A cached render with the BF16 NIF and BF16 cache against the same render
+    in FP32: same paths, image relative RMSE from the two networks' rounding."""
+    sc, nif = _box_setup(pt, ctx)
+    lo, hi = I.scene_bounds(sc)
+    c = _cache(lo, hi, seed=43, bias_std=0.5)
+    cfg = I.RenderCfg(64, 64, 4, 4, 0)
+    s, gc = pt.Scene(ctx, sc), pt.Cache(ctx, c)
+    nif_tc = I.nif_init(colour="yuv")
+    g = pt.Nif(ctx, nif_tc)
+    a = pt.render_cached(ctx, s, g, cfg, None, cache=gc, cache_vertex=2, precision="bf16")[0].cpu().numpy()
+    b = pt.render_cached(ctx, s, g, cfg, None, cache=gc, cache_vertex=2, precision="fp32")[0].cpu().numpy()
+    ctx.check()
+    rel = rel_rmse(a, b)
+    print(f"BF16 vs FP32 cached render: relative RMSE {rel:.3e}")
+    assert rel <= 2e-2
+
+
 def test_cache_loss_grad_matches_oracle(pt, ctx):
     """Relative L2 with the prediction held constant in the denominator;
     20% of the rows masked; 3000 rows (ragged against the 128-row tiles)."""
