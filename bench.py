@@ -367,7 +367,7 @@ def bench_ours(args):
                   BYTES_TRI * work["triangle"] + BYTES_RAY * rays)
         peak = float(meas["hbm_gbs"])
         achieved = nbytes / (trace_ms * 1e-3) / 1e9
-        roof = {"kernel": "k_bounce", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        roof = {"kernel": "k_trace+k_bounce", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
                 "per_unit": f"bytes per node fetch {BYTES_NODE}, per sphere/quad/triangle test "
                             f"{BYTES_SPHERE}/{BYTES_QUAD}/{BYTES_TRI}, per ray {BYTES_RAY}; {work['nodes']} node "
@@ -378,7 +378,7 @@ def bench_ours(args):
                OPS_TRI * work["triangle"])
         peak = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6 / 1e12
         achieved = ops / (trace_ms * 1e-3) / 1e12
-        roof = {"kernel": "k_bounce", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
+        roof = {"kernel": "k_trace+k_bounce", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
                 "frac": achieved / peak, "traffic": None,
                 "per_unit": f"FP32 ops per node fetch {OPS_NODE}, per sphere/quad/triangle test "
                             f"{OPS_SPHERE}/{OPS_QUAD}/{OPS_TRI}; {work['nodes']} node fetches and "
@@ -660,7 +660,7 @@ def bench_c5(args):
                OPS_TRI * work["triangle"])
         peak = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6 / 1e12
         achieved = ops / (t_tr * 1e-3) / 1e12
-        roof = {"kernel": "k_bounce", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
+        roof = {"kernel": "k_trace+k_bounce", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
                 "frac": achieved / peak, "traffic": None,
                 "per_unit": f"FP32 ops per node fetch {OPS_NODE}, per triangle test {OPS_TRI}; {work['nodes']} node "
                             f"fetches and {work['triangle']} triangle tests in the cached render "
