@@ -153,8 +153,9 @@ typedef struct pt_nif_desc {
     const float* params;       /* host, flat: B[F][2], then per layer W[out][in], b[out], then M[3][3] */
 } pt_nif_desc;
 
-/* Upload FP32 master weights and build the BF16 / FP8 operand images used by
-   the tensor-core kernel (when the shape is F = 64, H = 128, L = 3). */
+/* Upload FP32 master weights and build the BF16 operand image of the
+   tensor-core kernel (when the shape is F = 64, H = 128, L = 3; the FP8 image
+   is built on first use, see pt_nif_fp8_scales). */
 PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* desc, pt_nif** out);
 PT_API void pt_destroy_nif(pt_nif* nif);
 /* number of floats in the flat layout */
@@ -174,7 +175,10 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nif, int32_t precision, 
    (value = scale x E4M3 code).  Features use 1/448; hidden layers use their
    maximum over the FP32 network on a 32 x 32 grid of (u, v) pixel centres,
    divided by 448.  Weights use one scale per output row (row max / 448).
-   PT_EUNSUPPORTED for shapes other than F = 64, H = 128, L = 3. */
+   PT_EUNSUPPORTED for shapes other than F = 64, H = 128, L = 3.  The FP8
+   image (and with it these scales) is built on its first use after loading or
+   after the weights change: that call synchronises the device and runs the
+   calibration on the host. */
 PT_API pt_status pt_nif_fp8_scales(const pt_nif* nif, float* scales);
 
 /* Replace the FP32 master weights (host, flat layout of pt_nif_desc) and

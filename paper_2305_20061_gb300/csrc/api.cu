@@ -53,8 +53,12 @@ struct pt_nif {
     float* d_params = nullptr;   // flat FP32 master weights
     float* d_fp32 = nullptr;     // packed FP32 layout (Wt, bias, Wout, bout)
     unsigned char* d_tc = nullptr;  // BF16 shared-memory image of the tensor-core kernel (F=64, H=128, L=3 only)
-    unsigned char* d_fp8 = nullptr; // FP8 E4M3 image of the same shape
-    float fp8_scales[4] = {0, 0, 0, 0};
+    // FP8 E4M3 image of the same shape, built on first use (its calibration runs on the host) and
+    // rebuilt on the next use after the weights change
+    bool fp8_ok = false;
+    mutable unsigned char* d_fp8 = nullptr;
+    mutable bool fp8_stale = true;
+    mutable float fp8_scales[4] = {0, 0, 0, 0};
     DevNif dev = {};
     // training state (allocated by the first training call)
     int64_t n_trainable = 0;
@@ -235,6 +239,26 @@ pt_status check_cfg(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, const
     return PT_OK;
 }
 
+// Builds (or rebuilds after a weight change) the FP8 image: the calibration of
+// its activation scales runs on the host, so the master weights round-trip.
+pt_status ensure_fp8(pt_ctx* ctx, const pt_nif* nf, cudaStream_t s)
+{
+    if (!nf->fp8_ok) return fail(ctx, PT_EUNSUPPORTED, "the FP8 NIF needs F = 64, H = 128, L = 3");
+    if (nf->d_fp8 && !nf->fp8_stale) return PT_OK;
+    std::vector<float> host(nf->n_params);
+    std::vector<unsigned char> img;
+    PT_CUDA(cudaMemcpyAsync(host.data(), nf->d_params, host.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    PT_CUDA(cudaStreamSynchronize(s));
+    if (!pack_nif_fp8_image(host.data(), nf->F, nf->H, nf->L, img, nf->fp8_scales))
+        return fail(ctx, PT_EINVAL, "FP8 packing failed");
+    if (!nf->d_fp8 && cudaMalloc((void**)&nf->d_fp8, img.size()) != cudaSuccess)
+        return fail(ctx, PT_ENOMEM, "NIF FP8 image allocation failed");
+    PT_CUDA(cudaMemcpyAsync(nf->d_fp8, img.data(), img.size(), cudaMemcpyHostToDevice, s));
+    PT_CUDA(cudaStreamSynchronize(s));
+    nf->fp8_stale = false;
+    return PT_OK;
+}
+
 pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, int accumulate, cudaStream_t s)
 {
     NifEvalParams p = {};
@@ -254,7 +278,9 @@ pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, int ac
         PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nif->d_tc, p, 1, ctx->sm_count, s); }));
         return PT_OK;
     }
-    if (precision == PT_FP8E4M3 && nif->d_fp8) {
+    if (precision == PT_FP8E4M3 && nif->fp8_ok) {
+        const pt_status st = ensure_fp8(ctx, nif, s);
+        if (st != PT_OK) return st;
         PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_fp8(nif->d_fp8, p, 1, ctx->sm_count, s); }));
         return PT_OK;
     }
@@ -584,13 +610,7 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
             return fail(ctx, PT_ENOMEM, "NIF tensor-core image upload failed");
         }
     }
-    if (pack_nif_fp8_image(d->params, F, H, L, img, nf->fp8_scales)) {
-        if (cudaMalloc((void**)&nf->d_fp8, img.size()) != cudaSuccess ||
-            cudaMemcpy(nf->d_fp8, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-            pt_destroy_nif(nf);
-            return fail(ctx, PT_ENOMEM, "NIF FP8 image upload failed");
-        }
-    }
+    nf->fp8_ok = F == 64 && H == 128 && L == 3;
     *out = nf;
     return PT_OK;
 }
@@ -641,7 +661,9 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
         PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nf->d_tc, p, 0, ctx->sm_count, s); }));
         return PT_OK;
     }
-    if (precision == PT_FP8E4M3 && nf->d_fp8) {
+    if (precision == PT_FP8E4M3 && nf->fp8_ok) {
+        const pt_status st = ensure_fp8(ctx, nf, s);
+        if (st != PT_OK) return st;
         PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_fp8(nf->d_fp8, p, 0, ctx->sm_count, s); }));
         return PT_OK;
     }
@@ -718,17 +740,7 @@ pt_status refresh_layouts(pt_ctx* ctx, pt_nif* nf, cudaStream_t s)
 {
     PT_CUDA(repack_nif_fp32(nf->d_params, nf->F, nf->H, nf->L, nf->d_fp32, s));
     if (nf->d_tc) PT_CUDA(repack_nif_tc_image(nf->d_params, nf->d_tc, s));
-    if (nf->d_fp8) {
-        // the FP8 image needs the host calibration pass: round-trip the master weights
-        std::vector<float> host(nf->n_params);
-        std::vector<unsigned char> img;
-        PT_CUDA(cudaMemcpyAsync(host.data(), nf->d_params, host.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
-        PT_CUDA(cudaStreamSynchronize(s));
-        if (!pack_nif_fp8_image(host.data(), nf->F, nf->H, nf->L, img, nf->fp8_scales))
-            return fail(ctx, PT_EINVAL, "FP8 repack failed");
-        PT_CUDA(cudaMemcpyAsync(nf->d_fp8, img.data(), img.size(), cudaMemcpyHostToDevice, s));
-        PT_CUDA(cudaStreamSynchronize(s));
-    }
+    nf->fp8_stale = true;   // rebuilt on its next use
     return PT_OK;
 }
 
@@ -787,7 +799,9 @@ PT_API pt_status pt_train_nif(pt_ctx* ctx, pt_nif* nf, const float* d_sky, int32
 PT_API pt_status pt_nif_fp8_scales(const pt_nif* nf, float* scales)
 {
     if (!nf || !scales) return PT_EINVAL;
-    if (!nf->d_fp8) return PT_EUNSUPPORTED;
+    if (!nf->fp8_ok) return PT_EUNSUPPORTED;
+    const pt_status st = ensure_fp8(nf->ctx, nf, 0);
+    if (st != PT_OK) return st;
     for (int i = 0; i < 4; ++i) scales[i] = nf->fp8_scales[i];
     return PT_OK;
 }
@@ -1078,7 +1092,7 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
     const int64_t n_slots = n_pix * (int64_t)cfg->spp;
     if (n_slots > 0xFFFFFFFFll) return fail(ctx, PT_EINVAL, "more than 2^32 - 1 paths in one call");
     if (sc->dev.env_is_nif && cfg->precision != PT_FP32 && !(cfg->precision == PT_BF16 && nf->d_tc) &&
-        !(cfg->precision == PT_FP8E4M3 && nf->d_fp8))
+        !(cfg->precision == PT_FP8E4M3 && nf->fp8_ok))
         return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3");
     // chunk = whole samples
     int64_t chunk = cfg->chunk_slots > 0 ? cfg->chunk_slots : (int64_t)1 << 24;
