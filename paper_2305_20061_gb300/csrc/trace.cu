@@ -165,8 +165,11 @@ __device__ __forceinline__ void store_L(float* slot_L, uint32_t slot, float3 L, 
 constexpr int kRefillMin = PT_TRACE_REFILL_MIN;
 constexpr int kStepsPerCheck = PT_TRACE_STEPS;
 
+#ifndef PT_TRACE_MIN_BLOCKS
+#define PT_TRACE_MIN_BLOCKS 4
+#endif
 template <bool kWide>
-__global__ void __launch_bounds__(256, 4) k_trace(const BounceParams p)
+__global__ void __launch_bounds__(256, PT_TRACE_MIN_BLOCKS) k_trace(const BounceParams p)
 {
     const uint32_t count = (p.k == 1) ? p.n_chunk : min(*p.count_in, p.cap);
     const uint32_t lane = threadIdx.x & 31;
@@ -468,8 +471,8 @@ int grid_for(int64_t n, int block, int sm_count, int per_sm)
 cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s)
 {
     // traversal: persistent, 4 resident blocks of 256 threads per SM; shading: grid-stride over the queue
-    if (p.sc.wnodes) k_trace<true><<<sm_count * 4, 256, 0, s>>>(p);
-    else k_trace<false><<<sm_count * 4, 256, 0, s>>>(p);
+    if (p.sc.wnodes) k_trace<true><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
+    else k_trace<false><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
     k_bounce<<<sm_count * 8, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
