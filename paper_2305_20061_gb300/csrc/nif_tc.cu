@@ -5,25 +5,21 @@
 // The paper keeps the network's weights in IPU tile SRAM and lets the
 // Poplibs planner replicate layers across tiles (Section 3.3.1); here one
 // persistent CTA per SM holds all BF16 weights in shared memory for the
-// whole kernel and streams 128-row tiles of queries through them:
-//
-//   warps 0..23  three groups of eight; group s owns tile slot s.  Within a
-//                group, warps 4h..4h+3 handle half h of every row: row t is
-//                TMEM lane t, and half h covers accumulator columns
-//                [64h, 64h + 64) and Fourier frequencies [32h, 32h + 32).
-//                They compute the features, and after each MMA read their
-//                accumulator half-row from TMEM (bias included), apply ReLU
-//                while packing to BF16 and write it back into the slot's
-//                operand buffer in the UMMA SWIZZLE_128B K-major layout.
-//   warp 24      allocates TMEM; lane 0 issues every tcgen05.mma (128x128x16
-//                BF16 -> FP32 for the hidden layers plus one K = 16 step that
-//                adds the bias, 128x16x16 for the head) and commits each
-//                layer to the slot's mbarrier.
-//
-// Three slots in flight let the epilogue of one tile overlap the MMAs of
-// the others.  Every wait is bounded in time: a wait that gives up sets
-// PT_ERR_TIMEOUT, raises a CTA-wide abort flag, drains in-flight MMAs and
-// frees TMEM before the CTA returns.
+// whole kernel and streams 128-row tiles of queries through them.  Three
+// tile slots of eight warps each; within a slot, warps 4h..4h+3 handle half h
+// of every row: row t is TMEM lane t, and half h covers accumulator columns
+// [64h, 64h + 64) and Fourier frequencies [32h, 32h + 32).  A slot's warps
+// compute the features, and after each MMA read their accumulator half-row
+// from TMEM (bias included), apply ReLU while packing to BF16 and write it
+// back into the slot's operand buffer in the UMMA SWIZZLE_128B K-major
+// layout.  Each step ends with a slot-wide named barrier (bar.red.or, which
+// also carries the abort vote); the slot's first thread then issues the next
+// tcgen05.mma group itself (128x128x16 BF16 -> FP32 for the hidden layers
+// plus one K = 16 step that adds the bias, 128x16x16 for the head) and
+// commits it to the slot's mbarrier.  With three slots in flight the
+// epilogue of one tile overlaps the MMAs of the others.  Every wait is
+// bounded in time: a wait that gives up sets PT_ERR_TIMEOUT, raises a
+// CTA-wide abort flag, drains in-flight MMAs and frees TMEM.
 #include <cstring>
 #include <vector>
 
@@ -39,8 +35,7 @@ namespace {
 
 constexpr int kF = 64, kH = 128, kRows = 128;
 constexpr int kSlots = 3;
-constexpr int kThreads = 25 * 32;        // 3 slots x 8 epilogue warps + the MMA warp
-constexpr int kMmaWarp = 24;
+constexpr int kThreads = kSlots * 8 * 32;   // 3 slots x 8 warps
 constexpr uint32_t kTmemCols = 512;
 
 // shared-memory image (offsets from a 1024-byte aligned base)
@@ -107,44 +102,59 @@ struct TcParams {
     unsigned long long* stats;
 };
 
-// 25 warps: the busiest SM sub-partition holds seven of them (16K registers), so at most 72 per thread
-__global__ void __maxnreg__(72) k_nif_tc(const TcParams p, int mode)
+
+// bar.red.or over the 256 threads of a slot: true on every thread if any passed true
+__device__ __forceinline__ bool slot_vote_any(int id, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\n"
+        "setp.ne.u32 p, %1, 0;\n"
+        "bar.red.or.pred q, %2, 256, p;\n"
+        "selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id)
+        : "memory");
+    return r != 0;
+}
+
+// 24 warps: six per SM sub-partition, so up to 80 registers per thread
+__global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mode)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar_a = sbase + kOffBar;            // [kSlots] operand ready (count 128)
-    const uint32_t bar_acc = bar_a + 8 * kSlots;        // [kSlots] accumulator ready (commit)
-    const uint32_t bar_w = bar_acc + 8 * kSlots;        // weights loaded
-    const uint32_t bar_drain = bar_w + 8;               // final drain after an abort
+    const uint32_t bar_acc = sbase + kOffBar;            // [kSlots] accumulator ready (commit)
+    const uint32_t bar_w = bar_acc + 8 * kSlots;         // weights loaded
+    const uint32_t bar_drain = bar_w + 8;                // [kSlots] final drain after an abort
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 64);
     volatile int* abort = reinterpret_cast<volatile int*>(smem + kOffBar + 68);
     const float* tail = reinterpret_cast<const float*>(smem + kOffTail);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = warp >> 3;                       // tile slot (8 warps each)
+    const int half = (warp >> 2) & 1;              // which 64 columns / 32 frequencies of the row
+    const uint32_t row = (warp & 3) * 32 + lane;   // row in tile == TMEM lane
+    const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
     const int64_t count = mode == 0 ? p.n : (int64_t)min(*p.esc_count, p.esc_cap);
     const int64_t n_tiles = (count + kRows - 1) / kRows;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kSlots; ++s) {
-            mbar_init(bar_a + 8 * s, 2 * kRows);   // both halves of the slot arrive
-            mbar_init(bar_acc + 8 * s, 1);
+        for (int t = 0; t < kSlots; ++t) {
+            mbar_init(bar_acc + 8 * t, 1);
+            mbar_init(bar_drain + 8 * t, 1);
         }
         mbar_init(bar_w, 1);
-        mbar_init(bar_drain, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        // one bulk copy per 32 KB piece of the weight image, all on bar_w
         mbar_expect_tx(bar_w, kImageBytes);
-        for (uint32_t off = 0; off < kImageBytes; off += 32768u) {
-            const uint32_t sz = min(32768u, kImageBytes - off);
-            bulk_g2s(sbase + off, p.image + off, sz, bar_w);
-        }
+        for (uint32_t off = 0; off < kImageBytes; off += 32768u)
+            bulk_g2s(sbase + off, p.image + off, min(32768u, kImageBytes - off), bar_w);
     }
-    if (warp == kMmaWarp) {
+    if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -154,127 +164,50 @@ __global__ void __maxnreg__(72) k_nif_tc(const TcParams p, int mode)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     mbar_wait(bar_w, 0, abort, p.err);
+    __syncthreads();
+    bool dead = *abort != 0;   // CTA-uniform
 
-    if (warp == kMmaWarp) {
-        // ------------------------------------------------------------- MMA issuer
-        if (lane == 0 && !*abort) {
-            const uint32_t id_h = idesc_bf16(128, 128), id_o = idesc_bf16(128, kHeadRows);
-            // Event loop: serve whichever slot has its operand ready, so a slow
-            // epilogue in one slot never holds back the MMAs of the others.
-            uint32_t ph[kSlots] = {0, 0, 0};
-            int stage[kSlots] = {0, 0, 0};
-            int64_t it[kSlots] = {0, 0, 0};
-            int live = 0;
-            bool done[kSlots];
-            for (int s = 0; s < kSlots; ++s) {
-                done[s] = ((int64_t)blockIdx.x * kSlots + s) >= n_tiles;
-                live += done[s] ? 0 : 1;
-            }
-            uint64_t last = global_ns();
-            while (live > 0 && !*abort) {
-                bool progressed = false;
-                for (int s = 0; s < kSlots; ++s) {
-                    if (done[s] || !mbar_test_wait(bar_a + 8 * s, ph[s])) continue;
-                    progressed = true;
-                    ph[s] ^= 1;
-                    tc_fence_after();
-                    const uint32_t a_base = sbase + kOffA + s * kABytes;
-                    if (stage[s] < 3) {
-                        const uint32_t w_base = sbase + kOffW + stage[s] * kWBytes;
-                        const uint32_t d = tmem + s * 128;
-#pragma unroll
-                        for (int kk = 0; kk < 8; ++kk) {
-                            const uint32_t koff = (kk >> 2) * (kRows * 128) + (kk & 3) * 32;
-                            mma_bf16(d, sw128_desc(a_base + koff), sw128_desc(w_base + koff), id_h, kk > 0);
-                        }
-                        // + bias: ones x (hi, lo)
-                        mma_bf16(d, plain_desc(sbase + kOffOnes, kBiasLbo, kBiasSbo),
-                                 plain_desc(sbase + kOffBias + stage[s] * kBiasBytes, kBiasLbo, kBiasSbo), id_h, 1);
-                    } else {
-                        const uint32_t d = tmem + 384 + 32 * s;
-#pragma unroll
-                        for (int kk = 0; kk < 8; ++kk) {
-                            const uint32_t aoff = (kk >> 2) * (kRows * 128) + (kk & 3) * 32;
-                            const uint32_t boff = (kk >> 2) * (kHeadRows * 128) + (kk & 3) * 32;
-                            mma_bf16(d, sw128_desc(a_base + aoff), sw128_desc(sbase + kOffHead + boff), id_o, kk > 0);
-                        }
-                    }
-                    mma_commit(bar_acc + 8 * s);
-                    if (++stage[s] == 4) {
-                        stage[s] = 0;
-                        ++it[s];
-                        if ((it[s] * gridDim.x + blockIdx.x) * kSlots + s >= n_tiles) {
-                            done[s] = true;
-                            --live;
-                        }
-                    }
-                }
-                if (progressed) {
-                    last = global_ns();
-                } else {
-                    __nanosleep(32);   // nothing ready: yield the issue slots to the epilogue warps
-                }
-                if (!progressed && global_ns() - last > kWaitBudgetNs) {
-                    atomicOr(p.err, PT_ERR_TIMEOUT);
-                    *abort = 1;
-                }
-            }
-            if (*abort) {
-                // make sure no MMA is still writing TMEM before it is freed
-                mma_commit(bar_drain);
-                const uint64_t t0 = global_ns();
-                while (!mbar_try_wait(bar_drain, 0) && global_ns() - t0 < kWaitBudgetNs) {
-                }
+    const bool issuer = (warp & 7) == 0 && lane == 0;
+    const int bar_id = 1 + s;
+    const uint32_t a_base = sbase + kOffA + s * kABytes;
+    const uint32_t acc = tmem + s * 128;
+    const uint32_t head = tmem + 384 + 32 * s;
+    const uint32_t bar = bar_acc + 8 * s;
+    const float* Bm = tail + 3 * kH + 4;
+    const float* Mm = Bm + 2 * kF;
+    const uint32_t id_h = idesc_bf16(128, 128), id_o = idesc_bf16(128, kHeadRows);
+    uint32_t ph = 0;
+    auto load_inputs = [&](int64_t tile) {
+        TileIn t = {};
+        const int64_t gg = tile * kRows + row;
+        if (tile < n_tiles && gg < count) {
+            if (mode == 0) {
+                const float2 q = reinterpret_cast<const float2*>(p.uv)[gg];
+                t.u = q.x; t.v = q.y;
+            } else {
+                const float2* e = reinterpret_cast<const float2*>(p.esc + gg);
+                const float2 a = e[0], b = e[1], c = e[2];
+                t.slot = __float_as_uint(a.x); t.u = a.y; t.v = b.x; t.tr = b.y; t.tg = c.x; t.tb = c.y;
             }
         }
-    } else {
-        // ------------------------------------------------------- epilogue warps
-        const int s = warp >> 3;                       // tile slot (8 warps each)
-        const int half = (warp >> 2) & 1;              // which 64 columns / 32 frequencies of the row
-        const uint32_t row = (warp & 3) * 32 + lane;   // row in tile == TMEM lane
-        const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
-        const uint32_t a_base = sbase + kOffA + s * kABytes;
-        const float* Bm = tail + 3 * kH + 4;
-        const float* Mm = Bm + 2 * kF;
-        uint32_t ph = 0;
-        // inputs of this thread's row of a tile, loaded one tile ahead so the
-        // global-memory latency hides behind the previous tile's MMA chain
-        auto load_inputs = [&](int64_t tile) {
-            TileIn t = {};
-            const int64_t gg = tile * kRows + row;
-            if (tile < n_tiles && gg < count) {
-                if (mode == 0) {
-                    const float2 q = reinterpret_cast<const float2*>(p.uv)[gg];
-                    t.u = q.x; t.v = q.y;
-                } else {
-                    const float2* e = reinterpret_cast<const float2*>(p.esc + gg);
-                    const float2 a = e[0], b = e[1], c = e[2];
-                    t.slot = __float_as_uint(a.x); t.u = a.y; t.v = b.x; t.tr = b.y; t.tg = c.x; t.tb = c.y;
-                }
-            }
-            return t;
-        };
-        TileIn in = load_inputs(((int64_t)0 * gridDim.x + blockIdx.x) * kSlots + s);
-        for (int64_t i = 0;; ++i) {
-            const int64_t tile = ((int64_t)i * gridDim.x + blockIdx.x) * kSlots + s;
-            if (tile >= n_tiles) break;
-            if (__any_sync(0xFFFFFFFFu, *abort != 0)) break;  // warp-uniform exit
-            const int64_t g = tile * kRows + row;
-            const bool valid = g < count;
-            const float u = in.u, v = in.v, tr = in.tr, tg = in.tg, tb = in.tb;
-            const uint32_t slot = in.slot;
-            // Fourier features [sin 2 pi (Bx)_i, cos 2 pi (Bx)_i]: phase reduced to one turn in FP32,
-            // then the hardware sine / cosine (the result is rounded to BF16)
-            const uint64_t uu = pack_f32x2(u, u), vv = pack_f32x2(v, v);
+        return t;
+    };
+    TileIn in = load_inputs((int64_t)blockIdx.x * kSlots + s);
+    for (int64_t i = 0; !dead; ++i) {
+        const int64_t tile = ((int64_t)i * gridDim.x + blockIdx.x) * kSlots + s;
+        if (tile >= n_tiles) break;   // slot-uniform
+        const int64_t g = tile * kRows + row;
+        const bool valid = g < count;
+        {
+            const uint64_t uu = pack_f32x2(in.u, in.u), vv = pack_f32x2(in.v, in.v);
             const uint64_t two_pi = pack_f32x2(6.28318530717958648f, 6.28318530717958648f);
 #pragma unroll 1
             for (int c8 = half * 4; c8 < half * 4 + 4; ++c8) {
                 uint32_t sp[4], cp[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    // frequencies f, f + 1 in packed FP32 pairs: t = B0 u + B1 v, r = t - rint(t)
                     const int f = c8 * 8 + 2 * j;
-                    const float4 bq = *reinterpret_cast<const float4*>(Bm + 2 * f);   // B0 B1 of f, f + 1
+                    const float4 bq = *reinterpret_cast<const float4*>(Bm + 2 * f);
                     const uint64_t t = fma_f32x2(pack_f32x2(bq.x, bq.z), uu, mul_f32x2(pack_f32x2(bq.y, bq.w), vv));
                     const uint64_t r = sub_f32x2(t, pack_f32x2(rintf(lo_f32(t)), rintf(hi_f32(t))));
                     const uint64_t a = mul_f32x2(r, two_pi);
@@ -287,26 +220,49 @@ __global__ void __maxnreg__(72) k_nif_tc(const TcParams p, int mode)
                 st_shared_v4(a_base + sw128_chunk(row, c8), sp[0], sp[1], sp[2], sp[3]);
                 st_shared_v4(a_base + sw128_chunk(row, kF / 8 + c8), cp[0], cp[1], cp[2], cp[3]);
             }
-            fence_proxy_async();
-            mbar_arrive(bar_a + 8 * s);
-            const TileIn next = load_inputs(((int64_t)(i + 1) * gridDim.x + blockIdx.x) * kSlots + s);
-
-            bool ok = true;
-            for (int layer = 0; layer < 3; ++layer) {
-                const bool got = mbar_wait(bar_acc + 8 * s, ph, abort, p.err);
-                if (!__all_sync(0xFFFFFFFFu, got)) { ok = false; break; }  // tcgen05.ld needs the whole warp
-                ph ^= 1;
+        }
+        const float tr = in.tr, tg = in.tg, tb = in.tb;
+        const uint32_t slot = in.slot;
+        in = load_inputs(((int64_t)(i + 1) * gridDim.x + blockIdx.x) * kSlots + s);
+        fence_proxy_async();
+        bool fail = false;
+        for (int stage = 0; stage < 4; ++stage) {   // three hidden layers, then the head
+            tc_fence_before();
+            if (slot_vote_any(bar_id, fail)) { dead = true; break; }
+            if (issuer) {
                 tc_fence_after();
-                // this half-row's 64 accumulator columns in four groups of 16, the TMEM load of
-                // group g + 1 in flight while group g is packed (the bias is already in the
-                // accumulator: ReLU while rounding to BF16) and stored
-                const uint32_t tcol = tmem + lane_base + s * 128 + half * 64;
+                if (stage < 3) {
+                    const uint32_t w_base = sbase + kOffW + stage * kWBytes;
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const uint32_t koff = (kk >> 2) * (kRows * 128) + (kk & 3) * 32;
+                        mma_bf16(acc, sw128_desc(a_base + koff), sw128_desc(w_base + koff), id_h, kk > 0);
+                    }
+                    mma_bf16(acc, plain_desc(sbase + kOffOnes, kBiasLbo, kBiasSbo),
+                             plain_desc(sbase + kOffBias + stage * kBiasBytes, kBiasLbo, kBiasSbo), id_h, 1);
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const uint32_t aoff = (kk >> 2) * (kRows * 128) + (kk & 3) * 32;
+                        const uint32_t boff = (kk >> 2) * (kHeadRows * 128) + (kk & 3) * 32;
+                        mma_bf16(head, sw128_desc(a_base + aoff), sw128_desc(sbase + kOffHead + boff), id_o, kk > 0);
+                    }
+                }
+                mma_commit(bar);
+            }
+            const bool got = mbar_wait(bar, ph, abort, p.err);
+            ph ^= 1;
+            tc_fence_after();
+            if (!__all_sync(0xFFFFFFFFu, got)) { fail = true; continue; }   // voted at the next barrier
+            if (stage < 3) {
+                const uint32_t tcol = acc + lane_base + half * 64;
                 uint32_t ra[16], rb[16];
-                auto put16 = [&](const uint32_t (&x)[16], int g) {
+                auto put16 = [&](const uint32_t (&x)[16], int gq) {
                     uint32_t pk[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) pk[j] = pack_relu_bf16(__uint_as_float(x[2 * j]), __uint_as_float(x[2 * j + 1]));
-                    const int c8 = half * 8 + 2 * g;
+                    for (int j = 0; j < 8; ++j)
+                        pk[j] = pack_relu_bf16(__uint_as_float(x[2 * j]), __uint_as_float(x[2 * j + 1]));
+                    const int c8 = half * 8 + 2 * gq;
                     st_shared_v4(a_base + sw128_chunk(row, c8), pk[0], pk[1], pk[2], pk[3]);
                     st_shared_v4(a_base + sw128_chunk(row, c8 + 1), pk[4], pk[5], pk[6], pk[7]);
                 };
@@ -322,21 +278,16 @@ __global__ void __maxnreg__(72) k_nif_tc(const TcParams p, int mode)
                 put16(ra, 2);
                 tmem_wait_ld();
                 put16(rb, 3);
-                tc_fence_before();
                 fence_proxy_async();
-                mbar_arrive(bar_a + 8 * s);
             }
-            if (!ok) break;
-            const bool got_head = mbar_wait(bar_acc + 8 * s, ph, abort, p.err);
-            if (!__all_sync(0xFFFFFFFFu, got_head)) break;
-            ph ^= 1;
+        }
+        if (dead) break;
+        tc_fence_before();
+        if (slot_vote_any(bar_id, fail)) { dead = true; break; }
+        if (half == 0) {   // the first half of the slot owns the output
             tc_fence_after();
-            if (half == 1) {  // the other half of the slot owns the output
-                in = next;
-                continue;
-            }
             uint32_t yr[4];
-            tmem_ld4(tmem + lane_base + 384 + 32 * s, yr);
+            tmem_ld4(head + lane_base, yr);
             tmem_wait_ld();
             const float* b4 = tail + 3 * kH;
             const float y0 = __uint_as_float(yr[0]) + b4[0];
@@ -351,18 +302,24 @@ __global__ void __maxnreg__(72) k_nif_tc(const TcParams p, int mode)
                 } else {
                     float* L = p.slot_L + 3 * (size_t)slot;
                     float a = tr * r0, b = tg * r1, c = tb * r2;
-                    if (p.accumulate) { a += L[0]; b += L[1]; c += L[2]; }  // radiance gathered before the escape
+                    if (p.accumulate) { a += L[0]; b += L[1]; c += L[2]; }
                     if (!(isfinite(a) && isfinite(b) && isfinite(c))) atomicOr(p.err, PT_ERR_NONFINITE);
                     L[0] = a; L[1] = b; L[2] = c;
                 }
             }
-            tc_fence_before();
-            in = next;
+        }
+    }
+    if (issuer && *abort) {
+        // make sure no MMA of this slot is still writing TMEM before it is freed
+        mma_commit(bar_drain + 8 * s);
+        const uint64_t t0 = global_ns();
+        while (!mbar_try_wait(bar_drain + 8 * s, 0) && global_ns() - t0 < kWaitBudgetNs) {
         }
     }
     if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0 && p.stats) atomicAdd(p.stats, (unsigned long long)count);
+    tc_fence_before();
     __syncthreads();
-    if (warp == kMmaWarp) {
+    if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
