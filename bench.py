@@ -38,6 +38,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2305_20061_gb300 import inputs as I  # noqa: E402
+from paper_2305_20061_gb300 import replicas as R  # noqa: E402
 
 METRIC = "Msamples/s & NIF evals/s at 1 GB300; BF16-TC vs FP32 at stated image RMSE"
 UNIT = "Msamples/s"
@@ -263,7 +264,7 @@ def bench_ours(args):
     img = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    first_sample = rank * cfg.spp
+    first_sample = R.first_sample(rank, world, cfg.spp)
     rprec = precision or "fp32"
 
     def barrier():
@@ -290,11 +291,7 @@ def bench_ours(args):
         if profile:
             pt.profile_enable(ctx, False)
         ctx.check()
-        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = R.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, dev)
         return ms, prof
 
     sampler = ClockSampler(local)
@@ -548,7 +545,7 @@ def bench_c5(args):
         gc.train_frame(scene, gnif, W, H, f * world + rank, n_train=N_TRAIN, max_depth=cfg.max_depth,
                        rec_vertex=CACHE_VERTEX, seed=0, precision=prec, loss=losses[f:f + 1])
         pt.render_cached(ctx, scene, gnif, cfg, None, cache=gc, cache_vertex=CACHE_VERTEX, precision=prec,
-                         first_sample=(f * world + rank) * spp, out=img)
+                         first_sample=R.first_sample(rank, world, spp, f), out=img)
 
     def barrier():
         if world > 1:
@@ -574,11 +571,7 @@ def bench_c5(args):
     prof = pt.profile_read(ctx)
     clocks = sampler.stop()
     ctx.check()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = R.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / args.steps, dev)
     value = world * cfg.n_slots / (ms * 1e-3) / 1e6
     n_done = args.warmup + args.steps
 
