@@ -612,13 +612,13 @@ def bench_c5(args):
             frame(n_done)
             n_done += 1
         base = 1 << 24
-        R = []
+        ref = []
         for b in range(16):
             rc = I.RenderCfg(W, H, 256, cfg.max_depth, 0)
-            R.append(pt.render(ctx, scene, gnif, rc, "fp32", first_sample=base + 256 * b).double())
-        R = torch.stack(R)
-        R_mean, R_var = R.mean(0), R.var(0) / R.shape[0]
-        del R
+            ref.append(pt.render(ctx, scene, gnif, rc, "fp32", first_sample=base + 256 * b).double())
+        ref = torch.stack(ref)
+        R_mean, R_var = ref.mean(0), ref.var(0) / ref.shape[0]
+        del ref
         X = []
         for b in range(8):
             rc = I.RenderCfg(W, H, 128, cfg.max_depth, 0)
