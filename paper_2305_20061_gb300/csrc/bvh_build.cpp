@@ -1,15 +1,19 @@
 // Host BVH builder: binned SAH, one primitive per leaf, nodes packed for the
-// device with the two children's boxes stored in the parent.
+// device with the two children's boxes stored in the parent.  The upper
+// levels hand their left subtrees to other threads (node lists merged with
+// an index offset), so large meshes build on all host cores.
 //
 // Section 3.1.4 builds a BVH-2 on the host, compacts it into pointer-less
 // nodes with the first child stored next in the array, and stores box
 // extents in fp16 with a rounding that never shrinks the box.  The layout
-// here keeps those three properties (depth-first order, so an interior left
-// child is the next node; fp32 origin + fp16 extent rounded up) but places
-// both child boxes in the parent so one node fetch tests two boxes.
+// here keeps the fp32 origin + fp16 extent rounded up and a depth-first order
+// within each subtree, but stores both child references and both child boxes
+// in the parent, so one node fetch tests two boxes and subtrees can be built
+// apart and placed anywhere.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -43,12 +47,13 @@ constexpr int kBins = 16;
 
 struct Builder {
     const BuildInput& in;
-    std::vector<uint32_t> idx;
+    std::vector<uint32_t>& idx;      // shared by the builders of one tree (each works on its own range)
     std::vector<PackedNode> nodes;
     int32_t max_depth = 0;
+    int par_depth = 0;               // subtrees above this depth may be built on other threads
     std::string error;
 
-    explicit Builder(const BuildInput& i) : in(i) {}
+    Builder(const BuildInput& i, std::vector<uint32_t>& ix) : in(i), idx(ix) {}
 
     Box range_box(int64_t b, int64_t e) const
     {
@@ -57,10 +62,13 @@ struct Builder {
         return bx;
     }
 
-    // choose a split of idx[b, e) (count >= 2); returns the midpoint
-    int64_t split(int64_t b, int64_t e)
+    // choose a split of idx[b, e) (count >= 2): binned SAH over the three axes
+    // (one pass fills the bins of all axes); returns the midpoint and, when
+    // the split came from the bins, the two children's exact boxes
+    int64_t split(int64_t b, int64_t e, Box* bl, Box* br, bool* boxes_known)
     {
         const int64_t n = e - b;
+        *boxes_known = false;
         float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int64_t i = b; i < e; ++i)
             for (int a = 0; a < 3; ++a) {
@@ -68,36 +76,44 @@ struct Builder {
                 clo[a] = std::min(clo[a], c);
                 chi[a] = std::max(chi[a], c);
             }
+        float scale[3];
+        bool live[3];
+        for (int a = 0; a < 3; ++a) {
+            const float ext = chi[a] - clo[a];
+            live[a] = ext > 0.f;
+            scale[a] = live[a] ? kBins / ext : 0.f;
+        }
+        Box bb[3][kBins];
+        int64_t cnt[3][kBins] = {};
+        for (int64_t i = b; i < e; ++i) {
+            const uint32_t p = idx[i];
+            for (int a = 0; a < 3; ++a) {
+                if (!live[a]) continue;
+                int k = (int)((in.cen[3 * p + a] - clo[a]) * scale[a]);
+                k = std::min(std::max(k, 0), kBins - 1);
+                cnt[a][k]++;
+                bb[a][k].grow(&in.lo[3 * p], &in.hi[3 * p]);
+            }
+        }
         double best_cost = INFINITY;
         int best_axis = -1, best_bin = -1;
         for (int a = 0; a < 3; ++a) {
-            const float ext = chi[a] - clo[a];
-            if (!(ext > 0.f)) continue;
-            Box bb[kBins];
-            int64_t cnt[kBins] = {0};
-            const float scale = kBins / ext;
-            for (int64_t i = b; i < e; ++i) {
-                const uint32_t p = idx[i];
-                int k = (int)((in.cen[3 * p + a] - clo[a]) * scale);
-                k = std::min(std::max(k, 0), kBins - 1);
-                cnt[k]++;
-                bb[k].grow(&in.lo[3 * p], &in.hi[3 * p]);
-            }
+            if (!live[a]) continue;
             double left_area[kBins];
             int64_t left_cnt[kBins];
             Box acc;
             int64_t c = 0;
             for (int k = 0; k < kBins - 1; ++k) {
-                acc.grow(bb[k]);
-                c += cnt[k];
+                acc.grow(bb[a][k]);
+                c += cnt[a][k];
                 left_area[k] = acc.area();
                 left_cnt[k] = c;
             }
             Box racc;
             int64_t rc = 0;
             for (int k = kBins - 1; k >= 1; --k) {
-                racc.grow(bb[k]);
-                rc += cnt[k];
+                racc.grow(bb[a][k]);
+                rc += cnt[a][k];
                 const int64_t lc = left_cnt[k - 1];
                 if (lc == 0 || rc == 0) continue;
                 const double cost = left_area[k - 1] * (double)lc + racc.area() * (double)rc;
@@ -107,19 +123,22 @@ struct Builder {
         int64_t mid;
         if (best_axis >= 0) {
             const int a = best_axis;
-            const float ext = chi[a] - clo[a];
-            const float scale = kBins / ext;
             auto it = std::partition(idx.begin() + b, idx.begin() + e, [&](uint32_t p) {
-                int k = (int)((in.cen[3 * p + a] - clo[a]) * scale);
+                int k = (int)((in.cen[3 * p + a] - clo[a]) * scale[a]);
                 k = std::min(std::max(k, 0), kBins - 1);
                 return k < best_bin;
             });
             mid = it - idx.begin();
-        } else {
-            mid = b + n / 2;  // all centroids coincide: split the list in half
+            if (mid > b && mid < e) {
+                Box l, r;
+                for (int k = 0; k < kBins; ++k) (k < best_bin ? l : r).grow(bb[a][k]);
+                *bl = l;
+                *br = r;
+                *boxes_known = true;
+                return mid;
+            }
         }
-        if (mid <= b || mid >= e) mid = b + n / 2;
-        return mid;
+        return b + n / 2;   // no usable split (all centroids coincide): halve the list
     }
 
     // build idx[b, e); returns the child reference
@@ -129,10 +148,36 @@ struct Builder {
         if (e - b == 1) return kLeafBit | idx[b];
         const uint32_t me = (uint32_t)nodes.size();
         nodes.emplace_back();
-        const int64_t mid = split(b, e);
-        const Box bl = range_box(b, mid), br = range_box(mid, e);
-        const uint32_t cl = build(b, mid, depth + 1);
-        const uint32_t cr = build(mid, e, depth + 1);
+        Box bl, br;
+        bool known = false;
+        const int64_t mid = split(b, e, &bl, &br, &known);
+        if (!known) {
+            bl = range_box(b, mid);
+            br = range_box(mid, e);
+        }
+        uint32_t cl, cr;
+        if (depth < par_depth && e - b >= (int64_t)1 << 14) {
+            // the left subtree on another thread into its own node list, appended after the right one
+            Builder sub(in, idx);
+            sub.par_depth = par_depth;
+            sub.nodes.reserve((size_t)(mid - b));
+            uint32_t sub_root = kEmptyRef;
+            std::thread th([&] { sub_root = sub.build(b, mid, depth + 1); });
+            cr = build(mid, e, depth + 1);
+            th.join();
+            const uint32_t off = (uint32_t)nodes.size();
+            for (PackedNode nd : sub.nodes) {
+                for (int c = 9; c <= 10; ++c)
+                    if (!(nd.w[c] & kLeafBit)) nd.w[c] += off;
+                nodes.push_back(nd);
+            }
+            cl = (sub_root & kLeafBit) ? sub_root : sub_root + off;
+            max_depth = std::max(max_depth, sub.max_depth);
+            if (!sub.error.empty()) error = sub.error;
+        } else {
+            cl = build(b, mid, depth + 1);
+            cr = build(mid, e, depth + 1);
+        }
         if (!error.empty()) return kEmptyRef;
         uint16_t el[3], er[3];
         for (int a = 0; a < 3; ++a) {
@@ -194,9 +239,11 @@ bool build_bvh(const BuildInput& in, BuildOutput& out)
         out.root = kEmptyRef;
         return true;
     }
-    Builder bd(in);
-    bd.idx.resize((size_t)in.n_prims);
-    for (int64_t i = 0; i < in.n_prims; ++i) bd.idx[(size_t)i] = (uint32_t)i;
+    std::vector<uint32_t> idx((size_t)in.n_prims);
+    for (int64_t i = 0; i < in.n_prims; ++i) idx[(size_t)i] = (uint32_t)i;
+    Builder bd(in, idx);
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    while ((1u << bd.par_depth) < 2 * hw && bd.par_depth < 8) ++bd.par_depth;   // about two subtrees per core
     bd.nodes.reserve((size_t)std::max<int64_t>(in.n_prims - 1, 1));
     out.root = bd.build(0, in.n_prims, 0);
     if (!bd.error.empty()) {
