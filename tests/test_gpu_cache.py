@@ -344,3 +344,22 @@ def test_cache_argument_errors(pt, ctx):
     with pytest.raises(pt.PTError):
         pt.render_cached(ctx, s, g, cfg, None, cache=None, cache_vertex=2)
     ctx.check()
+
+
+def test_cached_render_chunking_is_invisible(pt, ctx):
+    """Chunks of whole samples change nothing: the cache queue and records are
+    rebuilt per chunk, so a render in one-sample chunks equals the one-chunk
+    render bit for bit, in FP32 and in BF16."""
+    sc, nif = _box_setup(pt, ctx)
+    lo, hi = I.scene_bounds(sc)
+    c = _cache(lo, hi, seed=51, bias_std=0.5)
+    cfg = I.RenderCfg(48, 40, 5, 4, 0)
+    s, g, gc = pt.Scene(ctx, sc), pt.Nif(ctx, I.nif_init(colour="yuv")), pt.Cache(ctx, c)
+    for prec in ("fp32", "bf16"):
+        one = pt.render_cached(ctx, s, g, cfg, None, cache=gc, cache_vertex=2, rec_vertex=2, precision=prec,
+                               want_slots=True)
+        many = pt.render_cached(ctx, s, g, cfg, None, cache=gc, cache_vertex=2, rec_vertex=2, precision=prec,
+                                want_slots=True, chunk_slots=48 * 40)
+        ctx.check()
+        assert torch.equal(one[1], many[1]) and torch.equal(one[2], many[2])
+        assert torch.allclose(one[0], many[0], rtol=1e-6, atol=0)
