@@ -203,23 +203,24 @@ def bench_reference(args):
     return 0
 
 
-def train_env_nif(pt, ctx, gnif, nif, steps, dev):
+def train_env_nif(pt, ctx, gnif, nif, steps, dev, precision):
     """Train the environment NIF on the procedural 2048 x 1024 HDR sky (not
-    timed as a frame); copies the trained weights back into `nif`."""
+    timed as a frame) with the given GEMM precision; copies the trained
+    weights back into `nif`."""
     import torch
     sky = torch.from_numpy(I.procedural_sky()).to(dev)
     batch = 1 << 16
-    gnif.train(sky, steps=5, batch=batch, lr=1e-3, seed=0)
+    gnif.train(sky, steps=5, batch=batch, lr=1e-3, seed=0, precision=precision)
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
-    losses = gnif.train(sky, steps=steps, batch=batch, lr=1e-3, seed=0)
+    losses = gnif.train(sky, steps=steps, batch=batch, lr=1e-3, seed=0, precision=precision)
     t1.record()
     torch.cuda.synchronize()
     ctx.check()
     tms = t0.elapsed_time(t1)
-    train = {"steps": steps + 5, "batch": batch, "ms_per_step": tms / steps,
+    train = {"steps": steps + 5, "batch": batch, "gemm_precision": precision, "ms_per_step": tms / steps,
              "samples_per_s": steps * batch / (tms * 1e-3),
              "fwd_bwd_tflops": steps * batch * 3 * FLOP_PER_EVAL / (tms * 1e-3) / 1e12,
              "loss_first": float(losses[0].item()), "loss_last": float(losses[-50:].mean().item())}
@@ -260,7 +261,8 @@ def bench_ours(args):
     gnif = pt.Nif(ctx, nif) if uses_nif else None
 
     # the environment NIF is trained on the procedural 2048 x 1024 HDR sky first (not timed as a frame)
-    train = train_env_nif(pt, ctx, gnif, nif, args.train_steps, dev) if uses_nif and args.train_steps > 0 else None
+    train = (train_env_nif(pt, ctx, gnif, nif, args.train_steps, dev, args.train_precision)
+             if uses_nif and args.train_steps > 0 else None)
     img = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -529,7 +531,7 @@ def bench_c5(args):
     scene = pt.Scene(ctx, sc)
     t_build = time.perf_counter() - t_build
     gnif = pt.Nif(ctx, nif)
-    train = train_env_nif(pt, ctx, gnif, nif, args.train_steps, dev) if args.train_steps > 0 else None
+    train = train_env_nif(pt, ctx, gnif, nif, args.train_steps, dev, args.train_precision) if args.train_steps > 0 else None
     lo, hi = I.scene_bounds(sc)
     cache0 = I.cache_init(lo, hi)
     gc = pt.Cache(ctx, cache0)
@@ -543,7 +545,8 @@ def bench_c5(args):
     def frame(f):
         # each rank runs its own online loop on its own samples (replicas, no collective)
         gc.train_frame(scene, gnif, W, H, f * world + rank, n_train=N_TRAIN, max_depth=cfg.max_depth,
-                       rec_vertex=CACHE_VERTEX, seed=0, precision=prec, loss=losses[f:f + 1])
+                       rec_vertex=CACHE_VERTEX, seed=0, precision=prec, loss=losses[f:f + 1],
+                       train_precision=args.train_precision)
         pt.render_cached(ctx, scene, gnif, cfg, None, cache=gc, cache_vertex=CACHE_VERTEX, precision=prec,
                          first_sample=R.first_sample(rank, world, spp, f), out=img)
 
@@ -577,7 +580,8 @@ def bench_c5(args):
 
     # split of one more frame: the training step, then the cached render alone
     gc.train_frame(scene, gnif, W, H, n_done * world + rank, n_train=N_TRAIN, max_depth=cfg.max_depth,
-                   rec_vertex=CACHE_VERTEX, seed=0, precision=prec, loss=losses[n_done:n_done + 1])
+                   rec_vertex=CACHE_VERTEX, seed=0, precision=prec, loss=losses[n_done:n_done + 1],
+                   train_precision=args.train_precision)
     prof_train = pt.profile_read(ctx)
     pt.render_cached(ctx, scene, gnif, cfg, None, cache=gc, cache_vertex=CACHE_VERTEX, precision=prec,
                      first_sample=(n_done * world + rank) * spp, out=img)
@@ -681,7 +685,7 @@ def bench_c5(args):
         for i in range(n_e2e):
             s2, n2, c2 = pt.Scene(ctx, sc), pt.Nif(ctx, nif), pt.Cache(ctx, cache_host)
             c2.train_frame(s2, n2, W, H, n_done + i, n_train=N_TRAIN, max_depth=cfg.max_depth,
-                           rec_vertex=CACHE_VERTEX, seed=0, precision=prec)
+                           rec_vertex=CACHE_VERTEX, seed=0, precision=prec, train_precision=args.train_precision)
             pt.render_cached(ctx, s2, n2, cfg, None, cache=c2, cache_vertex=CACHE_VERTEX, precision=prec,
                              first_sample=(n_done + i) * spp, out=img)
             host_img.copy_(img, non_blocking=True)
@@ -711,7 +715,8 @@ def bench_c5(args):
                                    f"at vertex {CACHE_VERTEX})",
                        "paths_per_frame": cfg.n_slots, "nif_precision": prec,
                        "cache": "12 freqs/axis position encoding + direction + normal (78) -> 5x FC-64 ReLU -> FC-3, "
-                                "FP32, Adam lr 1e-2, relative L2",
+                                "FP32 master weights, Adam lr 1e-2, relative L2",
+                       "cache_train_gemms": args.train_precision,
                        "l2": "512 MB L2 flush between timed frames (outside the timed events)"},
             "kernel_ms_per_step": kinds,
             "frame_split_ms": {"train": {k: v[0] for k, v in prof_train.items()},
@@ -743,6 +748,8 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=4.0, help="seconds per reference-arm step")
     ap.add_argument("--train-steps", type=int, default=2000,
                     help="Adam steps of the environment NIF on the procedural sky before the frames (0: random init)")
+    ap.add_argument("--train-precision", choices=["bf16", "fp32"], default="bf16",
+                    help="GEMMs of NIF and radiance-cache training (tensor cores or CUDA cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the other-precision frames and standalone NIF runs (profiler captures)")

@@ -196,6 +196,8 @@ typedef struct pt_train_cfg {
     float lr, beta1, beta2, eps;  /* Adam (Kingma & Ba) with bias correction */
     float huber_delta;         /* Huber loss threshold (the paper uses 1e-3) */
     uint32_t seed;             /* Philox key (seed, 1); counter (sample, global step, 0, 0) */
+    int32_t precision;         /* GEMMs: PT_FP32 (CUDA cores) or PT_BF16 (tcgen05: BF16 operands, FP32
+                                  accumulation; activations, gradients and master weights stay FP32) */
 } pt_train_cfg;
 
 /* Train for cfg->steps steps on d_sky, an equirect HDR image [h][w][3] float
@@ -203,17 +205,18 @@ typedef struct pt_train_cfg {
    clamps).  d_losses (nullable) receives the mean Huber loss of each step.
    Adam moments and the global step count persist in the pt_nif across calls,
    so calls continue one run.  The FP32 and tensor-core layouts are rebuilt
-   at the end of the call.  FP32 arithmetic, loss sums in FP64,
-   deterministic. */
+   at the end of the call.  FP32 arithmetic (or BF16 GEMM operands with
+   cfg->precision = PT_BF16), loss sums in FP64, deterministic in both. */
 PT_API pt_status pt_train_nif(pt_ctx* ctx, pt_nif* nif, const float* d_sky, int32_t w, int32_t h,
                               const pt_train_cfg* cfg, float* d_losses, void* stream);
 
 /* Loss and gradient of one batch without updating: d_uv [n][2], d_target
    [n][3] (log space, compared with the colour-matrix output) -> d_grad
    (nullable; trainable part of the flat layout: per layer W then b) and
-   *d_loss (nullable device double, mean Huber loss over n x 3). */
+   *d_loss (nullable device double, mean Huber loss over n x 3).  precision
+   as in pt_train_cfg. */
 PT_API pt_status pt_nif_loss_grad(pt_ctx* ctx, pt_nif* nif, int64_t n, const float* d_uv, const float* d_target,
-                                  float delta, float* d_grad, double* d_loss, void* stream);
+                                  float delta, int32_t precision, float* d_grad, double* d_loss, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Rendering (Section 3.1: paths without light sampling; radiance gathered   */
@@ -336,9 +339,11 @@ PT_API pt_status pt_cache_eval(pt_ctx* ctx, const pt_cache* cache, int32_t preci
    prediction constant in the gradient, averaged over all n x 3 entries;
    rows with d_mask[i] == 0 (d_mask nullable) contribute zero.  d_q [n][9],
    d_target [n][3] -> d_grad (nullable, flat layout) and *d_loss (nullable
-   device double).  Nothing is updated. */
+   device double).  Nothing is updated.  precision: the GEMMs, PT_FP32 (CUDA
+   cores) or PT_BF16 (tcgen05, BF16 operands, FP32 accumulation). */
 PT_API pt_status pt_cache_loss_grad(pt_ctx* ctx, pt_cache* cache, int64_t n, const float* d_q, const float* d_target,
-                                    const int32_t* d_mask, float* d_grad, double* d_loss, void* stream);
+                                    const int32_t* d_mask, int32_t precision, float* d_grad, double* d_loss,
+                                    void* stream);
 
 typedef struct pt_cache_train_cfg {
     int32_t width, height;     /* image whose pixels the training paths start from */
@@ -349,6 +354,7 @@ typedef struct pt_cache_train_cfg {
     uint32_t frame;            /* frame index */
     int32_t precision;         /* NIF precision at the training paths' escapes */
     float lr, beta1, beta2, eps;  /* Adam */
+    int32_t train_precision;   /* the network's training GEMMs: PT_FP32 or PT_BF16 (tcgen05) */
 } pt_cache_train_cfg;
 
 /* One online training step of a frame.  Pixel i of the n_train training

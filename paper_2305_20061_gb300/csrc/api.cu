@@ -676,6 +676,20 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
 // NIF training (Section 3.2.1)
 namespace {
 
+// training GEMM precision: PT_FP32, or PT_BF16 where the tensor-core kernels take the shape
+pt_status check_train_precision(pt_ctx* ctx, int L, int H, int in0, int32_t precision)
+{
+    if (precision == PT_FP32) return PT_OK;
+    if (precision != PT_BF16) return fail(ctx, PT_EINVAL, "training precision is PT_FP32 or PT_BF16");
+    TrainNet t = {};
+    t.L = L;
+    t.H = H;
+    t.in0 = in0;
+    if (!train_tc_supported(t))
+        return fail(ctx, PT_EUNSUPPORTED, "BF16 training needs at most 8 hidden layers of width <= 128, inputs <= 128");
+    return PT_OK;
+}
+
 TrainNet make_train_net(pt_nif* nf)
 {
     TrainNet t = {};
@@ -716,7 +730,8 @@ pt_status ensure_train(pt_ctx* ctx, pt_nif* nf, int64_t B)
     nf->d_batch = nullptr;
     const int G = 4 * ctx->sm_count;   // partial slots: up to four GEMM CTAs per SM
     const size_t rows = (size_t)B * 128;
-    const size_t bytes = (size_t)(nf->L + 1 + 2) * rows * sizeof(float) + (size_t)G * (128 * 128 + 128) * sizeof(float) +
+    // X[0 .. L], dX[2], G[0 .. L-2] (G[L-1] is dX[0]), partials, loss partials
+    const size_t bytes = (size_t)(2 * nf->L + 2) * rows * sizeof(float) + (size_t)G * (128 * 128 + 128) * sizeof(float) +
                          (size_t)G * sizeof(double) + 4096;
     if (cudaMalloc(&nf->d_work, bytes) != cudaSuccess || cudaMalloc((void**)&nf->d_batch, (size_t)B * 5 * sizeof(float)) != cudaSuccess) {
         nf->work_cap = 0;
@@ -728,6 +743,9 @@ pt_status ensure_train(pt_ctx* ctx, pt_nif* nf, int64_t B)
     nf->work.sm_count = ctx->sm_count;
     for (int l = 0; l <= nf->L; ++l) { nf->work.X[l] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
     for (int i = 0; i < 2; ++i) { nf->work.dX[i] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
+    for (int l = 0; l + 1 < nf->L; ++l) { nf->work.G[l] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
+    nf->work.G[nf->L - 1] = nf->work.dX[0];
+    nf->work.err = ctx->d_err;
     nf->work.partial = reinterpret_cast<float*>(w);
     w += (size_t)G * (128 * 128 + 128) * sizeof(float);
     nf->work.loss_partial = reinterpret_cast<double*>(w);
@@ -747,15 +765,18 @@ pt_status refresh_layouts(pt_ctx* ctx, pt_nif* nf, cudaStream_t s)
 }  // namespace
 
 PT_API pt_status pt_nif_loss_grad(pt_ctx* ctx, pt_nif* nf, int64_t n, const float* d_uv, const float* d_target,
-                                  float delta, float* d_grad, double* d_loss, void* stream)
+                                  float delta, int32_t precision, float* d_grad, double* d_loss, void* stream)
 {
     if (!ctx || !nf || n < 1 || !d_uv || !d_target || !(delta > 0.f)) return fail(ctx, PT_EINVAL, "bad argument");
-    pt_status st = ensure_train(ctx, nf, n);
+    pt_status st = check_train_precision(ctx, nf->L, nf->H, 2 * nf->F, precision);
+    if (st != PT_OK) return st;
+    st = ensure_train(ctx, nf, n);
     if (st != PT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     TrainNet net = make_train_net(nf);
     PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] {
-        return nif_loss_grad(net, n, d_uv, d_target, delta, nf->work, d_loss ? d_loss : nf->d_loss, nullptr, s);
+        return nif_loss_grad(net, n, d_uv, d_target, delta, precision, nf->work, d_loss ? d_loss : nf->d_loss, nullptr,
+                             s);
     }));
     if (d_grad)
         PT_CUDA(cudaMemcpyAsync(d_grad, nf->d_grad, nf->n_trainable * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -769,7 +790,9 @@ PT_API pt_status pt_train_nif(pt_ctx* ctx, pt_nif* nf, const float* d_sky, int32
     if (cfg->steps < 0 || cfg->batch < 1 || !(cfg->lr > 0.f) || !(cfg->huber_delta > 0.f) || !(cfg->beta1 >= 0.f) ||
         !(cfg->beta1 < 1.f) || !(cfg->beta2 >= 0.f) || !(cfg->beta2 < 1.f) || !(cfg->eps > 0.f))
         return fail(ctx, PT_EINVAL, "bad training configuration");
-    pt_status st = ensure_train(ctx, nf, cfg->batch);
+    pt_status st = check_train_precision(ctx, nf->L, nf->H, 2 * nf->F, cfg->precision);
+    if (st != PT_OK) return st;
+    st = ensure_train(ctx, nf, cfg->batch);
     if (st != PT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     TrainNet net = make_train_net(nf);
@@ -781,7 +804,7 @@ PT_API pt_status pt_train_nif(pt_ctx* ctx, pt_nif* nf, const float* d_sky, int32
             return train_inputs(cfg->seed, (uint32_t)t, cfg->batch, d_sky, w, h, uv, target, s);
         }));
         PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] {
-            return nif_loss_grad(net, cfg->batch, uv, target, cfg->huber_delta, nf->work, nullptr,
+            return nif_loss_grad(net, cfg->batch, uv, target, cfg->huber_delta, cfg->precision, nf->work, nullptr,
                                  d_losses ? d_losses + i : nullptr, s);
         }));
         const double c1 = 1.0 - std::pow((double)cfg->beta1, (double)(t + 1));
@@ -860,7 +883,8 @@ pt_status ensure_cache_train(pt_ctx* ctx, pt_cache* c, int64_t B)
     c->work_cap = 0;
     const int G = 4 * ctx->sm_count;   // partial slots: up to four GEMM CTAs per SM
     const size_t rows = (size_t)B * 128;
-    const size_t bytes = (size_t)(c->L + 1 + 2) * rows * sizeof(float) + (size_t)G * (128 * 128 + 128) * sizeof(float) +
+    // X[0 .. L], dX[2], G[0 .. L-2] (G[L-1] is dX[0]), partials, loss partials
+    const size_t bytes = (size_t)(2 * c->L + 2) * rows * sizeof(float) + (size_t)G * (128 * 128 + 128) * sizeof(float) +
                          (size_t)G * sizeof(double) + 4096;
     if (cudaMalloc(&c->d_work, bytes) != cudaSuccess) return fail(ctx, PT_ENOMEM, "cache work buffers allocation failed");
     char* w = static_cast<char*>(c->d_work);
@@ -869,6 +893,9 @@ pt_status ensure_cache_train(pt_ctx* ctx, pt_cache* c, int64_t B)
     c->work.sm_count = ctx->sm_count;
     for (int l = 0; l <= c->L; ++l) { c->work.X[l] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
     for (int i = 0; i < 2; ++i) { c->work.dX[i] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
+    for (int l = 0; l + 1 < c->L; ++l) { c->work.G[l] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
+    c->work.G[c->L - 1] = c->work.dX[0];
+    c->work.err = ctx->d_err;
     c->work.partial = reinterpret_cast<float*>(w);
     w += (size_t)G * (128 * 128 + 128) * sizeof(float);
     c->work.loss_partial = reinterpret_cast<double*>(w);
@@ -1006,10 +1033,13 @@ PT_API pt_status pt_cache_eval(pt_ctx* ctx, const pt_cache* c, int32_t precision
 }
 
 PT_API pt_status pt_cache_loss_grad(pt_ctx* ctx, pt_cache* c, int64_t n, const float* d_q, const float* d_target,
-                                    const int32_t* d_mask, float* d_grad, double* d_loss, void* stream)
+                                    const int32_t* d_mask, int32_t precision, float* d_grad, double* d_loss,
+                                    void* stream)
 {
     if (!ctx || !c || n < 1 || !d_q || !d_target) return fail(ctx, PT_EINVAL, "bad argument");
-    pt_status st = ensure_cache_train(ctx, c, n);
+    pt_status st = check_train_precision(ctx, c->L, c->H, c->in0, precision);
+    if (st != PT_OK) return st;
+    st = ensure_cache_train(ctx, c, n);
     if (st != PT_OK) return st;
     st = ensure_cache_paths(ctx, c, n);
     if (st != PT_OK) return st;
@@ -1021,7 +1051,8 @@ PT_API pt_status pt_cache_loss_grad(pt_ctx* ctx, pt_cache* c, int64_t n, const f
     PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] {
         cudaError_t e = cache_train_inputs(n, c->d_rec, nullptr, c->box, c->work.X[0], nullptr, nullptr, s);
         if (e != cudaSuccess) return e;
-        return mlp_loss_grad(net, n, d_target, 0.f, 1, d_mask, c->work, d_loss ? d_loss : c->d_loss, nullptr, s);
+        return mlp_loss_grad(net, n, d_target, 0.f, 1, d_mask, precision, c->work, d_loss ? d_loss : c->d_loss,
+                             nullptr, s);
     }));
     if (d_grad) PT_CUDA(cudaMemcpyAsync(d_grad, c->d_grad, c->n_params * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return PT_OK;
@@ -1043,6 +1074,8 @@ PT_API pt_status pt_train_cache(pt_ctx* ctx, const pt_scene* sc, const pt_nif* n
     rc.precision = cfg->precision;
     pt_status st = check_cfg(ctx, sc, nf, &rc);
     if (st != PT_OK) return st;
+    st = check_train_precision(ctx, c->L, c->H, c->in0, cfg->train_precision);
+    if (st != PT_OK) return st;
     const int64_t n = cfg->n_train;
     st = ensure_cache_train(ctx, c, n);
     if (st != PT_OK) return st;
@@ -1059,7 +1092,8 @@ PT_API pt_status pt_train_cache(pt_ctx* ctx, const pt_scene* sc, const pt_nif* n
     PT_CUDA(timed(ctx, PT_KIND_OTHER, s, [&] {
         cudaError_t e = cache_train_inputs(n, c->d_rec, c->d_Lpath, c->box, c->work.X[0], c->d_target, c->d_mask, s);
         if (e != cudaSuccess) return e;
-        return mlp_loss_grad(net, n, c->d_target, 0.f, 1, c->d_mask, c->work, c->d_loss, d_loss, s);
+        return mlp_loss_grad(net, n, c->d_target, 0.f, 1, c->d_mask, cfg->train_precision, c->work, c->d_loss, d_loss,
+                             s);
     }));
     const int64_t t = c->adam_t;
     const double c1 = 1.0 - std::pow((double)cfg->beta1, (double)(t + 1));

@@ -520,10 +520,55 @@ int layer_bwd_dw(const TrainWork& wk, int64_t B, const float* dXout, const float
 
 }  // namespace
 
+namespace {
+
+// output layer, loss and the head's gradients (both precisions); writes the
+// gradient at the last hidden layer's pre-activation to dX_last
+cudaError_t head_loss(const TrainNet& net, int64_t B, const float* target, float delta, int mode, const int32_t* mask,
+                      TrainWork& wk, float* dX_last, double* loss_d, float* loss_f, cudaStream_t s)
+{
+    cudaError_t e = set_smem((const void*)k_head_loss);
+    if (e != cudaSuccess) return e;
+    const size_t hsm = (size_t)pad_k(net.H) * kT * sizeof(float);
+    const int Gh = grid_of(wk, B, (const void*)k_head_loss, hsm);
+    k_head_loss<<<Gh, kT, hsm, s>>>(B, wk.X[net.L], target, net.W[net.L], net.b[net.L], net.H, net.M, delta,
+                                    1.f / (3.f * (float)B), dX_last, wk.partial, wk.loss_partial, mode, mask);
+    k_sum_partials<<<(3 * net.H + 3 + 31) / 32, 256, 0, s>>>(wk.partial, Gh, 3 * kD + 3, kD, 3 * kD, net.H, 3,
+                                                             net.gW[net.L], net.gb[net.L]);
+    k_sum_loss<<<1, 32, 0, s>>>(wk.loss_partial, Gh, 1.0 / (3.0 * (double)B), loss_d, loss_f);
+    return cudaGetLastError();
+}
+
+// BF16 operands on the tensor cores: forward and input-gradient chains and
+// the weight-gradient partials in train_tc.cu, partial sums here
+cudaError_t mlp_loss_grad_tc(const TrainNet& net, int64_t B, const float* target, float delta, int mode,
+                             const int32_t* mask, TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s)
+{
+    cudaError_t e = train_tc_forward(net, B, wk, wk.err, s);
+    if (e != cudaSuccess) return e;
+    e = head_loss(net, B, target, delta, mode, mask, wk, wk.G[net.L - 1], loss_d, loss_f, s);
+    if (e != cudaSuccess) return e;
+    int Gl = 0, stride = 0;
+    e = train_tc_backward(net, B, wk, wk.err, &Gl, &stride, s);
+    if (e != cudaSuccess) return e;
+    for (int l = 0; l < net.L; ++l) {
+        const int in = l == 0 ? net.in0 : net.H;
+        const int Kin = (in + 15) & ~15;
+        k_sum_partials<<<(in * net.H + net.H + 31) / 32, 256, 0, s>>>(wk.partial + (size_t)l * Gl * stride, Gl, stride,
+                                                                       Kin, net.H * Kin, in, net.H, net.gW[l],
+                                                                       net.gb[l]);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, float delta, int mode,
-                          const int32_t* mask, TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s)
+                          const int32_t* mask, int precision, TrainWork& wk, double* loss_d, float* loss_f,
+                          cudaStream_t s)
 {
     if (B <= 0) return cudaSuccess;
+    if (precision == PT_BF16) return mlp_loss_grad_tc(net, B, target, delta, mode, mask, wk, loss_d, loss_f, s);
     cudaError_t e;
     for (auto fn : {(const void*)k_layer_fwd<64>, (const void*)k_layer_fwd<128>, (const void*)k_layer_bwd_dx<64>,
                     (const void*)k_layer_bwd_dx<128>, (const void*)k_layer_bwd_dw<64, 64>,
@@ -538,15 +583,8 @@ cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, f
         layer_fwd(wk, B, wk.X[l], wk.X[l + 1], net.W[l], net.b[l], in, net.H, s);
     }
     // head + loss
-    e = set_smem((const void*)k_head_loss);
+    e = head_loss(net, B, target, delta, mode, mask, wk, wk.dX[0], loss_d, loss_f, s);
     if (e != cudaSuccess) return e;
-    const size_t hsm = (size_t)pad_k(net.H) * kT * sizeof(float);
-    const int Gh = grid_of(wk, B, (const void*)k_head_loss, hsm);
-    k_head_loss<<<Gh, kT, hsm, s>>>(B, wk.X[net.L], target, net.W[net.L], net.b[net.L], net.H, net.M, delta,
-                                    1.f / (3.f * (float)B), wk.dX[0], wk.partial, wk.loss_partial, mode, mask);
-    k_sum_partials<<<(3 * net.H + 3 + 31) / 32, 256, 0, s>>>(wk.partial, Gh, 3 * kD + 3, kD, 3 * kD, net.H, 3,
-                                                             net.gW[net.L], net.gb[net.L]);
-    k_sum_loss<<<1, 32, 0, s>>>(wk.loss_partial, Gh, 1.0 / (3.0 * (double)B), loss_d, loss_f);
     // backward through the hidden layers
     int cur = 0;
     for (int l = net.L - 1; l >= 0; --l) {
@@ -564,12 +602,12 @@ cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, f
 }
 
 cudaError_t nif_loss_grad(const TrainNet& net, int64_t B, const float* uv, const float* target, float delta,
-                          TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s)
+                          int precision, TrainWork& wk, double* loss_d, float* loss_f, cudaStream_t s)
 {
     if (B <= 0) return cudaSuccess;
     k_train_features<<<(unsigned)std::min<int64_t>((B * 64 + 255) / 256, 152 * 32), 256, 0, s>>>(B, uv, net.B, net.F,
                                                                                                  wk.X[0]);
-    return mlp_loss_grad(net, B, target, delta, 0, nullptr, wk, loss_d, loss_f, s);
+    return mlp_loss_grad(net, B, target, delta, 0, nullptr, precision, wk, loss_d, loss_f, s);
 }
 
 // ---------------------------------------------------------------------------

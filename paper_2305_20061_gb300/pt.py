@@ -56,7 +56,7 @@ class RenderCfg(C.Structure):
 
 class TrainCfg(C.Structure):
     _fields_ = [("steps", I64), ("batch", I64), ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("eps", C.c_float), ("huber_delta", C.c_float), ("seed", U32)]
+                ("eps", C.c_float), ("huber_delta", C.c_float), ("seed", U32), ("precision", I32)]
 
 
 class CacheDesc(C.Structure):
@@ -67,7 +67,7 @@ class CacheDesc(C.Structure):
 class CacheTrainCfg(C.Structure):
     _fields_ = [("width", I32), ("height", I32), ("n_train", I32), ("max_depth", I32), ("rec_vertex", I32),
                 ("seed", U32), ("frame", U32), ("precision", I32), ("lr", C.c_float), ("beta1", C.c_float),
-                ("beta2", C.c_float), ("eps", C.c_float)]
+                ("beta2", C.c_float), ("eps", C.c_float), ("train_precision", I32)]
 
 
 class PTError(RuntimeError):
@@ -113,14 +113,14 @@ def lib():
             "pt_nif_set_params": ([P, P, P, P], I32),
             "pt_nif_fp8_scales": ([P, P], I32),
             "pt_train_nif": ([P, P, P, I32, I32, P, P, P], I32),
-            "pt_nif_loss_grad": ([P, P, I64, P, P, C.c_float, P, P, P], I32),
+            "pt_nif_loss_grad": ([P, P, I64, P, P, C.c_float, I32, P, P, P], I32),
             "pt_create_cache": ([P, P, P], I32),
             "pt_destroy_cache": ([P], None),
             "pt_cache_param_count": ([P], I64),
             "pt_cache_get_params": ([P, P, P], I32),
             "pt_cache_set_params": ([P, P, P, P], I32),
             "pt_cache_eval": ([P, P, I32, I64, P, P, P], I32),
-            "pt_cache_loss_grad": ([P, P, I64, P, P, P, P, P, P], I32),
+            "pt_cache_loss_grad": ([P, P, I64, P, P, P, I32, P, P, P], I32),
             "pt_train_cache": ([P, P, P, P, P, P, P], I32),
             "pt_render_cached": ([P, P, P, P, I32, I32, P, I64, P, P, P, P, P, P], I32),
         }
@@ -268,23 +268,26 @@ class Nif:
         self.ctx._raise(lib().pt_nif_set_params(self.ctx.h, self.h, _np_ptr(flat), _stream(stream)))
 
     def train(self, sky: torch.Tensor, steps: int, batch: int = 1 << 16, lr: float = 1e-3, beta1: float = 0.9,
-              beta2: float = 0.999, eps: float = 1e-7, delta: float = 1e-3, seed: int = 0, stream=None) -> torch.Tensor:
-        """pt_train_nif on an HDR image [h, w, 3] (device tensor); returns per-step losses."""
+              beta2: float = 0.999, eps: float = 1e-7, delta: float = 1e-3, seed: int = 0, precision: str = "fp32",
+              stream=None) -> torch.Tensor:
+        """pt_train_nif on an HDR image [h, w, 3] (device tensor); returns per-step losses.  precision: the
+        training GEMMs, "fp32" (CUDA cores) or "bf16" (tensor cores, BF16 operands, FP32 accumulation)."""
         sky = sky.contiguous()
         losses = torch.zeros(max(steps, 1), dtype=torch.float32, device=sky.device)
-        cfg = TrainCfg(steps, batch, lr, beta1, beta2, eps, delta, seed)
+        cfg = TrainCfg(steps, batch, lr, beta1, beta2, eps, delta, seed, PRECISIONS[precision])
         self.ctx._raise(lib().pt_train_nif(self.ctx.h, self.h, _dptr(sky), sky.shape[1], sky.shape[0], C.byref(cfg),
                                            _dptr(losses), _stream(stream)))
         return losses[:steps]
 
-    def loss_grad(self, uv: torch.Tensor, target: torch.Tensor, delta: float = 1e-3, stream=None):
+    def loss_grad(self, uv: torch.Tensor, target: torch.Tensor, delta: float = 1e-3, precision: str = "fp32",
+                  stream=None):
         """pt_nif_loss_grad: (loss as a device double tensor, gradient in the trainable flat layout)."""
         uv, target = uv.contiguous(), target.contiguous()
         n_tr = self.param_count - 2 * self.src.n_freq - 9
         grad = torch.empty(n_tr, dtype=torch.float32, device=uv.device)
         loss = torch.zeros(1, dtype=torch.float64, device=uv.device)
         self.ctx._raise(lib().pt_nif_loss_grad(self.ctx.h, self.h, uv.shape[0], _dptr(uv), _dptr(target), delta,
-                                               _dptr(grad), _dptr(loss), _stream(stream)))
+                                               PRECISIONS[precision], _dptr(grad), _dptr(loss), _stream(stream)))
         return loss, grad
 
     def eval(self, uv: torch.Tensor, precision: str = "fp32", stream=None) -> torch.Tensor:
@@ -344,23 +347,26 @@ class Cache:
                                             _dptr(out), _stream(stream)))
         return out
 
-    def loss_grad(self, q: torch.Tensor, target: torch.Tensor, mask: Optional[torch.Tensor] = None, stream=None):
-        """pt_cache_loss_grad: (loss as a device double tensor, flat gradient)."""
+    def loss_grad(self, q: torch.Tensor, target: torch.Tensor, mask: Optional[torch.Tensor] = None,
+                  precision: str = "fp32", stream=None):
+        """pt_cache_loss_grad: (loss as a device double tensor, flat gradient); precision of the GEMMs."""
         q, target = q.contiguous(), target.contiguous()
         grad = torch.empty(self.param_count, dtype=torch.float32, device=q.device)
         loss = torch.zeros(1, dtype=torch.float64, device=q.device)
         self.ctx._raise(lib().pt_cache_loss_grad(self.ctx.h, self.h, q.shape[0], _dptr(q), _dptr(target),
-                                                 _dptr(None if mask is None else mask.contiguous()), _dptr(grad),
-                                                 _dptr(loss), _stream(stream)))
+                                                 _dptr(None if mask is None else mask.contiguous()),
+                                                 PRECISIONS[precision], _dptr(grad), _dptr(loss), _stream(stream)))
         return loss, grad
 
     def train_frame(self, scene: "Scene", nif: Optional["Nif"], width: int, height: int, frame: int,
                     n_train: int = 1 << 16, max_depth: int = 6, rec_vertex: int = 2, seed: int = 0,
                     precision: str = "fp32", lr: float = 1e-2, beta1: float = 0.9, beta2: float = 0.999,
-                    eps: float = 1e-7, loss: Optional[torch.Tensor] = None, stream=None) -> Optional[torch.Tensor]:
-        """pt_train_cache: one online training step; loss (optional [1] float32 device tensor) receives the loss."""
+                    eps: float = 1e-7, loss: Optional[torch.Tensor] = None, train_precision: str = "fp32",
+                    stream=None) -> Optional[torch.Tensor]:
+        """pt_train_cache: one online training step; loss (optional [1] float32 device tensor) receives the loss.
+        precision: the NIF at the training paths' escapes; train_precision: the network's training GEMMs."""
         cfg = CacheTrainCfg(width, height, n_train, max_depth, rec_vertex, seed, frame, PRECISIONS[precision], lr,
-                            beta1, beta2, eps)
+                            beta1, beta2, eps, PRECISIONS[train_precision])
         self.ctx._raise(lib().pt_train_cache(self.ctx.h, scene.h, nif.h if nif is not None else None, self.h,
                                              C.byref(cfg), _dptr(loss), _stream(stream)))
         return loss

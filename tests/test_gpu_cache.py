@@ -155,6 +155,65 @@ def test_cache_loss_grad_matches_oracle(pt, ctx):
     assert np.array_equal(gc.get_params(), pt.cache_flat(c))
 
 
+@pytest.mark.parametrize("J,L,H,n", [(12, 5, 64, 3000), (4, 3, 64, 129), (12, 5, 64, (1 << 16) + 3)])
+def test_bf16_cache_loss_grad_matches_rounding_model(pt, ctx, J, L, H, n):
+    """Tensor-core training GEMMs of the cache: relative-L2 loss and gradient
+    against the BF16 rounding model (pinned to the oracle on the CPU) to
+    2e-3 per layer, and against the FP64 oracle to 5e-2; 20% of the rows
+    masked; two calls are bit-identical."""
+    import bf16_model as BM
+    lo, hi = np.array([-1.0, -1.0, -1.0], np.float32), np.array([1.0, 1.0, 1.0], np.float32)
+    c = I.cache_init(lo, hi, n_freq=J, hidden=H, n_hidden_layers=L, seed=21)
+    rng = np.random.default_rng(22)
+    for b in c.b:
+        b[:] = rng.normal(0, 0.1, b.shape).astype(np.float32)
+    q = _queries(n, lo, hi, seed=23)
+    t = rng.uniform(0.0, 2.0, (n, 3)).astype(np.float32)
+    mask = (rng.uniform(size=n) > 0.2).astype(np.int32)
+    gc = pt.Cache(ctx, c)
+    args = (torch.from_numpy(q).cuda(), torch.from_numpy(t).cuda(), torch.from_numpy(mask).cuda())
+    loss, g = gc.loss_grad(*args, precision="bf16")
+    loss2, g2 = gc.loss_grad(*args, precision="bf16")
+    ctx.check()
+    assert torch.equal(loss, loss2) and torch.equal(g, g2)
+    g = g.cpu().numpy().astype(np.float64)
+    ml, mg = BM.mlp_loss_grad(BM.cache_features(c, q), c.W, c.b, t, "rel_l2", mask=mask)
+    assert abs(loss.item() - ml) <= 1e-4 * abs(ml)
+    wl, wg = O.Cache(c).loss_grad(q.astype(np.float64), t.astype(np.float64), mask=mask)
+    assert abs(loss.item() - wl) <= 1e-2 * abs(wl)
+    p = 0
+    for W, b in zip(c.W, c.b):
+        for size in (W.size, b.size):
+            a, m, w = g[p:p + size], mg[p:p + size], wg[p:p + size]
+            assert np.linalg.norm(a - m) <= 2e-3 * np.linalg.norm(m), (p, np.linalg.norm(a - m) / np.linalg.norm(m))
+            assert np.linalg.norm(a - w) <= 5e-2 * np.linalg.norm(w)
+            p += size
+
+
+def test_bf16_cache_training_frames(pt, ctx):
+    """Online frames with tensor-core training GEMMs: bit-reproducible, and
+    the per-frame losses stay within 5% of the FP32-trained run's."""
+    sc, nif = _box_setup(pt, ctx)
+    lo, hi = I.scene_bounds(sc)
+    c = _cache(lo, hi, seed=41)
+    s, g = pt.Scene(ctx, sc), pt.Nif(ctx, nif)
+    runs = {}
+    for tp in ("fp32", "bf16", "bf16"):
+        gc = pt.Cache(ctx, c)
+        losses = []
+        for frame in range(8):
+            loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+            gc.train_frame(s, g, 64, 64, frame, n_train=8192, loss=loss, train_precision=tp)
+            losses.append(loss.item())
+        ctx.check()
+        runs.setdefault(tp, []).append((np.array(losses), gc.get_params()))
+    (l32, _), = runs["fp32"]
+    (la, pa), (lb, pb) = runs["bf16"]
+    assert np.array_equal(la, lb) and np.array_equal(pa, pb)
+    assert np.all(np.isfinite(la))
+    assert np.all(np.abs(la - l32) <= 5e-2 * np.abs(l32)), np.abs(la - l32) / np.abs(l32)
+
+
 def _box_setup(pt, ctx):
     return I.make_scene("C1"), I.nif_init(seed=0)
 

@@ -144,3 +144,104 @@ def test_training_on_procedural_sky_improves_reconstruction(pt, ctx):
     print({"log_rmse_before": before, "log_rmse_after": after, "loss_first": float(losses[0]),
            "loss_last": float(losses[-20:].mean())})
     assert after < 0.5 * before
+
+
+# ----------------------------------------------------------------------------
+# BF16 tensor-core training GEMMs
+
+
+def _bf16_case(nif, n, seed, mode="noise"):
+    """targets: "noise" = output + N(0, 0.5) (the gradient is a small,
+    heavily cancelled sum); "shift" = output - 1 (a coherent gradient)"""
+    uv = I.uniform_uv(n, seed=seed)
+    _, z = O.Nif(nif).forward(uv.astype(np.float64))
+    if mode == "shift":
+        return uv, (z - 1.0).astype(np.float32)
+    target = (z + np.random.default_rng(seed + 1).normal(0, 0.5, z.shape)).astype(np.float32)
+    return uv, target
+
+
+@pytest.mark.parametrize("shape,n,mode,delta", [((64, 128, 3), 128 * 37 + 5, "shift", 10.0),
+                                                ((5, 12, 2), 128 * 37 + 5, "shift", 10.0),
+                                                ((64, 128, 3), (1 << 16) + 77, "shift", 10.0),
+                                                ((16, 64, 1), 1, "noise", 10.0),
+                                                ((64, 128, 3), 128 * 37 + 5, "noise", 10.0),
+                                                ((64, 128, 3), 128 * 37 + 5, "noise", 1e-3),
+                                                ((64, 128, 3), (1 << 16) + 77, "noise", 1e-3)])
+def test_bf16_loss_and_gradient_match_rounding_model(pt, ctx, shape, n, mode, delta):
+    """BF16 GEMM operands, FP32 accumulation, against the rounding model
+    (bf16_model, pinned to the oracle on the CPU): the loss to 1e-5 and every
+    layer's W / b gradient.  With delta = 10 the Huber loss is quadratic on
+    these residuals and the gradient smooth in the network outputs: 1e-3 per
+    layer.  With the paper's delta = 1e-3 most residuals sit on the constant
+    +-delta branch, so a BF16 rounding decision that FP32 noise tips the
+    other way can flip a sign; the FP32 kernels themselves move by 1e-3
+    against an FP64 model at 2^16 rows: 1e-2 per layer.  Against the FP64
+    oracle, where the gradient is coherent ("shift" targets; BF16 operands
+    then cost at most 2% on the CPU model): 5e-2 per layer; the loss to 1e-2
+    everywhere.  Sizes: ragged against the 128-row tiles, one row, and the
+    2^16 training batch."""
+    import bf16_model as BM
+    nif = _nif(*shape)
+    g = pt.Nif(ctx, nif)
+    uv, target = _bf16_case(nif, n, seed=3, mode=mode)
+    loss, grad = g.loss_grad(torch.from_numpy(uv).cuda(), torch.from_numpy(target).cuda(), delta, precision="bf16")
+    ctx.check()
+    got = grad.cpu().numpy().astype(np.float64)
+    m_loss, m_grad = BM.mlp_loss_grad(BM.nif_features(nif.B, uv), nif.W, nif.b, target, "huber", M=nif.M,
+                                      delta=delta)
+    assert abs(float(loss.item()) - m_loss) <= 1e-5 * abs(m_loss)
+    tol = 1e-3 if delta > 1.0 else 1e-2
+    for (gw, gb), (mw, mb) in zip(_split(nif, got), _split(nif, m_grad)):
+        assert _rel(gw, mw) <= tol and _rel(gb, mb) <= tol, (_rel(gw, mw), _rel(gb, mb))
+    ref_loss, ref_grad = O.Nif(nif).loss_grad(uv.astype(np.float64), target.astype(np.float64), delta)
+    assert abs(float(loss.item()) - ref_loss) <= 1e-2 * abs(ref_loss)
+    if mode == "shift":
+        for (gw, gb), (rw, rb) in zip(_split(nif, got), _split(nif, ref_grad)):
+            assert _rel(gw, rw) <= 5e-2 and _rel(gb, rb) <= 5e-2, (_rel(gw, rw), _rel(gb, rb))
+
+
+def test_bf16_gradient_is_deterministic(pt, ctx):
+    nif = _nif()
+    g = pt.Nif(ctx, nif)
+    uv, target = _bf16_case(nif, 128 * 200 + 9, seed=5)
+    uv_t, t_t = torch.from_numpy(uv).cuda(), torch.from_numpy(target).cuda()
+    a = g.loss_grad(uv_t, t_t, 1e-3, precision="bf16")
+    b = g.loss_grad(uv_t, t_t, 1e-3, precision="bf16")
+    ctx.check()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+
+
+def test_bf16_training_tracks_fp32_training(pt, ctx):
+    """The same 40 Adam steps with BF16 and FP32 GEMMs from the same weights:
+    the first step's loss agrees to 1e-3 (only the BF16 forward differs),
+    the trajectories then drift apart slowly (lr 1e-2): the last five steps'
+    mean loss is within 20% of the FP32 run's, the loss falls, and the BF16
+    run is bit-reproducible."""
+    nif = _nif()
+    sky = torch.from_numpy(I.procedural_sky(256, 128)).cuda()
+    out = {}
+    for prec in ("fp32", "bf16", "bf16"):
+        g = pt.Nif(ctx, nif)
+        losses = g.train(sky, steps=40, batch=4096, lr=1e-2, seed=2, precision=prec).cpu().numpy()
+        ctx.check()
+        out.setdefault(prec, []).append((losses, g.get_params()))
+    (l32, _), = out["fp32"]
+    (l16a, p16a), (l16b, p16b) = out["bf16"]
+    assert np.array_equal(l16a, l16b) and np.array_equal(p16a, p16b)
+    assert abs(l16a[0] - l32[0]) <= 1e-3 * l32[0], (l16a[0], l32[0])
+    assert abs(l16a[-5:].mean() - l32[-5:].mean()) <= 0.2 * l32[-5:].mean(), (l16a[-5:], l32[-5:])
+    assert l16a[-5:].mean() < 0.5 * l16a[:3].mean()
+
+
+def test_training_precision_argument(pt, ctx):
+    """Training GEMMs take PT_FP32 or PT_BF16; FP8 is refused and nothing runs."""
+    nif = _nif(8, 32, 2)
+    g = pt.Nif(ctx, nif)
+    uv, target = _bf16_case(nif, 256, seed=6)
+    with pytest.raises(pt.PTError):
+        g.loss_grad(torch.from_numpy(uv).cuda(), torch.from_numpy(target).cuda(), 1e-3, precision="fp8")
+    with pytest.raises(pt.PTError):
+        g.train(torch.from_numpy(I.procedural_sky(64, 32)).cuda(), steps=1, batch=256, precision="fp8")
+    assert np.array_equal(g.get_params(), O.nif_flat(nif).astype(np.float32))
+    ctx.check()
