@@ -730,8 +730,10 @@ pt_status ensure_train(pt_ctx* ctx, pt_nif* nf, int64_t B)
     nf->d_batch = nullptr;
     const int G = 4 * ctx->sm_count;   // partial slots: up to four GEMM CTAs per SM
     const size_t rows = (size_t)B * 128;
-    // X[0 .. L], dX[2], G[0 .. L-2] (G[L-1] is dX[0]), partials, loss partials
-    const size_t bytes = (size_t)(2 * nf->L + 2) * rows * sizeof(float) + (size_t)G * (128 * 128 + 128) * sizeof(float) +
+    // X[0 .. L], dX[2], BF16 operand tiles Xb[0 .. L-1] and Gb[0 .. L-1], partials, loss partials
+    const size_t tiles = (size_t)((B + 127) / 128) * 128 * 128 * 2;
+    const size_t bytes = (size_t)(nf->L + 3) * rows * sizeof(float) + 2 * (size_t)nf->L * tiles +
+                         (size_t)G * (128 * 128 + 128) * sizeof(float) +
                          (size_t)G * sizeof(double) + 4096;
     if (cudaMalloc(&nf->d_work, bytes) != cudaSuccess || cudaMalloc((void**)&nf->d_batch, (size_t)B * 5 * sizeof(float)) != cudaSuccess) {
         nf->work_cap = 0;
@@ -743,8 +745,12 @@ pt_status ensure_train(pt_ctx* ctx, pt_nif* nf, int64_t B)
     nf->work.sm_count = ctx->sm_count;
     for (int l = 0; l <= nf->L; ++l) { nf->work.X[l] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
     for (int i = 0; i < 2; ++i) { nf->work.dX[i] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
-    for (int l = 0; l + 1 < nf->L; ++l) { nf->work.G[l] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
-    nf->work.G[nf->L - 1] = nf->work.dX[0];
+    for (int l = 0; l < nf->L; ++l) {
+        nf->work.Xb[l] = reinterpret_cast<unsigned char*>(w);
+        w += tiles;
+        nf->work.Gb[l] = reinterpret_cast<unsigned char*>(w);
+        w += tiles;
+    }
     nf->work.err = ctx->d_err;
     nf->work.partial = reinterpret_cast<float*>(w);
     w += (size_t)G * (128 * 128 + 128) * sizeof(float);
@@ -883,8 +889,10 @@ pt_status ensure_cache_train(pt_ctx* ctx, pt_cache* c, int64_t B)
     c->work_cap = 0;
     const int G = 4 * ctx->sm_count;   // partial slots: up to four GEMM CTAs per SM
     const size_t rows = (size_t)B * 128;
-    // X[0 .. L], dX[2], G[0 .. L-2] (G[L-1] is dX[0]), partials, loss partials
-    const size_t bytes = (size_t)(2 * c->L + 2) * rows * sizeof(float) + (size_t)G * (128 * 128 + 128) * sizeof(float) +
+    // X[0 .. L], dX[2], BF16 operand tiles Xb[0 .. L-1] and Gb[0 .. L-1], partials, loss partials
+    const size_t tiles = (size_t)((B + 127) / 128) * 128 * 128 * 2;
+    const size_t bytes = (size_t)(c->L + 3) * rows * sizeof(float) + 2 * (size_t)c->L * tiles +
+                         (size_t)G * (128 * 128 + 128) * sizeof(float) +
                          (size_t)G * sizeof(double) + 4096;
     if (cudaMalloc(&c->d_work, bytes) != cudaSuccess) return fail(ctx, PT_ENOMEM, "cache work buffers allocation failed");
     char* w = static_cast<char*>(c->d_work);
@@ -893,8 +901,12 @@ pt_status ensure_cache_train(pt_ctx* ctx, pt_cache* c, int64_t B)
     c->work.sm_count = ctx->sm_count;
     for (int l = 0; l <= c->L; ++l) { c->work.X[l] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
     for (int i = 0; i < 2; ++i) { c->work.dX[i] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
-    for (int l = 0; l + 1 < c->L; ++l) { c->work.G[l] = reinterpret_cast<float*>(w); w += rows * sizeof(float); }
-    c->work.G[c->L - 1] = c->work.dX[0];
+    for (int l = 0; l < c->L; ++l) {
+        c->work.Xb[l] = reinterpret_cast<unsigned char*>(w);
+        w += tiles;
+        c->work.Gb[l] = reinterpret_cast<unsigned char*>(w);
+        w += tiles;
+    }
     c->work.err = ctx->d_err;
     c->work.partial = reinterpret_cast<float*>(w);
     w += (size_t)G * (128 * 128 + 128) * sizeof(float);

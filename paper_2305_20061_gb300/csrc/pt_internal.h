@@ -173,7 +173,8 @@ struct TrainWork {
     int32_t sm_count;
     float* X[9];                    // X[0] features, X[l] hidden outputs, each [batch][128]
     float* dX[2];                   // ping-pong [batch][128]
-    float* G[8];                    // tensor-core path: G[l] = gradient at layer l's pre-activation; G[L-1] = dX[0]
+    unsigned char* Xb[8];           // tensor-core path: BF16 operand tiles of X[l] and of the gradient G[l] at
+    unsigned char* Gb[8];           // layer l's pre-activation, l < L; [128-row tile][core-matrix layout]
     float* partial;                 // [n_blocks][128 * 128 + 128]
     double* loss_partial;           // [n_blocks]
     unsigned int* err;              // PT_ERR_* word of the context
@@ -188,13 +189,13 @@ cudaError_t adam_step(int64_t n, float* w, const float* g, float* m, float* v, f
 cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, float delta, int mode,
                           const int32_t* mask, int precision, TrainWork& wk, double* loss_d, float* loss_f,
                           cudaStream_t s);
-// tensor-core GEMMs of training (train_tc.cu): forward X[0] -> X[1..L]; backward G[L-1] -> G[L-2..0] and
-// per-CTA partials of every layer's dW / db (Gl CTAs per layer, stride floats each, layer l's at
-// partial + l * Gl * stride: [H][pad16(in)] dW then [H] db)
+// tensor-core GEMMs of training (train_tc.cu): forward X[0] -> X[1..L] (and BF16 tiles Xb); backward from
+// G[L-1] = dX[0] -> BF16 tiles Gb and per-CTA partials of every layer's dW / db (Gl CTAs per layer, stride
+// floats each, layer l's at partial + l * Gl * stride: [H][pitch[l]] dW then [H] db)
 bool train_tc_supported(const TrainNet& net);
 cudaError_t train_tc_forward(const TrainNet& net, int64_t B, TrainWork& wk, unsigned int* err, cudaStream_t s);
 cudaError_t train_tc_backward(const TrainNet& net, int64_t B, TrainWork& wk, unsigned int* err, int* Gl, int* stride,
-                              cudaStream_t s);
+                              int* pitch, cudaStream_t s);
 
 // Radiance cache (train.cu).  Rows of 16 floats: x[3], wo[3], n[3], tp[3],
 // L[3] (radiance gathered before the vertex), slot (query) or valid (record).

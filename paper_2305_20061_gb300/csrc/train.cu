@@ -546,17 +546,16 @@ cudaError_t mlp_loss_grad_tc(const TrainNet& net, int64_t B, const float* target
 {
     cudaError_t e = train_tc_forward(net, B, wk, wk.err, s);
     if (e != cudaSuccess) return e;
-    e = head_loss(net, B, target, delta, mode, mask, wk, wk.G[net.L - 1], loss_d, loss_f, s);
+    e = head_loss(net, B, target, delta, mode, mask, wk, wk.dX[0], loss_d, loss_f, s);
     if (e != cudaSuccess) return e;
-    int Gl = 0, stride = 0;
-    e = train_tc_backward(net, B, wk, wk.err, &Gl, &stride, s);
+    int Gl = 0, stride = 0, pitch[8] = {};
+    e = train_tc_backward(net, B, wk, wk.err, &Gl, &stride, pitch, s);
     if (e != cudaSuccess) return e;
     for (int l = 0; l < net.L; ++l) {
         const int in = l == 0 ? net.in0 : net.H;
-        const int Kin = (in + 15) & ~15;
         k_sum_partials<<<(in * net.H + net.H + 31) / 32, 256, 0, s>>>(wk.partial + (size_t)l * Gl * stride, Gl, stride,
-                                                                       Kin, net.H * Kin, in, net.H, net.gW[l],
-                                                                       net.gb[l]);
+                                                                       pitch[l], net.H * pitch[l], in, net.H,
+                                                                       net.gW[l], net.gb[l]);
     }
     return cudaGetLastError();
 }

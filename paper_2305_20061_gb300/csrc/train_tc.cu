@@ -1,7 +1,7 @@
 // Tensor-core GEMMs of MLP training: the HDR NIF (Section 3.2.1) and the
 // online radiance cache (Section 3.3).  BF16 operands, FP32 accumulation in
-// TMEM (tcgen05), FP32 activations and gradients in HBM ([sample][128] rows),
-// FP32 master weights.
+// TMEM (tcgen05), FP32 activations in HBM ([sample][128] rows), FP32 master
+// weights.
 //
 //   forward   X[l+1] = relu(X[l] W_l^T + b_l), l = 0 .. L-1.  A CTA holds
 //             every hidden layer's weights in shared memory and takes each
@@ -10,17 +10,20 @@
 //   backward  G[l-1] = (G[l] W_l) * [X[l] > 0], l = L-1 .. 1, chained the
 //             same way from the output layer's gradient G[L-1].
 //   weights   dW_l = G[l]^T X[l] and db_l = the column sums of G[l].  The
-//             batch is the reduction, so both operands are staged transposed
-//             (operand rows = features, K = samples), and a row of ones
-//             appended to X[l]^T yields db_l in the same MMA.  A CTA
+//             batch is the reduction.  The two chains also write every BF16
+//             operand tile they build (X[0 .. L-1], G[0 .. L-1]) to HBM in
+//             the MMA's core-matrix layout; read back as MN-major operands
+//             (rows = samples = K) they need no transposition, so the weight
+//             kernel is a TMA bulk-copy pipeline feeding the MMA.  A constant
+//             ones column appended to X[l] yields db_l in the same MMA.  A CTA
 //             accumulates its share of the batch for one layer in TMEM and
 //             writes one partial; partials are summed in a fixed order, so
 //             the gradient is deterministic.
 //
-// Operands use the K-major SWIZZLE_NONE layout (8-row x 16-byte core
-// matrices) with strides chosen so that the staging stores are free of
-// shared-memory bank conflicts.  Every mbarrier wait is bounded; a CTA that
-// gives up sets PT_ERR_TIMEOUT, waits (bounded) for its MMAs and frees TMEM.
+// Shared-memory operands use the SWIZZLE_NONE core-matrix layout (8 rows x
+// 16 bytes); the strides of the activation tiles keep the staging stores free
+// of bank conflicts.  Every mbarrier wait is bounded; a CTA that gives up
+// sets PT_ERR_TIMEOUT, waits (bounded) for its MMAs and frees TMEM.
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -34,11 +37,15 @@ namespace {
 using namespace tc;
 
 constexpr int kRows = 128;                   // samples per tile (M of the row GEMMs, K of the weight GEMM)
-constexpr int kThreads = 256;                // two warps per TMEM lane quarter
+constexpr int kThreads = 512;                // 16 warps: four per TMEM lane quarter; warp w stages rows 8w .. 8w+7
+constexpr int kGroups = kThreads / 128;      // warps sharing a lane quarter (they split the columns)
 constexpr int kMaxLayers = 8;
 constexpr uint32_t kActLbo = 16 * 128 + 16;  // activation tile: byte step between 8-column core blocks
-constexpr uint32_t kTSbo = 144;              // transposed tile: byte step between 8-feature groups
-constexpr uint32_t kTLboA = 16 * kTSbo;      // G^T tile (128 features): byte step between 8-sample blocks
+constexpr uint32_t kTileCb = 2048;           // HBM operand tile: byte step between 8-column blocks (128 rows x 16 B)
+constexpr uint32_t kBarBytes = 32;           // two MMA barriers, the drain barrier, TMEM address, abort flag
+constexpr int kDwThreads = 128;              // weight kernel: one thread drives the pipeline, four warps drain TMEM
+constexpr int kDwMaxStages = 4;
+constexpr uint32_t kDwBarBytes = 128;        // full / empty per stage, done, drain, TMEM address, abort flag
 constexpr int kSmemPerSm = 233472;           // 228 KiB of shared memory per SM
 constexpr int kSmemReserved = 1024;          // reserved per CTA
 
@@ -49,6 +56,7 @@ struct FwdParams {
     int L, in0, K0, H;
     const float* X0;
     float* X[kMaxLayers + 1];        // X[1 .. L] written
+    unsigned char* Xb[kMaxLayers];   // BF16 operand tiles of X[0 .. L-1] written
     const float* W[kMaxLayers];
     const float* b[kMaxLayers];
     unsigned int* err;
@@ -59,7 +67,7 @@ struct DxParams {
     int L, H;
     const float* Gtop;               // G[L-1]
     const float* X[kMaxLayers];      // X[1 .. L-1]: the ReLU masks
-    float* G[kMaxLayers];            // G[0 .. L-2] written
+    unsigned char* Gb[kMaxLayers];   // BF16 operand tiles of G[0 .. L-1] written
     const float* W[kMaxLayers];      // W[1 .. L-1]
     unsigned int* err;
 };
@@ -67,14 +75,15 @@ struct DxParams {
 struct DwParams {
     int64_t B;
     int L, H, in0, Gl, stride;       // Gl CTAs per layer, stride floats per partial
-    const float* G[kMaxLayers];
-    const float* X[kMaxLayers];
+    int stages;                      // pipeline depth
+    const unsigned char* Gb[kMaxLayers];
+    const unsigned char* Xb[kMaxLayers];
     float* partial;                  // [L * Gl][stride]: [H][pad16(in)] dW, then [H] db
     unsigned int* err;
 };
 
 struct Bars {
-    uint32_t bar, drain;
+    uint32_t bar[2], drain;
     uint32_t* tmem_slot;
     volatile int* abort;
 };
@@ -82,10 +91,11 @@ struct Bars {
 __device__ __forceinline__ Bars bars_at(unsigned char* smem, uint32_t off)
 {
     Bars b;
-    b.bar = smem_u32(smem + off);
-    b.drain = b.bar + 8;
-    b.tmem_slot = reinterpret_cast<uint32_t*>(smem + off + 16);
-    b.abort = reinterpret_cast<volatile int*>(smem + off + 20);
+    b.bar[0] = smem_u32(smem + off);
+    b.bar[1] = b.bar[0] + 8;
+    b.drain = b.bar[0] + 16;
+    b.tmem_slot = reinterpret_cast<uint32_t*>(smem + off + 24);
+    b.abort = reinterpret_cast<volatile int*>(smem + off + 28);
     return b;
 }
 
@@ -94,7 +104,8 @@ __device__ __forceinline__ Bars bars_at(unsigned char* smem, uint32_t off)
 __device__ __forceinline__ void tc_begin(const Bars& b, uint32_t cols)
 {
     if (threadIdx.x == 0) {
-        mbar_init(b.bar, 1);
+        mbar_init(b.bar[0], 1);
+        mbar_init(b.bar[1], 1);
         mbar_init(b.drain, 1);
         *b.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -130,10 +141,10 @@ __device__ __forceinline__ void tc_end(const Bars& b, uint32_t tmem, uint32_t co
     }
 }
 
-// the whole CTA waits for the MMA commit; true when every thread saw it
-__device__ __forceinline__ bool wait_all(const Bars& b, uint32_t ph, unsigned int* err)
+// the whole CTA waits for a commit on `bar`; true when every thread saw it
+__device__ __forceinline__ bool wait_all(const Bars& b, uint32_t bar, uint32_t ph, unsigned int* err)
 {
-    const bool got = mbar_wait(b.bar, ph, b.abort, err);
+    const bool got = mbar_wait(bar, ph, b.abort, err);
     const bool ok = __syncthreads_and(got) != 0;
     if (ok) tc_fence_after();
     return ok;
@@ -153,66 +164,33 @@ __device__ __forceinline__ float4 mask4(float4 v, int c, int width)
     return v;
 }
 
-// Rows [tile*128, +128) x columns [0, K) of a [B][128] FP32 matrix -> BF16
-// activation tile: byte (r>>3)*128 + (c>>3)*kActLbo + (r&7)*16 + (c&7)*2.
-// Columns >= width and rows >= B are zeros.  Warp w takes rows 16w .. 16w+15,
-// lane l columns 4l .. 4l+3 (one coalesced row per load).
-__device__ __forceinline__ void stage_rows(uint32_t a, const float* __restrict__ X, int64_t tile, int64_t B, int width,
-                                           int K)
+// This warp's 8 rows (8w .. 8w+7) of rows [tile*128, +128) of a [B][128]
+// FP32 matrix, columns 4l .. 4l+3 for lane l (one coalesced row per load);
+// columns >= width and rows >= B read as zeros.  Lanes with 4l >= K load
+// nothing.
+__device__ __forceinline__ void load_rows8(float4 (&v)[8], const float* __restrict__ X, int64_t tile, int64_t B,
+                                           int width, int K)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = 4 * lane;
-    if (c >= K) return;
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int warp = threadIdx.x >> 5, c = 4 * (threadIdx.x & 31);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float4 v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t g = tile * kRows + warp * 16 + h * 8 + i;
-            v[i] = (g < B && c < width) ? mask4(ld4(X + g * 128 + c), c, width) : z;
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const uint32_t r = warp * 16 + h * 8 + i;
-            const uint32_t addr = a + (r >> 3) * 128 + (c >> 3) * kActLbo + (r & 7) * 16 + (c & 7) * 2;
-            asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(pack_bf16(v[i].x, v[i].y)),
-                         "r"(pack_bf16(v[i].z, v[i].w))
-                         : "memory");
-        }
+    for (int i = 0; i < 8; ++i) {
+        const int64_t g = tile * kRows + warp * 8 + i;
+        v[i] = (c < K && g < B && c < width) ? mask4(ld4(X + g * 128 + c), c, width) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
-// Rows [tile*128, +128) x columns [0, Kc) of a [B][128] FP32 matrix,
-// transposed into a K-major operand whose rows are the columns c and whose K
-// is the sample: byte (c>>3)*kTSbo + (r>>3)*lbo + (c&7)*16 + (r&7)*2.  Warp w
-// takes the 8-sample blocks w and w + 8; lane l loads columns 4l .. 4l+3 of
-// the block's 8 rows and stores each column's 8 samples as one 16-byte row.
-__device__ __forceinline__ void stage_cols(uint32_t t, uint32_t lbo, const float* __restrict__ X, int64_t tile,
-                                           int64_t B, int width, int Kc)
+// ... as BF16 into the activation tile: byte (r>>3)*128 + (c>>3)*kActLbo +
+// (r&7)*16 + (c&7)*2 (the A operand of the row GEMMs, K = columns)
+__device__ __forceinline__ void store_rows8(uint32_t a, const float4 (&v)[8], int K)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = 4 * lane;
-    if (c >= Kc) return;
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int warp = threadIdx.x >> 5, c = 4 * (threadIdx.x & 31);
+    if (c >= K) return;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int rb = warp + 8 * h;
-        float4 v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int64_t g = tile * kRows + rb * 8 + i;
-            v[i] = (g < B && c < width) ? mask4(ld4(X + g * 128 + c), c, width) : z;
-        }
-        const uint32_t base = t + (c >> 3) * kTSbo + rb * lbo + (c & 7) * 16;
-        st_shared_v4(base, pack_bf16(v[0].x, v[1].x), pack_bf16(v[2].x, v[3].x), pack_bf16(v[4].x, v[5].x),
-                     pack_bf16(v[6].x, v[7].x));
-        st_shared_v4(base + 16, pack_bf16(v[0].y, v[1].y), pack_bf16(v[2].y, v[3].y), pack_bf16(v[4].y, v[5].y),
-                     pack_bf16(v[6].y, v[7].y));
-        st_shared_v4(base + 32, pack_bf16(v[0].z, v[1].z), pack_bf16(v[2].z, v[3].z), pack_bf16(v[4].z, v[5].z),
-                     pack_bf16(v[6].z, v[7].z));
-        st_shared_v4(base + 48, pack_bf16(v[0].w, v[1].w), pack_bf16(v[2].w, v[3].w), pack_bf16(v[4].w, v[5].w),
-                     pack_bf16(v[6].w, v[7].w));
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t addr = a + warp * 128 + (c >> 3) * kActLbo + i * 16 + (c & 7) * 2;
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(pack_bf16(v[i].x, v[i].y)),
+                     "r"(pack_bf16(v[i].z, v[i].w))
+                     : "memory");
     }
 }
 
@@ -241,13 +219,38 @@ __device__ __forceinline__ void store16(float* dst, const float (&v)[16])
 #pragma unroll
     for (int q = 0; q < 4; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
+__device__ __forceinline__ void pack16(const float (&v)[16], uint32_t (&w)[8])
+{
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+}
 // 16 columns c0 .. c0+15 of activation-tile row `row` (two core blocks)
-__device__ __forceinline__ void put_act16(uint32_t a_row, int c0, const float (&v)[16])
+__device__ __forceinline__ void put_act16(uint32_t a_row, int c0, const uint32_t (&w)[8])
 {
     const uint32_t p = a_row + (uint32_t)(c0 >> 3) * kActLbo;
-    st_shared_v4(p, pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-    st_shared_v4(p + kActLbo, pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
-                 pack_bf16(v[14], v[15]));
+    st_shared_v4(p, w[0], w[1], w[2], w[3]);
+    st_shared_v4(p + kActLbo, w[4], w[5], w[6], w[7]);
+}
+// ... and of the HBM operand tile: byte (r>>3)*128 + (c>>3)*kTileCb + (r&7)*16 + (c&7)*2 (a warp's 32 rows
+// are 512 contiguous bytes)
+__device__ __forceinline__ void put_tile16(unsigned char* tile, int row, int c0, const uint32_t (&w)[8])
+{
+    uint4* d = reinterpret_cast<uint4*>(tile + (size_t)(c0 >> 3) * kTileCb + row * 16);
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d[kTileCb / 16] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+// the activation tile's columns [0, C) -> the HBM operand tile (16-byte units, coalesced)
+__device__ __forceinline__ void copy_act_to_tile(unsigned char* tile, uint32_t a, int C)
+{
+    for (int u = threadIdx.x; u < kRows * (C / 8); u += kThreads) {
+        const int r = u & (kRows - 1), cb = u >> 7;
+        uint32_t x0, x1, x2, x3;
+        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(x0), "=r"(x1), "=r"(x2), "=r"(x3)
+                     : "r"(a + cb * kActLbo + r * 16)
+                     : "memory");
+        *reinterpret_cast<uint4*>(tile + (size_t)cb * kTileCb + r * 16) = make_uint4(x0, x1, x2, x3);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -261,7 +264,7 @@ __host__ __device__ constexpr uint32_t fwd_bar_offset(int L, int K0)
 }
 
 template <int NH>
-__global__ void __launch_bounds__(kThreads, NH <= 64 ? 2 : 1) k_tc_fwd(const FwdParams p)
+__global__ void __launch_bounds__(kThreads, 1) k_tc_fwd(const FwdParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const uint32_t sbase = smem_u32(smem);
@@ -290,10 +293,14 @@ __global__ void __launch_bounds__(kThreads, NH <= 64 ? 2 : 1) k_tc_fwd(const Fwd
     const int64_t n_tiles = (p.B + kRows - 1) / kRows;
     uint32_t ph = 0;
     bool ok = true;
+    float4 pf[8];   // the next tile's input rows, loaded while this tile runs through the layers
+    load_rows8(pf, p.X0, blockIdx.x, p.B, p.in0, K0);
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        stage_rows(a, p.X0, tile, p.B, p.in0, K0);
+        store_rows8(a, pf, K0);
         fence_proxy_async();
         __syncthreads();
+        if (tile + gridDim.x < n_tiles) load_rows8(pf, p.X0, tile + gridDim.x, p.B, p.in0, K0);
+        copy_act_to_tile(p.Xb[0] + (size_t)tile * kRows * K0 * 2, a, K0);   // read before layer 0's epilogue
         const int64_t g = tile * kRows + row;
         for (int l = 0; l < L; ++l) {
             if (threadIdx.x == 0 && !*bs.abort) {
@@ -303,14 +310,14 @@ __global__ void __launch_bounds__(kThreads, NH <= 64 ? 2 : 1) k_tc_fwd(const Fwd
                 for (int ks = 0; ks < K / 16; ++ks)
                     mma_bf16(tmem, plain_desc(a + ks * 2 * kActLbo, kActLbo, 128),
                              plain_desc(w + ks * 2 * (NH * 16), NH * 16, 128), idesc, ks > 0);
-                mma_commit(bs.bar);
+                mma_commit(bs.bar[0]);
             }
-            ok = wait_all(bs, ph, p.err);
+            ok = wait_all(bs, bs.bar[0], ph, p.err);
             if (!ok) break;
             ph ^= 1;
             float* dst = p.X[l + 1] + g * 128;
 #pragma unroll
-            for (int cc = grp; cc < NH / 16; cc += 2) {
+            for (int cc = grp; cc < NH / 16; cc += kGroups) {
                 uint32_t r[16];
                 tmem_ld16(tl + cc * 16, r);
                 tmem_wait_ld();
@@ -321,7 +328,12 @@ __global__ void __launch_bounds__(kThreads, NH <= 64 ? 2 : 1) k_tc_fwd(const Fwd
                     v[e] = c < p.H ? fmaxf(__uint_as_float(r[e]) + bias[l * NH + c], 0.f) : 0.f;
                 }
                 if (g < p.B) store16(dst + cc * 16, v);
-                if (l + 1 < L) put_act16(a_row, cc * 16, v);
+                if (l + 1 < L) {
+                    uint32_t w[8];
+                    pack16(v, w);
+                    put_act16(a_row, cc * 16, w);
+                    put_tile16(p.Xb[l + 1] + (size_t)tile * kRows * NH * 2, row, cc * 16, w);
+                }
             }
             tc_fence_before();
             fence_proxy_async();
@@ -340,7 +352,7 @@ __host__ __device__ constexpr uint32_t dx_bar_offset(int L)
 }
 
 template <int NH>
-__global__ void __launch_bounds__(kThreads, NH <= 64 ? 2 : 1) k_tc_dx(const DxParams p)
+__global__ void __launch_bounds__(kThreads, 1) k_tc_dx(const DxParams p)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const uint32_t sbase = smem_u32(smem);
@@ -360,14 +372,19 @@ __global__ void __launch_bounds__(kThreads, NH <= 64 ? 2 : 1) k_tc_dx(const DxPa
     const uint32_t tl = tmem + ((q * 32u) << 16);
     const uint32_t a_row = a + (row >> 3) * 128 + (row & 7) * 16;
     const uint32_t idesc = idesc_bf16(128, NH);
-    constexpr int kMine = (NH / 16 + 1) / 2;   // column chunks per thread
+    constexpr int kMine = (NH / 16 + kGroups - 1) / kGroups;   // column chunks per thread
     const int64_t n_tiles = (p.B + kRows - 1) / kRows;
     uint32_t ph = 0;
     bool ok = true;
+    float4 pf[8];
+    load_rows8(pf, p.Gtop, blockIdx.x, p.B, p.H, NH);
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        stage_rows(a, p.Gtop, tile, p.B, p.H, NH);
+        store_rows8(a, pf, NH);
         fence_proxy_async();
         __syncthreads();
+        if (tile + gridDim.x < n_tiles) load_rows8(pf, p.Gtop, tile + gridDim.x, p.B, p.H, NH);
+        copy_act_to_tile(p.Gb[L - 1] + (size_t)tile * kRows * NH * 2, a, NH);
+        if (L == 1) __syncthreads();   // no layer step below: the next tile's staging must wait for the copy
         const int64_t g = tile * kRows + row;
         for (int l = L - 1; l >= 1; --l) {
             if (threadIdx.x == 0 && !*bs.abort) {
@@ -376,25 +393,25 @@ __global__ void __launch_bounds__(kThreads, NH <= 64 ? 2 : 1) k_tc_dx(const DxPa
                 for (int ks = 0; ks < NH / 16; ++ks)
                     mma_bf16(tmem, plain_desc(a + ks * 2 * kActLbo, kActLbo, 128),
                              plain_desc(w + ks * 2 * (NH * 16), NH * 16, 128), idesc, ks > 0);
-                mma_commit(bs.bar);
+                mma_commit(bs.bar[0]);
             }
             // the ReLU mask of this row while the MMA runs
             float4 xm[kMine][4];
 #pragma unroll
             for (int i = 0; i < kMine; ++i) {
-                const int cc = grp + 2 * i;
+                const int cc = grp + kGroups * i;
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     xm[i][u] = (g < p.B && cc < NH / 16) ? ld4(p.X[l] + g * 128 + cc * 16 + 4 * u)
                                                         : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            ok = wait_all(bs, ph, p.err);
+            ok = wait_all(bs, bs.bar[0], ph, p.err);
             if (!ok) break;
             ph ^= 1;
-            float* dst = p.G[l - 1] + g * 128;
+            unsigned char* gt = p.Gb[l - 1] + (size_t)tile * kRows * NH * 2;
 #pragma unroll
             for (int i = 0; i < kMine; ++i) {
-                const int cc = grp + 2 * i;
+                const int cc = grp + kGroups * i;
                 if (cc >= NH / 16) break;
                 uint32_t r[16];
                 tmem_ld16(tl + cc * 16, r);
@@ -409,8 +426,10 @@ __global__ void __launch_bounds__(kThreads, NH <= 64 ? 2 : 1) k_tc_dx(const DxPa
                         v[4 * u + e] = (c < p.H && xs[e] > 0.f) ? __uint_as_float(r[4 * u + e]) : 0.f;
                     }
                 }
-                if (g < p.B) store16(dst + cc * 16, v);
-                if (l > 1) put_act16(a_row, cc * 16, v);
+                uint32_t w[8];
+                pack16(v, w);
+                if (l > 1) put_act16(a_row, cc * 16, w);
+                put_tile16(gt, row, cc * 16, w);
             }
             tc_fence_before();
             fence_proxy_async();
@@ -421,63 +440,127 @@ __global__ void __launch_bounds__(kThreads, NH <= 64 ? 2 : 1) k_tc_dx(const DxPa
 }
 
 // ---------------------------------------------------------------------------
-// weight and bias gradients: CTA b handles layer b / Gl, tiles (b % Gl) + i Gl
-__host__ __device__ constexpr uint32_t dw_lbo_b(int N) { return (uint32_t)(N / 8) * kTSbo; }
-__host__ __device__ constexpr uint32_t dw_bar_offset(int Nmax) { return 16 * kTLboA + 16 * dw_lbo_b(Nmax); }
+// weight and bias gradients: CTA b handles layer b / Gl, tiles (b % Gl) + i Gl.
+// Stage s of the pipeline: the G tile as the MN-major A operand (128 feature
+// rows; features >= NH stay zero), then the X tile followed by a ones column
+// (feature Kin) as the MN-major B operand.  Both are copied by TMA straight
+// from the HBM operand tiles, which have the same layout.
+__host__ __device__ constexpr uint32_t dw_a_bytes() { return 16 * kTileCb; }
+__host__ __device__ constexpr uint32_t dw_b_bytes(int Kmax)
+{
+    return (uint32_t)((Kmax / 8 + 2) > 16 ? (Kmax / 8 + 2) : 16) * kTileCb;   // >= 16 blocks: see the launch
+}
+__host__ __device__ constexpr uint32_t dw_stage_bytes(int Kmax) { return dw_a_bytes() + dw_b_bytes(Kmax); }
 
 template <int NH>
-__global__ void __launch_bounds__(kThreads, NH <= 64 ? 3 : 2) k_tc_dw(const DwParams p, uint32_t cols)
+__global__ void __launch_bounds__(kDwThreads, 1) k_tc_dw(const DwParams p, uint32_t cols)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const uint32_t sbase = smem_u32(smem);
     const int l = blockIdx.x / p.Gl, part = blockIdx.x % p.Gl;
-    const int in = l == 0 ? p.in0 : p.H;
-    const int Kin = pad16(in), N = Kin + 16;
-    const int Nmax = (pad16(p.in0) > NH ? pad16(p.in0) : NH) + 16;
-    const uint32_t at = sbase, bt = sbase + 16 * kTLboA, lbo_b = dw_lbo_b(N);
-    const Bars bs = bars_at(smem, dw_bar_offset(Nmax));
+    const int Kin = l == 0 ? pad16(p.in0) : NH;   // the X tile's width (as the chains wrote it)
+    const int N = Kin + 16;
+    const int Kmax = pad16(p.in0) > NH ? pad16(p.in0) : NH;
+    const uint32_t stage = dw_stage_bytes(Kmax);
+    const int S = p.stages;
+    const uint32_t bars = S * stage;
+    const uint32_t full0 = sbase + bars, empty0 = full0 + 8 * kDwMaxStages, done = empty0 + 8 * kDwMaxStages;
+    const uint32_t drain = done + 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + bars + 16 * kDwMaxStages + 16);
+    volatile int* abort = reinterpret_cast<volatile int*>(smem + bars + 16 * kDwMaxStages + 20);
 
-    tc_begin(bs, cols);
-    // G^T rows (features) NH .. 127 stay zero; X^T gets a ones row at feature Kin (the bias gradient)
-    for (int i = threadIdx.x; i < (int)(16 * kTLboA / 16); i += kThreads) st_shared_v4(at + 16 * i, 0u, 0u, 0u, 0u);
-    {
-        const int rb = threadIdx.x >> 4, f = threadIdx.x & 15;   // 16 sample blocks x 16 feature rows
-        const uint32_t one = f == 0 ? 0x3F803F80u : 0u;
-        st_shared_v4(bt + ((Kin + f) >> 3) * kTSbo + rb * lbo_b + ((Kin + f) & 7) * 16, one, one, one, one);
-    }
-    const uint32_t tmem = tc_begin_finish(bs);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, grp = warp >> 2;
-    const uint32_t idesc = idesc_bf16(128, N);
-    const int64_t n_tiles = (p.B + kRows - 1) / kRows;
-    uint32_t ph = 0;
-    int it = 0;
-    bool ok = true;
-    for (int64_t tile = part; tile < n_tiles; tile += p.Gl, ++it) {
-        stage_cols(at, kTLboA, p.G[l], tile, p.B, p.H, NH);
-        stage_cols(bt, lbo_b, p.X[l], tile, p.B, in, Kin);
-        fence_proxy_async();
-        __syncthreads();
-        if (threadIdx.x == 0 && !*bs.abort) {
-            tc_fence_after();
-#pragma unroll
-            for (int ks = 0; ks < kRows / 16; ++ks)
-                mma_bf16(tmem, plain_desc(at + ks * 2 * kTLboA, kTLboA, kTSbo), plain_desc(bt + ks * 2 * lbo_b, lbo_b, kTSbo),
-                         idesc, (it > 0 || ks > 0) ? 1u : 0u);
-            mma_commit(bs.bar);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(full0 + 8 * i, 1);
+            mbar_init(empty0 + 8 * i, 1);
         }
-        ok = wait_all(bs, ph, p.err);
-        if (!ok) break;
-        ph ^= 1;
+        mbar_init(done, 1);
+        mbar_init(drain, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (ok) {
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // constant parts of every stage: A feature blocks NH/8 .. 15 zero; B block Kin/8 = [1, 0 .. 0] per
+    // sample row (the ones column), block Kin/8 + 1 zero
+    for (int i = 0; i < S; ++i) {
+        const uint32_t st = sbase + i * stage;
+        for (int u = threadIdx.x; u < (int)((16 - NH / 8) * (kTileCb / 16)); u += kDwThreads)
+            st_shared_v4(st + (NH / 8) * kTileCb + 16 * u, 0u, 0u, 0u, 0u);
+        for (int u = threadIdx.x; u < 2 * kRows; u += kDwThreads) {
+            const int blk = u >> 7, r = u & (kRows - 1);
+            st_shared_v4(st + dw_a_bytes() + (Kin / 8 + blk) * kTileCb + r * 16, blk == 0 ? 0x3F80u : 0u, 0u, 0u, 0u);
+        }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int64_t n_tiles = (p.B + kRows - 1) / kRows;
+    const int n_my = part < n_tiles ? (int)((n_tiles - 1 - part) / p.Gl + 1) : 0;
+    if (threadIdx.x == 0) {
+        // MN-major A and B (transpose bits 15 and 16): core matrices of 8 samples x 16 bytes (8 features);
+        // K (samples) steps 128 bytes per 8 samples, features step kTileCb per 8
+        const uint32_t idesc = idesc_bf16(128, N) | (1u << 15) | (1u << 16);
+        const uint32_t gbytes = kRows * NH * 2, xbytes = kRows * Kin * 2;
+        const unsigned char* gsrc = p.Gb[l];
+        const unsigned char* xsrc = p.Xb[l];
+        bool ok = true;
+        for (int i = 0; i < n_my + S - 1 && ok; ++i) {
+            if (i < n_my) {   // TMA of tile i into stage i % S once the MMAs of tile i - S are done with it
+                const int s = i % S;
+                const int64_t tile = part + (int64_t)i * p.Gl;
+                if (i >= S) ok = mbar_wait(empty0 + 8 * s, (uint32_t)((i / S - 1) & 1), abort, p.err);
+                if (!ok) break;
+                const uint32_t st = sbase + s * stage;
+                mbar_expect_tx(full0 + 8 * s, gbytes + xbytes);
+                bulk_g2s(st, gsrc + (size_t)tile * gbytes, gbytes, full0 + 8 * s);
+                bulk_g2s(st + dw_a_bytes(), xsrc + (size_t)tile * xbytes, xbytes, full0 + 8 * s);
+            }
+            const int j = i - (S - 1);
+            if (j >= 0) {     // MMAs of tile j
+                const int s = j % S;
+                ok = mbar_wait(full0 + 8 * s, (uint32_t)((j / S) & 1), abort, p.err);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t st = sbase + s * stage;
+#pragma unroll
+                for (int ks = 0; ks < kRows / 16; ++ks)
+                    mma_bf16(tmem, plain_desc(st + ks * 256, 128, kTileCb),
+                             plain_desc(st + dw_a_bytes() + ks * 256, 128, kTileCb), idesc,
+                             (j > 0 || ks > 0) ? 1u : 0u);
+                mma_commit(empty0 + 8 * s);
+            }
+        }
+        if (ok) {
+            mma_commit(done);
+            ok = mbar_wait(done, 0, abort, p.err);
+        }
+        if (!ok) {
+            *abort = 1;
+            mma_commit(drain);
+            const uint64_t t0 = global_ns();
+            while (!mbar_try_wait(drain, 0) && global_ns() - t0 < kWaitBudgetNs) {
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (!*abort) {
         // TMEM lane j = row j of dW_l; columns k < Kin are dW_l[j][k], column Kin is db_l[j]
-        const int j = q * 32 + lane;
-        const uint32_t tl = tmem + ((q * 32u) << 16);
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int j = warp * 32 + lane;
+        const uint32_t tl = tmem + ((warp * 32u) << 16);
         float* P = p.partial + (size_t)blockIdx.x * p.stride;
-        for (int cc = grp; cc < N / 16; cc += 2) {
+        for (int cc = 0; cc < N / 16; ++cc) {
             float v[16];
-            if (it > 0) {
+            if (n_my > 0) {
                 uint32_t r[16];
                 tmem_ld16(tl + cc * 16, r);
                 tmem_wait_ld();
@@ -495,7 +578,12 @@ __global__ void __launch_bounds__(kThreads, NH <= 64 ? 3 : 2) k_tc_dw(const DwPa
             }
         }
     }
-    tc_end(bs, tmem, cols, ok);
+    tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -515,12 +603,14 @@ int smem_for_tmem(int need, int cols)
 
 // grid of a persistent launch: as many CTAs as fit at once; error when the
 // residency would oversubscribe TMEM
-cudaError_t resident_grid(const void* fn, int smem, int cols, int sm_count, int64_t want, int* grid)
+cudaError_t resident_grid(const void* fn, int threads, int smem, int cols, int sm_count, int64_t want, int* grid)
 {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1 || occ * cols > 512) return cudaErrorInvalidConfiguration;
     const int64_t g = (int64_t)occ * sm_count;
@@ -540,14 +630,16 @@ cudaError_t forward_nh(const TrainNet& net, int64_t B, TrainWork& wk, unsigned i
     p.X0 = wk.X[0];
     for (int l = 1; l <= net.L; ++l) p.X[l] = wk.X[l];
     for (int l = 0; l < net.L; ++l) {
+        p.Xb[l] = wk.Xb[l];
         p.W[l] = net.W[l];
         p.b[l] = net.b[l];
     }
     p.err = err;
     constexpr int kCols = NH < 32 ? 32 : NH;
-    const int smem = smem_for_tmem((int)fwd_bar_offset<NH>(net.L, p.K0) + 32, kCols);
+    const int smem = smem_for_tmem((int)(fwd_bar_offset<NH>(net.L, p.K0) + kBarBytes), kCols);
     int grid = 0;
-    cudaError_t e = resident_grid((const void*)k_tc_fwd<NH>, smem, kCols, wk.sm_count, (B + kRows - 1) / kRows, &grid);
+    cudaError_t e = resident_grid((const void*)k_tc_fwd<NH>, kThreads, smem, kCols, wk.sm_count,
+                                  (B + kRows - 1) / kRows, &grid);
     if (e != cudaSuccess) return e;
     k_tc_fwd<NH><<<grid, kThreads, smem, s>>>(p);
     return cudaGetLastError();
@@ -555,26 +647,26 @@ cudaError_t forward_nh(const TrainNet& net, int64_t B, TrainWork& wk, unsigned i
 
 template <int NH>
 cudaError_t backward_nh(const TrainNet& net, int64_t B, TrainWork& wk, unsigned int* err, int* Gl_out, int* stride_out,
-                        cudaStream_t s)
+                        int* pitch, cudaStream_t s)
 {
     const int64_t n_tiles = (B + kRows - 1) / kRows;
     constexpr int kCols = NH < 32 ? 32 : NH;
     cudaError_t e;
-    if (net.L > 1) {
+    {
         DxParams p = {};
         p.B = B;
         p.L = net.L;
         p.H = net.H;
-        p.Gtop = wk.G[net.L - 1];
+        p.Gtop = wk.dX[0];
         for (int l = 1; l < net.L; ++l) {
             p.X[l] = wk.X[l];
             p.W[l] = net.W[l];
         }
-        for (int l = 0; l + 1 < net.L; ++l) p.G[l] = wk.G[l];
+        for (int l = 0; l < net.L; ++l) p.Gb[l] = wk.Gb[l];
         p.err = err;
-        const int smem = smem_for_tmem((int)dx_bar_offset<NH>(net.L) + 32, kCols);
+        const int smem = smem_for_tmem((int)(dx_bar_offset<NH>(net.L) + kBarBytes), kCols);
         int grid = 0;
-        e = resident_grid((const void*)k_tc_dx<NH>, smem, kCols, wk.sm_count, n_tiles, &grid);
+        e = resident_grid((const void*)k_tc_dx<NH>, kThreads, smem, kCols, wk.sm_count, n_tiles, &grid);
         if (e != cudaSuccess) return e;
         k_tc_dx<NH><<<grid, kThreads, smem, s>>>(p);
         e = cudaGetLastError();
@@ -586,18 +678,25 @@ cudaError_t backward_nh(const TrainNet& net, int64_t B, TrainWork& wk, unsigned 
     p.H = net.H;
     p.in0 = net.in0;
     for (int l = 0; l < net.L; ++l) {
-        p.G[l] = wk.G[l];
-        p.X[l] = wk.X[l];
+        p.Gb[l] = wk.Gb[l];
+        p.Xb[l] = wk.Xb[l];
     }
     const int Kmax = pad16(net.in0) > NH ? pad16(net.in0) : NH;
     const int Nmax = Kmax + 16;
     p.stride = (NH * Kmax + NH + 3) & ~3;
     p.partial = wk.partial;
     p.err = err;
+    // B regions of at least 16 feature blocks and A regions of exactly 16: every operand read stays inside
+    // its stage for either assignment of the two descriptor strides to the two directions
+    const int budget = 227 * 1024 - (int)kDwBarBytes;
+    int stages = budget / (int)dw_stage_bytes(Kmax);
+    if (stages > kDwMaxStages) stages = kDwMaxStages;
+    if (stages < 2) return cudaErrorInvalidConfiguration;
+    p.stages = stages;
     const int cols = tmem_cols_for(Nmax);
-    const int smem = smem_for_tmem((int)dw_bar_offset(Nmax) + 32, cols);
+    const int smem = smem_for_tmem(stages * (int)dw_stage_bytes(Kmax) + (int)kDwBarBytes, cols);
     int resident = 0;
-    e = resident_grid((const void*)k_tc_dw<NH>, smem, cols, wk.sm_count, (int64_t)1 << 30, &resident);
+    e = resident_grid((const void*)k_tc_dw<NH>, kDwThreads, smem, cols, wk.sm_count, (int64_t)1 << 30, &resident);
     if (e != cudaSuccess) return e;
     int Gl = resident / net.L;
     if (Gl > wk.n_blocks / net.L) Gl = wk.n_blocks / net.L;   // partial slots
@@ -605,9 +704,10 @@ cudaError_t backward_nh(const TrainNet& net, int64_t B, TrainWork& wk, unsigned 
     if (Gl < 1) Gl = 1;
     if ((int64_t)Gl * net.L * p.stride > (int64_t)wk.n_blocks * (128 * 128 + 128)) return cudaErrorInvalidValue;
     p.Gl = Gl;
-    k_tc_dw<NH><<<Gl * net.L, kThreads, smem, s>>>(p, (uint32_t)cols);
+    k_tc_dw<NH><<<Gl * net.L, kDwThreads, smem, s>>>(p, (uint32_t)cols);
     *Gl_out = Gl;
     *stride_out = p.stride;
+    for (int l = 0; l < net.L; ++l) pitch[l] = l == 0 ? pad16(net.in0) : NH;
     return cudaGetLastError();
 }
 
@@ -628,12 +728,12 @@ cudaError_t train_tc_forward(const TrainNet& net, int64_t B, TrainWork& wk, unsi
 }
 
 cudaError_t train_tc_backward(const TrainNet& net, int64_t B, TrainWork& wk, unsigned int* err, int* Gl, int* stride,
-                              cudaStream_t s)
+                              int* pitch, cudaStream_t s)
 {
     if (!train_tc_supported(net)) return cudaErrorInvalidValue;
-    if (net.H <= 32) return backward_nh<32>(net, B, wk, err, Gl, stride, s);
-    if (net.H <= 64) return backward_nh<64>(net, B, wk, err, Gl, stride, s);
-    return backward_nh<128>(net, B, wk, err, Gl, stride, s);
+    if (net.H <= 32) return backward_nh<32>(net, B, wk, err, Gl, stride, pitch, s);
+    if (net.H <= 64) return backward_nh<64>(net, B, wk, err, Gl, stride, pitch, s);
+    return backward_nh<128>(net, B, wk, err, Gl, stride, pitch, s);
 }
 
 }  // namespace ptk
