@@ -613,21 +613,41 @@ cudaError_t nif_loss_grad(const TrainNet& net, int64_t B, const float* uv, const
 // Radiance cache (Mueller et al. 2021, cited in Section 2.1)
 namespace {
 
-// query / record rows: 16 floats = x[3], wo[3], n[3], tp[3], L[3], slot or valid (bits)
-__global__ void k_cache_features(int64_t cap, const uint32_t* __restrict__ n_dev, const float* __restrict__ rows,
-                                 CacheBox box, float* __restrict__ X0)
+// query / record rows: 16 floats = x[3], wo[3], n[3], tp[3], L[3], slot or valid (bits).
+// A CTA of 128 threads encodes 32 rows into shared memory (thread = (row,
+// part): parts 0-2 one axis' 2J frequency features each, part 3 wo and n)
+// and writes them out as whole 512-byte rows, zero-padded to 128 columns.
+constexpr int kFeatRows = 32;
+__global__ void __launch_bounds__(128) k_cache_features(int64_t cap, const uint32_t* __restrict__ n_dev,
+                                                        const float* __restrict__ rows, CacheBox box,
+                                                        float* __restrict__ X0)
 {
+    __shared__ float4 tile4[kFeatRows * kD / 4];
+    float* tile = reinterpret_cast<float*>(tile4);
     const int64_t n = n_dev ? min((int64_t)*n_dev, cap) : cap;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float* q = rows + 16 * i;
-        float* row = X0 + i * kD;
-        int k = 0;
-        for (int a = 0; a < 3; ++a) {
-            cache_axis_features(q[a], box.lo[a], box.eh[a], box.el[a], box.J, row + k, 1, row + k + box.J, 1);
-            k += 2 * box.J;
+    const int r = threadIdx.x >> 2, part = threadIdx.x & 3;
+    for (int64_t base = (int64_t)blockIdx.x * kFeatRows; base < n; base += (int64_t)gridDim.x * kFeatRows) {
+        __syncthreads();   // the previous rows are written out
+        for (int i = threadIdx.x; i < kFeatRows * kD / 4; i += blockDim.x) tile4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        const int64_t i = base + r;
+        if (i < n) {
+            const float* q = rows + 16 * i;
+            float* row = tile + r * kD;
+            if (part < 3) {
+                cache_axis_features(q[part], box.lo[part], box.eh[part], box.el[part], box.J, row + 2 * box.J * part, 1,
+                                    row + 2 * box.J * part + box.J, 1);
+            } else {
+                for (int t = 0; t < 6; ++t) row[6 * box.J + t] = q[3 + t];
+            }
         }
-        for (int t = 0; t < 6; ++t) row[k + t] = q[3 + t];
-        for (int t = k + 6; t < kD; ++t) row[t] = 0.f;
+        __syncthreads();
+        // warp w writes rows w, w + 4, ...: one coalesced 512-byte row per step
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int rr = warp; rr < kFeatRows; rr += 4) {
+            const int64_t g = base + rr;
+            if (g < n && 4 * lane < kD) reinterpret_cast<float4*>(X0 + g * kD)[lane] = tile4[rr * (kD / 4) + lane];
+        }
     }
 }
 
@@ -661,7 +681,8 @@ cudaError_t cache_train_inputs(int64_t n, const float* rec, const float* slot_L,
                                int32_t* mask, cudaStream_t s)
 {
     const unsigned g = (unsigned)std::min<int64_t>((n + 127) / 128, 152 * 8);
-    k_cache_features<<<g, 128, 0, s>>>(n, nullptr, rec, box, X0);
+    k_cache_features<<<(unsigned)std::min<int64_t>((n + kFeatRows - 1) / kFeatRows, 152 * 16), 128, 0, s>>>(
+        n, nullptr, rec, box, X0);
     if (slot_L) k_cache_targets<<<g, 128, 0, s>>>(n, rec, slot_L, target, mask);
     return cudaGetLastError();
 }

@@ -6,9 +6,11 @@
 //   forward   X[l+1] = relu(X[l] W_l^T + b_l), l = 0 .. L-1.  A CTA holds
 //             every hidden layer's weights in shared memory and takes each
 //             128-row tile through all layers: the ReLU output of one layer,
-//             rounded to BF16, is the A operand of the next.
+//             rounded to BF16, is the A operand of the next.  Only X[L], the
+//             output layer's input, is written in FP32.
 //   backward  G[l-1] = (G[l] W_l) * [X[l] > 0], l = L-1 .. 1, chained the
-//             same way from the output layer's gradient G[L-1].
+//             same way from the output layer's gradient G[L-1]; the ReLU
+//             masks come from the BF16 tiles of X[l].
 //   weights   dW_l = G[l]^T X[l] and db_l = the column sums of G[l].  The
 //             batch is the reduction.  The two chains also write every BF16
 //             operand tile they build (X[0 .. L-1], G[0 .. L-1]) to HBM in
@@ -55,7 +57,7 @@ struct FwdParams {
     int64_t B;
     int L, in0, K0, H;
     const float* X0;
-    float* X[kMaxLayers + 1];        // X[1 .. L] written
+    float* XL;                       // X[L] (the output layer's input) written in FP32
     unsigned char* Xb[kMaxLayers];   // BF16 operand tiles of X[0 .. L-1] written
     const float* W[kMaxLayers];
     const float* b[kMaxLayers];
@@ -66,7 +68,8 @@ struct DxParams {
     int64_t B;
     int L, H;
     const float* Gtop;               // G[L-1]
-    const float* X[kMaxLayers];      // X[1 .. L-1]: the ReLU masks
+    const unsigned char* Xb[kMaxLayers];   // BF16 tiles of X[1 .. L-1]: the ReLU masks (BF16 > 0 iff FP32 > 0
+                                           // for every value above 2^-134)
     unsigned char* Gb[kMaxLayers];   // BF16 operand tiles of G[0 .. L-1] written
     const float* W[kMaxLayers];      // W[1 .. L-1]
     unsigned int* err;
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fwd(const FwdParams p)
             ok = wait_all(bs, bs.bar[0], ph, p.err);
             if (!ok) break;
             ph ^= 1;
-            float* dst = p.X[l + 1] + g * 128;
+            float* dst = p.XL + g * 128;
 #pragma unroll
             for (int cc = grp; cc < NH / 16; cc += kGroups) {
                 uint32_t r[16];
@@ -327,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fwd(const FwdParams p)
                     const int c = cc * 16 + e;
                     v[e] = c < p.H ? fmaxf(__uint_as_float(r[e]) + bias[l * NH + c], 0.f) : 0.f;
                 }
-                if (g < p.B) store16(dst + cc * 16, v);
+                if (l + 1 == L && g < p.B) store16(dst + cc * 16, v);
                 if (l + 1 < L) {
                     uint32_t w[8];
                     pack16(v, w);
@@ -395,15 +398,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_dx(const DxParams p)
                              plain_desc(w + ks * 2 * (NH * 16), NH * 16, 128), idesc, ks > 0);
                 mma_commit(bs.bar[0]);
             }
-            // the ReLU mask of this row while the MMA runs
-            float4 xm[kMine][4];
+            // the ReLU mask of this row (16 BF16 values per chunk) while the MMA runs
+            uint4 xm[kMine][2];
+            const unsigned char* xt = p.Xb[l] + (size_t)tile * kRows * NH * 2 + row * 16;
 #pragma unroll
             for (int i = 0; i < kMine; ++i) {
                 const int cc = grp + kGroups * i;
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    xm[i][u] = (g < p.B && cc < NH / 16) ? ld4(p.X[l] + g * 128 + cc * 16 + 4 * u)
-                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int u = 0; u < 2; ++u)
+                    xm[i][u] = cc < NH / 16 ? __ldg(reinterpret_cast<const uint4*>(xt + (size_t)(2 * cc + u) * kTileCb))
+                                            : make_uint4(0u, 0u, 0u, 0u);
             }
             ok = wait_all(bs, bs.bar[0], ph, p.err);
             if (!ok) break;
@@ -418,12 +422,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_dx(const DxParams p)
                 tmem_wait_ld();
                 float v[16];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float xs[4] = {xm[i][u].x, xm[i][u].y, xm[i][u].z, xm[i][u].w};
+                for (int u = 0; u < 2; ++u) {
+                    const uint32_t xw[4] = {xm[i][u].x, xm[i][u].y, xm[i][u].z, xm[i][u].w};
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int c = cc * 16 + 4 * u + e;
-                        v[4 * u + e] = (c < p.H && xs[e] > 0.f) ? __uint_as_float(r[4 * u + e]) : 0.f;
+                    for (int e = 0; e < 8; ++e) {
+                        const int c = cc * 16 + 8 * u + e;
+                        const float x = __uint_as_float((e & 1) ? (xw[e >> 1] & 0xFFFF0000u) : (xw[e >> 1] << 16));
+                        v[8 * u + e] = (c < p.H && x > 0.f) ? __uint_as_float(r[8 * u + e]) : 0.f;
                     }
                 }
                 uint32_t w[8];
@@ -628,7 +633,7 @@ cudaError_t forward_nh(const TrainNet& net, int64_t B, TrainWork& wk, unsigned i
     p.K0 = pad16(net.in0);
     p.H = net.H;
     p.X0 = wk.X[0];
-    for (int l = 1; l <= net.L; ++l) p.X[l] = wk.X[l];
+    p.XL = wk.X[net.L];
     for (int l = 0; l < net.L; ++l) {
         p.Xb[l] = wk.Xb[l];
         p.W[l] = net.W[l];
@@ -659,7 +664,7 @@ cudaError_t backward_nh(const TrainNet& net, int64_t B, TrainWork& wk, unsigned 
         p.H = net.H;
         p.Gtop = wk.dX[0];
         for (int l = 1; l < net.L; ++l) {
-            p.X[l] = wk.X[l];
+            p.Xb[l] = wk.Xb[l];
             p.W[l] = net.W[l];
         }
         for (int l = 0; l < net.L; ++l) p.Gb[l] = wk.Gb[l];

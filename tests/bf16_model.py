@@ -6,7 +6,7 @@ the difference is accumulation-order noise), everything else is FP64.
   forward   x[l+1] = relu(bf16(x[l]) bf16(W_l)^T + b_l)
   head      y = x[L] W_L^T + b_L in full precision, loss and dL/dy
   backward  G[L-1] = (dy W_L) * [x[L] > 0]
-            G[l-1] = (bf16(G[l]) bf16(W_l)) * [x[l] > 0]
+            G[l-1] = (bf16(G[l]) bf16(W_l)) * [bf16(x[l]) > 0]
   weights   dW_l = bf16(G[l])^T bf16(x[l]),  db_l = sum of bf16(G[l]) rows
 
 With rounding switched off (`rounding=False`) the model is plain FP64
@@ -88,6 +88,6 @@ def mlp_loss_grad(X0, Ws, bs, target, loss="huber", M=None, delta=1e-3, mask=Non
         Gb = _r(G, rounding)
         grads[l] = (Gb.T @ _r(xs[l], rounding), Gb.sum(0))
         if l > 0:
-            G = (Gb @ _r(Ws[l], rounding)) * (xs[l] > 0)
+            G = (Gb @ _r(Ws[l], rounding)) * (_r(xs[l], rounding) > 0)
     flat = np.concatenate([np.concatenate([gw.ravel(), gb.ravel()]) for gw, gb in grads])
     return total, flat
