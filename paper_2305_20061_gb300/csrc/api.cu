@@ -729,7 +729,7 @@ pt_status ensure_train(pt_ctx* ctx, pt_nif* nf, int64_t B)
     nf->d_work = nullptr;
     nf->d_batch = nullptr;
     const int G = 4 * ctx->sm_count;   // partial slots: up to four GEMM CTAs per SM
-    const size_t rows = (size_t)B * 128;
+    const size_t rows = (size_t)((B + 127) / 128) * 128 * 128;   // whole 128-row tiles (tiled layouts)
     // X[0 .. L], dX[2], BF16 operand tiles Xb[0 .. L-1] and Gb[0 .. L-1], partials, loss partials
     const size_t tiles = (size_t)((B + 127) / 128) * 128 * 128 * 2;
     const size_t bytes = (size_t)(nf->L + 3) * rows * sizeof(float) + 2 * (size_t)nf->L * tiles +
@@ -888,7 +888,7 @@ pt_status ensure_cache_train(pt_ctx* ctx, pt_cache* c, int64_t B)
     c->d_work = nullptr;
     c->work_cap = 0;
     const int G = 4 * ctx->sm_count;   // partial slots: up to four GEMM CTAs per SM
-    const size_t rows = (size_t)B * 128;
+    const size_t rows = (size_t)((B + 127) / 128) * 128 * 128;   // whole 128-row tiles (tiled layouts)
     // X[0 .. L], dX[2], BF16 operand tiles Xb[0 .. L-1] and Gb[0 .. L-1], partials, loss partials
     const size_t tiles = (size_t)((B + 127) / 128) * 128 * 128 * 2;
     const size_t bytes = (size_t)(c->L + 3) * rows * sizeof(float) + 2 * (size_t)c->L * tiles +

@@ -288,12 +288,20 @@ __global__ void __launch_bounds__(kT, 1) k_layer_bwd_dw(int64_t B, const float* 
 //   mode 0 (NIF): Huber(delta) between M y and the target (log space).
 //   mode 1 (radiance cache): relative L2, (y - t)^2 / (sg(y)^2 + 0.01), on
 //          the linear output; rows with mask == 0 contribute nothing.
+// X layout: rows of 128 floats, or (x_tiled) 128-row tiles of 128 x 128 floats
+// in which 16-byte groups of 4 columns of consecutive rows are contiguous
+// (element (r, c) of tile t at t * 16384 + (c >> 2) * 512 + r * 4 + (c & 3)).
+__device__ __forceinline__ int64_t x_off(int64_t g, int c, bool tiled)
+{
+    return tiled ? (g >> 7) * (kT * kD) + (int64_t)(c >> 2) * (kT * 4) + (g & (kT - 1)) * 4 + (c & 3) : g * kD + c;
+}
+
 __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __restrict__ X, const float* __restrict__ target,
                                                      const float* __restrict__ W4, const float* __restrict__ b4, int H,
                                                      const float* __restrict__ Mm, float delta, float inv_n,
                                                      float* __restrict__ dX, float* __restrict__ head_partial,
                                                      double* __restrict__ loss_partial, int mode,
-                                                     const int32_t* __restrict__ mask)
+                                                     const int32_t* __restrict__ mask, int x_tiled)
 {
     extern __shared__ float4 smem4[];
     float* Xs = reinterpret_cast<float*>(smem4);   // the tile's last hidden layer, [k][row]
@@ -311,7 +319,21 @@ __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __r
     const int64_t n_tiles = (B + kT - 1) / kT;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         __syncthreads();   // the previous tile's readers of Xs and dys are done
-        load_rows_transposed(Xs, X, tile, B, Kh);
+        if (x_tiled) {
+            const int r = threadIdx.x;
+            const int64_t gr = tile * kT + r;
+#pragma unroll 4
+            for (int q = 0; q < Kh / 4; ++q) {
+                const float4 v = gr < B ? *reinterpret_cast<const float4*>(X + x_off(gr, 4 * q, true))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+                Xs[(4 * q + 0) * kT + r] = v.x;
+                Xs[(4 * q + 1) * kT + r] = v.y;
+                Xs[(4 * q + 2) * kT + r] = v.z;
+                Xs[(4 * q + 3) * kT + r] = v.w;
+            }
+        } else {
+            load_rows_transposed(Xs, X, tile, B, Kh);
+        }
         __syncthreads();
         // thread = row: output, loss and dL/dy
         const int64_t g = tile * kT + threadIdx.x;
@@ -348,7 +370,8 @@ __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __r
 #pragma unroll 8
         for (int i = 0; i < rows; ++i) {
             const int64_t gi = tile * kT + i;
-            const float xv = X[gi * kD + k];
+            const float xv = k < Kh ? X[x_off(gi, k, x_tiled != 0)] : 0.f;   // columns >= Kh >= H enter neither
+                                                                              // dX nor the head gradient
             const float v = dys[i][0] * w0 + dys[i][1] * w1 + dys[i][2] * w2;
             dX[gi * kD + k] = (k < H && xv > 0.f) ? v : 0.f;
             gW[0] = fmaf(dys[i][0], xv, gW[0]);
@@ -525,14 +548,15 @@ namespace {
 // output layer, loss and the head's gradients (both precisions); writes the
 // gradient at the last hidden layer's pre-activation to dX_last
 cudaError_t head_loss(const TrainNet& net, int64_t B, const float* target, float delta, int mode, const int32_t* mask,
-                      TrainWork& wk, float* dX_last, double* loss_d, float* loss_f, cudaStream_t s)
+                      TrainWork& wk, float* dX_last, double* loss_d, float* loss_f, int x_tiled, cudaStream_t s)
 {
     cudaError_t e = set_smem((const void*)k_head_loss);
     if (e != cudaSuccess) return e;
     const size_t hsm = (size_t)pad_k(net.H) * kT * sizeof(float);
     const int Gh = grid_of(wk, B, (const void*)k_head_loss, hsm);
     k_head_loss<<<Gh, kT, hsm, s>>>(B, wk.X[net.L], target, net.W[net.L], net.b[net.L], net.H, net.M, delta,
-                                    1.f / (3.f * (float)B), dX_last, wk.partial, wk.loss_partial, mode, mask);
+                                    1.f / (3.f * (float)B), dX_last, wk.partial, wk.loss_partial, mode, mask,
+                                    x_tiled);
     k_sum_partials<<<(3 * net.H + 3 + 31) / 32, 256, 0, s>>>(wk.partial, Gh, 3 * kD + 3, kD, 3 * kD, net.H, 3,
                                                              net.gW[net.L], net.gb[net.L]);
     k_sum_loss<<<1, 32, 0, s>>>(wk.loss_partial, Gh, 1.0 / (3.0 * (double)B), loss_d, loss_f);
@@ -546,7 +570,7 @@ cudaError_t mlp_loss_grad_tc(const TrainNet& net, int64_t B, const float* target
 {
     cudaError_t e = train_tc_forward(net, B, wk, wk.err, s);
     if (e != cudaSuccess) return e;
-    e = head_loss(net, B, target, delta, mode, mask, wk, wk.dX[0], loss_d, loss_f, s);
+    e = head_loss(net, B, target, delta, mode, mask, wk, wk.dX[0], loss_d, loss_f, 1, s);
     if (e != cudaSuccess) return e;
     int Gl = 0, stride = 0, pitch[8] = {};
     e = train_tc_backward(net, B, wk, wk.err, &Gl, &stride, pitch, s);
@@ -582,7 +606,7 @@ cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, f
         layer_fwd(wk, B, wk.X[l], wk.X[l + 1], net.W[l], net.b[l], in, net.H, s);
     }
     // head + loss
-    e = head_loss(net, B, target, delta, mode, mask, wk, wk.dX[0], loss_d, loss_f, s);
+    e = head_loss(net, B, target, delta, mode, mask, wk, wk.dX[0], loss_d, loss_f, 0, s);
     if (e != cudaSuccess) return e;
     // backward through the hidden layers
     int cur = 0;

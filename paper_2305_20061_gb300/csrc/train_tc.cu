@@ -57,7 +57,8 @@ struct FwdParams {
     int64_t B;
     int L, in0, K0, H;
     const float* X0;
-    float* XL;                       // X[L] (the output layer's input) written in FP32
+    float* XL;                       // X[L] (the output layer's input) written in FP32, tiled: element (r, c)
+                                     // of tile t at t * 16384 + (c >> 2) * 512 + r * 4 + (c & 3)
     unsigned char* Xb[kMaxLayers];   // BF16 operand tiles of X[0 .. L-1] written
     const float* W[kMaxLayers];
     const float* b[kMaxLayers];
@@ -168,9 +169,10 @@ __device__ __forceinline__ float4 mask4(float4 v, int c, int width)
 }
 
 // This warp's 8 rows (8w .. 8w+7) of rows [tile*128, +128) of a [B][128]
-// FP32 matrix, columns 4l .. 4l+3 for lane l (one coalesced row per load);
-// columns >= width and rows >= B read as zeros.  Lanes with 4l >= K load
-// nothing.
+// FP32 matrix, columns 4l .. 4l+3 for lane l (one coalesced row per load).
+// Rows >= B and lanes with 4l >= min(K, width) load nothing (their values are
+// left as they are); nothing here waits for the loads, so the registers can
+// fill while the caller works on the previous tile.
 __device__ __forceinline__ void load_rows8(float4 (&v)[8], const float* __restrict__ X, int64_t tile, int64_t B,
                                            int width, int K)
 {
@@ -178,21 +180,24 @@ __device__ __forceinline__ void load_rows8(float4 (&v)[8], const float* __restri
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int64_t g = tile * kRows + warp * 8 + i;
-        v[i] = (c < K && g < B && c < width) ? mask4(ld4(X + g * 128 + c), c, width) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c < K && c < width && g < B) v[i] = ld4(X + g * 128 + c);
     }
 }
 
 // ... as BF16 into the activation tile: byte (r>>3)*128 + (c>>3)*kActLbo +
-// (r&7)*16 + (c&7)*2 (the A operand of the row GEMMs, K = columns)
-__device__ __forceinline__ void store_rows8(uint32_t a, const float4 (&v)[8], int K)
+// (r&7)*16 + (c&7)*2 (the A operand of the row GEMMs, K = columns); rows >= B
+// and columns >= width become zeros
+__device__ __forceinline__ void store_rows8(uint32_t a, const float4 (&v)[8], int64_t tile, int64_t B, int width,
+                                            int K)
 {
     const int warp = threadIdx.x >> 5, c = 4 * (threadIdx.x & 31);
     if (c >= K) return;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
+        const int64_t g = tile * kRows + warp * 8 + i;
+        const float4 x = (g < B && c < width) ? mask4(v[i], c, width) : make_float4(0.f, 0.f, 0.f, 0.f);
         const uint32_t addr = a + warp * 128 + (c >> 3) * kActLbo + i * 16 + (c & 7) * 2;
-        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(pack_bf16(v[i].x, v[i].y)),
-                     "r"(pack_bf16(v[i].z, v[i].w))
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(pack_bf16(x.x, x.y)), "r"(pack_bf16(x.z, x.w))
                      : "memory");
     }
 }
@@ -296,10 +301,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fwd(const FwdParams p)
     const int64_t n_tiles = (p.B + kRows - 1) / kRows;
     uint32_t ph = 0;
     bool ok = true;
-    float4 pf[8];   // the next tile's input rows, loaded while this tile runs through the layers
+    float4 pf[8] = {};   // the next tile's input rows, loaded while this tile runs through the layers
     load_rows8(pf, p.X0, blockIdx.x, p.B, p.in0, K0);
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        store_rows8(a, pf, K0);
+        store_rows8(a, pf, tile, p.B, p.in0, K0);
         fence_proxy_async();
         __syncthreads();
         if (tile + gridDim.x < n_tiles) load_rows8(pf, p.X0, tile + gridDim.x, p.B, p.in0, K0);
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fwd(const FwdParams p)
             ok = wait_all(bs, bs.bar[0], ph, p.err);
             if (!ok) break;
             ph ^= 1;
-            float* dst = p.XL + g * 128;
+            float* dst = p.XL + tile * (kRows * 128) + row * 4;
 #pragma unroll
             for (int cc = grp; cc < NH / 16; cc += kGroups) {
                 uint32_t r[16];
@@ -330,7 +335,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fwd(const FwdParams p)
                     const int c = cc * 16 + e;
                     v[e] = c < p.H ? fmaxf(__uint_as_float(r[e]) + bias[l * NH + c], 0.f) : 0.f;
                 }
-                if (l + 1 == L && g < p.B) store16(dst + cc * 16, v);
+                if (l + 1 == L && g < p.B) {
+                    // four 16-byte column groups; a warp's 32 rows of one group are 512 contiguous bytes
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        *reinterpret_cast<float4*>(dst + (cc * 4 + u) * (kRows * 4)) =
+                            make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+                }
                 if (l + 1 < L) {
                     uint32_t w[8];
                     pack16(v, w);
@@ -379,10 +390,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_dx(const DxParams p)
     const int64_t n_tiles = (p.B + kRows - 1) / kRows;
     uint32_t ph = 0;
     bool ok = true;
-    float4 pf[8];
+    float4 pf[8] = {};
     load_rows8(pf, p.Gtop, blockIdx.x, p.B, p.H, NH);
     for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        store_rows8(a, pf, NH);
+        store_rows8(a, pf, tile, p.B, p.H, NH);
         fence_proxy_async();
         __syncthreads();
         if (tile + gridDim.x < n_tiles) load_rows8(pf, p.Gtop, tile + gridDim.x, p.B, p.H, NH);
