@@ -51,7 +51,8 @@ typedef enum pt_status {
     PT_ENOMEM = 2,        /* host or device allocation failed */
     PT_ECUDA = 3,         /* a CUDA runtime call failed */
     PT_EDEVICE = 4,       /* a kernel set bits in the device error word */
-    PT_EUNSUPPORTED = 5   /* valid request this build does not implement */
+    PT_EUNSUPPORTED = 5,  /* valid request this build does not implement */
+    PT_EIO = 6            /* a checkpoint file could not be written, read or verified */
 } pt_status;
 
 /* arithmetic of the neural image field's hidden layers */
@@ -406,6 +407,49 @@ PT_API pt_status pt_render_cached(pt_ctx* ctx, const pt_scene* scene, const pt_n
    reported by the return code only. */
 PT_API pt_status pt_render_noalloc(const pt_scene* scene, const pt_nif* nif, const pt_render_cfg* cfg,
                                    float* d_image, uint32_t* d_err, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Checkpoints: the trained NIF (Section 3.2.1, weights saved after training */
+/* and loaded by the renderer) and per-frame snapshots of the radiance cache. */
+/* A checkpoint is one little-endian binary file:                           */
+/*   bytes  0-7   magic "PTCKPT01"                                           */
+/*          8-11  uint32 kind: 1 = NIF, 2 = radiance cache                   */
+/*         12-15  uint32 version (1)                                         */
+/*         16-31  int32 dims[4]: NIF (n_freq, hidden, n_hidden_layers, 0),   */
+/*                cache (n_freq, hidden, n_hidden_layers, 0)                 */
+/*         32-55  float box[6]: cache lo[3], hi[3]; zeros for a NIF          */
+/*         56-63  int64 n_params (the flat FP32 layout of pt_nif_desc /      */
+/*                pt_cache_desc)                                             */
+/*         64-71  int64 n_adam: entries of each Adam moment, 0 when training */
+/*                has not started (NIF: the trainable part; cache: all)      */
+/*         72-79  int64 adam_t: Adam steps taken (also the NIF's Philox     */
+/*                step counter)                                              */
+/*   then float params[n_params], float m[n_adam], float v[n_adam], and a   */
+/*   uint64 FNV-1a hash of every preceding byte.                             */
+/* Loading a checkpoint restores the object and its training state, so      */
+/* training resumed from it continues the run bit-exactly.                   */
+/* ------------------------------------------------------------------------ */
+typedef struct pt_checkpoint_info {
+    int32_t kind;              /* 1 NIF, 2 radiance cache */
+    int32_t version;
+    int32_t dims[4];
+    float lo[3], hi[3];        /* cache box (zeros for a NIF) */
+    int64_t n_params, n_adam, adam_t;
+} pt_checkpoint_info;
+
+/* Write `nif` (weights and, once training started, Adam state) to `path`.
+   Synchronises `stream` first; PT_EIO when the file cannot be written. */
+PT_API pt_status pt_save_nif(pt_ctx* ctx, const pt_nif* nif, const char* path, void* stream);
+/* Create a NIF from a checkpoint (as pt_load_nif, plus the training state).
+   PT_EIO for a missing, truncated or corrupted file (hash mismatch), PT_EINVAL
+   for a checkpoint of another kind or an unknown version. */
+PT_API pt_status pt_load_nif_file(pt_ctx* ctx, const char* path, pt_nif** out);
+/* The same for a radiance cache (pt_create_cache plus its training state). */
+PT_API pt_status pt_save_cache(pt_ctx* ctx, const pt_cache* cache, const char* path, void* stream);
+PT_API pt_status pt_load_cache_file(pt_ctx* ctx, const char* path, pt_cache** out);
+/* Read and verify a checkpoint's header and hash without a device or
+   context (host only). */
+PT_API pt_status pt_checkpoint_read_info(const char* path, pt_checkpoint_info* out);
 
 #ifdef __cplusplus
 }

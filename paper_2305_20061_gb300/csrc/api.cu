@@ -80,6 +80,7 @@ struct pt_cache {
     float* d_params = nullptr;      // flat FP32 weights (pt_cache_desc layout)
     unsigned char* d_tc = nullptr;  // BF16 tensor-core image (J = 12, H = 64, L = 5 only), follows d_params
     CacheBox box = {};
+    float box_lo[3] = {0, 0, 0}, box_hi[3] = {0, 0, 0};   // the box as given (checkpoints)
     // online training state
     float* d_grad = nullptr;
     float* d_m = nullptr;
@@ -967,6 +968,10 @@ PT_API pt_status pt_create_cache(pt_ctx* ctx, const pt_cache_desc* d, pt_cache**
     c->J = J; c->H = H; c->L = L; c->in0 = in0;
     c->n_params = np;
     c->box = box;
+    for (int a = 0; a < 3; ++a) {
+        c->box_lo[a] = d->lo[a];
+        c->box_hi[a] = d->hi[a];
+    }
     if (cudaMalloc((void**)&c->d_params, np * sizeof(float)) != cudaSuccess ||
         cudaMemcpy(c->d_params, d->params, np * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
         pt_destroy_cache(c);
@@ -1346,3 +1351,262 @@ PT_API pt_status pt_profile_read(pt_ctx* ctx, double* ms, int64_t* launches, int
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Checkpoints (format in pt.h)
+namespace {
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t kind, version;
+    int32_t dims[4];
+    float box[6];
+    int64_t n_params, n_adam, adam_t;
+};
+static_assert(sizeof(CkptHeader) == 80, "checkpoint header layout");
+constexpr char kCkptMagic[8] = {'P', 'T', 'C', 'K', 'P', 'T', '0', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+uint64_t fnv1a(uint64_t h, const void* data, size_t n)
+{
+    const unsigned char* p = static_cast<const unsigned char*>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+constexpr uint64_t kFnvBasis = 14695981039346656037ull;
+
+// header + host arrays -> file; false when any write fails
+bool write_ckpt(const char* path, const CkptHeader& hd, const std::vector<float>& params, const std::vector<float>& m,
+                const std::vector<float>& v)
+{
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return false;
+    uint64_t h = kFnvBasis;
+    bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1;
+    h = fnv1a(h, &hd, sizeof hd);
+    for (const std::vector<float>* a : {&params, &m, &v}) {
+        if (!ok || a->empty()) continue;
+        ok = std::fwrite(a->data(), sizeof(float), a->size(), f) == a->size();
+        h = fnv1a(h, a->data(), a->size() * sizeof(float));
+    }
+    ok = ok && std::fwrite(&h, sizeof h, 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok;
+}
+
+// file -> header + arrays, checked: magic, version, sizes against the file length, hash
+pt_status read_ckpt(pt_ctx* ctx, const char* path, CkptHeader& hd, std::vector<float>* params, std::vector<float>* m,
+                    std::vector<float>* v)
+{
+    if (!path) return fail(ctx, PT_EINVAL, "null path");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, PT_EIO, std::string("cannot open checkpoint ") + path);
+    std::fseek(f, 0, SEEK_END);
+    const long len = std::ftell(f);
+    std::fseek(f, 0, SEEK_SET);
+    if (len < (long)(sizeof hd + 8) || std::fread(&hd, sizeof hd, 1, f) != 1) {
+        std::fclose(f);
+        return fail(ctx, PT_EIO, "checkpoint truncated");
+    }
+    if (std::memcmp(hd.magic, kCkptMagic, 8) != 0) {
+        std::fclose(f);
+        return fail(ctx, PT_EIO, "not a checkpoint (magic)");
+    }
+    if (hd.version != kCkptVersion) {
+        std::fclose(f);
+        return fail(ctx, PT_EINVAL, "unknown checkpoint version");
+    }
+    if (hd.n_params < 1 || hd.n_adam < 0 || hd.n_params > ((int64_t)1 << 28) || hd.n_adam > hd.n_params ||
+        (long)(sizeof hd + 4 * (hd.n_params + 2 * hd.n_adam) + 8) != len) {
+        std::fclose(f);
+        return fail(ctx, PT_EIO, "checkpoint sizes do not match the file");
+    }
+    std::vector<float> P((size_t)hd.n_params), M((size_t)hd.n_adam), V((size_t)hd.n_adam);
+    uint64_t stored = 0;
+    bool ok = std::fread(P.data(), sizeof(float), P.size(), f) == P.size();
+    if (ok && hd.n_adam > 0) {
+        ok = std::fread(M.data(), sizeof(float), M.size(), f) == M.size() &&
+             std::fread(V.data(), sizeof(float), V.size(), f) == V.size();
+    }
+    ok = ok && std::fread(&stored, sizeof stored, 1, f) == 1;
+    std::fclose(f);
+    if (!ok) return fail(ctx, PT_EIO, "checkpoint truncated");
+    uint64_t h = fnv1a(kFnvBasis, &hd, sizeof hd);
+    h = fnv1a(h, P.data(), P.size() * sizeof(float));
+    h = fnv1a(h, M.data(), M.size() * sizeof(float));
+    h = fnv1a(h, V.data(), V.size() * sizeof(float));
+    if (h != stored) return fail(ctx, PT_EIO, "checkpoint hash mismatch (corrupted)");
+    if (params) *params = std::move(P);
+    if (m) *m = std::move(M);
+    if (v) *v = std::move(V);
+    return PT_OK;
+}
+
+pt_status download(pt_ctx* ctx, const float* d, int64_t n, std::vector<float>& out)
+{
+    out.resize((size_t)n);
+    if (n > 0) PT_CUDA(cudaMemcpy(out.data(), d, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost));
+    return PT_OK;
+}
+
+}  // namespace
+
+PT_API pt_status pt_checkpoint_read_info(const char* path, pt_checkpoint_info* out)
+{
+    if (!out) return PT_EINVAL;
+    CkptHeader hd = {};
+    const pt_status st = read_ckpt(nullptr, path, hd, nullptr, nullptr, nullptr);
+    if (st != PT_OK) return st;
+    *out = pt_checkpoint_info{};
+    out->kind = (int32_t)hd.kind;
+    out->version = (int32_t)hd.version;
+    for (int i = 0; i < 4; ++i) out->dims[i] = hd.dims[i];
+    for (int a = 0; a < 3; ++a) {
+        out->lo[a] = hd.box[a];
+        out->hi[a] = hd.box[3 + a];
+    }
+    out->n_params = hd.n_params;
+    out->n_adam = hd.n_adam;
+    out->adam_t = hd.adam_t;
+    return PT_OK;
+}
+
+PT_API pt_status pt_save_nif(pt_ctx* ctx, const pt_nif* nf, const char* path, void* stream)
+{
+    if (!ctx || !nf || !path) return fail(ctx, PT_EINVAL, "null argument");
+    PT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    CkptHeader hd = {};
+    std::memcpy(hd.magic, kCkptMagic, 8);
+    hd.kind = 1;
+    hd.version = kCkptVersion;
+    hd.dims[0] = nf->F;
+    hd.dims[1] = nf->H;
+    hd.dims[2] = nf->L;
+    hd.n_params = nf->n_params;
+    hd.n_adam = nf->d_m ? nf->n_trainable : 0;
+    hd.adam_t = nf->adam_t;
+    std::vector<float> P, M, V;
+    pt_status st = download(ctx, nf->d_params, nf->n_params, P);
+    if (st == PT_OK && hd.n_adam) st = download(ctx, nf->d_m, hd.n_adam, M);
+    if (st == PT_OK && hd.n_adam) st = download(ctx, nf->d_v, hd.n_adam, V);
+    if (st != PT_OK) return st;
+    if (!write_ckpt(path, hd, P, M, V)) return fail(ctx, PT_EIO, std::string("cannot write checkpoint ") + path);
+    return PT_OK;
+}
+
+PT_API pt_status pt_load_nif_file(pt_ctx* ctx, const char* path, pt_nif** out)
+{
+    if (!ctx || !out) return fail(ctx, PT_EINVAL, "null argument");
+    *out = nullptr;
+    CkptHeader hd = {};
+    std::vector<float> P, M, V;
+    pt_status st = read_ckpt(ctx, path, hd, &P, &M, &V);
+    if (st != PT_OK) return st;
+    if (hd.kind != 1) return fail(ctx, PT_EINVAL, "checkpoint is not a NIF");
+    pt_nif_desc d = {};
+    d.n_freq = hd.dims[0];
+    d.hidden = hd.dims[1];
+    d.n_hidden_layers = hd.dims[2];
+    d.params = P.data();
+    // the parameter count implied by the dimensions must be the file's before anything reads P
+    {
+        const int64_t F = d.n_freq, H = d.hidden, L = d.n_hidden_layers;
+        if (F < 1 || F > 64 || H < 1 || H > 128 || L < 1 || L > 8)
+            return fail(ctx, PT_EIO, "checkpoint dimensions out of range");
+        int64_t n = 2 * F + 9;
+        for (int64_t l = 0; l <= L; ++l) {
+            const int64_t in = l == 0 ? 2 * F : H, o = l == L ? 3 : H;
+            n += in * o + o;
+        }
+        if (n != hd.n_params || (hd.n_adam && hd.n_adam != n - 2 * F - 9))
+            return fail(ctx, PT_EIO, "checkpoint sizes do not match its dimensions");
+    }
+    pt_nif* nf = nullptr;
+    st = pt_load_nif(ctx, &d, &nf);
+    if (st != PT_OK) return st;
+    if (hd.n_adam) {
+        st = ensure_train(ctx, nf, 0);
+        if (st == PT_OK && (cudaMemcpy(nf->d_m, M.data(), M.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+                            cudaMemcpy(nf->d_v, V.data(), V.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess))
+            st = fail(ctx, PT_ECUDA, "training state upload failed");
+        if (st != PT_OK) {
+            pt_destroy_nif(nf);
+            return st;
+        }
+    }
+    nf->adam_t = hd.adam_t;
+    *out = nf;
+    return PT_OK;
+}
+
+PT_API pt_status pt_save_cache(pt_ctx* ctx, const pt_cache* c, const char* path, void* stream)
+{
+    if (!ctx || !c || !path) return fail(ctx, PT_EINVAL, "null argument");
+    PT_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    CkptHeader hd = {};
+    std::memcpy(hd.magic, kCkptMagic, 8);
+    hd.kind = 2;
+    hd.version = kCkptVersion;
+    hd.dims[0] = c->J;
+    hd.dims[1] = c->H;
+    hd.dims[2] = c->L;
+    for (int a = 0; a < 3; ++a) {
+        hd.box[a] = c->box_lo[a];
+        hd.box[3 + a] = c->box_hi[a];
+    }
+    hd.n_params = c->n_params;
+    hd.n_adam = c->d_m ? c->n_params : 0;
+    hd.adam_t = c->adam_t;
+    std::vector<float> P, M, V;
+    pt_status st = download(ctx, c->d_params, c->n_params, P);
+    if (st == PT_OK && hd.n_adam) st = download(ctx, c->d_m, hd.n_adam, M);
+    if (st == PT_OK && hd.n_adam) st = download(ctx, c->d_v, hd.n_adam, V);
+    if (st != PT_OK) return st;
+    if (!write_ckpt(path, hd, P, M, V)) return fail(ctx, PT_EIO, std::string("cannot write checkpoint ") + path);
+    return PT_OK;
+}
+
+PT_API pt_status pt_load_cache_file(pt_ctx* ctx, const char* path, pt_cache** out)
+{
+    if (!ctx || !out) return fail(ctx, PT_EINVAL, "null argument");
+    *out = nullptr;
+    CkptHeader hd = {};
+    std::vector<float> P, M, V;
+    pt_status st = read_ckpt(ctx, path, hd, &P, &M, &V);
+    if (st != PT_OK) return st;
+    if (hd.kind != 2) return fail(ctx, PT_EINVAL, "checkpoint is not a radiance cache");
+    pt_cache_desc d = {};
+    d.n_freq = hd.dims[0];
+    d.hidden = hd.dims[1];
+    d.n_hidden_layers = hd.dims[2];
+    d.params = P.data();
+    for (int a = 0; a < 3; ++a) {
+        d.lo[a] = hd.box[a];
+        d.hi[a] = hd.box[3 + a];
+    }
+    // the parameter count implied by the dimensions must be the file's before anything reads P
+    const int64_t J = d.n_freq, H = d.hidden, L = d.n_hidden_layers, in0 = 6 * J + 6;
+    if (J < 1 || J > 15 || H < 1 || H > 128 || L < 1 || L > 7 ||
+        in0 * H + H + (L - 1) * (H * H + H) + 3 * H + 3 != hd.n_params ||
+        (hd.n_adam && hd.n_adam != hd.n_params))
+        return fail(ctx, PT_EIO, "checkpoint sizes do not match its dimensions");
+    pt_cache* c = nullptr;
+    st = pt_create_cache(ctx, &d, &c);
+    if (st != PT_OK) return st;
+    if (hd.n_adam) {
+        st = ensure_cache_train(ctx, c, 0);
+        if (st == PT_OK && (cudaMemcpy(c->d_m, M.data(), M.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+                            cudaMemcpy(c->d_v, V.data(), V.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess))
+            st = fail(ctx, PT_ECUDA, "training state upload failed");
+        if (st != PT_OK) {
+            pt_destroy_cache(c);
+            return st;
+        }
+    }
+    c->adam_t = hd.adam_t;
+    *out = c;
+    return PT_OK;
+}

@@ -19,7 +19,7 @@ from . import inputs as I
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpt.so")
 
-PT_OK, PT_EINVAL, PT_ENOMEM, PT_ECUDA, PT_EDEVICE, PT_EUNSUPPORTED = range(6)
+PT_OK, PT_EINVAL, PT_ENOMEM, PT_ECUDA, PT_EDEVICE, PT_EUNSUPPORTED, PT_EIO = range(7)
 PT_FP32, PT_BF16, PT_FP8E4M3 = 0, 1, 2
 PRECISIONS = {"fp32": PT_FP32, "bf16": PT_BF16, "fp8": PT_FP8E4M3}
 ERR_BITS = {0x1: "stack_overflow", 0x2: "queue_overflow", 0x4: "nonfinite", 0x8: "timeout", 0x10: "iter_cap",
@@ -68,6 +68,11 @@ class CacheTrainCfg(C.Structure):
     _fields_ = [("width", I32), ("height", I32), ("n_train", I32), ("max_depth", I32), ("rec_vertex", I32),
                 ("seed", U32), ("frame", U32), ("precision", I32), ("lr", C.c_float), ("beta1", C.c_float),
                 ("beta2", C.c_float), ("eps", C.c_float), ("train_precision", I32)]
+
+
+class CheckpointInfo(C.Structure):
+    _fields_ = [("kind", I32), ("version", I32), ("dims", I32 * 4), ("lo", C.c_float * 3), ("hi", C.c_float * 3),
+                ("n_params", I64), ("n_adam", I64), ("adam_t", I64)]
 
 
 class PTError(RuntimeError):
@@ -123,6 +128,11 @@ def lib():
             "pt_cache_loss_grad": ([P, P, I64, P, P, P, I32, P, P, P], I32),
             "pt_train_cache": ([P, P, P, P, P, P, P], I32),
             "pt_render_cached": ([P, P, P, P, I32, I32, P, I64, P, P, P, P, P, P], I32),
+            "pt_save_nif": ([P, P, C.c_char_p, P], I32),
+            "pt_load_nif_file": ([P, C.c_char_p, P], I32),
+            "pt_save_cache": ([P, P, C.c_char_p, P], I32),
+            "pt_load_cache_file": ([P, C.c_char_p, P], I32),
+            "pt_checkpoint_read_info": ([C.c_char_p, P], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -237,8 +247,34 @@ def nif_flat(nif: I.NIF) -> np.ndarray:
     return np.ascontiguousarray(np.concatenate(parts).astype(np.float32))
 
 
+def nif_from_flat(F: int, H: int, L: int, flat: np.ndarray) -> I.NIF:
+    """Inverse of nif_flat for a NIF of n_freq F, hidden width H and L hidden layers."""
+    p = 0
+    B = flat[p:p + 2 * F].reshape(F, 2).copy()
+    p += 2 * F
+    Ws, bs = [], []
+    for l in range(L + 1):
+        i, o = (2 * F if l == 0 else H), (3 if l == L else H)
+        Ws.append(flat[p:p + i * o].reshape(o, i).copy())
+        p += i * o
+        bs.append(flat[p:p + o].copy())
+        p += o
+    return I.NIF(B, Ws, bs, flat[p:p + 9].reshape(3, 3).copy())
+
+
+def checkpoint_info(path: str) -> dict:
+    """pt_checkpoint_read_info: header of a verified checkpoint file (no device needed)."""
+    inf = CheckpointInfo()
+    st = lib().pt_checkpoint_read_info(os.fsencode(path), C.byref(inf))
+    if st != PT_OK:
+        raise PTError(st, f"checkpoint {path} unreadable")
+    return {"kind": {1: "nif", 2: "cache"}.get(inf.kind, inf.kind), "version": inf.version, "dims": list(inf.dims),
+            "lo": list(inf.lo), "hi": list(inf.hi), "n_params": inf.n_params, "n_adam": inf.n_adam,
+            "adam_t": inf.adam_t}
+
+
 class Nif:
-    """pt_load_nif from an inputs.NIF."""
+    """pt_load_nif from an inputs.NIF (or Nif.load from a checkpoint file)."""
 
     def __init__(self, ctx: Context, nif: I.NIF):
         self.ctx = ctx
@@ -247,6 +283,21 @@ class Nif:
         d = NifDesc(nif.n_freq, nif.hidden, nif.n_hidden_layers, _np_ptr(flat))
         self.h = P()
         ctx._raise(lib().pt_load_nif(ctx.h, C.byref(d), C.byref(self.h)))
+
+    @classmethod
+    def load(cls, ctx: Context, path: str) -> "Nif":
+        """pt_load_nif_file: weights and training state from a checkpoint."""
+        self = cls.__new__(cls)
+        self.ctx = ctx
+        self.h = P()
+        ctx._raise(lib().pt_load_nif_file(ctx.h, os.fsencode(path), C.byref(self.h)))
+        F, H, L = checkpoint_info(path)["dims"][:3]
+        self.src = nif_from_flat(F, H, L, self.get_params())
+        return self
+
+    def save(self, path: str, stream=None) -> None:
+        """pt_save_nif: weights and (once training started) Adam state to a checkpoint file."""
+        self.ctx._raise(lib().pt_save_nif(self.ctx.h, self.h, os.fsencode(path), _stream(stream)))
 
     @property
     def param_count(self) -> int:
@@ -312,7 +363,7 @@ def cache_flat(cache: I.CacheNet) -> np.ndarray:
 
 
 class Cache:
-    """pt_create_cache from an inputs.CacheNet."""
+    """pt_create_cache from an inputs.CacheNet (or Cache.load from a checkpoint file)."""
 
     def __init__(self, ctx: Context, cache: I.CacheNet):
         self.ctx = ctx
@@ -324,6 +375,30 @@ class Cache:
             d.hi[a] = float(cache.hi[a])
         self.h = P()
         ctx._raise(lib().pt_create_cache(ctx.h, C.byref(d), C.byref(self.h)))
+
+    @classmethod
+    def load(cls, ctx: Context, path: str) -> "Cache":
+        """pt_load_cache_file: weights, box and training state from a checkpoint (a per-frame snapshot)."""
+        self = cls.__new__(cls)
+        self.ctx = ctx
+        self.h = P()
+        ctx._raise(lib().pt_load_cache_file(ctx.h, os.fsencode(path), C.byref(self.h)))
+        info = checkpoint_info(path)
+        J, H, L = info["dims"][:3]
+        flat = self.get_params()
+        Ws, bs, p = [], [], 0
+        for l in range(L + 1):
+            i, o = (6 * J + 6 if l == 0 else H), (3 if l == L else H)
+            Ws.append(flat[p:p + i * o].reshape(o, i).copy())
+            p += i * o
+            bs.append(flat[p:p + o].copy())
+            p += o
+        self.src = I.CacheNet(J, Ws, bs, np.array(info["lo"], np.float32), np.array(info["hi"], np.float32))
+        return self
+
+    def save(self, path: str, stream=None) -> None:
+        """pt_save_cache: weights, box and (once training started) Adam state to a checkpoint file."""
+        self.ctx._raise(lib().pt_save_cache(self.ctx.h, self.h, os.fsencode(path), _stream(stream)))
 
     @property
     def param_count(self) -> int:
