@@ -451,6 +451,15 @@ PT_API pt_status pt_load_cache_file(pt_ctx* ctx, const char* path, pt_cache** ou
    context (host only). */
 PT_API pt_status pt_checkpoint_read_info(const char* path, pt_checkpoint_info* out);
 
+/* Failure-path self-test of the device waits (no fault involved): one CTA
+   waits, with the same bounded mbarrier wait the tensor-core kernels use, on
+   a barrier nothing arrives on.  After `seconds` (0 < seconds <= 2) the wait
+   gives up, sets PT_ERR_TIMEOUT in the context's error word (reported by the
+   next pt_check) and the kernel returns; the context stays usable.
+   *waited_s (nullable) receives the time the device waited.  Synchronises
+   `stream`. */
+PT_API pt_status pt_selftest_wait_timeout(pt_ctx* ctx, double seconds, double* waited_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -113,12 +113,17 @@ constexpr int kWorkBase = kMaxDepth + 1;
 pt_status fail(pt_ctx* ctx, pt_status st, const std::string& msg)
 {
     if (ctx) ctx->last_error = msg;
+    // a failed allocation leaves its (non-sticky) error pending in the runtime, where the next call's launch
+    // check would report it: consume it here
+    if (st == PT_ENOMEM) (void)cudaGetLastError();
     return st;
 }
 
 pt_status cuda_fail(pt_ctx* ctx, cudaError_t e, const char* what)
 {
-    return fail(ctx, PT_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    (void)cudaGetLastError();   // consume a non-sticky error so that it is not reported again by the next call
+    return fail(ctx, e == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
 }
 
 #define PT_CUDA(call)                                      \
@@ -1608,5 +1613,24 @@ PT_API pt_status pt_load_cache_file(pt_ctx* ctx, const char* path, pt_cache** ou
     }
     c->adam_t = hd.adam_t;
     *out = c;
+    return PT_OK;
+}
+
+// ---------------------------------------------------------------------------
+PT_API pt_status pt_selftest_wait_timeout(pt_ctx* ctx, double seconds, double* waited_s, void* stream)
+{
+    if (!ctx) return PT_EINVAL;
+    if (!(seconds > 0.0 && seconds <= 2.0)) return fail(ctx, PT_EINVAL, "seconds must be in (0, 2]");
+    PT_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t* d_waited = nullptr;
+    PT_CUDA(cudaMalloc((void**)&d_waited, sizeof(uint64_t)));
+    cudaError_t e = wait_selftest(ctx->d_err, (uint64_t)(seconds * 1e9), d_waited, s);
+    uint64_t waited = 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&waited, d_waited, sizeof waited, cudaMemcpyDeviceToHost);
+    cudaFree(d_waited);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "wait self-test");
+    if (waited_s) *waited_s = (double)waited * 1e-9;
     return PT_OK;
 }

@@ -189,6 +189,9 @@ cudaError_t adam_step(int64_t n, float* w, const float* g, float* m, float* v, f
 cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, float delta, int mode,
                           const int32_t* mask, int precision, TrainWork& wk, double* loss_d, float* loss_f,
                           cudaStream_t s);
+// self-test of the bounded device wait (selftest.cu): waits on a barrier nothing arrives on for budget_ns,
+// then sets PT_ERR_TIMEOUT in *err; *d_waited_ns receives the time waited
+cudaError_t wait_selftest(uint32_t* err, uint64_t budget_ns, uint64_t* d_waited_ns, cudaStream_t s);
 // tensor-core GEMMs of training (train_tc.cu): forward X[0] -> X[1..L] (and BF16 tiles Xb); backward from
 // G[L-1] = dX[0] -> BF16 tiles Gb and per-CTA partials of every layer's dW / db (Gl CTAs per layer, stride
 // floats each, layer l's at partial + l * Gl * stride: [H][pitch[l]] dW then [H] db)

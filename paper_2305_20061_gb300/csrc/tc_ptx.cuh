@@ -74,20 +74,26 @@ __device__ __forceinline__ uint64_t global_ns()
 constexpr uint64_t kWaitBudgetNs = 2000000000ull;  // 2 s per wait
 constexpr uint32_t kSleepHintNs = 20000;            // suspend-time hint of a blocked wait
 
-// Bounded wait for `parity` on an mbarrier; false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t* err)
+// Bounded wait for `parity` on an mbarrier: false on abort, or after
+// budget_ns with PT_ERR_TIMEOUT set in *err and the abort flag raised.
+__device__ __forceinline__ bool mbar_wait_budget(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t* err,
+                                                 uint64_t budget_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
         if (mbar_try_wait_sleep(bar, parity, kSleepHintNs)) return true;
         if (*abort) return false;
-        if (global_ns() - t0 > kWaitBudgetNs) {
+        if (global_ns() - t0 > budget_ns) {
             atomicOr(err, PT_ERR_TIMEOUT);
             *abort = 1;
             return false;
         }
     }
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint32_t* err)
+{
+    return mbar_wait_budget(bar, parity, abort, err, kWaitBudgetNs);
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }

@@ -133,6 +133,7 @@ def lib():
             "pt_save_cache": ([P, P, C.c_char_p, P], I32),
             "pt_load_cache_file": ([P, C.c_char_p, P], I32),
             "pt_checkpoint_read_info": ([C.c_char_p, P], I32),
+            "pt_selftest_wait_timeout": ([P, C.c_double, P, P], I32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -183,6 +184,13 @@ class Context:
             names = [n for b, n in ERR_BITS.items() if bits.value & b]
             raise PTError(st, "device error bits " + ",".join(names), bits.value)
         return bits.value
+
+    def selftest_wait_timeout(self, seconds: float = 0.05, stream=None) -> float:
+        """pt_selftest_wait_timeout: a bounded device wait that nothing satisfies gives up after `seconds` and
+        sets PT_ERR_TIMEOUT (read by the next check()); returns the time the device waited."""
+        waited = C.c_double(0.0)
+        self._raise(lib().pt_selftest_wait_timeout(self.h, float(seconds), C.byref(waited), _stream(stream)))
+        return waited.value
 
     def close(self):
         if self.h:
