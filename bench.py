@@ -203,6 +203,25 @@ def bench_reference(args):
     return 0
 
 
+def nif_quality(gnif, sky, dev):
+    """Trained-NIF quality against the HDR sky at all of its pixel centres:
+    log-RMSE (natural log, per channel) and PSNR of the Reinhard-tonemapped
+    x / (1 + x) images (peak 1), for FP32 and BF16 evaluation."""
+    import torch
+    h, w = sky.shape[0], sky.shape[1]
+    jj, ii = torch.meshgrid(torch.arange(h, device=dev), torch.arange(w, device=dev), indexing="ij")
+    uv = torch.stack([(ii.reshape(-1) + 0.5) / w, (jj.reshape(-1) + 0.5) / h], 1).float().contiguous()
+    ref = sky.reshape(-1, 3).double()
+    out = {"grid": f"{w}x{h} pixel centres"}
+    for prec in ("fp32", "bf16"):
+        y = gnif.eval(uv, prec).double()
+        lr = torch.sqrt(torch.mean((torch.log(torch.clamp(y, min=1e-6)) - torch.log(torch.clamp(ref, min=1e-6))) ** 2))
+        mse = torch.mean((y / (1 + y) - ref / (1 + ref)) ** 2)
+        out[f"log_rmse_{prec}"] = float(lr)
+        out[f"psnr_tonemapped_{prec}"] = float(10 * torch.log10(1.0 / mse))
+    return out
+
+
 def train_env_nif(pt, ctx, gnif, nif, steps, dev, precision):
     """Train the environment NIF on the procedural 2048 x 1024 HDR sky (not
     timed as a frame) with the given GEMM precision; copies the trained
@@ -224,6 +243,7 @@ def train_env_nif(pt, ctx, gnif, nif, steps, dev, precision):
              "samples_per_s": steps * batch / (tms * 1e-3),
              "fwd_bwd_tflops": steps * batch * 3 * FLOP_PER_EVAL / (tms * 1e-3) / 1e12,
              "loss_first": float(losses[0].item()), "loss_last": float(losses[-50:].mean().item())}
+    train["quality"] = nif_quality(gnif, sky, dev)
     del sky
     params = gnif.get_params()
     p = 2 * nif.n_freq
