@@ -3,10 +3,13 @@
 // targets, Huber loss, backpropagation and Adam, all in hand-written CUDA.
 //
 // Layers are padded to 128 x 128.  Activations are kept in HBM as [sample]
-// [128] FP32 rows.  Every GEMM is a 128-row tile times a 128 x 128 matrix
-// staged in shared memory with a 4 x 32 register tile per thread; weight
-// gradients are split over the batch into one partial per CTA and summed in a
-// fixed order, so a training step is deterministic.  The loss is summed in
+// [128] FP32 rows.  With FP32 GEMMs (this file) every GEMM is a 128-row tile
+// times a 128 x 128 matrix staged in shared memory with a 4 x 32 register
+// tile per thread; with BF16 GEMMs the forward, input-gradient and weight-
+// gradient GEMMs run on the tensor cores (train_tc.cu) and only the output
+// layer, the loss, the partial sums and Adam run here.  Either way weight
+// gradients are split over the batch into one partial per CTA and summed in
+// a fixed order, so a training step is deterministic.  The loss is summed in
 // FP64.
 #include <algorithm>
 #include <cstdint>
