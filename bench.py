@@ -203,6 +203,22 @@ def bench_reference(args):
     return 0
 
 
+def profiled_split(pt, ctx, run_frame, steps, n_prof=3):
+    """Per-kernel-kind device time and launch counts of `steps` frames, from
+    n_prof extra frames run with per-launch CUDA events (the library then
+    launches directly instead of replaying its graphs), scaled to `steps`."""
+    import torch
+    n_prof = max(1, min(steps, n_prof))
+    pt.profile_enable(ctx, True)
+    pt.profile_read(ctx)
+    for i in range(n_prof):
+        run_frame(i)
+    torch.cuda.synchronize()
+    raw = pt.profile_read(ctx)
+    pt.profile_enable(ctx, False)
+    return {k: (v[0] * steps / n_prof, int(round(v[1] * steps / n_prof))) for k, v in raw.items()}
+
+
 def nif_quality(gnif, sky, dev):
     """Trained-NIF quality against the HDR sky at all of its pixel centres:
     log-RMSE (natural log, per channel) and PSNR of the Reinhard-tonemapped
@@ -298,22 +314,18 @@ def bench_ours(args):
         for _ in range(args.warmup):
             pt.render(ctx, scene, gnif, cfg, prec, out=img, first_sample=first_sample)
         ctx.check()
-        if profile:
-            pt.profile_enable(ctx, True)
-            pt.profile_read(ctx)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier()
         for i in range(steps):
             flush.fill_(float(i))           # evict L2 between timed steps (not timed)
             ev[i][0].record(stream)
-            pt.render(ctx, scene, gnif, cfg, prec, out=img, first_sample=first_sample)
+            pt.render(ctx, scene, gnif, cfg, prec, out=img, first_sample=first_sample)   # a CUDA-graph replay
             ev[i][1].record(stream)
         barrier()
-        prof = pt.profile_read(ctx) if profile else None
-        if profile:
-            pt.profile_enable(ctx, False)
         ctx.check()
         ms = R.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, dev)
+        prof = profiled_split(pt, ctx, lambda i: pt.render(ctx, scene, gnif, cfg, prec, out=img,
+                                                           first_sample=first_sample), steps) if profile else None
         return ms, prof
 
     sampler = ClockSampler(local)
@@ -581,22 +593,25 @@ def bench_c5(args):
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    pt.profile_enable(ctx, True)
-    pt.profile_read(ctx)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     for i in range(args.steps):
         flush.fill_(float(i))           # evict L2 between timed frames (not timed)
         ev[i][0].record(stream)
-        frame(args.warmup + i)
+        frame(args.warmup + i)          # renders replay the library's CUDA graphs
         ev[i][1].record(stream)
     barrier()
-    prof = pt.profile_read(ctx)
     clocks = sampler.stop()
     ctx.check()
     ms = R.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / args.steps, dev)
     value = world * cfg.n_slots / (ms * 1e-3) / 1e6
     n_done = args.warmup + args.steps
+    # per-kernel split from three more frames with per-launch events, scaled to the timed frames
+    n_prof = min(args.steps, 3)
+    prof = profiled_split(pt, ctx, lambda i: frame(n_done + i), args.steps, n_prof)
+    n_done += n_prof
+    pt.profile_enable(ctx, True)
+    pt.profile_read(ctx)
 
     # split of one more frame: the training step, then the cached render alone
     gc.train_frame(scene, gnif, W, H, n_done * world + rank, n_train=N_TRAIN, max_depth=cfg.max_depth,

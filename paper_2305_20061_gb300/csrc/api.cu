@@ -3,6 +3,7 @@
 // alternates traversal-and-shading steps with batched NIF evaluation
 // (Section 3.3).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -37,10 +38,22 @@ struct pt_ctx {
     std::vector<cudaEvent_t> prof_ev;      // pairs: start, stop
     std::vector<int> prof_kind;
     size_t prof_used = 0;
+    // CUDA graphs of render launch sequences (replayed when a render repeats with the same buffers)
+    uint64_t scratch_gen = 0;              // bumped whenever a scratch buffer moves
+    uint32_t* d_first_sample = nullptr;    // the sample offset the bounce kernels read
+    cudaStream_t cap_stream = nullptr;     // capture stream (captures record, nothing runs on it)
+    std::vector<std::pair<std::vector<unsigned char>, cudaGraphExec_t>> graphs;
+    size_t graph_next = 0;
+    std::vector<std::vector<unsigned char>> graph_seen;   // keys seen once (captured on their second use)
+    size_t seen_next = 0;
 };
+
+// identities that are never reused (a graph key must not match a new object at a recycled address)
+std::atomic<uint64_t> g_next_uid{1};
 
 struct pt_scene {
     pt_ctx* ctx = nullptr;
+    uint64_t uid = g_next_uid++;
     DevScene dev = {};
     pt_scene_info info = {};
     std::vector<void*> allocs;
@@ -48,6 +61,8 @@ struct pt_scene {
 
 struct pt_nif {
     pt_ctx* ctx = nullptr;
+    uint64_t uid = g_next_uid++;
+    uint64_t version = 0;        // bumped when host-side copies (colour matrix) change
     int32_t F = 0, H = 0, L = 0;
     int64_t n_params = 0;
     float* d_params = nullptr;   // flat FP32 master weights
@@ -75,6 +90,7 @@ struct pt_nif {
 
 struct pt_cache {
     pt_ctx* ctx = nullptr;
+    uint64_t uid = g_next_uid++;
     int32_t J = 0, H = 0, L = 0, in0 = 0;
     int64_t n_params = 0;
     float* d_params = nullptr;      // flat FP32 weights (pt_cache_desc layout)
@@ -169,6 +185,7 @@ pt_status ensure_scratch(pt_ctx* ctx, uint32_t chunk)
         return fail(ctx, PT_ENOMEM, "escape queue allocation failed");
     }
     ctx->chunk_cap = chunk;
+    ++ctx->scratch_gen;
     return PT_OK;
 }
 
@@ -317,10 +334,12 @@ PT_API pt_status pt_create(pt_ctx** out, int device)
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->counters, kCounters * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->stats, kStats * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, kStats * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_first_sample, sizeof(uint32_t));
     if (e != cudaSuccess) {
         cudaFree(ctx->d_err);
         cudaFree(ctx->counters);
         cudaFree(ctx->stats);
+        cudaFree(ctx->d_first_sample);
         delete ctx;
         return PT_ECUDA;
     }
@@ -334,9 +353,12 @@ PT_API void pt_destroy(pt_ctx* ctx)
     cudaSetDevice(ctx->device);
     free_scratch(ctx);
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.second);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     cudaFree(ctx->d_err);
     cudaFree(ctx->counters);
     cudaFree(ctx->stats);
+    cudaFree(ctx->d_first_sample);
     delete ctx;
 }
 
@@ -843,6 +865,7 @@ PT_API pt_status pt_nif_fp8_scales(const pt_nif* nf, float* scales)
 
 PT_API pt_status pt_nif_set_params(pt_ctx* ctx, pt_nif* nf, const float* params, void* stream)
 {
+    if (nf) ++nf->version;   // host-side copies (the colour matrix) may change
     if (!ctx || !nf || !params) return fail(ctx, PT_EINVAL, "bad argument");
     if (!finite3(params, nf->n_params)) return fail(ctx, PT_EINVAL, "non-finite NIF parameters");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1135,37 +1158,15 @@ PT_API pt_status pt_train_cache(pt_ctx* ctx, const pt_scene* sc, const pt_nif* n
 // the training paths of pt_train_cache.  first_sample is the Philox sample
 // index of the first path per pixel; cache (nullable) ends paths at
 // cache_vertex; rec_vertex > 0 writes vertex records to d_rec.
-static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
-                             uint32_t first_sample, const pt_cache* cache, int cache_vertex, int rec_vertex, float* d_rec,
-                             int64_t n_pix, const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb,
-                             int32_t* d_hit_ids, cudaStream_t s)
+// The launch sequence of one render (no host synchronisation, no allocation):
+// recorded once into a CUDA graph and replayed when the same render repeats.
+static pt_status render_launches(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
+                                 const pt_cache* cache, int cache_vertex, int rec_vertex, float* d_rec, int64_t n_pix,
+                                 const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb, int32_t* d_hit_ids,
+                                 int64_t n_slots, int64_t chunk, cudaStream_t s)
 {
     pt_status st = PT_OK;
-    const int64_t WH = (int64_t)cfg->width * cfg->height;
-    if (!d_pixels) n_pix = WH;
-    if (n_pix < 0 || (n_pix > 0 && !d_pixel_rgb)) return fail(ctx, PT_EINVAL, "bad pixel list or output");
-    if (n_pix == 0) return PT_OK;
-    const int64_t n_slots = n_pix * (int64_t)cfg->spp;
-    if (n_slots > 0xFFFFFFFFll) return fail(ctx, PT_EINVAL, "more than 2^32 - 1 paths in one call");
-    if (sc->dev.env_is_nif && cfg->precision != PT_FP32 && !(cfg->precision == PT_BF16 && nf->d_tc) &&
-        !(cfg->precision == PT_FP8E4M3 && nf->fp8_ok))
-        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3");
-    // chunk = whole samples
-    int64_t chunk = cfg->chunk_slots > 0 ? cfg->chunk_slots : (int64_t)1 << 24;
-    chunk = std::max<int64_t>(n_pix, (chunk / n_pix) * n_pix);
-    chunk = std::min(chunk, n_slots);
-    if (chunk > 0x7FFFFFFFll) chunk = (0x7FFFFFFFll / n_pix) * n_pix;
-    st = ensure_scratch(ctx, (uint32_t)chunk);
-    if (st != PT_OK) return st;
-    if (cache && ctx->cache_cap < (uint32_t)chunk) {
-        cudaFree(ctx->cache_rows);
-        ctx->cache_rows = nullptr;
-        ctx->cache_cap = 0;
-        if (dalloc(&ctx->cache_rows, (size_t)chunk * 16)) return fail(ctx, PT_ENOMEM, "cache query rows allocation failed");
-        ctx->cache_cap = (uint32_t)chunk;
-    }
     if (rec_vertex > 0) PT_CUDA(cudaMemsetAsync(d_rec, 0, (size_t)n_slots * 16 * sizeof(float), s));
-    ctx->last_depth = cfg->max_depth;
     PT_CUDA(cudaMemsetAsync(ctx->stats, 0, kStats * sizeof(unsigned long long), s));
     if (d_hit_ids) PT_CUDA(launch_fill_i32(d_hit_ids, n_slots * cfg->max_depth, -2, s));
 
@@ -1176,7 +1177,8 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
     bp.rr = cfg->rr;
     bp.rr_start = cfg->rr_start;
     bp.seed = cfg->seed;
-    bp.first_sample = first_sample;
+    bp.first_sample = 0;
+    bp.first_sample_dev = ctx->d_first_sample;   // written before the sequence runs
     bp.n_pix = (uint32_t)n_pix;
     bp.pixels = d_pixels;
     bp.W = cfg->width;
@@ -1240,6 +1242,120 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
     }
     return PT_OK;
 }
+
+
+// Key of a captured render: every value the launch sequence bakes into kernel
+// parameters (object identities, configuration, buffers, scratch generation).
+// The sample offset is not in it: it is a device word written per call.
+struct GraphKey {
+    uint64_t sc_uid, nf_uid, nf_version, cache_uid, scratch_gen;
+    int32_t width, height, spp, max_depth, rr, rr_start, precision, cache_vertex, rec_vertex;
+    uint32_t seed, cache_cap;
+    int64_t chunk, n_pix;
+    const void* ptrs[5];   // d_rec, d_pixels, d_pixel_rgb, d_slot_rgb, d_hit_ids
+};
+constexpr size_t kMaxGraphs = 8;
+
+static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
+                             uint32_t first_sample, const pt_cache* cache, int cache_vertex, int rec_vertex, float* d_rec,
+                             int64_t n_pix, const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb,
+                             int32_t* d_hit_ids, cudaStream_t s)
+{
+    pt_status st = PT_OK;
+    const int64_t WH = (int64_t)cfg->width * cfg->height;
+    if (!d_pixels) n_pix = WH;
+    if (n_pix < 0 || (n_pix > 0 && !d_pixel_rgb)) return fail(ctx, PT_EINVAL, "bad pixel list or output");
+    if (n_pix == 0) return PT_OK;
+    const int64_t n_slots = n_pix * (int64_t)cfg->spp;
+    if (n_slots > 0xFFFFFFFFll) return fail(ctx, PT_EINVAL, "more than 2^32 - 1 paths in one call");
+    if (sc->dev.env_is_nif && cfg->precision != PT_FP32 && !(cfg->precision == PT_BF16 && nf->d_tc) &&
+        !(cfg->precision == PT_FP8E4M3 && nf->fp8_ok))
+        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3");
+    // chunk = whole samples
+    int64_t chunk = cfg->chunk_slots > 0 ? cfg->chunk_slots : (int64_t)1 << 24;
+    chunk = std::max<int64_t>(n_pix, (chunk / n_pix) * n_pix);
+    chunk = std::min(chunk, n_slots);
+    if (chunk > 0x7FFFFFFFll) chunk = (0x7FFFFFFFll / n_pix) * n_pix;
+    st = ensure_scratch(ctx, (uint32_t)chunk);
+    if (st != PT_OK) return st;
+    if (cache && ctx->cache_cap < (uint32_t)chunk) {
+        cudaFree(ctx->cache_rows);
+        ctx->cache_rows = nullptr;
+        ctx->cache_cap = 0;
+        if (dalloc(&ctx->cache_rows, (size_t)chunk * 16)) return fail(ctx, PT_ENOMEM, "cache query rows allocation failed");
+        ctx->cache_cap = (uint32_t)chunk;
+        ++ctx->scratch_gen;
+    }
+    // host-side work a launch might otherwise do (the lazy FP8 image) happens before any capture
+    if (sc->dev.env_is_nif && cfg->precision == PT_FP8E4M3 && nf->fp8_ok) {
+        st = ensure_fp8(ctx, nf, s);
+        if (st != PT_OK) return st;
+    }
+    ctx->last_depth = cfg->max_depth;
+    PT_CUDA(launch_set_u32(ctx->d_first_sample, first_sample, s));
+    auto direct = [&](cudaStream_t st_) {
+        return render_launches(ctx, sc, nf, cfg, cache, cache_vertex, rec_vertex, d_rec, n_pix, d_pixels, d_pixel_rgb,
+                               d_slot_rgb, d_hit_ids, n_slots, chunk, st_);
+    };
+    if (ctx->prof_on) return direct(s);   // per-kernel events need the launches themselves
+    GraphKey key;
+    std::memset(&key, 0, sizeof key);
+    key.sc_uid = sc->uid;
+    key.nf_uid = nf ? nf->uid : 0;
+    key.nf_version = nf ? nf->version : 0;
+    key.cache_uid = cache ? cache->uid : 0;
+    key.scratch_gen = ctx->scratch_gen;
+    key.width = cfg->width; key.height = cfg->height; key.spp = cfg->spp; key.max_depth = cfg->max_depth;
+    key.rr = cfg->rr; key.rr_start = cfg->rr_start; key.precision = cfg->precision;
+    key.cache_vertex = cache_vertex; key.rec_vertex = rec_vertex;
+    key.seed = cfg->seed; key.cache_cap = ctx->cache_cap;
+    key.chunk = chunk; key.n_pix = n_pix;
+    key.ptrs[0] = d_rec; key.ptrs[1] = d_pixels; key.ptrs[2] = d_pixel_rgb; key.ptrs[3] = d_slot_rgb;
+    key.ptrs[4] = d_hit_ids;
+    std::vector<unsigned char> kb(sizeof key);
+    std::memcpy(kb.data(), &key, sizeof key);
+    for (auto& g : ctx->graphs)
+        if (g.first == kb) {
+            PT_CUDA(cudaGraphLaunch(g.second, s));
+            return PT_OK;
+        }
+    // a render seen for the first time launches directly (one-off renders never pay for a capture)
+    bool seen = false;
+    for (auto& k : ctx->graph_seen) seen = seen || k == kb;
+    if (!seen) {
+        if (ctx->graph_seen.size() < kMaxGraphs) {
+            ctx->graph_seen.push_back(kb);
+        } else {
+            ctx->graph_seen[ctx->seen_next] = kb;
+            ctx->seen_next = (ctx->seen_next + 1) % kMaxGraphs;
+        }
+        return direct(s);
+    }
+    // record the sequence on the capture stream (nothing runs there), instantiate, replay on `s`
+    if (!ctx->cap_stream) PT_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const pt_status lst = direct(ctx->cap_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        cudaGraphExec_t exec = nullptr;
+        if (lst == PT_OK && ce == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+            cudaGraphDestroy(graph);
+            if (ctx->graphs.size() < kMaxGraphs) {
+                ctx->graphs.emplace_back(kb, exec);
+            } else {
+                cudaGraphExecDestroy(ctx->graphs[ctx->graph_next].second);
+                ctx->graphs[ctx->graph_next] = {kb, exec};
+                ctx->graph_next = (ctx->graph_next + 1) % kMaxGraphs;
+            }
+            PT_CUDA(cudaGraphLaunch(exec, s));
+            return PT_OK;
+        }
+        if (graph) cudaGraphDestroy(graph);
+    }
+    (void)cudaGetLastError();   // a failed capture leaves nothing behind: launch directly
+    return direct(s);
+}
+
 
 PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
                                   int64_t n_pix, const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb,

@@ -74,7 +74,9 @@ struct BounceParams {
     int32_t max_depth;
     int32_t rr, rr_start;
     uint32_t seed;
-    uint32_t first_sample;  // sample index offset (Philox counter word 1)
+    uint32_t first_sample;  // sample index offset (Philox counter word 1), unless first_sample_dev is set
+    const uint32_t* first_sample_dev;   // nullable: the offset read on the device (one captured launch
+                                        // sequence then serves every frame)
     uint64_t chunk_first;   // global slot of the chunk's first path
     uint32_t n_chunk;       // paths in the chunk
     uint32_t n_pix;
@@ -192,6 +194,8 @@ cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, f
 // self-test of the bounded device wait (selftest.cu): waits on a barrier nothing arrives on for budget_ns,
 // then sets PT_ERR_TIMEOUT in *err; *d_waited_ns receives the time waited
 cudaError_t wait_selftest(uint32_t* err, uint64_t budget_ns, uint64_t* d_waited_ns, cudaStream_t s);
+// one 32-bit word written on the stream by a tiny kernel (values that change between graph replays)
+cudaError_t launch_set_u32(uint32_t* dst, uint32_t value, cudaStream_t s);
 // tensor-core GEMMs of training (train_tc.cu): forward X[0] -> X[1..L] (and BF16 tiles Xb); backward from
 // G[L-1] = dX[0] -> BF16 tiles Gb and per-CTA partials of every layer's dW / db (Gl CTAs per layer, stride
 // floats each, layer l's at partial + l * Gl * stride: [H][pitch[l]] dW then [H] db)

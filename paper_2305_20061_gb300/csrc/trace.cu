@@ -22,7 +22,7 @@ __device__ __forceinline__ void slot_to_pixel(const BounceParams& p, uint32_t j,
     const uint32_t g = (uint32_t)(p.chunk_first + j);
     const uint32_t s = g / p.n_pix;
     const uint32_t i = g - s * p.n_pix;
-    smp = s + p.first_sample;
+    smp = s + (p.first_sample_dev ? __ldg(p.first_sample_dev) : p.first_sample);
     pix = p.pixels ? (uint32_t)p.pixels[i] : i;
 }
 
@@ -515,4 +515,15 @@ cudaError_t launch_trace_rays(const DevScene& sc, int64_t n, const float* org, c
     return cudaGetLastError();
 }
 
+}  // namespace ptk
+
+namespace ptk {
+namespace {
+__global__ void k_set_u32(uint32_t* dst, uint32_t value) { *dst = value; }
+}  // namespace
+cudaError_t launch_set_u32(uint32_t* dst, uint32_t value, cudaStream_t s)
+{
+    k_set_u32<<<1, 1, 0, s>>>(dst, value);
+    return cudaGetLastError();
+}
 }  // namespace ptk
