@@ -116,18 +116,21 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload(name, spp=None):
+def workload(name, spp=None, depth=None, rr=False):
     sc = I.make_scene(name)
     cfg = I.CONFIGS[name]["cfg"]
     if spp:  # smaller case for profiler captures only
         cfg = I.RenderCfg(cfg.width, cfg.height, spp, cfg.max_depth, cfg.seed)
+    if depth or rr:  # the paper's perf mode: path length 10, Russian roulette from depth 3 (Section 3.1)
+        cfg = I.RenderCfg(cfg.width, cfg.height, cfg.spp, depth or cfg.max_depth, cfg.seed, rr=bool(rr), rr_start=3)
     nif = I.nif_init(colour="identity" if name == "C1" else "yuv") if sc.env_const is None else None
     return sc, cfg, nif
 
 
 def config_dict(name, cfg, precision, trained):
+    rr = f"Russian roulette from depth {cfg.rr_start}" if cfg.rr else "no RR"
     d = {"workload": f"{name}: {I.CONFIGS[name]['desc']}; rendered {cfg.width}x{cfg.height}, {cfg.spp} spp, "
-                     f"max depth {cfg.max_depth}, no RR",
+                     f"max depth {cfg.max_depth}, {rr}",
          "paths_per_frame": cfg.n_slots,
          "l2": "per-step working set > L2 (wavefront queues ~2.7 GB per 2^24 paths) and a 512 MB L2 flush between "
                "timed steps (outside the timed events)"}
@@ -163,7 +166,7 @@ def oracle_rate(sc, cfg, nif, target_s: float, n_threads: int):
 def bench_reference(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
-    sc, cfg, nif = workload(args.workload, args.spp)
+    sc, cfg, nif = workload(args.workload, args.spp, args.depth, args.rr)
     if args.workload == "C5":
         cache0 = I.cache_init(*I.scene_bounds(sc))
         vals = []
@@ -287,7 +290,7 @@ def bench_ours(args):
     from paper_2305_20061_gb300 import pt
 
     dev = f"cuda:{local}"
-    sc, cfg, nif = workload(args.workload, args.spp)
+    sc, cfg, nif = workload(args.workload, args.spp, args.depth, args.rr)
     uses_nif = nif is not None
     precision = args.precision if uses_nif else None
     ctx = pt.Context(local)
@@ -779,6 +782,8 @@ def main():
     ap.add_argument("--workload", choices=["C1", "C2", "C3", "C4", "C5"], default="C2")
     ap.add_argument("--precision", choices=["bf16", "fp32", "fp8"], default="bf16")
     ap.add_argument("--spp", type=int, default=None, help="override spp (small cases for profiler captures)")
+    ap.add_argument("--depth", type=int, default=None, help="override the maximum path length (C1-C4)")
+    ap.add_argument("--rr", action="store_true", help="Russian roulette from depth 3 (the paper's perf mode; C1-C4)")
     ap.add_argument("--cpu-s", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=4.0, help="seconds per reference-arm step")
     ap.add_argument("--train-steps", type=int, default=2000,

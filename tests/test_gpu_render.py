@@ -342,3 +342,32 @@ def test_invalid_arguments(pt, ctx):
     with pytest.raises((pt.PTError, AssertionError)):
         pt.Scene(ctx, bad)
     ctx.check()
+
+
+def test_russian_roulette_per_path_and_unbiased(pt, ctx):
+    """Russian roulette on the GPU (Section 3.1: from depth 3, survival
+    probability max(tp)).  Inside a closed Lambertian sphere of albedo 1/2
+    emitting 1/2 every throughput is a power of two, so the GPU and the
+    oracle draw the same survival decisions from the same Philox words and
+    every path's radiance agrees exactly; the mean stays 1 - a^D within 4
+    sigma (roulette adds variance, not bias)."""
+    a, D = 0.5, 10
+    sc = I.furnace_sphere_inside(a)
+    cfg = I.RenderCfg(32, 24, 8, D, rr=True, rr_start=3)
+    _, slots, _ = pt.render_pixels(ctx, pt.Scene(ctx, sc), None, cfg, None, want_slots=True)
+    ctx.check()
+    got = slots.cpu().numpy().transpose(1, 0, 2).astype(np.float64)
+    r = O.render(O.Scene(sc), cfg, want_slots=True)
+    assert np.array_equal(got, r["slots"])
+    L = got[..., 0].ravel()
+    want = 1.0 - a ** D
+    assert L.std() > 0 and abs(L.mean() - want) < 4 * L.std() / np.sqrt(L.size)
+
+
+def test_russian_roulette_box_parity(pt, ctx):
+    """Roulette on a general scene: per-path parity with the oracle (same
+    Philox words; a decision flips only when FP32 and FP64 throughputs
+    straddle the uniform draw)."""
+    cfg = I.RenderCfg(32, 32, 2, 8, rr=True, rr_start=3)
+    res = _compare_render(pt, ctx, I.box_scene(), cfg, nif=I.nif_init(), max_div=2e-3)
+    assert res["matched"] <= 1e-3, res
