@@ -233,7 +233,10 @@ def nif_quality(gnif, sky, dev):
     ref = sky.reshape(-1, 3).double()
     out = {"grid": f"{w}x{h} pixel centres"}
     for prec in ("fp32", "bf16"):
-        y = gnif.eval(uv, prec).double()
+        try:
+            y = gnif.eval(uv, prec).double()
+        except RuntimeError:   # no BF16 kernel for this shape
+            continue
         lr = torch.sqrt(torch.mean((torch.log(torch.clamp(y, min=1e-6)) - torch.log(torch.clamp(ref, min=1e-6))) ** 2))
         mse = torch.mean((y / (1 + y) - ref / (1 + ref)) ** 2)
         out[f"log_rmse_{prec}"] = float(lr)
@@ -773,6 +776,80 @@ def bench_c5(args):
     return 0
 
 
+def bench_nif_sweep(args):
+    """NIF size sweep (the paper's question of how large a network stays
+    resident in on-chip SRAM, Section 3.3): for each shape, BF16-GEMM
+    training on the procedural 2048 x 1024 sky, its quality against the sky,
+    standalone FP32 and BF16 evaluation rates on 2^24 coordinates, and the C2
+    frame rate with that network as the environment.  The BF16 kernel keeps
+    every weight in shared memory; it takes H = 128 with 1 to 5 hidden layers
+    (three, two, then one 128-row tile slot beside the weights) and no shape
+    beyond.  One JSON line."""
+    import torch
+    from paper_2305_20061_gb300 import build
+    build.build()
+    from paper_2305_20061_gb300 import pt
+    dev = "cuda:0"
+    ctx = pt.Context(0)
+    stream = torch.cuda.current_stream()
+    sky = torch.from_numpy(I.procedural_sky()).to(dev)
+    uv = torch.from_numpy(I.uniform_uv(1 << 24, seed=1)).to(dev)
+    sc, cfg, _ = workload("C2")
+    scene = pt.Scene(ctx, sc)
+    img = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=dev)
+    steps = max(args.train_steps, 1)
+
+    def ms_of(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    rows = []
+    for H, L in [(128, 1), (128, 2), (128, 3), (128, 4), (128, 5), (128, 6), (128, 8), (64, 3), (32, 3)]:
+        g = pt.Nif(ctx, I.nif_init(hidden=H, n_hidden_layers=L, colour="yuv"))
+        tprec = "bf16"
+        try:
+            g.train(sky, steps=1, batch=1024, lr=1e-3, seed=99, precision="bf16")
+        except RuntimeError:   # the BF16 training chains need the weights resident in shared memory too
+            tprec = "fp32"
+        g = pt.Nif(ctx, I.nif_init(hidden=H, n_hidden_layers=L, colour="yuv"))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.train(sky, steps=steps, batch=1 << 16, lr=1e-3, seed=0, precision=tprec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        train_ms = e0.elapsed_time(e1)
+        row = {"hidden": H, "layers": L, "params": g.param_count, "weights_kb_bf16": (g.param_count * 2) // 1024,
+               "train_gemms": tprec, "train_ms_per_step": train_ms / steps, "quality": nif_quality(g, sky, dev)}
+        row["fp32_evals_per_s"] = (1 << 24) / (ms_of(lambda: g.eval(uv, "fp32"), 2) * 1e-3)
+        bf16_ok = H == 128 and 1 <= L <= 5
+        if bf16_ok:
+            row["bf16_evals_per_s"] = (1 << 24) / (ms_of(lambda: g.eval(uv, "bf16"), 3) * 1e-3)
+            row["bf16_tile_slots"] = 3 if L <= 3 else (2 if L == 4 else 1)
+            fr = ms_of(lambda: pt.render(ctx, scene, g, cfg, "bf16", out=img), 3)
+            row["c2_bf16_msamples_s"] = cfg.n_slots / (fr * 1e-3) / 1e6
+        else:
+            row["bf16_evals_per_s"] = None
+            row["bf16_note"] = "not resident: the BF16 kernel needs H = 128 and L <= 5"
+        ctx.check()
+        rows.append(row)
+        del g
+    print(json.dumps({"metric": "NIF size sweep: quality vs evaluation and path rate", "n_gpus": 1,
+                      "train_steps": steps, "unit": "evals/s, Msamples/s", "higher_is_better": True,
+                      "config": {"sky": "procedural 2048x1024", "render": "C2 512x512 64 spp depth 8",
+                                 "training": "Adam lr 1e-3, batch 2^16, BF16 tensor-core GEMMs where the shape "
+                                             "fits (else FP32)"},
+                      "rows": rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -795,7 +872,11 @@ def main():
                     help="skip the other-precision frames and standalone NIF runs (profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bias", action="store_true", help="C5: skip the bias measurement against the 4096-spp render")
+    ap.add_argument("--nif-sweep", action="store_true",
+                    help="NIF size sweep (hidden width and depth vs quality, evaluation and path rate); one JSON line")
     args = ap.parse_args()
+    if args.nif_sweep:
+        return bench_nif_sweep(args)
     if args.impl == "reference":
         return bench_reference(args)
     if args.workload == "C5":

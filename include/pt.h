@@ -155,8 +155,11 @@ typedef struct pt_nif_desc {
 } pt_nif_desc;
 
 /* Upload FP32 master weights and build the BF16 operand image of the
-   tensor-core kernel (when the shape is F = 64, H = 128, L = 3; the FP8 image
-   is built on first use, see pt_nif_fp8_scales). */
+   tensor-core kernel (when F = 64, H = 128 and 1 <= L <= 5: the weights stay
+   resident in shared memory beside three 128-row tile slots for L <= 3, two
+   for L = 4, one for L = 5; from L = 6 they do not fit, and only the FP32
+   path serves; the FP8 image, L = 3 only, is built on first use, see
+   pt_nif_fp8_scales). */
 PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* desc, pt_nif** out);
 PT_API void pt_destroy_nif(pt_nif* nif);
 /* number of floats in the flat layout */
@@ -166,8 +169,8 @@ PT_API int64_t pt_nif_param_count(const pt_nif* nif);
 PT_API pt_status pt_nif_get_params(pt_ctx* ctx, const pt_nif* nif, float* params);
 
 /* Evaluate the NIF at n coordinates: d_uv [n][2] float -> d_rgb [n][3]
-   float, in the requested precision.  PT_EUNSUPPORTED for a tensor-core
-   precision on a shape other than F = 64, H = 128, L = 3. */
+   float, in the requested precision.  PT_EUNSUPPORTED for BF16 on a shape
+   other than F = 64, H = 128, 1 <= L <= 5, and for FP8 other than L = 3. */
 PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nif, int32_t precision, int64_t n, const float* d_uv,
                              float* d_rgb, void* stream);
 

@@ -67,7 +67,7 @@ struct pt_nif {
     int64_t n_params = 0;
     float* d_params = nullptr;   // flat FP32 master weights
     float* d_fp32 = nullptr;     // packed FP32 layout (Wt, bias, Wout, bout)
-    unsigned char* d_tc = nullptr;  // BF16 shared-memory image of the tensor-core kernel (F=64, H=128, L=3 only)
+    unsigned char* d_tc = nullptr;  // BF16 shared-memory image of the tensor-core kernel (F=64, H=128, L=1..5)
     // FP8 E4M3 image of the same shape, built on first use (its calibration runs on the host) and
     // rebuilt on the next use after the weights change
     bool fp8_ok = false;
@@ -298,7 +298,7 @@ pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, int ac
         return PT_OK;
     }
     if (precision == PT_BF16 && nif->d_tc) {
-        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nif->d_tc, p, 1, ctx->sm_count, s); }));
+        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nif->d_tc, nif->L, p, 1, ctx->sm_count, s); }));
         return PT_OK;
     }
     if (precision == PT_FP8E4M3 && nif->fp8_ok) {
@@ -307,7 +307,7 @@ pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, int ac
         PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_fp8(nif->d_fp8, p, 1, ctx->sm_count, s); }));
         return PT_OK;
     }
-    return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3");
+    return fail(ctx, PT_EUNSUPPORTED, "the BF16 NIF needs F = 64, H = 128, 1 <= L <= 5 (FP8: L = 3)");
 }
 
 }  // namespace
@@ -686,7 +686,7 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
         return PT_OK;
     }
     if (precision == PT_BF16 && nf->d_tc) {
-        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nf->d_tc, p, 0, ctx->sm_count, s); }));
+        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nf->d_tc, nf->L, p, 0, ctx->sm_count, s); }));
         return PT_OK;
     }
     if (precision == PT_FP8E4M3 && nf->fp8_ok) {
@@ -696,7 +696,7 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
         return PT_OK;
     }
     if (precision == PT_BF16 || precision == PT_FP8E4M3)
-        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3");
+        return fail(ctx, PT_EUNSUPPORTED, "the BF16 NIF needs F = 64, H = 128, 1 <= L <= 5 (FP8: L = 3)");
     return fail(ctx, PT_EINVAL, "unknown precision");
 }
 
@@ -714,7 +714,9 @@ pt_status check_train_precision(pt_ctx* ctx, int L, int H, int in0, int32_t prec
     t.H = H;
     t.in0 = in0;
     if (!train_tc_supported(t))
-        return fail(ctx, PT_EUNSUPPORTED, "BF16 training needs at most 8 hidden layers of width <= 128, inputs <= 128");
+        return fail(ctx, PT_EUNSUPPORTED,
+                    "BF16 training needs inputs and width <= 128 and every hidden layer's weights resident in shared "
+                    "memory (width 128: at most 5 layers)");
     return PT_OK;
 }
 
@@ -791,7 +793,7 @@ pt_status ensure_train(pt_ctx* ctx, pt_nif* nf, int64_t B)
 pt_status refresh_layouts(pt_ctx* ctx, pt_nif* nf, cudaStream_t s)
 {
     PT_CUDA(repack_nif_fp32(nf->d_params, nf->F, nf->H, nf->L, nf->d_fp32, s));
-    if (nf->d_tc) PT_CUDA(repack_nif_tc_image(nf->d_params, nf->d_tc, s));
+    if (nf->d_tc) PT_CUDA(repack_nif_tc_image(nf->d_params, nf->L, nf->d_tc, s));
     nf->fp8_stale = true;   // rebuilt on its next use
     return PT_OK;
 }
@@ -1270,7 +1272,7 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
     if (n_slots > 0xFFFFFFFFll) return fail(ctx, PT_EINVAL, "more than 2^32 - 1 paths in one call");
     if (sc->dev.env_is_nif && cfg->precision != PT_FP32 && !(cfg->precision == PT_BF16 && nf->d_tc) &&
         !(cfg->precision == PT_FP8E4M3 && nf->fp8_ok))
-        return fail(ctx, PT_EUNSUPPORTED, "tensor-core NIF needs F = 64, H = 128, L = 3");
+        return fail(ctx, PT_EUNSUPPORTED, "the BF16 NIF needs F = 64, H = 128, 1 <= L <= 5 (FP8: L = 3)");
     // chunk = whole samples
     int64_t chunk = cfg->chunk_slots > 0 ? cfg->chunk_slots : (int64_t)1 << 24;
     chunk = std::max<int64_t>(n_pix, (chunk / n_pix) * n_pix);

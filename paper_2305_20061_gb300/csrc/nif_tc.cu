@@ -1,12 +1,15 @@
 // Fused tensor-core evaluation of the HDR neural image field (Section 3.2)
-// for the shape F = 64 frequencies, three hidden FC-128 ReLU layers, FC-3
-// head, on sm_103a tcgen05 tensor cores.
+// for F = 64 frequencies, L = 1 .. 5 hidden FC-128 ReLU layers (three in the
+// workloads), FC-3 head, on sm_103a tcgen05 tensor cores.
 //
 // The paper keeps the network's weights in IPU tile SRAM and lets the
 // Poplibs planner replicate layers across tiles (Section 3.3.1); here one
 // persistent CTA per SM holds all BF16 weights in shared memory for the
-// whole kernel and streams 128-row tiles of queries through them.  Three
-// tile slots of eight warps each; within a slot, warps 4h..4h+3 handle half h
+// whole kernel and streams 128-row tiles of queries through them.  The
+// 32 KB tile slots that fit beside the weights set the overlap: three for
+// L <= 3, two for L = 4, one for L = 5; from L = 6 the weights and one tile
+// no longer fit in the 227 KB of shared memory (where SRAM residency breaks
+// on this GPU).  Tile slots of eight warps each; within a slot, warps 4h..4h+3 handle half h
 // of every row: row t is TMEM lane t, and half h covers accumulator columns
 // [64h, 64h + 64) and Fourier frequencies [32h, 32h + 32).  A slot's warps
 // compute the features, and after each MMA read their accumulator half-row
@@ -34,35 +37,43 @@ namespace ptk {
 namespace {
 
 constexpr int kF = 64, kH = 128, kRows = 128;
-constexpr int kSlots = 3;
-constexpr int kThreads = kSlots * 8 * 32;   // 3 slots x 8 warps
+constexpr int kMinL = 1, kMaxL = 5;
 constexpr uint32_t kTmemCols = 512;
 
-// shared-memory image (offsets from a 1024-byte aligned base)
 constexpr uint32_t kWBytes = kH * kH * 2;            // 32 KB per hidden layer (2 K-blocks x 128 rows x 128 B)
 constexpr uint32_t kHeadRows = 16;
 constexpr uint32_t kHeadBytes = kHeadRows * kH * 2;  // 4 KB
-constexpr uint32_t kOffW = 0;                        // W1 | W2 | W3
-constexpr uint32_t kOffHead = 3 * kWBytes;           // 98304
 // Hidden-layer biases ride on the tensor core as one more K = 16 step: A is a
 // block of ones (columns 0 and 1), B holds bias = hi + lo in BF16 (columns 0
 // and 1), both K-major without swizzle (core matrices 8 rows x 16 B, K step
 // 128 B, 8-row step 256 B).
 constexpr uint32_t kBiasBytes = kRows * 32;              // 4096 per block
 constexpr uint32_t kBiasLbo = 128, kBiasSbo = 256;
-constexpr uint32_t kOffBias = kOffHead + kHeadBytes;     // 102400: b1 | b2 | b3
-constexpr uint32_t kOffOnes = kOffBias + 3 * kBiasBytes; // 114688
-constexpr uint32_t kOffTail = kOffOnes + kBiasBytes;     // 118784: fp32 b1 b2 b3 [384], b4 [4], B [128], M [12]
-constexpr uint32_t kTailFloats = 3 * kH + 4 + 2 * kF + 12;
-constexpr uint32_t kImageBytes = kOffTail + kTailFloats * 4;  // 120896
-constexpr uint32_t kOffA = 121856;                   // 1024-aligned, three 32 KB activation buffers
-constexpr uint32_t kABytes = kRows * kH * 2;
-constexpr uint32_t kOffBar = kOffA + kSlots * kABytes;  // 203776
-constexpr uint32_t kSmemBytes = kOffBar + 128 + 1024;   // barriers + alignment slack
+constexpr uint32_t kABytes = kRows * kH * 2;             // one 128-row BF16 activation tile
+constexpr int kSmemLimit = 227 * 1024;
 
-static_assert(kImageBytes % 16 == 0, "bulk copy size");
-static_assert(kImageBytes <= kOffA && kSmemBytes <= 227 * 1024, "shared-memory budget");
-static_assert(kOffA % 1024 == 0 && kOffHead % 1024 == 0, "swizzle atoms need 1024-byte alignment");
+// Shared-memory image of a NIF with L hidden layers (offsets from a
+// 1024-byte aligned base): W1 .. WL | head | bias blocks b1 .. bL | ones |
+// FP32 tail (b1 .. bL [L x 128], b_head [4], B [128], M [12]), then the tile
+// slots that fit (at most three: TMEM holds 3 x (128 + 32) columns).
+template <int L>
+struct Layout {
+    static constexpr uint32_t off_w = 0;
+    static constexpr uint32_t off_head = L * kWBytes;
+    static constexpr uint32_t off_bias = off_head + kHeadBytes;
+    static constexpr uint32_t off_ones = off_bias + L * kBiasBytes;
+    static constexpr uint32_t off_tail = off_ones + kBiasBytes;
+    static constexpr uint32_t tail_floats = L * kH + 4 + 2 * kF + 12;
+    static constexpr uint32_t image_bytes = off_tail + tail_floats * 4;
+    static constexpr uint32_t off_a = (image_bytes + 1023) & ~1023u;
+    static constexpr int room = (kSmemLimit - 1024 - 128 - (int)off_a) / (int)kABytes;
+    static constexpr int slots = room > 3 ? 3 : room;
+    static constexpr uint32_t off_bar = off_a + (slots > 0 ? slots : 0) * kABytes;
+    static constexpr uint32_t smem_bytes = off_bar + 128 + 1024;   // barriers + alignment slack
+    static constexpr int threads = (slots > 0 ? slots : 1) * 256;
+};
+static_assert(Layout<3>::off_a == 121856 && Layout<3>::slots == 3, "the three-layer image");
+static_assert(Layout<kMaxL>::slots >= 1 && Layout<kMaxL + 1>::slots < 1, "residency limit");
 
 // --- PTX wrappers: tc_ptx.cuh ------------------------------------------------
 using namespace tc;
@@ -118,9 +129,15 @@ __device__ __forceinline__ bool slot_vote_any(int id, bool pred)
     return r != 0;
 }
 
-// 24 warps: six per SM sub-partition, so up to 80 registers per thread
-__global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mode)
+// three slots = 24 warps: six per SM sub-partition, so up to 80 registers per thread
+template <int L>
+__global__ void __launch_bounds__(Layout<L>::threads, 1) k_nif_tc(const TcParams p, int mode)
 {
+    using LY = Layout<L>;
+    constexpr int kSlots = LY::slots;
+    constexpr uint32_t kOffW = LY::off_w, kOffHead = LY::off_head, kOffBias = LY::off_bias, kOffOnes = LY::off_ones,
+                       kOffTail = LY::off_tail, kImageBytes = LY::image_bytes, kOffA = LY::off_a,
+                       kOffBar = LY::off_bar;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
@@ -173,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
     const uint32_t acc = tmem + s * 128;
     const uint32_t head = tmem + 384 + 32 * s;
     const uint32_t bar = bar_acc + 8 * s;
-    const float* Bm = tail + 3 * kH + 4;
+    const float* Bm = tail + L * kH + 4;
     const float* Mm = Bm + 2 * kF;
     const uint32_t id_h = idesc_bf16(128, 128), id_o = idesc_bf16(128, kHeadRows);
     uint32_t ph = 0;
@@ -226,12 +243,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
         in = load_inputs(((int64_t)(i + 1) * gridDim.x + blockIdx.x) * kSlots + s);
         fence_proxy_async();
         bool fail = false;
-        for (int stage = 0; stage < 4; ++stage) {   // three hidden layers, then the head
+        for (int stage = 0; stage <= L; ++stage) {   // the hidden layers, then the head
             tc_fence_before();
             if (slot_vote_any(bar_id, fail)) { dead = true; break; }
             if (issuer) {
                 tc_fence_after();
-                if (stage < 3) {
+                if (stage < L) {
                     const uint32_t w_base = sbase + kOffW + stage * kWBytes;
 #pragma unroll
                     for (int kk = 0; kk < 8; ++kk) {
@@ -254,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
             ph ^= 1;
             tc_fence_after();
             if (!__all_sync(0xFFFFFFFFu, got)) { fail = true; continue; }   // voted at the next barrier
-            if (stage < 3) {
+            if (stage < L) {
                 const uint32_t tcol = acc + lane_base + half * 64;
                 uint32_t ra[16], rb[16];
                 auto put16 = [&](const uint32_t (&x)[16], int gq) {
@@ -289,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
             uint32_t yr[4];
             tmem_ld4(head + lane_base, yr);
             tmem_wait_ld();
-            const float* b4 = tail + 3 * kH;
+            const float* b4 = tail + L * kH;
             const float y0 = __uint_as_float(yr[0]) + b4[0];
             const float y1 = __uint_as_float(yr[1]) + b4[1];
             const float y2 = __uint_as_float(yr[2]) + b4[2];
@@ -325,14 +342,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_tc(const TcParams p, int mo
     }
 }
 
-}  // namespace
-
-// Host-side packing of the weight image for k_nif_tc (see the offsets above).
+// Host-side packing of the weight image for k_nif_tc<L> (see Layout).
 // W[l] are PyTorch-layout [out][in] float matrices.
-bool pack_nif_tc_image(const float* params, int F, int H, int L, std::vector<unsigned char>& out)
+template <int L>
+void pack_image(const float* params, int F, int H, std::vector<unsigned char>& out)
 {
-    if (F != kF || H != kH || L != 3) return false;
-    out.assign(kImageBytes, 0);
+    using LY = Layout<L>;
+    out.assign(LY::image_bytes, 0);
     auto to_bf16 = [](float x) -> uint16_t {
         uint32_t u;
         std::memcpy(&u, &x, 4);
@@ -356,43 +372,68 @@ bool pack_nif_tc_image(const float* params, int F, int H, int L, std::vector<uns
         return x;
     };
     for (uint32_t r = 0; r < kRows; ++r) {
-        put_plain(kOffOnes + bias_elem(r, 0), 1.f);
-        put_plain(kOffOnes + bias_elem(r, 1), 1.f);
+        put_plain(LY::off_ones + bias_elem(r, 0), 1.f);
+        put_plain(LY::off_ones + bias_elem(r, 1), 1.f);
     }
     const float* p = params;
     const float* Bsrc = p;
     p += 2 * F;
-    float* tail = reinterpret_cast<float*>(&out[kOffTail]);
+    float* tail = reinterpret_cast<float*>(&out[LY::off_tail]);
     for (int l = 0; l <= L; ++l) {
         const int in = l == 0 ? 2 * F : H, o = l == L ? 3 : H;
         if (l < L) {
             for (int j = 0; j < o; ++j)
-                for (int k = 0; k < in; ++k) put(kOffW + l * kWBytes, kRows, j, k, p[(size_t)j * in + k]);
+                for (int k = 0; k < in; ++k) put(LY::off_w + l * kWBytes, kRows, j, k, p[(size_t)j * in + k]);
             p += (size_t)in * o;
             for (int j = 0; j < o; ++j) {
                 tail[l * kH + j] = p[j];
                 const float hi = from_bf16(to_bf16(p[j]));
-                put_plain(kOffBias + l * kBiasBytes + bias_elem(j, 0), hi);
-                put_plain(kOffBias + l * kBiasBytes + bias_elem(j, 1), p[j] - hi);
+                put_plain(LY::off_bias + l * kBiasBytes + bias_elem(j, 0), hi);
+                put_plain(LY::off_bias + l * kBiasBytes + bias_elem(j, 1), p[j] - hi);
             }
             p += o;
         } else {
             for (int j = 0; j < 3; ++j)
-                for (int k = 0; k < in; ++k) put(kOffHead, kHeadRows, j, k, p[(size_t)j * in + k]);
+                for (int k = 0; k < in; ++k) put(LY::off_head, kHeadRows, j, k, p[(size_t)j * in + k]);
             p += (size_t)in * 3;
-            for (int j = 0; j < 3; ++j) tail[3 * kH + j] = p[j];
+            for (int j = 0; j < 3; ++j) tail[L * kH + j] = p[j];
             p += 3;
         }
     }
-    for (int i = 0; i < 2 * F; ++i) tail[3 * kH + 4 + i] = Bsrc[i];
-    for (int i = 0; i < 9; ++i) tail[3 * kH + 4 + 2 * F + i] = p[i];
+    for (int i = 0; i < 2 * F; ++i) tail[L * kH + 4 + i] = Bsrc[i];
+    for (int i = 0; i < 9; ++i) tail[L * kH + 4 + 2 * F + i] = p[i];
+}
+
+template <int L>
+cudaError_t launch_l(const unsigned char* image, const TcParams& p, int mode, int sm_count, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_nif_tc<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Layout<L>::smem_bytes);
+    if (e != cudaSuccess) return e;
+    k_nif_tc<L><<<sm_count, Layout<L>::threads, Layout<L>::smem_bytes, s>>>(p, mode);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool nif_tc_supported(int F, int H, int L) { return F == kF && H == kH && L >= kMinL && L <= kMaxL; }
+
+bool pack_nif_tc_image(const float* params, int F, int H, int L, std::vector<unsigned char>& out)
+{
+    if (!nif_tc_supported(F, H, L)) return false;
+    switch (L) {
+    case 1: pack_image<1>(params, F, H, out); break;
+    case 2: pack_image<2>(params, F, H, out); break;
+    case 3: pack_image<3>(params, F, H, out); break;
+    case 4: pack_image<4>(params, F, H, out); break;
+    default: pack_image<5>(params, F, H, out); break;
+    }
     return true;
 }
 
-cudaError_t launch_nif_tc(const unsigned char* image, const NifEvalParams& np, int mode, int sm_count, cudaStream_t s)
+cudaError_t launch_nif_tc(const unsigned char* image, int L, const NifEvalParams& np, int mode, int sm_count,
+                          cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_nif_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-    if (e != cudaSuccess) return e;
     TcParams p = {};
     p.image = image;
     p.uv = np.uv;
@@ -405,11 +446,17 @@ cudaError_t launch_nif_tc(const unsigned char* image, const NifEvalParams& np, i
     p.accumulate = np.accumulate;
     p.err = np.err;
     p.stats = np.stats;
-    k_nif_tc<<<sm_count, kThreads, kSmemBytes, s>>>(p, mode);
-    return cudaGetLastError();
+    switch (L) {
+    case 1: return launch_l<1>(image, p, mode, sm_count, s);
+    case 2: return launch_l<2>(image, p, mode, sm_count, s);
+    case 3: return launch_l<3>(image, p, mode, sm_count, s);
+    case 4: return launch_l<4>(image, p, mode, sm_count, s);
+    case 5: return launch_l<5>(image, p, mode, sm_count, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
-size_t nif_tc_image_bytes() { return kImageBytes; }
+
 
 }  // namespace ptk
 
@@ -417,13 +464,15 @@ namespace ptk {
 namespace {
 // Flat master weights -> the tensor-core kernel's shared-memory image (same
 // layout as pack_nif_tc_image builds on the host; BF16 round-to-nearest-even).
+template <int L>
 __global__ void k_repack_tc(const float* __restrict__ params, unsigned char* __restrict__ image)
 {
-    const float* W[4];
-    const float* b[4];
+    using LY = Layout<L>;
+    const float* W[L + 1];
+    const float* b[L + 1];
     const float* p = params + 2 * kF;
-    for (int l = 0; l < 4; ++l) {
-        const int in = l == 0 ? 2 * kF : kH, o = l == 3 ? 3 : kH;
+    for (int l = 0; l <= L; ++l) {
+        const int in = l == 0 ? 2 * kF : kH, o = l == L ? 3 : kH;
         W[l] = p;
         p += (size_t)in * o;
         b[l] = p;
@@ -431,22 +480,22 @@ __global__ void k_repack_tc(const float* __restrict__ params, unsigned char* __r
     }
     const float* Mp = p;
     // bias blocks (hi, lo in columns 0, 1) and the block of ones; the rest of those blocks stays zero
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 4 * kRows; idx += gridDim.x * blockDim.x) {
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < (L + 1) * kRows; idx += gridDim.x * blockDim.x) {
         const int l = idx / kRows, r = idx % kRows;
-        unsigned short* hi = reinterpret_cast<unsigned short*>(image + kOffBias + l * kBiasBytes + bias_elem(r, 0));
-        unsigned short* lo = reinterpret_cast<unsigned short*>(image + kOffBias + l * kBiasBytes + bias_elem(r, 1));
-        if (l < 3) {
+        unsigned short* hi = reinterpret_cast<unsigned short*>(image + LY::off_bias + l * kBiasBytes + bias_elem(r, 0));
+        unsigned short* lo = reinterpret_cast<unsigned short*>(image + LY::off_bias + l * kBiasBytes + bias_elem(r, 1));
+        if (l < L) {
             const float x = b[l][r];
             const __nv_bfloat16 h = __float2bfloat16_rn(x);
             *hi = __bfloat16_as_ushort(h);
             *lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
-        } else {   // l == 3: the ones block directly follows the bias blocks
+        } else {   // l == L: the ones block directly follows the bias blocks
             *hi = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
             *lo = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
         }
     }
-    const int n_hidden = 3 * kH * kH, n_head = kHeadRows * kH;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_hidden + n_head + (int)kTailFloats;
+    const int n_hidden = L * kH * kH, n_head = kHeadRows * kH;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_hidden + n_head + (int)LY::tail_floats;
          idx += gridDim.x * blockDim.x) {
         if (idx < n_hidden + n_head) {
             uint32_t base, rows, r, k;
@@ -455,16 +504,16 @@ __global__ void k_repack_tc(const float* __restrict__ params, unsigned char* __r
                 const int l = idx / (kH * kH);
                 r = (idx / kH) % kH;
                 k = idx % kH;
-                base = kOffW + l * kWBytes;
+                base = LY::off_w + l * kWBytes;
                 rows = kRows;
                 x = W[l][(size_t)r * kH + k];
             } else {
                 const int q = idx - n_hidden;
                 r = q / kH;
                 k = q % kH;
-                base = kOffHead;
+                base = LY::off_head;
                 rows = kHeadRows;
-                x = r < 3 ? W[3][(size_t)r * kH + k] : 0.f;
+                x = r < 3 ? W[L][(size_t)r * kH + k] : 0.f;
             }
             const uint32_t off = base + (k >> 6) * (rows * 128) + r * 128 + ((((k & 63) >> 3) ^ (r & 7)) << 4) + (k & 7) * 2;
             const unsigned short bits = __bfloat16_as_ushort(__float2bfloat16_rn(x));
@@ -472,19 +521,26 @@ __global__ void k_repack_tc(const float* __restrict__ params, unsigned char* __r
         } else {
             const int t = idx - n_hidden - n_head;
             float val = 0.f;
-            if (t < 3 * kH) val = b[t / kH][t % kH];
-            else if (t < 3 * kH + 4) val = (t - 3 * kH) < 3 ? b[3][t - 3 * kH] : 0.f;
-            else if (t < 3 * kH + 4 + 2 * kF) val = params[t - 3 * kH - 4];
-            else if (t < 3 * kH + 4 + 2 * kF + 9) val = Mp[t - 3 * kH - 4 - 2 * kF];
-            reinterpret_cast<float*>(image + kOffTail)[t] = val;
+            if (t < L * kH) val = b[t / kH][t % kH];
+            else if (t < L * kH + 4) val = (t - L * kH) < 3 ? b[L][t - L * kH] : 0.f;
+            else if (t < L * kH + 4 + 2 * kF) val = params[t - L * kH - 4];
+            else if (t < L * kH + 4 + 2 * kF + 9) val = Mp[t - L * kH - 4 - 2 * kF];
+            reinterpret_cast<float*>(image + LY::off_tail)[t] = val;
         }
     }
 }
 }  // namespace
 
-cudaError_t repack_nif_tc_image(const float* params, unsigned char* image, cudaStream_t s)
+cudaError_t repack_nif_tc_image(const float* params, int L, unsigned char* image, cudaStream_t s)
 {
-    k_repack_tc<<<128, 256, 0, s>>>(params, image);
+    switch (L) {
+    case 1: k_repack_tc<1><<<128, 256, 0, s>>>(params, image); break;
+    case 2: k_repack_tc<2><<<128, 256, 0, s>>>(params, image); break;
+    case 3: k_repack_tc<3><<<128, 256, 0, s>>>(params, image); break;
+    case 4: k_repack_tc<4><<<128, 256, 0, s>>>(params, image); break;
+    case 5: k_repack_tc<5><<<128, 256, 0, s>>>(params, image); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 }  // namespace ptk

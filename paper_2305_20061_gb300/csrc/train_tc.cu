@@ -49,6 +49,7 @@ constexpr int kDwThreads = 128;              // weight kernel: one thread drives
 constexpr int kDwMaxStages = 4;
 constexpr uint32_t kDwBarBytes = 128;        // full / empty per stage, done, drain, TMEM address, abort flag
 constexpr int kSmemPerSm = 233472;           // 228 KiB of shared memory per SM
+constexpr int kSmemLimit = 227 * 1024;       // dynamic shared memory of one CTA
 constexpr int kSmemReserved = 1024;          // reserved per CTA
 
 __host__ __device__ constexpr int pad16(int n) { return (n + 15) & ~15; }
@@ -730,9 +731,24 @@ cudaError_t backward_nh(const TrainNet& net, int64_t B, TrainWork& wk, unsigned 
 }  // namespace
 
 // ---------------------------------------------------------------------------
+namespace {
+// the chains keep every layer's weights in shared memory: the shapes whose images fit
+template <int NH>
+bool fits(int L, int in0)
+{
+    const int K0 = pad16(in0);
+    return (int)(fwd_bar_offset<NH>(L, K0) + kBarBytes) <= kSmemLimit &&
+           (int)(dx_bar_offset<NH>(L) + kBarBytes) <= kSmemLimit;
+}
+}  // namespace
+
 bool train_tc_supported(const TrainNet& net)
 {
-    return net.L >= 1 && net.L <= kMaxLayers && net.H >= 1 && net.H <= 128 && net.in0 >= 1 && net.in0 <= 128;
+    if (!(net.L >= 1 && net.L <= kMaxLayers && net.H >= 1 && net.H <= 128 && net.in0 >= 1 && net.in0 <= 128))
+        return false;
+    if (net.H <= 32) return fits<32>(net.L, net.in0);
+    if (net.H <= 64) return fits<64>(net.L, net.in0);
+    return fits<128>(net.L, net.in0);
 }
 
 cudaError_t train_tc_forward(const TrainNet& net, int64_t B, TrainWork& wk, unsigned int* err, cudaStream_t s)

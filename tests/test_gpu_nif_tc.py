@@ -85,10 +85,44 @@ def test_bf16_nif_error_vs_oracle(pt, ctx):
 
 
 def test_bf16_nif_rejects_other_shapes(pt, ctx):
-    g = pt.Nif(ctx, I.nif_init(n_freq=32))
-    with pytest.raises(pt.PTError) as e:
-        g.eval(torch.zeros((10, 2), device="cuda"), precision="bf16")
-    assert e.value.status == pt.PT_EUNSUPPORTED
+    """Beyond F = 64, H = 128, 1 <= L <= 5 the BF16 kernel does not apply: 32
+    frequencies, or six hidden layers, whose weights (192 KB) no longer fit in
+    shared memory beside a 32 KB tile slot."""
+    for kw in ({"n_freq": 32}, {"n_hidden_layers": 6}):
+        g = pt.Nif(ctx, I.nif_init(**kw))
+        with pytest.raises(pt.PTError) as e:
+            g.eval(torch.zeros((10, 2), device="cuda"), precision="bf16")
+        assert e.value.status == pt.PT_EUNSUPPORTED
+        g.eval(torch.zeros((10, 2), device="cuda"), precision="fp32")   # the FP32 path serves every shape
+    ctx.check()
+
+
+@pytest.mark.parametrize("L", [1, 2, 4, 5])
+def test_bf16_nif_other_depths_match_rounding_model(pt, ctx, L):
+    """The kernel at 1, 2, 4 and 5 hidden layers (three, three, two and one
+    tile slots) against the same rounding model; a ragged count spanning
+    several tiles per SM, and training follows (the image is repacked)."""
+    nif = I.nif_init(colour="yuv", n_hidden_layers=L, seed=L)
+    rng = np.random.default_rng(L)
+    for b in nif.b:
+        b[:] = rng.normal(0, 0.05, b.shape)
+    g = pt.Nif(ctx, nif)
+    n = 128 * 152 * 4 + 37
+    uv = I.uniform_uv(n, seed=L + 10)
+    got = g.eval(torch.from_numpy(uv).cuda(), precision="bf16").cpu().numpy().astype(np.float64)
+    ctx.check()
+    ref = bf16_model(nif, uv)
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert np.all(np.isfinite(got))
+    assert np.median(rel) <= 2e-4 and rel.max() <= 2e-2, (np.median(rel), rel.max())
+    # after a training step the BF16 image follows the new weights
+    g.train(torch.from_numpy(I.procedural_sky(64, 32)).cuda(), steps=2, batch=1024, lr=1e-2, precision="bf16")
+    flat = g.get_params()
+    trained = pt.nif_from_flat(64, 128, L, flat)
+    got2 = g.eval(torch.from_numpy(uv[:4096]).cuda(), precision="bf16").cpu().numpy().astype(np.float64)
+    ref2 = bf16_model(trained, uv[:4096])
+    rel2 = np.abs(got2 - ref2) / np.abs(ref2)
+    assert np.median(rel2) <= 2e-4 and rel2.max() <= 2e-2, (np.median(rel2), rel2.max())
 
 
 @pytest.mark.parametrize("config", ["C1", "C2"])
