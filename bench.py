@@ -238,9 +238,17 @@ def nif_quality(gnif, sky, dev):
         except RuntimeError:   # no BF16 kernel for this shape
             continue
         lr = torch.sqrt(torch.mean((torch.log(torch.clamp(y, min=1e-6)) - torch.log(torch.clamp(ref, min=1e-6))) ** 2))
-        mse = torch.mean((y / (1 + y) - ref / (1 + ref)) ** 2)
+        ty, tr = y / (1 + y), ref / (1 + ref)
+        mse = torch.mean((ty - tr) ** 2)
         out[f"log_rmse_{prec}"] = float(lr)
         out[f"psnr_tonemapped_{prec}"] = float(10 * torch.log10(1.0 / mse))
+        if prec == "fp32":   # luma / chroma split of the tonemapped error (BT.601 Y, U, V)
+            wts = torch.tensor([0.299, 0.587, 0.114], dtype=torch.float64, device=ty.device)
+            ly, lr_ = ty @ wts, tr @ wts
+            uy = torch.stack([0.492 * (ty[:, 2] - ly), 0.877 * (ty[:, 0] - ly)], 1)
+            ur = torch.stack([0.492 * (tr[:, 2] - lr_), 0.877 * (tr[:, 0] - lr_)], 1)
+            out["psnr_luma_fp32"] = float(10 * torch.log10(1.0 / torch.mean((ly - lr_) ** 2)))
+            out["psnr_chroma_fp32"] = float(10 * torch.log10(1.0 / torch.mean((uy - ur) ** 2)))
     return out
 
 
@@ -850,6 +858,36 @@ def bench_nif_sweep(args):
     return 0
 
 
+def bench_colour_sweep(args):
+    """Colour space of the NIF's output head (Section 3.2: the network predicts
+    log colour in a chosen space and a fixed matrix maps it to RGB before exp):
+    RGB, YUV (BT.601) and YCoCg heads trained alike on the procedural sun sky,
+    quality against the sky (log-RMSE, tonemapped PSNR with its luma and
+    chroma parts).  A synthetic stand-in for the paper's HDRI study.  One JSON
+    line."""
+    import torch
+    from paper_2305_20061_gb300 import build
+    build.build()
+    from paper_2305_20061_gb300 import pt
+    dev = "cuda:0"
+    ctx = pt.Context(0)
+    sky = torch.from_numpy(I.procedural_sky()).to(dev)
+    steps = max(args.train_steps, 1)
+    rows = []
+    for colour in ("identity", "yuv", "ycocg"):
+        g = pt.Nif(ctx, I.nif_init(colour=colour))
+        losses = g.train(sky, steps=steps, batch=1 << 16, lr=1e-3, seed=0, precision=args.train_precision)
+        ctx.check()
+        rows.append({"head": {"identity": "RGB", "yuv": "YUV (BT.601)", "ycocg": "YCoCg"}[colour],
+                     "loss_last": float(losses[-50:].mean().item()), "quality": nif_quality(g, sky, dev)})
+    print(json.dumps({"metric": "NIF colour-space study: quality against the sky", "n_gpus": 1, "train_steps": steps,
+                      "higher_is_better": True, "unit": "dB / log-RMSE",
+                      "config": {"nif": "F=64, 3x FC-128, Adam lr 1e-3, batch 2^16",
+                                 "train_gemms": args.train_precision, "sky": "procedural 2048x1024"},
+                      "rows": rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -874,9 +912,13 @@ def main():
     ap.add_argument("--no-bias", action="store_true", help="C5: skip the bias measurement against the 4096-spp render")
     ap.add_argument("--nif-sweep", action="store_true",
                     help="NIF size sweep (hidden width and depth vs quality, evaluation and path rate); one JSON line")
+    ap.add_argument("--colour-sweep", action="store_true",
+                    help="NIF colour-space study (RGB / YUV / YCoCg heads); one JSON line")
     args = ap.parse_args()
     if args.nif_sweep:
         return bench_nif_sweep(args)
+    if args.colour_sweep:
+        return bench_colour_sweep(args)
     if args.impl == "reference":
         return bench_reference(args)
     if args.workload == "C5":

@@ -335,6 +335,8 @@ def random_triangles_scene(n_tri: int, seed: int = 0, n_spheres: int = 0, n_quad
 YUV_TO_RGB_BT601 = np.array([[1.0, 0.0, 1.13983],
                              [1.0, -0.39465, -0.58060],
                              [1.0, 2.03211, 0.0]], np.float32)
+# YCoCg -> RGB (R = Y + Co - Cg, G = Y + Cg, B = Y - Co - Cg): the network's three outputs are (Y, Co, Cg)
+YCOCG_TO_RGB = np.array([[1.0, 1.0, -1.0], [1.0, 0.0, 1.0], [1.0, -1.0, -1.0]], np.float32)
 
 
 def nif_init(n_freq: int = 64, hidden: int = 128, n_hidden_layers: int = 3, sigma: float = 10.0,
@@ -349,7 +351,12 @@ def nif_init(n_freq: int = 64, hidden: int = 128, n_hidden_layers: int = 3, sigm
         fan_in, fan_out = dims[i], dims[i + 1]
         W.append(rng.normal(0.0, 1.0 / math.sqrt(fan_in), size=(fan_out, fan_in)).astype(np.float32))
         b.append(np.zeros((fan_out,), np.float32))
-    M = np.eye(3, dtype=np.float32) if colour == "identity" else YUV_TO_RGB_BT601.copy()
+    if colour == "identity":
+        M = np.eye(3, dtype=np.float32)
+    elif colour == "ycocg":
+        M = YCOCG_TO_RGB.copy()
+    else:
+        M = YUV_TO_RGB_BT601.copy()
     return NIF(B, W, b, M)
 
 

@@ -163,3 +163,14 @@ def test_training_reduces_loss():
     o = O.Nif(nif)
     losses = o.train(sky, seed=0, steps=400, batch=128, lr=1e-2)
     assert losses[-20:].mean() < 0.75 * losses[:5].mean()
+
+
+def test_ycocg_head_inverts_the_forward_transform():
+    """The YCoCg head matrix maps (Y, Co, Cg) = (R/4 + G/2 + B/4, R/2 - B/2,
+    -R/4 + G/2 - B/4) back to RGB exactly."""
+    rgb = np.random.default_rng(3).uniform(-2, 2, (100, 3))
+    R, G, B = rgb.T
+    ycocg = np.stack([R / 4 + G / 2 + B / 4, R / 2 - B / 2, -R / 4 + G / 2 - B / 4], 1)
+    back = ycocg @ I.YCOCG_TO_RGB.astype(np.float64).T
+    assert np.allclose(back, rgb, atol=1e-12)
+    assert np.array_equal(I.nif_init(colour="ycocg").M, I.YCOCG_TO_RGB)
