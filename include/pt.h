@@ -226,6 +226,18 @@ PT_API pt_status pt_nif_loss_grad(pt_ctx* ctx, pt_nif* nif, int64_t n, const flo
 /* Rendering (Section 3.1: paths without light sampling; radiance gathered   */
 /* at emitters and at escapes, where the NIF is queried; Section 3.3).       */
 /* ------------------------------------------------------------------------ */
+/* Scheduling of a chunk's paths (Section 3.1).  Both schedules compute the
+   same paths bit for bit (same Philox counters, traversal and shading); only
+   the order of the NIF escape and cache query queues differs.
+   WAVEFRONT: one traversal and one shading launch per vertex, with compacted
+   queues between vertices (throughput for large chunks).
+   PATHS: one launch in which each thread follows whole paths (latency for
+   chunks that fit in one resident wave: a call pays for its slowest path once
+   instead of for the slowest ray of every vertex).
+   AUTO: PATHS when the chunk fits in one resident wave of the path kernel,
+   else WAVEFRONT. */
+typedef enum { PT_SCHED_AUTO = 0, PT_SCHED_WAVEFRONT = 1, PT_SCHED_PATHS = 2 } pt_schedule;
+
 typedef struct pt_render_cfg {
     int32_t width, height;     /* image size; pixel index = y * width + x */
     int32_t spp;               /* samples (paths) per pixel */
@@ -237,6 +249,7 @@ typedef struct pt_render_cfg {
     int64_t chunk_slots;       /* paths per wavefront chunk; 0 = automatic; rounded to whole samples */
     int32_t first_sample;      /* sample index of the first path per pixel (Philox counter word 1 =
                                   first_sample + s): disjoint ranges render independent sample sets */
+    int32_t schedule;          /* pt_schedule: how the paths of a chunk are scheduled (same results) */
 } pt_render_cfg;
 
 /* Render the image: d_image [height][width][3] float, the mean over spp
@@ -262,6 +275,11 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* scene, const pt_n
    k, counts[max_depth] = NIF evaluations; with n >= max_depth + 2,
    counts[max_depth + 1] = radiance-cache queries (pt_render_cached). */
 PT_API pt_status pt_last_render_counts(pt_ctx* ctx, int64_t* counts, int32_t n);
+
+/* Schedule the last render's last chunk ran with: PT_SCHED_WAVEFRONT or
+   PT_SCHED_PATHS (PT_SCHED_AUTO before the first render).  A replayed
+   render reports the schedule it was captured with, which is the same. */
+PT_API pt_status pt_last_render_schedule(pt_ctx* ctx, int32_t* schedule);
 
 /* Traversal work of the last render (valid after pt_check): work[0] BVH
    node fetches (each tests the two child boxes), work[1] sphere, work[2]
@@ -407,7 +425,8 @@ PT_API pt_status pt_render_cached(pt_ctx* ctx, const pt_scene* scene, const pt_n
    GPU work overlaps race: serialise them on one stream.  d_err (nullable,
    caller-owned device word) receives the PT_ERR_* bits the kernels set;
    without it they are discarded.  No context is needed; failures are
-   reported by the return code only. */
+   reported by the return code only.  It always runs the wavefront schedule
+   (cfg->schedule is not read; the image is the same either way). */
 PT_API pt_status pt_render_noalloc(const pt_scene* scene, const pt_nif* nif, const pt_render_cfg* cfg,
                                    float* d_image, uint32_t* d_err, void* stream);
 

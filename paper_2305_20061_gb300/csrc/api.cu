@@ -20,6 +20,7 @@ using namespace ptk;
 struct pt_ctx {
     int device = 0;
     int sm_count = 0;
+    int paths_threads[2] = {0, 0};   // resident threads of the path kernel (packed, decoded nodes)
     std::string last_error;
     uint32_t* d_err = nullptr;
     // wavefront scratch
@@ -33,6 +34,7 @@ struct pt_ctx {
     float* cache_rows = nullptr;           // radiance-cache query rows [cache_cap][16]
     uint32_t cache_cap = 0;
     int last_depth = 0;
+    int last_schedule = PT_SCHED_AUTO;    // schedule the last render's last chunk ran with
     // kernel timing (pt_profile_enable)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;      // pairs: start, stop
@@ -256,6 +258,7 @@ pt_status check_cfg(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, const
     if ((int64_t)cfg->width * cfg->height > (1ll << 31)) return fail(ctx, PT_EINVAL, "image too large");
     if (cfg->rr && cfg->rr_start < 1) return fail(ctx, PT_EINVAL, "rr_start must be >= 1");
     if (cfg->first_sample < 0) return fail(ctx, PT_EINVAL, "first_sample must be >= 0");
+    if (cfg->schedule < PT_SCHED_AUTO || cfg->schedule > PT_SCHED_PATHS) return fail(ctx, PT_EINVAL, "unknown schedule");
     if (scene->dev.env_is_nif && !nif) return fail(ctx, PT_EINVAL, "scene environment is a NIF but no NIF was given");
     if (cfg->precision != PT_FP32 && cfg->precision != PT_BF16 && cfg->precision != PT_FP8E4M3)
         return fail(ctx, PT_EINVAL, "unknown precision");
@@ -335,6 +338,10 @@ PT_API pt_status pt_create(pt_ctx** out, int device)
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->stats, kStats * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, kStats * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_first_sample, sizeof(uint32_t));
+    if (e == cudaSuccess) {
+        ctx->paths_threads[0] = paths_resident_threads(false, ctx->sm_count);
+        ctx->paths_threads[1] = paths_resident_threads(true, ctx->sm_count);
+    }
     if (e != cudaSuccess) {
         cudaFree(ctx->d_err);
         cudaFree(ctx->counters);
@@ -1162,6 +1169,14 @@ PT_API pt_status pt_train_cache(pt_ctx* ctx, const pt_scene* sc, const pt_nif* n
 // cache_vertex; rec_vertex > 0 writes vertex records to d_rec.
 // The launch sequence of one render (no host synchronisation, no allocation):
 // recorded once into a CUDA graph and replayed when the same render repeats.
+// Schedule of a chunk of n paths: the path-per-thread kernel when asked for,
+// or (automatic) when the chunk fits in one resident wave of it.
+static bool use_paths(const pt_ctx* ctx, const pt_scene* sc, const pt_render_cfg* cfg, int64_t n)
+{
+    const int resident = ctx->paths_threads[sc->dev.wnodes ? 1 : 0];
+    return cfg->schedule == PT_SCHED_PATHS || (cfg->schedule == PT_SCHED_AUTO && resident > 0 && n <= resident);
+}
+
 static pt_status render_launches(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
                                  const pt_cache* cache, int cache_vertex, int rec_vertex, float* d_rec, int64_t n_pix,
                                  const int64_t* d_pixels, float* d_pixel_rgb, float* d_slot_rgb, int32_t* d_hit_ids,
@@ -1209,7 +1224,13 @@ static pt_status render_launches(pt_ctx* ctx, const pt_scene* sc, const pt_nif* 
         bp.n_chunk = (uint32_t)n;
         // with a cache no path outlives its cache vertex
         const int k_end = cache ? std::min(cfg->max_depth, cache_vertex) : cfg->max_depth;
-        for (int k = 1; k <= k_end; ++k) {
+        const bool per_path = use_paths(ctx, sc, cfg, n);
+        if (per_path) {
+            bp.k = 1;
+            const int resident = ctx->paths_threads[sc->dev.wnodes ? 1 : 0];
+            PT_CUDA(timed(ctx, PT_KIND_TRACE, s, [&] { return launch_paths(bp, resident, s); }));
+        }
+        for (int k = 1; k <= k_end && !per_path; ++k) {
             bp.k = k;
             bp.qin = ctx->q[(k + 1) & 1];
             bp.qout = ctx->q[k & 1];
@@ -1251,7 +1272,7 @@ static pt_status render_launches(pt_ctx* ctx, const pt_scene* sc, const pt_nif* 
 // The sample offset is not in it: it is a device word written per call.
 struct GraphKey {
     uint64_t sc_uid, nf_uid, nf_version, cache_uid, scratch_gen;
-    int32_t width, height, spp, max_depth, rr, rr_start, precision, cache_vertex, rec_vertex;
+    int32_t width, height, spp, max_depth, rr, rr_start, precision, cache_vertex, rec_vertex, schedule;
     uint32_t seed, cache_cap;
     int64_t chunk, n_pix;
     const void* ptrs[5];   // d_rec, d_pixels, d_pixel_rgb, d_slot_rgb, d_hit_ids
@@ -1294,6 +1315,8 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
         if (st != PT_OK) return st;
     }
     ctx->last_depth = cfg->max_depth;
+    ctx->last_schedule = use_paths(ctx, sc, cfg, n_slots - ((n_slots + chunk - 1) / chunk - 1) * chunk)
+                             ? PT_SCHED_PATHS : PT_SCHED_WAVEFRONT;
     PT_CUDA(launch_set_u32(ctx->d_first_sample, first_sample, s));
     auto direct = [&](cudaStream_t st_) {
         return render_launches(ctx, sc, nf, cfg, cache, cache_vertex, rec_vertex, d_rec, n_pix, d_pixels, d_pixel_rgb,
@@ -1309,7 +1332,7 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
     key.scratch_gen = ctx->scratch_gen;
     key.width = cfg->width; key.height = cfg->height; key.spp = cfg->spp; key.max_depth = cfg->max_depth;
     key.rr = cfg->rr; key.rr_start = cfg->rr_start; key.precision = cfg->precision;
-    key.cache_vertex = cache_vertex; key.rec_vertex = rec_vertex;
+    key.cache_vertex = cache_vertex; key.rec_vertex = rec_vertex; key.schedule = cfg->schedule;
     key.seed = cfg->seed; key.cache_cap = ctx->cache_cap;
     key.chunk = chunk; key.n_pix = n_pix;
     key.ptrs[0] = d_rec; key.ptrs[1] = d_pixels; key.ptrs[2] = d_pixel_rgb; key.ptrs[3] = d_slot_rgb;
@@ -1390,6 +1413,13 @@ PT_API pt_status pt_render(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, co
 {
     if (!d_image) return fail(ctx, PT_EINVAL, "null image");
     return pt_render_pixels(ctx, sc, nf, cfg, 0, nullptr, d_image, nullptr, nullptr, stream);
+}
+
+PT_API pt_status pt_last_render_schedule(pt_ctx* ctx, int32_t* schedule)
+{
+    if (!ctx || !schedule) return fail(ctx, PT_EINVAL, "bad argument");
+    *schedule = ctx->last_schedule;
+    return PT_OK;
 }
 
 PT_API pt_status pt_last_render_work(pt_ctx* ctx, int64_t* work, int32_t n)

@@ -248,6 +248,145 @@ __global__ void __launch_bounds__(256, PT_TRACE_MIN_BLOCKS) k_trace(const Bounce
     }
 }
 
+// Lanes that arrive here together take consecutive slots of a queue with one
+// atomic; returns this lane's slot.
+__device__ __forceinline__ uint32_t active_append(uint32_t* counter)
+{
+    const unsigned m = __activemask();
+    const uint32_t lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if ((int)lane == leader) base = atomicAdd(counter, (uint32_t)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    return base + __popc(m & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ void push_escape(const BounceParams& p, uint32_t ei, const PathState& s, float eu, float ev)
+{
+    if (ei < p.cap) {
+        float2* dst = reinterpret_cast<float2*>(p.esc + ei);
+        dst[0] = make_float2(__uint_as_float(s.slot), eu);
+        dst[1] = make_float2(ev, s.tp.x);
+        dst[2] = make_float2(s.tp.y, s.tp.z);
+    } else {
+        atomicOr(p.err, PT_ERR_QUEUE_OVERFLOW);
+    }
+}
+
+struct VertexOut {
+    bool survive, escape_nif;
+    float eu, ev;
+};
+
+// Shading of path vertex k given its closest hit h (Section 3.1): the hit
+// record, the record row and the cache query at their vertices, emission, the
+// environment or the NIF escape (Section 3.3), BSDF sampling of the next
+// direction with the Philox words of (pixel, sample, k) and Russian roulette.
+// A path that ends here has its radiance stored, unless a later kernel stores
+// it (cache query; NIF escape without emitters); a surviving path continues
+// from s.o along s.d.  Shared by the wavefront step and the path-per-thread
+// kernel, which therefore compute the same paths.
+__device__ __forceinline__ VertexOut shade_vertex(const BounceParams& p, int k, PathState& s, uint32_t pix,
+                                                  uint32_t smp, Hit h)
+{
+    VertexOut v{false, false, 0.f, 0.f};
+    if (p.hit_ids) p.hit_ids[(p.chunk_first + s.slot) * (uint64_t)p.max_depth + (k - 1)] = h.prim;
+    if (h.prim < 0) {
+        if (p.sc.env_is_nif) {
+            // Section 3.3: direction -> equirect (u, v), shaded later by the NIF
+            v.eu = 0.5f + atan2f(s.d.x, -s.d.z) * (0.5f / kPi);
+            v.ev = acosf(fminf(1.f, fmaxf(-1.f, s.d.y))) * (1.f / kPi);
+            v.escape_nif = true;
+            // without emitters the NIF kernel stores the path's whole radiance itself
+            if (p.sc.has_emission) store_L(p.slot_L, s.slot, s.L, p.err);
+        } else {
+            s.L = s.L + s.tp * f3(p.sc.env[0], p.sc.env[1], p.sc.env[2]);
+            store_L(p.slot_L, s.slot, s.L, p.err);
+        }
+        return v;
+    }
+    const float3 hp = s.o + s.d * h.t;
+    const int32_t mat = __ldg(&p.sc.prim_mat[h.prim]);
+    bool cache_q = false;
+    if (p.rec_vertex == k || p.cache_vertex == k) {
+        // state at this vertex: position, direction to the previous vertex, normal facing it,
+        // throughput reaching it and radiance gathered before it
+        const float3 ng0 = geometric_normal(p.sc, (uint32_t)h.prim, hp);
+        const float3 nf = dot3(ng0, s.d) < 0.f ? ng0 : ng0 * -1.f;
+        float* row = nullptr;
+        float last = 1.f;   // record: valid
+        if (p.rec_vertex == k) row = p.rec + 16 * (p.chunk_first + s.slot);
+        if (p.cache_vertex == k) {
+            // the path ends here; its query row goes to the cache queue
+            cache_q = true;
+            const uint32_t ci = active_append(p.cache_count);
+            if (ci < p.cap) row = p.cache_rows + 16 * (size_t)ci;
+            else atomicOr(p.err, PT_ERR_QUEUE_OVERFLOW);
+            last = __uint_as_float(s.slot);
+        }
+        if (row) {
+            float4* r = reinterpret_cast<float4*>(row);
+            r[0] = make_float4(hp.x, hp.y, hp.z, -s.d.x);
+            r[1] = make_float4(-s.d.y, -s.d.z, nf.x, nf.y);
+            r[2] = make_float4(nf.z, s.tp.x, s.tp.y, s.tp.z);
+            r[3] = make_float4(s.L.x, s.L.y, s.L.z, last);
+        }
+    }
+    if (p.sc.has_emission && !cache_q) {
+        const float4 m1 = __ldg(&p.sc.mat[2 * mat + 1]);
+        s.L = s.L + s.tp * f3(m1.y, m1.z, m1.w);
+    }
+    bool alive = k < p.max_depth && !cache_q;
+    if (alive) {
+        const uint4 w = philox4x32_10(make_uint4(pix, smp, (uint32_t)k, 0u), p.seed, 0u);
+        const float3 ng = geometric_normal(p.sc, (uint32_t)h.prim, hp);
+        float3 wi, wt;
+        alive = sample_bsdf(p.sc, mat, s.d, ng, u01(w.x), u01(w.y), u01(w.z), wi, wt);
+        if (alive) {
+            s.tp = s.tp * wt;
+            if (p.rr && k >= p.rr_start) {
+                const float q = fminf(1.f, fmaxf(s.tp.x, fmaxf(s.tp.y, s.tp.z)));
+                if (u01(w.w) < q) s.tp = s.tp * (1.f / q);
+                else alive = false;
+            }
+        }
+        if (alive) {
+            const float eps = 1e-4f * fmaxf(1.f, fmaxf(fabsf(hp.x), fmaxf(fabsf(hp.y), fabsf(hp.z))));
+            const float3 off = dot3(wi, ng) > 0.f ? ng : ng * -1.f;
+            s.o = hp + off * eps;
+            s.d = wi;
+        }
+    }
+    if (alive) v.survive = true;
+    else if (!cache_q) store_L(p.slot_L, s.slot, s.L, p.err);   // a cache query writes it later
+    return v;
+}
+
+__device__ __forceinline__ void camera_ray(const BounceParams& p, uint32_t pix, uint32_t smp, PathState& s)
+{
+    const uint4 w = philox4x32_10(make_uint4(pix, smp, 0u, 0u), p.seed, 0u);
+    s.o = f3(p.sc.eye[0], p.sc.eye[1], p.sc.eye[2]);
+    s.d = camera_dir(p.sc, p.W, p.H, pix, u01(w.x), u01(w.y));
+    s.tp = f3(1.f, 1.f, 1.f);
+    s.L = f3(0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ void add_work(const BounceParams& p, Work work)
+{
+    for (int off = 16; off > 0; off >>= 1) {
+        work.nodes += __shfl_down_sync(0xFFFFFFFFu, work.nodes, off);
+        work.sph += __shfl_down_sync(0xFFFFFFFFu, work.sph, off);
+        work.quad += __shfl_down_sync(0xFFFFFFFFu, work.quad, off);
+        work.tri += __shfl_down_sync(0xFFFFFFFFu, work.tri, off);
+    }
+    if ((threadIdx.x & 31) == 0 && p.work && work.nodes + work.sph + work.quad + work.tri) {
+        atomicAdd(&p.work[0], (unsigned long long)work.nodes);
+        atomicAdd(&p.work[1], (unsigned long long)work.sph);
+        atomicAdd(&p.work[2], (unsigned long long)work.quad);
+        atomicAdd(&p.work[3], (unsigned long long)work.tri);
+    }
+}
+
 // One wavefront step at vertex k for every ray of the input queue: shading of
 // the hits k_trace found, next-bounce sampling and compaction.
 __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
@@ -266,11 +405,7 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
             if (p.k == 1) {
                 s.slot = i;
                 slot_to_pixel(p, i, pix, smp);
-                const uint4 w = philox4x32_10(make_uint4(pix, smp, 0u, 0u), p.seed, 0u);
-                s.o = f3(p.sc.eye[0], p.sc.eye[1], p.sc.eye[2]);
-                s.d = camera_dir(p.sc, p.W, p.H, pix, u01(w.x), u01(w.y));
-                s.tp = f3(1.f, 1.f, 1.f);
-                s.L = f3(0.f, 0.f, 0.f);
+                camera_ray(p, pix, smp, s);
             } else {
                 const float4 o = p.qin.o[i], d = p.qin.d[i], tp = p.qin.tp[i];
                 s.o = f3(o.x, o.y, o.z);
@@ -286,90 +421,15 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
                 slot_to_pixel(p, s.slot, pix, smp);
             }
         }
-        bool survive = false, escape_nif = false, cache_q = false;
-        float eu = 0.f, ev = 0.f;
+        VertexOut v{false, false, 0.f, 0.f};
         if (active) {
             ++traced;
             const int2 hv = p.hits[i];
-            const Hit h{__int_as_float(hv.x), hv.y};
-            if (p.hit_ids) p.hit_ids[(p.chunk_first + s.slot) * (uint64_t)p.max_depth + (p.k - 1)] = h.prim;
-            if (h.prim < 0) {
-                if (p.sc.env_is_nif) {
-                    // Section 3.3: direction -> equirect (u, v), shaded later by the NIF
-                    eu = 0.5f + atan2f(s.d.x, -s.d.z) * (0.5f / kPi);
-                    ev = acosf(fminf(1.f, fmaxf(-1.f, s.d.y))) * (1.f / kPi);
-                    escape_nif = true;
-                    // without emitters the NIF kernel stores the path's whole radiance itself
-                    if (p.sc.has_emission) store_L(p.slot_L, s.slot, s.L, p.err);
-                } else {
-                    s.L = s.L + s.tp * f3(p.sc.env[0], p.sc.env[1], p.sc.env[2]);
-                    store_L(p.slot_L, s.slot, s.L, p.err);
-                }
-            } else {
-                const float3 hp = s.o + s.d * h.t;
-                const int32_t mat = __ldg(&p.sc.prim_mat[h.prim]);
-                if (p.rec_vertex == p.k || p.cache_vertex == p.k) {
-                    // state at this vertex: position, direction to the previous vertex, normal facing it,
-                    // throughput reaching it and radiance gathered before it
-                    const float3 ng0 = geometric_normal(p.sc, (uint32_t)h.prim, hp);
-                    const float3 nf = dot3(ng0, s.d) < 0.f ? ng0 : ng0 * -1.f;
-                    float* row = nullptr;
-                    float last = 1.f;   // record: valid
-                    if (p.rec_vertex == p.k) row = p.rec + 16 * (p.chunk_first + s.slot);
-                    if (p.cache_vertex == p.k) {
-                        // the path ends here; its query row goes to the cache queue (aggregated over the
-                        // lanes that arrive together)
-                        cache_q = true;
-                        const unsigned m = __activemask();
-                        const int leader = __ffs(m) - 1;
-                        uint32_t base = 0;
-                        if ((int)lane == leader) base = atomicAdd(p.cache_count, (uint32_t)__popc(m));
-                        base = __shfl_sync(m, base, leader);
-                        const uint32_t ci = base + __popc(m & ((1u << lane) - 1u));
-                        if (ci < p.cap) row = p.cache_rows + 16 * (size_t)ci;
-                        else atomicOr(p.err, PT_ERR_QUEUE_OVERFLOW);
-                        last = __uint_as_float(s.slot);
-                    }
-                    if (row) {
-                        float4* r = reinterpret_cast<float4*>(row);
-                        r[0] = make_float4(hp.x, hp.y, hp.z, -s.d.x);
-                        r[1] = make_float4(-s.d.y, -s.d.z, nf.x, nf.y);
-                        r[2] = make_float4(nf.z, s.tp.x, s.tp.y, s.tp.z);
-                        r[3] = make_float4(s.L.x, s.L.y, s.L.z, last);
-                    }
-                }
-                if (p.sc.has_emission && !cache_q) {
-                    const float4 m1 = __ldg(&p.sc.mat[2 * mat + 1]);
-                    s.L = s.L + s.tp * f3(m1.y, m1.z, m1.w);
-                }
-                bool alive = p.k < p.max_depth && !cache_q;
-                if (alive) {
-                    const uint4 w = philox4x32_10(make_uint4(pix, smp, (uint32_t)p.k, 0u), p.seed, 0u);
-                    const float3 ng = geometric_normal(p.sc, (uint32_t)h.prim, hp);
-                    float3 wi, wt;
-                    alive = sample_bsdf(p.sc, mat, s.d, ng, u01(w.x), u01(w.y), u01(w.z), wi, wt);
-                    if (alive) {
-                        s.tp = s.tp * wt;
-                        if (p.rr && p.k >= p.rr_start) {
-                            const float q = fminf(1.f, fmaxf(s.tp.x, fmaxf(s.tp.y, s.tp.z)));
-                            if (u01(w.w) < q) s.tp = s.tp * (1.f / q);
-                            else alive = false;
-                        }
-                    }
-                    if (alive) {
-                        const float eps = 1e-4f * fmaxf(1.f, fmaxf(fabsf(hp.x), fmaxf(fabsf(hp.y), fabsf(hp.z))));
-                        const float3 off = dot3(wi, ng) > 0.f ? ng : ng * -1.f;
-                        s.o = hp + off * eps;
-                        s.d = wi;
-                    }
-                }
-                if (alive) survive = true;
-                else if (!cache_q) store_L(p.slot_L, s.slot, s.L, p.err);   // a cache query writes it later
-            }
+            v = shade_vertex(p, p.k, s, pix, smp, Hit{__int_as_float(hv.x), hv.y});
         }
         // compaction: survivors into the next queue, escapes into the NIF queue
-        const uint32_t qi = warp_append(survive, p.count_out);
-        if (survive) {
+        const uint32_t qi = warp_append(v.survive, p.count_out);
+        if (v.survive) {
             if (qi < p.cap) {
                 p.qout.o[qi] = make_float4(s.o.x, s.o.y, s.o.z, __uint_as_float(s.slot));
                 p.qout.d[qi] = make_float4(s.d.x, s.d.y, s.d.z, 0.f);
@@ -379,25 +439,53 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
                 atomicOr(p.err, PT_ERR_QUEUE_OVERFLOW);
             }
         }
-        const uint32_t ei = warp_append(escape_nif, p.esc_count);
-        if (escape_nif) {
-            if (ei < p.cap) {
-                EscapeRec r;
-                r.slot = s.slot; r.u = eu; r.v = ev; r.tr = s.tp.x; r.tg = s.tp.y; r.tb = s.tp.z;
-                float2* dst = reinterpret_cast<float2*>(p.esc + ei);
-                dst[0] = make_float2(__uint_as_float(r.slot), r.u);
-                dst[1] = make_float2(r.v, r.tr);
-                dst[2] = make_float2(r.tg, r.tb);
-            } else {
-                atomicOr(p.err, PT_ERR_QUEUE_OVERFLOW);
-            }
-        }
+        const uint32_t ei = warp_append(v.escape_nif, p.esc_count);
+        if (v.escape_nif) push_escape(p, ei, s, v.eu, v.ev);
     }
     // k_trace of this vertex has finished: its claim counter starts the next vertex at zero
     if (blockIdx.x == 0 && threadIdx.x == 0) *p.fetch = 0;
     // per-vertex ray count, one atomic per warp
     for (int off = 16; off > 0; off >>= 1) traced += __shfl_down_sync(0xFFFFFFFFu, traced, off);
     if (lane == 0 && traced) atomicAdd(&p.stats[p.k - 1], (unsigned long long)traced);
+}
+
+// Path-per-thread schedule for wavefronts smaller than one resident wave of
+// threads: each thread follows its paths through every vertex in one launch
+// (traversal, then shade_vertex), so a call pays for its slowest path once
+// instead of for the slowest ray of every vertex, with no queues between
+// vertices.  Same Philox counters, records, NIF escape queue and cache queue
+// as the wavefront schedule; only the order of the queues differs, and every
+// consumer of a queue entry addresses the path by its slot.
+template <bool kWide>
+__global__ void __launch_bounds__(256) k_paths(const BounceParams p)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const int k_end = p.cache_vertex ? min(p.max_depth, p.cache_vertex) : p.max_depth;
+    Work work;
+    uint32_t stack_ref[kStackSize];
+    float stack_t[kStackSize];
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < p.n_chunk; j += gridDim.x * blockDim.x) {
+        PathState s;
+        uint32_t pix, smp;
+        s.slot = j;
+        slot_to_pixel(p, j, pix, smp);
+        camera_ray(p, pix, smp, s);
+        for (int k = 1; k <= k_end; ++k) {
+            {   // rays traced at vertex k: one atomic per group of lanes at the same vertex
+                const unsigned m = __match_any_sync(__activemask(), k);
+                if ((int)lane == __ffs(m) - 1) atomicAdd(&p.stats[k - 1], (unsigned long long)__popc(m));
+            }
+            Trav t;
+            if (!trav_init(p.sc, s.o, s.d, t, work)) {
+                while (!trav_step<kWide>(p.sc, t, stack_ref, stack_t, p.err, work)) {
+                }
+            }
+            const VertexOut v = shade_vertex(p, k, s, pix, smp, t.h);
+            if (v.escape_nif) push_escape(p, active_append(p.esc_count), s, v.eu, v.ev);
+            if (!v.survive) break;
+        }
+    }
+    add_work(p, work);
 }
 
 // image[i] (+)= sum over the chunk's samples in sample order; scaled at the end
@@ -474,6 +562,30 @@ cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s)
     if (p.sc.wnodes) k_trace<true><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
     else k_trace<false><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
     k_bounce<<<sm_count * 8, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+int paths_resident_threads(bool wide, int sm_count)
+{
+    int per_sm = 0;
+    const cudaError_t e = wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<true>, 256, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<false>, 256, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * sm_count * 256;
+}
+
+cudaError_t launch_paths(const BounceParams& p, int resident_threads, cudaStream_t s)
+{
+    // one thread per path while they fit in one resident wave, grid-stride beyond
+    const int cap = resident_threads;
+    int64_t blocks = ((int64_t)p.n_chunk + 255) / 256;
+    if (cap > 0 && blocks > cap / 256) blocks = cap / 256;
+    if (blocks < 1) blocks = 1;
+    if (p.sc.wnodes) k_paths<true><<<(int)blocks, 256, 0, s>>>(p);
+    else k_paths<false><<<(int)blocks, 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 

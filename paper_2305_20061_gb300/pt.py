@@ -51,7 +51,7 @@ class NifDesc(C.Structure):
 class RenderCfg(C.Structure):
     _fields_ = [("width", I32), ("height", I32), ("spp", I32), ("max_depth", I32), ("seed", U32),
                 ("rr", I32), ("rr_start", I32), ("precision", I32), ("chunk_slots", I64),
-                ("first_sample", I32)]
+                ("first_sample", I32), ("schedule", I32)]
 
 
 class TrainCfg(C.Structure):
@@ -115,6 +115,7 @@ def lib():
             "pt_profile_read": ([P, P, P, I32], I32),
             "pt_render_noalloc": ([P, P, P, P, P, P], I32),
             "pt_last_render_work": ([P, P, I32], I32),
+            "pt_last_render_schedule": ([P, P], I32),
             "pt_nif_set_params": ([P, P, P, P], I32),
             "pt_nif_fp8_scales": ([P, P], I32),
             "pt_train_nif": ([P, P, P, I32, I32, P, P, P], I32),
@@ -460,9 +461,14 @@ class Cache:
             self.h = None
 
 
-def make_cfg(cfg: I.RenderCfg, precision: str = "fp32", chunk_slots: int = 0, first_sample: int = 0) -> RenderCfg:
+# pt_schedule: automatic, one launch per vertex (wavefront), one launch per chunk (path per thread)
+SCHEDULES = {"auto": 0, "wavefront": 1, "paths": 2}
+
+
+def make_cfg(cfg: I.RenderCfg, precision: str = "fp32", chunk_slots: int = 0, first_sample: int = 0,
+             schedule: str = "auto") -> RenderCfg:
     return RenderCfg(cfg.width, cfg.height, cfg.spp, cfg.max_depth, cfg.seed, int(cfg.rr), cfg.rr_start,
-                     PRECISIONS[precision], int(chunk_slots), int(first_sample))
+                     PRECISIONS[precision], int(chunk_slots), int(first_sample), SCHEDULES[schedule])
 
 
 KINDS = ("trace", "nif", "reduce", "other", "cache")
@@ -482,11 +488,11 @@ def profile_read(ctx: Context) -> dict:
 
 def render(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderCfg, precision: str = "fp32",
            out: Optional[torch.Tensor] = None, chunk_slots: int = 0, first_sample: int = 0,
-           stream=None) -> torch.Tensor:
+           stream=None, schedule: str = "auto") -> torch.Tensor:
     """pt_render: returns the [H, W, 3] float32 image on the context's device."""
     if out is None:
         out = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=f"cuda:{ctx.device}")
-    c = make_cfg(cfg, precision, chunk_slots, first_sample)
+    c = make_cfg(cfg, precision, chunk_slots, first_sample, schedule)
     ctx._raise(lib().pt_render(ctx.h, scene.h, nif.h if nif is not None else None, C.byref(c), _dptr(out),
                                _stream(stream)))
     return out
@@ -494,14 +500,14 @@ def render(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderCfg, pre
 
 def render_pixels(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderCfg, pixels: Optional[torch.Tensor],
                   precision: str = "fp32", want_slots: bool = False, want_ids: bool = False, chunk_slots: int = 0,
-                  stream=None):
+                  stream=None, schedule: str = "auto"):
     """pt_render_pixels: (pixel_rgb [n,3], slot_rgb [spp,n,3] or None, hit_ids [spp,n,D] or None)."""
     dev = f"cuda:{ctx.device}"
     n = cfg.width * cfg.height if pixels is None else int(pixels.shape[0])
     pix = torch.empty((n, 3), dtype=torch.float32, device=dev)
     slots = torch.empty((cfg.spp, n, 3), dtype=torch.float32, device=dev) if want_slots else None
     ids = torch.empty((cfg.spp, n, cfg.max_depth), dtype=torch.int32, device=dev) if want_ids else None
-    c = make_cfg(cfg, precision, chunk_slots)
+    c = make_cfg(cfg, precision, chunk_slots, schedule=schedule)
     ctx._raise(lib().pt_render_pixels(ctx.h, scene.h, nif.h if nif is not None else None, C.byref(c), n,
                                       _dptr(pixels), _dptr(pix), _dptr(slots), _dptr(ids), _stream(stream)))
     return pix, slots, ids
@@ -510,7 +516,7 @@ def render_pixels(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderC
 def render_cached(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderCfg, pixels: Optional[torch.Tensor],
                   cache: Optional[Cache] = None, cache_vertex: int = 0, rec_vertex: int = 0, precision: str = "fp32",
                   want_slots: bool = False, want_ids: bool = False, chunk_slots: int = 0, first_sample: int = 0,
-                  out: Optional[torch.Tensor] = None, stream=None):
+                  out: Optional[torch.Tensor] = None, stream=None, schedule: str = "auto"):
     """pt_render_cached: (pixel_rgb [n,3], slot_rgb [spp,n,3] or None, records [spp,n,16] or None,
     hit_ids [spp,n,D] or None).  out (optional): preallocated pixel_rgb."""
     dev = f"cuda:{ctx.device}"
@@ -519,7 +525,7 @@ def render_cached(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderC
     slots = torch.empty((cfg.spp, n, 3), dtype=torch.float32, device=dev) if want_slots else None
     rec = torch.empty((cfg.spp, n, 16), dtype=torch.float32, device=dev) if rec_vertex else None
     ids = torch.empty((cfg.spp, n, cfg.max_depth), dtype=torch.int32, device=dev) if want_ids else None
-    c = make_cfg(cfg, precision, chunk_slots, first_sample)
+    c = make_cfg(cfg, precision, chunk_slots, first_sample, schedule)
     ctx._raise(lib().pt_render_cached(ctx.h, scene.h, nif.h if nif is not None else None,
                                       cache.h if cache is not None else None, cache_vertex, rec_vertex, C.byref(c), n,
                                       _dptr(pixels), _dptr(pix), _dptr(slots), _dptr(rec), _dptr(ids),
@@ -532,6 +538,13 @@ def last_render_counts(ctx: Context, max_depth: int, with_cache: bool = False) -
     out = np.zeros(max_depth + 1 + int(with_cache), np.int64)
     ctx._raise(lib().pt_last_render_counts(ctx.h, _np_ptr(out), len(out)))
     return out
+
+
+def last_render_schedule(ctx: Context) -> str:
+    """"wavefront" or "paths": how the last render's last chunk was scheduled."""
+    v = C.c_int32(0)
+    ctx._raise(lib().pt_last_render_schedule(ctx.h, C.byref(v)))
+    return {v_: k for k, v_ in SCHEDULES.items()}[v.value]
 
 
 def last_render_work(ctx: Context) -> dict:

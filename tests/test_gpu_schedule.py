@@ -1,0 +1,159 @@
+"""The two path schedules of a render chunk (Section 3.1) compute the same
+paths: the wavefront schedule (one traversal and one shading launch per
+vertex, compacted queues between them) and the path-per-thread schedule (one
+launch, each thread follows whole paths).  Per-path radiance, hit IDs,
+vertex records, ray and work counts agree bit for bit across scenes with
+spheres, quads and triangles, NIF and constant environments, emitters,
+Russian roulette, the BF16 NIF and the radiance cache; both agree with the
+FP64 oracle per path."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2305_20061_gb300 import inputs as I
+
+from parity_helpers import rel_rmse
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pt():
+    from paper_2305_20061_gb300 import build
+    build.build()
+    from paper_2305_20061_gb300 import pt as _pt
+    return _pt
+
+
+@pytest.fixture(scope="module")
+def ctx(pt):
+    return pt.Context(0)
+
+
+def _both(pt, ctx, fn):
+    """Run fn(schedule) for both schedules; also the traversal counters."""
+    out = {}
+    for sched in ("wavefront", "paths"):
+        r = fn(sched)
+        ctx.check()
+        out[sched] = [None if x is None else x.cpu().numpy() for x in r] + \
+                     [pt.last_render_counts(ctx, r[-1].shape[-1] if r[-1] is not None else 1),
+                      np.array(list(pt.last_render_work(ctx).values()))]
+    return out["wavefront"], out["paths"]
+
+
+SCENES = {
+    "box_nif": (lambda: I.make_scene("C1"), I.RenderCfg(48, 40, 3, 5), "nif"),
+    "spheres_nif": (lambda: I.spheres_scene(64), I.RenderCfg(40, 32, 2, 8), "nif"),
+    "heightfield_const": (lambda: I.heightfield_scene(32, n_spheres=8, env_const=[0.6, 0.7, 0.9]),
+                          I.RenderCfg(40, 32, 2, 6), None),
+    "furnace_emitting": (lambda: I.furnace_sphere_inside(0.5), I.RenderCfg(16, 12, 4, 7), None),
+    "box_rr": (lambda: I.make_scene("C1"), I.RenderCfg(48, 40, 3, 8, rr=True, rr_start=2), "nif"),
+}
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_schedules_bit_identical(pt, ctx, name):
+    make, cfg, env = SCENES[name]
+    sc = make()
+    s = pt.Scene(ctx, sc)
+    g = pt.Nif(ctx, I.nif_init()) if env == "nif" else None
+    a, b = _both(pt, ctx, lambda sched: pt.render_pixels(ctx, s, g, cfg, None, want_slots=True, want_ids=True,
+                                                         schedule=sched))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert a[-2][0] == cfg.width * cfg.height * cfg.spp   # every path traced its primary ray
+
+
+def test_schedules_bit_identical_bf16_nif(pt, ctx):
+    """Escapes shaded by the tensor-core NIF: each escape's result does not
+    depend on its place in the escape queue."""
+    s = pt.Scene(ctx, I.make_scene("C1"))
+    g = pt.Nif(ctx, I.nif_init(colour="yuv"))
+    cfg = I.RenderCfg(64, 48, 2, 4)
+    a, b = _both(pt, ctx, lambda sched: pt.render_pixels(ctx, s, g, cfg, None, precision="bf16", want_slots=True,
+                                                         want_ids=True, schedule=sched))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_schedules_bit_identical_cached_with_records(pt, ctx, precision):
+    """Records at vertex 1 and cache queries at vertex 2, on a pixel list."""
+    sc = I.make_scene("C1")
+    lo, hi = I.scene_bounds(sc)
+    c = I.cache_init(lo, hi, n_freq=12, hidden=64, n_hidden_layers=5, seed=9)
+    s, g, gc = pt.Scene(ctx, sc), pt.Nif(ctx, I.nif_init(colour="yuv")), pt.Cache(ctx, c)
+    cfg = I.RenderCfg(64, 64, 3, 5)
+    pixels = torch.from_numpy(np.arange(0, 64 * 64, 5, dtype=np.int64)).cuda()
+    a, b = _both(pt, ctx, lambda sched: pt.render_cached(ctx, s, g, cfg, pixels, cache=gc, cache_vertex=2,
+                                                         rec_vertex=1, precision=precision, want_slots=True,
+                                                         want_ids=True, schedule=sched))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_paths_schedule_beyond_one_wave_and_chunked(pt, ctx):
+    """More paths than the path kernel keeps resident (grid-stride), and
+    several chunks with a sample offset."""
+    s = pt.Scene(ctx, I.make_scene("C1"))
+    g = pt.Nif(ctx, I.nif_init())
+    cfg = I.RenderCfg(512, 384, 1, 3)
+    a = pt.render(ctx, s, g, cfg, schedule="wavefront").cpu().numpy()
+    b = pt.render(ctx, s, g, cfg, schedule="paths").cpu().numpy()
+    cfg2 = I.RenderCfg(96, 64, 6, 4)
+    c = pt.render(ctx, s, g, cfg2, chunk_slots=96 * 64 * 2, first_sample=5, schedule="wavefront").cpu().numpy()
+    d = pt.render(ctx, s, g, cfg2, chunk_slots=96 * 64 * 2, first_sample=5, schedule="paths").cpu().numpy()
+    ctx.check()
+    assert np.array_equal(a, b)
+    assert np.array_equal(c, d)
+
+
+@pytest.mark.parametrize("schedule", ["wavefront", "paths"])
+def test_each_schedule_matches_oracle_per_path(pt, ctx, schedule):
+    """Box scene with the FP32 NIF and roulette: per-path radiance against
+    the oracle, paths whose hit sequence differs (an FP32 vs FP64 decision
+    flipped) counted and bounded."""
+    sc, nif = I.make_scene("C1"), I.nif_init()
+    cfg = I.RenderCfg(40, 40, 2, 6, rr=True, rr_start=3)
+    s, g = pt.Scene(ctx, sc), pt.Nif(ctx, nif)
+    img, slots, ids = pt.render_pixels(ctx, s, g, cfg, None, want_slots=True, want_ids=True, schedule=schedule)
+    ctx.check()
+    r = O.render(O.Scene(sc), cfg, O.Nif(nif), want_slots=True, want_ids=True)
+    gslots = slots.cpu().numpy().transpose(1, 0, 2)
+    gids = ids.cpu().numpy().transpose(1, 0, 2)
+    same = np.all(gids == r["ids"], axis=2)
+    assert same.mean() >= 0.998
+    assert rel_rmse(gslots[same], r["slots"][same]) <= 1e-3
+    assert rel_rmse(img.cpu().numpy(), r["image"]) <= 2e-3
+
+
+def test_schedule_argument_checked(pt, ctx):
+    s = pt.Scene(ctx, I.make_scene("C1"))
+    g = pt.Nif(ctx, I.nif_init())
+    c = pt.make_cfg(I.RenderCfg(8, 8, 1, 2))
+    c.schedule = 3
+    out = torch.empty((8, 8, 3), dtype=torch.float32, device="cuda")
+    st = pt.lib().pt_render(ctx.h, s.h, g.h, ctypes.byref(c), pt._dptr(out), None)
+    assert st == pt.PT_EINVAL
+    ctx.check()
+
+
+def test_last_render_schedule_reported(pt, ctx):
+    """The automatic choice takes the path kernel for a chunk that fits one
+    resident wave; a replayed (graph-captured) render reports its own
+    schedule, not the one of the render before it."""
+    s = pt.Scene(ctx, I.make_scene("C1"))
+    g = pt.Nif(ctx, I.nif_init())
+    small = I.RenderCfg(16, 16, 1, 3)
+    for _ in range(3):   # first sight, capture, replay
+        pt.render(ctx, s, g, small)
+        assert pt.last_render_schedule(ctx) == "paths"
+        pt.render(ctx, s, g, small, schedule="wavefront")
+        assert pt.last_render_schedule(ctx) == "wavefront"
+    pt.render(ctx, s, g, I.RenderCfg(512, 384, 1, 2), schedule="paths")
+    assert pt.last_render_schedule(ctx) == "paths"
+    ctx.check()
