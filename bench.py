@@ -283,6 +283,11 @@ def train_env_nif(pt, ctx, gnif, nif, steps, dev, precision):
              "fwd_bwd_tflops": steps * batch * 3 * FLOP_PER_EVAL / (tms * 1e-3) / 1e12,
              "loss_first": float(losses[0].item()), "loss_last": float(losses[-50:].mean().item())}
     train["quality"] = nif_quality(gnif, sky, dev)
+    # what the network replaces: the sky as an FP32 texture, at the quality above
+    n_par = 2 * nif.n_freq + sum(W.size + b.size for W, b in zip(nif.W, nif.b))
+    train["vs_texture"] = {"texture_bytes": int(sky.numel() * 4), "nif_bytes_fp32": int(4 * n_par),
+                           "nif_bytes_bf16": int(2 * n_par),
+                           "compression_bf16": float(sky.numel() * 4 / (2 * n_par))}
     del sky
     params = gnif.get_params()
     p = 2 * nif.n_freq
@@ -694,7 +699,31 @@ def bench_c5(args):
                 "cached": f"frozen cache after {n_done} frames, {prec} NIF, 1024 spp (8 batches of 128)",
                 "reference_noise_rel_rmse": float(torch.sqrt(R_var.sum() / (R_mean ** 2).sum()))}
         bias.update(image_stats(X, R_mean, R_var))
-        del X, R_mean, R_var
+        del X
+
+        # equal time: one cached frame (its training step included in the time) against plain frames of
+        # about the same duration; each single frame's relative RMSE against the 4096-spp reference,
+        # averaged over 8 independent frames
+        def frame_rmse(render_one, n=8):
+            v = []
+            for i in range(n):
+                Y = render_one(i).double().reshape(H, W, 3)
+                v.append(float(torch.sqrt(((Y - R_mean) ** 2).sum() / (R_mean ** 2).sum())))
+            return float(np.mean(v))
+        spp_eq = max(1, int(round(spp * ms / plain[f"{prec}_ms"])))
+        cfg_eq = I.RenderCfg(W, H, spp_eq, cfg.max_depth, 0)
+        bias["equal_time"] = {
+            "cached": {"ms": ms, "spp": spp, "rel_rmse": frame_rmse(lambda i: pt.render_cached(
+                ctx, scene, gnif, cfg, None, cache=gc, cache_vertex=CACHE_VERTEX, precision=prec,
+                first_sample=3 * base + spp * i)[0])},
+            f"plain_{prec}": {"ms_est": plain[f"{prec}_ms"] * spp_eq / spp, "spp": spp_eq,
+                              "rel_rmse": frame_rmse(lambda i: pt.render(ctx, scene, gnif, cfg_eq, prec,
+                                                                         first_sample=4 * base + spp_eq * i))},
+            "plain_fp32_same_spp": {"ms": plain["fp32_ms"], "spp": spp,
+                                    "rel_rmse": frame_rmse(lambda i: pt.render(ctx, scene, gnif, cfg, "fp32",
+                                                                               first_sample=5 * base + spp * i))}}
+        ctx.check()
+        del R_mean, R_var
 
     # roofline of the dominant kernel kind inside the frame
     meas, which = peaks()

@@ -456,8 +456,11 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
 // vertices.  Same Philox counters, records, NIF escape queue and cache queue
 // as the wavefront schedule; only the order of the queues differs, and every
 // consumer of a queue entry addresses the path by its slot.
+// Small blocks spread a small chunk over every SM (a latency-bound launch
+// runs fastest with the fewest warps per SM).
+constexpr int kPathsBlock = 64;
 template <bool kWide>
-__global__ void __launch_bounds__(256) k_paths(const BounceParams p)
+__global__ void __launch_bounds__(kPathsBlock, 12) k_paths(const BounceParams p)
 {
     const uint32_t lane = threadIdx.x & 31;
     const int k_end = p.cache_vertex ? min(p.max_depth, p.cache_vertex) : p.max_depth;
@@ -568,24 +571,24 @@ cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s)
 int paths_resident_threads(bool wide, int sm_count)
 {
     int per_sm = 0;
-    const cudaError_t e = wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<true>, 256, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<false>, 256, 0);
+    const cudaError_t e = wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<true>, kPathsBlock, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<false>, kPathsBlock, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    return per_sm * sm_count * 256;
+    return per_sm * sm_count * kPathsBlock;
 }
 
 cudaError_t launch_paths(const BounceParams& p, int resident_threads, cudaStream_t s)
 {
     // one thread per path while they fit in one resident wave, grid-stride beyond
     const int cap = resident_threads;
-    int64_t blocks = ((int64_t)p.n_chunk + 255) / 256;
-    if (cap > 0 && blocks > cap / 256) blocks = cap / 256;
+    int64_t blocks = ((int64_t)p.n_chunk + kPathsBlock - 1) / kPathsBlock;
+    if (cap > 0 && blocks > cap / kPathsBlock) blocks = cap / kPathsBlock;
     if (blocks < 1) blocks = 1;
-    if (p.sc.wnodes) k_paths<true><<<(int)blocks, 256, 0, s>>>(p);
-    else k_paths<false><<<(int)blocks, 256, 0, s>>>(p);
+    if (p.sc.wnodes) k_paths<true><<<(int)blocks, kPathsBlock, 0, s>>>(p);
+    else k_paths<false><<<(int)blocks, kPathsBlock, 0, s>>>(p);
     return cudaGetLastError();
 }
 
