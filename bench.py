@@ -344,22 +344,24 @@ def bench_ours(args):
         ctx.check()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier()
+        k0 = pt.kernel_launches()
         for i in range(steps):
             flush.fill_(float(i))           # evict L2 between timed steps (not timed)
             ev[i][0].record(stream)
             pt.render(ctx, scene, gnif, cfg, prec, out=img, first_sample=first_sample)   # a CUDA-graph replay
             ev[i][1].record(stream)
         barrier()
+        kernels = pt.kernel_launches() - k0
         ctx.check()
         ms = R.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / steps, dev)
         prof = profiled_split(pt, ctx, lambda i: pt.render(ctx, scene, gnif, cfg, prec, out=img,
                                                            first_sample=first_sample), steps) if profile else None
-        return ms, prof
+        return ms, prof, kernels
 
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    ms, prof = timed_frames(rprec, args.steps, profile=True)
+    ms, prof, kernels = timed_frames(rprec, args.steps, profile=True)
     clocks = sampler.stop()
     counts = pt.last_render_counts(ctx, cfg.max_depth)
     work = pt.last_render_work(ctx)
@@ -376,7 +378,7 @@ def bench_ours(args):
     lowp = rprec if rprec != "fp32" else "bf16"
     ms_other, rel_rmse = None, None
     if uses_nif and not args.no_compare:
-        ms_other, _ = timed_frames(other, max(2, min(args.steps, 5)))
+        ms_other, _, _ = timed_frames(other, max(2, min(args.steps, 5)))
         a = pt.render(ctx, scene, gnif, cfg, lowp, first_sample=first_sample).double()
         b = pt.render(ctx, scene, gnif, cfg, "fp32", first_sample=first_sample).double()
         ctx.check()
@@ -488,7 +490,7 @@ def bench_ours(args):
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "scene_build_s": t_build, "bvh_nodes": scene.info()["n_nodes"], "bvh_depth": scene.info()["bvh_depth"],
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": int(sum(v[1] for v in prof.values())),
+            "gpu_launches": int(kernels),
         }
         if uses_nif:
             line.update({
@@ -624,12 +626,14 @@ def bench_c5(args):
     time.sleep(0.3)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
+    k0 = pt.kernel_launches()
     for i in range(args.steps):
         flush.fill_(float(i))           # evict L2 between timed frames (not timed)
         ev[i][0].record(stream)
         frame(args.warmup + i)          # renders replay the library's CUDA graphs
         ev[i][1].record(stream)
     barrier()
+    kernels = pt.kernel_launches() - k0
     clocks = sampler.stop()
     ctx.check()
     ms = R.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / args.steps, dev)
@@ -817,7 +821,7 @@ def bench_c5(args):
             "rays_per_render": rays, "cache_queries_per_render": queries,
             "nif_evals_per_render": int(counts[cfg.max_depth]),
             "scene_build_s": t_build, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": int(sum(v[1] for v in prof.values())), "nif_training": train,
+            "gpu_launches": int(kernels), "nif_training": train,
         }))
     if world > 1:
         dist.destroy_process_group()

@@ -276,6 +276,12 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* scene, const pt_n
    counts[max_depth + 1] = radiance-cache queries (pt_render_cached). */
 PT_API pt_status pt_last_render_counts(pt_ctx* ctx, int64_t* counts, int32_t n);
 
+/* Kernels this library has launched in this process (all contexts and
+   threads), each kernel of a replayed CUDA graph included: the difference
+   across a region of work is the number of the library's kernels it ran.
+   Library copies and memsets are not kernels and are not counted. */
+PT_API pt_status pt_kernel_launches(uint64_t* count);
+
 /* Schedule the last render's last chunk ran with: PT_SCHED_WAVEFRONT or
    PT_SCHED_PATHS (PT_SCHED_AUTO before the first render).  A replayed
    render reports the schedule it was captured with, which is the same. */

@@ -44,11 +44,21 @@ struct pt_ctx {
     uint64_t scratch_gen = 0;              // bumped whenever a scratch buffer moves
     uint32_t* d_first_sample = nullptr;    // the sample offset the bounce kernels read
     cudaStream_t cap_stream = nullptr;     // capture stream (captures record, nothing runs on it)
-    std::vector<std::pair<std::vector<unsigned char>, cudaGraphExec_t>> graphs;
+    struct CachedGraph {
+        std::vector<unsigned char> key;
+        cudaGraphExec_t exec;
+        unsigned long long kernels;   // kernels one replay launches
+    };
+    std::vector<CachedGraph> graphs;
     size_t graph_next = 0;
     std::vector<std::vector<unsigned char>> graph_seen;   // keys seen once (captured on their second use)
     size_t seen_next = 0;
 };
+
+namespace ptk {
+std::atomic<unsigned long long> g_kernels_launched{0};
+thread_local unsigned long long t_kernels_launched = 0;
+}  // namespace ptk
 
 // identities that are never reused (a graph key must not match a new object at a recycled address)
 std::atomic<uint64_t> g_next_uid{1};
@@ -360,7 +370,7 @@ PT_API void pt_destroy(pt_ctx* ctx)
     cudaSetDevice(ctx->device);
     free_scratch(ctx);
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
-    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.second);
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     cudaFree(ctx->d_err);
     cudaFree(ctx->counters);
@@ -1340,8 +1350,9 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
     std::vector<unsigned char> kb(sizeof key);
     std::memcpy(kb.data(), &key, sizeof key);
     for (auto& g : ctx->graphs)
-        if (g.first == kb) {
-            PT_CUDA(cudaGraphLaunch(g.second, s));
+        if (g.key == kb) {
+            PT_CUDA(cudaGraphLaunch(g.exec, s));
+            count_launch(g.kernels);
             return PT_OK;
         }
     // a render seen for the first time launches directly (one-off renders never pay for a capture)
@@ -1359,20 +1370,26 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
     // record the sequence on the capture stream (nothing runs there), instantiate, replay on `s`
     if (!ctx->cap_stream) PT_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const unsigned long long before = t_kernels_launched;
         const pt_status lst = direct(ctx->cap_stream);
+        // the launches of a capture only record kernels: they count when the graph is launched
+        const unsigned long long kernels = t_kernels_launched - before;
+        g_kernels_launched.fetch_sub(kernels, std::memory_order_relaxed);
+        t_kernels_launched = before;
         cudaGraph_t graph = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
         cudaGraphExec_t exec = nullptr;
         if (lst == PT_OK && ce == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
             cudaGraphDestroy(graph);
             if (ctx->graphs.size() < kMaxGraphs) {
-                ctx->graphs.emplace_back(kb, exec);
+                ctx->graphs.push_back({kb, exec, kernels});
             } else {
-                cudaGraphExecDestroy(ctx->graphs[ctx->graph_next].second);
-                ctx->graphs[ctx->graph_next] = {kb, exec};
+                cudaGraphExecDestroy(ctx->graphs[ctx->graph_next].exec);
+                ctx->graphs[ctx->graph_next] = {kb, exec, kernels};
                 ctx->graph_next = (ctx->graph_next + 1) % kMaxGraphs;
             }
             PT_CUDA(cudaGraphLaunch(exec, s));
+            count_launch(kernels);
             return PT_OK;
         }
         if (graph) cudaGraphDestroy(graph);
@@ -1413,6 +1430,13 @@ PT_API pt_status pt_render(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, co
 {
     if (!d_image) return fail(ctx, PT_EINVAL, "null image");
     return pt_render_pixels(ctx, sc, nf, cfg, 0, nullptr, d_image, nullptr, nullptr, stream);
+}
+
+PT_API pt_status pt_kernel_launches(uint64_t* count)
+{
+    if (!count) return PT_EINVAL;
+    *count = g_kernels_launched.load(std::memory_order_relaxed);
+    return PT_OK;
 }
 
 PT_API pt_status pt_last_render_schedule(pt_ctx* ctx, int32_t* schedule)

@@ -191,7 +191,7 @@ cudaError_t launch(const EvalParams& p, int sm_count, cudaStream_t s)
     cudaError_t e = cudaFuncSetAttribute(k_cache_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (p.cap + kRows - 1) / kRows;
-    k_cache_eval<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, sm_count)), kThreads, bytes, s>>>(p);
+    k_cache_eval<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, sm_count)), kThreads, bytes, s>>>(p); count_launch();
     return cudaGetLastError();
 }
 

@@ -398,7 +398,7 @@ cudaError_t launch(const CacheTcParams& p, int sm_count, cudaStream_t s)
     if (p.cap <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_cache_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    k_cache_tc<<<sm_count, kThreads, kSmemBytes, s>>>(p);
+    k_cache_tc<<<sm_count, kThreads, kSmemBytes, s>>>(p); count_launch();
     return cudaGetLastError();
 }
 
@@ -411,7 +411,7 @@ size_t cache_tc_image_bytes() { return kImageBytes; }
 // (the zero padding of the blocks is never rewritten).
 cudaError_t repack_cache_tc(const float* params, unsigned char* image, cudaStream_t s)
 {
-    k_repack_cache_tc<<<64, 256, 0, s>>>(params, image);
+    k_repack_cache_tc<<<64, 256, 0, s>>>(params, image); count_launch();
     return cudaGetLastError();
 }
 

@@ -137,7 +137,7 @@ cudaError_t launch_nif_fp32(const NifEvalParams& p, int mode, int sm_count, cuda
 {
     cudaError_t e = cudaFuncSetAttribute(k_nif_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    k_nif_fp32<<<sm_count, kThreads, kSmemBytes, s>>>(p, mode);
+    k_nif_fp32<<<sm_count, kThreads, kSmemBytes, s>>>(p, mode); count_launch();
     return cudaGetLastError();
 }
 
@@ -193,7 +193,7 @@ __global__ void k_repack_fp32(const float* __restrict__ params, int F, int H, in
 
 cudaError_t repack_nif_fp32(const float* params, int F, int H, int L, float* packed, cudaStream_t s)
 {
-    k_repack_fp32<<<256, 256, 0, s>>>(params, F, H, L, packed);
+    k_repack_fp32<<<256, 256, 0, s>>>(params, F, H, L, packed); count_launch();
     return cudaGetLastError();
 }
 }  // namespace ptk

@@ -395,7 +395,7 @@ cudaError_t launch_nif_fp8(const unsigned char* image, const NifEvalParams& np, 
     p.accumulate = np.accumulate;
     p.err = np.err;
     p.stats = np.stats;
-    k_nif_fp8<<<sm_count, kThreads, kSmemBytes, s>>>(p, mode);
+    k_nif_fp8<<<sm_count, kThreads, kSmemBytes, s>>>(p, mode); count_launch();
     return cudaGetLastError();
 }
 

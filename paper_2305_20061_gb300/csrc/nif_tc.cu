@@ -410,7 +410,7 @@ cudaError_t launch_l(const unsigned char* image, const TcParams& p, int mode, in
     cudaError_t e = cudaFuncSetAttribute(k_nif_tc<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Layout<L>::smem_bytes);
     if (e != cudaSuccess) return e;
-    k_nif_tc<L><<<sm_count, Layout<L>::threads, Layout<L>::smem_bytes, s>>>(p, mode);
+    k_nif_tc<L><<<sm_count, Layout<L>::threads, Layout<L>::smem_bytes, s>>>(p, mode); count_launch();
     return cudaGetLastError();
 }
 
@@ -541,6 +541,7 @@ cudaError_t repack_nif_tc_image(const float* params, int L, unsigned char* image
     case 5: k_repack_tc<5><<<128, 256, 0, s>>>(params, image); break;
     default: return cudaErrorInvalidValue;
     }
+    count_launch();
     return cudaGetLastError();
 }
 }  // namespace ptk

@@ -2,6 +2,7 @@
 // Nothing here is part of the C ABI (include/pt.h).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -11,6 +12,17 @@
 #include "pt.h"
 
 namespace ptk {
+
+// Kernels this library has put on a stream, process-wide: every launch site
+// counts itself, and a CUDA-graph replay adds the kernels its graph holds
+// (launches recorded during a capture are taken back out).
+extern std::atomic<unsigned long long> g_kernels_launched;
+extern thread_local unsigned long long t_kernels_launched;   // this thread's share (graph capture)
+inline void count_launch(unsigned long long n = 1)
+{
+    g_kernels_launched.fetch_add(n, std::memory_order_relaxed);
+    t_kernels_launched += n;
+}
 
 constexpr uint32_t kLeafBit = 0x80000000u;   // child reference is a primitive
 constexpr uint32_t kEmptyRef = 0xFFFFFFFFu;  // empty scene

@@ -35,7 +35,7 @@ __global__ void k_wait_selftest(uint32_t* err, uint64_t budget_ns, uint64_t* wai
 
 cudaError_t wait_selftest(uint32_t* err, uint64_t budget_ns, uint64_t* d_waited_ns, cudaStream_t s)
 {
-    k_wait_selftest<<<1, 32, 0, s>>>(err, budget_ns, d_waited_ns);
+    k_wait_selftest<<<1, 32, 0, s>>>(err, budget_ns, d_waited_ns); count_launch();
     return cudaGetLastError();
 }
 

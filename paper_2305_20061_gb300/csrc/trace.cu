@@ -564,7 +564,8 @@ cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s)
     // traversal: persistent, 4 resident blocks of 256 threads per SM; shading: grid-stride over the queue
     if (p.sc.wnodes) k_trace<true><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
     else k_trace<false><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
-    k_bounce<<<sm_count * 8, 256, 0, s>>>(p);
+    count_launch();
+    k_bounce<<<sm_count * 8, 256, 0, s>>>(p); count_launch();
     return cudaGetLastError();
 }
 
@@ -589,20 +590,21 @@ cudaError_t launch_paths(const BounceParams& p, int resident_threads, cudaStream
     if (blocks < 1) blocks = 1;
     if (p.sc.wnodes) k_paths<true><<<(int)blocks, kPathsBlock, 0, s>>>(p);
     else k_paths<false><<<(int)blocks, kPathsBlock, 0, s>>>(p);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const float* slot_L, float* pix, uint32_t n_pix, uint32_t s_count, int first, float scale,
                           cudaStream_t s)
 {
-    k_reduce<<<(n_pix + 255) / 256, 256, 0, s>>>(slot_L, pix, n_pix, s_count, first, scale);
+    k_reduce<<<(n_pix + 255) / 256, 256, 0, s>>>(slot_L, pix, n_pix, s_count, first, scale); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_fill_i32<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(p, n, v);
+    k_fill_i32<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(p, n, v); count_launch();
     return cudaGetLastError();
 }
 
@@ -610,7 +612,7 @@ cudaError_t launch_philox(uint32_t seed, uint32_t tag, int64_t n, const uint32_t
 {
     if (n <= 0) return cudaSuccess;
     k_philox<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(seed, tag, n, reinterpret_cast<const uint4*>(ctr),
-                                                      reinterpret_cast<uint4*>(out));
+                                                      reinterpret_cast<uint4*>(out)); count_launch();
     return cudaGetLastError();
 }
 
@@ -618,7 +620,7 @@ cudaError_t launch_primary(const DevScene& sc, int W, int H, uint32_t seed, uint
                            int64_t n, float* org, float* dir, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_primary<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(sc, W, H, seed, first_sample, first, n, org, dir);
+    k_primary<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(sc, W, H, seed, first_sample, first, n, org, dir); count_launch();
     return cudaGetLastError();
 }
 
@@ -626,7 +628,7 @@ cudaError_t launch_trace_rays(const DevScene& sc, int64_t n, const float* org, c
                               int32_t* prim, uint32_t* err, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_trace_rays<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(sc, n, org, dir, t, prim, err);
+    k_trace_rays<<<grid_for(n, 256, 152, 16), 256, 0, s>>>(sc, n, org, dir, t, prim, err); count_launch();
     return cudaGetLastError();
 }
 
@@ -638,7 +640,7 @@ __global__ void k_set_u32(uint32_t* dst, uint32_t value) { *dst = value; }
 }  // namespace
 cudaError_t launch_set_u32(uint32_t* dst, uint32_t value, cudaStream_t s)
 {
-    k_set_u32<<<1, 1, 0, s>>>(dst, value);
+    k_set_u32<<<1, 1, 0, s>>>(dst, value); count_launch();
     return cudaGetLastError();
 }
 }  // namespace ptk

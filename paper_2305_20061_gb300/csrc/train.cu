@@ -466,7 +466,7 @@ cudaError_t train_inputs(uint32_t seed, uint32_t step, int64_t B, const float* s
                          float* target, cudaStream_t s)
 {
     k_train_inputs<<<(unsigned)std::min<int64_t>((B + 255) / 256, 152 * 16), 256, 0, s>>>(seed, step, B, sky, w, h, uv,
-                                                                                           target);
+                                                                                           target); count_launch();
     return cudaGetLastError();
 }
 
@@ -502,11 +502,11 @@ void layer_fwd(const TrainWork& wk, int64_t B, const float* Xin, float* Xout, co
     if (pad_width(out) == 64) {
         const size_t sm = (size_t)K * (64 + kT) * sizeof(float);
         const int G = grid_of(wk, B, (const void*)k_layer_fwd<64>, sm);
-        k_layer_fwd<64><<<G, kT, sm, s>>>(B, Xin, Xout, W, b, in, out, K);
+        k_layer_fwd<64><<<G, kT, sm, s>>>(B, Xin, Xout, W, b, in, out, K); count_launch();
     } else {
         const size_t sm = (size_t)K * (128 + kT) * sizeof(float);
         const int G = grid_of(wk, B, (const void*)k_layer_fwd<128>, sm);
-        k_layer_fwd<128><<<G, kT, sm, s>>>(B, Xin, Xout, W, b, in, out, K);
+        k_layer_fwd<128><<<G, kT, sm, s>>>(B, Xin, Xout, W, b, in, out, K); count_launch();
     }
 }
 
@@ -517,11 +517,11 @@ void layer_bwd_dx(const TrainWork& wk, int64_t B, const float* dXout, const floa
     if (pad_width(in) == 64) {
         const size_t sm = (size_t)K * (64 + kT) * sizeof(float);
         const int G = grid_of(wk, B, (const void*)k_layer_bwd_dx<64>, sm);
-        k_layer_bwd_dx<64><<<G, kT, sm, s>>>(B, dXout, Xin, dXin, W, in, out, K);
+        k_layer_bwd_dx<64><<<G, kT, sm, s>>>(B, dXout, Xin, dXin, W, in, out, K); count_launch();
     } else {
         const size_t sm = (size_t)K * (128 + kT) * sizeof(float);
         const int G = grid_of(wk, B, (const void*)k_layer_bwd_dx<128>, sm);
-        k_layer_bwd_dx<128><<<G, kT, sm, s>>>(B, dXout, Xin, dXin, W, in, out, K);
+        k_layer_bwd_dx<128><<<G, kT, sm, s>>>(B, dXout, Xin, dXin, W, in, out, K); count_launch();
     }
 }
 
@@ -541,6 +541,7 @@ int layer_bwd_dw(const TrainWork& wk, int64_t B, const float* dXout, const float
     else if (*MT == 64) k_layer_bwd_dw<64, 128><<<G, kT, sm, s>>>(B, dXout, Xin, partial);
     else if (*NT == 64) k_layer_bwd_dw<128, 64><<<G, kT, sm, s>>>(B, dXout, Xin, partial);
     else k_layer_bwd_dw<128, 128><<<G, kT, sm, s>>>(B, dXout, Xin, partial);
+    count_launch();
     return G;
 }
 
@@ -559,10 +560,10 @@ cudaError_t head_loss(const TrainNet& net, int64_t B, const float* target, float
     const int Gh = grid_of(wk, B, (const void*)k_head_loss, hsm);
     k_head_loss<<<Gh, kT, hsm, s>>>(B, wk.X[net.L], target, net.W[net.L], net.b[net.L], net.H, net.M, delta,
                                     1.f / (3.f * (float)B), dX_last, wk.partial, wk.loss_partial, mode, mask,
-                                    x_tiled);
+                                    x_tiled); count_launch();
     k_sum_partials<<<(3 * net.H + 3 + 31) / 32, 256, 0, s>>>(wk.partial, Gh, 3 * kD + 3, kD, 3 * kD, net.H, 3,
-                                                             net.gW[net.L], net.gb[net.L]);
-    k_sum_loss<<<1, 32, 0, s>>>(wk.loss_partial, Gh, 1.0 / (3.0 * (double)B), loss_d, loss_f);
+                                                             net.gW[net.L], net.gb[net.L]); count_launch();
+    k_sum_loss<<<1, 32, 0, s>>>(wk.loss_partial, Gh, 1.0 / (3.0 * (double)B), loss_d, loss_f); count_launch();
     return cudaGetLastError();
 }
 
@@ -582,7 +583,7 @@ cudaError_t mlp_loss_grad_tc(const TrainNet& net, int64_t B, const float* target
         const int in = l == 0 ? net.in0 : net.H;
         k_sum_partials<<<(in * net.H + net.H + 31) / 32, 256, 0, s>>>(wk.partial + (size_t)l * Gl * stride, Gl, stride,
                                                                        pitch[l], net.H * pitch[l], in, net.H,
-                                                                       net.gW[l], net.gb[l]);
+                                                                       net.gW[l], net.gb[l]); count_launch();
     }
     return cudaGetLastError();
 }
@@ -618,7 +619,7 @@ cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, f
         int MT = 0, NT = 0;
         const int Gw = layer_bwd_dw(wk, B, wk.dX[cur], wk.X[l], wk.partial, in, net.H, &MT, &NT, s);
         k_sum_partials<<<(in * net.H + net.H + 31) / 32, 256, 0, s>>>(wk.partial, Gw, MT * NT + MT, NT, MT * NT, in,
-                                                                       net.H, net.gW[l], net.gb[l]);
+                                                                       net.H, net.gW[l], net.gb[l]); count_launch();
         if (l > 0) {
             layer_bwd_dx(wk, B, wk.dX[cur], wk.X[l], wk.dX[cur ^ 1], net.W[l], in, net.H, s);
             cur ^= 1;
@@ -632,7 +633,7 @@ cudaError_t nif_loss_grad(const TrainNet& net, int64_t B, const float* uv, const
 {
     if (B <= 0) return cudaSuccess;
     k_train_features<<<(unsigned)std::min<int64_t>((B * 64 + 255) / 256, 152 * 32), 256, 0, s>>>(B, uv, net.B, net.F,
-                                                                                                 wk.X[0]);
+                                                                                                 wk.X[0]); count_launch();
     return mlp_loss_grad(net, B, target, delta, 0, nullptr, precision, wk, loss_d, loss_f, s);
 }
 
@@ -709,21 +710,24 @@ cudaError_t cache_train_inputs(int64_t n, const float* rec, const float* slot_L,
 {
     const unsigned g = (unsigned)std::min<int64_t>((n + 127) / 128, 152 * 8);
     k_cache_features<<<(unsigned)std::min<int64_t>((n + kFeatRows - 1) / kFeatRows, 152 * 16), 128, 0, s>>>(
-        n, nullptr, rec, box, X0);
-    if (slot_L) k_cache_targets<<<g, 128, 0, s>>>(n, rec, slot_L, target, mask);
+        n, nullptr, rec, box, X0); count_launch();
+    if (slot_L) {
+        k_cache_targets<<<g, 128, 0, s>>>(n, rec, slot_L, target, mask);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
 cudaError_t cache_train_pixels(uint32_t seed, uint32_t frame, int64_t n, uint32_t n_pix, int64_t* pixels, cudaStream_t s)
 {
-    k_train_pixels<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(seed, frame, n, n_pix, pixels);
+    k_train_pixels<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(seed, frame, n, n_pix, pixels); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t adam_step(int64_t n, float* w, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
                       float c1, float c2, cudaStream_t s)
 {
-    k_adam<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(n, w, g, m, v, lr, b1, b2, eps, c1, c2);
+    k_adam<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(n, w, g, m, v, lr, b1, b2, eps, c1, c2); count_launch();
     return cudaGetLastError();
 }
 

@@ -658,7 +658,7 @@ cudaError_t forward_nh(const TrainNet& net, int64_t B, TrainWork& wk, unsigned i
     cudaError_t e = resident_grid((const void*)k_tc_fwd<NH>, kThreads, smem, kCols, wk.sm_count,
                                   (B + kRows - 1) / kRows, &grid);
     if (e != cudaSuccess) return e;
-    k_tc_fwd<NH><<<grid, kThreads, smem, s>>>(p);
+    k_tc_fwd<NH><<<grid, kThreads, smem, s>>>(p); count_launch();
     return cudaGetLastError();
 }
 
@@ -685,7 +685,7 @@ cudaError_t backward_nh(const TrainNet& net, int64_t B, TrainWork& wk, unsigned 
         int grid = 0;
         e = resident_grid((const void*)k_tc_dx<NH>, kThreads, smem, kCols, wk.sm_count, n_tiles, &grid);
         if (e != cudaSuccess) return e;
-        k_tc_dx<NH><<<grid, kThreads, smem, s>>>(p);
+        k_tc_dx<NH><<<grid, kThreads, smem, s>>>(p); count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -721,7 +721,7 @@ cudaError_t backward_nh(const TrainNet& net, int64_t B, TrainWork& wk, unsigned 
     if (Gl < 1) Gl = 1;
     if ((int64_t)Gl * net.L * p.stride > (int64_t)wk.n_blocks * (128 * 128 + 128)) return cudaErrorInvalidValue;
     p.Gl = Gl;
-    k_tc_dw<NH><<<Gl * net.L, kDwThreads, smem, s>>>(p, (uint32_t)cols);
+    k_tc_dw<NH><<<Gl * net.L, kDwThreads, smem, s>>>(p, (uint32_t)cols); count_launch();
     *Gl_out = Gl;
     *stride_out = p.stride;
     for (int l = 0; l < net.L; ++l) pitch[l] = l == 0 ? pad16(net.in0) : NH;

@@ -116,6 +116,7 @@ def lib():
             "pt_render_noalloc": ([P, P, P, P, P, P], I32),
             "pt_last_render_work": ([P, P, I32], I32),
             "pt_last_render_schedule": ([P, P], I32),
+            "pt_kernel_launches": ([P], I32),
             "pt_nif_set_params": ([P, P, P, P], I32),
             "pt_nif_fp8_scales": ([P, P], I32),
             "pt_train_nif": ([P, P, P, I32, I32, P, P, P], I32),
@@ -538,6 +539,15 @@ def last_render_counts(ctx: Context, max_depth: int, with_cache: bool = False) -
     out = np.zeros(max_depth + 1 + int(with_cache), np.int64)
     ctx._raise(lib().pt_last_render_counts(ctx.h, _np_ptr(out), len(out)))
     return out
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process (graph replays included)."""
+    v = C.c_uint64(0)
+    st = lib().pt_kernel_launches(C.byref(v))
+    if st != PT_OK:
+        raise PTError(st, "pt_kernel_launches failed")
+    return int(v.value)
 
 
 def last_render_schedule(ctx: Context) -> str:

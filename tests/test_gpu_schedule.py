@@ -157,3 +157,21 @@ def test_last_render_schedule_reported(pt, ctx):
     pt.render(ctx, s, g, I.RenderCfg(512, 384, 1, 2), schedule="paths")
     assert pt.last_render_schedule(ctx) == "paths"
     ctx.check()
+
+
+def test_kernel_launch_counter(pt, ctx):
+    """pt_kernel_launches counts every kernel a render runs, on direct
+    launches, on the launch that captures a graph and on graph replays: one
+    sample-offset write, per vertex a traversal and a shading kernel (or one
+    path kernel), the NIF at the escapes and the reduction."""
+    s = pt.Scene(ctx, I.make_scene("C1"))
+    g = pt.Nif(ctx, I.nif_init())
+    cfg = I.RenderCfg(16, 16, 1, 3)
+    out = torch.empty((16, 16, 3), dtype=torch.float32, device="cuda")
+    for sched, want in (("wavefront", 1 + 2 * 3 + 1 + 1), ("paths", 1 + 1 + 1 + 1)):
+        for _ in range(3):   # first sight (direct), capture + replay, replay
+            k0 = pt.kernel_launches()
+            pt.render(ctx, s, g, cfg, out=out, schedule=sched)
+            torch.cuda.synchronize()
+            assert pt.kernel_launches() - k0 == want, sched
+    ctx.check()
