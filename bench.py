@@ -478,6 +478,11 @@ def bench_ours(args):
         n, dt = run(n_pix)
         cpu = {"value": n * cfg.spp / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"all {cfg.spp} samples of {n} evenly strided pixels ({n * cfg.spp} paths), FP64 oracle"}
+        # the same oracle on one thread, on a sample of about a fifth of the time
+        run1, n1 = oracle_rate(sc, cfg, nif, target_s=args.cpu_s / 5, n_threads=1)
+        n1, dt1 = run1(n1)
+        cpu["single_thread"] = {"value": n1 * cfg.spp / dt1 / 1e6, "cores": 1,
+                                "sample": f"all {cfg.spp} samples of {n1} evenly strided pixels"}
 
     if rank == 0:
         line = {
