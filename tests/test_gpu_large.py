@@ -81,3 +81,21 @@ def test_small_bvh_bf16_and_fp32(pt, ctx):
     rel = rel_rmse(b.cpu().numpy(), a.cpu().numpy())
     print({"fp32_vs_oracle": res, "bf16_vs_fp32_rel_rmse": rel})
     assert rel < 0.02
+
+
+def test_large_bvh_schedules_bit_identical(pt, ctx, large):
+    """The packed 48-byte node form (the 10M-triangle tree is too large for
+    the decoded form) under both schedules: a small chunk of full-depth
+    paths, per-path radiance, hit IDs, ray and work counts identical."""
+    sc, gs, _ = large
+    cfg = I.RenderCfg(1920, 1080, 2, 8)
+    pix = torch.from_numpy(subset_pixels(1920, 1080)[::8].copy()).cuda()
+    out = {}
+    for sched in ("wavefront", "paths"):
+        img, slots, ids = pt.render_pixels(ctx, gs, None, cfg, pix, want_slots=True, want_ids=True, schedule=sched)
+        ctx.check()
+        assert pt.last_render_schedule(ctx) == sched
+        out[sched] = (img.cpu().numpy(), slots.cpu().numpy(), ids.cpu().numpy(),
+                      pt.last_render_counts(ctx, cfg.max_depth), np.array(list(pt.last_render_work(ctx).values())))
+    for x, y in zip(out["wavefront"], out["paths"]):
+        assert np.array_equal(x, y)
