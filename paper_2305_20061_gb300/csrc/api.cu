@@ -1210,6 +1210,7 @@ static pt_status render_launches(pt_ctx* ctx, const pt_scene* sc, const pt_nif* 
     bp.pixels = d_pixels;
     bp.W = cfg->width;
     bp.H = cfg->height;
+    bp.tiled = !d_pixels && cfg->width % 8 == 0 && cfg->height % 4 == 0;
     bp.esc = ctx->esc;
     bp.esc_count = ctx->counters + kEscCounter;
     bp.slot_L = ctx->slot_L;

@@ -94,6 +94,7 @@ struct BounceParams {
     uint32_t n_pix;
     const int64_t* pixels;  // nullable pixel list
     int32_t W, H;
+    int32_t tiled;          // camera rays taken in 8x4-pixel tiles (whole images with W % 8 == 0, H % 4 == 0)
     RayQueue qin;           // unused when k == 1
     const uint32_t* count_in;
     RayQueue qout;

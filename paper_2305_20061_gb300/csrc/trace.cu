@@ -26,6 +26,21 @@ __device__ __forceinline__ void slot_to_pixel(const BounceParams& p, uint32_t j,
     pix = p.pixels ? (uint32_t)p.pixels[i] : i;
 }
 
+// Order in which the camera rays of a chunk are taken: the j-th ray is the
+// path of slot tile_slot(j).  For a whole image with W % 8 == 0 and
+// H % 4 == 0, 32 consecutive rays cover an 8 x 4 pixel tile of one sample
+// instead of 32 pixels of one row (more coherent warps); a bijection of the
+// chunk's slots, so every path is traced once and keeps its own slot.
+__device__ __forceinline__ uint32_t tile_slot(const BounceParams& p, uint32_t j)
+{
+    if (!p.tiled) return j;
+    const uint32_t s = j / p.n_pix, q = j - s * p.n_pix;
+    const uint32_t b = q >> 5, l = q & 31u;
+    const uint32_t per_band = (uint32_t)p.W >> 3;
+    const uint32_t band = b / per_band, bx = b - band * per_band;
+    return s * p.n_pix + (band * 4u + (l >> 3)) * (uint32_t)p.W + bx * 8u + (l & 7u);
+}
+
 __device__ __forceinline__ float3 camera_dir(const DevScene& sc, int W, int H, uint32_t pix, float jx, float jy)
 {
     const float x = (float)(pix % (uint32_t)W), y = (float)(pix / (uint32_t)W);
@@ -206,8 +221,9 @@ __global__ void __launch_bounds__(256, PT_TRACE_MIN_BLOCKS) k_trace(const Bounce
             if (!live && idx < count) {
                 float3 o, d;
                 if (p.k == 1) {
+                    ri = tile_slot(p, idx);   // camera rays: hits are stored per slot
                     uint32_t pix, smp;
-                    slot_to_pixel(p, idx, pix, smp);
+                    slot_to_pixel(p, ri, pix, smp);
                     const uint4 w = philox4x32_10(make_uint4(pix, smp, 0u, 0u), p.seed, 0u);
                     o = f3(p.sc.eye[0], p.sc.eye[1], p.sc.eye[2]);
                     d = camera_dir(p.sc, p.W, p.H, pix, u01(w.x), u01(w.y));
@@ -215,8 +231,8 @@ __global__ void __launch_bounds__(256, PT_TRACE_MIN_BLOCKS) k_trace(const Bounce
                     const float4 o4 = p.qin.o[idx], d4 = p.qin.d[idx];
                     o = f3(o4.x, o4.y, o4.z);
                     d = f3(d4.x, d4.y, d4.z);
+                    ri = idx;
                 }
-                ri = idx;
                 if (trav_init(p.sc, o, d, t, work)) p.hits[ri] = make_int2(__float_as_int(t.h.t), t.h.prim);
                 else live = true;
             }
@@ -470,8 +486,8 @@ __global__ void __launch_bounds__(kPathsBlock, 12) k_paths(const BounceParams p)
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < p.n_chunk; j += gridDim.x * blockDim.x) {
         PathState s;
         uint32_t pix, smp;
-        s.slot = j;
-        slot_to_pixel(p, j, pix, smp);
+        s.slot = tile_slot(p, j);
+        slot_to_pixel(p, s.slot, pix, smp);
         camera_ray(p, pix, smp, s);
         for (int k = 1; k <= k_end; ++k) {
             {   // rays traced at vertex k: one atomic per group of lanes at the same vertex

@@ -175,3 +175,19 @@ def test_kernel_launch_counter(pt, ctx):
             torch.cuda.synchronize()
             assert pt.kernel_launches() - k0 == want, sched
     ctx.check()
+
+
+@pytest.mark.parametrize("schedule", ["wavefront", "paths"])
+def test_tiled_camera_order_same_paths(pt, ctx, schedule):
+    """A whole image with W % 8 == 0 and H % 4 == 0 takes its camera rays in
+    8x4-pixel tiles; an explicit list of all pixels takes them in row order.
+    Every path keeps its slot, so radiance and hit IDs agree bit for bit."""
+    s = pt.Scene(ctx, I.make_scene("C1"))
+    g = pt.Nif(ctx, I.nif_init())
+    cfg = I.RenderCfg(64, 48, 3, 5)
+    everything = torch.arange(64 * 48, dtype=torch.int64, device="cuda")
+    a = pt.render_pixels(ctx, s, g, cfg, None, want_slots=True, want_ids=True, schedule=schedule)
+    b = pt.render_pixels(ctx, s, g, cfg, everything, want_slots=True, want_ids=True, schedule=schedule)
+    ctx.check()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
