@@ -419,8 +419,10 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
         uint32_t pix = 0, smp = 0;
         if (active) {
             if (p.k == 1) {
-                s.slot = i;
-                slot_to_pixel(p, i, pix, smp);
+                // camera paths in the traversal's tile order, so that the survivors' queue (the rays of
+                // vertex 2) keeps neighbouring pixels together
+                s.slot = tile_slot(p, i);
+                slot_to_pixel(p, s.slot, pix, smp);
                 camera_ray(p, pix, smp, s);
             } else {
                 const float4 o = p.qin.o[i], d = p.qin.d[i], tp = p.qin.tp[i];
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
         VertexOut v{false, false, 0.f, 0.f};
         if (active) {
             ++traced;
-            const int2 hv = p.hits[i];
+            const int2 hv = p.hits[p.k == 1 ? s.slot : i];   // camera-ray hits are stored per slot
             v = shade_vertex(p, p.k, s, pix, smp, Hit{__int_as_float(hv.x), hv.y});
         }
         // compaction: survivors into the next queue, escapes into the NIF queue
