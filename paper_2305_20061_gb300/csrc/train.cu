@@ -72,7 +72,7 @@ __device__ __forceinline__ void tile_mma(const float* As, const float* Bs, int K
 
 // columns [0, K) of rows [tile*128, tile*128+128) of a [B][128] matrix -> smem [k][row] (zeros past B)
 __device__ __forceinline__ void load_rows_transposed(float* S, const float* __restrict__ X, int64_t tile, int64_t B,
-                                                     int K)
+                                                     int K, int stride = kT)
 {
     const int r = threadIdx.x;
     const int64_t g = tile * kT + r;
@@ -80,10 +80,10 @@ __device__ __forceinline__ void load_rows_transposed(float* S, const float* __re
 #pragma unroll 4
     for (int q = 0; q < K / 4; ++q) {
         const float4 v = g < B ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-        S[(4 * q + 0) * kT + r] = v.x;
-        S[(4 * q + 1) * kT + r] = v.y;
-        S[(4 * q + 2) * kT + r] = v.z;
-        S[(4 * q + 3) * kT + r] = v.w;
+        S[(4 * q + 0) * stride + r] = v.x;
+        S[(4 * q + 1) * stride + r] = v.y;
+        S[(4 * q + 2) * stride + r] = v.z;
+        S[(4 * q + 3) * stride + r] = v.w;
     }
 }
 
@@ -307,7 +307,10 @@ __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __r
                                                      const int32_t* __restrict__ mask, int x_tiled)
 {
     extern __shared__ float4 smem4[];
-    float* Xs = reinterpret_cast<float*>(smem4);   // the tile's last hidden layer, [k][row]
+    // the tile's last hidden layer, [k][row] with a padded row pitch: read along rows (thread = row) by the
+    // forward pass and along columns (thread = k) by the gradient pass, without bank conflicts either way
+    float* Xs = reinterpret_cast<float*>(smem4);
+    constexpr int kXs = kT + 1;
     __shared__ float dys[kT][3];
     __shared__ double lsum[kT];
     const int Kh = pad_k(H);
@@ -329,13 +332,13 @@ __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __r
             for (int q = 0; q < Kh / 4; ++q) {
                 const float4 v = gr < B ? *reinterpret_cast<const float4*>(X + x_off(gr, 4 * q, true))
                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-                Xs[(4 * q + 0) * kT + r] = v.x;
-                Xs[(4 * q + 1) * kT + r] = v.y;
-                Xs[(4 * q + 2) * kT + r] = v.z;
-                Xs[(4 * q + 3) * kT + r] = v.w;
+                Xs[(4 * q + 0) * kXs + r] = v.x;
+                Xs[(4 * q + 1) * kXs + r] = v.y;
+                Xs[(4 * q + 2) * kXs + r] = v.z;
+                Xs[(4 * q + 3) * kXs + r] = v.w;
             }
         } else {
-            load_rows_transposed(Xs, X, tile, B, Kh);
+            load_rows_transposed(Xs, X, tile, B, Kh, kXs);
         }
         __syncthreads();
         // thread = row: output, loss and dL/dy
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __r
         if (g < B && !(mask && !mask[g])) {
             float y[3] = {__ldg(&b4[0]), __ldg(&b4[1]), __ldg(&b4[2])};
             for (int kk = 0; kk < H; ++kk) {
-                const float xv = Xs[kk * kT + threadIdx.x];
+                const float xv = Xs[kk * kXs + threadIdx.x];
                 y[0] = fmaf(__ldg(&W4[kk]), xv, y[0]);
                 y[1] = fmaf(__ldg(&W4[H + kk]), xv, y[1]);
                 y[2] = fmaf(__ldg(&W4[2 * H + kk]), xv, y[2]);
@@ -373,8 +376,8 @@ __global__ void __launch_bounds__(kT, 1) k_head_loss(int64_t B, const float* __r
 #pragma unroll 8
         for (int i = 0; i < rows; ++i) {
             const int64_t gi = tile * kT + i;
-            const float xv = k < Kh ? X[x_off(gi, k, x_tiled != 0)] : 0.f;   // columns >= Kh >= H enter neither
-                                                                              // dX nor the head gradient
+            const float xv = k < Kh ? Xs[k * kXs + i] : 0.f;   // columns >= Kh >= H enter neither dX nor the
+                                                                // head gradient
             const float v = dys[i][0] * w0 + dys[i][1] * w1 + dys[i][2] * w2;
             dX[gi * kD + k] = (k < H && xv > 0.f) ? v : 0.f;
             gW[0] = fmaf(dys[i][0], xv, gW[0]);
@@ -556,7 +559,7 @@ cudaError_t head_loss(const TrainNet& net, int64_t B, const float* target, float
 {
     cudaError_t e = set_smem((const void*)k_head_loss);
     if (e != cudaSuccess) return e;
-    const size_t hsm = (size_t)pad_k(net.H) * kT * sizeof(float);
+    const size_t hsm = (size_t)pad_k(net.H) * (kT + 1) * sizeof(float);
     const int Gh = grid_of(wk, B, (const void*)k_head_loss, hsm);
     k_head_loss<<<Gh, kT, hsm, s>>>(B, wk.X[net.L], target, net.W[net.L], net.b[net.L], net.H, net.M, delta,
                                     1.f / (3.f * (float)B), dX_last, wk.partial, wk.loss_partial, mode, mask,
