@@ -434,6 +434,48 @@ __global__ void __launch_bounds__(256) k_sum_partials(const float* __restrict__ 
                ((part[4][lane] + part[5][lane]) + (part[6][lane] + part[7][lane]));
 }
 
+// The same fixed-order sums for several layers in one launch: job j owns the
+// CTAs [first[j], first[j + 1]) and sums exactly as k_sum_partials would.
+constexpr int kMaxSumJobs = 8;
+struct SumJobs {
+    int n_jobs;
+    int first[kMaxSumJobs + 1];
+    const float* partial[kMaxSumJobs];
+    int n_blocks, stride;
+    int pitch[kMaxSumJobs], bofs[kMaxSumJobs], in[kMaxSumJobs], out[kMaxSumJobs];
+    float* dst_W[kMaxSumJobs];
+    float* dst_b[kMaxSumJobs];
+};
+
+__global__ void __launch_bounds__(256) k_sum_partials_jobs(const SumJobs jobs)
+{
+    int j = 0;
+    while (j + 1 < jobs.n_jobs && (int)blockIdx.x >= jobs.first[j + 1]) ++j;
+    __shared__ float part[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int in = jobs.in[j], out = jobs.out[j];
+    const int n = out * in + out;
+    const int idx = ((int)blockIdx.x - jobs.first[j]) * 32 + lane;
+    int src = 0;
+    float* dst = nullptr;
+    if (idx < out * in) {
+        const int r = idx / in, k = idx % in;
+        src = r * jobs.pitch[j] + k;
+        dst = jobs.dst_W[j] + idx;
+    } else if (idx < n) {
+        src = jobs.bofs[j] + (idx - out * in);
+        dst = jobs.dst_b[j] + (idx - out * in);
+    }
+    float acc = 0.f;
+    if (idx < n)
+        for (int b = w; b < jobs.n_blocks; b += 8) acc += jobs.partial[j][(size_t)b * jobs.stride + src];
+    part[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && idx < n)
+        *dst = ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane])) +
+               ((part[4][lane] + part[5][lane]) + (part[6][lane] + part[7][lane]));
+}
+
 // one warp: lane l sums partials l, l + 32, ... in order, then a fixed shuffle tree
 __global__ void k_sum_loss(const double* __restrict__ partial, int n, double scale, double* __restrict__ out_d,
                            float* __restrict__ out_f)
@@ -582,12 +624,27 @@ cudaError_t mlp_loss_grad_tc(const TrainNet& net, int64_t B, const float* target
     int Gl = 0, stride = 0, pitch[8] = {};
     e = train_tc_backward(net, B, wk, wk.err, &Gl, &stride, pitch, s);
     if (e != cudaSuccess) return e;
+    // every hidden layer's partials are summed by one launch
+    SumJobs jobs = {};
+    if (net.L > kMaxSumJobs) return cudaErrorInvalidValue;
+    jobs.n_jobs = net.L;
+    jobs.n_blocks = Gl;
+    jobs.stride = stride;
+    int blocks = 0;
     for (int l = 0; l < net.L; ++l) {
         const int in = l == 0 ? net.in0 : net.H;
-        k_sum_partials<<<(in * net.H + net.H + 31) / 32, 256, 0, s>>>(wk.partial + (size_t)l * Gl * stride, Gl, stride,
-                                                                       pitch[l], net.H * pitch[l], in, net.H,
-                                                                       net.gW[l], net.gb[l]); count_launch();
+        jobs.first[l] = blocks;
+        jobs.partial[l] = wk.partial + (size_t)l * Gl * stride;
+        jobs.pitch[l] = pitch[l];
+        jobs.bofs[l] = net.H * pitch[l];
+        jobs.in[l] = in;
+        jobs.out[l] = net.H;
+        jobs.dst_W[l] = net.gW[l];
+        jobs.dst_b[l] = net.gb[l];
+        blocks += (in * net.H + net.H + 31) / 32;
     }
+    jobs.first[net.L] = blocks;
+    k_sum_partials_jobs<<<blocks, 256, 0, s>>>(jobs); count_launch();
     return cudaGetLastError();
 }
 
