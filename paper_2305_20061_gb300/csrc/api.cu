@@ -77,6 +77,7 @@ struct pt_nif {
     uint64_t version = 0;        // bumped when host-side copies (colour matrix) change
     int32_t F = 0, H = 0, L = 0;
     int64_t n_params = 0;
+    unsigned char* d_arena = nullptr;   // one allocation holding d_params, d_fp32 and d_tc
     float* d_params = nullptr;   // flat FP32 master weights
     float* d_fp32 = nullptr;     // packed FP32 layout (Wt, bias, Wout, bout)
     unsigned char* d_tc = nullptr;  // BF16 shared-memory image of the tensor-core kernel (F=64, H=128, L=1..5)
@@ -494,29 +495,11 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
         if (m[5] != 0.f || m[6] != 0.f || m[7] != 0.f) has_em = 1;
     }
 
-    pt_scene* sc = new pt_scene();
-    sc->ctx = ctx;
-    auto upload = [&](const void* src, size_t bytes, void** dst) -> bool {
-        if (cudaMalloc(dst, bytes ? bytes : 16) != cudaSuccess) return false;
-        sc->allocs.push_back(*dst);
-        return bytes == 0 || cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
-    };
-    void *dn, *ds, *dq, *dt, *dpm, *dm, *dmt;
-    bool ok = upload(bo.nodes.data(), bo.nodes.size() * sizeof(PackedNode), &dn) &&
-              upload(sph.data(), sph.size() * sizeof(float4), &ds) &&
-              upload(quad.data(), quad.size() * sizeof(float4), &dq) &&
-              upload(tri.data(), tri.size() * sizeof(float4), &dt) &&
-              upload(pmat.data(), pmat.size() * sizeof(int32_t), &dpm) &&
-              upload(mat.data(), mat.size() * sizeof(float4), &dm) &&
-              upload(d->mat_type, d->n_mats * sizeof(int32_t), &dmt);
-    if (!ok) {
-        pt_destroy_scene(sc);
-        return fail(ctx, PT_ENOMEM, "scene upload failed");
-    }
     // BVHs that fit comfortably in L2 also get the decoded 64-byte form
     constexpr size_t kWideLimit = 48u << 20;
+    std::vector<float> wide;
     if (!bo.nodes.empty() && bo.nodes.size() * 64 <= kWideLimit) {
-        std::vector<float> wide(bo.nodes.size() * 16, 0.f);
+        wide.assign(bo.nodes.size() * 16, 0.f);
         for (size_t i = 0; i < bo.nodes.size(); ++i) {
             const uint32_t* w = bo.nodes[i].w;
             float lo[6], hi[6];
@@ -534,13 +517,55 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
             std::memcpy(&o[12], &w[9], 4);
             std::memcpy(&o[13], &w[10], 4);
         }
-        void* dw = nullptr;
-        if (!upload(wide.data(), wide.size() * sizeof(float), &dw)) {
-            pt_destroy_scene(sc);
-            return fail(ctx, PT_ENOMEM, "scene upload failed");
-        }
-        sc->dev.wnodes = (const uint4*)dw;
     }
+
+    // one device arena per scene (one allocation; small scenes also one copy)
+    struct Segment { const void* src; size_t bytes; size_t off; };
+    Segment seg[8] = {{bo.nodes.data(), bo.nodes.size() * sizeof(PackedNode), 0},
+                      {sph.data(), sph.size() * sizeof(float4), 0},
+                      {quad.data(), quad.size() * sizeof(float4), 0},
+                      {tri.data(), tri.size() * sizeof(float4), 0},
+                      {pmat.data(), pmat.size() * sizeof(int32_t), 0},
+                      {mat.data(), mat.size() * sizeof(float4), 0},
+                      {d->mat_type, (size_t)d->n_mats * sizeof(int32_t), 0},
+                      {wide.data(), wide.size() * sizeof(float), 0}};
+    size_t total = 0;
+    for (Segment& g : seg) {
+        g.off = total;
+        total += (g.bytes + 255) & ~(size_t)255;
+    }
+    pt_scene* sc = new pt_scene();
+    sc->ctx = ctx;
+    unsigned char* arena = nullptr;
+    if (cudaMalloc((void**)&arena, std::max<size_t>(total, 256)) != cudaSuccess) {
+        cudaGetLastError();
+        pt_destroy_scene(sc);
+        return fail(ctx, PT_ENOMEM, "scene upload failed");
+    }
+    sc->allocs.push_back(arena);
+    bool ok = true;
+    constexpr size_t kStageLimit = 64u << 20;
+    if (total <= kStageLimit) {
+        std::vector<unsigned char> stage(total);
+        for (const Segment& g : seg)
+            if (g.bytes) std::memcpy(stage.data() + g.off, g.src, g.bytes);
+        ok = cudaMemcpy(arena, stage.data(), total, cudaMemcpyHostToDevice) == cudaSuccess;
+    } else {
+        for (const Segment& g : seg)
+            if (ok && g.bytes) ok = cudaMemcpy(arena + g.off, g.src, g.bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (!ok) {
+        pt_destroy_scene(sc);
+        return fail(ctx, PT_ECUDA, "scene upload failed");
+    }
+    void* dn = arena + seg[0].off;
+    void* ds = arena + seg[1].off;
+    void* dq = arena + seg[2].off;
+    void* dt = arena + seg[3].off;
+    void* dpm = arena + seg[4].off;
+    void* dm = arena + seg[5].off;
+    void* dmt = arena + seg[6].off;
+    if (!wide.empty()) sc->dev.wnodes = (const uint4*)(arena + seg[7].off);
     DevScene& v = sc->dev;
     v.nodes = (const uint4*)dn;
     v.root = bo.root;
@@ -629,15 +654,29 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
     pt_nif* nf = new pt_nif();
     nf->ctx = ctx;
     nf->F = F; nf->H = H; nf->L = L; nf->n_params = n;
-    if (cudaMalloc((void**)&nf->d_params, n * sizeof(float)) != cudaSuccess ||
-        cudaMalloc((void**)&nf->d_fp32, fp32_floats * sizeof(float)) != cudaSuccess) {
+    std::vector<unsigned char> img;
+    const bool tc = pack_nif_tc_image(d->params, F, H, L, img);
+    // one allocation and one copy: master weights | FP32 layout | tensor-core image
+    const size_t b_params = ((size_t)n * sizeof(float) + 255) & ~(size_t)255;
+    const size_t b_fp32 = (fp32_floats * sizeof(float) + 255) & ~(size_t)255;
+    const size_t total = b_params + b_fp32 + (tc ? img.size() : 0);
+    if (cudaMalloc((void**)&nf->d_arena, total) != cudaSuccess) {
+        cudaGetLastError();
         pt_destroy_nif(nf);
         return fail(ctx, PT_ENOMEM, "NIF allocation failed");
     }
-    if (cudaMemcpy(nf->d_params, d->params, n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(nf->d_fp32, pk.data(), fp32_floats * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
-        pt_destroy_nif(nf);
-        return fail(ctx, PT_ECUDA, "NIF upload failed");
+    nf->d_params = reinterpret_cast<float*>(nf->d_arena);
+    nf->d_fp32 = reinterpret_cast<float*>(nf->d_arena + b_params);
+    if (tc) nf->d_tc = nf->d_arena + b_params + b_fp32;
+    {
+        std::vector<unsigned char> stage(total, 0);
+        std::memcpy(stage.data(), d->params, (size_t)n * sizeof(float));
+        std::memcpy(stage.data() + b_params, pk.data(), fp32_floats * sizeof(float));
+        if (tc) std::memcpy(stage.data() + b_params + b_fp32, img.data(), img.size());
+        if (cudaMemcpy(nf->d_arena, stage.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+            pt_destroy_nif(nf);
+            return fail(ctx, PT_ECUDA, "NIF upload failed");
+        }
     }
     DevNif& v = nf->dev;
     v.F = F; v.H = H; v.L = L;
@@ -647,14 +686,6 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
     v.bout = v.Wout + 3 * 128;
     v.B = v.bout + 3;
     for (int i = 0; i < 9; ++i) v.M[i] = d->params[n - 9 + i];
-    std::vector<unsigned char> img;
-    if (pack_nif_tc_image(d->params, F, H, L, img)) {
-        if (cudaMalloc((void**)&nf->d_tc, img.size()) != cudaSuccess ||
-            cudaMemcpy(nf->d_tc, img.data(), img.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-            pt_destroy_nif(nf);
-            return fail(ctx, PT_ENOMEM, "NIF tensor-core image upload failed");
-        }
-    }
     nf->fp8_ok = F == 64 && H == 128 && L == 3;
     *out = nf;
     return PT_OK;
@@ -663,9 +694,7 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
 PT_API void pt_destroy_nif(pt_nif* nf)
 {
     if (!nf) return;
-    cudaFree(nf->d_params);
-    cudaFree(nf->d_fp32);
-    cudaFree(nf->d_tc);
+    cudaFree(nf->d_arena);   // d_params, d_fp32 and d_tc live in it
     cudaFree(nf->d_fp8);
     cudaFree(nf->d_grad);
     cudaFree(nf->d_m);

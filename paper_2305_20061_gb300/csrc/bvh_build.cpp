@@ -69,6 +69,22 @@ struct Builder {
     {
         const int64_t n = e - b;
         *boxes_known = false;
+        if (n == 2) {
+            // two leaves whatever the split; the binned sweep below would order them by centroid along the
+            // first axis where the centroids differ (ties: as listed), which this reproduces without the bins
+            const uint32_t p0 = idx[b], p1 = idx[b + 1];
+            for (int a = 0; a < 3; ++a) {
+                const float c0 = in.cen[3 * p0 + a], c1 = in.cen[3 * p1 + a];
+                if (c0 != c1) {
+                    if (c1 < c0) std::swap(idx[b], idx[b + 1]);
+                    break;
+                }
+            }
+            bl->grow(&in.lo[3 * idx[b]], &in.hi[3 * idx[b]]);
+            br->grow(&in.lo[3 * idx[b + 1]], &in.hi[3 * idx[b + 1]]);
+            *boxes_known = true;
+            return b + 1;
+        }
         float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int64_t i = b; i < e; ++i)
             for (int a = 0; a < 3; ++a) {
@@ -99,24 +115,34 @@ struct Builder {
         int best_axis = -1, best_bin = -1;
         for (int a = 0; a < 3; ++a) {
             if (!live[a]) continue;
+            // an empty bin leaves the running box and count unchanged, so its area is carried over
+            // instead of recomputed (same values, fewer operations on small ranges)
             double left_area[kBins];
             int64_t left_cnt[kBins];
             Box acc;
             int64_t c = 0;
+            double area = 0.0;
             for (int k = 0; k < kBins - 1; ++k) {
-                acc.grow(bb[a][k]);
-                c += cnt[a][k];
-                left_area[k] = acc.area();
+                if (cnt[a][k]) {
+                    acc.grow(bb[a][k]);
+                    c += cnt[a][k];
+                    area = acc.area();
+                }
+                left_area[k] = area;
                 left_cnt[k] = c;
             }
             Box racc;
             int64_t rc = 0;
+            double rarea = 0.0;
             for (int k = kBins - 1; k >= 1; --k) {
-                racc.grow(bb[a][k]);
-                rc += cnt[a][k];
+                if (cnt[a][k]) {
+                    racc.grow(bb[a][k]);
+                    rc += cnt[a][k];
+                    rarea = racc.area();
+                }
                 const int64_t lc = left_cnt[k - 1];
                 if (lc == 0 || rc == 0) continue;
-                const double cost = left_area[k - 1] * (double)lc + racc.area() * (double)rc;
+                const double cost = left_area[k - 1] * (double)lc + rarea * (double)rc;
                 if (cost < best_cost) { best_cost = cost; best_axis = a; best_bin = k; }
             }
         }
