@@ -167,9 +167,14 @@ __device__ __forceinline__ void store_L(float* slot_L, uint32_t slot, float3 L, 
 // Persistent warps keep their lanes busy: whenever at least kRefillMin lanes
 // have finished, the idle lanes take the next ray indices from a range the
 // warp claimed with one atomic (kFetchRange indices at a time), so a warp no
-// longer waits for its slowest ray before starting new ones.
+// longer waits for its slowest ray before starting new ones.  Trees in the
+// decoded form (small enough for L2; the node step is issue-bound) refill
+// in larger groups than large packed trees (the node step waits on memory).
 #ifndef PT_TRACE_REFILL_MIN
 #define PT_TRACE_REFILL_MIN 12
+#endif
+#ifndef PT_TRACE_REFILL_MIN_WIDE
+#define PT_TRACE_REFILL_MIN_WIDE 20
 #endif
 #ifndef PT_TRACE_STEPS
 #define PT_TRACE_STEPS 3
@@ -177,7 +182,8 @@ __device__ __forceinline__ void store_L(float* slot_L, uint32_t slot, float3 L, 
 #ifndef PT_TRACE_RANGE_DIV
 #define PT_TRACE_RANGE_DIV 4096
 #endif
-constexpr int kRefillMin = PT_TRACE_REFILL_MIN;
+constexpr int kRefillMinPacked = PT_TRACE_REFILL_MIN;
+constexpr int kRefillMinWide = PT_TRACE_REFILL_MIN_WIDE;
 constexpr int kStepsPerCheck = PT_TRACE_STEPS;
 
 #ifndef PT_TRACE_MIN_BLOCKS
@@ -203,6 +209,7 @@ __global__ void __launch_bounds__(256, PT_TRACE_MIN_BLOCKS) k_trace(const Bounce
     uint32_t rnext = 0, rend = 0;   // the warp's claimed index range (warp-uniform)
     while (true) {
         const unsigned idle = __ballot_sync(0xFFFFFFFFu, !live);
+        constexpr int kRefillMin = kWide ? kRefillMinWide : kRefillMinPacked;
         if (idle && !exhausted && (__popc(idle) >= kRefillMin || idle == 0xFFFFFFFFu)) {
             const uint32_t n = __popc(idle), rank = __popc(idle & lanes_below);
             const uint32_t avail = rend - rnext;
