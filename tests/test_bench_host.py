@@ -1,0 +1,65 @@
+"""Host-side logic of bench.py, on the CPU: the reference arm's JSON line
+(the FP64 oracle timed on the host cores), the bias estimate of the cache
+comparison, and the naming of the traversal kernels in the roofline."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import torch
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "C1", "--steps", "2",
+                        "--warmup", "1", "--ref-step-s", "0.2"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["higher_is_better"] is True and line["n_gpus"] == 1
+    assert line["steps"] == 2 and line["warmup"] == 1
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    cpu = line["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"]
+    assert isinstance(cpu["sample"], str) and cpu["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    assert line["config"]["workload"].startswith("C1")
+
+
+def test_image_stats_separates_bias_from_noise():
+    """Batches X_b = (1 + beta) R + noise against a reference with its own
+    noise: the noise-corrected bias recovers beta, the raw relative RMSE
+    includes the noise."""
+    g = torch.Generator().manual_seed(3)
+    H, W, nb, beta, sx = 32, 32, 64, 0.02, 0.05
+    R = 1.0 + torch.rand((H, W, 3), generator=g, dtype=torch.float64)
+    R_batches = R + 0.01 * torch.randn((16, H, W, 3), generator=g, dtype=torch.float64)
+    R_mean, R_var = R_batches.mean(0), R_batches.var(0) / 16
+    X = (1 + beta) * R + sx * torch.randn((nb, H, W, 3), generator=g, dtype=torch.float64)
+    st = bench.image_stats(X, R_mean, R_var)
+    true_bias = float(torch.sqrt(((beta * R) ** 2).sum() / (R_mean ** 2).sum()))
+    assert abs(st["bias_rel_rmse"] - true_bias) < 0.15 * true_bias, st
+    assert st["rel_rmse"] > st["bias_rel_rmse"] and st["noise_rel_rmse"] > 0
+    # no bias: the estimate is small and may come out negative (signed)
+    st0 = bench.image_stats(R + sx * torch.randn((nb, H, W, 3), generator=g, dtype=torch.float64), R_mean, R_var)
+    assert abs(st0["bias_rel_rmse"]) < 0.3 * true_bias, st0
+
+
+def test_trace_kernel_names_follow_the_schedule():
+    class FakePt:
+        def __init__(self, sched):
+            self.sched = sched
+
+        def last_render_schedule(self, ctx):
+            return self.sched
+
+    assert bench.trace_kernels(FakePt("paths"), None, 8) == ("k_paths", 1)
+    assert bench.trace_kernels(FakePt("wavefront"), None, 8) == ("k_trace+k_bounce", 8)
