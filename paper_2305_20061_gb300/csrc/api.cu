@@ -544,7 +544,7 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
     }
     sc->allocs.push_back(arena);
     bool ok = true;
-    constexpr size_t kStageLimit = 64u << 20;
+    constexpr size_t kStageLimit = 4u << 20;   // small scenes: one copy; large: no extra host copy
     if (total <= kStageLimit) {
         std::vector<unsigned char> stage(total);
         for (const Segment& g : seg)
