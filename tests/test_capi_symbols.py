@@ -49,3 +49,25 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(pt, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         pt.lib()
+
+
+def _declared_arity():
+    arity = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"PT_API\s+[\w\s\*]+?\b(pt_\w+)\s*\(([^)]*)\)\s*;", src):
+            params = m.group(2).strip()
+            arity[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return arity
+
+
+def test_binding_types_every_entry_point(libpt):
+    """The ctypes binding gives every declared entry point its argument
+    types, as many as the header declares (no untyped calls)."""
+    from paper_2305_20061_gb300 import pt
+    L = pt.lib()
+    arity = _declared_arity()
+    assert set(arity) == set(_declared())
+    wrong = {n: (len(getattr(L, n).argtypes or []), k) for n, k in arity.items()
+             if getattr(L, n).argtypes is None or len(getattr(L, n).argtypes) != k}
+    assert not wrong, wrong
