@@ -137,6 +137,21 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* desc, pt_scen
 PT_API void pt_destroy_scene(pt_scene* scene);
 PT_API pt_status pt_scene_get_info(const pt_scene* scene, pt_scene_info* info);
 
+/* The scene builder's BVH step alone, on the host (no context, no device):
+   binned SAH over n primitive boxes lo[i][3], hi[i][3] with centroids at
+   the box centres, one primitive per leaf, children's boxes packed as in
+   pt_create_scene (12 uint32 per node: w[0..2] left fp32 origin, w[3..5]
+   right fp32 origin, w[6..8] the six fp16 extents rounded up (left x, y, z,
+   right x, y, z, two per word, low half first), w[9] left and w[10] right
+   child reference (bit 31 set: primitive index), w[11] 0).  nodes: host
+   [cap][12] (cap >= n - 1), *n_nodes the count written, *root the root
+   reference (bit 31 set when n == 1; 0xFFFFFFFF when n == 0), *depth the
+   tree depth.  PT_EINVAL for n < 0, a NULL output, cap too small or
+   non-finite bounds; PT_EUNSUPPORTED when an extent exceeds the fp16
+   range. */
+PT_API pt_status pt_build_bvh_host(int64_t n, const float* lo, const float* hi, uint32_t* nodes, int64_t cap,
+                                   int64_t* n_nodes, uint32_t* root, int32_t* depth);
+
 /* Copy the packed BVH back to the host for inspection: nodes as 12 uint32
    per node (see the packing in the library source), root reference in
    *root.  Either buffer may be NULL; sizes come from pt_scene_get_info. */

@@ -601,6 +601,29 @@ PT_API pt_status pt_scene_get_info(const pt_scene* sc, pt_scene_info* info)
     return PT_OK;
 }
 
+PT_API pt_status pt_build_bvh_host(int64_t n, const float* lo, const float* hi, uint32_t* nodes, int64_t cap,
+                                   int64_t* n_nodes, uint32_t* root, int32_t* depth)
+{
+    if (n < 0 || !n_nodes || !root || !depth || (n > 0 && (!lo || !hi))) return PT_EINVAL;
+    if (n >= (int64_t)kLeafBit - 1) return PT_EINVAL;
+    if (!finite3(lo, 3 * n) || !finite3(hi, 3 * n)) return PT_EINVAL;
+    if (n > 1 && (!nodes || cap < n - 1)) return PT_EINVAL;
+    BuildInput bin;
+    bin.n_prims = n;
+    bin.lo.assign(lo, lo + 3 * n);
+    bin.hi.assign(hi, hi + 3 * n);
+    bin.cen.resize(3 * n);
+    for (int64_t i = 0; i < 3 * n; ++i) bin.cen[i] = 0.5f * (bin.lo[i] + bin.hi[i]);
+    BuildOutput bo;
+    if (!build_bvh(bin, bo)) return PT_EUNSUPPORTED;
+    if ((int64_t)bo.nodes.size() > cap && !bo.nodes.empty()) return PT_EINVAL;
+    if (!bo.nodes.empty()) std::memcpy(nodes, bo.nodes.data(), bo.nodes.size() * sizeof(PackedNode));
+    *n_nodes = (int64_t)bo.nodes.size();
+    *root = bo.root;
+    *depth = bo.depth;
+    return PT_OK;
+}
+
 PT_API pt_status pt_scene_download_bvh(pt_ctx* ctx, const pt_scene* sc, uint32_t* nodes, uint32_t* root)
 {
     if (!ctx || !sc) return fail(ctx, PT_EINVAL, "null argument");

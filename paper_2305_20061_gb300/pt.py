@@ -117,6 +117,7 @@ def lib():
             "pt_last_render_work": ([P, P, I32], I32),
             "pt_last_render_schedule": ([P, P], I32),
             "pt_kernel_launches": ([P], I32),
+            "pt_build_bvh_host": ([I64, P, P, P, I64, P, P, P], I32),
             "pt_nif_set_params": ([P, P, P, P], I32),
             "pt_nif_fp8_scales": ([P, P], I32),
             "pt_train_nif": ([P, P, P, I32, I32, P, P, P], I32),
@@ -539,6 +540,21 @@ def last_render_counts(ctx: Context, max_depth: int, with_cache: bool = False) -
     out = np.zeros(max_depth + 1 + int(with_cache), np.int64)
     ctx._raise(lib().pt_last_render_counts(ctx.h, _np_ptr(out), len(out)))
     return out
+
+
+def build_bvh_host(lo: np.ndarray, hi: np.ndarray):
+    """pt_build_bvh_host: the scene builder's BVH from primitive boxes
+    [n, 3] on the host.  Returns (nodes [n - 1, 12] uint32, root, depth)."""
+    lo = np.ascontiguousarray(lo, np.float32)
+    hi = np.ascontiguousarray(hi, np.float32)
+    n = int(lo.shape[0])
+    nodes = np.zeros((max(n - 1, 1), 12), np.uint32)
+    n_nodes, root, depth = C.c_int64(0), C.c_uint32(0), C.c_int32(0)
+    st = lib().pt_build_bvh_host(n, _np_ptr(lo), _np_ptr(hi), _np_ptr(nodes), nodes.shape[0], C.byref(n_nodes),
+                                 C.byref(root), C.byref(depth))
+    if st != PT_OK:
+        raise PTError(st, "pt_build_bvh_host failed")
+    return nodes[:n_nodes.value], int(root.value), int(depth.value)
 
 
 def kernel_launches() -> int:
