@@ -17,7 +17,9 @@
  *   BVH ................... pinned (brute force)
  *   estimator ............. pinned (white-furnace closed forms, energy bounds)
  *   BSDF lobes ............ pinned (cosine moments, Fresnel at normal incidence,
- *                           Snell's law, total internal reflection, Schlick/Smith at h = n)
+ *                           Snell's law, total internal reflection, Schlick/Smith at h = n;
+ *                           GGX metal: mean weight = directional albedo from an independent
+ *                           quadrature of the microfacet BRDF, half-vector chi-square)
  *   NIF forward ........... pinned (B = 0, zero weights, relu(x) - relu(-x) = x wiring)
  *   NIF backward / Adam ... pinned (central finite differences, Adam closed-form steps)
  *   sky lookup ............ pinned (pixel centres, wrap/clamp, four-centre average)
@@ -986,6 +988,15 @@ OR_API int or_sample_bsdf(const OrScene* s, int mat, const double* d, const doub
     weight[0] = wt.x; weight[1] = wt.y; weight[2] = wt.z;
     if (!ok) { wi[0] = wi[1] = wi[2] = 0.0; weight[0] = weight[1] = weight[2] = 0.0; }
     return ok;
+}
+
+/* n independent draws of or_sample_bsdf for one incident direction and
+   normal: u is n x 3 (u1, u2, lobe), wi and weight n x 3, ok n flags */
+OR_API void or_sample_bsdf_batch(const OrScene* s, int mat, const double* d, const double* ng, int64_t n,
+                                 const double* u, double* wi, double* weight, int32_t* ok)
+{
+    for (int64_t i = 0; i < n; ++i)
+        ok[i] = or_sample_bsdf(s, mat, d, ng, u[3 * i], u[3 * i + 1], u[3 * i + 2], wi + 3 * i, weight + 3 * i);
 }
 
 /* ------------------------------------------------------------------------ */

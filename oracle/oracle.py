@@ -58,6 +58,7 @@ def lib():
         L.or_dir_to_uv.argtypes = [I64, P, P]
         L.or_sample_bsdf.argtypes = [P, C.c_int, P, P, C.c_double, C.c_double, C.c_double, P, P]
         L.or_sample_bsdf.restype = C.c_int
+        L.or_sample_bsdf_batch.argtypes = [P, C.c_int, P, P, I64, P, P, P, P]
         L.or_render.argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_int, U32, C.c_int, C.c_int,
                                 I64, P, P, P, P, C.c_int]
         _lib = L
@@ -241,6 +242,19 @@ def sample_bsdf(oscene: Scene, mat: int, d, ng, u1: float, u2: float, ul: float)
     wt = np.zeros(3)
     ok = lib().or_sample_bsdf(oscene.h, mat, _ptr(d), _ptr(ng), u1, u2, ul, _ptr(wi), _ptr(wt))
     return bool(ok), wi, wt
+
+
+def sample_bsdf_batch(oscene: Scene, mat: int, d, ng, u: np.ndarray):
+    """sample_bsdf for every row (u1, u2, lobe) of u [n, 3]: (ok [n], wi [n, 3], weight [n, 3])."""
+    d = np.ascontiguousarray(d, np.float64)
+    ng = np.ascontiguousarray(ng, np.float64)
+    u = np.ascontiguousarray(u, np.float64).reshape(-1, 3)
+    n = len(u)
+    wi = np.zeros((n, 3))
+    wt = np.zeros((n, 3))
+    ok = np.zeros(n, np.int32)
+    lib().or_sample_bsdf_batch(oscene.h, mat, _ptr(d), _ptr(ng), n, _ptr(u), _ptr(wi), _ptr(wt), _ptr(ok))
+    return ok.astype(bool), wi, wt
 
 
 # ----------------------------------------------------------------------------

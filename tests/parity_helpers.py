@@ -4,6 +4,7 @@ import numpy as np
 import torch
 
 from oracle import oracle as O
+from paper_2305_20061_gb300 import inputs as I
 
 
 def rel_rmse(img, ref):
@@ -47,3 +48,51 @@ def compare_render(pt, ctx, sc, cfg, nif=None, pixels=None, max_div=1e-3, tol=1e
     assert res["divergent"] <= max_div, res
     assert res["matched"] <= tol, res
     return res
+
+
+def specular_vertices(sc, ids):
+    """Number of metal or dielectric hits on each path (ids [n, D], -1 miss, -2 unused)."""
+    prim_mat = np.concatenate([sc.sphere_mat, sc.quad_mat, sc.tri_mat])
+    spec = np.isin(sc.mat_type[prim_mat], [I.METAL, I.DIELECTRIC])
+    hit = ids >= 0
+    return (hit & spec[np.where(hit, ids, 0)]).sum(1)
+
+
+def conditioning_table(sc, ids_ref, L_ref, runs, max_bin=4):
+    """Per specular-vertex count k of the reference path (k >= max_bin pooled):
+    for each named run (L, ids), the fraction of divergent paths and the
+    relative RMSE over matched paths."""
+    ns = np.minimum(specular_vertices(sc, ids_ref), max_bin)
+    rows = []
+    for k in range(max_bin + 1):
+        m = ns == k
+        row = dict(k=k, n=int(m.sum()))
+        for name, (L, ids) in runs.items():
+            same = np.all(ids == ids_ref, axis=1)
+            mm = m & same
+            row[name + "_div"] = float(1 - same[m].mean()) if m.any() else 0.0
+            row[name + "_matched"] = rel_rmse(L[mm], L_ref[mm]) if mm.any() else 0.0
+        rows.append(row)
+    return rows
+
+
+def perturbed_camera(cam):
+    """The camera moved by one float32 ulp along z (eye z -> the next float32
+    towards +inf): the smallest change of the FP32 inputs, used to measure how
+    strongly the FP64 paths themselves react to one rounding."""
+    c = I.Camera.make(cam.eye.copy(), cam.target.copy(), cam.up.copy(), cam.fov_deg)
+    c.eye[2] = np.nextafter(c.eye[2], np.float32(np.inf))
+    return c
+
+
+def assert_within_floor(rows, min_n=200, factor=3.0):
+    """Each bin of a conditioning table with at least min_n paths: the GPU's
+    divergent fraction within factor x the FP64 floor plus three binomial
+    standard deviations, and its matched-path relative RMSE within factor x
+    the floor's plus 1e-4."""
+    for r in rows:
+        if r["n"] < min_n:
+            continue
+        sd = np.sqrt(max(r["floor_div"], 1.0 / r["n"]) / r["n"])
+        assert r["gpu_div"] <= factor * r["floor_div"] + 3 * sd, r
+        assert r["gpu_matched"] <= factor * r["floor_matched"] + 1e-4, r

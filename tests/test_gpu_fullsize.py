@@ -12,7 +12,7 @@ import torch
 from oracle import oracle as O
 from paper_2305_20061_gb300 import inputs as I
 
-from parity_helpers import rel_rmse
+from parity_helpers import assert_within_floor, conditioning_table, perturbed_camera, rel_rmse
 
 pytestmark = pytest.mark.gpu
 
@@ -57,30 +57,68 @@ def _full_frame(pt, ctx, sc, nif, cfg, precision="fp32"):
     return img, slots, ids
 
 
-@pytest.mark.parametrize("config,max_div,tol", [("C2", 1e-2, 1e-2), ("C3", 2e-3, 1e-3)])
-def test_full_frame_sampled_paths(pt, ctx, config, max_div, tol):
-    """C2 (256 spheres, 512x512, 64 spp, depth 8) and C3 (heightfield,
-    1024x1024, 16 spp, depth 6) with the FP32 NIF: sampled paths of the
-    whole-frame render against the oracle.  C2's chained specular bounces
-    feed a sigma = 10 Fourier field, so its matched-path bound is the looser
-    one of the reduced-size test."""
-    sc, nif, cfg = I.make_scene(config), I.nif_init(colour="yuv"), I.CONFIGS[config]["cfg"]
+def _oracle_paths(sc, nif, cfg, P, S, camera=None):
+    L, _, oids = O.trace_paths(O.Scene(sc), sc.camera if camera is None else camera, cfg.width, cfg.height,
+                               cfg.max_depth, cfg.seed, P, S, nif=O.Nif(nif), want_ids=True)
+    return L, oids
+
+
+def _gpu_paths(pt, ctx, sc, nif, cfg, P, S):
     img, slots, ids = _full_frame(pt, ctx, sc, nif, cfg)
-    P, S = _sample(cfg, 11)
     n_pix = cfg.width * cfg.height
     sl = torch.from_numpy(S * n_pix + P).cuda()
     gL = slots.reshape(-1, 3)[sl].cpu().numpy().astype(np.float64)
     gids = ids.reshape(-1, cfg.max_depth)[sl].cpu().numpy()
-    L, _, oids = O.trace_paths(O.Scene(sc), sc.camera, cfg.width, cfg.height, cfg.max_depth, cfg.seed, P, S,
-                               nif=O.Nif(nif), want_ids=True)
-    res = _compare(gL, gids, L, oids)
-    print(config, res)
-    assert res["div_v1"] <= 1e-3, res
-    assert res["divergent"] <= max_div, res
-    assert res["matched"] <= tol, res
     # the frame is the mean of its slots in sample order
     want = slots.double().mean(0).reshape(cfg.height, cfg.width, 3)
     assert torch.allclose(img.double().reshape(cfg.height, cfg.width, 3), want, rtol=1e-5, atol=1e-6)
+    return gL, gids
+
+
+def test_c3_full_frame_sampled_paths(pt, ctx):
+    """C3 (heightfield, 1024x1024, 16 spp, depth 6) with the FP32 NIF:
+    sampled paths of the whole-frame render against the oracle."""
+    sc, nif, cfg = I.make_scene("C3"), I.nif_init(colour="yuv"), I.CONFIGS["C3"]["cfg"]
+    P, S = _sample(cfg, 11)
+    gL, gids = _gpu_paths(pt, ctx, sc, nif, cfg, P, S)
+    L, oids = _oracle_paths(sc, nif, cfg, P, S)
+    res = _compare(gL, gids, L, oids)
+    print("C3", res)
+    assert res["div_v1"] <= 1e-3, res
+    assert res["divergent"] <= 2e-3, res
+    assert res["matched"] <= 1e-3, res
+
+
+def test_c2_full_frame_parity_by_specular_vertices(pt, ctx):
+    """C2 (256 spheres, 512x512, 64 spp, depth 8, FP32 NIF): sampled paths of
+    the whole-frame render against the oracle, binned by the number of
+    specular (metal or dielectric) vertices on the oracle's path.
+
+    Reflection off a sphere of radius r seen from distance D multiplies a
+    direction error by about 2D/r (Lambertian bounces also inherit the
+    normal's error), so an error of one float32 rounding in the path state
+    grows bounce by bounce until the path hits another sphere or leaves
+    through another part of the sigma = 10 Fourier field.  The floor is
+    measured with the oracle itself: the same paths rendered in FP64 from a
+    camera moved by one float32 ulp (eye z = 35 -> nextafter) diverge from
+    the unperturbed FP64 paths at the rates in the 'floor' columns.  The
+    FP32 GPU path is held to that floor per bin (a factor of 3, plus three
+    binomial standard deviations of the GPU's divergence count), and to the
+    absolute bar (matched-path relative RMSE <= 1e-3) on paths without a
+    specular vertex."""
+    sc, nif, cfg = I.make_scene("C2"), I.nif_init(colour="yuv"), I.CONFIGS["C2"]["cfg"]
+    P, S = _sample(cfg, 11)
+    gL, gids = _gpu_paths(pt, ctx, sc, nif, cfg, P, S)
+    L, oids = _oracle_paths(sc, nif, cfg, P, S)
+    Lp, pids = _oracle_paths(sc, nif, cfg, P, S, camera=perturbed_camera(sc.camera))
+    res = _compare(gL, gids, L, oids)
+    rows = conditioning_table(sc, oids, L, dict(gpu=(gL, gids), floor=(Lp, pids)))
+    print("C2", res)
+    for r in rows:
+        print("C2 specular vertices", r)
+    assert res["div_v1"] <= 1e-3, res
+    assert_within_floor(rows)
+    assert rows[0]["gpu_matched"] <= 1e-3, rows[0]
 
 
 def test_c2_full_frame_bf16_paths_follow_fp32(pt, ctx):
