@@ -146,9 +146,9 @@ PT_API pt_status pt_scene_get_info(const pt_scene* scene, pt_scene_info* info);
    child reference (bit 31 set: primitive index), w[11] 0).  nodes: host
    [cap][12] (cap >= n - 1), *n_nodes the count written, *root the root
    reference (bit 31 set when n == 1; 0xFFFFFFFF when n == 0), *depth the
-   tree depth.  PT_EINVAL for n < 0, a NULL output, cap too small or
-   non-finite bounds; PT_EUNSUPPORTED when an extent exceeds the fp16
-   range. */
+   tree depth.  PT_EINVAL for n < 0, a NULL output, cap too small,
+   non-finite bounds or an inverted box (lo > hi on some axis);
+   PT_EUNSUPPORTED when an extent exceeds the fp16 range. */
 PT_API pt_status pt_build_bvh_host(int64_t n, const float* lo, const float* hi, uint32_t* nodes, int64_t cap,
                                    int64_t* n_nodes, uint32_t* root, int32_t* depth);
 

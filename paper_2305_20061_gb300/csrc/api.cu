@@ -607,6 +607,8 @@ PT_API pt_status pt_build_bvh_host(int64_t n, const float* lo, const float* hi, 
     if (n < 0 || !n_nodes || !root || !depth || (n > 0 && (!lo || !hi))) return PT_EINVAL;
     if (n >= (int64_t)kLeafBit - 1) return PT_EINVAL;
     if (!finite3(lo, 3 * n) || !finite3(hi, 3 * n)) return PT_EINVAL;
+    for (int64_t i = 0; i < 3 * n; ++i)
+        if (lo[i] > hi[i]) return PT_EINVAL;   // an inverted box would give negative extents
     if (n > 1 && (!nodes || cap < n - 1)) return PT_EINVAL;
     BuildInput bin;
     bin.n_prims = n;

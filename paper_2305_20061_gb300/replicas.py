@@ -32,8 +32,16 @@ def max_over_ranks(value: float, device) -> float:
 
 def average_images(img: torch.Tensor) -> torch.Tensor:
     """Mean of the ranks' images (each the mean of its own samples, all ranks the
-    same spp): the image of all ranks' samples together.  In place; returns img."""
+    same spp): the image of all ranks' samples together.  Every rank gathers all
+    partial images, promotes them to FP64 and adds them in rank order before the
+    one division and the cast back, so the result is the same on every rank and
+    does not depend on the collective's reduction order.  In place; returns img."""
     if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
-        dist.all_reduce(img, op=dist.ReduceOp.SUM)
-        img /= dist.get_world_size()
+        world = dist.get_world_size()
+        parts = [torch.empty_like(img) for _ in range(world)]
+        dist.all_gather(parts, img.contiguous())
+        acc = torch.zeros(img.shape, dtype=torch.float64, device=img.device)
+        for p in parts:                     # rank order
+            acc += p.to(torch.float64)
+        img.copy_((acc / world).to(img.dtype))
     return img

@@ -121,3 +121,15 @@ def test_empty_and_errors(pt):
     with pytest.raises(pt.PTError) as e:
         pt.build_bvh_host(huge_lo, huge_hi)
     assert e.value.status == pt.PT_EUNSUPPORTED
+
+
+def test_inverted_box_is_refused(pt):
+    """A box with lo > hi on some axis would pack negative extents: refused."""
+    lo = np.array([[0, 0, 0], [1, 1, 1]], np.float32)
+    hi = np.array([[1, 1, 1], [2, 0.5, 2]], np.float32)   # second box inverted in y
+    with pytest.raises(pt.PTError) as e:
+        pt.build_bvh_host(lo, hi)
+    assert e.value.status == pt.PT_EINVAL
+    # a flat box (lo == hi) is fine
+    nodes, root, _ = pt.build_bvh_host(lo, np.array([[1, 1, 1], [2, 1, 2]], np.float32))
+    assert len(nodes) == 1
