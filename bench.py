@@ -46,11 +46,17 @@ FLOP_PER_EVAL = 2 * (3 * 128 * 128 + 128 * 3)   # 99,072: three 128x128 layers +
 TC_FLOP_PER_EVAL = 2 * 3 * 128 * 128            # 98,304 in the three hidden layers
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# FP32 operations per traversal step as implemented in k_bounce (node slab test of both children, sphere,
-# axis-aligned quad and watertight triangle tests)
+# Algorithmic FP32 FLOPs of the traversal's tests: a slab test of one child box is 12 (six plane distances,
+# each a subtraction and a multiplication), a node fetch tests both children (24); a sphere test 20; an
+# axis-aligned quad 10; the watertight triangle test 41 (9 vertex differences, 12 for the shear, 9 for the
+# three edge functions, 2 for the determinant, 8 for the scaled distance, 1 division).
+FLOP_NODE, FLOP_SPHERE, FLOP_QUAD, FLOP_TRI = 24, 20, 10, 41
+# FP32 instructions per traversal step as implemented (node step of both children, sphere, quad and
+# triangle tests), for the secondary issue-rate fraction
 OPS_NODE, OPS_SPHERE, OPS_QUAD, OPS_TRI = 58, 36, 12, 46
-# algorithmic bytes per traversal step and per ray-bounce of queue traffic
-BYTES_NODE, BYTES_SPHERE, BYTES_QUAD, BYTES_TRI, BYTES_RAY = 48, 16, 32, 48, 140
+# algorithmic bytes per traversal step (a node fetch reads both children's boxes and references), per ray of
+# the traversal kernel (origin and direction in, hit out) and per ray-bounce of trace + shade queue traffic
+BYTES_NODE, BYTES_SPHERE, BYTES_QUAD, BYTES_TRI, BYTES_RAY_TRACE, BYTES_RAY = 48, 16, 32, 48, 40, 140
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -207,12 +213,39 @@ def bench_reference(args):
 
 
 def trace_kernels(pt, ctx, vertices):
-    """Name of the traversal kernels of the last render and their launches
-    per chunk: one k_trace + k_bounce pair per vertex on the wavefront
-    schedule, one k_paths launch on the path-per-thread schedule."""
+    """Name of the traversal kernel of the last render (profile kind
+    "trace") and its launches per chunk: k_trace once per vertex on the
+    wavefront schedule (shading, k_bounce, is timed apart), one k_paths
+    launch (traversal and shading together) on the path-per-thread
+    schedule."""
     if pt.last_render_schedule(ctx) == "paths":
         return "k_paths", 1
-    return "k_trace+k_bounce", vertices
+    return "k_trace", vertices
+
+
+def traversal_roofline(work, t_ms, kernel, launches, ffma_tflops, clock, context):
+    """Roofline of the traversal kernel over one frame: algorithmic FLOPs of
+    its tests (FLOP_*) per frame / its device time per frame, against the
+    FP32 FMA rate measured on this device; the issue-rate fraction of the
+    implementation's own instruction counts rides along."""
+    flop = (FLOP_NODE * work["nodes"] + FLOP_SPHERE * work["sphere"] + FLOP_QUAD * work["quad"] +
+            FLOP_TRI * work["triangle"])
+    achieved = flop / (t_ms * 1e-3) / 1e12
+    ops = (OPS_NODE * work["nodes"] + OPS_SPHERE * work["sphere"] + OPS_QUAD * work["quad"] +
+           OPS_TRI * work["triangle"])
+    issue_peak = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6 / 1e12
+    return {"kernel": kernel, "bound": "alu", "achieved": achieved, "peak": ffma_tflops, "unit": "TFLOP/s",
+            "frac": achieved / ffma_tflops, "traffic": None,
+            "per_unit": f"FP32 FLOP per node fetch (two child slabs) {FLOP_NODE}, per sphere/quad/triangle test "
+                        f"{FLOP_SPHERE}/{FLOP_QUAD}/{FLOP_TRI}; {work['nodes']} node fetches and "
+                        f"{work['sphere']}/{work['quad']}/{work['triangle']} sphere/quad/triangle tests per frame "
+                        f"over {launches} launches, {t_ms:.3f} ms of {kernel} per frame{context}",
+            "peak_note": "FP32 FMA rate measured live by pt_microbench_ffma (8 chains per thread, 2048 threads "
+                         "per SM, CUDA events)",
+            "issue_frac": ops * 1e-12 / (t_ms * 1e-3) / issue_peak,
+            "issue_note": f"implementation's FP32 instructions per node/sphere/quad/triangle step {OPS_NODE}/"
+                          f"{OPS_SPHERE}/{OPS_QUAD}/{OPS_TRI} over {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x "
+                          f"{clock:.0f} MHz"}
 
 
 def profiled_split(pt, ctx, run_frame, steps, n_prof=3):
@@ -407,16 +440,17 @@ def bench_ours(args):
     # live roofline of the dominant kernel of the timed frames
     meas, which = peaks()
     clock = float(meas.get("sm_max_mhz", 2070.0))
-    dom = max(("trace", "nif", "reduce"), key=lambda k: prof[k][0])
+    dom = max(("trace", "shade", "nif", "reduce"), key=lambda k: prof[k][0])
     big_scene = scene.info()["node_bytes"] > 128 * 1024 * 1024   # BVH larger than L2
     if dom == "nif" and rprec in ("bf16", "fp8"):
-        peak = float(meas.get("bf16_tflops_sustained", meas["bf16_tflops"])) * (2.0 if rprec == "fp8" else 1.0)
+        peak = float(meas["bf16_tflops"]) * (2.0 if rprec == "fp8" else 1.0)
         achieved = evals * TC_FLOP_PER_EVAL / (nif_ms * 1e-3) / 1e12
         roof = {"kernel": "k_nif_tc" if rprec == "bf16" else "k_nif_fp8", "bound": "tensor", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "per_unit": f"{TC_FLOP_PER_EVAL} tensor FLOP per NIF evaluation x {evals} evaluations per launch",
-                "peak_note": (f"dense BF16, sustained ({which})" if rprec == "bf16" else
-                              f"dense FP8 = sustained BF16 ({which}) x 2 (nominal 4.5 / 2.25 PFLOP/s)")}
+                "peak_note": (f"dense BF16 cuBLAS burst ({which}; the NIF launches are timed in a region of well "
+                              f"under a second)" if rprec == "bf16" else
+                              f"dense FP8 = BF16 cuBLAS burst ({which}) x 2 (nominal 4.5 / 2.25 PFLOP/s)")}
     elif dom == "nif":
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * clock * 1e6 / 1e12
         achieved = evals * FLOP_PER_EVAL / (nif_ms * 1e-3) / 1e12
@@ -424,29 +458,29 @@ def bench_ours(args):
                 "frac": achieved / peak, "traffic": None,
                 "per_unit": f"{FLOP_PER_EVAL} FLOP per NIF evaluation x {evals} evaluations per launch",
                 "peak_note": f"FP32 FFMA derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clock:.0f} MHz"}
-    elif big_scene:
+    elif big_scene and dom == "trace":
         nbytes = (BYTES_NODE * work["nodes"] + BYTES_SPHERE * work["sphere"] + BYTES_QUAD * work["quad"] +
-                  BYTES_TRI * work["triangle"] + BYTES_RAY * rays)
+                  BYTES_TRI * work["triangle"] + BYTES_RAY_TRACE * rays)
         peak = float(meas["hbm_gbs"])
         achieved = nbytes / (trace_ms * 1e-3) / 1e9
         roof = {"kernel": trace_kernel, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
                 "per_unit": f"bytes per node fetch {BYTES_NODE}, per sphere/quad/triangle test "
-                            f"{BYTES_SPHERE}/{BYTES_QUAD}/{BYTES_TRI}, per ray {BYTES_RAY}; {work['nodes']} node "
-                            f"fetches, {work['triangle']} triangle tests, {rays} rays per frame",
+                            f"{BYTES_SPHERE}/{BYTES_QUAD}/{BYTES_TRI}, per ray {BYTES_RAY_TRACE} (origin and "
+                            f"direction in, hit out); {work['nodes']} node fetches, {work['triangle']} triangle "
+                            f"tests, {rays} rays per frame over {trace_launches} launches",
                 "peak_note": f"HBM copy bandwidth ({which}); BVH {scene.info()['node_bytes'] / 2**20:.0f} MiB > L2"}
-    else:
-        ops = (OPS_NODE * work["nodes"] + OPS_SPHERE * work["sphere"] + OPS_QUAD * work["quad"] +
-               OPS_TRI * work["triangle"])
-        peak = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6 / 1e12
-        achieved = ops / (trace_ms * 1e-3) / 1e12
-        roof = {"kernel": trace_kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
+    elif dom == "shade":
+        shade_ms = prof["shade"][0] / args.steps
+        achieved = BYTES_RAY * rays / (shade_ms * 1e-3) / 1e9
+        peak = float(meas["hbm_gbs"])
+        roof = {"kernel": "k_bounce", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
-                "per_unit": f"FP32 ops per node fetch {OPS_NODE}, per sphere/quad/triangle test "
-                            f"{OPS_SPHERE}/{OPS_QUAD}/{OPS_TRI}; {work['nodes']} node fetches and "
-                            f"{work['sphere'] + work['quad'] + work['triangle']} primitive tests per frame "
-                            f"({trace_launches} launches)",
-                "peak_note": f"FP32 issue rate derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x {clock:.0f} MHz"}
+                "per_unit": f"{BYTES_RAY} queue bytes per ray-bounce x {rays} rays per frame",
+                "peak_note": f"HBM copy bandwidth ({which})"}
+    else:
+        roof = traversal_roofline(work, trace_ms, trace_kernel, trace_launches, pt.ffma_rate_tflops(local), clock,
+                                  "")
 
     # end to end through the C ABI with host buffers: scene + weights in, image out
     e2e = None
@@ -750,17 +784,8 @@ def bench_c5(args):
                 "per_unit": f"{CACHE_FLOP_PER_QUERY} FLOP per query x {queries} queries per launch",
                 "peak_note": f"FP32 FFMA derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {clock:.0f} MHz"}
     else:
-        t_tr = prof_render["trace"][0]
-        ops = (OPS_NODE * work["nodes"] + OPS_SPHERE * work["sphere"] + OPS_QUAD * work["quad"] +
-               OPS_TRI * work["triangle"])
-        peak = SM_COUNT * FP32_LANES_PER_SM * clock * 1e6 / 1e12
-        achieved = ops / (t_tr * 1e-3) / 1e12
-        roof = {"kernel": trace_kernel, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s",
-                "frac": achieved / peak, "traffic": None,
-                "per_unit": f"FP32 ops per node fetch {OPS_NODE}, per triangle test {OPS_TRI}; {work['nodes']} node "
-                            f"fetches and {work['triangle']} triangle tests in the cached render "
-                            f"({trace_launches} launches, {t_tr:.3f} ms)",
-                "peak_note": f"FP32 issue rate derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x {clock:.0f} MHz"}
+        roof = traversal_roofline(work, prof_render["trace"][0], trace_kernel, trace_launches,
+                                  pt.ffma_rate_tflops(local), clock, " (the cached render)")
 
     e2e = None
     if not args.no_e2e:

@@ -69,6 +69,7 @@ typedef enum pt_precision {
 #define PT_ERR_TIMEOUT        0x8u   /* a bounded device wait gave up */
 #define PT_ERR_ITER_CAP       0x10u  /* traversal exceeded its iteration cap */
 #define PT_ERR_BAD_NODE       0x20u  /* traversal met a node reference outside the node array */
+#define PT_ERR_UNREADABLE     0x80000000u  /* pt_device_error_bits could not read the word */
 
 typedef struct pt_ctx pt_ctx;
 typedef struct pt_scene pt_scene;
@@ -80,7 +81,9 @@ typedef struct pt_cache pt_cache;
 /* ------------------------------------------------------------------------ */
 
 /* Create a context on CUDA device `device` (made current for the calling
-   thread).  *out receives the handle; release it with pt_destroy. */
+   thread).  *out receives the handle; release it with pt_destroy.  It also
+   resolves, once per device, the fixed scratch array of pt_render_noalloc
+   (about 43 MiB that the driver reserves for the library's lifetime). */
 PT_API pt_status pt_create(pt_ctx** out, int device);
 PT_API void pt_destroy(pt_ctx* ctx);
 
@@ -92,6 +95,12 @@ PT_API const char* pt_last_error(const pt_ctx* ctx);
    *bits (may be NULL).  Returns PT_EDEVICE if any bit was set, PT_ECUDA if
    the stream reported a CUDA error. */
 PT_API pt_status pt_check(pt_ctx* ctx, void* stream, uint32_t* bits);
+
+/* The context's device error word without clearing it: waits for all work
+   on the context's device (cudaDeviceSynchronize), then returns the PT_ERR_*
+   bits set since the last pt_check.  Returns PT_ERR_UNREADABLE alone when
+   ctx is NULL or the word cannot be read (a CUDA failure). */
+PT_API uint32_t pt_device_error_bits(pt_ctx* ctx);
 
 /* ------------------------------------------------------------------------ */
 /* Scenes (Section 3.1.1: the scene description is replicated per core and  */
@@ -265,15 +274,26 @@ typedef struct pt_render_cfg {
     int32_t first_sample;      /* sample index of the first path per pixel (Philox counter word 1 =
                                   first_sample + s): disjoint ranges render independent sample sets */
     int32_t schedule;          /* pt_schedule: how the paths of a chunk are scheduled (same results) */
+    int32_t cache_vertex;      /* pt_render with a radiance cache: paths end in the cache at this vertex
+                                  (>= 2); 0 without a cache.  pt_render_pixels and pt_render_noalloc
+                                  need 0; pt_render_cached takes its own argument (0 here or equal) */
 } pt_render_cfg;
 
-/* Render the image: d_image [height][width][3] float, the mean over spp
-   paths of each pixel.  Path (pixel p, sample s) draws Philox-4x32-10 words
-   with key (seed, 0) and counter (p, first_sample + s, k, 0) at vertex k
-   (k = 0 for the camera jitter).  `nif` is required when the scene's environment is a NIF
-   and ignored otherwise. */
-PT_API pt_status pt_render(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, const pt_render_cfg* cfg,
-                           float* d_image, void* stream);
+/* Render the image (Section 3.3: paths traced through the scene, escapes
+   shaded by the NIF): d_image [height][width][3] float, caller-owned device
+   memory, the mean over spp paths of each pixel.  Path (pixel p, sample s)
+   draws Philox-4x32-10 words with key (seed, 0) and counter (p,
+   first_sample + s, k, 0) at vertex k (k = 0 for the camera jitter).  `nif`
+   is required when the scene's environment is a NIF and ignored otherwise.
+   `cache` (nullable): a radiance cache on the same device; with it, paths
+   that reach vertex cfg->cache_vertex (>= 2) end there with the cache's
+   prediction of the radiance leaving that vertex (the same paths and image
+   as pt_render_cached over all pixels).  PT_EINVAL when cache and
+   cfg->cache_vertex do not go together (a cache needs cache_vertex >= 2,
+   no cache needs 0).  Asynchronous on `stream`; device-side failures are
+   reported through the error word (pt_check, pt_device_error_bits). */
+PT_API pt_status pt_render(pt_ctx* ctx, const pt_scene* scene, const pt_nif* nif, const pt_cache* cache,
+                           const pt_render_cfg* cfg, float* d_image, void* stream);
 
 /* Render all spp paths of a list of pixels.  d_pixels: [n_pix] int64 pixel
    indices (NULL = all width*height pixels in order).  Outputs: d_pixel_rgb
@@ -309,19 +329,32 @@ PT_API pt_status pt_last_render_work(pt_ctx* ctx, int64_t* work, int32_t n);
 
 /* Kernel timing.  While enabled, the library records a CUDA event pair on
    the launching stream around each of its kernel launches and accumulates
-   the device time per kernel kind: 0 trace/shade step, 1 NIF evaluation,
-   2 sample reduction, 3 other (training and utilities), 4 radiance-cache
-   queries.  pt_profile_read
-   synchronises the device, writes up to n kinds of total milliseconds and
-   launch counts (either pointer may be NULL) and resets the totals. */
+   the device time per kernel kind: 0 traversal (k_trace of each wavefront
+   vertex, or the whole path-per-thread launch k_paths, which also shades),
+   1 NIF evaluation, 2 sample reduction, 3 other (training and utilities),
+   4 radiance-cache queries, 5 wavefront shading and compaction (k_bounce).
+   pt_profile_read synchronises the device, writes up to n kinds of total
+   milliseconds and launch counts (either pointer may be NULL) and resets
+   the totals. */
 #define PT_KIND_TRACE 0
 #define PT_KIND_NIF 1
 #define PT_KIND_REDUCE 2
 #define PT_KIND_OTHER 3
 #define PT_KIND_CACHE 4    /* radiance-cache queries */
-#define PT_N_KINDS 5
+#define PT_KIND_SHADE 5    /* wavefront shading step */
+#define PT_N_KINDS 6
 PT_API pt_status pt_profile_enable(pt_ctx* ctx, int32_t enable);
 PT_API pt_status pt_profile_read(pt_ctx* ctx, double* ms, int64_t* launches, int32_t n);
+
+/* Measurement helper (the paper has no counterpart): the FP32 FMA rate of
+   the current device, the denominator of the traversal roofline.  Launches
+   one kernel on `stream` in which every thread of 8 resident 256-thread
+   blocks per SM runs 8 independent chains of `iters` dependent FMAs;
+   *flop receives the FLOPs it performs (2 per FMA), to be divided by the
+   launch's event-timed duration.  d_sink: one caller-owned device float,
+   never written for the values used.  PT_EINVAL for iters < 1 or NULL
+   pointers. */
+PT_API pt_status pt_microbench_ffma(int64_t iters, float* d_sink, double* flop, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Building blocks of the same path, exposed for testing and for callers    */
@@ -439,9 +472,11 @@ PT_API pt_status pt_render_cached(pt_ctx* ctx, const pt_scene* scene, const pt_n
    cudaFree or other allocating call.  Limits: at most 262144 pixels per
    frame (one sample of the frame must fit the array) and the FP32 network;
    larger frames return PT_EINVAL, other precisions PT_EUNSUPPORTED.
-   The scene's device must be current.  The first call on a device looks up
-   the array's device address there; make that first call before capturing
-   the stream into a graph.  All calls share the array and it keeps the last
+   The scene's device must be current.  The array's device address is
+   looked up by pt_create on that device (which is when the driver loads
+   and reserves the array, also under lazy module loading), so the render
+   call itself only reads it; no object of this library survives a
+   cudaDeviceReset.  All calls share the array and it keeps the last
    call's contents (the call clears what must start at zero), so calls whose
    GPU work overlaps race: serialise them on one stream.  d_err (nullable,
    caller-owned device word) receives the PT_ERR_* bits the kernels set;

@@ -353,6 +353,9 @@ PT_API pt_status pt_create(pt_ctx** out, int device)
         ctx->paths_threads[0] = paths_resident_threads(false, ctx->sm_count);
         ctx->paths_threads[1] = paths_resident_threads(true, ctx->sm_count);
     }
+    // the no-allocation render path's fixed scratch: resolved here so that the driver reserves it now,
+    // not inside a later pt_render_noalloc call
+    if (e == cudaSuccess) e = noalloc_setup(device, nullptr);
     if (e != cudaSuccess) {
         cudaFree(ctx->d_err);
         cudaFree(ctx->counters);
@@ -402,6 +405,18 @@ PT_API pt_status pt_check(pt_ctx* ctx, void* stream, uint32_t* bits)
         return fail(ctx, PT_EDEVICE, buf);
     }
     return PT_OK;
+}
+
+PT_API uint32_t pt_device_error_bits(pt_ctx* ctx)
+{
+    if (!ctx) return PT_ERR_UNREADABLE;
+    uint32_t h = 0;
+    if (cudaSetDevice(ctx->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&h, ctx->d_err, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return PT_ERR_UNREADABLE;
+    }
+    return h;
 }
 
 // ---------------------------------------------------------------------------
@@ -1301,7 +1316,8 @@ static pt_status render_launches(pt_ctx* ctx, const pt_scene* sc, const pt_nif* 
             bp.qout = ctx->q[k & 1];
             bp.count_in = ctx->counters + (k - 1);
             bp.count_out = ctx->counters + k;
-            PT_CUDA(timed(ctx, PT_KIND_TRACE, s, [&] { return launch_bounce(bp, ctx->sm_count, s); }));
+            PT_CUDA(timed(ctx, PT_KIND_TRACE, s, [&] { return launch_trace(bp, ctx->sm_count, s); }));
+            PT_CUDA(timed(ctx, PT_KIND_SHADE, s, [&] { return launch_shade(bp, ctx->sm_count, s); }));
         }
         if (sc->dev.env_is_nif) {
             st = eval_nif_escapes(ctx, nf, cfg->precision, sc->dev.has_emission, s);
@@ -1460,6 +1476,7 @@ PT_API pt_status pt_render_pixels(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
 {
     pt_status st = check_cfg(ctx, sc, nf, cfg);
     if (st != PT_OK) return st;
+    if (cfg->cache_vertex != 0) return fail(ctx, PT_EINVAL, "cache_vertex needs a cache (pt_render, pt_render_cached)");
     return render_impl(ctx, sc, nf, cfg, (uint32_t)cfg->first_sample, nullptr, 0, 0, nullptr, n_pix, d_pixels,
                        d_pixel_rgb, d_slot_rgb, d_hit_ids, (cudaStream_t)stream);
 }
@@ -1473,6 +1490,8 @@ PT_API pt_status pt_render_cached(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
     if (st != PT_OK) return st;
     if ((cache != nullptr) != (cache_vertex != 0) || cache_vertex < 0 || cache_vertex == 1)
         return fail(ctx, PT_EINVAL, "cache and cache_vertex >= 2 go together");
+    if (cfg->cache_vertex != 0 && cfg->cache_vertex != cache_vertex)
+        return fail(ctx, PT_EINVAL, "cfg->cache_vertex differs from the cache_vertex argument");
     if (cache && cache->ctx->device != ctx->device) return fail(ctx, PT_EINVAL, "cache lives on another device");
     if (rec_vertex < 0 || rec_vertex > cfg->max_depth || (rec_vertex > 0 && !d_rec))
         return fail(ctx, PT_EINVAL, "rec_vertex must be in [0, max_depth] with d_rec");
@@ -1480,11 +1499,15 @@ PT_API pt_status pt_render_cached(pt_ctx* ctx, const pt_scene* sc, const pt_nif*
                        d_pixels, d_pixel_rgb, d_slot_rgb, d_hit_ids, (cudaStream_t)stream);
 }
 
-PT_API pt_status pt_render(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_render_cfg* cfg,
-                           float* d_image, void* stream)
+PT_API pt_status pt_render(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, const pt_cache* cache,
+                           const pt_render_cfg* cfg, float* d_image, void* stream)
 {
     if (!d_image) return fail(ctx, PT_EINVAL, "null image");
-    return pt_render_pixels(ctx, sc, nf, cfg, 0, nullptr, d_image, nullptr, nullptr, stream);
+    if (!cfg) return fail(ctx, PT_EINVAL, "null cfg");
+    if (!cache) return pt_render_pixels(ctx, sc, nf, cfg, 0, nullptr, d_image, nullptr, nullptr, stream);
+    if (cfg->cache_vertex < 2) return fail(ctx, PT_EINVAL, "a cache needs cfg->cache_vertex >= 2");
+    return pt_render_cached(ctx, sc, nf, cache, cfg->cache_vertex, 0, cfg, 0, nullptr, d_image, nullptr, nullptr,
+                            nullptr, stream);
 }
 
 PT_API pt_status pt_kernel_launches(uint64_t* count)

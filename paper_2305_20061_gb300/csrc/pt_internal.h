@@ -151,12 +151,17 @@ struct NifEvalParams {
 };
 
 // kernel launchers (trace.cu)
-cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s);
+cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s);   // launch_trace + launch_shade
+cudaError_t launch_trace(const BounceParams& p, int sm_count, cudaStream_t s);    // closest hits of vertex k
+cudaError_t launch_shade(const BounceParams& p, int sm_count, cudaStream_t s);    // shading + compaction
 // path-per-thread schedule: every vertex of the chunk's paths in one launch;
 // resident_threads (from paths_resident_threads) caps the grid at one wave
 cudaError_t launch_paths(const BounceParams& p, int resident_threads, cudaStream_t s);
 // threads of k_paths resident at once on the device (0 if the query failed)
 int paths_resident_threads(bool wide, int sm_count);
+// Looks up (once per device; `device` current) the fixed scratch array of
+// pt_render_noalloc, which makes the driver load and reserve it.
+cudaError_t noalloc_setup(int device, unsigned char** out);
 cudaError_t launch_reduce(const float* slot_L, float* pix, uint32_t n_pix, uint32_t s_count, int first, float scale,
                           cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t* p, int64_t n, int32_t v, cudaStream_t s);

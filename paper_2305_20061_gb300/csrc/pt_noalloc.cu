@@ -13,9 +13,12 @@
 // allocating library routine.
 //
 // The array exists once per GPU that loads the library and stays until the
-// process exits.  Every call shares it, so calls whose GPU work overlaps (on
-// two streams, or from two threads) race and corrupt each other's results;
-// serialise them on one stream.
+// process exits.  Its address is looked up (and the array reserved by the
+// driver) when pt_create makes a context on the device, before any render
+// call.  Every call shares it, so calls whose GPU work overlaps (on two
+// streams, or from two threads) race and corrupt each other's results;
+// serialise them on one stream.  The cached address does not survive a
+// cudaDeviceReset, after which no object of this library is valid anyway.
 #include <algorithm>
 #include <mutex>
 
@@ -38,10 +41,16 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_dev_ptr[kMaxDevices] = {};
 
-// Device address of g_scratch on `device` (which must be current).  Looked
-// up once per device on the first call there.
-cudaError_t scratch_address(int device, unsigned char** out)
+}  // namespace
+
+// Device address of g_scratch on `device` (which must be current), looked up
+// once per device.  pt_create calls this for its device: the lookup is where
+// the driver loads this file's module and reserves the array (under lazy
+// module loading that would otherwise happen inside the first render call),
+// so pt_render_noalloc itself only reads the cached address.
+cudaError_t noalloc_setup(int device, unsigned char** out)
 {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_dev_ptr[device]) {
         void* p = nullptr;
@@ -49,10 +58,11 @@ cudaError_t scratch_address(int device, unsigned char** out)
         if (e != cudaSuccess) return e;
         g_dev_ptr[device] = static_cast<unsigned char*>(p);
     }
-    *out = g_dev_ptr[device];
+    if (out) *out = g_dev_ptr[device];
     return cudaSuccess;
 }
 
+namespace {
 }  // namespace
 }  // namespace ptk
 
@@ -74,11 +84,12 @@ extern "C" PT_API pt_status pt_render_noalloc(const pt_scene* scene, const pt_ni
     if (n_pix > (int64_t)kMaxSlots) return PT_EINVAL;   // one sample of the frame must fit the fixed scratch
     if (sv->env_is_nif && !nif) return PT_EINVAL;
     if (sv->env_is_nif && cfg->precision != PT_FP32) return PT_EUNSUPPORTED;
+    if (cfg->cache_vertex != 0) return PT_EUNSUPPORTED;   // no radiance cache on this path
     const int64_t n_slots = n_pix * (int64_t)cfg->spp;
     if (n_slots > 0xFFFFFFFFll) return PT_EINVAL;
 
     unsigned char* base = nullptr;
-    if (scratch_address(device, &base) != cudaSuccess) return PT_ECUDA;
+    if (noalloc_setup(device, &base) != cudaSuccess) return PT_ECUDA;
     uint32_t* counters = reinterpret_cast<uint32_t*>(base);
     unsigned long long* stats = reinterpret_cast<unsigned long long*>(base + 512);
     uint32_t* err = d_err ? d_err : reinterpret_cast<uint32_t*>(base + 1536);

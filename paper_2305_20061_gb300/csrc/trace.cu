@@ -584,14 +584,26 @@ int grid_for(int64_t n, int block, int sm_count, int per_sm)
 
 }  // namespace
 
-cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s)
+cudaError_t launch_trace(const BounceParams& p, int sm_count, cudaStream_t s)
 {
-    // traversal: persistent, 4 resident blocks of 256 threads per SM; shading: grid-stride over the queue
+    // traversal: persistent, 4 resident blocks of 256 threads per SM
     if (p.sc.wnodes) k_trace<true><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
     else k_trace<false><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
     count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shade(const BounceParams& p, int sm_count, cudaStream_t s)
+{
+    // shading: grid-stride over the queue
     k_bounce<<<sm_count * 8, 256, 0, s>>>(p); count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s)
+{
+    const cudaError_t e = launch_trace(p, sm_count, s);
+    return e != cudaSuccess ? e : launch_shade(p, sm_count, s);
 }
 
 int paths_resident_threads(bool wide, int sm_count)

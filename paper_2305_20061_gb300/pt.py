@@ -23,7 +23,7 @@ PT_OK, PT_EINVAL, PT_ENOMEM, PT_ECUDA, PT_EDEVICE, PT_EUNSUPPORTED, PT_EIO = ran
 PT_FP32, PT_BF16, PT_FP8E4M3 = 0, 1, 2
 PRECISIONS = {"fp32": PT_FP32, "bf16": PT_BF16, "fp8": PT_FP8E4M3}
 ERR_BITS = {0x1: "stack_overflow", 0x2: "queue_overflow", 0x4: "nonfinite", 0x8: "timeout", 0x10: "iter_cap",
-            0x20: "bad_node"}
+            0x20: "bad_node", 0x80000000: "unreadable"}
 
 P = C.c_void_p
 I32 = C.c_int32
@@ -51,7 +51,7 @@ class NifDesc(C.Structure):
 class RenderCfg(C.Structure):
     _fields_ = [("width", I32), ("height", I32), ("spp", I32), ("max_depth", I32), ("seed", U32),
                 ("rr", I32), ("rr_start", I32), ("precision", I32), ("chunk_slots", I64),
-                ("first_sample", I32), ("schedule", I32)]
+                ("first_sample", I32), ("schedule", I32), ("cache_vertex", I32)]
 
 
 class TrainCfg(C.Structure):
@@ -105,7 +105,9 @@ def lib():
             "pt_nif_param_count": ([P], I64),
             "pt_nif_get_params": ([P, P, P], I32),
             "pt_nif_eval": ([P, P, I32, I64, P, P, P], I32),
-            "pt_render": ([P, P, P, P, P, P], I32),
+            "pt_render": ([P, P, P, P, P, P, P], I32),
+            "pt_device_error_bits": ([P], U32),
+            "pt_microbench_ffma": ([I64, P, P, P], I32),
             "pt_render_pixels": ([P, P, P, P, I64, P, P, P, P, P], I32),
             "pt_last_render_counts": ([P, P, I32], I32),
             "pt_philox": ([P, U32, U32, I64, P, P, P], I32),
@@ -468,12 +470,13 @@ SCHEDULES = {"auto": 0, "wavefront": 1, "paths": 2}
 
 
 def make_cfg(cfg: I.RenderCfg, precision: str = "fp32", chunk_slots: int = 0, first_sample: int = 0,
-             schedule: str = "auto") -> RenderCfg:
+             schedule: str = "auto", cache_vertex: int = 0) -> RenderCfg:
     return RenderCfg(cfg.width, cfg.height, cfg.spp, cfg.max_depth, cfg.seed, int(cfg.rr), cfg.rr_start,
-                     PRECISIONS[precision], int(chunk_slots), int(first_sample), SCHEDULES[schedule])
+                     PRECISIONS[precision], int(chunk_slots), int(first_sample), SCHEDULES[schedule],
+                     int(cache_vertex))
 
 
-KINDS = ("trace", "nif", "reduce", "other", "cache")
+KINDS = ("trace", "nif", "reduce", "other", "cache", "shade")
 
 
 def profile_enable(ctx: Context, enable: bool = True) -> None:
@@ -490,14 +493,42 @@ def profile_read(ctx: Context) -> dict:
 
 def render(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderCfg, precision: str = "fp32",
            out: Optional[torch.Tensor] = None, chunk_slots: int = 0, first_sample: int = 0,
-           stream=None, schedule: str = "auto") -> torch.Tensor:
-    """pt_render: returns the [H, W, 3] float32 image on the context's device."""
+           stream=None, schedule: str = "auto", cache: Optional["Cache"] = None,
+           cache_vertex: int = 0) -> torch.Tensor:
+    """pt_render: returns the [H, W, 3] float32 image on the context's device
+    (with a radiance cache, paths end in it at cache_vertex)."""
     if out is None:
         out = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=f"cuda:{ctx.device}")
-    c = make_cfg(cfg, precision, chunk_slots, first_sample, schedule)
-    ctx._raise(lib().pt_render(ctx.h, scene.h, nif.h if nif is not None else None, C.byref(c), _dptr(out),
-                               _stream(stream)))
+    c = make_cfg(cfg, precision, chunk_slots, first_sample, schedule, cache_vertex)
+    ctx._raise(lib().pt_render(ctx.h, scene.h, nif.h if nif is not None else None,
+                               cache.h if cache is not None else None, C.byref(c), _dptr(out), _stream(stream)))
     return out
+
+
+def ffma_rate_tflops(device: int, iters: int = 1 << 16, reps: int = 3) -> float:
+    """FP32 FMA rate of the device in TFLOP/s: pt_microbench_ffma timed with
+    CUDA events on the current stream (best of reps, after one warm-up)."""
+    dev = f"cuda:{device}"
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    flop = C.c_double(0)
+    s = torch.cuda.current_stream(device)
+    best = 0.0
+    for i in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        st = lib().pt_microbench_ffma(iters, _dptr(sink), C.byref(flop), _stream(s))
+        e1.record(s)
+        if st != PT_OK:
+            raise PTError(st, "pt_microbench_ffma failed")
+        torch.cuda.synchronize(dev)
+        if i:
+            best = max(best, flop.value / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
+def device_error_bits(ctx: Context) -> int:
+    """pt_device_error_bits: the context's device error word, not cleared."""
+    return int(lib().pt_device_error_bits(ctx.h))
 
 
 def render_pixels(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderCfg, pixels: Optional[torch.Tensor],

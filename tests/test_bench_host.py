@@ -62,4 +62,19 @@ def test_trace_kernel_names_follow_the_schedule():
             return self.sched
 
     assert bench.trace_kernels(FakePt("paths"), None, 8) == ("k_paths", 1)
-    assert bench.trace_kernels(FakePt("wavefront"), None, 8) == ("k_trace+k_bounce", 8)
+    assert bench.trace_kernels(FakePt("wavefront"), None, 8) == ("k_trace", 8)
+
+
+def test_traversal_roofline_counts_algorithmic_flops():
+    """The traversal roofline divides the tests' algorithmic FLOPs (24 per
+    node fetch of two child slabs, 20 per sphere, 10 per quad, 41 per
+    triangle) by the kernel time and the measured FMA rate."""
+    import bench
+    work = {"nodes": 1000, "sphere": 100, "quad": 10, "triangle": 1}
+    r = bench.traversal_roofline(work, 1e-3, "k_trace", 8, 50.0, 2070.0, "")
+    flop = 24 * 1000 + 20 * 100 + 10 * 10 + 41 * 1
+    assert abs(r["achieved"] - flop / 1e-6 / 1e12) < 1e-12
+    assert abs(r["frac"] - r["achieved"] / 50.0) < 1e-15
+    assert r["unit"] == "TFLOP/s" and r["bound"] == "alu" and r["kernel"] == "k_trace"
+    ops = 58 * 1000 + 36 * 100 + 12 * 10 + 46
+    assert abs(r["issue_frac"] - ops / 1e-6 / (152 * 128 * 2070e6)) < 1e-12

@@ -71,3 +71,30 @@ def test_binding_types_every_entry_point(libpt):
     wrong = {n: (len(getattr(L, n).argtypes or []), k) for n, k in arity.items()
              if getattr(L, n).argtypes is None or len(getattr(L, n).argtypes) != k}
     assert not wrong, wrong
+
+
+def _decl(name):
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        m = re.search(r"PT_API\s+([\w\s\*]+?)\b" + name + r"\s*\(([^)]*)\)\s*;", src)
+        if m:
+            return " ".join(m.group(1).split()), [" ".join(p.split()) for p in m.group(2).split(",")]
+    raise KeyError(name)
+
+
+def test_render_and_error_word_signatures():
+    """pt_render takes a nullable radiance cache before the configuration;
+    pt_device_error_bits returns the word itself; the configuration carries
+    the cache vertex."""
+    ret, params = _decl("pt_render")
+    assert ret == "pt_status"
+    assert params[:5] == ["pt_ctx* ctx", "const pt_scene* scene", "const pt_nif* nif", "const pt_cache* cache",
+                          "const pt_render_cfg* cfg"]
+    assert params[5:] == ["float* d_image", "void* stream"]
+    ret, params = _decl("pt_device_error_bits")
+    assert ret == "uint32_t" and params == ["pt_ctx* ctx"]
+    src = open(os.path.join(ROOT, "include", "pt.h")).read()
+    body = src[src.index("typedef struct pt_render_cfg"):src.index("} pt_render_cfg;")]
+    assert "int32_t cache_vertex;" in body
+    from paper_2305_20061_gb300 import pt
+    assert [f for f, _ in pt.RenderCfg._fields_][-1] == "cache_vertex"

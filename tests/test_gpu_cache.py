@@ -422,3 +422,38 @@ def test_cached_render_chunking_is_invisible(pt, ctx):
         ctx.check()
         assert torch.equal(one[1], many[1]) and torch.equal(one[2], many[2])
         assert torch.allclose(one[0], many[0], rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_pt_render_with_cache_equals_render_cached(pt, ctx, precision):
+    """A full cached image from one pt_render call (cache and cfg cache_vertex)
+    is bit for bit pt_render_cached over every pixel: C5 at 1024x1024, 4 spp,
+    cache at vertex 2."""
+    sc, nif, cfg = I.make_scene("C5"), I.nif_init(colour="yuv"), I.CONFIGS["C5"]["cfg"]
+    lo, hi = I.scene_bounds(sc)
+    s, g, c = pt.Scene(ctx, sc), pt.Nif(ctx, nif), pt.Cache(ctx, _cache(lo, hi))
+    img = pt.render(ctx, s, g, cfg, precision, cache=c, cache_vertex=2)
+    ref = pt.render_cached(ctx, s, g, cfg, None, cache=c, cache_vertex=2, precision=precision)[0]
+    ctx.check()
+    assert torch.equal(img.reshape(-1, 3), ref)
+    plain = pt.render(ctx, s, g, cfg, precision)
+    ctx.check()
+    assert not torch.equal(plain, img)        # the cache did end the paths
+
+
+def test_pt_render_cache_arguments(pt, ctx):
+    import ctypes
+    sc = I.make_scene("C1")
+    lo, hi = I.scene_bounds(sc)
+    s, g, c = pt.Scene(ctx, sc), pt.Nif(ctx, I.nif_init()), pt.Cache(ctx, _cache(lo, hi))
+    cfg = I.RenderCfg(8, 8, 1, 3)
+    out = torch.empty((8, 8, 3), device="cuda")
+    for cache, cv in ((c, 0), (c, 1), (None, 2)):
+        k = pt.make_cfg(cfg, cache_vertex=cv)
+        st = pt.lib().pt_render(ctx.h, s.h, g.h, cache.h if cache is not None else None, ctypes.byref(k),
+                                pt._dptr(out), None)
+        assert st == pt.PT_EINVAL, (cache, cv)
+    k = pt.make_cfg(cfg, cache_vertex=2)       # render_pixels has no cache
+    st = pt.lib().pt_render_pixels(ctx.h, s.h, g.h, ctypes.byref(k), 0, None, pt._dptr(out), None, None, None)
+    assert st == pt.PT_EINVAL
+    ctx.check()

@@ -51,6 +51,20 @@ def test_device_wait_gives_up_and_reports(pt, ctx, seconds):
     _still_usable(pt, ctx)
 
 
+def test_device_error_bits_reads_without_clearing(pt, ctx):
+    """pt_device_error_bits shows the word as it stands, as often as asked;
+    pt_check then reports and clears it."""
+    assert ctx.check() == 0
+    assert pt.device_error_bits(ctx) == 0
+    ctx.selftest_wait_timeout(0.02)
+    assert pt.device_error_bits(ctx) == 0x8 and pt.device_error_bits(ctx) == 0x8
+    with pytest.raises(pt.PTError) as e:
+        ctx.check()
+    assert e.value.bits == 0x8
+    assert pt.device_error_bits(ctx) == 0
+    assert pt.lib().pt_device_error_bits(None) == 0x80000000          # PT_ERR_UNREADABLE
+
+
 def test_wait_selftest_arguments(pt, ctx):
     for bad in (0.0, -1.0, 3.0):
         with pytest.raises(pt.PTError) as e:

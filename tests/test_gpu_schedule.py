@@ -137,7 +137,7 @@ def test_schedule_argument_checked(pt, ctx):
     c = pt.make_cfg(I.RenderCfg(8, 8, 1, 2))
     c.schedule = 3
     out = torch.empty((8, 8, 3), dtype=torch.float32, device="cuda")
-    st = pt.lib().pt_render(ctx.h, s.h, g.h, ctypes.byref(c), pt._dptr(out), None)
+    st = pt.lib().pt_render(ctx.h, s.h, g.h, None, ctypes.byref(c), pt._dptr(out), None)
     assert st == pt.PT_EINVAL
     ctx.check()
 
