@@ -9,16 +9,17 @@
 // 32 KB tile slots that fit beside the weights set the overlap: three for
 // L <= 3, two for L = 4, one for L = 5; from L = 6 the weights and one tile
 // no longer fit in the 227 KB of shared memory (where SRAM residency breaks
-// on this GPU).  Tile slots of eight warps each; within a slot, warps 4h..4h+3 handle half h
-// of every row: row t is TMEM lane t, and half h covers accumulator columns
-// [64h, 64h + 64) and Fourier frequencies [32h, 32h + 32).  A slot's warps
-// compute the features, and after each MMA read their accumulator half-row
-// from TMEM (bias included), apply ReLU while packing to BF16 and write it
-// back into the slot's operand buffer in the UMMA SWIZZLE_128B K-major
-// layout.  Each step ends with a slot-wide named barrier (bar.red.or, which
-// also carries the abort vote); the slot's first thread then issues the next
-// tcgen05.mma group itself (128x128x16 BF16 -> FP32 for the hidden layers
-// plus one K = 16 step that adds the bias, 128x16x16 for the head) and
+// on this GPU).  Tile slots of four warps (one warpgroup) each: thread t of
+// a slot owns row t of the tile, which is TMEM lane t, with all 128
+// accumulator columns and all 64 Fourier frequencies of that row.  A slot's
+// warps compute the features, and after each MMA read their accumulator row
+// from TMEM (bias included, 32 columns per load with the next load in
+// flight), apply ReLU while packing to BF16 and write it back into the
+// slot's operand buffer in the UMMA SWIZZLE_128B K-major layout.  Each step
+// ends with a slot-wide named barrier (bar.red.or, which also carries the
+// abort vote); the slot's first thread then issues the next tcgen05.mma
+// group itself (128x128x16 BF16 -> FP32 for the hidden layers plus one
+// K = 16 step that adds the bias, 128x16x16 for the head) and
 // commits it to the slot's mbarrier.  With three slots in flight the
 // epilogue of one tile overlaps the MMAs of the others.  Every wait is
 // bounded in time: a wait that gives up sets PT_ERR_TIMEOUT, raises a
@@ -55,7 +56,9 @@ constexpr int kSmemLimit = 227 * 1024;
 // Shared-memory image of a NIF with L hidden layers (offsets from a
 // 1024-byte aligned base): W1 .. WL | head | bias blocks b1 .. bL | ones |
 // FP32 tail (b1 .. bL [L x 128], b_head [4], B [128], M [12]), then the tile
-// slots that fit (at most three: TMEM holds 3 x (128 + 32) columns).
+// slots that fit (at most three: TMEM holds 3 x (128 + 32) columns).  The
+// tail holds B in pairs of frequencies (B[f][0], B[f+1][0], B[f][1],
+// B[f+1][1]) so that one 16-byte load gives both packed FP32x2 operands.
 template <int L>
 struct Layout {
     static constexpr uint32_t off_w = 0;
@@ -70,7 +73,7 @@ struct Layout {
     static constexpr int slots = room > 3 ? 3 : room;
     static constexpr uint32_t off_bar = off_a + (slots > 0 ? slots : 0) * kABytes;
     static constexpr uint32_t smem_bytes = off_bar + 128 + 1024;   // barriers + alignment slack
-    static constexpr int threads = (slots > 0 ? slots : 1) * 256;
+    static constexpr int threads = (slots > 0 ? slots : 1) * 128;
 };
 static_assert(Layout<3>::off_a == 121856 && Layout<3>::slots == 3, "the three-layer image");
 static_assert(Layout<kMaxL>::slots >= 1 && Layout<kMaxL + 1>::slots < 1, "residency limit");
@@ -114,14 +117,14 @@ struct TcParams {
 };
 
 
-// bar.red.or over the 256 threads of a slot: true on every thread if any passed true
+// bar.red.or over the 128 threads of a slot: true on every thread if any passed true
 __device__ __forceinline__ bool slot_vote_any(int id, bool pred)
 {
     uint32_t r;
     asm volatile(
         "{\n.reg .pred p, q;\n"
         "setp.ne.u32 p, %1, 0;\n"
-        "bar.red.or.pred q, %2, 256, p;\n"
+        "bar.red.or.pred q, %2, 128, p;\n"
         "selp.u32 %0, 1, 0, q;\n}"
         : "=r"(r)
         : "r"((uint32_t)pred), "r"(id)
@@ -129,7 +132,7 @@ __device__ __forceinline__ bool slot_vote_any(int id, bool pred)
     return r != 0;
 }
 
-// three slots = 24 warps: six per SM sub-partition, so up to 80 registers per thread
+// three slots = 12 warps: three per SM sub-partition, up to 168 registers per thread
 template <int L>
 __global__ void __launch_bounds__(Layout<L>::threads, 1) k_nif_tc(const TcParams p, int mode)
 {
@@ -149,8 +152,7 @@ __global__ void __launch_bounds__(Layout<L>::threads, 1) k_nif_tc(const TcParams
     const float* tail = reinterpret_cast<const float*>(smem + kOffTail);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = warp >> 3;                       // tile slot (8 warps each)
-    const int half = (warp >> 2) & 1;              // which 64 columns / 32 frequencies of the row
+    const int s = warp >> 2;                       // tile slot (4 warps each)
     const uint32_t row = (warp & 3) * 32 + lane;   // row in tile == TMEM lane
     const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
     const int64_t count = mode == 0 ? p.n : (int64_t)min(*p.esc_count, p.esc_cap);
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(Layout<L>::threads, 1) k_nif_tc(const TcParams
     __syncthreads();
     bool dead = *abort != 0;   // CTA-uniform
 
-    const bool issuer = (warp & 7) == 0 && lane == 0;
+    const bool issuer = (warp & 3) == 0 && lane == 0;
     const int bar_id = 1 + s;
     const uint32_t a_base = sbase + kOffA + s * kABytes;
     const uint32_t acc = tmem + s * 128;
@@ -218,15 +220,19 @@ __global__ void __launch_bounds__(Layout<L>::threads, 1) k_nif_tc(const TcParams
         {
             const uint64_t uu = pack_f32x2(in.u, in.u), vv = pack_f32x2(in.v, in.v);
             const uint64_t two_pi = pack_f32x2(6.28318530717958648f, 6.28318530717958648f);
-#pragma unroll 1
-            for (int c8 = half * 4; c8 < half * 4 + 4; ++c8) {
+            const uint64_t magic = pack_f32x2(12582912.f, 12582912.f);
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) {
                 uint32_t sp[4], cp[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int f = c8 * 8 + 2 * j;
-                    const float4 bq = *reinterpret_cast<const float4*>(Bm + 2 * f);
-                    const uint64_t t = fma_f32x2(pack_f32x2(bq.x, bq.z), uu, mul_f32x2(pack_f32x2(bq.y, bq.w), vv));
-                    const uint64_t r = sub_f32x2(t, pack_f32x2(rintf(lo_f32(t)), rintf(hi_f32(t))));
+                    const float4 bq = *reinterpret_cast<const float4*>(Bm + 2 * f);   // frequencies f, f + 1
+                    const uint64_t t = fma_f32x2(pack_f32x2(bq.x, bq.y), uu, mul_f32x2(pack_f32x2(bq.z, bq.w), vv));
+                    // t - rint(t) by the 1.5 * 2^23 shift: exact for |t| < 2^22; beyond, n is still an integer
+                    // and only the phase's precision (not its value modulo 1) degrades
+                    const uint64_t n = sub_f32x2(add_f32x2(t, magic), magic);
+                    const uint64_t r = sub_f32x2(t, n);
                     const uint64_t a = mul_f32x2(r, two_pi);
                     float sv[2], cv[2];
                     __sincosf(lo_f32(a), &sv[0], &cv[0]);
@@ -272,36 +278,39 @@ __global__ void __launch_bounds__(Layout<L>::threads, 1) k_nif_tc(const TcParams
             tc_fence_after();
             if (!__all_sync(0xFFFFFFFFu, got)) { fail = true; continue; }   // voted at the next barrier
             if (stage < L) {
-                const uint32_t tcol = acc + lane_base + half * 64;
-                uint32_t ra[16], rb[16];
-                auto put16 = [&](const uint32_t (&x)[16], int gq) {
-                    uint32_t pk[8];
+                const uint32_t tcol = acc + lane_base;
+                uint32_t ra[32], rb[32];
+                auto put32 = [&](const uint32_t (&x)[32], int gq) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        pk[j] = pack_relu_bf16(__uint_as_float(x[2 * j]), __uint_as_float(x[2 * j + 1]));
-                    const int c8 = half * 8 + 2 * gq;
-                    st_shared_v4(a_base + sw128_chunk(row, c8), pk[0], pk[1], pk[2], pk[3]);
-                    st_shared_v4(a_base + sw128_chunk(row, c8 + 1), pk[4], pk[5], pk[6], pk[7]);
+                    for (int h = 0; h < 2; ++h) {
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            pk[j] = pack_relu_bf16(__uint_as_float(x[16 * h + 2 * j]), __uint_as_float(x[16 * h + 2 * j + 1]));
+                        const int c8 = 4 * gq + 2 * h;
+                        st_shared_v4(a_base + sw128_chunk(row, c8), pk[0], pk[1], pk[2], pk[3]);
+                        st_shared_v4(a_base + sw128_chunk(row, c8 + 1), pk[4], pk[5], pk[6], pk[7]);
+                    }
                 };
-                tmem_ld16(tcol, ra);
+                TMEM_LD32(tcol, ra);
                 tmem_wait_ld();
-                tmem_ld16(tcol + 16, rb);
-                put16(ra, 0);
+                TMEM_LD32(tcol + 32, rb);
+                put32(ra, 0);
                 tmem_wait_ld();
-                tmem_ld16(tcol + 32, ra);
-                put16(rb, 1);
+                TMEM_LD32(tcol + 64, ra);
+                put32(rb, 1);
                 tmem_wait_ld();
-                tmem_ld16(tcol + 48, rb);
-                put16(ra, 2);
+                TMEM_LD32(tcol + 96, rb);
+                put32(ra, 2);
                 tmem_wait_ld();
-                put16(rb, 3);
+                put32(rb, 3);
                 fence_proxy_async();
             }
         }
         if (dead) break;
         tc_fence_before();
         if (slot_vote_any(bar_id, fail)) { dead = true; break; }
-        if (half == 0) {   // the first half of the slot owns the output
+        {
             tc_fence_after();
             uint32_t yr[4];
             tmem_ld4(head + lane_base, yr);
@@ -400,7 +409,7 @@ void pack_image(const float* params, int F, int H, std::vector<unsigned char>& o
             p += 3;
         }
     }
-    for (int i = 0; i < 2 * F; ++i) tail[L * kH + 4 + i] = Bsrc[i];
+    for (int i = 0; i < 2 * F; ++i) tail[L * kH + 4 + i] = Bsrc[(i & ~3) | ((i & 1) << 1) | ((i >> 1) & 1)];
     for (int i = 0; i < 9; ++i) tail[L * kH + 4 + 2 * F + i] = p[i];
 }
 
@@ -523,7 +532,10 @@ __global__ void k_repack_tc(const float* __restrict__ params, unsigned char* __r
             float val = 0.f;
             if (t < L * kH) val = b[t / kH][t % kH];
             else if (t < L * kH + 4) val = (t - L * kH) < 3 ? b[L][t - L * kH] : 0.f;
-            else if (t < L * kH + 4 + 2 * kF) val = params[t - L * kH - 4];
+            else if (t < L * kH + 4 + 2 * kF) {
+                const int i = t - L * kH - 4;
+                val = params[(i & ~3) | ((i & 1) << 1) | ((i >> 1) & 1)];
+            }
             else if (t < L * kH + 4 + 2 * kF + 9) val = Mp[t - L * kH - 4 - 2 * kF];
             reinterpret_cast<float*>(image + LY::off_tail)[t] = val;
         }
