@@ -58,6 +58,29 @@ OPS_NODE, OPS_SPHERE, OPS_QUAD, OPS_TRI = 58, 36, 12, 46
 # the traversal kernel (origin and direction in, hit out) and per ray-bounce of trace + shade queue traffic
 BYTES_NODE, BYTES_SPHERE, BYTES_QUAD, BYTES_TRI, BYTES_RAY_TRACE, BYTES_RAY = 48, 16, 32, 48, 40, 140
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes (read + write) of the traversal kernel per traced ray, from one ncu capture of a smaller frame of
+# the same workload (summaries and commands in profiles/), scaled to a frame by the rays it traces.  Valid only
+# while the traversal source is the one captured (sha256 of trace.cu + device_common.cuh, first 16 hex digits).
+TRACE_TRAFFIC = {}
+TRACE_SOURCES = ("paper_2305_20061_gb300/csrc/trace.cu", "paper_2305_20061_gb300/csrc/device_common.cuh")
+
+
+def trace_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRACE_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def trace_traffic(workload: str, rays: int):
+    """DRAM bytes of the traversal kernel over a frame of `rays` traced rays, or None when no capture of
+    this workload exists or the traversal source changed since it was taken."""
+    rec = TRACE_TRAFFIC.get(workload)
+    if rec is None or rec["src"] != trace_source_hash():
+        return None
+    return rec["bytes_per_ray"] * rays
 
 
 def peaks():
@@ -353,7 +376,7 @@ def bench_ours(args):
     precision = args.precision if uses_nif else None
     ctx = pt.Context(local)
     t_build = time.perf_counter()
-    scene = pt.Scene(ctx, sc)
+    scene = pt.Scene(ctx, sc, node_format=args.nodes)
     t_build = time.perf_counter() - t_build
     gnif = pt.Nif(ctx, nif) if uses_nif else None
 
@@ -482,6 +505,11 @@ def bench_ours(args):
         roof = traversal_roofline(work, trace_ms, trace_kernel, trace_launches, pt.ffma_rate_tflops(local), clock,
                                   "")
 
+    if roof["kernel"] in ("k_trace", "k_paths"):
+        roof["traffic"] = trace_traffic(args.workload, rays) if trace_kernel == "k_trace" else None
+        roof["traffic_note"] = ("DRAM bytes per frame of k_trace (all its launches), from the ncu capture in "
+                                "profiles/ scaled by traced rays; null when no capture of this workload matches "
+                                "the current traversal source")
     # end to end through the C ABI with host buffers: scene + weights in, image out
     e2e = None
     if not args.no_e2e:
@@ -494,7 +522,7 @@ def bench_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            s2 = pt.Scene(ctx, sc)
+            s2 = pt.Scene(ctx, sc, node_format=args.nodes)
             n2 = pt.Nif(ctx, nif) if uses_nif else None
             pt.render(ctx, s2, n2, cfg, rprec, out=img, first_sample=first_sample)
             host_img.copy_(img, non_blocking=True)
@@ -528,6 +556,7 @@ def bench_ours(args):
             "rays_per_step": rays, "traversal_work_per_step": work,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "scene_build_s": t_build, "bvh_nodes": scene.info()["n_nodes"], "bvh_depth": scene.info()["bvh_depth"],
+            "bvh_node_form": {1: "packed 48 B", 2: "decoded 64 B", 3: "quantised 32 B"}[scene.info()["node_format"]],
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": int(kernels),
         }
@@ -630,7 +659,7 @@ def bench_c5(args):
     prec = args.precision
     ctx = pt.Context(local)
     t_build = time.perf_counter()
-    scene = pt.Scene(ctx, sc)
+    scene = pt.Scene(ctx, sc, node_format=args.nodes)
     t_build = time.perf_counter() - t_build
     gnif = pt.Nif(ctx, nif)
     train = train_env_nif(pt, ctx, gnif, nif, args.train_steps, dev, args.train_precision) if args.train_steps > 0 else None
@@ -806,7 +835,7 @@ def bench_c5(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(n_e2e):
-            s2, n2, c2 = pt.Scene(ctx, sc), pt.Nif(ctx, nif), pt.Cache(ctx, cache_host)
+            s2, n2, c2 = pt.Scene(ctx, sc, node_format=args.nodes), pt.Nif(ctx, nif), pt.Cache(ctx, cache_host)
             c2.train_frame(s2, n2, W, H, n_done + i, n_train=N_TRAIN, max_depth=cfg.max_depth,
                            rec_vertex=CACHE_VERTEX, seed=0, precision=prec, train_precision=args.train_precision)
             pt.render_cached(ctx, s2, n2, cfg, None, cache=c2, cache_vertex=CACHE_VERTEX, precision=prec,
@@ -877,7 +906,7 @@ def bench_nif_sweep(args):
     sky = torch.from_numpy(I.procedural_sky()).to(dev)
     uv = torch.from_numpy(I.uniform_uv(1 << 24, seed=1)).to(dev)
     sc, cfg, _ = workload("C2")
-    scene = pt.Scene(ctx, sc)
+    scene = pt.Scene(ctx, sc, node_format=args.nodes)
     img = torch.empty((cfg.height, cfg.width, 3), dtype=torch.float32, device=dev)
     steps = max(args.train_steps, 1)
 
@@ -979,6 +1008,8 @@ def main():
                     help="Adam steps of the environment NIF on the procedural sky before the frames (0: random init)")
     ap.add_argument("--train-precision", choices=["bf16", "fp32"], default="bf16",
                     help="GEMMs of NIF and radiance-cache training (tensor cores or CUDA cores)")
+    ap.add_argument("--nodes", choices=["auto", "packed", "decoded", "quant8"], default="auto",
+                    help="BVH node form the traversal reads (pt_scene_desc.node_format)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the other-precision frames and standalone NIF runs (profiler captures)")

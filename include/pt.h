@@ -126,7 +126,20 @@ typedef struct pt_scene_desc {
     float camera[10];          /* eye[3], target[3], up[3], vertical fov in degrees */
     int32_t env_is_nif;        /* 1: environment = NIF passed at render; 0: constant env_rgb */
     float env_rgb[3];
+    int32_t node_format;       /* pt_node_format: the BVH node form traversal reads (0 = automatic) */
 } pt_scene_desc;
+
+/* BVH node forms (all hold the same tree; every form's child boxes contain
+   the exact fp32 boxes, so every form finds the same closest hits):
+   PACKED  48 bytes per node: both children as fp32 origin + fp16 extent
+           rounded up (Section 3.1.4);
+   DECODED 64 bytes per node: the packed boxes decoded to fp32 bounds;
+   QUANT8  32 bytes per node: both children on an 8-bit grid of the node
+           (origin + 8-bit codes, lo rounded down, hi up; the paper's
+           quarter-precision outlook, Section 5); needs fewer than 2^24
+           nodes and primitives (PT_EUNSUPPORTED otherwise).
+   AUTO    DECODED for trees up to 48 MiB in that form, else PACKED. */
+typedef enum { PT_NODES_AUTO = 0, PT_NODES_PACKED = 1, PT_NODES_DECODED = 2, PT_NODES_QUANT8 = 3 } pt_node_format;
 
 typedef struct pt_scene_info {
     int64_t n_prims;
@@ -135,6 +148,9 @@ typedef struct pt_scene_info {
     int64_t prim_bytes;        /* device bytes of primitive data */
     int32_t bvh_depth;         /* longest root-to-leaf path */
     int32_t has_emission;
+    int32_t node_format;       /* pt_node_format the traversal reads (never AUTO) */
+    int32_t reserved;
+    int64_t traversed_node_bytes;  /* device bytes of the node form the traversal reads */
 } pt_scene_info;
 
 /* Build the BVH on the host (binned SAH, one primitive per leaf, child boxes
@@ -160,6 +176,22 @@ PT_API pt_status pt_scene_get_info(const pt_scene* scene, pt_scene_info* info);
    PT_EUNSUPPORTED when an extent exceeds the fp16 range. */
 PT_API pt_status pt_build_bvh_host(int64_t n, const float* lo, const float* hi, uint32_t* nodes, int64_t cap,
                                    int64_t* n_nodes, uint32_t* root, int32_t* depth);
+
+/* The quantised node form (PT_NODES_QUANT8) of a packed tree, on the host
+   (no context, no device): nodes [n_nodes][12] as pt_build_bvh_host writes
+   them, out [n_nodes][8] uint32 in the same order with the same child
+   references: w[0..2] the node's grid origin (fp32 bits, per-axis minimum of
+   the two children's decoded boxes); w[3] bits 0-7 the biased exponent e,
+   bits 8-9 / 10-11 / 12-13 the axis offsets d_x, d_y, d_z, bit 14 / 15 the
+   left / right child is a primitive, bits 16-31 the left reference's low 16
+   bits; w[4] bits 0-7 the left reference's high 8 bits, bits 8-31 the right
+   reference; w[5..7] twelve 8-bit codes (lo_l xyz, hi_l xyz, lo_r xyz, hi_r
+   xyz, low byte first).  A bound on axis a decodes in fp32 as origin_a +
+   q * 2^(e - 127 - d_a) (exact product, one rounding to nearest) and
+   contains the decoded fp16-extent box: lo codes rounded down, hi codes up.
+   PT_EINVAL for a NULL buffer; PT_EUNSUPPORTED when a reference or
+   primitive ID needs more than 24 bits. */
+PT_API pt_status pt_quantize_bvh_host(int64_t n_nodes, const uint32_t* nodes, uint32_t* out);
 
 /* Copy the packed BVH back to the host for inspection: nodes as 12 uint32
    per node (see the packing in the library source), root reference in

@@ -20,7 +20,7 @@ using namespace ptk;
 struct pt_ctx {
     int device = 0;
     int sm_count = 0;
-    int paths_threads[2] = {0, 0};   // resident threads of the path kernel (packed, decoded nodes)
+    int paths_threads[3] = {0, 0, 0};   // resident threads of the path kernel (packed, decoded, quantised nodes)
     std::string last_error;
     uint32_t* d_err = nullptr;
     // wavefront scratch
@@ -350,8 +350,7 @@ PT_API pt_status pt_create(pt_ctx** out, int device)
     if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, kStats * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_first_sample, sizeof(uint32_t));
     if (e == cudaSuccess) {
-        ctx->paths_threads[0] = paths_resident_threads(false, ctx->sm_count);
-        ctx->paths_threads[1] = paths_resident_threads(true, ctx->sm_count);
+        for (int f = 0; f < 3; ++f) ctx->paths_threads[f] = paths_resident_threads(f, ctx->sm_count);
     }
     // the no-allocation render path's fixed scratch: resolved here so that the driver reserves it now,
     // not inside a later pt_render_noalloc call
@@ -510,10 +509,20 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
         if (m[5] != 0.f || m[6] != 0.f || m[7] != 0.f) has_em = 1;
     }
 
-    // BVHs that fit comfortably in L2 also get the decoded 64-byte form
+    // The node form the traversal reads: automatic = the decoded 64-byte form for BVHs that fit
+    // comfortably in L2, else the packed 48-byte form; or the form the descriptor asks for.
     constexpr size_t kWideLimit = 48u << 20;
+    const int32_t form_req = d->node_format;
+    if (form_req < PT_NODES_AUTO || form_req > PT_NODES_QUANT8) return fail(ctx, PT_EINVAL, "unknown node_format");
+    const bool want_wide = form_req == PT_NODES_DECODED ||
+                           (form_req == PT_NODES_AUTO && bo.nodes.size() * 64 <= kWideLimit);
+    std::vector<QuantNode> qn;
+    if (form_req == PT_NODES_QUANT8 && !bo.nodes.empty()) {
+        std::string qerr;
+        if (!quantize_bvh(bo.nodes, qn, &qerr)) return fail(ctx, PT_EUNSUPPORTED, qerr);
+    }
     std::vector<float> wide;
-    if (!bo.nodes.empty() && bo.nodes.size() * 64 <= kWideLimit) {
+    if (!bo.nodes.empty() && want_wide) {
         wide.assign(bo.nodes.size() * 16, 0.f);
         for (size_t i = 0; i < bo.nodes.size(); ++i) {
             const uint32_t* w = bo.nodes[i].w;
@@ -536,14 +545,15 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
 
     // one device arena per scene (one allocation; small scenes also one copy)
     struct Segment { const void* src; size_t bytes; size_t off; };
-    Segment seg[8] = {{bo.nodes.data(), bo.nodes.size() * sizeof(PackedNode), 0},
+    Segment seg[9] = {{bo.nodes.data(), bo.nodes.size() * sizeof(PackedNode), 0},
                       {sph.data(), sph.size() * sizeof(float4), 0},
                       {quad.data(), quad.size() * sizeof(float4), 0},
                       {tri.data(), tri.size() * sizeof(float4), 0},
                       {pmat.data(), pmat.size() * sizeof(int32_t), 0},
                       {mat.data(), mat.size() * sizeof(float4), 0},
                       {d->mat_type, (size_t)d->n_mats * sizeof(int32_t), 0},
-                      {wide.data(), wide.size() * sizeof(float), 0}};
+                      {wide.data(), wide.size() * sizeof(float), 0},
+                      {qn.data(), qn.size() * sizeof(QuantNode), 0}};
     size_t total = 0;
     for (Segment& g : seg) {
         g.off = total;
@@ -581,6 +591,7 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
     void* dm = arena + seg[5].off;
     void* dmt = arena + seg[6].off;
     if (!wide.empty()) sc->dev.wnodes = (const uint4*)(arena + seg[7].off);
+    if (!qn.empty()) sc->dev.qnodes = (const uint4*)(arena + seg[8].off);
     DevScene& v = sc->dev;
     v.nodes = (const uint4*)dn;
     v.root = bo.root;
@@ -595,6 +606,8 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
     sc->info.n_prims = nP;
     sc->info.n_nodes = (int64_t)bo.nodes.size();
     sc->info.node_bytes = (int64_t)(bo.nodes.size() * sizeof(PackedNode));
+    sc->info.node_format = !qn.empty() ? PT_NODES_QUANT8 : (!wide.empty() ? PT_NODES_DECODED : PT_NODES_PACKED);
+    sc->info.traversed_node_bytes = (int64_t)bo.nodes.size() * (!qn.empty() ? 32 : (!wide.empty() ? 64 : 48));
     sc->info.prim_bytes = (int64_t)((sph.size() + quad.size() + tri.size()) * sizeof(float4) + pmat.size() * 4);
     sc->info.bvh_depth = bo.depth;
     sc->info.has_emission = has_em;
@@ -638,6 +651,18 @@ PT_API pt_status pt_build_bvh_host(int64_t n, const float* lo, const float* hi, 
     *n_nodes = (int64_t)bo.nodes.size();
     *root = bo.root;
     *depth = bo.depth;
+    return PT_OK;
+}
+
+PT_API pt_status pt_quantize_bvh_host(int64_t n_nodes, const uint32_t* nodes, uint32_t* out)
+{
+    if (n_nodes < 0 || (n_nodes > 0 && (!nodes || !out))) return PT_EINVAL;
+    std::vector<PackedNode> in((size_t)n_nodes);
+    if (n_nodes) std::memcpy(in.data(), nodes, (size_t)n_nodes * sizeof(PackedNode));
+    std::vector<QuantNode> q;
+    std::string err;
+    if (!quantize_bvh(in, q, &err)) return PT_EUNSUPPORTED;
+    if (n_nodes) std::memcpy(out, q.data(), (size_t)n_nodes * sizeof(QuantNode));
     return PT_OK;
 }
 
@@ -1252,7 +1277,7 @@ PT_API pt_status pt_train_cache(pt_ctx* ctx, const pt_scene* sc, const pt_nif* n
 // or (automatic) when the chunk fits in one resident wave of it.
 static bool use_paths(const pt_ctx* ctx, const pt_scene* sc, const pt_render_cfg* cfg, int64_t n)
 {
-    const int resident = ctx->paths_threads[sc->dev.wnodes ? 1 : 0];
+    const int resident = ctx->paths_threads[sc->dev.qnodes ? 2 : (sc->dev.wnodes ? 1 : 0)];
     return cfg->schedule == PT_SCHED_PATHS || (cfg->schedule == PT_SCHED_AUTO && resident > 0 && n <= resident);
 }
 
@@ -1307,7 +1332,7 @@ static pt_status render_launches(pt_ctx* ctx, const pt_scene* sc, const pt_nif* 
         const bool per_path = use_paths(ctx, sc, cfg, n);
         if (per_path) {
             bp.k = 1;
-            const int resident = ctx->paths_threads[sc->dev.wnodes ? 1 : 0];
+            const int resident = ctx->paths_threads[sc->dev.qnodes ? 2 : (sc->dev.wnodes ? 1 : 0)];
             PT_CUDA(timed(ctx, PT_KIND_TRACE, s, [&] { return launch_paths(bp, resident, s); }));
         }
         for (int k = 1; k <= k_end && !per_path; ++k) {

@@ -257,6 +257,111 @@ bool round_up_half_extent(float lo, float hi, uint16_t* out_bits)
     return false;
 }
 
+void decode_packed_boxes(const PackedNode& n, float box[12])
+{
+    const uint16_t ext[6] = {(uint16_t)(n.w[6] & 0xFFFFu), (uint16_t)(n.w[6] >> 16), (uint16_t)(n.w[7] & 0xFFFFu),
+                             (uint16_t)(n.w[7] >> 16), (uint16_t)(n.w[8] & 0xFFFFu), (uint16_t)(n.w[8] >> 16)};
+    for (int c = 0; c < 2; ++c)
+        for (int a = 0; a < 3; ++a) {
+            float lo;
+            std::memcpy(&lo, &n.w[3 * c + a], 4);
+            __half h;
+            std::memcpy(&h, &ext[3 * c + a], 2);
+            volatile float top = lo + __half2float(h);   // fp32 addition as the device performs it
+            box[6 * c + a] = lo;
+            box[6 * c + 3 + a] = top;
+        }
+}
+
+namespace {
+
+// fp32 value of origin + q * 2^(E - 127), as the device computes it (exact product, one rounding)
+float grid_value(float origin, int q, int E)
+{
+    volatile float step = std::ldexp(1.0f, E - 127);
+    volatile float prod = (float)q * step;
+    volatile float sum = origin + prod;
+    return sum;
+}
+
+// 8-bit codes of [lo, hi] on the grid origin + q * 2^(E - 127): lo rounded down, hi rounded up, each
+// checked in the device's fp32 arithmetic; false if hi needs a code above 255
+bool quantize_interval(float origin, float lo, float hi, int E, int* qlo, int* qhi)
+{
+    const double step = std::ldexp(1.0, E - 127);
+    int a = (int)std::floor(((double)lo - (double)origin) / step);
+    int b = (int)std::ceil(((double)hi - (double)origin) / step);
+    a = std::min(std::max(a, 0), 255);
+    while (a > 0 && grid_value(origin, a, E) > lo) --a;
+    while (a < 255 && grid_value(origin, a + 1, E) <= lo) ++a;   // the tightest code that still contains lo
+    b = std::max(b, a);
+    while (b <= 255 && grid_value(origin, b, E) < hi) ++b;
+    if (b > 255) return false;
+    while (b > a && grid_value(origin, b - 1, E) >= hi) --b;
+    if (grid_value(origin, a, E) > lo) return false;
+    *qlo = a;
+    *qhi = b;
+    return true;
+}
+
+}  // namespace
+
+bool quantize_bvh(const std::vector<PackedNode>& in, std::vector<QuantNode>& out, std::string* error)
+{
+    out.assign(in.size(), QuantNode{});
+    for (size_t i = 0; i < in.size(); ++i) {
+        const PackedNode& n = in[i];
+        float box[12];
+        decode_packed_boxes(n, box);
+        const uint32_t refs[2] = {n.w[9], n.w[10]};
+        for (uint32_t r : refs)
+            if ((r & ~kLeafBit) >= kQuantRefLimit) {
+                if (error) *error = "BVH too large for 24-bit references of quantised nodes";
+                return false;
+            }
+        float origin[3];
+        int e_axis[3];
+        for (int a = 0; a < 3; ++a) {
+            origin[a] = std::min(box[a], box[6 + a]);
+            const double span = std::max((double)box[3 + a], (double)box[9 + a]) - (double)origin[a];
+            // smallest grid step 2^k with 255 steps covering the span (with a little slack for the rounding)
+            int k = span > 0.0 ? (int)std::ceil(std::log2(span * (1.0 + 1e-6) / 255.0)) : -126;
+            e_axis[a] = std::min(std::max(k + 127, 4), 254);
+        }
+        int e = std::max(e_axis[0], std::max(e_axis[1], e_axis[2]));
+        int q[12];
+        for (int guard = 0;; ++guard) {
+            int d[3];
+            bool ok = e <= 254;
+            for (int a = 0; a < 3 && ok; ++a) {
+                d[a] = std::min(3, e - e_axis[a]);
+                for (int c = 0; c < 2 && ok; ++c)
+                    ok = quantize_interval(origin[a], box[6 * c + a], box[6 * c + 3 + a], e - d[a], &q[6 * c + a],
+                                           &q[6 * c + 3 + a]);
+            }
+            if (ok) {
+                QuantNode& o = out[i];
+                for (int a = 0; a < 3; ++a) std::memcpy(&o.w[a], &origin[a], 4);
+                const uint32_t cl = refs[0] & ~kLeafBit, cr = refs[1] & ~kLeafBit;
+                o.w[3] = (uint32_t)e | ((uint32_t)d[0] << 8) | ((uint32_t)d[1] << 10) | ((uint32_t)d[2] << 12) |
+                         ((refs[0] & kLeafBit) ? 1u << 14 : 0u) | ((refs[1] & kLeafBit) ? 1u << 15 : 0u) |
+                         ((cl & 0xFFFFu) << 16);
+                o.w[4] = (cl >> 16) | (cr << 8);
+                for (int j = 0; j < 3; ++j)
+                    o.w[5 + j] = (uint32_t)q[4 * j] | ((uint32_t)q[4 * j + 1] << 8) | ((uint32_t)q[4 * j + 2] << 16) |
+                                 ((uint32_t)q[4 * j + 3] << 24);
+                break;
+            }
+            if (guard > 8 || e >= 254) {
+                if (error) *error = "BVH box does not fit an 8-bit grid";
+                return false;
+            }
+            ++e;   // a coarser grid
+        }
+    }
+    return true;
+}
+
 bool build_bvh(const BuildInput& in, BuildOutput& out)
 {
     out.nodes.clear();

@@ -258,7 +258,13 @@ __device__ __forceinline__ bool trav_init(const DevScene& sc, float3 o, float3 d
     return false;
 }
 
-template <bool kWide>
+// node forms the traversal reads (DevScene: nodes, wnodes, qnodes)
+constexpr int kNodesPacked = 0, kNodesWide = 1, kNodesQuant = 2;
+
+// byte k (0..3) of w as a float
+__device__ __forceinline__ float byte_f(uint32_t w, int k) { return (float)((w >> (8 * k)) & 0xFFu); }
+
+template <int kForm>
 __device__ __forceinline__ bool trav_step(const DevScene& sc, Trav& s, uint32_t* stack_ref, float* stack_t,
                                           uint32_t* err, Work& w)
 {
@@ -266,7 +272,28 @@ __device__ __forceinline__ bool trav_step(const DevScene& sc, Trav& s, uint32_t*
     if (s.cur >= sc.n_nodes) { atomicOr(err, PT_ERR_BAD_NODE); return true; }  // never fetch outside the node array
     uint32_t cl, cr;
     float tl, trr;
-    if (kWide) {
+    if (kForm == kNodesQuant) {
+        // 8-bit grid boxes: bound = origin + q * 2^(e - 127 - d_axis), exact product, one rounding
+        const uint4* np = sc.qnodes + 2 * (size_t)s.cur;
+        const uint4 q0 = __ldg(np), q1 = __ldg(np + 1);
+        const float3 org = f3(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z));
+        const uint32_t meta = q0.w, e = meta & 0xFFu;
+        const float3 step = f3(__uint_as_float((e - ((meta >> 8) & 3u)) << 23),
+                               __uint_as_float((e - ((meta >> 10) & 3u)) << 23),
+                               __uint_as_float((e - ((meta >> 12) & 3u)) << 23));
+        cl = ((meta >> 16) | ((q1.x & 0xFFu) << 16)) | ((meta & (1u << 14)) ? kLeafBit : 0u);
+        cr = (q1.x >> 8) | ((meta & (1u << 15)) ? kLeafBit : 0u);
+        const float3 lo_l = f3(fmaf(byte_f(q1.y, 0), step.x, org.x), fmaf(byte_f(q1.y, 1), step.y, org.y),
+                               fmaf(byte_f(q1.y, 2), step.z, org.z));
+        const float3 hi_l = f3(fmaf(byte_f(q1.y, 3), step.x, org.x), fmaf(byte_f(q1.z, 0), step.y, org.y),
+                               fmaf(byte_f(q1.z, 1), step.z, org.z));
+        const float3 lo_r = f3(fmaf(byte_f(q1.z, 2), step.x, org.x), fmaf(byte_f(q1.z, 3), step.y, org.y),
+                               fmaf(byte_f(q1.w, 0), step.z, org.z));
+        const float3 hi_r = f3(fmaf(byte_f(q1.w, 1), step.x, org.x), fmaf(byte_f(q1.w, 2), step.y, org.y),
+                               fmaf(byte_f(q1.w, 3), step.z, org.z));
+        tl = slab_box(lo_l, hi_l, s.o, s.inv, s.h.t);
+        trr = slab_box(lo_r, hi_r, s.o, s.inv, s.h.t);
+    } else if (kForm == kNodesWide) {
         // decoded boxes: the same bounds the packed form decodes to, without the fp16 conversions
         const uint4* np = sc.wnodes + 4 * (size_t)s.cur;
         const uint4 q0 = __ldg(np), q1 = __ldg(np + 1), q2 = __ldg(np + 2), q3 = __ldg(np + 3);
@@ -328,7 +355,7 @@ __device__ __forceinline__ Hit trace_closest(const DevScene& sc, float3 o, float
     if (trav_init(sc, o, d, s, w)) return s.h;
     uint32_t stack_ref[kStackSize];
     float stack_t[kStackSize];
-    while (!trav_step<false>(sc, s, stack_ref, stack_t, err, w)) {
+    while (!trav_step<kNodesPacked>(sc, s, stack_ref, stack_t, err, w)) {
     }
     return s.h;
 }

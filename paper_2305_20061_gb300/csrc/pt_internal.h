@@ -40,6 +40,25 @@ constexpr uint32_t kIterCap = 1u << 22;      // node visits per ray before givin
 struct PackedNode { uint32_t w[12]; };
 static_assert(sizeof(PackedNode) == 48, "node packing");
 
+// Quantised BVH node (the paper's "quarter precision" outlook, Section 5):
+// the same tree as PackedNode, both children's boxes on an 8-bit grid of the
+// node, 32 bytes = two 128-bit loads = one DRAM sector:
+//   q0 = origin.x origin.y origin.z meta
+//   q1 = refs qbytes[0..3] qbytes[4..7] qbytes[8..11]
+// origin: per-axis minimum of the two children's decoded boxes (fp32).
+// meta: bits 0-7 e (biased fp32 exponent), 8-9 / 10-11 / 12-13 the axis
+// offsets dx, dy, dz (0..3), bit 14 left child is a primitive, bit 15 right
+// child is a primitive, bits 16-31 the low 16 bits of the left reference.
+// refs: bits 0-7 the high 8 bits of the left reference, bits 8-31 the right
+// reference (24-bit node index or primitive ID).
+// qbytes: lo_l.xyz hi_l.xyz lo_r.xyz hi_r.xyz; axis a's grid step is
+// s_a = 2^(e - 127 - d_a) and a bound decodes as origin_a + q * s_a in fp32
+// (the product is exact, the sum rounds to nearest), which the builder
+// checks to contain the fp16-extent box (lo rounded down, hi up).
+struct QuantNode { uint32_t w[8]; };
+static_assert(sizeof(QuantNode) == 32, "quantised node packing");
+constexpr uint32_t kQuantRefLimit = 1u << 24;   // node indices and primitive IDs a quantised node can hold
+
 // Device view of a scene (passed by value in kernel parameters).
 struct DevScene {
     const uint4* nodes;     // 3 x uint4 per node
@@ -47,6 +66,8 @@ struct DevScene {
     //   lo_l.xyz hi_l.x | hi_l.yz lo_r.xy | lo_r.z hi_r.xyz | child_l child_r 0 0
     // kept for BVHs small enough to stay cache-resident, where decoding costs more than the bytes
     const uint4* wnodes;
+    // nullable: the same tree as QuantNode, 2 x uint4 per node; when set, traversal reads this form
+    const uint4* qnodes;
     uint32_t root;          // node index, leaf reference, or kEmptyRef
     uint32_t n_nodes;
     uint32_t nS, nQ, nT;    // primitive counts; IDs: [0,nS) spheres, [nS,nS+nQ) quads, rest triangles
@@ -158,7 +179,7 @@ cudaError_t launch_shade(const BounceParams& p, int sm_count, cudaStream_t s);  
 // resident_threads (from paths_resident_threads) caps the grid at one wave
 cudaError_t launch_paths(const BounceParams& p, int resident_threads, cudaStream_t s);
 // threads of k_paths resident at once on the device (0 if the query failed)
-int paths_resident_threads(bool wide, int sm_count);
+int paths_resident_threads(int form, int sm_count);   // form: node form of the traversal (device_common.cuh)
 // Looks up (once per device; `device` current) the fixed scratch array of
 // pt_render_noalloc, which makes the driver load and reserve it.
 cudaError_t noalloc_setup(int device, unsigned char** out);
@@ -278,5 +299,11 @@ struct BuildOutput {
 };
 bool build_bvh(const BuildInput& in, BuildOutput& out);
 bool round_up_half_extent(float lo, float hi, uint16_t* out_bits);
+// The packed tree's children boxes as decoded on the device (fp32 origin + fp16 extent, fp32 sum):
+// box[0..2] lo_l, [3..5] hi_l, [6..8] lo_r, [9..11] hi_r.
+void decode_packed_boxes(const PackedNode& n, float box[12]);
+// Quantised form of a packed tree (same node order and references); false with *error set when a
+// reference or primitive ID does not fit 24 bits.
+bool quantize_bvh(const std::vector<PackedNode>& in, std::vector<QuantNode>& out, std::string* error);
 
 }  // namespace ptk

@@ -189,7 +189,7 @@ constexpr int kStepsPerCheck = PT_TRACE_STEPS;
 #ifndef PT_TRACE_MIN_BLOCKS
 #define PT_TRACE_MIN_BLOCKS 4
 #endif
-template <bool kWide>
+template <int kForm>
 __global__ void __launch_bounds__(256, PT_TRACE_MIN_BLOCKS) k_trace(const BounceParams p)
 {
     const uint32_t count = (p.k == 1) ? p.n_chunk : min(*p.count_in, p.cap);
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(256, PT_TRACE_MIN_BLOCKS) k_trace(const Bounce
     uint32_t rnext = 0, rend = 0;   // the warp's claimed index range (warp-uniform)
     while (true) {
         const unsigned idle = __ballot_sync(0xFFFFFFFFu, !live);
-        constexpr int kRefillMin = kWide ? kRefillMinWide : kRefillMinPacked;
+        constexpr int kRefillMin = kForm == kNodesWide ? kRefillMinWide : kRefillMinPacked;
         if (idle && !exhausted && (__popc(idle) >= kRefillMin || idle == 0xFFFFFFFFu)) {
             const uint32_t n = __popc(idle), rank = __popc(idle & lanes_below);
             const uint32_t avail = rend - rnext;
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(256, PT_TRACE_MIN_BLOCKS) k_trace(const Bounce
         }
 #pragma unroll 1
         for (int st = 0; st < kStepsPerCheck; ++st) {
-            if (live && trav_step<kWide>(p.sc, t, stack_ref, stack_t, p.err, work)) {
+            if (live && trav_step<kForm>(p.sc, t, stack_ref, stack_t, p.err, work)) {
                 p.hits[ri] = make_int2(__float_as_int(t.h.t), t.h.prim);
                 live = false;
             }
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(256, 4) k_bounce(const BounceParams p)
 // Small blocks spread a small chunk over every SM (a latency-bound launch
 // runs fastest with the fewest warps per SM).
 constexpr int kPathsBlock = 64;
-template <bool kWide>
+template <int kForm>
 __global__ void __launch_bounds__(kPathsBlock, 12) k_paths(const BounceParams p)
 {
     const uint32_t lane = threadIdx.x & 31;
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(kPathsBlock, 12) k_paths(const BounceParams p)
             }
             Trav t;
             if (!trav_init(p.sc, s.o, s.d, t, work)) {
-                while (!trav_step<kWide>(p.sc, t, stack_ref, stack_t, p.err, work)) {
+                while (!trav_step<kForm>(p.sc, t, stack_ref, stack_t, p.err, work)) {
                 }
             }
             const VertexOut v = shade_vertex(p, k, s, pix, smp, t.h);
@@ -587,8 +587,9 @@ int grid_for(int64_t n, int block, int sm_count, int per_sm)
 cudaError_t launch_trace(const BounceParams& p, int sm_count, cudaStream_t s)
 {
     // traversal: persistent, 4 resident blocks of 256 threads per SM
-    if (p.sc.wnodes) k_trace<true><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
-    else k_trace<false><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
+    if (p.sc.qnodes) k_trace<kNodesQuant><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
+    else if (p.sc.wnodes) k_trace<kNodesWide><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
+    else k_trace<kNodesPacked><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
     count_launch();
     return cudaGetLastError();
 }
@@ -606,11 +607,13 @@ cudaError_t launch_bounce(const BounceParams& p, int sm_count, cudaStream_t s)
     return e != cudaSuccess ? e : launch_shade(p, sm_count, s);
 }
 
-int paths_resident_threads(bool wide, int sm_count)
+int paths_resident_threads(int form, int sm_count)
 {
     int per_sm = 0;
-    const cudaError_t e = wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<true>, kPathsBlock, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<false>, kPathsBlock, 0);
+    const cudaError_t e =
+        form == kNodesQuant  ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<kNodesQuant>, kPathsBlock, 0)
+        : form == kNodesWide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<kNodesWide>, kPathsBlock, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paths<kNodesPacked>, kPathsBlock, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -625,8 +628,9 @@ cudaError_t launch_paths(const BounceParams& p, int resident_threads, cudaStream
     int64_t blocks = ((int64_t)p.n_chunk + kPathsBlock - 1) / kPathsBlock;
     if (cap > 0 && blocks > cap / kPathsBlock) blocks = cap / kPathsBlock;
     if (blocks < 1) blocks = 1;
-    if (p.sc.wnodes) k_paths<true><<<(int)blocks, kPathsBlock, 0, s>>>(p);
-    else k_paths<false><<<(int)blocks, kPathsBlock, 0, s>>>(p);
+    if (p.sc.qnodes) k_paths<kNodesQuant><<<(int)blocks, kPathsBlock, 0, s>>>(p);
+    else if (p.sc.wnodes) k_paths<kNodesWide><<<(int)blocks, kPathsBlock, 0, s>>>(p);
+    else k_paths<kNodesPacked><<<(int)blocks, kPathsBlock, 0, s>>>(p);
     count_launch();
     return cudaGetLastError();
 }

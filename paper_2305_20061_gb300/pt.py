@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libpt.so")
 PT_OK, PT_EINVAL, PT_ENOMEM, PT_ECUDA, PT_EDEVICE, PT_EUNSUPPORTED, PT_EIO = range(7)
 PT_FP32, PT_BF16, PT_FP8E4M3 = 0, 1, 2
 PRECISIONS = {"fp32": PT_FP32, "bf16": PT_BF16, "fp8": PT_FP8E4M3}
+NODE_FORMATS = {"auto": 0, "packed": 1, "decoded": 2, "quant8": 3}
 ERR_BITS = {0x1: "stack_overflow", 0x2: "queue_overflow", 0x4: "nonfinite", 0x8: "timeout", 0x10: "iter_cap",
             0x20: "bad_node", 0x80000000: "unreadable"}
 
@@ -36,12 +37,13 @@ class SceneDesc(C.Structure):
                 ("n_quads", I64), ("quads", P), ("quad_axis", P), ("quad_mat", P),
                 ("n_verts", I64), ("verts", P), ("n_tris", I64), ("tris", P), ("tri_mat", P),
                 ("n_mats", I64), ("mat_type", P), ("mats", P),
-                ("camera", C.c_float * 10), ("env_is_nif", I32), ("env_rgb", C.c_float * 3)]
+                ("camera", C.c_float * 10), ("env_is_nif", I32), ("env_rgb", C.c_float * 3), ("node_format", I32)]
 
 
 class SceneInfo(C.Structure):
     _fields_ = [("n_prims", I64), ("n_nodes", I64), ("node_bytes", I64), ("prim_bytes", I64),
-                ("bvh_depth", I32), ("has_emission", I32)]
+                ("bvh_depth", I32), ("has_emission", I32), ("node_format", I32), ("reserved", I32),
+                ("traversed_node_bytes", I64)]
 
 
 class NifDesc(C.Structure):
@@ -120,6 +122,7 @@ def lib():
             "pt_last_render_schedule": ([P, P], I32),
             "pt_kernel_launches": ([P], I32),
             "pt_build_bvh_host": ([I64, P, P, P, I64, P, P, P], I32),
+            "pt_quantize_bvh_host": ([I64, P, P], I32),
             "pt_nif_set_params": ([P, P, P, P], I32),
             "pt_nif_fp8_scales": ([P, P], I32),
             "pt_train_nif": ([P, P, P, I32, I32, P, P, P], I32),
@@ -212,7 +215,7 @@ class Context:
 class Scene:
     """pt_create_scene from an inputs.Scene (host arrays, read during the call)."""
 
-    def __init__(self, ctx: Context, scene: I.Scene):
+    def __init__(self, ctx: Context, scene: I.Scene, node_format: str = "auto"):
         scene.validate()
         self.ctx = ctx
         self.src = scene
@@ -230,6 +233,7 @@ class Scene:
         env = scene.env_const if scene.env_const is not None else np.zeros(3)
         for i in range(3):
             d.env_rgb[i] = float(env[i])
+        d.node_format = NODE_FORMATS[node_format]
         self.h = P()
         ctx._raise(lib().pt_create_scene(ctx.h, C.byref(d), C.byref(self.h)))
 
@@ -586,6 +590,16 @@ def build_bvh_host(lo: np.ndarray, hi: np.ndarray):
     if st != PT_OK:
         raise PTError(st, "pt_build_bvh_host failed")
     return nodes[:n_nodes.value], int(root.value), int(depth.value)
+
+
+def quantize_bvh_host(nodes: np.ndarray) -> np.ndarray:
+    """pt_quantize_bvh_host: the 32-byte quantised form [n, 8] uint32 of packed nodes [n, 12]."""
+    nodes = np.ascontiguousarray(nodes, np.uint32).reshape(-1, 12)
+    out = np.zeros((max(len(nodes), 1), 8), np.uint32)
+    st = lib().pt_quantize_bvh_host(len(nodes), _np_ptr(nodes), _np_ptr(out))
+    if st != PT_OK:
+        raise PTError(st, "pt_quantize_bvh_host failed")
+    return out[:len(nodes)]
 
 
 def kernel_launches() -> int:

@@ -78,3 +78,14 @@ def test_traversal_roofline_counts_algorithmic_flops():
     assert r["unit"] == "TFLOP/s" and r["bound"] == "alu" and r["kernel"] == "k_trace"
     ops = 58 * 1000 + 36 * 100 + 12 * 10 + 46
     assert abs(r["issue_frac"] - ops / 1e-6 / (152 * 128 * 2070e6)) < 1e-12
+
+
+def test_trace_traffic_follows_the_captured_source(monkeypatch):
+    """The traversal's DRAM traffic is reported only while the traversal
+    source is the one the ncu capture was taken on."""
+    import bench
+    monkeypatch.setattr(bench, "TRACE_TRAFFIC", {"C2": {"bytes_per_ray": 40.0, "src": bench.trace_source_hash()}})
+    assert bench.trace_traffic("C2", 1000) == 40000.0
+    assert bench.trace_traffic("C3", 1000) is None
+    monkeypatch.setattr(bench, "TRACE_TRAFFIC", {"C2": {"bytes_per_ray": 40.0, "src": "0" * 16}})
+    assert bench.trace_traffic("C2", 1000) is None

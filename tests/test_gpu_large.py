@@ -99,3 +99,43 @@ def test_large_bvh_schedules_bit_identical(pt, ctx, large):
                       pt.last_render_counts(ctx, cfg.max_depth), np.array(list(pt.last_render_work(ctx).values())))
     for x, y in zip(out["wavefront"], out["paths"]):
         assert np.array_equal(x, y)
+
+
+@pytest.fixture(scope="module")
+def large_quant(pt, ctx, large):
+    sc, _, _ = large
+    return pt.Scene(ctx, sc, node_format="quant8")
+
+
+def test_large_bvh_quantised_nodes_same_paths(pt, ctx, large, large_quant):
+    """The 32-byte quantised node form (8-bit grid per node) of the
+    10M-triangle tree: every decoded box contains the packed one, so the
+    same closest hits and the same paths as the packed 48-byte form, bit for
+    bit (both schedules); the node and triangle visits of both forms are
+    printed (the looser boxes change the visiting order, so neither count
+    bounds the other path by path)."""
+    sc, gs, _ = large
+    gq = large_quant
+    info = gq.info()
+    assert info["node_format"] == 3 and info["traversed_node_bytes"] == 32 * info["n_nodes"]
+    cfg = I.RenderCfg(1920, 1080, 2, 8)
+    pix = torch.from_numpy(subset_pixels(1920, 1080)[::4].copy()).cuda()
+    ref = pt.render_pixels(ctx, gs, None, cfg, pix, want_slots=True, want_ids=True, schedule="wavefront")
+    ctx.check()
+    w_packed = pt.last_render_work(ctx)
+    for sched in ("wavefront", "paths"):
+        got = pt.render_pixels(ctx, gq, None, cfg, pix, want_slots=True, want_ids=True, schedule=sched)
+        ctx.check()
+        for x, y in zip(ref, got):
+            assert torch.equal(x, y)
+        print({"packed": w_packed, "quant8": pt.last_render_work(ctx)})
+
+
+def test_large_bvh_quantised_subset_parity(pt, ctx, large, large_quant):
+    """Per-path parity with the oracle on the pixel subset, quantised nodes."""
+    sc, _, osc = large
+    cfg = I.RenderCfg(1920, 1080, 1, 8)
+    res = compare_render(pt, ctx, sc, cfg, pixels=subset_pixels(1920, 1080), gpu_scene=large_quant,
+                         oracle_scene=osc, max_div=5e-3)
+    print(res)
+    assert res["overall"] <= 1e-3, res
