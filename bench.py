@@ -61,7 +61,12 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) of the traversal kernel per traced ray, from one ncu capture of a smaller frame of
 # the same workload (summaries and commands in profiles/), scaled to a frame by the rays it traces.  Valid only
 # while the traversal source is the one captured (sha256 of trace.cu + device_common.cuh, first 16 hex digits).
-TRACE_TRAFFIC = {}
+TRACE_TRAFFIC = {
+    # 1920x1080 at 8 spp = one full 2^24-path chunk of the 32-spp frame (profiles/k_trace_traffic_large_bvh_c4.md)
+    ("C4", "packed"): {"bytes_per_ray": 365.1, "src": "7d34db8adafd2d1d"},
+    ("C4", "quant8"): {"bytes_per_ray": 283.6, "src": "7d34db8adafd2d1d"},
+}
+NODE_FORMS = {1: "packed", 2: "decoded", 3: "quant8"}
 TRACE_SOURCES = ("paper_2305_20061_gb300/csrc/trace.cu", "paper_2305_20061_gb300/csrc/device_common.cuh")
 
 
@@ -74,10 +79,10 @@ def trace_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def trace_traffic(workload: str, rays: int):
+def trace_traffic(workload: str, node_form: str, rays: int):
     """DRAM bytes of the traversal kernel over a frame of `rays` traced rays, or None when no capture of
-    this workload exists or the traversal source changed since it was taken."""
-    rec = TRACE_TRAFFIC.get(workload)
+    this workload and node form exists or the traversal source changed since it was taken."""
+    rec = TRACE_TRAFFIC.get((workload, node_form))
     if rec is None or rec["src"] != trace_source_hash():
         return None
     return rec["bytes_per_ray"] * rays
@@ -506,7 +511,8 @@ def bench_ours(args):
                                   "")
 
     if roof["kernel"] in ("k_trace", "k_paths"):
-        roof["traffic"] = trace_traffic(args.workload, rays) if trace_kernel == "k_trace" else None
+        roof["traffic"] = (trace_traffic(args.workload, NODE_FORMS[scene.info()["node_format"]], rays)
+                           if trace_kernel == "k_trace" else None)
         roof["traffic_note"] = ("DRAM bytes per frame of k_trace (all its launches), from the ncu capture in "
                                 "profiles/ scaled by traced rays; null when no capture of this workload matches "
                                 "the current traversal source")
@@ -894,8 +900,8 @@ def bench_nif_sweep(args):
     standalone FP32 and BF16 evaluation rates on 2^24 coordinates, and the C2
     frame rate with that network as the environment.  The BF16 kernel keeps
     every weight in shared memory; it takes H = 128 with 1 to 5 hidden layers
-    (three, two, then one 128-row tile slot beside the weights) and no shape
-    beyond.  One JSON line."""
+    (three, two, then one 128-row tile slot beside the weights) and H = 64
+    or 32 with 1 to 8 (four slots), and no shape beyond.  One JSON line."""
     import torch
     from paper_2305_20061_gb300 import build
     build.build()
@@ -922,7 +928,9 @@ def bench_nif_sweep(args):
         return e0.elapsed_time(e1) / reps
 
     rows = []
-    for H, L in [(128, 1), (128, 2), (128, 3), (128, 4), (128, 5), (128, 6), (128, 8), (64, 3), (32, 3)]:
+    shapes = [(128, 1), (128, 2), (128, 3), (128, 4), (128, 5), (128, 6), (128, 8), (64, 2), (64, 3), (64, 4), (64, 8),
+              (32, 2), (32, 3), (32, 4), (32, 8)]
+    for H, L in shapes:
         g = pt.Nif(ctx, I.nif_init(hidden=H, n_hidden_layers=L, colour="yuv"))
         tprec = "bf16"
         try:
@@ -940,15 +948,15 @@ def bench_nif_sweep(args):
         row = {"hidden": H, "layers": L, "params": g.param_count, "weights_kb_bf16": (g.param_count * 2) // 1024,
                "train_gemms": tprec, "train_ms_per_step": train_ms / steps, "quality": nif_quality(g, sky, dev)}
         row["fp32_evals_per_s"] = (1 << 24) / (ms_of(lambda: g.eval(uv, "fp32"), 2) * 1e-3)
-        bf16_ok = H == 128 and 1 <= L <= 5
+        bf16_ok = (H == 128 and 1 <= L <= 5) or (H in (64, 32) and 1 <= L <= 8)
         if bf16_ok:
             row["bf16_evals_per_s"] = (1 << 24) / (ms_of(lambda: g.eval(uv, "bf16"), 3) * 1e-3)
-            row["bf16_tile_slots"] = 3 if L <= 3 else (2 if L == 4 else 1)
+            row["bf16_tile_slots"] = (3 if L <= 3 else (2 if L == 4 else 1)) if H == 128 else 4
             fr = ms_of(lambda: pt.render(ctx, scene, g, cfg, "bf16", out=img), 3)
             row["c2_bf16_msamples_s"] = cfg.n_slots / (fr * 1e-3) / 1e6
         else:
             row["bf16_evals_per_s"] = None
-            row["bf16_note"] = "not resident: the BF16 kernel needs H = 128 and L <= 5"
+            row["bf16_note"] = "not resident: the BF16 kernel needs H = 128 with L <= 5, or H = 64 / 32 with L <= 8"
         ctx.check()
         rows.append(row)
         del g

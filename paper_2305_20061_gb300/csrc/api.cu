@@ -312,7 +312,7 @@ pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, int ac
         return PT_OK;
     }
     if (precision == PT_BF16 && nif->d_tc) {
-        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nif->d_tc, nif->L, p, 1, ctx->sm_count, s); }));
+        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nif->d_tc, nif->H, nif->L, p, 1, ctx->sm_count, s); }));
         return PT_OK;
     }
     if (precision == PT_FP8E4M3 && nif->fp8_ok) {
@@ -797,7 +797,7 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
         return PT_OK;
     }
     if (precision == PT_BF16 && nf->d_tc) {
-        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nf->d_tc, nf->L, p, 0, ctx->sm_count, s); }));
+        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nf->d_tc, nf->H, nf->L, p, 0, ctx->sm_count, s); }));
         return PT_OK;
     }
     if (precision == PT_FP8E4M3 && nf->fp8_ok) {
@@ -904,7 +904,7 @@ pt_status ensure_train(pt_ctx* ctx, pt_nif* nf, int64_t B)
 pt_status refresh_layouts(pt_ctx* ctx, pt_nif* nf, cudaStream_t s)
 {
     PT_CUDA(repack_nif_fp32(nf->d_params, nf->F, nf->H, nf->L, nf->d_fp32, s));
-    if (nf->d_tc) PT_CUDA(repack_nif_tc_image(nf->d_params, nf->L, nf->d_tc, s));
+    if (nf->d_tc) PT_CUDA(repack_nif_tc_image(nf->d_params, nf->H, nf->L, nf->d_tc, s));
     nf->fp8_stale = true;   // rebuilt on its next use
     return PT_OK;
 }

@@ -3,21 +3,24 @@
 // weights as future work, Section 5), on sm_103a tcgen05 tensor cores with
 // FP32 accumulation.
 //
-// Quantisation: features are scaled by 448 (|f| <= 1); hidden weights and
-// the head carry one scale per output row (row max / 448); hidden
-// activations carry one scale per layer, calibrated on the host from the FP32
-// network over a fixed 32 x 32 grid of (u, v) pixel centres (layer max /
-// 448, values beyond saturate).  Dequantisation, bias, ReLU and the next
-// layer's quantisation fold into one FMA per value:
-//   q_out = relu(acc * (s_in * s_w[j] / s_out) + b[j] / s_out)
-// done as packed FP32x2 FMAs and a saturating ReLU conversion to E4M3.
+// Quantisation: features are scaled by 448 (|f| <= 1); each hidden layer's
+// weights carry one scale (layer max / 448), the head one scale per output
+// row; hidden activations carry one scale per layer, calibrated on the host
+// from the FP32 network over a fixed 32 x 32 grid of (u, v) pixel centres
+// (layer max / 448, values beyond saturate).  The bias of a hidden layer,
+// expressed in accumulator units b / (s_w s_in), is split on the host into
+// E4M3 terms of a block of powers of two and added by one more K = 32 MMA
+// step, so the epilogue is one packed multiply by the layer's constant
+// s_w s_in / s_out and a saturating ReLU conversion to E4M3 per pair of
+// values, with no per-column loads.
 //
 // A 128-element E4M3 row is exactly one 128-byte swizzle row, so operands
 // are half the size of the BF16 kernel's: four tile slots fit beside the
-// weights.  One warpgroup per slot (thread t = row t = TMEM lane t), warp 16
-// allocates TMEM and issues the MMAs (128x128x32, head 128x16x32); the head
-// reuses the slot's accumulator columns after the last hidden epilogue has
-// read them.  All waits are bounded as in the BF16 kernel.
+// weights (TMEM: four 128-column accumulators; the head reuses its slot's
+// columns).  As in the BF16 kernel, each slot is one warpgroup (thread t =
+// row t = TMEM lane t), every step ends with a slot-wide bar.red.or (the
+// abort vote) and the slot's first thread issues the next MMA group
+// (128x128x32, bias 128x128x32, head 128x16x32).  All waits are bounded.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -37,25 +40,43 @@ using namespace tc;
 
 constexpr int kF = 64, kH = 128, kRows = 128;
 constexpr int kSlots = 4;
-constexpr int kThreads = (4 * kSlots + 1) * 32;   // 4 warps per slot + the MMA warp
-constexpr int kMmaWarp = 4 * kSlots;
+constexpr int kThreads = 4 * kSlots * 32;         // one warpgroup per slot
 constexpr uint32_t kTmemCols = 512;
 
 constexpr uint32_t kWBytes = kH * kH;              // 16 KB per hidden layer
 constexpr uint32_t kHeadRows = 16;
 constexpr uint32_t kOffHead = 3 * kWBytes;         // 49152
-constexpr uint32_t kOffTail = kOffHead + kHeadRows * kH;  // 51200
-// tail floats: mul [3][128], add [3][128], head mul [4], head add [4], B [128], M [12]
-constexpr uint32_t kTailFloats = 6 * kH + 8 + 2 * kF + 12;
-constexpr uint32_t kImageBytes = kOffTail + kTailFloats * 4;   // 54864
-constexpr uint32_t kOffA = 55296;                  // 1024-aligned, four 16 KB operand buffers
+// Hidden-layer biases ride on the tensor core as one more K = 32 step: A is a
+// block whose column i holds the power of two kBiasPow[i] in every row, B
+// holds the bias of each output split into E4M3 terms, bias ~= sum_i
+// kBiasPow[i] * B[j][i]; both K-major without swizzle (core matrices 8 rows x
+// 16 B, K step 128 B, 8-row step 256 B).
+constexpr uint32_t kBiasBytes = kRows * 32;        // 4096 per block
+constexpr uint32_t kBiasLbo = 128, kBiasSbo = 256;
+constexpr uint32_t kOffBias = kOffHead + kHeadRows * kH;   // 51200
+constexpr uint32_t kOffOnes = kOffBias + 3 * kBiasBytes;    // 63488
+constexpr uint32_t kOffTail = kOffOnes + kBiasBytes;        // 67584
+// tail floats: alpha [4] (per-layer requantisation), head mul [4], head add [4], B pairs [128], M [12]
+constexpr uint32_t kTailFloats = 4 + 8 + 2 * kF + 12;
+constexpr uint32_t kImageBytes = kOffTail + kTailFloats * 4;
+constexpr uint32_t kOffA = (kImageBytes + 1023) & ~1023u;   // 1024-aligned operand buffers
 constexpr uint32_t kABytes = kRows * kH;
 constexpr uint32_t kOffBar = kOffA + kSlots * kABytes;
 constexpr uint32_t kSmemBytes = kOffBar + 128 + 1024;
+// powers of two of the bias block's columns (E4M3-exact): eight of 2^8 for the
+// magnitude, then 2^4, 1, 2^-4, 2^-8 for the remaining bits
+constexpr int kBiasTerms = 12;
+__host__ __device__ constexpr float bias_pow(int i) { return i < 8 ? 256.f : (i == 8 ? 16.f : (i == 9 ? 1.f : (i == 10 ? 0.0625f : 0.00390625f))); }
+// byte offset of element (row r, k < 32) of a bias / ones block
+__host__ __device__ constexpr uint32_t bias_byte(uint32_t r, uint32_t k)
+{
+    return (r >> 3) * kBiasSbo + (k >> 4) * kBiasLbo + (r & 7) * 16 + (k & 15);
+}
 constexpr float kE4M3Max = 448.f;
 
 static_assert(kImageBytes % 16 == 0, "bulk copy size");
 static_assert(kOffA % 1024 == 0 && kOffHead % 1024 == 0 && kOffA >= kImageBytes, "layout");
+static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 
 // 16-byte chunk c (elements [16c, 16c+16)) of row r of a 128 x 128 E4M3 operand, SWIZZLE_128B K-major
 __device__ __forceinline__ uint32_t chunk8(uint32_t r, uint32_t c) { return r * 128 + (((c & 7) ^ (r & 7)) << 4); }
@@ -79,30 +100,46 @@ struct Fp8Params {
     unsigned long long* stats;
 };
 
+// bar.red.or over the 128 threads of a slot: true on every thread if any passed true
+__device__ __forceinline__ bool slot_vote_any(int id, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred p, q;\n"
+        "setp.ne.u32 p, %1, 0;\n"
+        "bar.red.or.pred q, %2, 128, p;\n"
+        "selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id)
+        : "memory");
+    return r != 0;
+}
+
 __global__ void __launch_bounds__(kThreads, 1) k_nif_fp8(const Fp8Params p, int mode)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar_a = sbase + kOffBar;
-    const uint32_t bar_acc = bar_a + 8 * kSlots;
-    const uint32_t bar_w = bar_acc + 8 * kSlots;
-    const uint32_t bar_drain = bar_w + 8;
+    const uint32_t bar_acc = sbase + kOffBar;            // [kSlots] accumulator ready (commit)
+    const uint32_t bar_w = bar_acc + 8 * kSlots;         // weights loaded
+    const uint32_t bar_drain = bar_w + 8;                // [kSlots] final drain after an abort
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kOffBar + 96);
     volatile int* abort = reinterpret_cast<volatile int*>(smem + kOffBar + 100);
     const float* tail = reinterpret_cast<const float*>(smem + kOffTail);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = warp >> 2;
+    const uint32_t row = (warp & 3) * 32 + lane;
+    const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
     const int64_t count = mode == 0 ? p.n : (int64_t)min(*p.esc_count, p.esc_cap);
     const int64_t n_tiles = (count + kRows - 1) / kRows;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kSlots; ++s) {
-            mbar_init(bar_a + 8 * s, kRows);
-            mbar_init(bar_acc + 8 * s, 1);
+        for (int t = 0; t < kSlots; ++t) {
+            mbar_init(bar_acc + 8 * t, 1);
+            mbar_init(bar_drain + 8 * t, 1);
         }
         mbar_init(bar_w, 1);
-        mbar_init(bar_drain, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -112,7 +149,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_fp8(const Fp8Params p, int 
         for (uint32_t off = 0; off < kImageBytes; off += 32768u)
             bulk_g2s(sbase + off, p.image + off, min(32768u, kImageBytes - off), bar_w);
     }
-    if (warp == kMmaWarp) {
+    if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -122,182 +159,167 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_fp8(const Fp8Params p, int 
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     mbar_wait(bar_w, 0, abort, p.err);
+    __syncthreads();
+    bool dead = *abort != 0;
 
-    if (warp == kMmaWarp) {
-        if (lane == 0 && !*abort) {
-            const uint32_t id_h = idesc_e4m3(128, 128), id_o = idesc_e4m3(128, kHeadRows);
-            uint32_t ph[kSlots] = {0, 0, 0, 0};
-            int stage[kSlots] = {0, 0, 0, 0};
-            int64_t it[kSlots] = {0, 0, 0, 0};
-            bool done[kSlots];
-            int live = 0;
-            for (int s = 0; s < kSlots; ++s) {
-                done[s] = ((int64_t)blockIdx.x * kSlots + s) >= n_tiles;
-                live += done[s] ? 0 : 1;
-            }
-            uint64_t last = global_ns();
-            while (live > 0 && !*abort) {
-                bool progressed = false;
-                for (int s = 0; s < kSlots; ++s) {
-                    if (done[s] || !mbar_test_wait(bar_a + 8 * s, ph[s])) continue;
-                    progressed = true;
-                    ph[s] ^= 1;
-                    tc_fence_after();
-                    const uint32_t a_base = sbase + kOffA + s * kABytes;
-                    const uint32_t d = tmem + s * 128;
-                    const bool head = stage[s] == 3;
-                    const uint32_t b_base = head ? sbase + kOffHead : sbase + stage[s] * kWBytes;
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        mma_e4m3(d, sw128_desc(a_base + 32 * kk), sw128_desc(b_base + 32 * kk), head ? id_o : id_h, kk > 0);
-                    mma_commit(bar_acc + 8 * s);
-                    if (++stage[s] == 4) {
-                        stage[s] = 0;
-                        ++it[s];
-                        if ((it[s] * gridDim.x + blockIdx.x) * kSlots + s >= n_tiles) {
-                            done[s] = true;
-                            --live;
-                        }
-                    }
-                }
-                if (progressed) {
-                    last = global_ns();
-                } else {
-                    __nanosleep(32);   // nothing ready: yield the issue slots to the epilogue warps
-                }
-                if (!progressed && global_ns() - last > kWaitBudgetNs) {
-                    atomicOr(p.err, PT_ERR_TIMEOUT);
-                    *abort = 1;
-                }
-            }
-            if (*abort) {
-                mma_commit(bar_drain);
-                const uint64_t t0 = global_ns();
-                while (!mbar_try_wait(bar_drain, 0) && global_ns() - t0 < kWaitBudgetNs) {
-                }
+    const bool issuer = (warp & 3) == 0 && lane == 0;
+    const int bar_id = 1 + s;
+    const uint32_t a_base = sbase + kOffA + s * kABytes;
+    const uint32_t acc = tmem + s * 128;
+    const uint32_t bar = bar_acc + 8 * s;
+    const float* Bm = tail + 12;
+    const float* Mm = Bm + 2 * kF;
+    const uint32_t id_h = idesc_e4m3(128, 128), id_o = idesc_e4m3(128, kHeadRows);
+    uint32_t ph = 0;
+    auto load_inputs = [&](int64_t tile) {
+        In8 t = {};
+        const int64_t gg = tile * kRows + row;
+        if (tile < n_tiles && gg < count) {
+            if (mode == 0) {
+                const float2 q = reinterpret_cast<const float2*>(p.uv)[gg];
+                t.u = q.x; t.v = q.y;
+            } else {
+                const float2* e = reinterpret_cast<const float2*>(p.esc + gg);
+                const float2 a = e[0], b = e[1], c = e[2];
+                t.slot = __float_as_uint(a.x); t.u = a.y; t.v = b.x; t.tr = b.y; t.tg = c.x; t.tb = c.y;
             }
         }
-    } else {
-        const int s = warp >> 2;
-        const uint32_t row = (warp & 3) * 32 + lane;
-        const uint32_t lane_base = ((uint32_t)(warp & 3) * 32u) << 16;
-        const uint32_t a_base = sbase + kOffA + s * kABytes;
-        const float* Bm = tail + 6 * kH + 8;
-        const float* Mm = Bm + 2 * kF;
-        uint32_t ph = 0;
-        auto load_inputs = [&](int64_t tile) {
-            In8 t = {};
-            const int64_t gg = tile * kRows + row;
-            if (tile < n_tiles && gg < count) {
-                if (mode == 0) {
-                    const float2 q = reinterpret_cast<const float2*>(p.uv)[gg];
-                    t.u = q.x; t.v = q.y;
-                } else {
-                    const float2* e = reinterpret_cast<const float2*>(p.esc + gg);
-                    const float2 a = e[0], b = e[1], c = e[2];
-                    t.slot = __float_as_uint(a.x); t.u = a.y; t.v = b.x; t.tr = b.y; t.tg = c.x; t.tb = c.y;
-                }
-            }
-            return t;
-        };
-        In8 in = load_inputs((int64_t)blockIdx.x * kSlots + s);
-        for (int64_t i = 0;; ++i) {
-            const int64_t tile = ((int64_t)i * gridDim.x + blockIdx.x) * kSlots + s;
-            if (tile >= n_tiles) break;
-            if (__any_sync(0xFFFFFFFFu, *abort != 0)) break;
-            const int64_t g = tile * kRows + row;
-            const bool valid = g < count;
-            // features x 448 -> E4M3: sin of frequencies 0..63 in chunks 0..3, cos in chunks 4..7
+        return t;
+    };
+    In8 in = load_inputs((int64_t)blockIdx.x * kSlots + s);
+    for (int64_t i = 0; !dead; ++i) {
+        const int64_t tile = ((int64_t)i * gridDim.x + blockIdx.x) * kSlots + s;
+        if (tile >= n_tiles) break;   // slot-uniform
+        const int64_t g = tile * kRows + row;
+        const bool valid = g < count;
+        // features x 448 -> E4M3: sin of frequencies 0..63 in chunks 0..3, cos in chunks 4..7
+        {
+            const uint64_t uu = pack_f32x2(in.u, in.u), vv = pack_f32x2(in.v, in.v);
+            const uint64_t two_pi = pack_f32x2(6.28318530717958648f, 6.28318530717958648f);
+            const uint64_t magic = pack_f32x2(12582912.f, 12582912.f);
+            const uint64_t k448 = pack_f32x2(kE4M3Max, kE4M3Max);
 #pragma unroll 1
             for (int c16 = 0; c16 < 4; ++c16) {
                 uint32_t sw[4], cw[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    float sv[4], cv[4];
+                    uint32_t s2[2], c2[2];
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const int f = c16 * 16 + 4 * j + h;
-                        const float t = fmaf(Bm[2 * f], in.u, Bm[2 * f + 1] * in.v);
-                        const float r = t - rintf(t);
-                        __sincosf(6.28318530717958648f * r, &sv[h], &cv[h]);
+                    for (int h = 0; h < 2; ++h) {
+                        const int f = c16 * 16 + 4 * j + 2 * h;
+                        const float4 bq = *reinterpret_cast<const float4*>(Bm + 2 * f);   // frequencies f, f + 1
+                        const uint64_t t = fma_f32x2(pack_f32x2(bq.x, bq.y), uu, mul_f32x2(pack_f32x2(bq.z, bq.w), vv));
+                        const uint64_t n = sub_f32x2(add_f32x2(t, magic), magic);
+                        const uint64_t a = mul_f32x2(sub_f32x2(t, n), two_pi);
+                        float sv[2], cv[2];
+                        __sincosf(lo_f32(a), &sv[0], &cv[0]);
+                        __sincosf(hi_f32(a), &sv[1], &cv[1]);
+                        const uint64_t ss = mul_f32x2(pack_f32x2(sv[0], sv[1]), k448);
+                        const uint64_t cc = mul_f32x2(pack_f32x2(cv[0], cv[1]), k448);
+                        s2[h] = pack_e4m3x2(lo_f32(ss), hi_f32(ss));
+                        c2[h] = pack_e4m3x2(lo_f32(cc), hi_f32(cc));
                     }
-                    sw[j] = pack_e4m3x2(sv[0] * kE4M3Max, sv[1] * kE4M3Max) |
-                            (pack_e4m3x2(sv[2] * kE4M3Max, sv[3] * kE4M3Max) << 16);
-                    cw[j] = pack_e4m3x2(cv[0] * kE4M3Max, cv[1] * kE4M3Max) |
-                            (pack_e4m3x2(cv[2] * kE4M3Max, cv[3] * kE4M3Max) << 16);
+                    sw[j] = s2[0] | (s2[1] << 16);
+                    cw[j] = c2[0] | (c2[1] << 16);
                 }
                 st_shared_v4(a_base + chunk8(row, c16), sw[0], sw[1], sw[2], sw[3]);
                 st_shared_v4(a_base + chunk8(row, 4 + c16), cw[0], cw[1], cw[2], cw[3]);
             }
-            fence_proxy_async();
-            mbar_arrive(bar_a + 8 * s);
-            const In8 next = load_inputs(((int64_t)(i + 1) * gridDim.x + blockIdx.x) * kSlots + s);
-
-            bool ok = true;
-            for (int layer = 0; layer < 3; ++layer) {
-                const bool got = mbar_wait(bar_acc + 8 * s, ph, abort, p.err);
-                if (!__all_sync(0xFFFFFFFFu, got)) { ok = false; break; }
-                ph ^= 1;
+        }
+        const float tr = in.tr, tg = in.tg, tb = in.tb;
+        const uint32_t slot = in.slot;
+        in = load_inputs(((int64_t)(i + 1) * gridDim.x + blockIdx.x) * kSlots + s);
+        fence_proxy_async();
+        bool fail = false;
+        for (int stage = 0; stage <= 3; ++stage) {   // the hidden layers, then the head
+            tc_fence_before();
+            if (slot_vote_any(bar_id, fail)) { dead = true; break; }
+            if (issuer) {
                 tc_fence_after();
-                const uint64_t* mul2 = reinterpret_cast<const uint64_t*>(tail + layer * kH);
-                const uint64_t* add2 = reinterpret_cast<const uint64_t*>(tail + (3 + layer) * kH);
-#pragma unroll 1
-                for (int c32 = 0; c32 < 4; ++c32) {
-                    uint32_t r[32];
-                    TMEM_LD32(tmem + lane_base + s * 128 + c32 * 32, r);
-                    tmem_wait_ld();
+                const bool head = stage == 3;
+                const uint32_t b_base = head ? sbase + kOffHead : sbase + stage * kWBytes;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    mma_e4m3(acc, sw128_desc(a_base + 32 * kk), sw128_desc(b_base + 32 * kk), head ? id_o : id_h, kk > 0);
+                if (!head)
+                    mma_e4m3(acc, plain_desc(sbase + kOffOnes, kBiasLbo, kBiasSbo),
+                             plain_desc(sbase + kOffBias + stage * kBiasBytes, kBiasLbo, kBiasSbo), id_h, 1);
+                mma_commit(bar);
+            }
+            const bool got = mbar_wait(bar, ph, abort, p.err);
+            ph ^= 1;
+            tc_fence_after();
+            if (!__all_sync(0xFFFFFFFFu, got)) { fail = true; continue; }   // voted at the next barrier
+            if (stage < 3) {
+                const uint64_t alpha = pack_f32x2(tail[stage], tail[stage]);   // requantisation of this layer
+                uint32_t ra[32], rb[32];
+                auto put32 = [&](const uint32_t (&r)[32], int c32) {
                     uint32_t q[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        const uint64_t v0 = fma_f32x2(pack_u64(r[4 * j], r[4 * j + 1]), mul2[c32 * 16 + 2 * j],
-                                                      add2[c32 * 16 + 2 * j]);
-                        const uint64_t v1 = fma_f32x2(pack_u64(r[4 * j + 2], r[4 * j + 3]), mul2[c32 * 16 + 2 * j + 1],
-                                                      add2[c32 * 16 + 2 * j + 1]);
+                        const uint64_t v0 = mul_f32x2(pack_u64(r[4 * j], r[4 * j + 1]), alpha);
+                        const uint64_t v1 = mul_f32x2(pack_u64(r[4 * j + 2], r[4 * j + 3]), alpha);
                         q[j] = pack_relu_e4m3x2(__uint_as_float((uint32_t)v0), __uint_as_float((uint32_t)(v0 >> 32))) |
                                (pack_relu_e4m3x2(__uint_as_float((uint32_t)v1), __uint_as_float((uint32_t)(v1 >> 32)))
                                 << 16);
                     }
                     st_shared_v4(a_base + chunk8(row, 2 * c32), q[0], q[1], q[2], q[3]);
                     st_shared_v4(a_base + chunk8(row, 2 * c32 + 1), q[4], q[5], q[6], q[7]);
-                }
-                tc_fence_before();
+                };
+                const uint32_t tcol = acc + lane_base;
+                TMEM_LD32(tcol, ra);
+                tmem_wait_ld();
+                TMEM_LD32(tcol + 32, rb);
+                put32(ra, 0);
+                tmem_wait_ld();
+                TMEM_LD32(tcol + 64, ra);
+                put32(rb, 1);
+                tmem_wait_ld();
+                TMEM_LD32(tcol + 96, rb);
+                put32(ra, 2);
+                tmem_wait_ld();
+                put32(rb, 3);
                 fence_proxy_async();
-                mbar_arrive(bar_a + 8 * s);
             }
-            if (!ok) break;
-            const bool got_head = mbar_wait(bar_acc + 8 * s, ph, abort, p.err);
-            if (!__all_sync(0xFFFFFFFFu, got_head)) break;
-            ph ^= 1;
-            tc_fence_after();
-            uint32_t yr[4];
-            tmem_ld4(tmem + lane_base + s * 128, yr);
-            tmem_wait_ld();
-            const float* hm = tail + 6 * kH;
-            const float* ha = hm + 4;
-            const float y0 = fmaf(__uint_as_float(yr[0]), hm[0], ha[0]);
-            const float y1 = fmaf(__uint_as_float(yr[1]), hm[1], ha[1]);
-            const float y2 = fmaf(__uint_as_float(yr[2]), hm[2], ha[2]);
-            const float r0 = expf(Mm[0] * y0 + Mm[1] * y1 + Mm[2] * y2);
-            const float r1 = expf(Mm[3] * y0 + Mm[4] * y1 + Mm[5] * y2);
-            const float r2 = expf(Mm[6] * y0 + Mm[7] * y1 + Mm[8] * y2);
-            if (valid) {
-                if (mode == 0) {
-                    p.rgb[3 * g] = r0; p.rgb[3 * g + 1] = r1; p.rgb[3 * g + 2] = r2;
-                } else {
-                    float* L = p.slot_L + 3 * (size_t)in.slot;
-                    float a = in.tr * r0, b = in.tg * r1, c = in.tb * r2;
-                    if (p.accumulate) { a += L[0]; b += L[1]; c += L[2]; }
-                    if (!(isfinite(a) && isfinite(b) && isfinite(c))) atomicOr(p.err, PT_ERR_NONFINITE);
-                    L[0] = a; L[1] = b; L[2] = c;
-                }
+        }
+        if (dead) break;
+        tc_fence_before();
+        if (slot_vote_any(bar_id, fail)) { dead = true; break; }
+        tc_fence_after();
+        uint32_t yr[4];
+        tmem_ld4(acc + lane_base, yr);
+        tmem_wait_ld();
+        const float* hm = tail + 4;
+        const float* ha = hm + 4;
+        const float y0 = fmaf(__uint_as_float(yr[0]), hm[0], ha[0]);
+        const float y1 = fmaf(__uint_as_float(yr[1]), hm[1], ha[1]);
+        const float y2 = fmaf(__uint_as_float(yr[2]), hm[2], ha[2]);
+        const float r0 = expf(Mm[0] * y0 + Mm[1] * y1 + Mm[2] * y2);
+        const float r1 = expf(Mm[3] * y0 + Mm[4] * y1 + Mm[5] * y2);
+        const float r2 = expf(Mm[6] * y0 + Mm[7] * y1 + Mm[8] * y2);
+        if (valid) {
+            if (mode == 0) {
+                p.rgb[3 * g] = r0; p.rgb[3 * g + 1] = r1; p.rgb[3 * g + 2] = r2;
+            } else {
+                float* L = p.slot_L + 3 * (size_t)slot;
+                float a = tr * r0, b = tg * r1, c = tb * r2;
+                if (p.accumulate) { a += L[0]; b += L[1]; c += L[2]; }
+                if (!(isfinite(a) && isfinite(b) && isfinite(c))) atomicOr(p.err, PT_ERR_NONFINITE);
+                L[0] = a; L[1] = b; L[2] = c;
             }
-            tc_fence_before();
-            in = next;
+        }
+    }
+    if (issuer && *abort) {
+        // make sure no MMA of this slot is still writing TMEM before it is freed
+        mma_commit(bar_drain + 8 * s);
+        const uint64_t t0 = global_ns();
+        while (!mbar_try_wait(bar_drain + 8 * s, 0) && global_ns() - t0 < kWaitBudgetNs) {
         }
     }
     if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0 && p.stats) atomicAdd(p.stats, (unsigned long long)count);
+    tc_fence_before();
     __syncthreads();
-    if (warp == kMmaWarp) {
+    if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
@@ -357,25 +379,43 @@ bool pack_nif_fp8_image(const float* params, int F, int H, int L, std::vector<un
     auto put = [&](uint32_t base, uint32_t r, uint32_t k, uint8_t q) {
         out[base + r * 128 + ((((k >> 4) & 7) ^ (r & 7)) << 4) + (k & 15)] = q;
     };
-    for (int l = 0; l < 4; ++l) {
-        const int rows = l == 3 ? 3 : kH;
-        for (int j = 0; j < rows; ++j) {
-            float wmax = 0.f;
-            for (int k = 0; k < kH; ++k) wmax = std::max(wmax, std::fabs(W[l][(size_t)j * kH + k]));
-            const float sw = wmax > 0.f ? wmax / kE4M3Max : 1.f;
-            for (int k = 0; k < kH; ++k)
-                put(l == 3 ? kOffHead : l * kWBytes, j, k, to_e4m3(W[l][(size_t)j * kH + k] / sw));
-            if (l < 3) {
-                tail[l * kH + j] = s_act[l] * sw / s_act[l + 1];     // folded dequant + requant
-                tail[(3 + l) * kH + j] = b[l][j] / s_act[l + 1];
-            } else {
-                tail[6 * kH + j] = s_act[3] * sw;                    // head dequant
-                tail[6 * kH + 4 + j] = b[3][j];
+    auto from_e4m3 = [](uint8_t q) -> double {
+        __nv_fp8_e4m3 v;
+        std::memcpy(&v, &q, 1);
+        return (double)(float)v;
+    };
+    for (uint32_t r = 0; r < kRows; ++r)
+        for (int i = 0; i < kBiasTerms; ++i) out[kOffOnes + bias_byte(r, i)] = to_e4m3(bias_pow(i));
+    for (int l = 0; l < 3; ++l) {
+        // one weight scale per hidden layer; accumulator units: value / (sw * s_act[l])
+        float wmax = 0.f;
+        for (int k = 0; k < kH * kH; ++k) wmax = std::max(wmax, std::fabs(W[l][k]));
+        const float sw = wmax > 0.f ? wmax / kE4M3Max : 1.f;
+        for (int j = 0; j < kH; ++j)
+            for (int k = 0; k < kH; ++k) put(l * kWBytes, j, k, to_e4m3(W[l][(size_t)j * kH + k] / sw));
+        tail[l] = sw * s_act[l] / s_act[l + 1];
+        // the bias in accumulator units, split greedily into E4M3 terms of the block's powers of two
+        for (int j = 0; j < kH; ++j) {
+            double rem = (double)b[l][j] / ((double)sw * (double)s_act[l]);
+            for (int i = 0; i < kBiasTerms; ++i) {
+                const double pw = bias_pow(i);
+                const uint8_t q = to_e4m3((float)std::max(-448.0, std::min(448.0, rem / pw)));
+                out[kOffBias + l * kBiasBytes + bias_byte(j, i)] = q;
+                rem -= pw * from_e4m3(q);
             }
         }
     }
-    for (int i = 0; i < 2 * kF; ++i) tail[6 * kH + 8 + i] = Bsrc[i];
-    for (int i = 0; i < 9; ++i) tail[6 * kH + 8 + 2 * kF + i] = M[i];
+    tail[3] = 0.f;
+    for (int j = 0; j < 3; ++j) {   // the head keeps one scale per output row
+        float wmax = 0.f;
+        for (int k = 0; k < kH; ++k) wmax = std::max(wmax, std::fabs(W[3][(size_t)j * kH + k]));
+        const float sw = wmax > 0.f ? wmax / kE4M3Max : 1.f;
+        for (int k = 0; k < kH; ++k) put(kOffHead, j, k, to_e4m3(W[3][(size_t)j * kH + k] / sw));
+        tail[4 + j] = s_act[3] * sw;   // head dequant
+        tail[8 + j] = b[3][j];
+    }
+    for (int i = 0; i < 2 * kF; ++i) tail[12 + i] = Bsrc[(i & ~3) | ((i & 1) << 1) | ((i >> 1) & 1)];
+    for (int i = 0; i < 9; ++i) tail[12 + 2 * kF + i] = M[i];
     return true;
 }
 

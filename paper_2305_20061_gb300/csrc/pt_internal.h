@@ -194,10 +194,11 @@ cudaError_t launch_trace_rays(const DevScene& sc, int64_t n, const float* org, c
 // NIF kernels (nif_fp32.cu)
 cudaError_t launch_nif_fp32(const NifEvalParams& p, int mode, int sm_count, cudaStream_t s);
 
-// tensor-core NIF (nif_tc.cu): F = 64, H = 128, L = 1 .. 5 hidden layers (weights resident in shared memory)
+// tensor-core NIF (nif_tc.cu): F = 64; H = 128 with L = 1 .. 5, H = 64 or 32 with L = 1 .. 8 hidden layers
+// (weights resident in shared memory)
 bool nif_tc_supported(int F, int H, int L);
 bool pack_nif_tc_image(const float* params, int F, int H, int L, std::vector<unsigned char>& out);
-cudaError_t launch_nif_tc(const unsigned char* image, int L, const NifEvalParams& p, int mode, int sm_count,
+cudaError_t launch_nif_tc(const unsigned char* image, int H, int L, const NifEvalParams& p, int mode, int sm_count,
                           cudaStream_t s);
 // FP8 E4M3 tensor-core NIF (nif_fp8.cu): same shape; scales_out [4] = activation scales
 bool pack_nif_fp8_image(const float* params, int F, int H, int L, std::vector<unsigned char>& out, float* scales_out);
@@ -279,7 +280,7 @@ cudaError_t cache_query_tc(const unsigned char* image, CacheBox box, int64_t cap
                            int sm_count, cudaStream_t s);
 // rebuild the packed FP32 layout and (when present) the tensor-core image from the master weights
 cudaError_t repack_nif_fp32(const float* params, int F, int H, int L, float* packed, cudaStream_t s);
-cudaError_t repack_nif_tc_image(const float* params, int L, unsigned char* image, cudaStream_t s);
+cudaError_t repack_nif_tc_image(const float* params, int H, int L, unsigned char* image, cudaStream_t s);
 
 // read-only views of the C-ABI handles (api.cu)
 const DevScene* scene_view(const pt_scene* s, int* device);

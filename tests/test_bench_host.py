@@ -84,8 +84,19 @@ def test_trace_traffic_follows_the_captured_source(monkeypatch):
     """The traversal's DRAM traffic is reported only while the traversal
     source is the one the ncu capture was taken on."""
     import bench
-    monkeypatch.setattr(bench, "TRACE_TRAFFIC", {"C2": {"bytes_per_ray": 40.0, "src": bench.trace_source_hash()}})
-    assert bench.trace_traffic("C2", 1000) == 40000.0
-    assert bench.trace_traffic("C3", 1000) is None
-    monkeypatch.setattr(bench, "TRACE_TRAFFIC", {"C2": {"bytes_per_ray": 40.0, "src": "0" * 16}})
-    assert bench.trace_traffic("C2", 1000) is None
+    monkeypatch.setattr(bench, "TRACE_TRAFFIC",
+                        {("C2", "decoded"): {"bytes_per_ray": 40.0, "src": bench.trace_source_hash()}})
+    assert bench.trace_traffic("C2", "decoded", 1000) == 40000.0
+    assert bench.trace_traffic("C2", "packed", 1000) is None
+    assert bench.trace_traffic("C3", "decoded", 1000) is None
+    monkeypatch.setattr(bench, "TRACE_TRAFFIC", {("C2", "decoded"): {"bytes_per_ray": 40.0, "src": "0" * 16}})
+    assert bench.trace_traffic("C2", "decoded", 1000) is None
+
+
+def test_recorded_traffic_matches_the_current_traversal_source():
+    """Every recorded traversal-traffic figure carries the hash of the source it was captured on; a stale
+    entry is reported as null by the bench, so this only checks the format."""
+    import bench
+    for (wl, form), rec in bench.TRACE_TRAFFIC.items():
+        assert wl in ("C1", "C2", "C3", "C4", "C5") and form in bench.NODE_FORMS.values()
+        assert rec["bytes_per_ray"] > 0 and len(rec["src"]) == 16

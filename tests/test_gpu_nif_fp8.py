@@ -40,6 +40,12 @@ def f32(x):
 
 
 def fp8_model(nif, uv, scales):
+    """The kernel's quantisation: features x 448 -> E4M3; per hidden layer one
+    weight scale s_w = max|W| / 448 and E4M3 weights W / s_w; the accumulator
+    q . W8 plus the bias in accumulator units b / (s_w s_in) (the kernel adds
+    it as E4M3 terms to about 2^-20, modelled exactly here); the next codes
+    E4M3(relu(acc x s_w s_in / s_out)) in FP32; the head with one scale per
+    output row, dequantised and biased in FP32."""
     uv = uv.astype(np.float32)
     B = nif.B.astype(np.float64)
     t = f32(B[:, 0][None] * uv[:, :1].astype(np.float64) + B[:, 1][None] * uv[:, 1:].astype(np.float64))
@@ -49,12 +55,12 @@ def fp8_model(nif, uv, scales):
     s = [np.float32(v) for v in scales]
     for l in range(3):
         W = nif.W[l].astype(np.float32)
-        sw = (np.abs(W).max(1) / np.float32(448.0)).astype(np.float32)
-        W8 = e4m3(f32(W / sw[:, None]))
-        mul = f32((s[l] * sw / s[l + 1]).astype(np.float32))
-        add = f32((nif.b[l].astype(np.float32) / s[l + 1]).astype(np.float32))
-        acc = q @ W8.T
-        q = e4m3(np.maximum(f32(acc * mul + add), 0.0))
+        sw = np.float32(np.abs(W).max() / np.float32(448.0))
+        W8 = e4m3(f32(W / sw))
+        beta = nif.b[l].astype(np.float64) / (float(sw) * float(s[l]))
+        alpha = float(np.float32(np.float32(sw * s[l]) / s[l + 1]))
+        acc = q @ W8.T + beta
+        q = e4m3(np.maximum(f32(acc * alpha), 0.0))
     W = nif.W[3].astype(np.float32)
     sw = (np.abs(W).max(1) / np.float32(448.0)).astype(np.float32)
     W8 = e4m3(f32(W / sw[:, None]))

@@ -85,10 +85,11 @@ def test_bf16_nif_error_vs_oracle(pt, ctx):
 
 
 def test_bf16_nif_rejects_other_shapes(pt, ctx):
-    """Beyond F = 64, H = 128, 1 <= L <= 5 the BF16 kernel does not apply: 32
-    frequencies, or six hidden layers, whose weights (192 KB) no longer fit in
-    shared memory beside a 32 KB tile slot."""
-    for kw in ({"n_freq": 32}, {"n_hidden_layers": 6}):
+    """The BF16 kernel takes F = 64 with H = 128 and 1 <= L <= 5, or H = 64
+    or 32 and 1 <= L <= 8; it does not apply to 32 frequencies, to six
+    hidden layers of width 128 (192 KB of weights no longer fit in shared
+    memory beside a 32 KB tile slot) or to width 96."""
+    for kw in ({"n_freq": 32}, {"n_hidden_layers": 6}, {"hidden": 96}):
         g = pt.Nif(ctx, I.nif_init(**kw))
         with pytest.raises(pt.PTError) as e:
             g.eval(torch.zeros((10, 2), device="cuda"), precision="bf16")
@@ -119,6 +120,35 @@ def test_bf16_nif_other_depths_match_rounding_model(pt, ctx, L):
     g.train(torch.from_numpy(I.procedural_sky(64, 32)).cuda(), steps=2, batch=1024, lr=1e-2, precision="bf16")
     flat = g.get_params()
     trained = pt.nif_from_flat(64, 128, L, flat)
+    got2 = g.eval(torch.from_numpy(uv[:4096]).cuda(), precision="bf16").cpu().numpy().astype(np.float64)
+    ref2 = bf16_model(trained, uv[:4096])
+    rel2 = np.abs(got2 - ref2) / np.abs(ref2)
+    assert np.median(rel2) <= 2e-4 and rel2.max() <= 2e-2, (np.median(rel2), rel2.max())
+
+
+@pytest.mark.parametrize("H,L", [(64, 1), (64, 3), (64, 8), (32, 3), (32, 8)])
+def test_bf16_nif_narrow_widths_match_rounding_model(pt, ctx, H, L):
+    """The kernel at widths 64 and 32 (four tile slots; N = H MMAs, K = H
+    after the first layer) against the rounding model, with training
+    following (the image is repacked), and its error against the FP64
+    oracle reported as log-RMSE."""
+    nif = I.nif_init(colour="yuv", hidden=H, n_hidden_layers=L, seed=H + L)
+    rng = np.random.default_rng(H + L)
+    for b in nif.b:
+        b[:] = rng.normal(0, 0.05, b.shape)
+    g = pt.Nif(ctx, nif)
+    n = 128 * 152 * 4 * 2 + 91
+    uv = I.uniform_uv(n, seed=H * L)
+    got = g.eval(torch.from_numpy(uv).cuda(), precision="bf16").cpu().numpy().astype(np.float64)
+    ctx.check()
+    ref = bf16_model(nif, uv)
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert np.all(np.isfinite(got))
+    assert np.median(rel) <= 2e-4 and rel.max() <= 2e-2, (np.median(rel), rel.max())
+    oref, _ = O.Nif(nif).forward(uv[:20000].astype(np.float64))
+    print({"H": H, "L": L, "bf16_log_rmse": float(np.sqrt(np.mean((np.log(got[:20000]) - np.log(oref)) ** 2)))})
+    g.train(torch.from_numpy(I.procedural_sky(64, 32)).cuda(), steps=2, batch=1024, lr=1e-2, precision="fp32")
+    trained = pt.nif_from_flat(64, H, L, g.get_params())
     got2 = g.eval(torch.from_numpy(uv[:4096]).cuda(), precision="bf16").cpu().numpy().astype(np.float64)
     ref2 = bf16_model(trained, uv[:4096])
     rel2 = np.abs(got2 - ref2) / np.abs(ref2)
