@@ -20,7 +20,10 @@
  *                           Snell's law, total internal reflection, Schlick/Smith at h = n;
  *                           GGX metal: mean weight = directional albedo from an independent
  *                           quadrature of the microfacet BRDF, half-vector chi-square)
- *   NIF forward ........... pinned (B = 0, zero weights, relu(x) - relu(-x) = x wiring)
+ *   NIF forward ........... pinned (B = 0, zero weights, relu(x) - relu(-x) = x wiring;
+ *                           skip concatenation: a silent skip layer reduces to the
+ *                           shorter plain network, features routed around it,
+ *                           97.7 KiB parameter count of the paper's network)
  *   NIF backward / Adam ... pinned (central finite differences, Adam closed-form steps)
  *   sky lookup ............ pinned (pixel centres, wrap/clamp, four-centre average)
  *   radiance cache ........ pinned (zero weights, wiring closed forms, fixed-denominator
@@ -441,25 +444,29 @@ static V3 geometric_normal(const OrScene* s, int64_t id, V3 p)
 /* -> fixed colour matrix -> exp (inverse of the log compression).          */
 /* Flat float32 parameter layout: B (F x 2), then per layer W (out x in) and */
 /* b (out), then M (3 x 3).                                                  */
+/* Skip concatenation (Section 3.2, the paper's network): with skip = s >= 1 */
+/* the s-th hidden layer (1-based) has H - 2F outputs, and the input of      */
+/* hidden layer s + 1 is those outputs followed by the 2F Fourier features.  */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int F, H, L;        /* frequencies, hidden width, hidden layers */
+    int skip;           /* 0: plain MLP; s: hidden layer s feeds [h_s, features] to layer s + 1 */
     int nl;             /* linear layers = L + 1 */
     int in[9], out[9];
     double *B, *W[9], *b[9], M[9];
 } OrNif;
 
-OR_API OrNif* or_nif_create(int F, int H, int L, const float* flat)
+OR_API OrNif* or_nif_create_skip(int F, int H, int L, int skip, const float* flat)
 {
-    if (L < 1 || L > 8) return NULL;
+    if (L < 1 || L > 8 || skip < 0 || skip >= L || (skip > 0 && H <= 2 * F)) return NULL;
     OrNif* n = (OrNif*)calloc(1, sizeof(OrNif));
-    n->F = F; n->H = H; n->L = L; n->nl = L + 1;
+    n->F = F; n->H = H; n->L = L; n->skip = skip; n->nl = L + 1;
     const float* p = flat;
     n->B = (double*)malloc(sizeof(double) * 2 * F);
     for (int i = 0; i < 2 * F; ++i) n->B[i] = *p++;
     for (int l = 0; l < n->nl; ++l) {
         n->in[l] = (l == 0) ? 2 * F : H;
-        n->out[l] = (l == n->nl - 1) ? 3 : H;
+        n->out[l] = (l == n->nl - 1) ? 3 : (skip > 0 && l == skip - 1 ? H - 2 * F : H);
         n->W[l] = (double*)malloc(sizeof(double) * n->in[l] * n->out[l]);
         n->b[l] = (double*)malloc(sizeof(double) * n->out[l]);
         for (int i = 0; i < n->in[l] * n->out[l]; ++i) n->W[l][i] = *p++;
@@ -468,6 +475,8 @@ OR_API OrNif* or_nif_create(int F, int H, int L, const float* flat)
     for (int i = 0; i < 9; ++i) n->M[i] = *p++;
     return n;
 }
+
+OR_API OrNif* or_nif_create(int F, int H, int L, const float* flat) { return or_nif_create_skip(F, H, L, 0, flat); }
 
 OR_API void or_nif_destroy(OrNif* n)
 {
@@ -497,31 +506,37 @@ OR_API void or_nif_export(const OrNif* n, double* flat_out)
     for (int i = 0; i < 9; ++i) *p++ = n->M[i];
 }
 
-/* Forward for one input.  acts (optional) receives every layer's
-   post-activation vector: features (2F), then L hidden vectors (H), and pre
-   (optional) the pre-activation of each hidden layer; y = final linear
-   output (3), z = M y (3). */
-static void nif_forward_one(const OrNif* n, double u, double v, double* feat, double* hid /* L x H */,
-                            double* pre /* L x H */, double y[3], double z[3])
+/* Forward for one input.  xin receives every linear layer's input vector
+   (layer l at xin + l * XW, XW = max(2F, H)): the features for layer 0, the
+   previous hidden output otherwise, and for the layer after the skip layer
+   that output followed by the features.  pre (optional) receives each hidden
+   layer's pre-activation (layer l at pre + l * H); y = final linear output
+   (3), z = M y (3). */
+static int nif_xw(const OrNif* n) { return 2 * n->F > n->H ? 2 * n->F : n->H; }
+
+static void nif_forward_one(const OrNif* n, double u, double v, double* xin, double* pre, double y[3], double z[3])
 {
-    int F = n->F, H = n->H;
+    const int F = n->F, H = n->H, XW = nif_xw(n);
+    double* feat = xin;
     for (int i = 0; i < F; ++i) {
         double ph = n->B[2 * i] * u + n->B[2 * i + 1] * v;
         feat[i] = sin(2.0 * OR_PI * ph);
         feat[F + i] = cos(2.0 * OR_PI * ph);
     }
-    const double* x = feat;
     for (int l = 0; l < n->L; ++l) {
-        double* h = hid + (size_t)l * H;
-        for (int j = 0; j < H; ++j) {
+        const double* x = xin + (size_t)l * XW;
+        double* h = xin + (size_t)(l + 1) * XW;   /* the next layer's input */
+        for (int j = 0; j < n->out[l]; ++j) {
             double acc = n->b[l][j];
             for (int k = 0; k < n->in[l]; ++k) acc += n->W[l][(size_t)j * n->in[l] + k] * x[k];
             if (pre) pre[(size_t)l * H + j] = acc;
             h[j] = acc > 0.0 ? acc : 0.0;
         }
-        x = h;
+        if (n->skip > 0 && l == n->skip - 1)
+            for (int k = 0; k < 2 * F; ++k) h[n->out[l] + k] = feat[k];
     }
     int lo = n->nl - 1;
+    const double* x = xin + (size_t)n->L * XW;
     for (int j = 0; j < 3; ++j) {
         double acc = n->b[lo][j];
         for (int k = 0; k < H; ++k) acc += n->W[lo][(size_t)j * H + k] * x[k];
@@ -532,17 +547,16 @@ static void nif_forward_one(const OrNif* n, double u, double v, double* feat, do
 
 OR_API void or_nif_forward(const OrNif* n, int64_t cnt, const double* uv, double* rgb, double* z_out)
 {
-    double* feat = (double*)malloc(sizeof(double) * 2 * n->F);
-    double* hid = (double*)malloc(sizeof(double) * n->L * n->H);
+    double* xin = (double*)malloc(sizeof(double) * (size_t)(n->L + 1) * nif_xw(n));
     for (int64_t i = 0; i < cnt; ++i) {
         double y[3], z[3];
-        nif_forward_one(n, uv[2 * i], uv[2 * i + 1], feat, hid, NULL, y, z);
+        nif_forward_one(n, uv[2 * i], uv[2 * i + 1], xin, NULL, y, z);
         for (int c = 0; c < 3; ++c) {
             rgb[3 * i + c] = exp(z[c]);
             if (z_out) z_out[3 * i + c] = z[c];
         }
     }
-    free(feat); free(hid);
+    free(xin);
 }
 
 /* Huber loss (Section 3.2.1): 0.5 r^2 for |r| <= delta, else
@@ -564,22 +578,21 @@ static double huber_grad(double r, double delta)
 OR_API double or_nif_loss_grad(const OrNif* n, int64_t cnt, const double* uv, const double* target,
                                double delta, double* grad)
 {
-    int F = n->F, H = n->H, L = n->L;
+    int H = n->H, L = n->L, XW = nif_xw(n);
     int64_t nt = or_nif_n_trainable(n);
     memset(grad, 0, sizeof(double) * (size_t)nt);
     double* gW[9]; double* gb[9];
     double* p = grad;
     for (int l = 0; l < n->nl; ++l) { gW[l] = p; p += n->in[l] * n->out[l]; gb[l] = p; p += n->out[l]; }
-    double* feat = (double*)malloc(sizeof(double) * 2 * F);
-    double* hid = (double*)malloc(sizeof(double) * L * H);
+    double* xin = (double*)malloc(sizeof(double) * (size_t)(L + 1) * XW);
     double* pre = (double*)malloc(sizeof(double) * L * H);
-    double* dh = (double*)malloc(sizeof(double) * H);
-    double* dprev = (double*)malloc(sizeof(double) * H);
+    double* dh = (double*)malloc(sizeof(double) * XW);
+    double* dprev = (double*)malloc(sizeof(double) * XW);
     double loss = 0.0;
     double scale = 1.0 / (3.0 * (double)cnt);
     for (int64_t s = 0; s < cnt; ++s) {
         double y[3], z[3], dz[3], dy[3];
-        nif_forward_one(n, uv[2 * s], uv[2 * s + 1], feat, hid, pre, y, z);
+        nif_forward_one(n, uv[2 * s], uv[2 * s + 1], xin, pre, y, z);
         for (int c = 0; c < 3; ++c) {
             double r = z[c] - target[3 * s + c];
             loss += huber(r, delta) * scale;
@@ -588,37 +601,38 @@ OR_API double or_nif_loss_grad(const OrNif* n, int64_t cnt, const double* uv, co
         for (int j = 0; j < 3; ++j) dy[j] = n->M[j] * dz[0] + n->M[3 + j] * dz[1] + n->M[6 + j] * dz[2];
         /* output layer */
         int lo = n->nl - 1;
-        const double* xin = hid + (size_t)(L - 1) * H;
+        const double* x_out = xin + (size_t)L * XW;
         for (int j = 0; j < 3; ++j) {
             gb[lo][j] += dy[j];
-            for (int k = 0; k < H; ++k) gW[lo][(size_t)j * H + k] += dy[j] * xin[k];
+            for (int k = 0; k < H; ++k) gW[lo][(size_t)j * H + k] += dy[j] * x_out[k];
         }
         for (int k = 0; k < H; ++k) {
             double acc = 0.0;
             for (int j = 0; j < 3; ++j) acc += n->W[lo][(size_t)j * H + k] * dy[j];
             dh[k] = acc;
         }
-        /* hidden layers, last to first */
+        /* hidden layers, last to first; dh holds the gradient at layer l's output (its first out[l]
+           entries: at the skip layer the entries of the concatenated features are dropped, B is fixed) */
         for (int l = L - 1; l >= 0; --l) {
             const double* pl = pre + (size_t)l * H;
-            for (int j = 0; j < H; ++j) dh[j] = pl[j] > 0.0 ? dh[j] : 0.0;
-            const double* x = (l == 0) ? feat : hid + (size_t)(l - 1) * H;
-            int nin = n->in[l];
-            for (int j = 0; j < H; ++j) {
+            const int nout = n->out[l], nin = n->in[l];
+            for (int j = 0; j < nout; ++j) dh[j] = pl[j] > 0.0 ? dh[j] : 0.0;
+            const double* x = xin + (size_t)l * XW;
+            for (int j = 0; j < nout; ++j) {
                 gb[l][j] += dh[j];
                 for (int k = 0; k < nin; ++k) gW[l][(size_t)j * nin + k] += dh[j] * x[k];
             }
             if (l > 0) {
-                for (int k = 0; k < H; ++k) {
+                for (int k = 0; k < nin; ++k) {
                     double acc = 0.0;
-                    for (int j = 0; j < H; ++j) acc += n->W[l][(size_t)j * nin + k] * dh[j];
+                    for (int j = 0; j < nout; ++j) acc += n->W[l][(size_t)j * nin + k] * dh[j];
                     dprev[k] = acc;
                 }
-                memcpy(dh, dprev, sizeof(double) * H);
+                memcpy(dh, dprev, sizeof(double) * nin);
             }
         }
     }
-    free(feat); free(hid); free(pre); free(dh); free(dprev);
+    free(xin); free(pre); free(dh); free(dprev);
     return loss;
 }
 

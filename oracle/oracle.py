@@ -40,6 +40,8 @@ def lib():
         L.or_closest_hit.argtypes = [P, I64, P, P, C.c_int, P, P]
         L.or_nif_create.argtypes = [C.c_int, C.c_int, C.c_int, P]
         L.or_nif_create.restype = P
+        L.or_nif_create_skip.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P]
+        L.or_nif_create_skip.restype = P
         L.or_nif_destroy.argtypes = [P]
         L.or_nif_n_trainable.argtypes = [P]
         L.or_nif_n_trainable.restype = I64
@@ -131,7 +133,8 @@ class Nif:
     def __init__(self, nif):
         self.src = nif
         self.flat = nif_flat(nif)
-        self.h = lib().or_nif_create(nif.n_freq, nif.hidden, nif.n_hidden_layers, _ptr(self.flat))
+        self.h = lib().or_nif_create_skip(nif.n_freq, nif.hidden, nif.n_hidden_layers, int(nif.skip_after),
+                                          _ptr(self.flat))
         if not self.h:
             raise ValueError("unsupported NIF shape")
 

@@ -110,11 +110,14 @@ class RenderCfg:
 
 @dataclasses.dataclass
 class NIF:
-    """HDR neural image field parameters (float32, PyTorch Linear layout)."""
+    """HDR neural image field parameters (float32, PyTorch Linear layout).
+    skip_after = s >= 1: hidden layer s (1-based) has H - 2F outputs, and
+    hidden layer s + 1 takes them followed by the 2F Fourier features."""
     B: np.ndarray                 # [F, 2] Gaussian Fourier frequencies
     W: List[np.ndarray]           # per layer [out, in]
     b: List[np.ndarray]           # per layer [out]
     M: np.ndarray                 # [3, 3] fixed colour matrix applied before exp
+    skip_after: int = 0           # 0: plain MLP
 
     @property
     def n_freq(self) -> int:
@@ -122,14 +125,15 @@ class NIF:
 
     @property
     def hidden(self) -> int:
-        return int(self.W[0].shape[0])
+        return int(self.W[-1].shape[1])   # the head's input width (the first layer may be the narrowed one)
 
     @property
     def n_hidden_layers(self) -> int:
         return len(self.W) - 1
 
     def copy(self) -> "NIF":
-        return NIF(self.B.copy(), [w.copy() for w in self.W], [x.copy() for x in self.b], self.M.copy())
+        return NIF(self.B.copy(), [w.copy() for w in self.W], [x.copy() for x in self.b], self.M.copy(),
+                   self.skip_after)
 
 
 def _empty_scene_arrays():
@@ -339,16 +343,29 @@ YUV_TO_RGB_BT601 = np.array([[1.0, 0.0, 1.13983],
 YCOCG_TO_RGB = np.array([[1.0, 1.0, -1.0], [1.0, 0.0, 1.0], [1.0, -1.0, -1.0]], np.float32)
 
 
+def paper_skip_layer(n_hidden_layers: int) -> int:
+    """The 1-based hidden layer whose output the paper concatenates with the
+    Fourier features: the last odd layer (0-based) before the middle of the
+    network; 0 when there is none (fewer than three hidden layers)."""
+    odd = [i for i in range(n_hidden_layers) if i % 2 == 1 and i < n_hidden_layers / 2]
+    return odd[-1] + 1 if odd else 0
+
+
 def nif_init(n_freq: int = 64, hidden: int = 128, n_hidden_layers: int = 3, sigma: float = 10.0,
-             seed: int = 0, colour: str = "identity") -> NIF:
+             seed: int = 0, colour: str = "identity", skip_after: int = 0) -> NIF:
     """Random-init NIF: Fourier matrix entries N(0, sigma^2), weights
-    N(0, 1/fan_in), zero biases.  Layer widths: 2F -> H (x L) -> 3."""
+    N(0, 1/fan_in), zero biases.  Layer widths: 2F -> H (x L) -> 3; with
+    skip_after = s, hidden layer s has H - 2F outputs and layer s + 1 takes
+    them with the 2F features appended."""
     rng = _rng(seed, TAG_NIF_INIT)
     B = rng.normal(0.0, sigma, size=(n_freq, 2)).astype(np.float32)
+    assert 0 <= skip_after < n_hidden_layers and (skip_after == 0 or hidden > 2 * n_freq)
     dims = [2 * n_freq] + [hidden] * n_hidden_layers + [3]
     W, b = [], []
     for i in range(len(dims) - 1):
         fan_in, fan_out = dims[i], dims[i + 1]
+        if skip_after and i == skip_after - 1:
+            fan_out = hidden - 2 * n_freq
         W.append(rng.normal(0.0, 1.0 / math.sqrt(fan_in), size=(fan_out, fan_in)).astype(np.float32))
         b.append(np.zeros((fan_out,), np.float32))
     if colour == "identity":
@@ -357,7 +374,7 @@ def nif_init(n_freq: int = 64, hidden: int = 128, n_hidden_layers: int = 3, sigm
         M = YCOCG_TO_RGB.copy()
     else:
         M = YUV_TO_RGB_BT601.copy()
-    return NIF(B, W, b, M)
+    return NIF(B, W, b, M, skip_after)
 
 
 def procedural_sky(width: int = 2048, height: int = 1024, seed: int = 0) -> np.ndarray:

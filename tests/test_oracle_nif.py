@@ -174,3 +174,73 @@ def test_ycocg_head_inverts_the_forward_transform():
     back = ycocg @ I.YCOCG_TO_RGB.astype(np.float64).T
     assert np.allclose(back, rgb, atol=1e-12)
     assert np.array_equal(I.nif_init(colour="ycocg").M, I.YCOCG_TO_RGB)
+
+
+# ---------------------------------------------------------------------------
+# The paper's network shape: the Fourier features concatenated with the output
+# of the last odd hidden layer before the middle (Section 3.2), whose width is
+# reduced by 2F to keep the next layer's input at H.
+
+
+def test_paper_network_has_97_kib_of_fp16_weights():
+    """F = 20 (a 40-wide encoding), H = 128, four hidden ReLU layers and the
+    head, the features joined to the output of hidden layer 2 (0-based odd
+    layer 1, the last odd one before the middle): 50,011 parameters = 97.7 KiB
+    in FP16, the size the paper quotes for its H128 network."""
+    assert I.paper_skip_layer(4) == 2 and I.paper_skip_layer(5) == 2 and I.paper_skip_layer(8) == 4
+    assert I.paper_skip_layer(2) == 0
+    nif = I.nif_init(n_freq=20, hidden=128, n_hidden_layers=4, skip_after=I.paper_skip_layer(4))
+    assert [W.shape for W in nif.W] == [(128, 40), (88, 128), (128, 128), (128, 128), (3, 128)]
+    n = O.Nif(nif).n_trainable
+    assert n == 50011 and 97.0 <= 2 * n / 1024 < 98.0
+
+
+def test_skip_network_with_a_silent_skip_layer_is_the_shorter_plain_network():
+    """If hidden layer s outputs nothing (zero weights and biases), layer
+    s + 1 sees [0, features], so the network equals a plain network that
+    starts at layer s + 1 with the feature columns of its weights."""
+    F, H, L, s = 6, 32, 4, 2
+    nif = I.nif_init(n_freq=F, hidden=H, n_hidden_layers=L, skip_after=s, colour="yuv", seed=4)
+    rng = np.random.default_rng(4)
+    for b in nif.b:
+        b[:] = rng.normal(0, 0.1, b.shape)
+    nif.W[s - 1][:] = 0
+    nif.b[s - 1][:] = 0
+    short = I.NIF(nif.B.copy(), [nif.W[s][:, H - 2 * F:].copy()] + [W.copy() for W in nif.W[s + 1:]],
+                  [b.copy() for b in nif.b[s:]], nif.M.copy())
+    uv = rng.uniform(0, 1, (40, 2))
+    a, _ = O.Nif(nif).forward(uv)
+    b, _ = O.Nif(short).forward(uv)
+    assert np.allclose(a, b, rtol=1e-13, atol=0)
+
+
+def test_skip_network_passes_a_feature_around_the_skip_layer():
+    """relu(x) - relu(-x) = x through the concatenated features only: the
+    layers before the join are zero, layer s + 1 picks feature i from the
+    appended block, the layers after pass it on, and the head returns it."""
+    F, H, L, s = 4, 16, 3, 1
+    nif = _zero_like(I.nif_init(n_freq=F, hidden=H, n_hidden_layers=L, skip_after=s))
+    i = 3                                   # sin of frequency 3
+    col = (H - 2 * F) + i                   # its column in layer s + 1's input
+    nif.W[s][0, col], nif.W[s][1, col] = 1.0, -1.0
+    nif.W[s + 1][0, 0], nif.W[s + 1][1, 1] = 1.0, 1.0
+    nif.W[L][0, 0], nif.W[L][0, 1] = 1.0, -1.0
+    uv = np.random.default_rng(5).uniform(0, 1, (30, 2)).astype(np.float32).astype(np.float64)
+    _, z = O.Nif(nif).forward(uv)
+    B = nif.B.astype(np.float64)
+    want = np.sin(2 * math.pi * (B[i, 0] * uv[:, 0] + B[i, 1] * uv[:, 1]))
+    assert np.allclose(z[:, 0], want, atol=1e-12)
+
+
+@pytest.mark.parametrize("L,s", [(3, 1), (4, 2), (5, 3)])
+def test_skip_network_gradient_matches_central_differences(L, s):
+    nif = I.nif_init(n_freq=3, hidden=14, n_hidden_layers=L, skip_after=s, colour="yuv", seed=L)
+    rng = np.random.default_rng(L)
+    for b in nif.b:
+        b[:] = rng.normal(0, 0.1, b.shape)
+    uv = rng.uniform(0, 1, (6, 2))
+    target = rng.normal(0, 2, (6, 3))
+    n = O.Nif(nif).n_trainable
+    idx = list(range(0, n, max(1, n // 150))) + [n - 1, n - 4]
+    g = _fd_check(nif, uv, target, 10.0, idx)
+    assert np.abs(g).max() > 0
