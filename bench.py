@@ -58,13 +58,15 @@ OPS_NODE, OPS_SPHERE, OPS_QUAD, OPS_TRI = 58, 36, 12, 46
 # the traversal kernel (origin and direction in, hit out) and per ray-bounce of trace + shade queue traffic
 BYTES_NODE, BYTES_SPHERE, BYTES_QUAD, BYTES_TRI, BYTES_RAY_TRACE, BYTES_RAY = 48, 16, 32, 48, 40, 140
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes (read + write) of the traversal kernel per traced ray, from one ncu capture of a smaller frame of
-# the same workload (summaries and commands in profiles/), scaled to a frame by the rays it traces.  Valid only
+# DRAM bytes (read + write) of the traversal kernel per traced ray, from one ncu capture of the workload's frame
+# (or a smaller frame of it) (summaries and commands in profiles/), scaled to a frame by the rays it traces.  Valid only
 # while the traversal source is the one captured (sha256 of trace.cu + device_common.cuh, first 16 hex digits).
 TRACE_TRAFFIC = {
     # 1920x1080 at 8 spp = one full 2^24-path chunk of the 32-spp frame (profiles/k_trace_traffic_large_bvh_c4.md)
     ("C4", "packed"): {"bytes_per_ray": 365.1, "src": "7d34db8adafd2d1d"},
     ("C4", "quant8"): {"bytes_per_ray": 283.6, "src": "7d34db8adafd2d1d"},
+    # 512x512 at 64 spp, the full frame, one pass per launch (profiles/k_trace_traffic_spheres_c2.md)
+    ("C2", "decoded"): {"bytes_per_ray": 22.71, "src": "7d34db8adafd2d1d"},
 }
 NODE_FORMS = {1: "packed", 2: "decoded", 3: "quant8"}
 TRACE_SOURCES = ("paper_2305_20061_gb300/csrc/trace.cu", "paper_2305_20061_gb300/csrc/device_common.cuh")
@@ -901,7 +903,9 @@ def bench_nif_sweep(args):
     frame rate with that network as the environment.  The BF16 kernel keeps
     every weight in shared memory; it takes H = 128 with 1 to 5 hidden layers
     (three, two, then one 128-row tile slot beside the weights) and H = 64
-    or 32 with 1 to 8 (four slots), and no shape beyond.  One JSON line."""
+    or 32 with 1 to 8 (four slots), and no shape beyond.  The last row is
+    the paper's network (20 frequencies, four layers of 128, the features
+    joined after the second), on the FP32 kernels.  One JSON line."""
     import torch
     from paper_2305_20061_gb300 import build
     build.build()
@@ -928,16 +932,21 @@ def bench_nif_sweep(args):
         return e0.elapsed_time(e1) / reps
 
     rows = []
-    shapes = [(128, 1), (128, 2), (128, 3), (128, 4), (128, 5), (128, 6), (128, 8), (64, 2), (64, 3), (64, 4), (64, 8),
-              (32, 2), (32, 3), (32, 4), (32, 8)]
-    for H, L in shapes:
-        g = pt.Nif(ctx, I.nif_init(hidden=H, n_hidden_layers=L, colour="yuv"))
+    # (frequencies, width, hidden layers, skip layer); the last row is the paper's network: 20 frequencies,
+    # four layers of 128, the second layer's output joined with the features (Section 3.2)
+    shapes = [(64, H, L, 0) for H, L in ((128, 1), (128, 2), (128, 3), (128, 4), (128, 5), (128, 6), (128, 8),
+                                         (64, 2), (64, 3), (64, 4), (64, 8), (32, 2), (32, 3), (32, 4), (32, 8))]
+    shapes.append((20, 128, 4, I.paper_skip_layer(4)))
+    for F, H, L, S in shapes:
+        def make():
+            return pt.Nif(ctx, I.nif_init(n_freq=F, hidden=H, n_hidden_layers=L, colour="yuv", skip_after=S))
+        g = make()
         tprec = "bf16"
         try:
             g.train(sky, steps=1, batch=1024, lr=1e-3, seed=99, precision="bf16")
         except RuntimeError:   # the BF16 training chains need the weights resident in shared memory too
             tprec = "fp32"
-        g = pt.Nif(ctx, I.nif_init(hidden=H, n_hidden_layers=L, colour="yuv"))
+        g = make()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -945,10 +954,11 @@ def bench_nif_sweep(args):
         e1.record(stream)
         torch.cuda.synchronize()
         train_ms = e0.elapsed_time(e1)
-        row = {"hidden": H, "layers": L, "params": g.param_count, "weights_kb_bf16": (g.param_count * 2) // 1024,
+        row = {"n_freq": F, "hidden": H, "layers": L, "skip_after": S, "params": g.param_count,
+               "weights_kb_bf16": (g.param_count * 2) // 1024,
                "train_gemms": tprec, "train_ms_per_step": train_ms / steps, "quality": nif_quality(g, sky, dev)}
         row["fp32_evals_per_s"] = (1 << 24) / (ms_of(lambda: g.eval(uv, "fp32"), 2) * 1e-3)
-        bf16_ok = (H == 128 and 1 <= L <= 5) or (H in (64, 32) and 1 <= L <= 8)
+        bf16_ok = F == 64 and S == 0 and ((H == 128 and 1 <= L <= 5) or (H in (64, 32) and 1 <= L <= 8))
         if bf16_ok:
             row["bf16_evals_per_s"] = (1 << 24) / (ms_of(lambda: g.eval(uv, "bf16"), 3) * 1e-3)
             row["bf16_tile_slots"] = (3 if L <= 3 else (2 if L == 4 else 1)) if H == 128 else 4
@@ -956,7 +966,10 @@ def bench_nif_sweep(args):
             row["c2_bf16_msamples_s"] = cfg.n_slots / (fr * 1e-3) / 1e6
         else:
             row["bf16_evals_per_s"] = None
-            row["bf16_note"] = "not resident: the BF16 kernel needs H = 128 with L <= 5, or H = 64 / 32 with L <= 8"
+            row["bf16_note"] = ("no BF16 kernel for the skip-joined network" if S else
+                                "not resident: the BF16 kernel needs H = 128 with L <= 5, or H = 64 / 32 with L <= 8")
+            fr = ms_of(lambda: pt.render(ctx, scene, g, cfg, "fp32", out=img), 3)
+            row["c2_fp32_msamples_s"] = cfg.n_slots / (fr * 1e-3) / 1e6
         ctx.check()
         rows.append(row)
         del g
@@ -966,6 +979,69 @@ def bench_nif_sweep(args):
                                  "training": "Adam lr 1e-3, batch 2^16, BF16 tensor-core GEMMs where the shape "
                                              "fits (else FP32)"},
                       "rows": rows}))
+    return 0
+
+
+def bench_nif_eval(args):
+    """Standalone NIF evaluation (the network of Section 3.2 that the renderer
+    evaluates for its escaped rays), one kernel: 2^n uniform (u, v) through
+    the --precision kernel, W untimed launches then K launches timed one by
+    one with CUDA events, a 512 MB L2 flush between them (outside the events).
+    The shape is the renderer's (F = 64, 3 x FC-128).  One JSON line with the
+    evaluation rate and the kernel's roofline."""
+    import torch
+    from paper_2305_20061_gb300 import build
+    build.build()
+    from paper_2305_20061_gb300 import pt
+    dev = "cuda:0"
+    ctx = pt.Context(0)
+    stream = torch.cuda.current_stream()
+    n = 1 << args.nif_eval
+    g = pt.Nif(ctx, I.nif_init(colour="yuv"))
+    uv = torch.from_numpy(I.uniform_uv(n, seed=1)).to(dev)
+    flush = torch.empty(128 << 20, dtype=torch.float32, device=dev)
+    prec = args.precision
+    for _ in range(max(args.warmup, 3)):
+        g.eval(uv, prec)
+    torch.cuda.synchronize()
+    ctx.check()
+    sampler = ClockSampler(0)
+    sampler.start()
+    times = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.eval(uv, prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    ctx.check()
+    ms = float(np.mean(times))
+    meas, which = peaks()
+    if prec == "fp32":
+        flop = FLOP_PER_EVAL
+        peak = pt.ffma_rate_tflops(0)
+        bound, kernel, note = "alu", "k_nif_fp32", "FP32 FMA rate measured live by pt_microbench_ffma"
+    else:
+        flop = TC_FLOP_PER_EVAL
+        peak = float(meas["bf16_tflops"]) * (2.0 if prec == "fp8" else 1.0)
+        bound, kernel = "tensor", ("k_nif_tc" if prec == "bf16" else "k_nif_fp8")
+        note = (f"dense BF16 cuBLAS burst ({which})" if prec == "bf16" else
+                f"dense FP8 = BF16 cuBLAS burst ({which}) x 2 (nominal 4.5 / 2.25 PFLOP/s)")
+    achieved = n * flop / (ms * 1e-3) / 1e12
+    print(json.dumps({"metric": "NIF evaluations per second (standalone)", "value": n / (ms * 1e-3), "unit": "evals/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+                      "ms_min": float(np.min(times)), "higher_is_better": True, "dtype": prec, "data": "synthetic",
+                      "config": {"workload": f"2^{args.nif_eval} uniform (u, v), F=64 Fourier (sigma 10) -> 3x FC-128 "
+                                             f"ReLU -> FC-3 -> colour matrix -> exp, random-init weights",
+                                 "l2": "512 MB flush between timed launches"},
+                      "roofline": {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak,
+                                   "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                                   "per_unit": f"{flop} FLOP per evaluation x {n} evaluations per launch",
+                                   "peak_note": note},
+                      "clocks": clocks, "gpu_launches": args.steps}))
     return 0
 
 
@@ -1025,11 +1101,15 @@ def main():
     ap.add_argument("--no-bias", action="store_true", help="C5: skip the bias measurement against the 4096-spp render")
     ap.add_argument("--nif-sweep", action="store_true",
                     help="NIF size sweep (hidden width and depth vs quality, evaluation and path rate); one JSON line")
+    ap.add_argument("--nif-eval", type=int, default=None, metavar="LOG2N",
+                    help="standalone NIF evaluation of 2^LOG2N coordinates in --precision; one JSON line")
     ap.add_argument("--colour-sweep", action="store_true",
                     help="NIF colour-space study (RGB / YUV / YCoCg heads); one JSON line")
     args = ap.parse_args()
     if args.nif_sweep:
         return bench_nif_sweep(args)
+    if args.nif_eval is not None:
+        return bench_nif_eval(args)
     if args.colour_sweep:
         return bench_colour_sweep(args)
     if args.impl == "reference":

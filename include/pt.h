@@ -208,6 +208,10 @@ typedef struct pt_nif_desc {
     int32_t hidden;            /* H */
     int32_t n_hidden_layers;   /* L (1..8) */
     const float* params;       /* host, flat: B[F][2], then per layer W[out][in], b[out], then M[3][3] */
+    int32_t skip_after;        /* 0: plain MLP.  s in [1, L - 1] (needs H > 2F): hidden layer s has H - 2F
+                                  outputs and hidden layer s + 1 takes them followed by the 2F Fourier
+                                  features (the paper's network: F = 20, H = 128, L = 4, s = 2, Section
+                                  3.2).  Evaluated on the FP32 path and trained with FP32 GEMMs. */
 } pt_nif_desc;
 
 /* Upload FP32 master weights and build the BF16 operand image of the
@@ -525,7 +529,8 @@ PT_API pt_status pt_render_noalloc(const pt_scene* scene, const pt_nif* nif, con
 /*   bytes  0-7   magic "PTCKPT01"                                           */
 /*          8-11  uint32 kind: 1 = NIF, 2 = radiance cache                   */
 /*         12-15  uint32 version (1)                                         */
-/*         16-31  int32 dims[4]: NIF (n_freq, hidden, n_hidden_layers, 0),   */
+/*         16-31  int32 dims[4]: NIF (n_freq, hidden, n_hidden_layers,       */
+/*                skip_after),                                               */
 /*                cache (n_freq, hidden, n_hidden_layers, 0)                 */
 /*         32-55  float box[6]: cache lo[3], hi[3]; zeros for a NIF          */
 /*         56-63  int64 n_params (the flat FP32 layout of pt_nif_desc /      */

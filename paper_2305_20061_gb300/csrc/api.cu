@@ -76,6 +76,7 @@ struct pt_nif {
     uint64_t uid = g_next_uid++;
     uint64_t version = 0;        // bumped when host-side copies (colour matrix) change
     int32_t F = 0, H = 0, L = 0;
+    int32_t skip = 0;             // hidden layer joined with the features (1-based), 0: none
     int64_t n_params = 0;
     unsigned char* d_arena = nullptr;   // one allocation holding d_params, d_fp32 and d_tc
     float* d_params = nullptr;   // flat FP32 master weights
@@ -321,7 +322,7 @@ pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, int ac
         PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_fp8(nif->d_fp8, p, 1, ctx->sm_count, s); }));
         return PT_OK;
     }
-    return fail(ctx, PT_EUNSUPPORTED, "the BF16 NIF needs F = 64, H = 128, 1 <= L <= 5 (FP8: L = 3)");
+    return fail(ctx, PT_EUNSUPPORTED, "the BF16 NIF needs F = 64, H = 128, 1 <= L <= 5 and no skip layer (FP8: L = 3)");
 }
 
 }  // namespace
@@ -680,12 +681,15 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
 {
     if (!ctx || !d || !out || !d->params) return fail(ctx, PT_EINVAL, "null argument");
     *out = nullptr;
-    const int F = d->n_freq, H = d->hidden, L = d->n_hidden_layers;
+    const int F = d->n_freq, H = d->hidden, L = d->n_hidden_layers, S = d->skip_after;
     if (F < 1 || 2 * F > 128 || H < 1 || H > 128 || L < 1 || L > 8)
         return fail(ctx, PT_EUNSUPPORTED, "NIF shape outside 2F <= 128, H <= 128, 1 <= L <= 8");
+    if (S < 0 || S >= L || (S > 0 && H <= 2 * F))
+        return fail(ctx, PT_EINVAL, "skip_after must be 0 or in [1, L - 1] with H > 2F");
     int64_t n = 2 * F;
     for (int l = 0; l <= L; ++l) {
-        const int in = l == 0 ? 2 * F : H, o = l == L ? 3 : H;
+        int in, o;
+        nif_layer_dims(F, H, L, S, l, &in, &o);
         n += (int64_t)in * o + o;
     }
     n += 9;
@@ -701,7 +705,8 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
     const float* p = d->params;
     for (int i = 0; i < 2 * F; ++i) Bc[i] = *p++;
     for (int l = 0; l <= L; ++l) {
-        const int in = l == 0 ? 2 * F : H, o = l == L ? 3 : H;
+        int in, o;
+        nif_layer_dims(F, H, L, S, l, &in, &o);
         if (l < L) {
             for (int j = 0; j < o; ++j)
                 for (int k = 0; k < in; ++k) Wt[(size_t)l * 128 * 128 + (size_t)k * 128 + j] = p[(size_t)j * in + k];
@@ -718,9 +723,9 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
     }
     pt_nif* nf = new pt_nif();
     nf->ctx = ctx;
-    nf->F = F; nf->H = H; nf->L = L; nf->n_params = n;
+    nf->F = F; nf->H = H; nf->L = L; nf->skip = S; nf->n_params = n;
     std::vector<unsigned char> img;
-    const bool tc = pack_nif_tc_image(d->params, F, H, L, img);
+    const bool tc = S == 0 && pack_nif_tc_image(d->params, F, H, L, img);
     // one allocation and one copy: master weights | FP32 layout | tensor-core image
     const size_t b_params = ((size_t)n * sizeof(float) + 255) & ~(size_t)255;
     const size_t b_fp32 = (fp32_floats * sizeof(float) + 255) & ~(size_t)255;
@@ -744,14 +749,14 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
         }
     }
     DevNif& v = nf->dev;
-    v.F = F; v.H = H; v.L = L;
+    v.F = F; v.H = H; v.L = L; v.skip = S;
     v.Wt = nf->d_fp32;
     v.bias = nf->d_fp32 + (size_t)L * 128 * 128;
     v.Wout = v.bias + (size_t)L * 128;
     v.bout = v.Wout + 3 * 128;
     v.B = v.bout + 3;
     for (int i = 0; i < 9; ++i) v.M[i] = d->params[n - 9 + i];
-    nf->fp8_ok = F == 64 && H == 128 && L == 3;
+    nf->fp8_ok = F == 64 && H == 128 && L == 3 && S == 0;
     *out = nf;
     return PT_OK;
 }
@@ -807,7 +812,7 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
         return PT_OK;
     }
     if (precision == PT_BF16 || precision == PT_FP8E4M3)
-        return fail(ctx, PT_EUNSUPPORTED, "the BF16 NIF needs F = 64, H = 128, 1 <= L <= 5 (FP8: L = 3)");
+        return fail(ctx, PT_EUNSUPPORTED, "the BF16 NIF needs F = 64, H = 128, 1 <= L <= 5 and no skip layer (FP8: L = 3)");
     return fail(ctx, PT_EINVAL, "unknown precision");
 }
 
@@ -816,10 +821,11 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
 namespace {
 
 // training GEMM precision: PT_FP32, or PT_BF16 where the tensor-core kernels take the shape
-pt_status check_train_precision(pt_ctx* ctx, int L, int H, int in0, int32_t precision)
+pt_status check_train_precision(pt_ctx* ctx, int L, int H, int in0, int32_t precision, int skip = 0)
 {
     if (precision == PT_FP32) return PT_OK;
     if (precision != PT_BF16) return fail(ctx, PT_EINVAL, "training precision is PT_FP32 or PT_BF16");
+    if (skip > 0) return fail(ctx, PT_EUNSUPPORTED, "the skip-concatenated NIF trains with FP32 GEMMs");
     TrainNet t = {};
     t.L = L;
     t.H = H;
@@ -836,12 +842,16 @@ TrainNet make_train_net(pt_nif* nf)
     TrainNet t = {};
     t.F = nf->F; t.H = nf->H; t.L = nf->L;
     t.in0 = 2 * nf->F;
+    t.skip = nf->skip;
     const float* p = nf->d_params;
     float* g = nf->d_grad;
     t.B = p;
     p += 2 * nf->F;
     for (int l = 0; l <= nf->L; ++l) {
-        const int in = l == 0 ? 2 * nf->F : nf->H, o = l == nf->L ? 3 : nf->H;
+        int in, o;
+        nif_layer_dims(nf->F, nf->H, nf->L, nf->skip, l, &in, &o);
+        t.in[l] = in;
+        t.out[l] = o;
         t.W[l] = p; t.gW[l] = g;
         p += (size_t)in * o; g += (size_t)in * o;
         t.b[l] = p; t.gb[l] = g;
@@ -903,7 +913,7 @@ pt_status ensure_train(pt_ctx* ctx, pt_nif* nf, int64_t B)
 // FP32 packed layout and tensor-core image follow the master weights
 pt_status refresh_layouts(pt_ctx* ctx, pt_nif* nf, cudaStream_t s)
 {
-    PT_CUDA(repack_nif_fp32(nf->d_params, nf->F, nf->H, nf->L, nf->d_fp32, s));
+    PT_CUDA(repack_nif_fp32(nf->d_params, nf->F, nf->H, nf->L, nf->skip, nf->d_fp32, s));
     if (nf->d_tc) PT_CUDA(repack_nif_tc_image(nf->d_params, nf->H, nf->L, nf->d_tc, s));
     nf->fp8_stale = true;   // rebuilt on its next use
     return PT_OK;
@@ -915,7 +925,7 @@ PT_API pt_status pt_nif_loss_grad(pt_ctx* ctx, pt_nif* nf, int64_t n, const floa
                                   float delta, int32_t precision, float* d_grad, double* d_loss, void* stream)
 {
     if (!ctx || !nf || n < 1 || !d_uv || !d_target || !(delta > 0.f)) return fail(ctx, PT_EINVAL, "bad argument");
-    pt_status st = check_train_precision(ctx, nf->L, nf->H, 2 * nf->F, precision);
+    pt_status st = check_train_precision(ctx, nf->L, nf->H, 2 * nf->F, precision, nf->skip);
     if (st != PT_OK) return st;
     st = ensure_train(ctx, nf, n);
     if (st != PT_OK) return st;
@@ -937,7 +947,7 @@ PT_API pt_status pt_train_nif(pt_ctx* ctx, pt_nif* nf, const float* d_sky, int32
     if (cfg->steps < 0 || cfg->batch < 1 || !(cfg->lr > 0.f) || !(cfg->huber_delta > 0.f) || !(cfg->beta1 >= 0.f) ||
         !(cfg->beta1 < 1.f) || !(cfg->beta2 >= 0.f) || !(cfg->beta2 < 1.f) || !(cfg->eps > 0.f))
         return fail(ctx, PT_EINVAL, "bad training configuration");
-    pt_status st = check_train_precision(ctx, nf->L, nf->H, 2 * nf->F, cfg->precision);
+    pt_status st = check_train_precision(ctx, nf->L, nf->H, 2 * nf->F, cfg->precision, nf->skip);
     if (st != PT_OK) return st;
     st = ensure_train(ctx, nf, cfg->batch);
     if (st != PT_OK) return st;
@@ -1005,6 +1015,8 @@ TrainNet make_cache_net(pt_cache* c)
     float* g = c->d_grad;
     for (int l = 0; l <= c->L; ++l) {
         const int in = l == 0 ? c->in0 : c->H, o = l == c->L ? 3 : c->H;
+        t.in[l] = in;
+        t.out[l] = o;
         t.W[l] = p; t.gW[l] = g;
         p += (size_t)in * o; g += (size_t)in * o;
         t.b[l] = p; t.gb[l] = g;
@@ -1399,7 +1411,7 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
     if (n_slots > 0xFFFFFFFFll) return fail(ctx, PT_EINVAL, "more than 2^32 - 1 paths in one call");
     if (sc->dev.env_is_nif && cfg->precision != PT_FP32 && !(cfg->precision == PT_BF16 && nf->d_tc) &&
         !(cfg->precision == PT_FP8E4M3 && nf->fp8_ok))
-        return fail(ctx, PT_EUNSUPPORTED, "the BF16 NIF needs F = 64, H = 128, 1 <= L <= 5 (FP8: L = 3)");
+        return fail(ctx, PT_EUNSUPPORTED, "the BF16 NIF needs F = 64, H = 128, 1 <= L <= 5 and no skip layer (FP8: L = 3)");
     // chunk = whole samples
     int64_t chunk = cfg->chunk_slots > 0 ? cfg->chunk_slots : (int64_t)1 << 24;
     chunk = std::max<int64_t>(n_pix, (chunk / n_pix) * n_pix);
@@ -1765,6 +1777,7 @@ PT_API pt_status pt_save_nif(pt_ctx* ctx, const pt_nif* nf, const char* path, vo
     hd.dims[0] = nf->F;
     hd.dims[1] = nf->H;
     hd.dims[2] = nf->L;
+    hd.dims[3] = nf->skip;
     hd.n_params = nf->n_params;
     hd.n_adam = nf->d_m ? nf->n_trainable : 0;
     hd.adam_t = nf->adam_t;
@@ -1790,16 +1803,18 @@ PT_API pt_status pt_load_nif_file(pt_ctx* ctx, const char* path, pt_nif** out)
     d.n_freq = hd.dims[0];
     d.hidden = hd.dims[1];
     d.n_hidden_layers = hd.dims[2];
+    d.skip_after = hd.dims[3];
     d.params = P.data();
     // the parameter count implied by the dimensions must be the file's before anything reads P
     {
-        const int64_t F = d.n_freq, H = d.hidden, L = d.n_hidden_layers;
-        if (F < 1 || F > 64 || H < 1 || H > 128 || L < 1 || L > 8)
+        const int F = d.n_freq, H = d.hidden, L = d.n_hidden_layers, S = d.skip_after;
+        if (F < 1 || F > 64 || H < 1 || H > 128 || L < 1 || L > 8 || S < 0 || S >= L || (S > 0 && H <= 2 * F))
             return fail(ctx, PT_EIO, "checkpoint dimensions out of range");
-        int64_t n = 2 * F + 9;
-        for (int64_t l = 0; l <= L; ++l) {
-            const int64_t in = l == 0 ? 2 * F : H, o = l == L ? 3 : H;
-            n += in * o + o;
+        int64_t n = 2 * (int64_t)F + 9;
+        for (int l = 0; l <= L; ++l) {
+            int in, o;
+            nif_layer_dims(F, H, L, S, l, &in, &o);
+            n += (int64_t)in * o + o;
         }
         if (n != hd.n_params || (hd.n_adam && hd.n_adam != n - 2 * F - 9))
             return fail(ctx, PT_EIO, "checkpoint sizes do not match its dimensions");

@@ -101,6 +101,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_fp32(const NifEvalParams p,
             }
             if (l + 1 < nf.L) stage_weights(Ws, nf.Wt + (size_t)(l + 1) * kDim * kDim);
             __syncthreads();
+            if (nf.skip > 0 && l == nf.skip - 1) {
+                // the skip layer's H - 2F outputs are followed by the Fourier features (Section 3.2)
+                const int base = nf.H - 2 * nf.F;
+                for (int i = 0; i < nf.F; ++i) {
+                    float sv, cv;
+                    fourier_feature(__ldg(&nf.B[2 * i]), __ldg(&nf.B[2 * i + 1]), u, v, sv, cv);
+                    hs[(base + i) * kRows + tid] = sv;
+                    hs[(base + nf.F + i) * kRows + tid] = cv;
+                }
+                __syncthreads();
+            }
         }
 
         // ---- output layer, colour matrix, exp (row `tid`) ----
@@ -147,35 +158,43 @@ namespace ptk {
 namespace {
 // Flat master weights -> packed FP32 layout of k_nif_fp32:
 // [L][128][128] transposed hidden weights, [L][128] biases, [3][128] output
-// weights, [3] output bias, [2F] frequencies (zero padding elsewhere).
-__global__ void k_repack_fp32(const float* __restrict__ params, int F, int H, int L, float* __restrict__ packed)
+// weights, [3] output bias, [2F] frequencies (zero padding elsewhere, also
+// beyond the skip layer's H - 2F outputs).
+__global__ void k_repack_fp32(const float* __restrict__ params, int F, int H, int L, int skip, float* __restrict__ packed)
 {
     float* Wt = packed;
     float* bias = Wt + (size_t)L * 128 * 128;
     float* Wout = bias + (size_t)L * 128;
     float* bout = Wout + 3 * 128;
     float* Bc = bout + 3;
+    // offset of linear layer l's weights in the flat layout
+    auto layer_off = [&](int l) {
+        size_t off = 2 * (size_t)F;
+        for (int q = 0; q < l; ++q) {
+            int in, out;
+            nif_layer_dims(F, H, L, skip, q, &in, &out);
+            off += (size_t)in * out + out;
+        }
+        return off;
+    };
     const size_t total = (size_t)L * 128 * 128 + (size_t)L * 128 + 3 * 128 + 3 + 2 * F;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
         float val = 0.f;
         if (idx < (size_t)L * 128 * 128) {
             const int l = (int)(idx / (128 * 128)), k = (int)((idx / 128) % 128), j = (int)(idx % 128);
-            const int in = l == 0 ? 2 * F : H;
-            size_t off = 2 * (size_t)F;
-            for (int q = 0; q < l; ++q) off += (size_t)(q == 0 ? 2 * F : H) * H + H;
-            if (j < H && k < in) val = params[off + (size_t)j * in + k];
+            int in, out;
+            nif_layer_dims(F, H, L, skip, l, &in, &out);
+            if (j < out && k < in) val = params[layer_off(l) + (size_t)j * in + k];
             Wt[idx] = val;
         } else if (idx < (size_t)L * 128 * 128 + (size_t)L * 128) {
             const size_t r = idx - (size_t)L * 128 * 128;
             const int l = (int)(r / 128), j = (int)(r % 128);
-            const int in = l == 0 ? 2 * F : H;
-            size_t off = 2 * (size_t)F;
-            for (int q = 0; q < l; ++q) off += (size_t)(q == 0 ? 2 * F : H) * H + H;
-            if (j < H) val = params[off + (size_t)in * H + j];
+            int in, out;
+            nif_layer_dims(F, H, L, skip, l, &in, &out);
+            if (j < out) val = params[layer_off(l) + (size_t)in * out + j];
             bias[r] = val;
         } else {
-            size_t off = 2 * (size_t)F;
-            for (int q = 0; q < L; ++q) off += (size_t)(q == 0 ? 2 * F : H) * H + H;
+            const size_t off = layer_off(L);
             const size_t r = idx - (size_t)L * 128 * 128 - (size_t)L * 128;
             if (r < 3 * 128) {
                 const int c = (int)(r / 128), k = (int)(r % 128);
@@ -191,9 +210,9 @@ __global__ void k_repack_fp32(const float* __restrict__ params, int F, int H, in
 }
 }  // namespace
 
-cudaError_t repack_nif_fp32(const float* params, int F, int H, int L, float* packed, cudaStream_t s)
+cudaError_t repack_nif_fp32(const float* params, int F, int H, int L, int skip, float* packed, cudaStream_t s)
 {
-    k_repack_fp32<<<256, 256, 0, s>>>(params, F, H, L, packed); count_launch();
+    k_repack_fp32<<<256, 256, 0, s>>>(params, F, H, L, skip, packed); count_launch();
     return cudaGetLastError();
 }
 }  // namespace ptk

@@ -143,8 +143,23 @@ struct BounceParams {
 };
 
 // NIF parameters on the device.
+// Widths of linear layer l (0 .. L, L = the head) of a NIF with F frequencies, width H, L hidden layers and
+// skip layer `skip` (0: none; s >= 1: hidden layer s has H - 2F outputs and layer s + 1 takes them with the
+// 2F Fourier features appended, Section 3.2).
+#ifdef __CUDACC__
+#define PT_HOST_DEVICE __host__ __device__
+#else
+#define PT_HOST_DEVICE
+#endif
+PT_HOST_DEVICE inline void nif_layer_dims(int F, int H, int L, int skip, int l, int* in, int* out)
+{
+    *in = l == 0 ? 2 * F : H;
+    *out = l == L ? 3 : (skip > 0 && l == skip - 1 ? H - 2 * F : H);
+}
+
 struct DevNif {
     int32_t F, H, L;         // frequencies, hidden width, hidden layers
+    int32_t skip;            // 0, or the hidden layer whose output is joined with the features (1-based)
     const float* B;          // [F][2]
     // FP32 path: each linear layer padded to 128 x 128 and stored transposed
     // ([in][out]); the output layer is stored [3][H] untransposed
@@ -209,6 +224,8 @@ cudaError_t launch_nif_fp8(const unsigned char* image, const NifEvalParams& p, i
 struct TrainNet {
     int32_t F, H, L;
     int32_t in0;                    // width of layer 0's input (2F for the NIF, 6J + 6 for the cache)
+    int32_t skip;                   // NIF skip layer (1-based) or 0; its output is joined with the features
+    int32_t in[9], out[9];          // widths of each linear layer
     const float* B;                 // [F][2]
     const float* W[9];              // per linear layer, [out][in]
     const float* b[9];
@@ -279,7 +296,7 @@ cudaError_t cache_query_tc(const unsigned char* image, CacheBox box, int64_t cap
                            const float* rows, float* slot_L, int accumulate, uint32_t* err, unsigned long long* stats,
                            int sm_count, cudaStream_t s);
 // rebuild the packed FP32 layout and (when present) the tensor-core image from the master weights
-cudaError_t repack_nif_fp32(const float* params, int F, int H, int L, float* packed, cudaStream_t s);
+cudaError_t repack_nif_fp32(const float* params, int F, int H, int L, int skip, float* packed, cudaStream_t s);
 cudaError_t repack_nif_tc_image(const float* params, int H, int L, unsigned char* image, cudaStream_t s);
 
 // read-only views of the C-ABI handles (api.cu)

@@ -590,6 +590,16 @@ int layer_bwd_dw(const TrainWork& wk, int64_t B, const float* dXout, const float
     return G;
 }
 
+// dst[:, d0 + c] = src[:, s0 + c] for c < n (rows [B][128])
+__global__ void k_copy_columns(int64_t B, const float* __restrict__ src, int s0, float* __restrict__ dst, int d0, int n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < B * n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / n;
+        const int c = (int)(i - r * n);
+        dst[r * kD + d0 + c] = src[r * kD + s0 + c];
+    }
+}
+
 }  // namespace
 
 namespace {
@@ -666,22 +676,27 @@ cudaError_t mlp_loss_grad(const TrainNet& net, int64_t B, const float* target, f
     }
     // forward through the hidden layers
     for (int l = 0; l < net.L; ++l) {
-        const int in = l == 0 ? net.in0 : net.H;
-        layer_fwd(wk, B, wk.X[l], wk.X[l + 1], net.W[l], net.b[l], in, net.H, s);
+        layer_fwd(wk, B, wk.X[l], wk.X[l + 1], net.W[l], net.b[l], net.in[l], net.out[l], s);
+        if (net.skip > 0 && l == net.skip - 1) {
+            // the skip layer's outputs are followed by the Fourier features (Section 3.2)
+            k_copy_columns<<<(unsigned)std::min<int64_t>((B * net.in0 + 255) / 256, 152 * 32), 256, 0, s>>>(
+                B, wk.X[0], 0, wk.X[l + 1], net.out[l], net.in0); count_launch();
+        }
     }
     // head + loss
     e = head_loss(net, B, target, delta, mode, mask, wk, wk.dX[0], loss_d, loss_f, 0, s);
     if (e != cudaSuccess) return e;
     // backward through the hidden layers
     int cur = 0;
+    // (at the layer after the skip layer the input gradient's feature columns are computed and not used)
     for (int l = net.L - 1; l >= 0; --l) {
-        const int in = l == 0 ? net.in0 : net.H;
+        const int in = net.in[l], out = net.out[l];
         int MT = 0, NT = 0;
-        const int Gw = layer_bwd_dw(wk, B, wk.dX[cur], wk.X[l], wk.partial, in, net.H, &MT, &NT, s);
-        k_sum_partials<<<(in * net.H + net.H + 31) / 32, 256, 0, s>>>(wk.partial, Gw, MT * NT + MT, NT, MT * NT, in,
-                                                                       net.H, net.gW[l], net.gb[l]); count_launch();
+        const int Gw = layer_bwd_dw(wk, B, wk.dX[cur], wk.X[l], wk.partial, in, out, &MT, &NT, s);
+        k_sum_partials<<<(in * out + out + 31) / 32, 256, 0, s>>>(wk.partial, Gw, MT * NT + MT, NT, MT * NT, in,
+                                                                  out, net.gW[l], net.gb[l]); count_launch();
         if (l > 0) {
-            layer_bwd_dx(wk, B, wk.dX[cur], wk.X[l], wk.dX[cur ^ 1], net.W[l], in, net.H, s);
+            layer_bwd_dx(wk, B, wk.dX[cur], wk.X[l], wk.dX[cur ^ 1], net.W[l], in, out, s);
             cur ^= 1;
         }
     }

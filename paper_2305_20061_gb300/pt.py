@@ -47,7 +47,7 @@ class SceneInfo(C.Structure):
 
 
 class NifDesc(C.Structure):
-    _fields_ = [("n_freq", I32), ("hidden", I32), ("n_hidden_layers", I32), ("params", P)]
+    _fields_ = [("n_freq", I32), ("hidden", I32), ("n_hidden_layers", I32), ("params", P), ("skip_after", I32)]
 
 
 class RenderCfg(C.Structure):
@@ -264,19 +264,19 @@ def nif_flat(nif: I.NIF) -> np.ndarray:
     return np.ascontiguousarray(np.concatenate(parts).astype(np.float32))
 
 
-def nif_from_flat(F: int, H: int, L: int, flat: np.ndarray) -> I.NIF:
-    """Inverse of nif_flat for a NIF of n_freq F, hidden width H and L hidden layers."""
+def nif_from_flat(F: int, H: int, L: int, flat: np.ndarray, skip_after: int = 0) -> I.NIF:
+    """Inverse of nif_flat for a NIF of n_freq F, hidden width H, L hidden layers and skip layer skip_after."""
     p = 0
     B = flat[p:p + 2 * F].reshape(F, 2).copy()
     p += 2 * F
     Ws, bs = [], []
     for l in range(L + 1):
-        i, o = (2 * F if l == 0 else H), (3 if l == L else H)
+        i, o = (2 * F if l == 0 else H), (3 if l == L else (H - 2 * F if skip_after and l == skip_after - 1 else H))
         Ws.append(flat[p:p + i * o].reshape(o, i).copy())
         p += i * o
         bs.append(flat[p:p + o].copy())
         p += o
-    return I.NIF(B, Ws, bs, flat[p:p + 9].reshape(3, 3).copy())
+    return I.NIF(B, Ws, bs, flat[p:p + 9].reshape(3, 3).copy(), int(skip_after))
 
 
 def checkpoint_info(path: str) -> dict:
@@ -297,7 +297,7 @@ class Nif:
         self.ctx = ctx
         self.src = nif
         flat = nif_flat(nif)
-        d = NifDesc(nif.n_freq, nif.hidden, nif.n_hidden_layers, _np_ptr(flat))
+        d = NifDesc(nif.n_freq, nif.hidden, nif.n_hidden_layers, _np_ptr(flat), int(nif.skip_after))
         self.h = P()
         ctx._raise(lib().pt_load_nif(ctx.h, C.byref(d), C.byref(self.h)))
 
@@ -308,8 +308,8 @@ class Nif:
         self.ctx = ctx
         self.h = P()
         ctx._raise(lib().pt_load_nif_file(ctx.h, os.fsencode(path), C.byref(self.h)))
-        F, H, L = checkpoint_info(path)["dims"][:3]
-        self.src = nif_from_flat(F, H, L, self.get_params())
+        F, H, L, S = checkpoint_info(path)["dims"][:4]
+        self.src = nif_from_flat(F, H, L, self.get_params(), S)
         return self
 
     def save(self, path: str, stream=None) -> None:
