@@ -903,9 +903,12 @@ def bench_nif_sweep(args):
     frame rate with that network as the environment.  The BF16 kernel keeps
     every weight in shared memory; it takes H = 128 with 1 to 5 hidden layers
     (three, two, then one 128-row tile slot beside the weights) and H = 64
-    or 32 with 1 to 8 (four slots), and no shape beyond.  The last row is
-    the paper's network (20 frequencies, four layers of 128, the features
-    joined after the second), on the FP32 kernels.  One JSON line."""
+    or 32 with 1 to 8 (four slots), H = 256 with one (two 64 KB slots),
+    and no shape beyond.  Networks wider than 128 are not trained (the
+    training chains are 128 wide): their rows give the rates of the
+    random-init network.  The last row is the paper's network (20
+    frequencies, four layers of 128, the features joined after the second).
+    One JSON line."""
     import torch
     from paper_2305_20061_gb300 import build
     build.build()
@@ -935,39 +938,46 @@ def bench_nif_sweep(args):
     # (frequencies, width, hidden layers, skip layer); the last row is the paper's network: 20 frequencies,
     # four layers of 128, the second layer's output joined with the features (Section 3.2)
     shapes = [(64, H, L, 0) for H, L in ((128, 1), (128, 2), (128, 3), (128, 4), (128, 5), (128, 6), (128, 8),
-                                         (64, 2), (64, 3), (64, 4), (64, 8), (32, 2), (32, 3), (32, 4), (32, 8))]
+                                         (64, 2), (64, 3), (64, 4), (64, 8), (32, 2), (32, 3), (32, 4), (32, 8),
+                                         (256, 1), (256, 2), (256, 4), (256, 8))]
     shapes.append((20, 128, 4, I.paper_skip_layer(4)))
     for F, H, L, S in shapes:
         def make():
             return pt.Nif(ctx, I.nif_init(n_freq=F, hidden=H, n_hidden_layers=L, colour="yuv", skip_after=S))
         g = make()
-        tprec = "bf16"
-        try:
-            g.train(sky, steps=1, batch=1024, lr=1e-3, seed=99, precision="bf16")
-        except RuntimeError:   # the BF16 training chains need the weights resident in shared memory too
-            tprec = "fp32"
-        g = make()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        g.train(sky, steps=steps, batch=1 << 16, lr=1e-3, seed=0, precision=tprec)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        train_ms = e0.elapsed_time(e1)
         row = {"n_freq": F, "hidden": H, "layers": L, "skip_after": S, "params": g.param_count,
-               "weights_kb_bf16": (g.param_count * 2) // 1024,
-               "train_gemms": tprec, "train_ms_per_step": train_ms / steps, "quality": nif_quality(g, sky, dev)}
+               "weights_kb_bf16": (g.param_count * 2) // 1024}
+        if H <= 128:
+            tprec = "bf16"
+            try:
+                g.train(sky, steps=1, batch=1024, lr=1e-3, seed=99, precision="bf16")
+            except RuntimeError:   # the BF16 training chains need the weights resident in shared memory too
+                tprec = "fp32"
+            g = make()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.train(sky, steps=steps, batch=1 << 16, lr=1e-3, seed=0, precision=tprec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row.update({"train_gemms": tprec, "train_ms_per_step": e0.elapsed_time(e1) / steps,
+                        "quality": nif_quality(g, sky, dev)})
+        else:
+            row.update({"train_gemms": None, "train_ms_per_step": None, "quality": None,
+                        "train_note": "not trained: the training chains are 128 wide; rates of the random-init "
+                                      "network"})
         row["fp32_evals_per_s"] = (1 << 24) / (ms_of(lambda: g.eval(uv, "fp32"), 2) * 1e-3)
-        bf16_ok = F == 64 and S == 0 and ((H == 128 and 1 <= L <= 5) or (H in (64, 32) and 1 <= L <= 8))
+        bf16_ok = ((F == 64 and S == 0 and ((H == 128 and 1 <= L <= 5) or (H in (64, 32) and 1 <= L <= 8) or
+                                            (H == 256 and L == 1))) or (F, H, L, S) == (20, 128, 4, 2))
         if bf16_ok:
             row["bf16_evals_per_s"] = (1 << 24) / (ms_of(lambda: g.eval(uv, "bf16"), 3) * 1e-3)
-            row["bf16_tile_slots"] = (3 if L <= 3 else (2 if L == 4 else 1)) if H == 128 else 4
+            row["bf16_tile_slots"] = ({256: 2, 128: 3 if L <= 3 else (2 if L == 4 else 1)}.get(H, 4) if not S else 3)
             fr = ms_of(lambda: pt.render(ctx, scene, g, cfg, "bf16", out=img), 3)
             row["c2_bf16_msamples_s"] = cfg.n_slots / (fr * 1e-3) / 1e6
         else:
             row["bf16_evals_per_s"] = None
-            row["bf16_note"] = ("no BF16 kernel for the skip-joined network" if S else
-                                "not resident: the BF16 kernel needs H = 128 with L <= 5, or H = 64 / 32 with L <= 8")
+            row["bf16_note"] = ("not resident: the BF16 kernel needs H = 128 with L <= 5, H = 64 / 32 with L <= 8 "
+                                "or H = 256 with L = 1")
             fr = ms_of(lambda: pt.render(ctx, scene, g, cfg, "fp32", out=img), 3)
             row["c2_fp32_msamples_s"] = cfg.n_slots / (fr * 1e-3) / 1e6
         ctx.check()

@@ -204,22 +204,26 @@ PT_API pt_status pt_scene_download_bvh(pt_ctx* ctx, const pt_scene* scene, uint3
 /* of width H -> linear layer to 3 -> fixed 3x3 colour matrix M -> exp.     */
 /* ------------------------------------------------------------------------ */
 typedef struct pt_nif_desc {
-    int32_t n_freq;            /* F */
-    int32_t hidden;            /* H */
+    int32_t n_freq;            /* F (2F <= 128) */
+    int32_t hidden;            /* H (1..256) */
     int32_t n_hidden_layers;   /* L (1..8) */
     const float* params;       /* host, flat: B[F][2], then per layer W[out][in], b[out], then M[3][3] */
     int32_t skip_after;        /* 0: plain MLP.  s in [1, L - 1] (needs H > 2F): hidden layer s has H - 2F
                                   outputs and hidden layer s + 1 takes them followed by the 2F Fourier
                                   features (the paper's network: F = 20, H = 128, L = 4, s = 2, Section
-                                  3.2).  Evaluated on the FP32 path and trained with FP32 GEMMs. */
+                                  3.2).  Trained with FP32 GEMMs. */
 } pt_nif_desc;
 
 /* Upload FP32 master weights and build the BF16 operand image of the
-   tensor-core kernel (when F = 64, H = 128 and 1 <= L <= 5: the weights stay
-   resident in shared memory beside three 128-row tile slots for L <= 3, two
-   for L = 4, one for L = 5; from L = 6 they do not fit, and only the FP32
-   path serves; the FP8 image, L = 3 only, is built on first use, see
-   pt_nif_fp8_scales). */
+   tensor-core kernel where one exists for the shape: F = 64 without a skip
+   layer and H = 128, 1 <= L <= 5 (the weights stay resident in shared memory
+   beside three 128-row tile slots for L <= 3, two for L = 4, one for L = 5;
+   from L = 6 they do not fit, and only the FP32 path serves), H = 64 or 32,
+   1 <= L <= 8 (four slots), H = 256, L = 1 (two slots); and the paper's
+   network F = 20, H = 128, L = 4, skip_after = 2 (three slots).  The FP8
+   image (F = 64, H = 128, L = 3 only) is built on first use, see
+   pt_nif_fp8_scales.  PT_EUNSUPPORTED outside 2F <= 128, H <= 256,
+   1 <= L <= 8; PT_EINVAL for a bad skip layer. */
 PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* desc, pt_nif** out);
 PT_API void pt_destroy_nif(pt_nif* nif);
 /* number of floats in the flat layout */
@@ -230,7 +234,8 @@ PT_API pt_status pt_nif_get_params(pt_ctx* ctx, const pt_nif* nif, float* params
 
 /* Evaluate the NIF at n coordinates: d_uv [n][2] float -> d_rgb [n][3]
    float, in the requested precision.  PT_EUNSUPPORTED for BF16 on a shape
-   other than F = 64, H = 128, 1 <= L <= 5, and for FP8 other than L = 3. */
+   without a tensor-core kernel (see pt_load_nif), and for FP8 other than
+   F = 64, H = 128, L = 3. */
 PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nif, int32_t precision, int64_t n, const float* d_uv,
                              float* d_rgb, void* stream);
 
@@ -270,7 +275,9 @@ typedef struct pt_train_cfg {
    Adam moments and the global step count persist in the pt_nif across calls,
    so calls continue one run.  The FP32 and tensor-core layouts are rebuilt
    at the end of the call.  FP32 arithmetic (or BF16 GEMM operands with
-   cfg->precision = PT_BF16), loss sums in FP64, deterministic in both. */
+   cfg->precision = PT_BF16), loss sums in FP64, deterministic in both.
+   PT_EUNSUPPORTED for hidden widths above 128 and for BF16 GEMMs on a shape
+   whose weights do not stay resident or with a skip layer. */
 PT_API pt_status pt_train_nif(pt_ctx* ctx, pt_nif* nif, const float* d_sky, int32_t w, int32_t h,
                               const pt_train_cfg* cfg, float* d_losses, void* stream);
 

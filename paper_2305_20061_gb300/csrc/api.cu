@@ -313,7 +313,7 @@ pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, int ac
         return PT_OK;
     }
     if (precision == PT_BF16 && nif->d_tc) {
-        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nif->d_tc, nif->H, nif->L, p, 1, ctx->sm_count, s); }));
+        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nif->d_tc, nif->F, nif->H, nif->L, nif->skip, p, 1, ctx->sm_count, s); }));
         return PT_OK;
     }
     if (precision == PT_FP8E4M3 && nif->fp8_ok) {
@@ -322,7 +322,7 @@ pt_status eval_nif_escapes(pt_ctx* ctx, const pt_nif* nif, int precision, int ac
         PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_fp8(nif->d_fp8, p, 1, ctx->sm_count, s); }));
         return PT_OK;
     }
-    return fail(ctx, PT_EUNSUPPORTED, "the BF16 NIF needs F = 64, H = 128, 1 <= L <= 5 and no skip layer (FP8: L = 3)");
+    return fail(ctx, PT_EUNSUPPORTED, "no BF16 kernel for this NIF shape (F = 64 with H = 128 and L <= 5, H = 64 or 32 and L <= 8, H = 256 and L = 1; the paper's F = 20 skip network); FP8: F = 64, H = 128, L = 3");
 }
 
 }  // namespace
@@ -682,8 +682,8 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
     if (!ctx || !d || !out || !d->params) return fail(ctx, PT_EINVAL, "null argument");
     *out = nullptr;
     const int F = d->n_freq, H = d->hidden, L = d->n_hidden_layers, S = d->skip_after;
-    if (F < 1 || 2 * F > 128 || H < 1 || H > 128 || L < 1 || L > 8)
-        return fail(ctx, PT_EUNSUPPORTED, "NIF shape outside 2F <= 128, H <= 128, 1 <= L <= 8");
+    if (F < 1 || 2 * F > 128 || H < 1 || H > 256 || L < 1 || L > 8)
+        return fail(ctx, PT_EUNSUPPORTED, "NIF shape outside 2F <= 128, H <= 256, 1 <= L <= 8");
     if (S < 0 || S >= L || (S > 0 && H <= 2 * F))
         return fail(ctx, PT_EINVAL, "skip_after must be 0 or in [1, L - 1] with H > 2F");
     int64_t n = 2 * F;
@@ -694,13 +694,14 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
     }
     n += 9;
     if (!finite3(d->params, n)) return fail(ctx, PT_EINVAL, "non-finite NIF parameters");
-    // FP32 packed layout
-    const size_t fp32_floats = (size_t)L * 128 * 128 + (size_t)L * 128 + 3 * 128 + 3 + 2 * F;
+    // FP32 packed layout, each layer padded to D x D
+    const int D = nif_fp32_width(H);
+    const size_t fp32_floats = (size_t)L * D * D + (size_t)L * D + 3 * (size_t)D + 3 + 2 * F;
     std::vector<float> pk(fp32_floats, 0.f);
     float* Wt = pk.data();
-    float* bias = Wt + (size_t)L * 128 * 128;
-    float* Wout = bias + (size_t)L * 128;
-    float* bout = Wout + 3 * 128;
+    float* bias = Wt + (size_t)L * D * D;
+    float* Wout = bias + (size_t)L * D;
+    float* bout = Wout + 3 * D;
     float* Bc = bout + 3;
     const float* p = d->params;
     for (int i = 0; i < 2 * F; ++i) Bc[i] = *p++;
@@ -709,13 +710,13 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
         nif_layer_dims(F, H, L, S, l, &in, &o);
         if (l < L) {
             for (int j = 0; j < o; ++j)
-                for (int k = 0; k < in; ++k) Wt[(size_t)l * 128 * 128 + (size_t)k * 128 + j] = p[(size_t)j * in + k];
+                for (int k = 0; k < in; ++k) Wt[(size_t)l * D * D + (size_t)k * D + j] = p[(size_t)j * in + k];
             p += (size_t)in * o;
-            for (int j = 0; j < o; ++j) bias[l * 128 + j] = p[j];
+            for (int j = 0; j < o; ++j) bias[l * D + j] = p[j];
             p += o;
         } else {
             for (int j = 0; j < 3; ++j)
-                for (int k = 0; k < in; ++k) Wout[j * 128 + k] = p[(size_t)j * in + k];
+                for (int k = 0; k < in; ++k) Wout[j * D + k] = p[(size_t)j * in + k];
             p += (size_t)in * 3;
             for (int j = 0; j < 3; ++j) bout[j] = p[j];
             p += 3;
@@ -725,7 +726,7 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
     nf->ctx = ctx;
     nf->F = F; nf->H = H; nf->L = L; nf->skip = S; nf->n_params = n;
     std::vector<unsigned char> img;
-    const bool tc = S == 0 && pack_nif_tc_image(d->params, F, H, L, img);
+    const bool tc = pack_nif_tc_image(d->params, F, H, L, S, img);
     // one allocation and one copy: master weights | FP32 layout | tensor-core image
     const size_t b_params = ((size_t)n * sizeof(float) + 255) & ~(size_t)255;
     const size_t b_fp32 = (fp32_floats * sizeof(float) + 255) & ~(size_t)255;
@@ -749,11 +750,11 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
         }
     }
     DevNif& v = nf->dev;
-    v.F = F; v.H = H; v.L = L; v.skip = S;
+    v.F = F; v.H = H; v.L = L; v.skip = S; v.D = D;
     v.Wt = nf->d_fp32;
-    v.bias = nf->d_fp32 + (size_t)L * 128 * 128;
-    v.Wout = v.bias + (size_t)L * 128;
-    v.bout = v.Wout + 3 * 128;
+    v.bias = nf->d_fp32 + (size_t)L * D * D;
+    v.Wout = v.bias + (size_t)L * D;
+    v.bout = v.Wout + 3 * D;
     v.B = v.bout + 3;
     for (int i = 0; i < 9; ++i) v.M[i] = d->params[n - 9 + i];
     nf->fp8_ok = F == 64 && H == 128 && L == 3 && S == 0;
@@ -802,7 +803,7 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
         return PT_OK;
     }
     if (precision == PT_BF16 && nf->d_tc) {
-        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nf->d_tc, nf->H, nf->L, p, 0, ctx->sm_count, s); }));
+        PT_CUDA(timed(ctx, PT_KIND_NIF, s, [&] { return launch_nif_tc(nf->d_tc, nf->F, nf->H, nf->L, nf->skip, p, 0, ctx->sm_count, s); }));
         return PT_OK;
     }
     if (precision == PT_FP8E4M3 && nf->fp8_ok) {
@@ -812,7 +813,7 @@ PT_API pt_status pt_nif_eval(pt_ctx* ctx, const pt_nif* nf, int32_t precision, i
         return PT_OK;
     }
     if (precision == PT_BF16 || precision == PT_FP8E4M3)
-        return fail(ctx, PT_EUNSUPPORTED, "the BF16 NIF needs F = 64, H = 128, 1 <= L <= 5 and no skip layer (FP8: L = 3)");
+        return fail(ctx, PT_EUNSUPPORTED, "no BF16 kernel for this NIF shape (F = 64 with H = 128 and L <= 5, H = 64 or 32 and L <= 8, H = 256 and L = 1; the paper's F = 20 skip network); FP8: F = 64, H = 128, L = 3");
     return fail(ctx, PT_EINVAL, "unknown precision");
 }
 
@@ -823,6 +824,7 @@ namespace {
 // training GEMM precision: PT_FP32, or PT_BF16 where the tensor-core kernels take the shape
 pt_status check_train_precision(pt_ctx* ctx, int L, int H, int in0, int32_t precision, int skip = 0)
 {
+    if (H > 128) return fail(ctx, PT_EUNSUPPORTED, "training takes hidden widths up to 128");
     if (precision == PT_FP32) return PT_OK;
     if (precision != PT_BF16) return fail(ctx, PT_EINVAL, "training precision is PT_FP32 or PT_BF16");
     if (skip > 0) return fail(ctx, PT_EUNSUPPORTED, "the skip-concatenated NIF trains with FP32 GEMMs");
@@ -914,7 +916,7 @@ pt_status ensure_train(pt_ctx* ctx, pt_nif* nf, int64_t B)
 pt_status refresh_layouts(pt_ctx* ctx, pt_nif* nf, cudaStream_t s)
 {
     PT_CUDA(repack_nif_fp32(nf->d_params, nf->F, nf->H, nf->L, nf->skip, nf->d_fp32, s));
-    if (nf->d_tc) PT_CUDA(repack_nif_tc_image(nf->d_params, nf->H, nf->L, nf->d_tc, s));
+    if (nf->d_tc) PT_CUDA(repack_nif_tc_image(nf->d_params, nf->F, nf->H, nf->L, nf->skip, nf->d_tc, s));
     nf->fp8_stale = true;   // rebuilt on its next use
     return PT_OK;
 }
@@ -1411,7 +1413,7 @@ static pt_status render_impl(pt_ctx* ctx, const pt_scene* sc, const pt_nif* nf, 
     if (n_slots > 0xFFFFFFFFll) return fail(ctx, PT_EINVAL, "more than 2^32 - 1 paths in one call");
     if (sc->dev.env_is_nif && cfg->precision != PT_FP32 && !(cfg->precision == PT_BF16 && nf->d_tc) &&
         !(cfg->precision == PT_FP8E4M3 && nf->fp8_ok))
-        return fail(ctx, PT_EUNSUPPORTED, "the BF16 NIF needs F = 64, H = 128, 1 <= L <= 5 and no skip layer (FP8: L = 3)");
+        return fail(ctx, PT_EUNSUPPORTED, "no BF16 kernel for this NIF shape (F = 64 with H = 128 and L <= 5, H = 64 or 32 and L <= 8, H = 256 and L = 1; the paper's F = 20 skip network); FP8: F = 64, H = 128, L = 3");
     // chunk = whole samples
     int64_t chunk = cfg->chunk_slots > 0 ? cfg->chunk_slots : (int64_t)1 << 24;
     chunk = std::max<int64_t>(n_pix, (chunk / n_pix) * n_pix);
@@ -1808,7 +1810,7 @@ PT_API pt_status pt_load_nif_file(pt_ctx* ctx, const char* path, pt_nif** out)
     // the parameter count implied by the dimensions must be the file's before anything reads P
     {
         const int F = d.n_freq, H = d.hidden, L = d.n_hidden_layers, S = d.skip_after;
-        if (F < 1 || F > 64 || H < 1 || H > 128 || L < 1 || L > 8 || S < 0 || S >= L || (S > 0 && H <= 2 * F))
+        if (F < 1 || F > 64 || H < 1 || H > 256 || L < 1 || L > 8 || S < 0 || S >= L || (S > 0 && H <= 2 * F))
             return fail(ctx, PT_EIO, "checkpoint dimensions out of range");
         int64_t n = 2 * (int64_t)F + 9;
         for (int l = 0; l <= L; ++l) {

@@ -157,15 +157,19 @@ PT_HOST_DEVICE inline void nif_layer_dims(int F, int H, int L, int skip, int l, 
     *out = l == L ? 3 : (skip > 0 && l == skip - 1 ? H - 2 * F : H);
 }
 
+// padded width D of the FP32 evaluation layout: 128, or 256 for networks wider than 128
+PT_HOST_DEVICE inline int nif_fp32_width(int H) { return H > 128 ? 256 : 128; }
+
 struct DevNif {
     int32_t F, H, L;         // frequencies, hidden width, hidden layers
     int32_t skip;            // 0, or the hidden layer whose output is joined with the features (1-based)
+    int32_t D;               // padded width of the FP32 layout (nif_fp32_width(H))
     const float* B;          // [F][2]
-    // FP32 path: each linear layer padded to 128 x 128 and stored transposed
+    // FP32 path: each linear layer padded to D x D and stored transposed
     // ([in][out]); the output layer is stored [3][H] untransposed
-    const float* Wt;         // [L][128][128]
-    const float* bias;       // [L][128]
-    const float* Wout;       // [3][128]
+    const float* Wt;         // [L][D][D]
+    const float* bias;       // [L][D]
+    const float* Wout;       // [3][D]
     const float* bout;       // [3]
     float M[9];
 };
@@ -211,10 +215,11 @@ cudaError_t launch_nif_fp32(const NifEvalParams& p, int mode, int sm_count, cuda
 
 // tensor-core NIF (nif_tc.cu): F = 64; H = 128 with L = 1 .. 5, H = 64 or 32 with L = 1 .. 8 hidden layers
 // (weights resident in shared memory)
-bool nif_tc_supported(int F, int H, int L);
-bool pack_nif_tc_image(const float* params, int F, int H, int L, std::vector<unsigned char>& out);
-cudaError_t launch_nif_tc(const unsigned char* image, int H, int L, const NifEvalParams& p, int mode, int sm_count,
-                          cudaStream_t s);
+// the BF16 tensor-core NIF: shapes (F, H, L, skip layer) with a kernel, image packing, launch
+bool nif_tc_supported(int F, int H, int L, int S);
+bool pack_nif_tc_image(const float* params, int F, int H, int L, int S, std::vector<unsigned char>& out);
+cudaError_t launch_nif_tc(const unsigned char* image, int F, int H, int L, int S, const NifEvalParams& p, int mode,
+                          int sm_count, cudaStream_t s);
 // FP8 E4M3 tensor-core NIF (nif_fp8.cu): same shape; scales_out [4] = activation scales
 bool pack_nif_fp8_image(const float* params, int F, int H, int L, std::vector<unsigned char>& out, float* scales_out);
 cudaError_t launch_nif_fp8(const unsigned char* image, const NifEvalParams& p, int mode, int sm_count, cudaStream_t s);
@@ -297,7 +302,7 @@ cudaError_t cache_query_tc(const unsigned char* image, CacheBox box, int64_t cap
                            int sm_count, cudaStream_t s);
 // rebuild the packed FP32 layout and (when present) the tensor-core image from the master weights
 cudaError_t repack_nif_fp32(const float* params, int F, int H, int L, int skip, float* packed, cudaStream_t s);
-cudaError_t repack_nif_tc_image(const float* params, int H, int L, unsigned char* image, cudaStream_t s);
+cudaError_t repack_nif_tc_image(const float* params, int F, int H, int L, int S, unsigned char* image, cudaStream_t s);
 
 // read-only views of the C-ABI handles (api.cu)
 const DevScene* scene_view(const pt_scene* s, int* device);

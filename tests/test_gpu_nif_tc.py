@@ -41,11 +41,13 @@ def bf16_model(nif, uv):
     t = (B[:, 0][None] * uv[:, :1].astype(np.float64) + B[:, 1][None] * uv[:, 1:].astype(np.float64))
     t = t.astype(np.float32).astype(np.float64)
     r = t - np.rint(t)
-    h = bf16(np.concatenate([np.sin(2 * np.pi * r), np.cos(2 * np.pi * r)], 1).astype(np.float32))
-    h = h.astype(np.float64)
-    for W, b in zip(nif.W[:-1], nif.b[:-1]):
+    feat = bf16(np.concatenate([np.sin(2 * np.pi * r), np.cos(2 * np.pi * r)], 1).astype(np.float32))
+    h = feat.astype(np.float64)
+    for l, (W, b) in enumerate(zip(nif.W[:-1], nif.b[:-1])):
         a = h @ bf16(W).astype(np.float64).T + b.astype(np.float64)
         h = bf16(np.maximum(a, 0).astype(np.float32)).astype(np.float64)
+        if nif.skip_after and l == nif.skip_after - 1:   # the narrowed layer joined with the features
+            h = np.concatenate([h, feat.astype(np.float64)], 1)
     y = h @ bf16(nif.W[-1]).astype(np.float64).T + nif.b[-1].astype(np.float64)
     z = y @ nif.M.astype(np.float64).T
     return np.exp(z)
@@ -85,11 +87,12 @@ def test_bf16_nif_error_vs_oracle(pt, ctx):
 
 
 def test_bf16_nif_rejects_other_shapes(pt, ctx):
-    """The BF16 kernel takes F = 64 with H = 128 and 1 <= L <= 5, or H = 64
-    or 32 and 1 <= L <= 8; it does not apply to 32 frequencies, to six
-    hidden layers of width 128 (192 KB of weights no longer fit in shared
-    memory beside a 32 KB tile slot) or to width 96."""
-    for kw in ({"n_freq": 32}, {"n_hidden_layers": 6}, {"hidden": 96}):
+    """The BF16 kernel takes F = 64 with H = 128 and 1 <= L <= 5, H = 64 or
+    32 and 1 <= L <= 8, or H = 256 and L = 1, and the paper's skip network;
+    it does not apply to 32 frequencies, to six hidden layers of width 128
+    (192 KB of weights no longer fit in shared memory beside a 32 KB tile
+    slot), to width 96 or to two layers of width 256."""
+    for kw in ({"n_freq": 32}, {"n_hidden_layers": 6}, {"hidden": 96}, {"hidden": 256, "n_hidden_layers": 2}):
         g = pt.Nif(ctx, I.nif_init(**kw))
         with pytest.raises(pt.PTError) as e:
             g.eval(torch.zeros((10, 2), device="cuda"), precision="bf16")
@@ -168,4 +171,88 @@ def test_bf16_render_close_to_fp32(pt, ctx, config):
     rel = float(np.sqrt(((a - b) ** 2).sum() / (a ** 2).sum()))
     print({"config": config, "bf16_vs_fp32_rel_rmse": rel})
     assert np.array_equal(b, b2)
+    assert rel < 0.05
+
+
+def _with_biases(nif, seed):
+    rng = np.random.default_rng(seed)
+    for b in nif.b:
+        b[:] = rng.normal(0, 0.05, b.shape)
+    return nif
+
+
+def _check_model(got, ref):
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert np.all(np.isfinite(got))
+    assert np.median(rel) <= 2e-4 and rel.max() <= 2e-2, (np.median(rel), rel.max())
+
+
+def test_bf16_paper_skip_network_matches_rounding_model(pt, ctx):
+    """The paper's network (Section 3.2: 20 frequencies, four layers of 128,
+    the second narrowed to 88 outputs and joined with the 40 features) on the
+    tensor cores: K = 48 first layer, N = 96 narrowed layer whose last 40
+    operand columns are the features again, against the rounding model; its
+    error against the FP64 oracle reported as log-RMSE; FP32 training is
+    followed by the repacked image."""
+    nif = _with_biases(I.nif_init(n_freq=20, hidden=128, n_hidden_layers=4, skip_after=2, colour="yuv", seed=5), 5)
+    g = pt.Nif(ctx, nif)
+    n = 128 * 152 * 3 * 2 + 59
+    uv = I.uniform_uv(n, seed=77)
+    got = g.eval(torch.from_numpy(uv).cuda(), precision="bf16").cpu().numpy().astype(np.float64)
+    ctx.check()
+    _check_model(got, bf16_model(nif, uv))
+    oref, _ = O.Nif(nif).forward(uv[:20000].astype(np.float64))
+    log_rmse = float(np.sqrt(np.mean((np.log(got[:20000]) - np.log(oref)) ** 2)))
+    print({"paper_skip_bf16_log_rmse": log_rmse})
+    assert log_rmse < 0.05
+    g.train(torch.from_numpy(I.procedural_sky(64, 32)).cuda(), steps=2, batch=1024, lr=1e-2, precision="fp32")
+    trained = pt.nif_from_flat(20, 128, 4, g.get_params(), 2)
+    got2 = g.eval(torch.from_numpy(uv[:4096]).cuda(), precision="bf16").cpu().numpy().astype(np.float64)
+    _check_model(got2, bf16_model(trained, uv[:4096]))
+
+
+def test_bf16_width_256_matches_rounding_model(pt, ctx):
+    """One hidden layer of width 256 (two 64 KB tile slots, N = 256 MMAs, the
+    head reusing the accumulator's TMEM columns) against the rounding model,
+    and its log-RMSE against the oracle."""
+    nif = _with_biases(I.nif_init(hidden=256, n_hidden_layers=1, colour="yuv", seed=8), 8)
+    g = pt.Nif(ctx, nif)
+    n = 128 * 152 * 2 * 3 + 101
+    uv = I.uniform_uv(n, seed=88)
+    got = g.eval(torch.from_numpy(uv).cuda(), precision="bf16").cpu().numpy().astype(np.float64)
+    ctx.check()
+    _check_model(got, bf16_model(nif, uv))
+    oref, _ = O.Nif(nif).forward(uv[:20000].astype(np.float64))
+    print({"h256_bf16_log_rmse": float(np.sqrt(np.mean((np.log(got[:20000]) - np.log(oref)) ** 2)))})
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_fp32_width_256_matches_oracle(pt, ctx, L):
+    """The FP32 path at width 256 (64-row tiles, weights staged in four
+    K-chunks) within 1e-5 relative of the FP64 oracle; training refuses the
+    width (the training chains are 128 wide)."""
+    nif = _with_biases(I.nif_init(hidden=256, n_hidden_layers=L, colour="yuv", seed=L), L)
+    g = pt.Nif(ctx, nif)
+    uv = I.uniform_uv(64 * 29 + 13, seed=L)
+    got = g.eval(torch.from_numpy(uv).cuda(), precision="fp32").cpu().numpy().astype(np.float64)
+    ctx.check()
+    ref, _ = O.Nif(nif).forward(uv.astype(np.float64))
+    assert (np.abs(got - ref) / np.abs(ref)).max() <= 1e-5
+    with pytest.raises(pt.PTError) as e:
+        g.train(torch.from_numpy(I.procedural_sky(64, 32)).cuda(), steps=1, batch=256)
+    assert e.value.status == pt.PT_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("shape", [dict(hidden=256, n_hidden_layers=1),
+                                   dict(n_freq=20, hidden=128, n_hidden_layers=4, skip_after=2)])
+def test_bf16_render_of_other_shapes_close_to_fp32(pt, ctx, shape):
+    sc = I.make_scene("C2")
+    cfg = I.RenderCfg(128, 128, 4, 4)
+    s = pt.Scene(ctx, sc)
+    g = pt.Nif(ctx, I.nif_init(colour="yuv", **shape))
+    a = pt.render(ctx, s, g, cfg, "fp32").cpu().numpy().astype(np.float64)
+    b = pt.render(ctx, s, g, cfg, "bf16").cpu().numpy().astype(np.float64)
+    ctx.check()
+    rel = float(np.sqrt(((a - b) ** 2).sum() / (a ** 2).sum()))
+    print({"shape": shape, "bf16_vs_fp32_rel_rmse": rel})
     assert rel < 0.05
