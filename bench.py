@@ -163,18 +163,31 @@ def workload(name, spp=None, depth=None, rr=False):
     return sc, cfg, nif
 
 
-def config_dict(name, cfg, precision, trained):
+def config_dict(name, cfg):
+    """The workload of a line (the same for the GPU arm and the oracle arm; no model keys)."""
     rr = f"Russian roulette from depth {cfg.rr_start}" if cfg.rr else "no RR"
-    d = {"workload": f"{name}: {I.CONFIGS[name]['desc']}; rendered {cfg.width}x{cfg.height}, {cfg.spp} spp, "
-                     f"max depth {cfg.max_depth}, {rr}",
-         "paths_per_frame": cfg.n_slots,
-         "l2": "per-step working set > L2 (wavefront queues ~2.7 GB per 2^24 paths) and a 512 MB L2 flush between "
-               "timed steps (outside the timed events)"}
-    if precision is not None:
-        d["nif"] = ("F=64 Gaussian Fourier (sigma 10) -> 3x FC-128 ReLU -> FC-3 -> colour matrix -> exp; " +
-                    ("weights trained by pt_train_nif on the procedural 2048x1024 sky" if trained else "random init"))
-        d["nif_precision"] = precision
-    return d
+    return {"workload": f"{name}: {I.CONFIGS[name]['desc']}; rendered {cfg.width}x{cfg.height}, {cfg.spp} spp, "
+                        f"max depth {cfg.max_depth}, {rr}",
+            "paths_per_frame": cfg.n_slots,
+            "l2": "per-step working set > L2 (wavefront queues ~2.7 GB per 2^24 paths) and a 512 MB L2 flush between "
+                  "timed steps (outside the timed events)"}
+
+
+def nif_dict(precision, trained):
+    """The environment network of a line."""
+    return {"shape": "F=64 Gaussian Fourier (sigma 10) -> 3x FC-128 ReLU -> FC-3 -> colour matrix -> exp",
+            "weights": ("trained by pt_train_nif on the procedural 2048x1024 sky" if trained else
+                        "random init (the work per path does not depend on the weights: the environment's values "
+                        "change no path's geometry)"),
+            "precision": precision}
+
+
+def c5_config(cfg):
+    return {"workload": f"C5: {I.CONFIGS['C5']['desc']}; a step = one frame = pt_train_cache ({N_TRAIN} training "
+                        f"paths, depth {cfg.max_depth}, records at vertex {CACHE_VERTEX}) + pt_render_cached "
+                        f"({cfg.width}x{cfg.height}, {cfg.spp} spp, paths end in the cache at vertex {CACHE_VERTEX})",
+            "paths_per_frame": cfg.n_slots,
+            "l2": "512 MB L2 flush between timed frames (outside the timed events)"}
 
 
 # ----------------------------------------------------------------------------
@@ -215,7 +228,7 @@ def bench_reference(args):
             "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * cfg.n_slots / (value * 1e6),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"C5: {I.CONFIGS['C5']['desc']}", "paths_per_frame": cfg.n_slots},
+            "config": c5_config(cfg), "nif": nif_dict("fp64-oracle", False),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
@@ -235,7 +248,8 @@ def bench_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_dict(args.workload, cfg, "fp64-oracle" if nif else None, False),
+        "data": "synthetic", "config": config_dict(args.workload, cfg),
+        "nif": nif_dict("fp64-oracle", False) if nif else None,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -560,7 +574,7 @@ def bench_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": rprec if uses_nif and rprec != "fp32" else "f32",
             "data": "synthetic (procedural scene" + (" and sky, NIF trained on the sky" if train else "") + "; seeds 0)",
-            "config": config_dict(args.workload, cfg, precision, train is not None),
+            "config": config_dict(args.workload, cfg), "nif": nif_dict(precision, train is not None) if uses_nif else None,
             "rays_per_step": rays, "traversal_work_per_step": work,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "scene_build_s": t_build, "bvh_nodes": scene.info()["n_nodes"], "bvh_depth": scene.info()["bvh_depth"],
@@ -869,15 +883,10 @@ def bench_c5(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec,
             "data": "synthetic (procedural heightfield and sky, NIF trained on the sky, cache trained online; seeds 0)",
-            "config": {"workload": f"C5: {I.CONFIGS['C5']['desc']}; a step = one frame = pt_train_cache "
-                                   f"({N_TRAIN} training paths, depth {cfg.max_depth}, records at vertex "
-                                   f"{CACHE_VERTEX}) + pt_render_cached ({W}x{H}, {spp} spp, paths end in the cache "
-                                   f"at vertex {CACHE_VERTEX})",
-                       "paths_per_frame": cfg.n_slots, "nif_precision": prec,
-                       "cache": "12 freqs/axis position encoding + direction + normal (78) -> 5x FC-64 ReLU -> FC-3, "
-                                "FP32 master weights, Adam lr 1e-2, relative L2",
-                       "cache_train_gemms": args.train_precision,
-                       "l2": "512 MB L2 flush between timed frames (outside the timed events)"},
+            "config": c5_config(cfg), "nif": nif_dict(prec, train is not None),
+            "cache": {"shape": "12 freqs/axis position encoding + direction + normal (78) -> 5x FC-64 ReLU -> FC-3",
+                      "training": "FP32 master weights, Adam lr 1e-2, relative L2",
+                      "train_gemms": args.train_precision},
             "kernel_ms_per_step": kinds,
             "frame_split_ms": {"train": {k: v[0] for k, v in prof_train.items()},
                                "render": {k: v[0] for k, v in prof_render.items()}},
