@@ -54,9 +54,18 @@ FLOP_NODE, FLOP_SPHERE, FLOP_QUAD, FLOP_TRI = 24, 20, 10, 41
 # FP32 instructions per traversal step as implemented (node step of both children, sphere, quad and
 # triangle tests), for the secondary issue-rate fraction
 OPS_NODE, OPS_SPHERE, OPS_QUAD, OPS_TRI = 58, 36, 12, 46
-# algorithmic bytes per traversal step (a node fetch reads both children's boxes and references), per ray of
-# the traversal kernel (origin and direction in, hit out) and per ray-bounce of trace + shade queue traffic
-BYTES_NODE, BYTES_SPHERE, BYTES_QUAD, BYTES_TRI, BYTES_RAY_TRACE, BYTES_RAY = 48, 16, 32, 48, 40, 140
+# algorithmic bytes per traversal step (a node fetch reads both children's boxes and references) and per ray of
+# the traversal kernel (origin and direction in, hit out)
+BYTES_NODE, BYTES_SPHERE, BYTES_QUAD, BYTES_TRI, BYTES_RAY_TRACE = 48, 16, 32, 48, 40
+
+
+def shade_bytes(counts, depth: int, emits: bool) -> int:
+    """Queue bytes of the shading kernel over a frame, from the rays traced per vertex (counts[:depth]) and the
+    escapes (counts[depth]): a camera ray's 8-byte hit; a later ray's origin, direction and throughput (48 B) and
+    hit (8 B) read; every later ray was written once as a survivor (48 B), and with emitters its radiance (16 B)
+    is written and read too; each escape a 24-byte record."""
+    cam, later, esc = int(counts[0]), int(sum(counts[1:depth])), int(counts[depth])
+    return 8 * cam + (56 + 48 + (32 if emits else 0)) * later + 24 * esc
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) of the traversal kernel per traced ray, from one ncu capture of the workload's frame
 # (or a smaller frame of it) (summaries and commands in profiles/), scaled to a frame by the rays it traces.  Valid only
@@ -516,11 +525,13 @@ def bench_ours(args):
                 "peak_note": f"HBM copy bandwidth ({which}); BVH {scene.info()['node_bytes'] / 2**20:.0f} MiB > L2"}
     elif dom == "shade":
         shade_ms = prof["shade"][0] / args.steps
-        achieved = BYTES_RAY * rays / (shade_ms * 1e-3) / 1e9
+        nbytes = shade_bytes(counts, cfg.max_depth, bool(scene.info()["has_emission"]))
+        achieved = nbytes / (shade_ms * 1e-3) / 1e9
         peak = float(meas["hbm_gbs"])
         roof = {"kernel": "k_bounce", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None,
-                "per_unit": f"{BYTES_RAY} queue bytes per ray-bounce x {rays} rays per frame",
+                "per_unit": f"8 B per camera-ray hit, 104 B per later ray (queue read and survivor write; +32 B with "
+                            f"emitters), 24 B per escape: {nbytes} B over {rays} rays per frame",
                 "peak_note": f"HBM copy bandwidth ({which})"}
     else:
         roof = traversal_roofline(work, trace_ms, trace_kernel, trace_launches, pt.ffma_rate_tflops(local), clock,

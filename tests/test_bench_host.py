@@ -100,3 +100,12 @@ def test_recorded_traffic_matches_the_current_traversal_source():
     for (wl, form), rec in bench.TRACE_TRAFFIC.items():
         assert wl in ("C1", "C2", "C3", "C4", "C5") and form in bench.NODE_FORMS.values()
         assert rec["bytes_per_ray"] > 0 and len(rec["src"]) == 16
+
+
+def test_shade_bytes_counts_the_queue_records():
+    """Shading traffic per frame: 8 B per camera-ray hit, 56 B read and 48 B written per later ray (32 B more of
+    radiance with emitters), 24 B per escape record."""
+    import bench
+    counts = [100, 50, 20, 5]   # rays at vertices 1..3, then escapes
+    assert bench.shade_bytes(counts, 3, False) == 8 * 100 + 104 * 70 + 24 * 5
+    assert bench.shade_bytes(counts, 3, True) == 8 * 100 + 136 * 70 + 24 * 5
