@@ -139,3 +139,26 @@ def test_large_bvh_quantised_subset_parity(pt, ctx, large, large_quant):
                          oracle_scene=osc, max_div=5e-3)
     print(res)
     assert res["overall"] <= 1e-3, res
+
+
+def test_large_bvh_full_frame_in_the_bench_chunks(pt, ctx, large):
+    """The benchmark's launch configuration: the whole 1920 x 1080 frame at
+    32 spp (66.4M paths in four chunks of eight samples, packed nodes,
+    wavefront schedule) against the same pixels rendered on their own with
+    all 32 samples in one chunk.  Every path is the same (Philox streams
+    are keyed by pixel, sample and vertex), so the pixels agree to the
+    rounding of the per-pixel sums."""
+    sc, gs, _ = large
+    cfg = I.CONFIGS["C4"]["cfg"]
+    assert cfg.width * cfg.height * cfg.spp > 3 * (1 << 24)
+    img = pt.render(ctx, gs, None, cfg, "fp32")
+    ctx.check()
+    rng = np.random.default_rng(11)
+    pix = np.sort(rng.choice(cfg.width * cfg.height, 20000, replace=False)).astype(np.int64)
+    sub, _, _ = pt.render_pixels(ctx, gs, None, cfg, torch.from_numpy(pix).cuda())
+    ctx.check()
+    full = img.reshape(-1, 3)[torch.from_numpy(pix).cuda()].cpu().numpy().astype(np.float64)
+    sub = sub.cpu().numpy().astype(np.float64)
+    rel = np.abs(full - sub) / np.maximum(np.abs(sub), 1e-6)
+    assert np.all(np.isfinite(full)) and full.mean() > 0
+    assert rel.max() <= 1e-5, rel.max()
