@@ -489,6 +489,15 @@ def bench_ours(args):
             nif_alone[prec] = {"evals_per_s": (1 << 24) / (t * 1e-3), "ms": t,
                                "tflops": (1 << 24) * flop / (t * 1e-3) / 1e12}
         ctx.check()
+        # the tensor-core kernels against the measured dense peak (FP8: twice the BF16 burst), the FP32 kernel
+        # against the measured FFMA rate
+        meas0, which0 = peaks()
+        for prec, rec in nif_alone.items():
+            peak0 = (pt.ffma_rate_tflops(local) if prec == "fp32" else
+                     float(meas0["bf16_tflops"]) * (2.0 if prec == "fp8" else 1.0))
+            rec.update({"frac_of_peak": rec["tflops"] / peak0, "peak_tflops": peak0,
+                        "peak": "FP32 FMA rate (pt_microbench_ffma)" if prec == "fp32" else
+                                f"dense BF16 cuBLAS burst ({which0})" + (" x 2" if prec == "fp8" else "")})
 
     # live roofline of the dominant kernel of the timed frames
     meas, which = peaks()
