@@ -77,6 +77,11 @@ TRACE_TRAFFIC = {
     # 512x512 at 64 spp, the full frame, one pass per launch (profiles/k_trace_traffic_spheres_c2.md)
     ("C2", "decoded"): {"bytes_per_ray": 22.71, "src": "7d34db8adafd2d1d"},
 }
+# L2 bytes (lts__t_bytes) of the traversal kernel per traced ray on the large tree, from the same captures
+TRACE_L2 = {
+    ("C4", "packed"): {"bytes_per_ray": 1707.0, "src": "7d34db8adafd2d1d"},
+    ("C4", "quant8"): {"bytes_per_ray": 1322.0, "src": "7d34db8adafd2d1d"},
+}
 NODE_FORMS = {1: "packed", 2: "decoded", 3: "quant8"}
 TRACE_SOURCES = ("paper_2305_20061_gb300/csrc/trace.cu", "paper_2305_20061_gb300/csrc/device_common.cuh")
 
@@ -88,6 +93,14 @@ def trace_source_hash() -> str:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def trace_l2_bytes(workload: str, node_form: str, rays: int):
+    """L2 bytes of the traversal kernel over a frame of `rays` traced rays, or None (as trace_traffic)."""
+    rec = TRACE_L2.get((workload, node_form))
+    if rec is None or rec["src"] != trace_source_hash():
+        return None
+    return rec["bytes_per_ray"] * rays
 
 
 def trace_traffic(workload: str, node_form: str, rays: int):
@@ -532,6 +545,14 @@ def bench_ours(args):
                             f"direction in, hit out); {work['nodes']} node fetches, {work['triangle']} triangle "
                             f"tests, {rays} rays per frame over {trace_launches} launches",
                 "peak_note": f"HBM copy bandwidth ({which}); BVH {scene.info()['node_bytes'] / 2**20:.0f} MiB > L2"}
+        l2b = trace_l2_bytes(args.workload, NODE_FORMS[scene.info()["node_format"]], rays)
+        if l2b is not None:
+            l2_peak = pt.l2_read_rate_gbs(local)
+            l2_gbs = l2b / (trace_ms * 1e-3) / 1e9
+            roof["l2"] = {"achieved": l2_gbs, "peak": l2_peak, "unit": "GB/s", "frac": l2_gbs / l2_peak,
+                          "bytes": l2b, "note": "L2 bytes per frame (lts__t_bytes per traced ray from the ncu capture "
+                                                "in profiles/, times the frame's rays) over k_trace's time, against "
+                                                "the L2 read rate measured live by pt_microbench_l2_read"}
     elif dom == "shade":
         shade_ms = prof["shade"][0] / args.steps
         nbytes = shade_bytes(counts, cfg.max_depth, bool(scene.info()["has_emission"]))

@@ -399,6 +399,19 @@ PT_API pt_status pt_profile_read(pt_ctx* ctx, double* ms, int64_t* launches, int
    pointers. */
 PT_API pt_status pt_microbench_ffma(int64_t iters, float* d_sink, double* flop, void* stream);
 
+/* Measurement helper (the paper has no counterpart): the L2 read bandwidth
+   of the current device, the denominator of the large tree's L2 traffic.
+   Launches one kernel on `stream` in which 8 resident 256-thread blocks per
+   SM read the caller's device buffer d_buf (bytes, 16-byte aligned; pick it
+   well inside L2, e.g. 48 MiB) `reps` times over in 16-byte words with
+   loads that bypass L1; *bytes_read receives the bytes read (bytes rounded
+   down to 16 x reps), to be divided by the event-timed duration of a launch
+   after a warm-up launch has brought the buffer into L2.  d_sink: one
+   caller-owned device word, never written in practice.  PT_EINVAL for a
+   NULL pointer, an unaligned buffer, bytes < 16 or reps < 1. */
+PT_API pt_status pt_microbench_l2_read(const void* d_buf, int64_t bytes, int32_t reps, uint32_t* d_sink,
+                                       double* bytes_read, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Building blocks of the same path, exposed for testing and for callers    */
 /* that stream their own rays (Section 3.1.2).                               */

@@ -110,6 +110,7 @@ def lib():
             "pt_render": ([P, P, P, P, P, P, P], I32),
             "pt_device_error_bits": ([P], U32),
             "pt_microbench_ffma": ([I64, P, P, P], I32),
+            "pt_microbench_l2_read": ([P, I64, I32, P, P, P], I32),
             "pt_render_pixels": ([P, P, P, P, I64, P, P, P, P, P], I32),
             "pt_last_render_counts": ([P, P, I32], I32),
             "pt_philox": ([P, U32, U32, I64, P, P, P], I32),
@@ -507,6 +508,29 @@ def render(ctx: Context, scene: Scene, nif: Optional[Nif], cfg: I.RenderCfg, pre
     ctx._raise(lib().pt_render(ctx.h, scene.h, nif.h if nif is not None else None,
                                cache.h if cache is not None else None, C.byref(c), _dptr(out), _stream(stream)))
     return out
+
+
+def l2_read_rate_gbs(device: int, mib: int = 48, reps: int = 20, trials: int = 3) -> float:
+    """L2 read bandwidth of the device in GB/s: pt_microbench_l2_read over a
+    buffer of `mib` MiB (inside L2), timed with CUDA events on the current
+    stream (best of `trials` after one warm-up launch)."""
+    dev = f"cuda:{device}"
+    buf = torch.zeros(mib << 18, dtype=torch.float32, device=dev)   # mib MiB
+    sink = torch.zeros(1, dtype=torch.int32, device=dev)
+    nbytes = C.c_double(0)
+    s = torch.cuda.current_stream(device)
+    best = 0.0
+    for i in range(trials + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        st = lib().pt_microbench_l2_read(_dptr(buf), buf.numel() * 4, reps, _dptr(sink), C.byref(nbytes), _stream(s))
+        e1.record(s)
+        if st != PT_OK:
+            raise PTError(st, "pt_microbench_l2_read failed")
+        torch.cuda.synchronize(dev)
+        if i:
+            best = max(best, nbytes.value / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
 
 
 def ffma_rate_tflops(device: int, iters: int = 1 << 16, reps: int = 3) -> float:

@@ -109,3 +109,12 @@ def test_shade_bytes_counts_the_queue_records():
     counts = [100, 50, 20, 5]   # rays at vertices 1..3, then escapes
     assert bench.shade_bytes(counts, 3, False) == 8 * 100 + 104 * 70 + 24 * 5
     assert bench.shade_bytes(counts, 3, True) == 8 * 100 + 136 * 70 + 24 * 5
+
+
+def test_trace_l2_bytes_follow_the_captured_source(monkeypatch):
+    import bench
+    monkeypatch.setattr(bench, "TRACE_L2", {("C4", "packed"): {"bytes_per_ray": 10.0, "src": bench.trace_source_hash()}})
+    assert bench.trace_l2_bytes("C4", "packed", 100) == 1000.0
+    assert bench.trace_l2_bytes("C4", "quant8", 100) is None
+    monkeypatch.setattr(bench, "TRACE_L2", {("C4", "packed"): {"bytes_per_ray": 10.0, "src": "0" * 16}})
+    assert bench.trace_l2_bytes("C4", "packed", 100) is None
