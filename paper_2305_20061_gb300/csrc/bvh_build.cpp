@@ -45,20 +45,27 @@ struct Box {
 
 constexpr int kBins = 16;
 
+// One primitive's centroid, bounds and input index.  The builder reorders
+// these records themselves (not indices into the input), so every pass over
+// a range reads memory in order.
+struct Prim {
+    float cen[3], lo[3], hi[3];
+    uint32_t id;
+};
+
 struct Builder {
-    const BuildInput& in;
-    std::vector<uint32_t>& idx;      // shared by the builders of one tree (each works on its own range)
+    std::vector<Prim>& prims;        // shared by the builders of one tree (each works on its own range)
     std::vector<PackedNode> nodes;
     int32_t max_depth = 0;
     int par_depth = 0;               // subtrees above this depth may be built on other threads
     std::string error;
 
-    Builder(const BuildInput& i, std::vector<uint32_t>& ix) : in(i), idx(ix) {}
+    explicit Builder(std::vector<Prim>& pr) : prims(pr) {}
 
     Box range_box(int64_t b, int64_t e) const
     {
         Box bx;
-        for (int64_t i = b; i < e; ++i) bx.grow(&in.lo[3 * idx[i]], &in.hi[3 * idx[i]]);
+        for (int64_t i = b; i < e; ++i) bx.grow(prims[i].lo, prims[i].hi);
         return bx;
     }
 
@@ -72,23 +79,22 @@ struct Builder {
         if (n == 2) {
             // two leaves whatever the split; the binned sweep below would order them by centroid along the
             // first axis where the centroids differ (ties: as listed), which this reproduces without the bins
-            const uint32_t p0 = idx[b], p1 = idx[b + 1];
             for (int a = 0; a < 3; ++a) {
-                const float c0 = in.cen[3 * p0 + a], c1 = in.cen[3 * p1 + a];
+                const float c0 = prims[b].cen[a], c1 = prims[b + 1].cen[a];
                 if (c0 != c1) {
-                    if (c1 < c0) std::swap(idx[b], idx[b + 1]);
+                    if (c1 < c0) std::swap(prims[b], prims[b + 1]);
                     break;
                 }
             }
-            bl->grow(&in.lo[3 * idx[b]], &in.hi[3 * idx[b]]);
-            br->grow(&in.lo[3 * idx[b + 1]], &in.hi[3 * idx[b + 1]]);
+            bl->grow(prims[b].lo, prims[b].hi);
+            br->grow(prims[b + 1].lo, prims[b + 1].hi);
             *boxes_known = true;
             return b + 1;
         }
         float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int64_t i = b; i < e; ++i)
             for (int a = 0; a < 3; ++a) {
-                const float c = in.cen[3 * idx[i] + a];
+                const float c = prims[i].cen[a];
                 clo[a] = std::min(clo[a], c);
                 chi[a] = std::max(chi[a], c);
             }
@@ -102,13 +108,13 @@ struct Builder {
         Box bb[3][kBins];
         int64_t cnt[3][kBins] = {};
         for (int64_t i = b; i < e; ++i) {
-            const uint32_t p = idx[i];
+            const Prim& q = prims[i];
             for (int a = 0; a < 3; ++a) {
                 if (!live[a]) continue;
-                int k = (int)((in.cen[3 * p + a] - clo[a]) * scale[a]);
+                int k = (int)((q.cen[a] - clo[a]) * scale[a]);
                 k = std::min(std::max(k, 0), kBins - 1);
                 cnt[a][k]++;
-                bb[a][k].grow(&in.lo[3 * p], &in.hi[3 * p]);
+                bb[a][k].grow(q.lo, q.hi);
             }
         }
         double best_cost = INFINITY;
@@ -149,12 +155,12 @@ struct Builder {
         int64_t mid;
         if (best_axis >= 0) {
             const int a = best_axis;
-            auto it = std::partition(idx.begin() + b, idx.begin() + e, [&](uint32_t p) {
-                int k = (int)((in.cen[3 * p + a] - clo[a]) * scale[a]);
+            auto it = std::partition(prims.begin() + b, prims.begin() + e, [&](const Prim& q) {
+                int k = (int)((q.cen[a] - clo[a]) * scale[a]);
                 k = std::min(std::max(k, 0), kBins - 1);
                 return k < best_bin;
             });
-            mid = it - idx.begin();
+            mid = it - prims.begin();
             if (mid > b && mid < e) {
                 Box l, r;
                 for (int k = 0; k < kBins; ++k) (k < best_bin ? l : r).grow(bb[a][k]);
@@ -171,7 +177,7 @@ struct Builder {
     uint32_t build(int64_t b, int64_t e, int depth)
     {
         max_depth = std::max(max_depth, depth);
-        if (e - b == 1) return kLeafBit | idx[b];
+        if (e - b == 1) return kLeafBit | prims[b].id;
         const uint32_t me = (uint32_t)nodes.size();
         nodes.emplace_back();
         Box bl, br;
@@ -184,7 +190,7 @@ struct Builder {
         uint32_t cl, cr;
         if (depth < par_depth && e - b >= (int64_t)1 << 14) {
             // the left subtree on another thread into its own node list, appended after the right one
-            Builder sub(in, idx);
+            Builder sub(prims);
             sub.par_depth = par_depth;
             sub.nodes.reserve((size_t)(mid - b));
             uint32_t sub_root = kEmptyRef;
@@ -370,9 +376,17 @@ bool build_bvh(const BuildInput& in, BuildOutput& out)
         out.root = kEmptyRef;
         return true;
     }
-    std::vector<uint32_t> idx((size_t)in.n_prims);
-    for (int64_t i = 0; i < in.n_prims; ++i) idx[(size_t)i] = (uint32_t)i;
-    Builder bd(in, idx);
+    std::vector<Prim> prims((size_t)in.n_prims);
+    for (int64_t i = 0; i < in.n_prims; ++i) {
+        Prim& q = prims[(size_t)i];
+        for (int a = 0; a < 3; ++a) {
+            q.cen[a] = in.cen[3 * i + a];
+            q.lo[a] = in.lo[3 * i + a];
+            q.hi[a] = in.hi[3 * i + a];
+        }
+        q.id = (uint32_t)i;
+    }
+    Builder bd(prims);
     const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
     while ((1u << bd.par_depth) < 2 * hw && bd.par_depth < 8) ++bd.par_depth;   // about two subtrees per core
     bd.nodes.reserve((size_t)std::max<int64_t>(in.n_prims - 1, 1));
