@@ -455,7 +455,6 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
     bin.n_prims = nP;
     bin.lo.resize(3 * nP);
     bin.hi.resize(3 * nP);
-    bin.cen.resize(3 * nP);
     std::vector<float4> sph(nS), quad(2 * nQ), tri(3 * nT);
     std::vector<int32_t> pmat(nP);
     for (int64_t i = 0; i < nS; ++i) {
@@ -482,21 +481,21 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
         bin.lo[3 * g + v] = q[3]; bin.hi[3 * g + v] = q[4];
         pmat[g] = d->quad_mat[i];
     }
-    for (int64_t i = 0; i < nT; ++i) {
-        const int64_t g = nS + nQ + i;
-        for (int k = 0; k < 3; ++k) {
-            const float* p = d->verts + 3 * (int64_t)d->tris[3 * i + k];
-            tri[3 * i + k] = make_float4(p[0], p[1], p[2], 0.f);
-            for (int a = 0; a < 3; ++a) {
-                if (k == 0) { bin.lo[3 * g + a] = p[a]; bin.hi[3 * g + a] = p[a]; }
-                bin.lo[3 * g + a] = std::min(bin.lo[3 * g + a], p[a]);
-                bin.hi[3 * g + a] = std::max(bin.hi[3 * g + a], p[a]);
+    for_chunks(0, nT, host_pass_threads(nT), [&](int, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) {
+            const int64_t g = nS + nQ + i;
+            for (int k = 0; k < 3; ++k) {
+                const float* p = d->verts + 3 * (int64_t)d->tris[3 * i + k];
+                tri[3 * i + k] = make_float4(p[0], p[1], p[2], 0.f);
+                for (int a = 0; a < 3; ++a) {
+                    if (k == 0) { bin.lo[3 * g + a] = p[a]; bin.hi[3 * g + a] = p[a]; }
+                    bin.lo[3 * g + a] = std::min(bin.lo[3 * g + a], p[a]);
+                    bin.hi[3 * g + a] = std::max(bin.hi[3 * g + a], p[a]);
+                }
             }
+            pmat[g] = d->tri_mat[i];
         }
-        pmat[g] = d->tri_mat[i];
-    }
-    for (int64_t i = 0; i < nP; ++i)
-        for (int a = 0; a < 3; ++a) bin.cen[3 * i + a] = 0.5f * (bin.lo[3 * i + a] + bin.hi[3 * i + a]);
+    });
     BuildOutput bo;
     if (!build_bvh(bin, bo)) return fail(ctx, PT_EINVAL, bo.error);
     if (bo.depth > kStackSize) return fail(ctx, PT_EUNSUPPORTED, "BVH deeper than the traversal stack");
@@ -517,10 +516,10 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
     if (form_req < PT_NODES_AUTO || form_req > PT_NODES_QUANT8) return fail(ctx, PT_EINVAL, "unknown node_format");
     const bool want_wide = form_req == PT_NODES_DECODED ||
                            (form_req == PT_NODES_AUTO && bo.nodes.size() * 64 <= kWideLimit);
-    std::vector<QuantNode> qn;
+    QuantVec qn;
     if (form_req == PT_NODES_QUANT8 && !bo.nodes.empty()) {
         std::string qerr;
-        if (!quantize_bvh(bo.nodes, qn, &qerr)) return fail(ctx, PT_EUNSUPPORTED, qerr);
+        if (!quantize_bvh(bo.nodes.data(), bo.nodes.size(), qn, &qerr)) return fail(ctx, PT_EUNSUPPORTED, qerr);
     }
     std::vector<float> wide;
     if (!bo.nodes.empty() && want_wide) {
@@ -643,8 +642,6 @@ PT_API pt_status pt_build_bvh_host(int64_t n, const float* lo, const float* hi, 
     bin.n_prims = n;
     bin.lo.assign(lo, lo + 3 * n);
     bin.hi.assign(hi, hi + 3 * n);
-    bin.cen.resize(3 * n);
-    for (int64_t i = 0; i < 3 * n; ++i) bin.cen[i] = 0.5f * (bin.lo[i] + bin.hi[i]);
     BuildOutput bo;
     if (!build_bvh(bin, bo)) return PT_EUNSUPPORTED;
     if ((int64_t)bo.nodes.size() > cap && !bo.nodes.empty()) return PT_EINVAL;
@@ -658,11 +655,11 @@ PT_API pt_status pt_build_bvh_host(int64_t n, const float* lo, const float* hi, 
 PT_API pt_status pt_quantize_bvh_host(int64_t n_nodes, const uint32_t* nodes, uint32_t* out)
 {
     if (n_nodes < 0 || (n_nodes > 0 && (!nodes || !out))) return PT_EINVAL;
-    std::vector<PackedNode> in((size_t)n_nodes);
+    NodeVec in((size_t)n_nodes);
     if (n_nodes) std::memcpy(in.data(), nodes, (size_t)n_nodes * sizeof(PackedNode));
-    std::vector<QuantNode> q;
+    QuantVec q;
     std::string err;
-    if (!quantize_bvh(in, q, &err)) return PT_EUNSUPPORTED;
+    if (!quantize_bvh(in.data(), in.size(), q, &err)) return PT_EUNSUPPORTED;
     if (n_nodes) std::memcpy(out, q.data(), (size_t)n_nodes * sizeof(QuantNode));
     return PT_OK;
 }

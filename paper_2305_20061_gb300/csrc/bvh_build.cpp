@@ -44,78 +44,156 @@ struct Box {
 };
 
 constexpr int kBins = 16;
+// ranges of at least this many primitives run their split passes on several threads
+constexpr int64_t kParallelPass = (int64_t)1 << 16;
+// ranges of at least this many primitives (above par_depth) hand their left subtree to another thread
+constexpr int64_t kParallelSubtree = (int64_t)1 << 14;
 
-// One primitive's centroid, bounds and input index.  The builder reorders
-// these records themselves (not indices into the input), so every pass over
-// a range reads memory in order.
+// One primitive's bounds and input index; its centroid is the box midpoint.
+// The builder moves these records themselves (not indices into the input),
+// so every pass over a range reads memory in order.
 struct Prim {
-    float cen[3], lo[3], hi[3];
+    float lo[3], hi[3];
     uint32_t id;
+    float cen(int a) const { return 0.5f * (lo[a] + hi[a]); }
+};
+
+struct CenBounds {
+    float lo[3] = {INFINITY, INFINITY, INFINITY};
+    float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    void grow(const Prim& q)
+    {
+        for (int a = 0; a < 3; ++a) {
+            const float c = q.cen(a);
+            lo[a] = std::min(lo[a], c);
+            hi[a] = std::max(hi[a], c);
+        }
+    }
+    void grow(const CenBounds& o)   // o may be empty (lo = +inf, hi = -inf)
+    {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], o.lo[a]);
+            hi[a] = std::max(hi[a], o.hi[a]);
+        }
+    }
+};
+
+struct Bins {
+    Box bb[3][kBins];
+    int64_t cnt[3][kBins] = {};
+};
+
+// What the builders of one tree share.  Each works on its own range [b, e)
+// of the two record buffers and writes its own nodes: a subtree over m
+// primitives holds exactly m - 1 nodes, so where each subtree's nodes go
+// follows from the split counts alone.
+struct Tree {
+    std::vector<Prim, NoInitAlloc<Prim>> buf[2];
+    NodeVec nodes;
+    int par_depth = 0;       // subtrees above this depth may be built on other threads
+    unsigned threads = 1;
 };
 
 struct Builder {
-    std::vector<Prim>& prims;        // shared by the builders of one tree (each works on its own range)
-    std::vector<PackedNode> nodes;
+    Tree& tr;
     int32_t max_depth = 0;
-    int par_depth = 0;               // subtrees above this depth may be built on other threads
     std::string error;
 
-    explicit Builder(std::vector<Prim>& pr) : prims(pr) {}
+    explicit Builder(Tree& t) : tr(t) {}
 
-    Box range_box(int64_t b, int64_t e) const
+    // threads for the passes over a range: the 2^depth ranges of one level above par_depth are split at
+    // the same time, so each takes its share
+    int pass_threads(int64_t n, int depth) const
+    {
+        if (n < kParallelPass || depth >= 16) return 1;
+        return std::max(1, (int)(tr.threads >> depth));
+    }
+
+    static Box range_box(const Prim* P, int64_t b, int64_t e)
     {
         Box bx;
-        for (int64_t i = b; i < e; ++i) bx.grow(prims[i].lo, prims[i].hi);
+        for (int64_t i = b; i < e; ++i) bx.grow(P[i].lo, P[i].hi);
         return bx;
     }
 
-    // choose a split of idx[b, e) (count >= 2): binned SAH over the three axes
-    // (one pass fills the bins of all axes); returns the midpoint and, when
-    // the split came from the bins, the two children's exact boxes
-    int64_t split(int64_t b, int64_t e, Box* bl, Box* br, bool* boxes_known)
+    static CenBounds range_centroids(const Prim* P, int64_t b, int64_t e)
     {
+        CenBounds c;
+        for (int64_t i = b; i < e; ++i) c.grow(P[i]);
+        return c;
+    }
+
+    // choose a split of [b, e) (count >= 2), whose records are in *src: binned SAH over the three axes
+    // (one pass fills the bins of all axes; cb holds the range's centroid bounds), then a partition that
+    // also takes the children's centroid bounds.  Ranges of kParallelPass records or more are partitioned
+    // stably into the other buffer (on several threads where the level has them to spare), which then
+    // holds the children's records (*src is swapped with *dst); smaller ranges in place.  Returns the
+    // midpoint and, when the split came from the bins, the two children's exact boxes and centroid bounds.
+    int64_t split(int64_t b, int64_t e, int depth, const CenBounds& cb, Prim** src, Prim** dst, Box* bl,
+                  Box* br, CenBounds* cl, CenBounds* cr, bool* known)
+    {
+        Prim* P = *src;
         const int64_t n = e - b;
-        *boxes_known = false;
+        *known = false;
         if (n == 2) {
             // two leaves whatever the split; the binned sweep below would order them by centroid along the
             // first axis where the centroids differ (ties: as listed), which this reproduces without the bins
             for (int a = 0; a < 3; ++a) {
-                const float c0 = prims[b].cen[a], c1 = prims[b + 1].cen[a];
+                const float c0 = P[b].cen(a), c1 = P[b + 1].cen(a);
                 if (c0 != c1) {
-                    if (c1 < c0) std::swap(prims[b], prims[b + 1]);
+                    if (c1 < c0) std::swap(P[b], P[b + 1]);
                     break;
                 }
             }
-            bl->grow(prims[b].lo, prims[b].hi);
-            br->grow(prims[b + 1].lo, prims[b + 1].hi);
-            *boxes_known = true;
+            bl->grow(P[b].lo, P[b].hi);
+            br->grow(P[b + 1].lo, P[b + 1].hi);
+            cl->grow(P[b]);
+            cr->grow(P[b + 1]);
+            *known = true;
             return b + 1;
         }
-        float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int64_t i = b; i < e; ++i)
-            for (int a = 0; a < 3; ++a) {
-                const float c = prims[i].cen[a];
-                clo[a] = std::min(clo[a], c);
-                chi[a] = std::max(chi[a], c);
-            }
+        const int T = pass_threads(n, depth);
         float scale[3];
         bool live[3];
         for (int a = 0; a < 3; ++a) {
-            const float ext = chi[a] - clo[a];
+            const float ext = cb.hi[a] - cb.lo[a];
             live[a] = ext > 0.f;
             scale[a] = live[a] ? kBins / ext : 0.f;
         }
-        Box bb[3][kBins];
-        int64_t cnt[3][kBins] = {};
-        for (int64_t i = b; i < e; ++i) {
-            const Prim& q = prims[i];
-            for (int a = 0; a < 3; ++a) {
-                if (!live[a]) continue;
-                int k = (int)((q.cen[a] - clo[a]) * scale[a]);
-                k = std::min(std::max(k, 0), kBins - 1);
-                cnt[a][k]++;
-                bb[a][k].grow(q.lo, q.hi);
+        // bin index along axis a (kept in locals: stores to the bins could otherwise alias cb and scale)
+        struct BinOf {
+            float o[3], s[3];
+            int operator()(const Prim& q, int a) const
+            {
+                const int k = (int)((q.cen(a) - o[a]) * s[a]);
+                return std::min(std::max(k, 0), kBins - 1);
             }
+        };
+        const BinOf bin_of{{cb.lo[0], cb.lo[1], cb.lo[2]}, {scale[0], scale[1], scale[2]}};
+        // bins per chunk, merged in chunk order (exact: integer counts, min and max)
+        Bins bins;
+        {
+            std::vector<Bins> part(T > 1 ? (size_t)T : 0);
+            for_chunks(b, e, T, [&](int t, int64_t lo, int64_t hi) {
+                Bins& acc = T > 1 ? part[t] : bins;
+                const BinOf bo = bin_of;
+                const bool lv[3] = {live[0], live[1], live[2]};
+                for (int64_t i = lo; i < hi; ++i) {
+                    const Prim q = P[i];   // a copy: the bin updates cannot change it
+                    for (int a = 0; a < 3; ++a) {
+                        if (!lv[a]) continue;
+                        const int k = bo(q, a);
+                        acc.cnt[a][k]++;
+                        acc.bb[a][k].grow(q.lo, q.hi);
+                    }
+                }
+            });
+            for (const Bins& p : part)
+                for (int a = 0; a < 3; ++a)
+                    for (int k = 0; k < kBins; ++k) {
+                        bins.cnt[a][k] += p.cnt[a][k];
+                        bins.bb[a][k].grow(p.bb[a][k]);
+                    }
         }
         double best_cost = INFINITY;
         int best_axis = -1, best_bin = -1;
@@ -129,9 +207,9 @@ struct Builder {
             int64_t c = 0;
             double area = 0.0;
             for (int k = 0; k < kBins - 1; ++k) {
-                if (cnt[a][k]) {
-                    acc.grow(bb[a][k]);
-                    c += cnt[a][k];
+                if (bins.cnt[a][k]) {
+                    acc.grow(bins.bb[a][k]);
+                    c += bins.cnt[a][k];
                     area = acc.area();
                 }
                 left_area[k] = area;
@@ -141,9 +219,9 @@ struct Builder {
             int64_t rc = 0;
             double rarea = 0.0;
             for (int k = kBins - 1; k >= 1; --k) {
-                if (cnt[a][k]) {
-                    racc.grow(bb[a][k]);
-                    rc += cnt[a][k];
+                if (bins.cnt[a][k]) {
+                    racc.grow(bins.bb[a][k]);
+                    rc += bins.cnt[a][k];
                     rarea = racc.area();
                 }
                 const int64_t lc = left_cnt[k - 1];
@@ -152,63 +230,113 @@ struct Builder {
                 if (cost < best_cost) { best_cost = cost; best_axis = a; best_bin = k; }
             }
         }
-        int64_t mid;
-        if (best_axis >= 0) {
-            const int a = best_axis;
-            auto it = std::partition(prims.begin() + b, prims.begin() + e, [&](const Prim& q) {
-                int k = (int)((q.cen[a] - clo[a]) * scale[a]);
-                k = std::min(std::max(k, 0), kBins - 1);
-                return k < best_bin;
-            });
-            mid = it - prims.begin();
-            if (mid > b && mid < e) {
-                Box l, r;
-                for (int k = 0; k < kBins; ++k) (k < best_bin ? l : r).grow(bb[a][k]);
-                *bl = l;
-                *br = r;
-                *boxes_known = true;
-                return mid;
+        if (best_axis < 0) return b + n / 2;   // no usable split (all centroids coincide): halve the list
+        const int a = best_axis;
+        int64_t n_left = 0;
+        for (int k = 0; k < best_bin; ++k) n_left += bins.cnt[a][k];
+        const int64_t mid = b + n_left;
+        struct Left {
+            float o, s;
+            int a, bin;
+            bool operator()(const Prim& q) const
+            {
+                const int k = (int)((q.cen(a) - o) * s);
+                return std::min(std::max(k, 0), kBins - 1) < bin;
             }
+        };
+        const Left left{bin_of.o[a], bin_of.s[a], a, best_bin};
+        if (n < kParallelPass) {
+            // in place: swap the first right record from the front with the last left one from the back
+            CenBounds gl, gr;
+            int64_t i = b, j = e - 1;
+            for (;;) {
+                while (i <= j && left(P[i])) gl.grow(P[i++]);
+                while (i <= j && !left(P[j])) gr.grow(P[j--]);
+                if (i >= j) break;
+                std::swap(P[i], P[j]);
+                gl.grow(P[i++]);
+                gr.grow(P[j--]);
+            }
+            *cl = gl;
+            *cr = gr;
+        } else {
+            // stable, into the other buffer: chunk t's left records go to [b + L_t, ...) and its right
+            // records to [mid + R_t, ...), L_t and R_t the counts in the chunks before it
+            Prim* D = *dst;
+            std::vector<int64_t> nl((size_t)T, 0), lo_at((size_t)T), ro_at((size_t)T);
+            if (T > 1)
+                for_chunks(b, e, T, [&](int t, int64_t lo, int64_t hi) {
+                    int64_t c = 0;
+                    for (int64_t i = lo; i < hi; ++i) c += left(P[i]);
+                    nl[t] = c;
+                });
+            else
+                nl[0] = n_left;
+            int64_t l = 0, r = 0;
+            for (int t = 0; t < T; ++t) {
+                lo_at[t] = b + l;
+                ro_at[t] = mid + r;
+                l += nl[t];
+                r += n * (t + 1) / T - n * t / T - nl[t];
+            }
+            std::vector<CenBounds> pl((size_t)T), pr((size_t)T);
+            for_chunks(b, e, T, [&](int t, int64_t lo, int64_t hi) {
+                int64_t wl = lo_at[t], wr = ro_at[t];
+                CenBounds gl, gr;
+                for (int64_t i = lo; i < hi; ++i) {
+                    const Prim q = P[i];
+                    if (left(q)) {
+                        D[wl++] = q;
+                        gl.grow(q);
+                    } else {
+                        D[wr++] = q;
+                        gr.grow(q);
+                    }
+                }
+                pl[t] = gl;
+                pr[t] = gr;
+            });
+            for (int t = 0; t < T; ++t) {
+                cl->grow(pl[t]);
+                cr->grow(pr[t]);
+            }
+            std::swap(*src, *dst);
         }
-        return b + n / 2;   // no usable split (all centroids coincide): halve the list
+        for (int k = 0; k < kBins; ++k) (k < best_bin ? *bl : *br).grow(bins.bb[a][k]);
+        *known = true;
+        return mid;
     }
 
-    // build idx[b, e); returns the child reference
-    uint32_t build(int64_t b, int64_t e, int depth)
+    // build [b, e) (records in src, centroid bounds cb; dst the other buffer) with its first node, if it
+    // has one, at index `at`; returns the child reference.  The nodes are in depth-first order, left
+    // subtree first, whichever thread builds which subtree.
+    uint32_t build(int64_t b, int64_t e, int depth, uint32_t at, const CenBounds& cb, Prim* src, Prim* dst)
     {
         max_depth = std::max(max_depth, depth);
-        if (e - b == 1) return kLeafBit | prims[b].id;
-        const uint32_t me = (uint32_t)nodes.size();
-        nodes.emplace_back();
+        if (e - b == 1) return kLeafBit | src[b].id;
         Box bl, br;
+        CenBounds cbl, cbr;
         bool known = false;
-        const int64_t mid = split(b, e, &bl, &br, &known);
+        const int64_t mid = split(b, e, depth, cb, &src, &dst, &bl, &br, &cbl, &cbr, &known);
         if (!known) {
-            bl = range_box(b, mid);
-            br = range_box(mid, e);
+            bl = range_box(src, b, mid);
+            br = range_box(src, mid, e);
+            cbl = range_centroids(src, b, mid);
+            cbr = range_centroids(src, mid, e);
         }
         uint32_t cl, cr;
-        if (depth < par_depth && e - b >= (int64_t)1 << 14) {
-            // the left subtree on another thread into its own node list, appended after the right one
-            Builder sub(prims);
-            sub.par_depth = par_depth;
-            sub.nodes.reserve((size_t)(mid - b));
+        if (depth < tr.par_depth && e - b >= kParallelSubtree) {
+            Builder sub(tr);
             uint32_t sub_root = kEmptyRef;
-            std::thread th([&] { sub_root = sub.build(b, mid, depth + 1); });
-            cr = build(mid, e, depth + 1);
+            std::thread th([&] { sub_root = sub.build(b, mid, depth + 1, at + 1, cbl, src, dst); });
+            cr = build(mid, e, depth + 1, at + (uint32_t)(mid - b), cbr, src, dst);
             th.join();
-            const uint32_t off = (uint32_t)nodes.size();
-            for (PackedNode nd : sub.nodes) {
-                for (int c = 9; c <= 10; ++c)
-                    if (!(nd.w[c] & kLeafBit)) nd.w[c] += off;
-                nodes.push_back(nd);
-            }
-            cl = (sub_root & kLeafBit) ? sub_root : sub_root + off;
+            cl = sub_root;
             max_depth = std::max(max_depth, sub.max_depth);
             if (!sub.error.empty()) error = sub.error;
         } else {
-            cl = build(b, mid, depth + 1);
-            cr = build(mid, e, depth + 1);
+            cl = build(b, mid, depth + 1, at + 1, cbl, src, dst);
+            cr = build(mid, e, depth + 1, at + (uint32_t)(mid - b), cbr, src, dst);
         }
         if (!error.empty()) return kEmptyRef;
         uint16_t el[3], er[3];
@@ -218,7 +346,7 @@ struct Builder {
                 return kEmptyRef;
             }
         }
-        PackedNode& nd = nodes[me];
+        PackedNode& nd = tr.nodes[at];
         std::memset(&nd, 0, sizeof(nd));
         std::memcpy(&nd.w[0], &bl.lo[0], 4);
         std::memcpy(&nd.w[1], &bl.lo[1], 4);
@@ -232,7 +360,7 @@ struct Builder {
         nd.w[9] = cl;
         nd.w[10] = cr;
         nd.w[11] = 0;
-        return me;
+        return at;
     }
 };
 
@@ -312,63 +440,78 @@ bool quantize_interval(float origin, float lo, float hi, int E, int* qlo, int* q
 
 }  // namespace
 
-bool quantize_bvh(const std::vector<PackedNode>& in, std::vector<QuantNode>& out, std::string* error)
+namespace {
+
+// one node's quantised form; nullptr, or the reason it has none
+const char* quantize_node(const PackedNode& n, QuantNode& o)
 {
-    out.assign(in.size(), QuantNode{});
-    for (size_t i = 0; i < in.size(); ++i) {
-        const PackedNode& n = in[i];
-        float box[12];
-        decode_packed_boxes(n, box);
-        const uint32_t refs[2] = {n.w[9], n.w[10]};
-        for (uint32_t r : refs)
-            if ((r & ~kLeafBit) >= kQuantRefLimit) {
-                if (error) *error = "BVH too large for 24-bit references of quantised nodes";
-                return false;
-            }
-        float origin[3];
-        int e_axis[3];
-        for (int a = 0; a < 3; ++a) {
-            origin[a] = std::min(box[a], box[6 + a]);
-            const double span = std::max((double)box[3 + a], (double)box[9 + a]) - (double)origin[a];
-            // smallest grid step 2^k with 255 steps covering the span (with a little slack for the rounding)
-            int k = span > 0.0 ? (int)std::ceil(std::log2(span * (1.0 + 1e-6) / 255.0)) : -126;
-            e_axis[a] = std::min(std::max(k + 127, 4), 254);
-        }
-        int e = std::max(e_axis[0], std::max(e_axis[1], e_axis[2]));
-        int q[12];
-        for (int guard = 0;; ++guard) {
-            int d[3];
-            bool ok = e <= 254;
-            for (int a = 0; a < 3 && ok; ++a) {
-                d[a] = std::min(3, e - e_axis[a]);
-                for (int c = 0; c < 2 && ok; ++c)
-                    ok = quantize_interval(origin[a], box[6 * c + a], box[6 * c + 3 + a], e - d[a], &q[6 * c + a],
-                                           &q[6 * c + 3 + a]);
-            }
-            if (ok) {
-                QuantNode& o = out[i];
-                for (int a = 0; a < 3; ++a) std::memcpy(&o.w[a], &origin[a], 4);
-                const uint32_t cl = refs[0] & ~kLeafBit, cr = refs[1] & ~kLeafBit;
-                o.w[3] = (uint32_t)e | ((uint32_t)d[0] << 8) | ((uint32_t)d[1] << 10) | ((uint32_t)d[2] << 12) |
-                         ((refs[0] & kLeafBit) ? 1u << 14 : 0u) | ((refs[1] & kLeafBit) ? 1u << 15 : 0u) |
-                         ((cl & 0xFFFFu) << 16);
-                o.w[4] = (cl >> 16) | (cr << 8);
-                for (int j = 0; j < 3; ++j)
-                    o.w[5 + j] = (uint32_t)q[4 * j] | ((uint32_t)q[4 * j + 1] << 8) | ((uint32_t)q[4 * j + 2] << 16) |
-                                 ((uint32_t)q[4 * j + 3] << 24);
-                break;
-            }
-            if (guard > 8 || e >= 254) {
-                if (error) *error = "BVH box does not fit an 8-bit grid";
-                return false;
-            }
-            ++e;   // a coarser grid
-        }
+    float box[12];
+    decode_packed_boxes(n, box);
+    const uint32_t refs[2] = {n.w[9], n.w[10]};
+    for (uint32_t r : refs)
+        if ((r & ~kLeafBit) >= kQuantRefLimit) return "BVH too large for 24-bit references of quantised nodes";
+    float origin[3];
+    int e_axis[3];
+    for (int a = 0; a < 3; ++a) {
+        origin[a] = std::min(box[a], box[6 + a]);
+        const double span = std::max((double)box[3 + a], (double)box[9 + a]) - (double)origin[a];
+        // smallest grid step 2^k with 255 steps covering the span (with a little slack for the rounding)
+        int k = span > 0.0 ? (int)std::ceil(std::log2(span * (1.0 + 1e-6) / 255.0)) : -126;
+        e_axis[a] = std::min(std::max(k + 127, 4), 254);
     }
+    int e = std::max(e_axis[0], std::max(e_axis[1], e_axis[2]));
+    int q[12];
+    for (int guard = 0;; ++guard) {
+        int d[3];
+        bool ok = e <= 254;
+        for (int a = 0; a < 3 && ok; ++a) {
+            d[a] = std::min(3, e - e_axis[a]);
+            for (int c = 0; c < 2 && ok; ++c)
+                ok = quantize_interval(origin[a], box[6 * c + a], box[6 * c + 3 + a], e - d[a], &q[6 * c + a],
+                                       &q[6 * c + 3 + a]);
+        }
+        if (ok) {
+            for (int a = 0; a < 3; ++a) std::memcpy(&o.w[a], &origin[a], 4);
+            const uint32_t cl = refs[0] & ~kLeafBit, cr = refs[1] & ~kLeafBit;
+            o.w[3] = (uint32_t)e | ((uint32_t)d[0] << 8) | ((uint32_t)d[1] << 10) | ((uint32_t)d[2] << 12) |
+                     ((refs[0] & kLeafBit) ? 1u << 14 : 0u) | ((refs[1] & kLeafBit) ? 1u << 15 : 0u) |
+                     ((cl & 0xFFFFu) << 16);
+            o.w[4] = (cl >> 16) | (cr << 8);
+            for (int j = 0; j < 3; ++j)
+                o.w[5 + j] = (uint32_t)q[4 * j] | ((uint32_t)q[4 * j + 1] << 8) | ((uint32_t)q[4 * j + 2] << 16) |
+                             ((uint32_t)q[4 * j + 3] << 24);
+            return nullptr;
+        }
+        if (guard > 8 || e >= 254) return "BVH box does not fit an 8-bit grid";
+        ++e;   // a coarser grid
+    }
+}
+
+}  // namespace
+
+bool quantize_bvh(const PackedNode* in, size_t n, QuantVec& out, std::string* error)
+{
+    out.resize(n);
+    const int T = host_pass_threads((int64_t)n);
+    std::vector<int64_t> bad((size_t)T, -1);   // each chunk's first failing node
+    std::vector<const char*> why((size_t)T, nullptr);
+    for_chunks(0, (int64_t)n, T, [&](int t, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i)
+            if (const char* w = quantize_node(in[i], out[(size_t)i])) {
+                bad[t] = i;
+                why[t] = w;
+                return;
+            }
+    });
+    for (int t = 0; t < T; ++t)
+        if (bad[t] >= 0) {
+            if (error) *error = why[t];
+            return false;
+        }
     return true;
 }
 
-bool build_bvh(const BuildInput& in, BuildOutput& out)
+bool build_bvh(const BuildInput& in, BuildOutput& out, unsigned threads)
 {
     out.nodes.clear();
     out.depth = 0;
@@ -376,26 +519,35 @@ bool build_bvh(const BuildInput& in, BuildOutput& out)
         out.root = kEmptyRef;
         return true;
     }
-    std::vector<Prim> prims((size_t)in.n_prims);
-    for (int64_t i = 0; i < in.n_prims; ++i) {
-        Prim& q = prims[(size_t)i];
-        for (int a = 0; a < 3; ++a) {
-            q.cen[a] = in.cen[3 * i + a];
-            q.lo[a] = in.lo[3 * i + a];
-            q.hi[a] = in.hi[3 * i + a];
+    const int64_t n = in.n_prims;
+    Tree tr;
+    tr.threads = threads ? threads : std::max(1u, std::thread::hardware_concurrency());
+    while ((1u << tr.par_depth) < 2 * tr.threads && tr.par_depth < 8) ++tr.par_depth;   // about two subtrees per core
+    tr.buf[0].resize((size_t)n);
+    tr.buf[1].resize((size_t)n);
+    tr.nodes.resize((size_t)std::max<int64_t>(n - 1, 0));
+    const int T = n >= kParallelPass ? (int)tr.threads : 1;
+    std::vector<CenBounds> part((size_t)T);
+    for_chunks(0, n, T, [&](int t, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) {
+            Prim& q = tr.buf[0][(size_t)i];
+            for (int a = 0; a < 3; ++a) {
+                q.lo[a] = in.lo[3 * i + a];
+                q.hi[a] = in.hi[3 * i + a];
+            }
+            q.id = (uint32_t)i;
+            part[t].grow(q);
         }
-        q.id = (uint32_t)i;
-    }
-    Builder bd(prims);
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    while ((1u << bd.par_depth) < 2 * hw && bd.par_depth < 8) ++bd.par_depth;   // about two subtrees per core
-    bd.nodes.reserve((size_t)std::max<int64_t>(in.n_prims - 1, 1));
-    out.root = bd.build(0, in.n_prims, 0);
+    });
+    CenBounds cb;
+    for (const CenBounds& p : part) cb.grow(p);
+    Builder bd(tr);
+    out.root = bd.build(0, n, 0, 0, cb, tr.buf[0].data(), tr.buf[1].data());
     if (!bd.error.empty()) {
         out.error = bd.error;
         return false;
     }
-    out.nodes = std::move(bd.nodes);
+    out.nodes = std::move(tr.nodes);
     out.depth = bd.max_depth;
     return true;
 }

@@ -4,7 +4,12 @@
 
 #include <atomic>
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
+#include <thread>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -309,24 +314,66 @@ const DevScene* scene_view(const pt_scene* s, int* device);
 const DevNif* nif_view(const pt_nif* n);
 
 // host BVH builder (bvh_build.cpp)
+
+// An allocator whose value-initialisation leaves trivially constructible
+// elements as they are, so the builder's arrays of tens of millions of
+// records are not zeroed serially before its threads fill them.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind { using other = NoInitAlloc<U>; };
+    NoInitAlloc() = default;
+    template <class U>
+    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+    template <class U>
+    void construct(U* p) noexcept(std::is_nothrow_default_constructible<U>::value) { ::new ((void*)p) U; }
+    template <class U, class... A>
+    void construct(U* p, A&&... a) { ::new ((void*)p) U(std::forward<A>(a)...); }
+};
+using NodeVec = std::vector<PackedNode, NoInitAlloc<PackedNode>>;
+
+// f(t, lo, hi) over T contiguous chunks [b + n t / T, b + n (t + 1) / T) of [b, e), one host thread each
+// (the caller runs chunk 0)
+template <class F>
+void for_chunks(int64_t b, int64_t e, int T, F&& f)
+{
+    const int64_t n = e - b;
+    if (T <= 1) {
+        f(0, b, e);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve((size_t)T - 1);
+    for (int t = 1; t < T; ++t) th.emplace_back([&f, t, b, n, T] { f(t, b + n * t / T, b + n * (t + 1) / T); });
+    f(0, b, b + n / T);
+    for (auto& x : th) x.join();
+}
+// host threads for a pass over n records: all hardware threads from 2^16 records up, else one
+inline int host_pass_threads(int64_t n)
+{
+    return n >= ((int64_t)1 << 16) ? (int)std::max(1u, std::thread::hardware_concurrency()) : 1;
+}
+using QuantVec = std::vector<QuantNode, NoInitAlloc<QuantNode>>;
+
 struct BuildInput {
     int64_t n_prims;
-    std::vector<float> lo, hi;  // [n][3] primitive bounds
-    std::vector<float> cen;     // [n][3] centroids
+    std::vector<float> lo, hi;  // [n][3] primitive bounds (the builder splits on the box midpoints)
 };
 struct BuildOutput {
-    std::vector<PackedNode> nodes;
+    NodeVec nodes;
     uint32_t root = kEmptyRef;
     int32_t depth = 0;
     std::string error;
 };
-bool build_bvh(const BuildInput& in, BuildOutput& out);
+// threads = 0: all hardware threads; the tree does not depend on the count
+bool build_bvh(const BuildInput& in, BuildOutput& out, unsigned threads = 0);
 bool round_up_half_extent(float lo, float hi, uint16_t* out_bits);
 // The packed tree's children boxes as decoded on the device (fp32 origin + fp16 extent, fp32 sum):
 // box[0..2] lo_l, [3..5] hi_l, [6..8] lo_r, [9..11] hi_r.
 void decode_packed_boxes(const PackedNode& n, float box[12]);
-// Quantised form of a packed tree (same node order and references); false with *error set when a
-// reference or primitive ID does not fit 24 bits.
-bool quantize_bvh(const std::vector<PackedNode>& in, std::vector<QuantNode>& out, std::string* error);
+// Quantised form of a packed tree of n nodes (same node order and references; nodes on all hardware
+// threads); false with *error set (the first failing node's reason) when a reference or primitive ID does
+// not fit 24 bits or a box does not fit the grid.
+bool quantize_bvh(const PackedNode* in, size_t n, QuantVec& out, std::string* error);
 
 }  // namespace ptk

@@ -133,3 +133,51 @@ def test_inverted_box_is_refused(pt):
     # a flat box (lo == hi) is fine
     nodes, root, _ = pt.build_bvh_host(lo, np.array([[1, 1, 1], [2, 1, 2]], np.float32))
     assert len(nodes) == 1
+
+
+def _check_large_tree(nodes, root, depth, lo, hi):
+    """check_tree for large inputs: children follow their parent (depth-first
+    order), every primitive and node is reached once, and each stored child
+    box, decoded as the traversal decodes it, contains its subtree."""
+    n = len(lo)
+    assert len(nodes) == n - 1 and root == 0
+    refs = nodes[:, 9:11].astype(np.int64)
+    leaf = (refs & LEAF) != 0
+    idx = refs & ~LEAF
+    assert np.array_equal(np.sort(idx[leaf]), np.arange(n))
+    assert np.array_equal(np.sort(idx[~leaf]), np.arange(1, n - 1))
+    parent = np.repeat(np.arange(n - 1), 2).reshape(-1, 2)
+    assert np.all(idx[~leaf] > parent[~leaf])
+    assert np.all(idx[:, 0][~leaf[:, 0]] == np.arange(n - 1)[~leaf[:, 0]] + 1)   # left subtree first
+    origin = nodes[:, 0:6].view(np.float32).reshape(-1, 2, 3)
+    ext = np.stack([nodes[:, 6] & 0xFFFF, nodes[:, 6] >> 16, nodes[:, 7] & 0xFFFF, nodes[:, 7] >> 16,
+                    nodes[:, 8] & 0xFFFF, nodes[:, 8] >> 16], 1).astype(np.uint16).view(np.float16)
+    top = origin + ext.astype(np.float32).reshape(-1, 2, 3)       # the FP32 add of the traversal
+    sub_lo = np.zeros((n - 1, 3), np.float32)
+    sub_hi = np.zeros((n - 1, 3), np.float32)
+    dep = np.zeros(n - 1, np.int64)
+    for i in range(n - 2, -1, -1):                                 # children have larger indices
+        blo, bhi, d = np.full(3, np.inf, np.float32), np.full(3, -np.inf, np.float32), 0
+        for c in range(2):
+            j = idx[i, c]
+            clo, chi, cd = (lo[j], hi[j], 0) if leaf[i, c] else (sub_lo[j], sub_hi[j], dep[j])
+            assert np.all(origin[i, c] <= clo) and np.all(top[i, c] >= chi), (i, c)
+            blo, bhi, d = np.minimum(blo, clo), np.maximum(bhi, chi), max(d, cd + 1)
+        sub_lo[i], sub_hi[i], dep[i] = blo, bhi, d
+    assert dep[0] == depth
+
+
+@pytest.mark.parametrize("case", ["heightfield", "coincident"])
+def test_large_inputs_split_on_several_threads(pt, case):
+    """Inputs above 2^16 primitives, whose upper splits bin and partition on
+    several host threads into a second record buffer: a valid tree in
+    depth-first order, the same on every call."""
+    if case == "heightfield":
+        lo, hi = _tri_bounds(I.heightfield_scene(200))            # 80,000 triangles
+    else:                                                          # the halving fallback on large ranges
+        c = np.repeat(np.float32([0, 1]), [70000, 30000])[:, None] * np.ones((1, 3), np.float32)
+        lo, hi = c - 0.25, c + 0.25
+    nodes, root, depth = pt.build_bvh_host(lo, hi)
+    _check_large_tree(nodes, root, depth, lo, hi)
+    again = pt.build_bvh_host(lo, hi)
+    assert np.array_equal(nodes, again[0]) and root == again[1] and depth == again[2]
