@@ -69,21 +69,23 @@ def shade_bytes(counts, depth: int, emits: bool) -> int:
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) of the traversal kernel per traced ray, from one ncu capture of the workload's frame
 # (or a smaller frame of it) (summaries and commands in profiles/), scaled to a frame by the rays it traces.  Valid only
-# while the traversal source is the one captured (sha256 of trace.cu + device_common.cuh, first 16 hex digits).
+# while the traversal source and the BVH builder are the ones captured (sha256 of trace.cu + device_common.cuh +
+# bvh_build.cpp, first 16 hex digits): the bytes depend on the kernel and on the tree it walks.
 TRACE_TRAFFIC = {
     # 1920x1080 at 8 spp = one full 2^24-path chunk of the 32-spp frame (profiles/k_trace_traffic_large_bvh_c4.md)
-    ("C4", "packed"): {"bytes_per_ray": 365.1, "src": "7d34db8adafd2d1d"},
-    ("C4", "quant8"): {"bytes_per_ray": 283.6, "src": "7d34db8adafd2d1d"},
+    ("C4", "packed"): {"bytes_per_ray": 365.7, "src": "1b0e9acfff431087"},
+    ("C4", "quant8"): {"bytes_per_ray": 283.6, "src": "1b0e9acfff431087"},
     # 512x512 at 64 spp, the full frame, one pass per launch (profiles/k_trace_traffic_spheres_c2.md)
-    ("C2", "decoded"): {"bytes_per_ray": 22.71, "src": "7d34db8adafd2d1d"},
+    ("C2", "decoded"): {"bytes_per_ray": 22.72, "src": "1b0e9acfff431087"},
 }
 # L2 bytes (lts__t_bytes) of the traversal kernel per traced ray on the large tree, from the same captures
 TRACE_L2 = {
-    ("C4", "packed"): {"bytes_per_ray": 1707.0, "src": "7d34db8adafd2d1d"},
-    ("C4", "quant8"): {"bytes_per_ray": 1322.0, "src": "7d34db8adafd2d1d"},
+    ("C4", "packed"): {"bytes_per_ray": 1695.6, "src": "1b0e9acfff431087"},
+    ("C4", "quant8"): {"bytes_per_ray": 1322.5, "src": "1b0e9acfff431087"},
 }
 NODE_FORMS = {1: "packed", 2: "decoded", 3: "quant8"}
-TRACE_SOURCES = ("paper_2305_20061_gb300/csrc/trace.cu", "paper_2305_20061_gb300/csrc/device_common.cuh")
+TRACE_SOURCES = ("paper_2305_20061_gb300/csrc/trace.cu", "paper_2305_20061_gb300/csrc/device_common.cuh",
+                 "paper_2305_20061_gb300/csrc/bvh_build.cpp")
 
 
 def trace_source_hash() -> str:
@@ -105,7 +107,7 @@ def trace_l2_bytes(workload: str, node_form: str, rays: int):
 
 def trace_traffic(workload: str, node_form: str, rays: int):
     """DRAM bytes of the traversal kernel over a frame of `rays` traced rays, or None when no capture of
-    this workload and node form exists or the traversal source changed since it was taken."""
+    this workload and node form exists or the traversal source or the BVH builder changed since it was taken."""
     rec = TRACE_TRAFFIC.get((workload, node_form))
     if rec is None or rec["src"] != trace_source_hash():
         return None
