@@ -297,7 +297,10 @@ PT_API pt_status pt_nif_loss_grad(pt_ctx* ctx, pt_nif* nif, int64_t n, const flo
    same paths bit for bit (same Philox counters, traversal and shading); only
    the order of the NIF escape and cache query queues differs.
    WAVEFRONT: one traversal and one shading launch per vertex, with compacted
-   queues between vertices (throughput for large chunks).
+   queues between vertices (throughput for large chunks).  The camera rays of
+   a whole image (no pixel list, width % 8 == 0, height % 4 == 0) walk the
+   upper tree as warp packets of 8 x 4 pixels: the same hits, but the
+   traversal work of pt_last_render_work follows the packets' visiting order.
    PATHS: one launch in which each thread follows whole paths (latency for
    chunks that fit in one resident wave: a call pays for its slowest path once
    instead of for the slowest ray of every vertex).
@@ -367,7 +370,9 @@ PT_API pt_status pt_last_render_schedule(pt_ctx* ctx, int32_t* schedule);
 
 /* Traversal work of the last render (valid after pt_check): work[0] BVH
    node fetches (each tests the two child boxes), work[1] sphere, work[2]
-   quad, work[3] triangle intersection tests.  Writes min(n, 4) values. */
+   quad, work[3] triangle intersection tests, summed over rays (a node that a
+   warp packet visits counts once for each lane whose ray entered it).
+   Writes min(n, 4) values. */
 PT_API pt_status pt_last_render_work(pt_ctx* ctx, int64_t* work, int32_t n);
 
 /* Kernel timing.  While enabled, the library records a CUDA event pair on

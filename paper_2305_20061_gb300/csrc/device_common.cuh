@@ -264,17 +264,16 @@ constexpr int kNodesPacked = 0, kNodesWide = 1, kNodesQuant = 2;
 // byte k (0..3) of w as a float
 __device__ __forceinline__ float byte_f(uint32_t w, int k) { return (float)((w >> (8 * k)) & 0xFFu); }
 
+// Node `cur`'s two child references and the entry distances of the ray
+// (origin o, reciprocal direction inv) into their boxes, +inf for a box
+// missed or entered beyond tbest.
 template <int kForm>
-__device__ __forceinline__ bool trav_step(const DevScene& sc, Trav& s, uint32_t* stack_ref, float* stack_t,
-                                          uint32_t* err, Work& w)
+__device__ __forceinline__ void node_children(const DevScene& sc, uint32_t cur, float3 o, float3 inv, float tbest,
+                                              uint32_t& cl, uint32_t& cr, float& tl, float& trr)
 {
-    if (++s.iters > kIterCap) { atomicOr(err, PT_ERR_ITER_CAP); return true; }
-    if (s.cur >= sc.n_nodes) { atomicOr(err, PT_ERR_BAD_NODE); return true; }  // never fetch outside the node array
-    uint32_t cl, cr;
-    float tl, trr;
     if (kForm == kNodesQuant) {
         // 8-bit grid boxes: bound = origin + q * 2^(e - 127 - d_axis), exact product, one rounding
-        const uint4* np = sc.qnodes + 2 * (size_t)s.cur;
+        const uint4* np = sc.qnodes + 2 * (size_t)cur;
         const uint4 q0 = __ldg(np), q1 = __ldg(np + 1);
         const float3 org = f3(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z));
         const uint32_t meta = q0.w, e = meta & 0xFFu;
@@ -291,11 +290,11 @@ __device__ __forceinline__ bool trav_step(const DevScene& sc, Trav& s, uint32_t*
                                fmaf(byte_f(q1.w, 0), step.z, org.z));
         const float3 hi_r = f3(fmaf(byte_f(q1.w, 1), step.x, org.x), fmaf(byte_f(q1.w, 2), step.y, org.y),
                                fmaf(byte_f(q1.w, 3), step.z, org.z));
-        tl = slab_box(lo_l, hi_l, s.o, s.inv, s.h.t);
-        trr = slab_box(lo_r, hi_r, s.o, s.inv, s.h.t);
+        tl = slab_box(lo_l, hi_l, o, inv, tbest);
+        trr = slab_box(lo_r, hi_r, o, inv, tbest);
     } else if (kForm == kNodesWide) {
         // decoded boxes: the same bounds the packed form decodes to, without the fp16 conversions
-        const uint4* np = sc.wnodes + 4 * (size_t)s.cur;
+        const uint4* np = sc.wnodes + 4 * (size_t)cur;
         const uint4 q0 = __ldg(np), q1 = __ldg(np + 1), q2 = __ldg(np + 2), q3 = __ldg(np + 3);
         const float3 lo_l = f3(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z));
         const float3 hi_l = f3(__uint_as_float(q0.w), __uint_as_float(q1.x), __uint_as_float(q1.y));
@@ -303,10 +302,10 @@ __device__ __forceinline__ bool trav_step(const DevScene& sc, Trav& s, uint32_t*
         const float3 hi_r = f3(__uint_as_float(q2.y), __uint_as_float(q2.z), __uint_as_float(q2.w));
         cl = q3.x;
         cr = q3.y;
-        tl = slab_box(lo_l, hi_l, s.o, s.inv, s.h.t);
-        trr = slab_box(lo_r, hi_r, s.o, s.inv, s.h.t);
+        tl = slab_box(lo_l, hi_l, o, inv, tbest);
+        trr = slab_box(lo_r, hi_r, o, inv, tbest);
     } else {
-        const uint4* np = sc.nodes + 3 * (size_t)s.cur;
+        const uint4* np = sc.nodes + 3 * (size_t)cur;
         const uint4 q0 = __ldg(np), q1 = __ldg(np + 1), q2 = __ldg(np + 2);
         const float3 lo_l = f3(__uint_as_float(q0.x), __uint_as_float(q0.y), __uint_as_float(q0.z));
         const float3 lo_r = f3(__uint_as_float(q0.w), __uint_as_float(q1.x), __uint_as_float(q1.y));
@@ -316,9 +315,20 @@ __device__ __forceinline__ bool trav_step(const DevScene& sc, Trav& s, uint32_t*
                                 half_bits_to_float(q2.x >> 16));
         cl = q2.y;
         cr = q2.z;
-        tl = slab(lo_l, ext_l, s.o, s.inv, s.h.t);
-        trr = slab(lo_r, ext_r, s.o, s.inv, s.h.t);
+        tl = slab(lo_l, ext_l, o, inv, tbest);
+        trr = slab(lo_r, ext_r, o, inv, tbest);
     }
+}
+
+template <int kForm>
+__device__ __forceinline__ bool trav_step(const DevScene& sc, Trav& s, uint32_t* stack_ref, float* stack_t,
+                                          uint32_t* err, Work& w)
+{
+    if (++s.iters > kIterCap) { atomicOr(err, PT_ERR_ITER_CAP); return true; }
+    if (s.cur >= sc.n_nodes) { atomicOr(err, PT_ERR_BAD_NODE); return true; }  // never fetch outside the node array
+    uint32_t cl, cr;
+    float tl, trr;
+    node_children<kForm>(sc, s.cur, s.o, s.inv, s.h.t, cl, cr, tl, trr);
     ++w.nodes;
     // leaf children are intersected right away
     if ((cl & kLeafBit) && tl < INFINITY) {

@@ -271,6 +271,143 @@ __global__ void __launch_bounds__(256, PT_TRACE_MIN_BLOCKS) k_trace(const Bounce
     }
 }
 
+// Camera rays (vertex 1) of a whole image traced as warp packets.  The 32
+// rays a warp takes together are an 8 x 4 pixel tile of one sample
+// (tile_slot), close enough in origin and direction to walk the upper tree
+// together: the warp visits every node that any of its rays enters, fetching
+// each once for all lanes, and each lane tests its own ray against the node's
+// two child boxes.  The near child is the one most of the lanes that enter a
+// child reach first; the other is stacked with each lane's own entry
+// distance, and a stacked node is visited while any lane still needs it.
+// Once fewer than PT_PACKET_MIN_LANES lanes enter the current node (the rays
+// part near the leaves of a large tree), each lane finishes on its own from
+// that state with the per-ray step.  The closest hit does not depend on the
+// order of the visits (boxes are entered at equal distance, equal distances
+// go to the lower primitive ID), and a lane only finds hits inside every box
+// above them, so the hits equal those of the per-ray traversal bit for bit.
+// Work counts only the nodes a lane's own ray entered.
+#ifndef PT_TRACE_CAMERA_PACKETS
+#define PT_TRACE_CAMERA_PACKETS 1
+#endif
+// below this many lanes entering the current node, each lane goes on alone
+#ifndef PT_PACKET_MIN_LANES
+#define PT_PACKET_MIN_LANES 24
+#endif
+constexpr uint32_t kCameraClaim = 128;   // camera rays claimed per warp atomic (four packets)
+
+template <int kForm>
+__global__ void __launch_bounds__(256, PT_TRACE_MIN_BLOCKS) k_trace_camera(const BounceParams p)
+{
+    const uint32_t count = p.n_chunk;
+    const uint32_t lane = threadIdx.x & 31;
+    Work work;
+    uint32_t stack_ref[kStackSize];
+    float stack_t[kStackSize];
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(p.fetch, kCameraClaim);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= count) break;
+        for (uint32_t pk = base; pk < base + kCameraClaim && pk < count; pk += 32) {
+            const uint32_t idx = pk + lane;
+            const bool valid = idx < count;
+            uint32_t ri = 0;
+            float3 o = f3(p.sc.eye[0], p.sc.eye[1], p.sc.eye[2]), d = f3(0.f, 0.f, 1.f);
+            if (valid) {
+                ri = tile_slot(p, idx);   // hits are stored per slot
+                uint32_t pix, smp;
+                slot_to_pixel(p, ri, pix, smp);
+                const uint4 w = philox4x32_10(make_uint4(pix, smp, 0u, 0u), p.seed, 0u);
+                d = camera_dir(p.sc, p.W, p.H, pix, u01(w.x), u01(w.y));
+            }
+            Trav t;
+            bool done = trav_init(p.sc, o, d, t, work);   // the same for every lane: empty tree or one leaf
+            if (!valid) t.h.t = -1.f;                      // a lane without a ray enters no box
+            uint32_t cur = t.cur;
+            int sp = 0;
+            uint32_t iters = 0;
+            bool need = valid;   // this lane's ray entered `cur`
+            bool split = false;  // too few lanes left on one path: each lane goes on alone
+            while (!done) {
+                if (__popc(__ballot_sync(0xFFFFFFFFu, need)) < PT_PACKET_MIN_LANES) { split = true; break; }
+                if (++iters > kIterCap) { if (lane == 0) atomicOr(p.err, PT_ERR_ITER_CAP); break; }
+                if (cur >= p.sc.n_nodes) { if (lane == 0) atomicOr(p.err, PT_ERR_BAD_NODE); break; }
+                uint32_t cl, cr;
+                float tl, trr;
+                node_children<kForm>(p.sc, cur, t.o, t.inv, t.h.t, cl, cr, tl, trr);
+                if (need) ++work.nodes;
+                if ((cl & kLeafBit) && tl < INFINITY) {
+                    isect_prim(p.sc, cl & ~kLeafBit, t.o, t.d, t.tr, t.h.t, t.h.prim, work);
+                    tl = INFINITY;
+                }
+                if ((cr & kLeafBit) && trr < INFINITY) {
+                    isect_prim(p.sc, cr & ~kLeafBit, t.o, t.d, t.tr, t.h.t, t.h.prim, work);
+                    trr = INFINITY;
+                }
+                const bool hl = tl < INFINITY && tl <= t.h.t, hr = trr < INFINITY && trr <= t.h.t;
+                const unsigned bl = __ballot_sync(0xFFFFFFFFu, hl), br = __ballot_sync(0xFFFFFFFFu, hr);
+                if (bl && br) {
+                    const unsigned pref = __ballot_sync(0xFFFFFFFFu, hl && (!hr || tl <= trr));
+                    const bool left_first = 2 * __popc(pref) >= __popc(bl | br);
+                    if (sp >= kStackSize) { if (lane == 0) atomicOr(p.err, PT_ERR_STACK_OVERFLOW); break; }
+                    stack_ref[sp] = left_first ? cr : cl;
+                    stack_t[sp] = left_first ? (hr ? trr : INFINITY) : (hl ? tl : INFINITY);
+                    ++sp;
+                    cur = left_first ? cl : cr;
+                    need = left_first ? hl : hr;
+                } else if (bl) {
+                    cur = cl;
+                    need = hl;
+                } else if (br) {
+                    cur = cr;
+                    need = hr;
+                } else {
+                    done = true;
+                    while (sp > 0) {
+                        --sp;
+                        const bool want = stack_t[sp] <= t.h.t;
+                        if (__any_sync(0xFFFFFFFFu, want)) {
+                            cur = stack_ref[sp];
+                            need = want;
+                            done = false;
+                            break;
+                        }
+                    }
+                }
+            }
+            if (split && valid) {
+                // the rest of this lane's traversal on its own: from `cur` if its ray entered it, else from
+                // the nearest stacked node it still needs (the stack holds its own entry distances)
+                bool alive = need;
+                while (!alive && sp > 0) {
+                    --sp;
+                    if (stack_t[sp] <= t.h.t) { cur = stack_ref[sp]; alive = true; }
+                }
+                if (alive) {
+                    t.cur = cur;
+                    t.sp = sp;
+                    t.iters = iters;
+                    while (!trav_step<kForm>(p.sc, t, stack_ref, stack_t, p.err, work)) {
+                    }
+                }
+            }
+            if (valid) p.hits[ri] = make_int2(__float_as_int(t.h.t), t.h.prim);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        work.nodes += __shfl_down_sync(0xFFFFFFFFu, work.nodes, off);
+        work.sph += __shfl_down_sync(0xFFFFFFFFu, work.sph, off);
+        work.quad += __shfl_down_sync(0xFFFFFFFFu, work.quad, off);
+        work.tri += __shfl_down_sync(0xFFFFFFFFu, work.tri, off);
+    }
+    if (lane == 0 && p.work && work.nodes + work.sph + work.quad + work.tri) {
+        atomicAdd(&p.work[0], (unsigned long long)work.nodes);
+        atomicAdd(&p.work[1], (unsigned long long)work.sph);
+        atomicAdd(&p.work[2], (unsigned long long)work.quad);
+        atomicAdd(&p.work[3], (unsigned long long)work.tri);
+    }
+}
+
 // Lanes that arrive here together take consecutive slots of a queue with one
 // atomic; returns this lane's slot.
 __device__ __forceinline__ uint32_t active_append(uint32_t* counter)
@@ -586,10 +723,19 @@ int grid_for(int64_t n, int block, int sm_count, int per_sm)
 
 cudaError_t launch_trace(const BounceParams& p, int sm_count, cudaStream_t s)
 {
-    // traversal: persistent, 4 resident blocks of 256 threads per SM
-    if (p.sc.qnodes) k_trace<kNodesQuant><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
-    else if (p.sc.wnodes) k_trace<kNodesWide><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
-    else k_trace<kNodesPacked><<<sm_count * PT_TRACE_MIN_BLOCKS, 256, 0, s>>>(p);
+    // traversal: persistent, 4 resident blocks of 256 threads per SM; camera rays as warp packets
+    const int grid = sm_count * PT_TRACE_MIN_BLOCKS;
+    if (PT_TRACE_CAMERA_PACKETS && p.k == 1 && p.tiled) {
+        if (p.sc.qnodes) k_trace_camera<kNodesQuant><<<grid, 256, 0, s>>>(p);
+        else if (p.sc.wnodes) k_trace_camera<kNodesWide><<<grid, 256, 0, s>>>(p);
+        else k_trace_camera<kNodesPacked><<<grid, 256, 0, s>>>(p);
+    } else if (p.sc.qnodes) {
+        k_trace<kNodesQuant><<<grid, 256, 0, s>>>(p);
+    } else if (p.sc.wnodes) {
+        k_trace<kNodesWide><<<grid, 256, 0, s>>>(p);
+    } else {
+        k_trace<kNodesPacked><<<grid, 256, 0, s>>>(p);
+    }
     count_launch();
     return cudaGetLastError();
 }

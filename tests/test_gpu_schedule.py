@@ -2,10 +2,13 @@
 paths: the wavefront schedule (one traversal and one shading launch per
 vertex, compacted queues between them) and the path-per-thread schedule (one
 launch, each thread follows whole paths).  Per-path radiance, hit IDs,
-vertex records, ray and work counts agree bit for bit across scenes with
-spheres, quads and triangles, NIF and constant environments, emitters,
-Russian roulette, the BF16 NIF and the radiance cache; both agree with the
-FP64 oracle per path."""
+vertex records and ray counts agree bit for bit across scenes with spheres,
+quads and triangles, NIF and constant environments, emitters, Russian
+roulette, the BF16 NIF and the radiance cache; both agree with the FP64
+oracle per path.  The traversal work agrees bit for bit where both
+schedules trace every ray on its own (pixel lists); a whole image's camera
+rays walk the tree as warp packets in the wavefront schedule, whose work
+counts test_gpu_work_counts checks."""
 import ctypes
 
 import numpy as np
@@ -34,15 +37,16 @@ def ctx(pt):
 
 
 def _both(pt, ctx, fn):
-    """Run fn(schedule) for both schedules; also the traversal counters."""
-    out = {}
+    """Run fn(schedule) for both schedules: the outputs with the ray counts per
+    vertex, and the traversal work."""
+    out, work = {}, {}
     for sched in ("wavefront", "paths"):
         r = fn(sched)
         ctx.check()
         out[sched] = [None if x is None else x.cpu().numpy() for x in r] + \
-                     [pt.last_render_counts(ctx, r[-1].shape[-1] if r[-1] is not None else 1),
-                      np.array(list(pt.last_render_work(ctx).values()))]
-    return out["wavefront"], out["paths"]
+                     [pt.last_render_counts(ctx, r[-1].shape[-1] if r[-1] is not None else 1)]
+        work[sched] = pt.last_render_work(ctx)
+    return out["wavefront"], out["paths"], work["wavefront"], work["paths"]
 
 
 SCENES = {
@@ -55,17 +59,24 @@ SCENES = {
 }
 
 
+@pytest.mark.parametrize("as_list", [False, True])
 @pytest.mark.parametrize("name", list(SCENES))
-def test_schedules_bit_identical(pt, ctx, name):
+def test_schedules_bit_identical(pt, ctx, name, as_list):
+    """The whole image (camera rays in warp packets in the wavefront
+    schedule), and every pixel as a list (every ray on its own in both
+    schedules: the same work too)."""
     make, cfg, env = SCENES[name]
     sc = make()
     s = pt.Scene(ctx, sc)
     g = pt.Nif(ctx, I.nif_init()) if env == "nif" else None
-    a, b = _both(pt, ctx, lambda sched: pt.render_pixels(ctx, s, g, cfg, None, want_slots=True, want_ids=True,
-                                                         schedule=sched))
+    pix = torch.arange(cfg.width * cfg.height, dtype=torch.int64, device="cuda") if as_list else None
+    a, b, wa, wb = _both(pt, ctx, lambda sched: pt.render_pixels(ctx, s, g, cfg, pix, want_slots=True,
+                                                                 want_ids=True, schedule=sched))
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
-    assert a[-2][0] == cfg.width * cfg.height * cfg.spp   # every path traced its primary ray
+    assert a[-1][0] == cfg.width * cfg.height * cfg.spp   # every path traced its primary ray
+    if as_list:
+        assert wa == wb
 
 
 def test_schedules_bit_identical_bf16_nif(pt, ctx):
@@ -74,8 +85,8 @@ def test_schedules_bit_identical_bf16_nif(pt, ctx):
     s = pt.Scene(ctx, I.make_scene("C1"))
     g = pt.Nif(ctx, I.nif_init(colour="yuv"))
     cfg = I.RenderCfg(64, 48, 2, 4)
-    a, b = _both(pt, ctx, lambda sched: pt.render_pixels(ctx, s, g, cfg, None, precision="bf16", want_slots=True,
-                                                         want_ids=True, schedule=sched))
+    a, b, _, _ = _both(pt, ctx, lambda sched: pt.render_pixels(ctx, s, g, cfg, None, precision="bf16",
+                                                               want_slots=True, want_ids=True, schedule=sched))
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
 
@@ -89,11 +100,12 @@ def test_schedules_bit_identical_cached_with_records(pt, ctx, precision):
     s, g, gc = pt.Scene(ctx, sc), pt.Nif(ctx, I.nif_init(colour="yuv")), pt.Cache(ctx, c)
     cfg = I.RenderCfg(64, 64, 3, 5)
     pixels = torch.from_numpy(np.arange(0, 64 * 64, 5, dtype=np.int64)).cuda()
-    a, b = _both(pt, ctx, lambda sched: pt.render_cached(ctx, s, g, cfg, pixels, cache=gc, cache_vertex=2,
-                                                         rec_vertex=1, precision=precision, want_slots=True,
-                                                         want_ids=True, schedule=sched))
+    a, b, wa, wb = _both(pt, ctx, lambda sched: pt.render_cached(ctx, s, g, cfg, pixels, cache=gc, cache_vertex=2,
+                                                                 rec_vertex=1, precision=precision, want_slots=True,
+                                                                 want_ids=True, schedule=sched))
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+    assert wa == wb
 
 
 def test_paths_schedule_beyond_one_wave_and_chunked(pt, ctx):
