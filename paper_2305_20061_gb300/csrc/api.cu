@@ -26,7 +26,7 @@ struct pt_ctx {
     // wavefront scratch
     uint32_t chunk_cap = 0;
     RayQueue q[2] = {};
-    EscapeRec* esc = nullptr;
+    EscapeQueue esc = {};
     float* slot_L = nullptr;
     uint32_t* counters = nullptr;          // [kCounters]
     unsigned long long* stats = nullptr;   // [kMaxDepth + 1]
@@ -176,7 +176,7 @@ void free_scratch(pt_ctx* ctx)
         cudaFree(q.o); cudaFree(q.d); cudaFree(q.tp); cudaFree(q.L);
         q = RayQueue{};
     }
-    cudaFree(ctx->esc); ctx->esc = nullptr;
+    cudaFree(ctx->esc.uv); cudaFree(ctx->esc.tp); ctx->esc = EscapeQueue{};
     cudaFree(ctx->slot_L); ctx->slot_L = nullptr;
     cudaFree(ctx->hits); ctx->hits = nullptr;
     ctx->chunk_cap = 0;
@@ -194,7 +194,8 @@ pt_status ensure_scratch(pt_ctx* ctx, uint32_t chunk)
             return fail(ctx, PT_ENOMEM, "wavefront queue allocation failed");
         }
     }
-    if (dalloc(&ctx->esc, chunk) || dalloc(&ctx->slot_L, (size_t)chunk * 3) || dalloc(&ctx->hits, chunk)) {
+    if (dalloc(&ctx->esc.uv, chunk) || dalloc(&ctx->esc.tp, chunk) || dalloc(&ctx->slot_L, (size_t)chunk * 3) ||
+        dalloc(&ctx->hits, chunk)) {
         free_scratch(ctx);
         return fail(ctx, PT_ENOMEM, "escape queue allocation failed");
     }

@@ -64,9 +64,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_nif_fp32(const NifEvalParams p,
                 const float2 uv = reinterpret_cast<const float2*>(p.uv)[g];
                 u = uv.x; v = uv.y;
             } else {
-                const float2* e = reinterpret_cast<const float2*>(p.esc + g);
-                const float2 a = e[0], b = e[1], c = e[2];
-                slot = __float_as_uint(a.x); u = a.y; v = b.x; tr = b.y; tg = c.x; tb = c.y;
+                const float2 uv = p.esc.uv[g];
+                const float4 tp = p.esc.tp[g];
+                slot = __float_as_uint(tp.w); u = uv.x; v = uv.y; tr = tp.x; tg = tp.y; tb = tp.z;
             }
         }
         if (row_thread) {

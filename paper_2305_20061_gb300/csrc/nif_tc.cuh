@@ -163,7 +163,7 @@ struct TcParams {
     float* rgb;
     int64_t n;
     // mode 1
-    const EscapeRec* esc;
+    EscapeQueue esc;
     const uint32_t* esc_count;
     uint32_t esc_cap;
     float* slot_L;
@@ -358,9 +358,9 @@ __global__ void __launch_bounds__(Layout<F, H, L, S>::threads, 1) k_nif_tc(const
                 const float2 q = reinterpret_cast<const float2*>(p.uv)[gg];
                 t.u = q.x; t.v = q.y;
             } else {
-                const float2* e = reinterpret_cast<const float2*>(p.esc + gg);
-                const float2 a = e[0], b = e[1], c = e[2];
-                t.slot = __float_as_uint(a.x); t.u = a.y; t.v = b.x; t.tr = b.y; t.tg = c.x; t.tb = c.y;
+                const float2 uv = p.esc.uv[gg];
+                const float4 tp = p.esc.tp[gg];
+                t.slot = __float_as_uint(tp.w); t.u = uv.x; t.v = uv.y; t.tr = tp.x; t.tg = tp.y; t.tb = tp.z;
             }
         }
         return t;

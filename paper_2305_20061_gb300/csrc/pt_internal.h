@@ -90,13 +90,14 @@ struct DevScene {
     int32_t has_emission;
 };
 
-// Escape record handed from the shading kernel to the NIF kernel (24 B).
-struct EscapeRec {
-    uint32_t slot;          // chunk-relative path index
-    float u, v;             // equirect coordinates of the escape direction
-    float tr, tg, tb;       // path throughput
+// Escape queue handed from the shading kernel to the NIF kernel, as two
+// arrays (24 B per escape): the NIF loads each part of an escape with one
+// coalesced vector load per lane, not three 8-byte loads at a 24-byte stride.
+struct EscapeQueue {
+    float2* uv;             // [i] equirect (u, v) of the escape direction
+    float4* tp;             // [i] path throughput (x, y, z) and the chunk-relative slot (w, as the uint32 bits)
 };
-static_assert(sizeof(EscapeRec) == 24, "escape record");
+constexpr size_t kEscapeBytes = sizeof(float2) + sizeof(float4);
 
 // Ray queue in structure-of-arrays form (one float4 stream per field).
 struct RayQueue {
@@ -126,7 +127,7 @@ struct BounceParams {
     RayQueue qout;
     uint32_t* count_out;
     uint32_t cap;
-    EscapeRec* esc;
+    EscapeQueue esc;
     uint32_t* esc_count;
     float* slot_L;          // [n_chunk][3]
     int32_t* hit_ids;       // nullable [global slot][max_depth]
@@ -186,7 +187,7 @@ struct NifEvalParams {
     float* rgb;
     int64_t n;
     // mode 1: escape records -> slot radiance += tp * rgb
-    const EscapeRec* esc;
+    EscapeQueue esc;
     const uint32_t* esc_count;
     uint32_t esc_cap;
     float* slot_L;

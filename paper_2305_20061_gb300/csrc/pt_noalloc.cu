@@ -32,7 +32,7 @@ namespace {
 constexpr uint32_t kMaxSlots = 1u << 18;   // paths per chunk; the frame must have <= this many pixels
 constexpr int kMaxDepthNA = 64;
 constexpr size_t kHeaderBytes = 2048;      // counters (128 x u32), stats (65 x u64), error word
-constexpr size_t kBytesPerSlot = 2 * 4 * sizeof(float4) + sizeof(EscapeRec) + sizeof(int2) + 3 * sizeof(float);  // 172
+constexpr size_t kBytesPerSlot = 2 * 4 * sizeof(float4) + kEscapeBytes + sizeof(int2) + 3 * sizeof(float);  // 172
 constexpr size_t kScratchBytes = kHeaderBytes + (size_t)kMaxSlots * kBytesPerSlot;            // ~43 MiB
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -101,7 +101,9 @@ extern "C" PT_API pt_status pt_render_noalloc(const pt_scene* scene, const pt_ni
         qq.tp = reinterpret_cast<float4*>(p); p += (size_t)kMaxSlots * sizeof(float4);
         qq.L = reinterpret_cast<float4*>(p); p += (size_t)kMaxSlots * sizeof(float4);
     }
-    EscapeRec* esc = reinterpret_cast<EscapeRec*>(p); p += (size_t)kMaxSlots * sizeof(EscapeRec);
+    EscapeQueue esc;
+    esc.uv = reinterpret_cast<float2*>(p); p += (size_t)kMaxSlots * sizeof(float2);
+    esc.tp = reinterpret_cast<float4*>(p); p += (size_t)kMaxSlots * sizeof(float4);
     int2* hits = reinterpret_cast<int2*>(p); p += (size_t)kMaxSlots * sizeof(int2);
     float* slot_L = reinterpret_cast<float*>(p);
 

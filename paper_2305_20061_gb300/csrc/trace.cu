@@ -424,10 +424,8 @@ __device__ __forceinline__ uint32_t active_append(uint32_t* counter)
 __device__ __forceinline__ void push_escape(const BounceParams& p, uint32_t ei, const PathState& s, float eu, float ev)
 {
     if (ei < p.cap) {
-        float2* dst = reinterpret_cast<float2*>(p.esc + ei);
-        dst[0] = make_float2(__uint_as_float(s.slot), eu);
-        dst[1] = make_float2(ev, s.tp.x);
-        dst[2] = make_float2(s.tp.y, s.tp.z);
+        p.esc.uv[ei] = make_float2(eu, ev);
+        p.esc.tp[ei] = make_float4(s.tp.x, s.tp.y, s.tp.z, __uint_as_float(s.slot));
     } else {
         atomicOr(p.err, PT_ERR_QUEUE_OVERFLOW);
     }
