@@ -149,6 +149,21 @@ pt_status fail(pt_ctx* ctx, pt_status st, const std::string& msg)
     return st;
 }
 
+// Runs the body of an entry point that builds large host arrays or starts host
+// threads: a failed host allocation or thread start becomes PT_ENOMEM instead
+// of an exception crossing the C ABI.
+template <class F>
+pt_status no_throw(pt_ctx* ctx, F&& body)
+{
+    try {
+        return body();
+    } catch (const std::bad_alloc&) {
+        return fail(ctx, PT_ENOMEM, "host allocation failed");
+    } catch (const std::exception& e) {
+        return fail(ctx, PT_ENOMEM, std::string("host resources exhausted: ") + e.what());
+    }
+}
+
 pt_status cuda_fail(pt_ctx* ctx, cudaError_t e, const char* what)
 {
     (void)cudaGetLastError();   // consume a non-sticky error so that it is not reported again by the next call
@@ -421,7 +436,7 @@ PT_API uint32_t pt_device_error_bits(pt_ctx* ctx)
 }
 
 // ---------------------------------------------------------------------------
-PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene** out)
+static pt_status create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene** out)
 {
     if (!ctx || !d || !out) return fail(ctx, PT_EINVAL, "null argument");
     *out = nullptr;
@@ -616,6 +631,11 @@ PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene**
     return PT_OK;
 }
 
+PT_API pt_status pt_create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene** out)
+{
+    return no_throw(ctx, [&] { return create_scene(ctx, d, out); });
+}
+
 PT_API void pt_destroy_scene(pt_scene* sc)
 {
     if (!sc) return;
@@ -630,7 +650,7 @@ PT_API pt_status pt_scene_get_info(const pt_scene* sc, pt_scene_info* info)
     return PT_OK;
 }
 
-PT_API pt_status pt_build_bvh_host(int64_t n, const float* lo, const float* hi, uint32_t* nodes, int64_t cap,
+static pt_status build_bvh_host(int64_t n, const float* lo, const float* hi, uint32_t* nodes, int64_t cap,
                                    int64_t* n_nodes, uint32_t* root, int32_t* depth)
 {
     if (n < 0 || !n_nodes || !root || !depth || (n > 0 && (!lo || !hi))) return PT_EINVAL;
@@ -653,7 +673,13 @@ PT_API pt_status pt_build_bvh_host(int64_t n, const float* lo, const float* hi, 
     return PT_OK;
 }
 
-PT_API pt_status pt_quantize_bvh_host(int64_t n_nodes, const uint32_t* nodes, uint32_t* out)
+PT_API pt_status pt_build_bvh_host(int64_t n, const float* lo, const float* hi, uint32_t* nodes, int64_t cap,
+                                   int64_t* n_nodes, uint32_t* root, int32_t* depth)
+{
+    return no_throw(nullptr, [&] { return build_bvh_host(n, lo, hi, nodes, cap, n_nodes, root, depth); });
+}
+
+static pt_status quantize_bvh_host(int64_t n_nodes, const uint32_t* nodes, uint32_t* out)
 {
     if (n_nodes < 0 || (n_nodes > 0 && (!nodes || !out))) return PT_EINVAL;
     NodeVec in((size_t)n_nodes);
@@ -663,6 +689,11 @@ PT_API pt_status pt_quantize_bvh_host(int64_t n_nodes, const uint32_t* nodes, ui
     if (!quantize_bvh(in.data(), in.size(), q, &err)) return PT_EUNSUPPORTED;
     if (n_nodes) std::memcpy(out, q.data(), (size_t)n_nodes * sizeof(QuantNode));
     return PT_OK;
+}
+
+PT_API pt_status pt_quantize_bvh_host(int64_t n_nodes, const uint32_t* nodes, uint32_t* out)
+{
+    return no_throw(nullptr, [&] { return quantize_bvh_host(n_nodes, nodes, out); });
 }
 
 PT_API pt_status pt_scene_download_bvh(pt_ctx* ctx, const pt_scene* sc, uint32_t* nodes, uint32_t* root)
@@ -675,7 +706,7 @@ PT_API pt_status pt_scene_download_bvh(pt_ctx* ctx, const pt_scene* sc, uint32_t
 }
 
 // ---------------------------------------------------------------------------
-PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
+static pt_status load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
 {
     if (!ctx || !d || !out || !d->params) return fail(ctx, PT_EINVAL, "null argument");
     *out = nullptr;
@@ -758,6 +789,11 @@ PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
     nf->fp8_ok = F == 64 && H == 128 && L == 3 && S == 0;
     *out = nf;
     return PT_OK;
+}
+
+PT_API pt_status pt_load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
+{
+    return no_throw(ctx, [&] { return load_nif(ctx, d, out); });
 }
 
 PT_API void pt_destroy_nif(pt_nif* nf)
@@ -1094,7 +1130,7 @@ bool adam_cfg_ok(float lr, float b1, float b2, float eps)
 
 }  // namespace
 
-PT_API pt_status pt_create_cache(pt_ctx* ctx, const pt_cache_desc* d, pt_cache** out)
+static pt_status create_cache(pt_ctx* ctx, const pt_cache_desc* d, pt_cache** out)
 {
     if (!ctx || !d || !out || !d->params) return fail(ctx, PT_EINVAL, "null argument");
     *out = nullptr;
@@ -1140,6 +1176,11 @@ PT_API pt_status pt_create_cache(pt_ctx* ctx, const pt_cache_desc* d, pt_cache**
     }
     *out = c;
     return PT_OK;
+}
+
+PT_API pt_status pt_create_cache(pt_ctx* ctx, const pt_cache_desc* d, pt_cache** out)
+{
+    return no_throw(ctx, [&] { return create_cache(ctx, d, out); });
 }
 
 PT_API void pt_destroy_cache(pt_cache* c)
