@@ -20,6 +20,12 @@
  *    overflow, non-finite radiance, a bounded wait that gave up) set bits in
  *    the context's device error word and are reported by pt_check().  No
  *    kernel traps or asserts.
+ *  - Calls that create objects from host arrays (pt_create_scene,
+ *    pt_load_nif, pt_create_cache) copy them on a stream of the context's own
+ *    that does not wait for other streams, and return once the copy is
+ *    complete: they do not wait for renders still running, so the next
+ *    scene or network can be built while the GPU works.  The pt_destroy_*
+ *    calls free device memory with cudaFree, which waits for the device.
  *  - Every call returns a pt_status; on failure pt_last_error() describes it.
  *    No exception or exit() crosses this boundary.
  *  - A context is used by one host thread at a time.

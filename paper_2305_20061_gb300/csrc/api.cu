@@ -35,6 +35,9 @@ struct pt_ctx {
     uint32_t cache_cap = 0;
     int last_depth = 0;
     int last_schedule = PT_SCHED_AUTO;    // schedule the last render's last chunk ran with
+    // non-blocking stream of the host-array uploads (scene, weights, cache): an upload does not wait for
+    // renders queued on the caller's streams, so the next scene can be built while the GPU renders
+    cudaStream_t upload = nullptr;
     // kernel timing (pt_profile_enable)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;      // pairs: start, stop
@@ -147,6 +150,16 @@ pt_status fail(pt_ctx* ctx, pt_status st, const std::string& msg)
     // check would report it: consume it here
     if (st == PT_ENOMEM) (void)cudaGetLastError();
     return st;
+}
+
+// Copies host memory to the device on the context's upload stream and waits
+// for it: the copy is complete on return, and it does not wait for work queued
+// on the legacy default stream or the caller's streams.
+cudaError_t upload_host(pt_ctx* ctx, void* dst, const void* src, size_t bytes)
+{
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->upload);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->upload);
+    return e;
 }
 
 // Runs the body of an entry point that builds large host arrays or starts host
@@ -366,6 +379,7 @@ PT_API pt_status pt_create(pt_ctx** out, int device)
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->stats, kStats * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(ctx->stats, 0, kStats * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_first_sample, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->upload, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
         for (int f = 0; f < 3; ++f) ctx->paths_threads[f] = paths_resident_threads(f, ctx->sm_count);
     }
@@ -377,6 +391,7 @@ PT_API pt_status pt_create(pt_ctx** out, int device)
         cudaFree(ctx->counters);
         cudaFree(ctx->stats);
         cudaFree(ctx->d_first_sample);
+        if (ctx->upload) cudaStreamDestroy(ctx->upload);
         delete ctx;
         return PT_ECUDA;
     }
@@ -392,6 +407,7 @@ PT_API void pt_destroy(pt_ctx* ctx)
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
     for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->upload) cudaStreamDestroy(ctx->upload);
     cudaFree(ctx->d_err);
     cudaFree(ctx->counters);
     cudaFree(ctx->stats);
@@ -590,10 +606,10 @@ static pt_status create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene** ou
         std::vector<unsigned char> stage(total);
         for (const Segment& g : seg)
             if (g.bytes) std::memcpy(stage.data() + g.off, g.src, g.bytes);
-        ok = cudaMemcpy(arena, stage.data(), total, cudaMemcpyHostToDevice) == cudaSuccess;
+        ok = upload_host(ctx, arena, stage.data(), total) == cudaSuccess;
     } else {
         for (const Segment& g : seg)
-            if (ok && g.bytes) ok = cudaMemcpy(arena + g.off, g.src, g.bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+            if (ok && g.bytes) ok = upload_host(ctx, arena + g.off, g.src, g.bytes) == cudaSuccess;
     }
     if (!ok) {
         pt_destroy_scene(sc);
@@ -773,7 +789,7 @@ static pt_status load_nif(pt_ctx* ctx, const pt_nif_desc* d, pt_nif** out)
         std::memcpy(stage.data(), d->params, (size_t)n * sizeof(float));
         std::memcpy(stage.data() + b_params, pk.data(), fp32_floats * sizeof(float));
         if (tc) std::memcpy(stage.data() + b_params + b_fp32, img.data(), img.size());
-        if (cudaMemcpy(nf->d_arena, stage.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (upload_host(ctx, nf->d_arena, stage.data(), total) != cudaSuccess) {
             pt_destroy_nif(nf);
             return fail(ctx, PT_ECUDA, "NIF upload failed");
         }
@@ -1162,7 +1178,7 @@ static pt_status create_cache(pt_ctx* ctx, const pt_cache_desc* d, pt_cache** ou
         c->box_hi[a] = d->hi[a];
     }
     if (cudaMalloc((void**)&c->d_params, np * sizeof(float)) != cudaSuccess ||
-        cudaMemcpy(c->d_params, d->params, np * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+        upload_host(ctx, c->d_params, d->params, np * sizeof(float)) != cudaSuccess) {
         pt_destroy_cache(c);
         return fail(ctx, PT_ENOMEM, "cache parameter upload failed");
     }
