@@ -27,28 +27,28 @@ def ctx(pt):
 
 
 def test_objects_built_during_a_render_give_the_same_images(pt, ctx):
-    cfg = I.RenderCfg(256, 256, 64, 8)
+    cfg_a, cfg_b = I.RenderCfg(256, 256, 512, 8), I.RenderCfg(256, 256, 16, 8)   # a: about 13 ms of GPU work
     sa, sb = I.spheres_scene(256, seed=0), I.spheres_scene(256, seed=3)
     na, nb = I.nif_init(colour="yuv", seed=0), I.nif_init(colour="yuv", seed=4)
     # the plain sequence
-    ref_a = pt.render(ctx, pt.Scene(ctx, sa), pt.Nif(ctx, na), cfg, "bf16").clone()
-    ref_b = pt.render(ctx, pt.Scene(ctx, sb), pt.Nif(ctx, nb), cfg, "bf16").clone()
+    ref_a = pt.render(ctx, pt.Scene(ctx, sa), pt.Nif(ctx, na), cfg_a, "bf16").clone()
+    ref_b = pt.render(ctx, pt.Scene(ctx, sb), pt.Nif(ctx, nb), cfg_b, "bf16").clone()
     torch.cuda.synchronize()
     ctx.check()
     # b's scene and weights built and uploaded while a renders
     s_a, n_a = pt.Scene(ctx, sa), pt.Nif(ctx, na)
-    img_a = pt.render(ctx, s_a, n_a, cfg, "bf16")
+    img_a = pt.render(ctx, s_a, n_a, cfg_a, "bf16")
     t0 = time.perf_counter()
     s_b, n_b = pt.Scene(ctx, sb), pt.Nif(ctx, nb)
     t_build = time.perf_counter() - t0
-    img_b = pt.render(ctx, s_b, n_b, cfg, "bf16")
+    img_b = pt.render(ctx, s_b, n_b, cfg_b, "bf16")
     torch.cuda.synchronize()
     t_all = time.perf_counter() - t0
     ctx.check()
     assert torch.equal(img_a, ref_a) and torch.equal(img_b, ref_b)
     print({"build_ms": 1e3 * t_build, "build_and_render_ms": 1e3 * t_all})
     # building b took a small part of the time a's render still had to run (it did not wait for it)
-    assert t_build < 0.5 * t_all
+    assert t_build < 0.25 * t_all
 
 
 def test_scene_destroyed_after_its_render_completes(pt, ctx):
