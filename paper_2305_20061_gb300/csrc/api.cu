@@ -232,13 +232,6 @@ pt_status ensure_scratch(pt_ctx* ctx, uint32_t chunk)
     return PT_OK;
 }
 
-float half_to_float_host(uint16_t bits)
-{
-    __half h;
-    std::memcpy(&h, &bits, 2);
-    return __half2float(h);
-}
-
 bool finite3(const float* p, int64_t n)
 {
     for (int64_t i = 0; i < n; ++i)
@@ -556,23 +549,24 @@ static pt_status create_scene(pt_ctx* ctx, const pt_scene_desc* d, pt_scene** ou
     std::vector<float> wide;
     if (!bo.nodes.empty() && want_wide) {
         wide.assign(bo.nodes.size() * 16, 0.f);
-        for (size_t i = 0; i < bo.nodes.size(); ++i) {
-            const uint32_t* w = bo.nodes[i].w;
-            float lo[6], hi[6];
-            for (int a = 0; a < 6; ++a) std::memcpy(&lo[a], &w[a], 4);
-            const uint16_t ext[6] = {(uint16_t)(w[6] & 0xFFFFu), (uint16_t)(w[6] >> 16), (uint16_t)(w[7] & 0xFFFFu),
-                                     (uint16_t)(w[7] >> 16), (uint16_t)(w[8] & 0xFFFFu), (uint16_t)(w[8] >> 16)};
-            for (int a = 0; a < 6; ++a) {
-                volatile float top = lo[a] + half_to_float_host(ext[a]);   // FP32 add, as the device does
-                hi[a] = top;
+        const int64_t n_nodes = (int64_t)bo.nodes.size();
+        for_chunks(0, n_nodes, host_pass_threads(n_nodes), [&](int, int64_t i0, int64_t i1) {
+            for (int64_t i = i0; i < i1; ++i) {
+                const uint32_t* w = bo.nodes[(size_t)i].w;
+                float lo[6], hi[6];
+                for (int a = 0; a < 6; ++a) std::memcpy(&lo[a], &w[a], 4);
+                const uint16_t ext[6] = {(uint16_t)(w[6] & 0xFFFFu), (uint16_t)(w[6] >> 16),
+                                         (uint16_t)(w[7] & 0xFFFFu), (uint16_t)(w[7] >> 16),
+                                         (uint16_t)(w[8] & 0xFFFFu), (uint16_t)(w[8] >> 16)};
+                for (int a = 0; a < 6; ++a) hi[a] = lo[a] + half_bits_to_float(ext[a]);   // FP32 add, as the device does
+                float* o = &wide[16 * (size_t)i];
+                o[0] = lo[0]; o[1] = lo[1]; o[2] = lo[2]; o[3] = hi[0];
+                o[4] = hi[1]; o[5] = hi[2]; o[6] = lo[3]; o[7] = lo[4];
+                o[8] = lo[5]; o[9] = hi[3]; o[10] = hi[4]; o[11] = hi[5];
+                std::memcpy(&o[12], &w[9], 4);
+                std::memcpy(&o[13], &w[10], 4);
             }
-            float* o = &wide[16 * i];
-            o[0] = lo[0]; o[1] = lo[1]; o[2] = lo[2]; o[3] = hi[0];
-            o[4] = hi[1]; o[5] = hi[2]; o[6] = lo[3]; o[7] = lo[4];
-            o[8] = lo[5]; o[9] = hi[3]; o[10] = hi[4]; o[11] = hi[5];
-            std::memcpy(&o[12], &w[9], 4);
-            std::memcpy(&o[13], &w[10], 4);
-        }
+        });
     }
 
     // one device arena per scene (one allocation; small scenes also one copy)

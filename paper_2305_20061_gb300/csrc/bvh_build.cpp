@@ -78,9 +78,41 @@ struct CenBounds {
     }
 };
 
+// Bins of one split, filled lazily: a bin's box and count are valid only
+// where its bit in `used` is set, so a split of a few primitives does not
+// initialise 48 boxes.
 struct Bins {
     Box bb[3][kBins];
-    int64_t cnt[3][kBins] = {};
+    int64_t cnt[3][kBins];
+    uint32_t used[3] = {0, 0, 0};
+    void add(int a, int k, const Prim& q)
+    {
+        const uint32_t bit = 1u << k;
+        if (used[a] & bit) {
+            cnt[a][k]++;
+            bb[a][k].grow(q.lo, q.hi);
+        } else {
+            used[a] |= bit;
+            cnt[a][k] = 1;
+            bb[a][k] = Box();
+            bb[a][k].grow(q.lo, q.hi);
+        }
+    }
+    void merge(const Bins& o)   // exact: integer counts, min and max
+    {
+        for (int a = 0; a < 3; ++a)
+            for (uint32_t m = o.used[a]; m; m &= m - 1) {
+                const int k = __builtin_ctz(m);
+                if (used[a] & (1u << k)) {
+                    cnt[a][k] += o.cnt[a][k];
+                    bb[a][k].grow(o.bb[a][k]);
+                } else {
+                    used[a] |= 1u << k;
+                    cnt[a][k] = o.cnt[a][k];
+                    bb[a][k] = o.bb[a][k];
+                }
+            }
+    }
 };
 
 // What the builders of one tree share.  Each works on its own range [b, e)
@@ -180,60 +212,44 @@ struct Builder {
                 const bool lv[3] = {live[0], live[1], live[2]};
                 for (int64_t i = lo; i < hi; ++i) {
                     const Prim q = P[i];   // a copy: the bin updates cannot change it
-                    for (int a = 0; a < 3; ++a) {
-                        if (!lv[a]) continue;
-                        const int k = bo(q, a);
-                        acc.cnt[a][k]++;
-                        acc.bb[a][k].grow(q.lo, q.hi);
-                    }
+                    for (int a = 0; a < 3; ++a)
+                        if (lv[a]) acc.add(a, bo(q, a), q);
                 }
             });
-            for (const Bins& p : part)
-                for (int a = 0; a < 3; ++a)
-                    for (int k = 0; k < kBins; ++k) {
-                        bins.cnt[a][k] += p.cnt[a][k];
-                        bins.bb[a][k].grow(p.bb[a][k]);
-                    }
+            for (const Bins& p : part) bins.merge(p);
         }
+        // SAH over the split positions between non-empty bins: every position between two neighbouring
+        // non-empty bins gives the same two children and the same cost, so the sweep visits one per
+        // group (the highest, where a sweep over all 15 positions from the top meets each group first)
         double best_cost = INFINITY;
         int best_axis = -1, best_bin = -1;
         for (int a = 0; a < 3; ++a) {
             if (!live[a]) continue;
-            // an empty bin leaves the running box and count unchanged, so its area is carried over
-            // instead of recomputed (same values, fewer operations on small ranges)
+            int ks[kBins], nk = 0;   // the non-empty bins, ascending
+            for (uint32_t m = bins.used[a]; m; m &= m - 1) ks[nk++] = __builtin_ctz(m);
             double left_area[kBins];
             int64_t left_cnt[kBins];
             Box acc;
             int64_t c = 0;
-            double area = 0.0;
-            for (int k = 0; k < kBins - 1; ++k) {
-                if (bins.cnt[a][k]) {
-                    acc.grow(bins.bb[a][k]);
-                    c += bins.cnt[a][k];
-                    area = acc.area();
-                }
-                left_area[k] = area;
-                left_cnt[k] = c;
+            for (int j = 0; j + 1 < nk; ++j) {
+                acc.grow(bins.bb[a][ks[j]]);
+                c += bins.cnt[a][ks[j]];
+                left_area[j] = acc.area();
+                left_cnt[j] = c;
             }
             Box racc;
             int64_t rc = 0;
-            double rarea = 0.0;
-            for (int k = kBins - 1; k >= 1; --k) {
-                if (bins.cnt[a][k]) {
-                    racc.grow(bins.bb[a][k]);
-                    rc += bins.cnt[a][k];
-                    rarea = racc.area();
-                }
-                const int64_t lc = left_cnt[k - 1];
-                if (lc == 0 || rc == 0) continue;
-                const double cost = left_area[k - 1] * (double)lc + rarea * (double)rc;
-                if (cost < best_cost) { best_cost = cost; best_axis = a; best_bin = k; }
+            for (int j = nk - 1; j >= 1; --j) {
+                racc.grow(bins.bb[a][ks[j]]);
+                rc += bins.cnt[a][ks[j]];
+                const double cost = left_area[j - 1] * (double)left_cnt[j - 1] + racc.area() * (double)rc;
+                if (cost < best_cost) { best_cost = cost; best_axis = a; best_bin = ks[j]; }
             }
         }
         if (best_axis < 0) return b + n / 2;   // no usable split (all centroids coincide): halve the list
         const int a = best_axis;
         int64_t n_left = 0;
-        for (int k = 0; k < best_bin; ++k) n_left += bins.cnt[a][k];
+        for (uint32_t m = bins.used[a] & ((1u << best_bin) - 1u); m; m &= m - 1) n_left += bins.cnt[a][__builtin_ctz(m)];
         const int64_t mid = b + n_left;
         struct Left {
             float o, s;
@@ -302,7 +318,10 @@ struct Builder {
             }
             std::swap(*src, *dst);
         }
-        for (int k = 0; k < kBins; ++k) (k < best_bin ? *bl : *br).grow(bins.bb[a][k]);
+        for (uint32_t m = bins.used[a]; m; m &= m - 1) {
+            const int k = __builtin_ctz(m);
+            (k < best_bin ? *bl : *br).grow(bins.bb[a][k]);
+        }
         *known = true;
         return mid;
     }
@@ -369,20 +388,58 @@ struct Builder {
 // Smallest fp16 extent h >= 0 such that lo + float(h), evaluated in fp32,
 // is >= hi: the decoded box then contains [lo, hi] ("round-to-nearest-not-
 // lower").  Fails if no finite half qualifies.
+// IEEE 754 binary16, non-negative values only (1 sign bit, 5 exponent bits
+// biased by 15, 10 fraction bits; exponent field 0: subnormal m * 2^-24,
+// field 31: infinity or NaN).
+float half_bits_to_float(uint16_t h)
+{
+    const uint32_t e = (h >> 10) & 0x1Fu, m = h & 0x3FFu;
+    if (e == 0) return (float)m * 5.9604644775390625e-8f;   // m * 2^-24, exact in fp32
+    if (e == 31) return INFINITY;
+    const uint32_t bits = ((e - 15u + 127u) << 23) | (m << 13);
+    float f;
+    std::memcpy(&f, &bits, 4);
+    return f;
+}
+
+namespace {
+
+// the smallest binary16 value >= x, for 0 <= x <= 65504, from the bits of the double
+uint16_t half_at_least(double x)
+{
+    if (!(x > 0.0)) return 0;
+    uint64_t b;
+    std::memcpy(&b, &x, 8);
+    const int ex = (int)((b >> 52) & 0x7FFu) - 1023;
+    if (ex < -1022) return 1;                                          // double subnormal: far below 2^-24
+    const uint64_t sig = (b & ((1ull << 52) - 1)) | (1ull << 52);     // x = sig * 2^(ex - 52)
+    if (ex < -14) {
+        // half subnormal: ceil(x 2^24) = ceil(sig / 2^(28 - ex)); 1024 is the smallest normal half's pattern
+        const int sh = 28 - ex;
+        if (sh >= 64) return 1;
+        return (uint16_t)((sig >> sh) + ((sig & ((1ull << sh) - 1)) != 0));
+    }
+    uint64_t m = (sig >> 42) + ((sig & ((1ull << 42) - 1)) != 0);   // 1 + 10 fraction bits, rounded up
+    int E = ex;
+    if (m == 2048) {
+        m = 1024;
+        ++E;
+    }
+    return (uint16_t)(((uint32_t)(E + 15) << 10) | (uint32_t)(m - 1024));
+}
+
+}  // namespace
+
 bool round_up_half_extent(float lo, float hi, uint16_t* out_bits)
 {
     const double ext = std::max(0.0, (double)hi - (double)lo);
     if (!(ext <= 65504.0)) return false;
-    __half h = __float2half_rn((float)ext);
-    uint16_t bits;
-    std::memcpy(&bits, &h, 2);
+    uint16_t bits = half_at_least(ext);   // every smaller half is below the exact extent
     for (int guard = 0; guard < 64; ++guard) {
-        __half hh;
-        std::memcpy(&hh, &bits, 2);
-        const float e = __half2float(hh);
+        const float e = half_bits_to_float(bits);
         if (!std::isfinite(e)) return false;
-        volatile float top = lo + e;  // fp32 addition as the device performs it
-        if ((double)e >= ext && top >= hi) {
+        const float top = lo + e;  // fp32 addition as the device performs it
+        if (top >= hi) {
             *out_bits = bits;
             return true;
         }
@@ -399,9 +456,7 @@ void decode_packed_boxes(const PackedNode& n, float box[12])
         for (int a = 0; a < 3; ++a) {
             float lo;
             std::memcpy(&lo, &n.w[3 * c + a], 4);
-            __half h;
-            std::memcpy(&h, &ext[3 * c + a], 2);
-            volatile float top = lo + __half2float(h);   // fp32 addition as the device performs it
+            const float top = lo + half_bits_to_float(ext[3 * c + a]);   // fp32 addition as the device performs it
             box[6 * c + a] = lo;
             box[6 * c + 3 + a] = top;
         }

@@ -369,6 +369,8 @@ struct BuildOutput {
 // threads = 0: all hardware threads; the tree does not depend on the count
 bool build_bvh(const BuildInput& in, BuildOutput& out, unsigned threads = 0);
 bool round_up_half_extent(float lo, float hi, uint16_t* out_bits);
+// value of a non-negative IEEE binary16 bit pattern (fp16 extents of the packed nodes)
+float half_bits_to_float(uint16_t h);
 // The packed tree's children boxes as decoded on the device (fp32 origin + fp16 extent, fp32 sum):
 // box[0..2] lo_l, [3..5] hi_l, [6..8] lo_r, [9..11] hi_r.
 void decode_packed_boxes(const PackedNode& n, float box[12]);
