@@ -282,10 +282,11 @@ def bench_reference(args):
 
 def trace_kernels(pt, ctx, vertices):
     """Name of the traversal kernel of the last render (profile kind
-    "trace") and its launches per chunk: k_trace once per vertex on the
-    wavefront schedule (shading, k_bounce, is timed apart), one k_paths
-    launch (traversal and shading together) on the path-per-thread
-    schedule."""
+    "trace") and its launches per chunk: on the wavefront schedule one
+    traversal launch per vertex, labelled k_trace (the camera rays of a
+    whole image go through k_trace_camera, the warp-packet variant; shading,
+    k_bounce, is timed apart), one k_paths launch (traversal and shading
+    together) on the path-per-thread schedule."""
     if pt.last_render_schedule(ctx) == "paths":
         return "k_paths", 1
     return "k_trace", vertices
@@ -307,7 +308,8 @@ def traversal_roofline(work, t_ms, kernel, launches, ffma_tflops, clock, context
             "per_unit": f"FP32 FLOP per node fetch (two child slabs) {FLOP_NODE}, per sphere/quad/triangle test "
                         f"{FLOP_SPHERE}/{FLOP_QUAD}/{FLOP_TRI}; {work['nodes']} node fetches and "
                         f"{work['sphere']}/{work['quad']}/{work['triangle']} sphere/quad/triangle tests per frame "
-                        f"over {launches} launches, {t_ms:.3f} ms of {kernel} per frame{context}",
+                        f"over {launches} launches, {t_ms:.3f} ms of {kernel} per frame{context}"
+                        + (" (k_trace_camera traces the camera rays of a whole image)" if kernel == "k_trace" else ""),
             "peak_note": "FP32 FMA rate measured live by pt_microbench_ffma (8 chains per thread, 2048 threads "
                          "per SM, CUDA events)",
             "issue_frac": ops * 1e-12 / (t_ms * 1e-3) / issue_peak,
@@ -572,9 +574,10 @@ def bench_ours(args):
     if roof["kernel"] in ("k_trace", "k_paths"):
         roof["traffic"] = (trace_traffic(args.workload, NODE_FORMS[scene.info()["node_format"]], rays)
                            if trace_kernel == "k_trace" else None)
-        roof["traffic_note"] = ("DRAM bytes per frame of k_trace (all its launches), from the ncu capture in "
-                                "profiles/ scaled by traced rays; null when no capture of this workload matches "
-                                "the current traversal source")
+        roof["traffic_note"] = ("DRAM bytes per frame of the traversal launches (k_trace_camera at vertex 1 of a "
+                                "whole image, k_trace at the others), from the ncu capture in profiles/ scaled by "
+                                "traced rays; null when no capture of this workload matches the current traversal "
+                                "and BVH-builder source")
     # end to end through the C ABI with host buffers: scene + weights in, image out
     e2e = None
     if not args.no_e2e:
