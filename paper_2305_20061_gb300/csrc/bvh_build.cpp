@@ -347,9 +347,22 @@ struct Builder {
         if (depth < tr.par_depth && e - b >= kParallelSubtree) {
             Builder sub(tr);
             uint32_t sub_root = kEmptyRef;
-            std::thread th([&] { sub_root = sub.build(b, mid, depth + 1, at + 1, cbl, src, dst); });
+            auto left = [&] {
+                try {
+                    sub_root = sub.build(b, mid, depth + 1, at + 1, cbl, src, dst);
+                } catch (...) {
+                    sub.error = "host allocation failed in the BVH build";
+                }
+            };
+            std::thread th;
+            try {
+                th = std::thread(left);
+            } catch (...) {
+                // no thread to spare: the left subtree is built here, after the right one
+            }
             cr = build(mid, e, depth + 1, at + (uint32_t)(mid - b), cbr, src, dst);
-            th.join();
+            if (th.joinable()) th.join();
+            else left();
             cl = sub_root;
             max_depth = std::max(max_depth, sub.max_depth);
             if (!sub.error.empty()) error = sub.error;

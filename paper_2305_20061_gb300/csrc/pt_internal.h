@@ -334,7 +334,7 @@ struct NoInitAlloc : std::allocator<T> {
 using NodeVec = std::vector<PackedNode, NoInitAlloc<PackedNode>>;
 
 // f(t, lo, hi) over T contiguous chunks [b + n t / T, b + n (t + 1) / T) of [b, e), one host thread each
-// (the caller runs chunk 0)
+// (the caller runs chunk 0, and every chunk whose thread could not be started); f must not throw
 template <class F>
 void for_chunks(int64_t b, int64_t e, int T, F&& f)
 {
@@ -344,8 +344,17 @@ void for_chunks(int64_t b, int64_t e, int T, F&& f)
         return;
     }
     std::vector<std::thread> th;
-    th.reserve((size_t)T - 1);
-    for (int t = 1; t < T; ++t) th.emplace_back([&f, t, b, n, T] { f(t, b + n * t / T, b + n * (t + 1) / T); });
+    int started = 1;   // chunks 1 .. started - 1 have a thread
+    try {
+        th.reserve((size_t)T - 1);
+        for (int t = 1; t < T; ++t) {
+            th.emplace_back([&f, t, b, n, T] { f(t, b + n * t / T, b + n * (t + 1) / T); });
+            started = t + 1;
+        }
+    } catch (...) {
+        // out of threads or memory: the remaining chunks run here
+    }
+    for (int t = started; t < T; ++t) f(t, b + n * t / T, b + n * (t + 1) / T);
     f(0, b, b + n / T);
     for (auto& x : th) x.join();
 }
