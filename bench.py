@@ -73,15 +73,15 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # bvh_build.cpp, first 16 hex digits): the bytes depend on the kernel and on the tree it walks.
 TRACE_TRAFFIC = {
     # 1920x1080 at 8 spp = one full 2^24-path chunk of the 32-spp frame (profiles/k_trace_traffic_large_bvh_c4.md)
-    ("C4", "packed"): {"bytes_per_ray": 365.6, "src": "41346669d195e829"},
-    ("C4", "quant8"): {"bytes_per_ray": 284.7, "src": "41346669d195e829"},
+    ("C4", "packed"): {"bytes_per_ray": 366.0, "src": "b595122a4af8ee56"},
+    ("C4", "quant8"): {"bytes_per_ray": 284.6, "src": "b595122a4af8ee56"},
     # 512x512 at 64 spp, the full frame, one pass per launch (profiles/k_trace_traffic_spheres_c2.md)
-    ("C2", "decoded"): {"bytes_per_ray": 22.70, "src": "41346669d195e829"},
+    ("C2", "decoded"): {"bytes_per_ray": 22.69, "src": "b595122a4af8ee56"},
 }
 # L2 bytes (lts__t_bytes) of the traversal kernel per traced ray on the large tree, from the same captures
 TRACE_L2 = {
-    ("C4", "packed"): {"bytes_per_ray": 1638.2, "src": "41346669d195e829"},
-    ("C4", "quant8"): {"bytes_per_ray": 1276.6, "src": "41346669d195e829"},
+    ("C4", "packed"): {"bytes_per_ray": 1641.9, "src": "b595122a4af8ee56"},
+    ("C4", "quant8"): {"bytes_per_ray": 1279.1, "src": "b595122a4af8ee56"},
 }
 NODE_FORMS = {1: "packed", 2: "decoded", 3: "quant8"}
 TRACE_SOURCES = ("paper_2305_20061_gb300/csrc/trace.cu", "paper_2305_20061_gb300/csrc/device_common.cuh",
