@@ -203,3 +203,32 @@ def test_tiled_camera_order_same_paths(pt, ctx, schedule):
     ctx.check()
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("case", [("spheres", 64, 1), ("spheres", 512, 2), ("spheres", 2048, 3),
+                                  ("heightfield", 48, 4), ("heightfield", 96, 5), ("box", 0, 6)])
+def test_camera_packets_give_the_per_ray_hits(pt, ctx, case):
+    """Whole images, whose camera rays walk the tree as warp packets on the
+    wavefront schedule, against the path-per-thread schedule (every ray on
+    its own): per-path radiance, hit IDs and ray counts bit for bit over
+    scenes of several sizes and seeds (trees from 64 to 18,000 primitives,
+    spheres, triangles and quads)."""
+    kind, size, seed = case
+    if kind == "spheres":
+        sc = I.spheres_scene(size, seed)
+        env = "nif"
+    elif kind == "heightfield":
+        sc = I.heightfield_scene(size, n_spheres=16, seed=seed, env_const=(0.7, 0.8, 1.0))
+        env = None
+    else:
+        sc = I.box_scene(seed)
+        env = "nif"
+    cfg = I.RenderCfg(64, 48, 4, 6, seed=seed)
+    s = pt.Scene(ctx, sc)
+    g = pt.Nif(ctx, I.nif_init(seed=seed)) if env == "nif" else None
+    a, b, wa, wb = _both(pt, ctx, lambda sched: pt.render_pixels(ctx, s, g, cfg, None, want_slots=True,
+                                                                 want_ids=True, schedule=sched))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    assert a[-1][0] == cfg.width * cfg.height * cfg.spp
+    print({case: {"packets": wa, "per_ray": wb}})
